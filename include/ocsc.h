@@ -1,0 +1,164 @@
+/*
+ * ocsc.h -- C ABI of the GB300 (sm_103a) online convolutional sparse coding
+ * library (Wang, Yao, Kwok & Ni, "Scalable Online Convolutional Sparse Coding").
+ *
+ * The library runs the method's hot path on one GPU:
+ *   ocsc_code        -- per-sample code ADMM in the frequency domain
+ *                       (Sec. II-C.1 problem (fcsc_code); Sec. III-B.2 says
+ *                       codes are updated per sample as in batch CSC; ADMM
+ *                       template of Sec. II-B, eqs. (admm_aux), (admm_dual)).
+ *   ocsc_update_dict -- the online dictionary step of Algorithm 3: fold the
+ *                       new codes into the per-frequency history A^p, b^p
+ *                       (Sec. III-B, eqs. (A_update), (B_update)), then
+ *                       DictOCSC (Algorithm 2): the D-row solve of eq.
+ *                       (sub_d_sol) with C^p = (A^p + rho I)^-1 held as an FP64
+ *                       Cholesky factor, the support + unit-ball projection of
+ *                       Proposition 2 and the scaled dual update.
+ *   ocsc_get_dict    -- the filters D_t (Algorithm 3, last loop).
+ *
+ * Conventions (shared by every call):
+ *  - All image, code and filter arrays are float32, row-major.
+ *  - Images are square or rectangular H x W; each is zero-padded at the end of
+ *    both axes to an N x N FFT domain, N = the smallest supported size
+ *    >= max(H, W) + pad.  Convolution is circular on that domain and filters
+ *    occupy its top-left M x M corner.  Supported N: 64 and 128.
+ *  - lambda is the l1 weight (beta in the paper); rho is a spatial-domain
+ *    ADMM penalty used by both ADMMs (the paper's frequency-domain penalty
+ *    rho' of eq. (sub_d_sol) equals rho / P; opts.rho_convention = 1 uses the
+ *    printed A + rho*P*I instead).
+ *  - Device work is enqueued on the CUDA stream given to ocsc_init and is
+ *    asynchronous with respect to the host unless a call says it synchronises.
+ *  - Every call returns an ocsc_status; on failure ocsc_last_error() gives a
+ *    message.  Nothing aborts the process.  A context is not thread-safe.
+ *  - Ownership: the caller owns the images and code buffers it passes (they
+ *    must stay valid until the stream has finished the work); the library owns
+ *    all method state (dictionary spectra, duals, histories, factors,
+ *    workspaces) and frees it in ocsc_destroy.
+ */
+#ifndef OCSC_H
+#define OCSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ocsc_ctx ocsc_ctx;
+
+typedef enum {
+  OCSC_OK = 0,
+  OCSC_EINVAL = 1,       /* bad argument (null pointer, non-positive size ...) */
+  OCSC_ENOMEM = 2,       /* device allocation failed */
+  OCSC_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+  OCSC_ETIMEOUT = 4,     /* a bounded device wait gave up */
+  OCSC_ESTATE = 5,       /* call not valid in the current state */
+  OCSC_EUNSUPPORTED = 6, /* size or option outside what this build supports */
+  OCSC_ENUMERIC = 7      /* a factorisation met a non-positive pivot */
+} ocsc_status;
+
+typedef struct {
+  int Jz;             /* code-ADMM iterations per sample (default 50) */
+  int Jd;             /* dictionary-ADMM iterations per update (default 10) */
+  int pad;            /* zeros appended per axis before the FFT; -1 (default)
+                         means filter side - 1, so that the circular model has
+                         no wrap-around across the image boundary */
+  int max_batch;      /* most samples that may be pending between two
+                         ocsc_update_dict calls (default 1) */
+  int fft_size;       /* the FFT side N of this context: 64 or 128 (default
+                         128); every image must pad to exactly this size */
+  int warm_start;     /* 1 (default): V and the dual theta of DictOCSC carry
+                         over between updates; 0: restart at 0 each update as
+                         Algorithm 2 prints its initialisation */
+  int return_feasible;/* 1 (default): code against F(V_{t,J}) (feasible);
+                         0: against D~_{t,J} as Algorithm 2 returns it */
+  int rho_convention; /* 0 (default): D-row matrix A + rho I; 1: A + rho P I */
+  uint64_t seed;      /* seed of the Gaussian initial filters */
+} ocsc_opts;
+
+/* Fill *o with the defaults listed above. */
+void ocsc_default_opts(ocsc_opts *o);
+
+/*
+ * Create a context for K filters of filter_h x filter_w (square only:
+ * filter_h == filter_w = M, M <= 16; K <= 128), l1 weight lambda >= 0 and
+ * penalty rho > 0.  opts may be NULL (defaults).  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  The initial dictionary is
+ * Algorithm 3's Gaussian random initialisation: K x M x M N(0,1) draws from a
+ * splitmix64/Box-Muller generator seeded by opts->seed, each filter scaled to
+ * unit l2 norm; ocsc_set_dict replaces it.
+ * Allocates all device state (history and factor: 2 * F * K(K+1)/2 * 8 bytes
+ * with F = N * (N/2 + 1), N = opts.fft_size).  On failure *out is NULL and
+ * ocsc_last_error(NULL) gives the reason.
+ */
+ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double lambda,
+                      double rho, const ocsc_opts *opts, void *cuda_stream);
+
+/* Release every device and host resource of ctx (NULL is a no-op).
+ * Synchronises ctx's stream first. */
+void ocsc_destroy(ocsc_ctx *ctx);
+
+/* Padded FFT side N for an H x W image under ctx's pad policy. */
+ocsc_status ocsc_padded_size(const ocsc_ctx *ctx, int H, int W, int *N);
+
+/*
+ * Code n samples against the current dictionary (Algorithm 3, FFT and code
+ * steps).  x[i] is a DEVICE pointer to an H[i] x W[i] float image; u[i] is a
+ * DEVICE pointer to a caller-owned K x N x N float buffer that receives the
+ * sparse code U_i after the last U-step, or NULL to skip writing it.  x, H, W
+ * and u are HOST arrays of length n.  All n images must map to the same N.
+ * The last Z~-step of each sample and its spectrum stay pending inside the
+ * library for the next ocsc_update_dict; pending + n must not exceed
+ * opts.max_batch (OCSC_ESTATE otherwise).  Asynchronous.
+ */
+ocsc_status ocsc_code(ocsc_ctx *ctx, int n, const float *const *x, const int *H,
+                      const int *W, float *const *u);
+
+/*
+ * Fold every pending sample into the history (running mean over all samples
+ * seen) and run DictOCSC for Jd iterations.  No pending samples: no-op.
+ * Asynchronous; errors found on the device (non-positive pivot) are reported
+ * by the next synchronising call.
+ */
+ocsc_status ocsc_update_dict(ocsc_ctx *ctx);
+
+/*
+ * Copy the filters D_t (K x M x M floats) to HOST memory D_host and the
+ * dictionary version (number of completed updates) to *version (nullable).
+ * Synchronises ctx's stream and reports pending device-side errors.
+ */
+ocsc_status ocsc_get_dict(ocsc_ctx *ctx, float *D_host, uint64_t *version);
+
+/*
+ * Replace the dictionary with K x M x M floats from HOST memory.  normalize=1
+ * scales each filter to unit l2 norm (the initialisation of Algorithm 3);
+ * normalize=0 takes them as given (they must satisfy ||D_k|| <= 1).  Resets
+ * the DictOCSC dual to 0; the history is kept.  Synchronises.
+ */
+ocsc_status ocsc_set_dict(ocsc_ctx *ctx, const float *D_host, int normalize);
+
+/* Block until all work queued on ctx's stream is done; reports device errors. */
+ocsc_status ocsc_sync(ocsc_ctx *ctx);
+
+/* Message of the last failed call on ctx, or of the last failed ocsc_init on
+ * this thread when ctx is NULL (never NULL). */
+const char *ocsc_last_error(const ocsc_ctx *ctx);
+
+/*
+ * Building block: forward 2D DFT (the F of Sec. II-C, unnormalised) of
+ * `planes` real N x N float planes x (DEVICE, contiguous) into half spectra
+ * N x (N/2+1) of interleaved complex float X (DEVICE), N = ctx's fft_size.
+ * Enqueued on ctx's stream.
+ */
+ocsc_status ocsc_fft2_r2c(ocsc_ctx *ctx, const float *x, float *X, int planes);
+
+/* Building block: inverse of ocsc_fft2_r2c, including the 1/P factor.  The
+ * input half spectra must be those of real planes (Hermitian symmetric). */
+ocsc_status ocsc_fft2_c2r(ocsc_ctx *ctx, const float *X, float *x, int planes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OCSC_H */

@@ -1,0 +1,241 @@
+"""GB300-native online convolutional sparse coding (OCSC) -- Python binding.
+
+A thin ctypes layer over ``libocsc.so`` (the C ABI declared in
+``include/ocsc.h``).  Every step of the method runs in the library's CUDA
+kernels; this module only marshals pointers, sizes and the CUDA stream.  There
+is no CPU fallback: if the library is missing or no GPU is present, calls fail
+loudly.
+
+Low-level functions carry the C names (``ocsc_init``, ``ocsc_code``, ...);
+:class:`OCSC` wraps them for torch CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libocsc.so")
+
+STATUS = {
+    0: "OCSC_OK", 1: "OCSC_EINVAL", 2: "OCSC_ENOMEM", 3: "OCSC_ECUDA", 4: "OCSC_ETIMEOUT",
+    5: "OCSC_ESTATE", 6: "OCSC_EUNSUPPORTED", 7: "OCSC_ENUMERIC",
+}
+
+
+class OCSCError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class ocsc_opts(ctypes.Structure):
+    _fields_ = [
+        ("Jz", ctypes.c_int), ("Jd", ctypes.c_int), ("pad", ctypes.c_int),
+        ("max_batch", ctypes.c_int), ("fft_size", ctypes.c_int), ("warm_start", ctypes.c_int),
+        ("return_feasible", ctypes.c_int), ("rho_convention", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_PROTOS = {
+    "ocsc_default_opts": (None, [ctypes.POINTER(ocsc_opts)]),
+    "ocsc_init": (_I, [ctypes.POINTER(_P), _I, _I, _I, ctypes.c_double, ctypes.c_double,
+                       ctypes.POINTER(ocsc_opts), _P]),
+    "ocsc_destroy": (None, [_P]),
+    "ocsc_padded_size": (_I, [_P, _I, _I, ctypes.POINTER(_I)]),
+    "ocsc_code": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                       ctypes.POINTER(_P)]),
+    "ocsc_update_dict": (_I, [_P]),
+    "ocsc_get_dict": (_I, [_P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "ocsc_set_dict": (_I, [_P, _P, _I]),
+    "ocsc_sync": (_I, [_P]),
+    "ocsc_last_error": (ctypes.c_char_p, [_P]),
+    "ocsc_fft2_r2c": (_I, [_P, _P, _P, _I]),
+    "ocsc_fft2_c2r": (_I, [_P, _P, _P, _I]),
+}
+EXPORTED = tuple(_PROTOS)
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libocsc.so (fails loudly if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; g.build()\"`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _PROTOS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(ctx, status: int):
+    if status != 0:
+        msg = lib().ocsc_last_error(ctx)
+        raise OCSCError(status, msg.decode() if msg else "")
+
+
+# --- low-level functions with the C names ------------------------------------
+
+def ocsc_default_opts() -> ocsc_opts:
+    o = ocsc_opts()
+    lib().ocsc_default_opts(ctypes.byref(o))
+    return o
+
+
+def ocsc_init(K: int, filter_h: int, filter_w: int, lam: float, rho: float,
+              opts: ocsc_opts | None = None, stream: int = 0) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    st = lib().ocsc_init(ctypes.byref(ctx), K, filter_h, filter_w, lam, rho,
+                         ctypes.byref(opts) if opts is not None else None, ctypes.c_void_p(stream))
+    _check(None, st)
+    return ctx
+
+
+def ocsc_destroy(ctx) -> None:
+    lib().ocsc_destroy(ctx)
+
+
+def ocsc_padded_size(ctx, H: int, W: int) -> int:
+    n = ctypes.c_int()
+    _check(ctx, lib().ocsc_padded_size(ctx, H, W, ctypes.byref(n)))
+    return n.value
+
+
+def ocsc_code(ctx, x_ptrs, H, W, u_ptrs=None) -> None:
+    n = len(x_ptrs)
+    xs = (_P * n)(*x_ptrs)
+    hs = (_I * n)(*H)
+    ws = (_I * n)(*W)
+    us = (_P * n)(*u_ptrs) if u_ptrs is not None else None
+    _check(ctx, lib().ocsc_code(ctx, n, xs, hs, ws, us))
+
+
+def ocsc_update_dict(ctx) -> None:
+    _check(ctx, lib().ocsc_update_dict(ctx))
+
+
+def ocsc_get_dict(ctx, D_host_ptr: int) -> int:
+    v = ctypes.c_uint64()
+    _check(ctx, lib().ocsc_get_dict(ctx, ctypes.c_void_p(D_host_ptr), ctypes.byref(v)))
+    return v.value
+
+
+def ocsc_set_dict(ctx, D_host_ptr: int, normalize: int) -> None:
+    _check(ctx, lib().ocsc_set_dict(ctx, ctypes.c_void_p(D_host_ptr), normalize))
+
+
+def ocsc_sync(ctx) -> None:
+    _check(ctx, lib().ocsc_sync(ctx))
+
+
+def ocsc_last_error(ctx) -> str:
+    m = lib().ocsc_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def ocsc_fft2_r2c(ctx, x_ptr: int, X_ptr: int, planes: int) -> None:
+    _check(ctx, lib().ocsc_fft2_r2c(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(X_ptr), planes))
+
+
+def ocsc_fft2_c2r(ctx, X_ptr: int, x_ptr: int, planes: int) -> None:
+    _check(ctx, lib().ocsc_fft2_c2r(ctx, ctypes.c_void_p(X_ptr), ctypes.c_void_p(x_ptr), planes))
+
+
+# --- torch convenience wrapper --------------------------------------------------
+
+class OCSC:
+    """One OCSC learner on the current CUDA device.
+
+    Images and codes are torch CUDA float32 tensors; the dictionary is read and
+    written as numpy float32 [K, M, M].  Work is queued on ``stream`` (default:
+    torch's current stream when the object is created).
+    """
+
+    def __init__(self, K: int, M: int, lam: float, rho: float, *, stream=None, **opts):
+        import torch
+
+        self._torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("OCSC needs a CUDA GPU; there is no CPU fallback")
+        o = ocsc_default_opts()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = ocsc_init(K, M, M, lam, rho, o, self.stream.cuda_stream)
+        self.K, self.M, self.N = K, M, o.fft_size
+        self.opts = o
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ocsc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def padded_size(self, H: int, W: int) -> int:
+        return ocsc_padded_size(self.ctx, H, W)
+
+    def code(self, images, out=None, want_codes: bool = True):
+        """Code a list of 2D float32 CUDA tensors; returns [K, N, N] codes."""
+        torch = self._torch
+        xs = [im.contiguous() for im in images]
+        for im in xs:
+            if not (im.is_cuda and im.dtype == torch.float32 and im.dim() == 2):
+                raise ValueError("images must be 2D float32 CUDA tensors")
+        if out is None and want_codes:
+            out = [torch.empty((self.K, self.N, self.N), device=im.device, dtype=torch.float32)
+                   for im in xs]
+        ocsc_code(self.ctx, [im.data_ptr() for im in xs], [im.shape[0] for im in xs],
+                  [im.shape[1] for im in xs], [u.data_ptr() for u in out] if out is not None else None)
+        self._keep = xs  # images must outlive the queued work
+        return out
+
+    def update_dict(self):
+        ocsc_update_dict(self.ctx)
+
+    def get_dict(self):
+        import numpy as np
+
+        D = np.empty((self.K, self.M, self.M), np.float32)
+        self.version = ocsc_get_dict(self.ctx, D.ctypes.data)
+        return D
+
+    def set_dict(self, D, normalize: bool = True):
+        import numpy as np
+
+        D = np.ascontiguousarray(D, dtype=np.float32)
+        if D.shape != (self.K, self.M, self.M):
+            raise ValueError(f"dictionary must be {(self.K, self.M, self.M)}")
+        ocsc_set_dict(self.ctx, D.ctypes.data, int(normalize))
+
+    def sync(self):
+        ocsc_sync(self.ctx)
+
+    def fft2_r2c(self, x):
+        torch = self._torch
+        x = x.contiguous()
+        X = torch.empty((x.shape[0], self.N, self.N // 2 + 1), device=x.device, dtype=torch.complex64)
+        ocsc_fft2_r2c(self.ctx, x.data_ptr(), X.data_ptr(), x.shape[0])
+        return X
+
+    def fft2_c2r(self, X):
+        torch = self._torch
+        X = X.contiguous()
+        x = torch.empty((X.shape[0], self.N, self.N), device=X.device, dtype=torch.float32)
+        ocsc_fft2_c2r(self.ctx, X.data_ptr(), x.data_ptr(), X.shape[0])
+        return x

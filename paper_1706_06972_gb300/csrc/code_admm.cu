@@ -1,0 +1,303 @@
+// Per-sample code ADMM in the frequency domain (Sec. II-C.1, problem
+// (fcsc_code), with the scaled-dual ADMM template of Sec. II-B).
+//
+// One iteration, with W^ = F(U - Gamma), for every frequency p of the half
+// spectrum and d = D~(p,:)^T:
+//   Z~-step: (conj(d) d^T + rho I) z = conj(d) x~(p) + rho w^(p).  The matrix
+//            is rank one plus rho*I; by Sherman-Morrison the solution is
+//            z = w^ + conj(d) r_p  with  r_p = (x~(p) - d^T w^) / (rho + |d|^2).
+//   Z       = F^-1(Z~)
+//   U       = S_{lambda/rho}(Z + Gamma)          (soft threshold)
+//   Gamma   = Gamma + Z - U
+// The only coupling across filters is r_p (a reduction over k at each p); the
+// only coupling across frequencies is the FFT of each filter plane.  So each
+// iteration is two kernels:
+//   code_resid  -- r_p for every (sample, p): reduce d_k w^_k over k;
+//   code_plane  -- one CTA per (sample, pair of filters): build z for both
+//                  filters, pack them as one complex plane z_a + i z_b, inverse
+//                  2D FFT in shared memory, shrink + dual update in registers,
+//                  forward FFT of W = U - Gamma, split back into the two half
+//                  spectra.  Gamma is the only spatial array that goes to
+//                  global memory.
+#include "fft.cuh"
+#include "launch.h"
+
+namespace ocsc {
+
+template <int N, int NT>
+__device__ __forceinline__ void load_twiddles(float2 *s_tw, const float2 *__restrict__ tw) {
+  for (int i = threadIdx.x; i < N; i += NT) s_tw[i] = tw[i];
+}
+
+__device__ __forceinline__ float soft_threshold(float v, float t) {
+  return v > t ? v - t : (v < -t ? v + t : 0.0f);
+}
+
+// x~ = F(zero-padded image): one CTA per image.
+template <int N>
+__global__ void __launch_bounds__(TileThreads<N>::value)
+    image_spectrum_kernel(ImgBatch b, const float2 *__restrict__ tw, float2 *__restrict__ xh) {
+  constexpr int NT = TileThreads<N>::value, PITCH = tile_pitch<N>(), NH = N / 2 + 1;
+  constexpr int F = N * NH;
+  extern __shared__ float2 smem[];
+  float2 *tile = smem;
+  float2 *s_tw = smem + N * PITCH;
+  const int img = blockIdx.x;
+  const float *x = b.x[img];
+  const int H = b.H[img], W = b.W[img];
+  load_twiddles<N, NT>(s_tw, tw);
+  for (int q = threadIdx.x; q < N * N; q += NT) {
+    const int q1 = q / N, q2 = q % N;
+    const float v = (q1 < H && q2 < W) ? x[q1 * W + q2] : 0.0f;
+    tile[q1 * PITCH + q2] = make_float2(v, 0.0f);
+  }
+  __syncthreads();
+  fft2d_tile<N, NT, false>(tile, s_tw);
+  float2 *out = xh + (size_t)img * F;
+  for (int p = threadIdx.x; p < F; p += NT) {
+    const int k1 = p / NH, k2 = p % NH;
+    out[p] = tile[k1 * PITCH + k2];
+  }
+}
+
+// r_p = (x~(p) - sum_k D~_k(p) W^_k(p)) / (rho + |d_p|^2); block (32, 8).
+__global__ void code_resid_kernel(int K, int F, float rho, int first,
+                                  const float2 *__restrict__ Dh, const float *__restrict__ dn,
+                                  const float2 *__restrict__ xh, const float2 *__restrict__ What,
+                                  float2 *__restrict__ r) {
+  __shared__ float2 part[8][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int p = blockIdx.x * 32 + tx;
+  const int img = blockIdx.y;
+  float2 s = make_float2(0.f, 0.f);
+  if (!first && p < F) {
+    const float2 *w = What + (size_t)img * K * F;
+    for (int k = ty; k < K; k += 8) s = cadd(s, cmul(Dh[(size_t)k * F + p], w[(size_t)k * F + p]));
+  }
+  part[ty][tx] = s;
+  __syncthreads();
+  if (ty == 0 && p < F) {
+    float2 t = part[0][tx];
+#pragma unroll
+    for (int y = 1; y < 8; ++y) t = cadd(t, part[y][tx]);
+    const float2 x = xh[(size_t)img * F + p];
+    const float inv = 1.0f / (rho + dn[p]);
+    r[(size_t)img * F + p] = make_float2((x.x - t.x) * inv, (x.y - t.y) * inv);
+  }
+}
+
+// One fused ADMM iteration for filters (a, a+1) of one sample.
+template <int N>
+__global__ void __launch_bounds__(TileThreads<N>::value)
+    code_plane_kernel(CodeIter it, ImgBatch b, const float2 *__restrict__ tw) {
+  constexpr int NT = TileThreads<N>::value, PITCH = tile_pitch<N>(), NH = N / 2 + 1;
+  constexpr int F = N * NH, P = N * N;
+  extern __shared__ float2 smem[];
+  float2 *tile = smem;
+  float2 *s_tw = smem + N * PITCH;
+  const int K = it.K;
+  const int ka = 2 * blockIdx.x;
+  const int kb = ka + 1;
+  const bool hasb = kb < K;
+  const int img = blockIdx.y;
+  load_twiddles<N, NT>(s_tw, tw);
+
+  const float2 *Da = it.Dh + (size_t)ka * F;
+  const float2 *Db = it.Dh + (size_t)(hasb ? kb : ka) * F;
+  const float2 *rr = it.r + (size_t)img * F;
+  float2 *Wa = it.What + ((size_t)img * K + ka) * F;
+  float2 *Wb = it.What + ((size_t)img * K + (hasb ? kb : ka)) * F;
+  float2 *Za = it.Zp + ((size_t)img * K + ka) * F;
+  float2 *Zb = it.Zp + ((size_t)img * K + (hasb ? kb : ka)) * F;
+
+  // Z~-step for both filters; pack z_a + i z_b over the full spectrum.
+  for (int p = threadIdx.x; p < F; p += NT) {
+    const int k1 = p / NH, k2 = p % NH;
+    const float2 rp = rr[p];
+    float2 za = cconjmul(Da[p], rp);
+    float2 zb = hasb ? cconjmul(Db[p], rp) : make_float2(0.f, 0.f);
+    if (!it.first) {
+      za = cadd(za, Wa[p]);
+      if (hasb) zb = cadd(zb, Wb[p]);
+    }
+    if (it.last) {
+      Za[p] = za;
+      if (hasb) Zb[p] = zb;
+    }
+    tile[k1 * PITCH + k2] = make_float2(za.x - zb.y, za.y + zb.x);
+    if (k2 > 0 && k2 < N / 2) {
+      const int m1 = (N - k1) & (N - 1);
+      tile[m1 * PITCH + (N - k2)] = make_float2(za.x + zb.y, zb.x - za.y);
+    }
+  }
+  __syncthreads();
+  fft2d_tile<N, NT, true>(tile, s_tw);
+
+  // Spatial step: U = S(Z + Gamma), Gamma += Z - U, W = U - Gamma.
+  const float invP = 1.0f / (float)P;
+  float *Ga = it.Gam + ((size_t)img * K + ka) * P;
+  float *Gb = it.Gam + ((size_t)img * K + (hasb ? kb : ka)) * P;
+  float *Ua = b.u[img] ? b.u[img] + (size_t)ka * P : nullptr;
+  float *Ub = (b.u[img] && hasb) ? b.u[img] + (size_t)kb * P : nullptr;
+  for (int q = threadIdx.x; q < P; q += NT) {
+    const int q1 = q / N, q2 = q % N;
+    const float2 c = tile[q1 * PITCH + q2];
+    const float ga = it.first ? 0.f : Ga[q];
+    const float gb = (it.first || !hasb) ? 0.f : Gb[q];
+    const float va = c.x * invP + ga;
+    const float vb = c.y * invP + gb;
+    const float ua = soft_threshold(va, it.thr);
+    const float ub = soft_threshold(vb, it.thr);
+    const float ga2 = va - ua, gb2 = vb - ub;
+    Ga[q] = ga2;
+    if (hasb) Gb[q] = gb2;
+    if (it.last) {
+      if (Ua) Ua[q] = ua;
+      if (Ub) Ub[q] = ub;
+    } else {
+      tile[q1 * PITCH + q2] = make_float2(ua - ga2, hasb ? ub - gb2 : 0.f);
+    }
+  }
+  if (it.last) return;
+  __syncthreads();
+  fft2d_tile<N, NT, false>(tile, s_tw);
+
+  // Split the packed spectrum into the two half spectra W^_a, W^_b.
+  for (int p = threadIdx.x; p < F; p += NT) {
+    const int k1 = p / NH, k2 = p % NH;
+    const float2 c = tile[k1 * PITCH + k2];
+    const float2 cm = tile[((N - k1) & (N - 1)) * PITCH + ((N - k2) & (N - 1))];
+    Wa[p] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
+    if (hasb) Wb[p] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+  }
+}
+
+// Building block: batched real 2D FFT (pairs of planes share one complex FFT).
+template <int N, bool INV>
+__global__ void __launch_bounds__(TileThreads<N>::value)
+    fft2_pair_kernel(const float *__restrict__ in, float *__restrict__ out, int planes,
+                     const float2 *__restrict__ tw) {
+  constexpr int NT = TileThreads<N>::value, PITCH = tile_pitch<N>(), NH = N / 2 + 1;
+  constexpr int F = N * NH, P = N * N;
+  extern __shared__ float2 smem[];
+  float2 *tile = smem;
+  float2 *s_tw = smem + N * PITCH;
+  const int pa = 2 * blockIdx.x, pb = pa + 1;
+  const bool hasb = pb < planes;
+  load_twiddles<N, NT>(s_tw, tw);
+  if (!INV) {
+    const float *xa = in + (size_t)pa * P;
+    const float *xb = in + (size_t)pb * P;
+    for (int q = threadIdx.x; q < P; q += NT)
+      tile[(q / N) * PITCH + (q % N)] = make_float2(xa[q], hasb ? xb[q] : 0.f);
+    __syncthreads();
+    fft2d_tile<N, NT, false>(tile, s_tw);
+    float2 *Xa = reinterpret_cast<float2 *>(out) + (size_t)pa * F;
+    float2 *Xb = reinterpret_cast<float2 *>(out) + (size_t)pb * F;
+    for (int p = threadIdx.x; p < F; p += NT) {
+      const int k1 = p / NH, k2 = p % NH;
+      const float2 c = tile[k1 * PITCH + k2];
+      const float2 cm = tile[((N - k1) & (N - 1)) * PITCH + ((N - k2) & (N - 1))];
+      Xa[p] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
+      if (hasb) Xb[p] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+    }
+  } else {
+    const float2 *Xa = reinterpret_cast<const float2 *>(in) + (size_t)pa * F;
+    const float2 *Xb = reinterpret_cast<const float2 *>(in) + (size_t)pb * F;
+    for (int p = threadIdx.x; p < F; p += NT) {
+      const int k1 = p / NH, k2 = p % NH;
+      const float2 za = Xa[p];
+      const float2 zb = hasb ? Xb[p] : make_float2(0.f, 0.f);
+      tile[k1 * PITCH + k2] = make_float2(za.x - zb.y, za.y + zb.x);
+      if (k2 > 0 && k2 < N / 2)
+        tile[((N - k1) & (N - 1)) * PITCH + (N - k2)] = make_float2(za.x + zb.y, zb.x - za.y);
+    }
+    __syncthreads();
+    fft2d_tile<N, NT, true>(tile, s_tw);
+    const float invP = 1.0f / (float)P;
+    float *xa = out + (size_t)pa * P;
+    float *xb = out + (size_t)pb * P;
+    for (int q = threadIdx.x; q < P; q += NT) {
+      const float2 c = tile[(q / N) * PITCH + (q % N)];
+      xa[q] = c.x * invP;
+      if (hasb) xb[q] = c.y * invP;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+
+template <typename Kern>
+static cudaError_t set_smem(Kern k, size_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int N>
+static cudaError_t image_spectrum_n(const ImgBatch &b, const float2 *tw, float2 *xh, cudaStream_t s) {
+  const size_t sm = tile_smem_bytes<N>();
+  cudaError_t e = set_smem(image_spectrum_kernel<N>, sm);
+  if (e != cudaSuccess) return e;
+  image_spectrum_kernel<N><<<b.n, TileThreads<N>::value, sm, s>>>(b, tw, xh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_image_spectrum(int N, const ImgBatch &b, const float2 *tw, float2 *xh,
+                                  cudaStream_t s) {
+  if (b.n <= 0) return cudaSuccess;
+  switch (N) {
+    case 64: return image_spectrum_n<64>(b, tw, xh, s);
+    case 128: return image_spectrum_n<128>(b, tw, xh, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_code_resid(int N, int n, int K, float rho, int first, const float2 *Dh,
+                              const float *dn, const float2 *xh, const float2 *What, float2 *r,
+                              cudaStream_t s) {
+  const int F = N * (N / 2 + 1);
+  dim3 grid((F + 31) / 32, n), block(32, 8);
+  code_resid_kernel<<<grid, block, 0, s>>>(K, F, rho, first, Dh, dn, xh, What, r);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t code_plane_n(const CodeIter &it, const ImgBatch &b, const float2 *tw,
+                                cudaStream_t s) {
+  const size_t sm = tile_smem_bytes<N>();
+  cudaError_t e = set_smem(code_plane_kernel<N>, sm);
+  if (e != cudaSuccess) return e;
+  dim3 grid((it.K + 1) / 2, b.n);
+  code_plane_kernel<N><<<grid, TileThreads<N>::value, sm, s>>>(it, b, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, const float2 *tw,
+                              cudaStream_t s) {
+  if (b.n <= 0) return cudaSuccess;
+  switch (N) {
+    case 64: return code_plane_n<64>(it, b, tw, s);
+    case 128: return code_plane_n<128>(it, b, tw, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int N, bool INV>
+static cudaError_t fft2_n(const float *in, float *out, int planes, const float2 *tw, cudaStream_t s) {
+  const size_t sm = tile_smem_bytes<N>();
+  cudaError_t e = set_smem(fft2_pair_kernel<N, INV>, sm);
+  if (e != cudaSuccess) return e;
+  fft2_pair_kernel<N, INV><<<(planes + 1) / 2, TileThreads<N>::value, sm, s>>>(in, out, planes, tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fft2(int N, int inverse, const float *in, float *out, int planes,
+                        const float2 *tw, cudaStream_t s) {
+  if (planes <= 0) return cudaSuccess;
+  if (N == 64) return inverse ? fft2_n<64, true>(in, out, planes, tw, s) : fft2_n<64, false>(in, out, planes, tw, s);
+  if (N == 128) return inverse ? fft2_n<128, true>(in, out, planes, tw, s) : fft2_n<128, false>(in, out, planes, tw, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ocsc

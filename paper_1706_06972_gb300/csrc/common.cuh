@@ -1,0 +1,44 @@
+// Shared device helpers: complex arithmetic on float2/double2 and the packed
+// lower-triangular layout of the per-frequency K x K Hermitian matrices.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ocsc {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cconjmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// Packed lower triangle, column-major: column j holds rows j..K-1.
+// Offset of column j: j*K - j*(j-1)/2.
+__host__ __device__ __forceinline__ int tri_off(int j, int K) { return j * (2 * K - j + 1) / 2; }
+__host__ __device__ __forceinline__ int tri_size(int K) { return K * (K + 1) / 2; }
+
+// Inverse of tri_off: packed index t -> (i, j) with i >= j.
+__device__ __forceinline__ void tri_ij(int t, int K, int &i, int &j) {
+  const float kf = 2.0f * K + 1.0f;
+  int jj = (int)floorf(0.5f * (kf - sqrtf(fmaxf(kf * kf - 8.0f * (float)t, 0.0f))));
+  jj = max(0, min(jj, K - 1));
+  while (jj > 0 && tri_off(jj, K) > t) --jj;
+  while (jj < K - 1 && tri_off(jj + 1, K) <= t) ++jj;
+  j = jj;
+  i = t - tri_off(jj, K) + jj;
+}
+
+// Device error word bits.
+enum : int { ERR_PIVOT = 1 };
+
+}  // namespace ocsc

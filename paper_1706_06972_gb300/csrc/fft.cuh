@@ -1,0 +1,156 @@
+// Shared-memory 2D complex FFT on an N x N tile for one CTA.
+//
+// The 2D DFT of Sec. II-C (convolution theorem) is computed as 1D transforms
+// along columns and rows.  Each 1D transform is a Stockham auto-sort
+// decimation-in-time sequence of radix-R passes (Stockham; see Govindaraju et
+// al., SC'08, for the GPU formulation): a pass reads R elements at stride N/R,
+// multiplies by twiddles W_N^(r*(j mod Ns)*N/(Ns*R)), applies an R-point DFT in
+// registers and writes them at stride Ns, so the output comes out in natural
+// order with no bit reversal.  All N lines of the tile are transformed in the
+// same pass; consecutive threads take consecutive lines, which with a row pitch
+// of N+1 complex elements keeps 64-bit shared-memory accesses conflict-free for
+// both row and column passes.
+//
+// Twiddles W_N^m = exp(-2 pi i m / N) come from a table computed on the host in
+// double precision and rounded once to float.
+#pragma once
+#include "common.cuh"
+
+namespace ocsc {
+
+// exp(-+ 2 pi i k / 16) for k in [0, 8): cos(k pi/8) and sin(k pi/8).
+template <int K16, bool INV>
+__device__ __forceinline__ float2 tw_mul16(float2 o) {
+  if constexpr (K16 == 0) {
+    return o;
+  } else if constexpr (K16 == 4) {  // -i (forward) / +i (inverse)
+    return INV ? make_float2(-o.y, o.x) : make_float2(o.y, -o.x);
+  } else {
+    constexpr float c = K16 == 1 ? 0.92387953251128674f
+                      : K16 == 2 ? 0.70710678118654752f
+                      : K16 == 3 ? 0.38268343236508978f
+                      : K16 == 5 ? -0.38268343236508978f
+                      : K16 == 6 ? -0.70710678118654752f
+                                 : -0.92387953251128674f;
+    constexpr float s0 = K16 == 1 ? 0.38268343236508978f
+                       : K16 == 2 ? 0.70710678118654752f
+                       : K16 == 3 ? 0.92387953251128674f
+                       : K16 == 5 ? 0.92387953251128674f
+                       : K16 == 6 ? 0.70710678118654752f
+                                  : 0.38268343236508978f;
+    constexpr float s = INV ? s0 : -s0;
+    return make_float2(o.x * c - o.y * s, o.x * s + o.y * c);
+  }
+}
+
+// In-register R-point DFT (R = 2, 4, 8, 16), natural order in and out,
+// by even/odd splitting.
+template <int R, bool INV>
+struct RegDFT {
+  template <int K>
+  static __device__ __forceinline__ void combine(float2 *v, const float2 *e, const float2 *o) {
+    if constexpr (K < R / 2) {
+      const float2 t = tw_mul16<K * (16 / R), INV>(o[K]);
+      v[K] = make_float2(e[K].x + t.x, e[K].y + t.y);
+      v[K + R / 2] = make_float2(e[K].x - t.x, e[K].y - t.y);
+      combine<K + 1>(v, e, o);
+    }
+  }
+  static __device__ __forceinline__ void run(float2 *v) {
+    float2 e[R / 2], o[R / 2];
+#pragma unroll
+    for (int n = 0; n < R / 2; ++n) {
+      e[n] = v[2 * n];
+      o[n] = v[2 * n + 1];
+    }
+    RegDFT<R / 2, INV>::run(e);
+    RegDFT<R / 2, INV>::run(o);
+    combine<0>(v, e, o);
+  }
+};
+template <bool INV>
+struct RegDFT<1, INV> {
+  static __device__ __forceinline__ void run(float2 *) {}
+};
+
+// Radix plan per transform length.
+template <int N> struct FFTPlan;
+template <> struct FFTPlan<64> { static constexpr int R0 = 8, R1 = 8; };
+template <> struct FFTPlan<128> { static constexpr int R0 = 16, R1 = 8; };
+
+template <int N>
+__host__ __device__ constexpr int tile_pitch() { return N + 1; }
+
+// One Stockham radix-R pass over all N lines of the tile.  ROWS: transform
+// along the second index (contiguous); otherwise along the first index.
+template <int N, int R, int NS, bool INV, bool ROWS, int NT>
+__device__ __forceinline__ void fft_pass(float2 *__restrict__ tile, const float2 *__restrict__ tw) {
+  constexpr int PITCH = tile_pitch<N>();
+  constexpr int G = N * (N / R);
+  static_assert(G % NT == 0, "threads must divide the butterfly groups");
+  constexpr int PER = G / NT;
+  float2 v[PER][R];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int gi = 0; gi < PER; ++gi) {
+    const int g = tid + gi * NT;
+    const int line = g % N;
+    const int j = g / N;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = j + r * (N / R);
+      v[gi][r] = ROWS ? tile[line * PITCH + e] : tile[e * PITCH + line];
+    }
+    if constexpr (NS > 1) {
+      const int jm = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = tw[(r * jm * (N / (NS * R))) & (N - 1)];
+        if (INV) w.y = -w.y;
+        v[gi][r] = cmul(v[gi][r], w);
+      }
+    }
+    RegDFT<R, INV>::run(v[gi]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int gi = 0; gi < PER; ++gi) {
+    const int g = tid + gi * NT;
+    const int line = g % N;
+    const int j = g / N;
+    const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = base + r * NS;
+      if (ROWS)
+        tile[line * PITCH + e] = v[gi][r];
+      else
+        tile[e * PITCH + line] = v[gi][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Full 2D transform of the tile (columns, then rows).  The caller must have
+// synchronised after writing the tile; the tile is complete on return.
+template <int N, int NT, bool INV>
+__device__ __forceinline__ void fft2d_tile(float2 *tile, const float2 *tw) {
+  constexpr int R0 = FFTPlan<N>::R0, R1 = FFTPlan<N>::R1;
+  static_assert(R0 * R1 == N, "two-pass plan");
+  fft_pass<N, R0, 1, INV, false, NT>(tile, tw);
+  fft_pass<N, R1, R0, INV, false, NT>(tile, tw);
+  fft_pass<N, R0, 1, INV, true, NT>(tile, tw);
+  fft_pass<N, R1, R0, INV, true, NT>(tile, tw);
+}
+
+// Threads per CTA used with an N x N tile.
+template <int N> struct TileThreads;
+template <> struct TileThreads<64> { static constexpr int value = 256; };
+template <> struct TileThreads<128> { static constexpr int value = 512; };
+
+template <int N>
+__host__ __device__ constexpr size_t tile_smem_bytes() {
+  return (size_t)N * tile_pitch<N>() * sizeof(float2) + (size_t)N * sizeof(float2);
+}
+
+}  // namespace ocsc

@@ -1,0 +1,65 @@
+// Internal launch interface between the C-ABI runtime and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ocsc {
+
+constexpr int kMaxCallImages = 64;  // images per kernel-parameter batch
+
+// Per-call image table, passed by value as a kernel parameter.
+struct ImgBatch {
+  const float *x[kMaxCallImages];  // device images, H x W row-major
+  float *u[kMaxCallImages];        // device code outputs K x N x N (or null)
+  int H[kMaxCallImages];
+  int W[kMaxCallImages];
+  int n;
+};
+
+// Code-ADMM iteration parameters.
+struct CodeIter {
+  int K, F;
+  int first, last;     // first / last ADMM iteration of this call
+  float thr;           // lambda / rho
+  const float2 *Dh;    // [K][F] dictionary spectrum used for coding
+  const float2 *r;     // [n][F] per-frequency residual multipliers
+  float2 *What;        // [n][K][F] F(U - Gamma)
+  float *Gam;          // [n][K][N*N] scaled dual
+  float2 *Zp;          // [n][K][F] last Z~ (written on the last iteration)
+};
+
+cudaError_t launch_image_spectrum(int N, const ImgBatch &b, const float2 *tw, float2 *xh,
+                                  cudaStream_t s);
+cudaError_t launch_code_resid(int N, int n, int K, float rho, int first, const float2 *Dh,
+                              const float *dn, const float2 *xh, const float2 *What, float2 *r,
+                              cudaStream_t s);
+cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, const float2 *tw,
+                              cudaStream_t s);
+cudaError_t launch_fft2(int N, int inverse, const float *in, float *out, int planes,
+                        const float2 *tw, cudaStream_t s);
+
+// Dictionary step.
+struct FoldArgs {
+  int K, F, B, first;
+  double alpha, beta, w, rho_eff;
+  float2 *A;            // [F][K(K+1)/2] history, packed lower, FP32
+  float2 *b;            // [K][F]
+  const float2 *Zp;     // [B][K][F]
+  const float2 *xh;     // [B][F]
+  float2 *L;            // [F][K(K+1)/2] Cholesky factor, diagonal holds 1/L_jj
+  float2 *g;            // [K][F]  (w A + rho I)^-1 (w b)
+  int *err;
+};
+cudaError_t launch_fold_factor(const FoldArgs &a, cudaStream_t s);
+cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *L, const float2 *g,
+                         const float2 *Vh, const float2 *th, float2 *Dcur, float2 *E,
+                         cudaStream_t s);
+cudaError_t launch_vstep_cols(int K, int N, int M, const float2 *E, const float2 *tw, float2 *Y,
+                              cudaStream_t s);
+// mode 0: V-step from Y (projection, Vh, dual update); mode 1: Vh from given V.
+cudaError_t launch_vstep_project(int mode, int K, int N, int M, const float2 *Y, float *V,
+                                 float2 *Vh, float2 *th, const float2 *Dcur, const float2 *tw,
+                                 cudaStream_t s);
+cudaError_t launch_dict_norms(int K, int F, const float2 *Dh, float *dn, cudaStream_t s);
+
+}  // namespace ocsc

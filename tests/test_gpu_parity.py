@@ -1,0 +1,236 @@
+"""Parity of the CUDA path with the FP64 oracle on the same seeded inputs.
+
+All GPU work goes through the C ABI (libocsc.so via the ctypes binding).
+Tolerances come from FP32 arithmetic: FFTs of N x N planes carry a relative
+error of a few eps32 * log2(N^2) (eps32 = 6e-8), and the ADMM iterates
+propagate it through Jz = 50 code iterations and Jd = 10 dictionary
+iterations; the dictionary solve adds the FP32 triangular solves with the FP64
+Cholesky factor, whose error grows with the condition number of A + rho I.
+The bars below are those of the method statement: relative objective 1e-4 on
+the FP32 path, and norm-relative code / dictionary errors 1e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import WORKLOADS, make_image, raw_filters
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+OBJ_TOL = 1e-4      # relative objective, FP32 path
+REL_TOL = 1e-3      # norm-relative code and dictionary errors
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    a = a.astype(np.complex128) if np.iscomplexobj(a) else a.astype(np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def run_gpu(images, raw, K, M, lam, rho, N, Jz, Jd, batch=1, normalize=True, **opts):
+    import paper_1706_06972_gb300 as pkg
+
+    learner = pkg.OCSC(K, M, lam, rho, fft_size=N, Jz=Jz, Jd=Jd, max_batch=batch, **opts)
+    learner.set_dict(raw, normalize=normalize)
+    codes, dicts = [], []
+    for s in range(0, len(images), batch):
+        xs = [torch.from_numpy(np.ascontiguousarray(im, np.float32)).cuda() for im in images[s:s + batch]]
+        us = learner.code(xs)
+        learner.update_dict()
+        codes.extend([u.cpu().numpy() for u in us])
+        dicts.append(learner.get_dict())
+    learner.close()
+    return codes, dicts
+
+
+def run_oracle(images, raw, N, lam, rho, Jz, Jd, batch=1, **flags):
+    st = oracle.init_state(np.asarray(raw, np.float64), N, N, lam, rho, **flags)
+    codes, dicts, coding_dicts = [], [], []
+    for s in range(0, len(images), batch):
+        coding_dicts.append(oracle.published_filters(st))
+        res = [oracle.code(st, im, Jz) for im in images[s:s + batch]]
+        oracle.update_dict(st, res, Jd)
+        codes.extend([r.U for r in res])
+        dicts.append(oracle.published_filters(st))
+    return codes, dicts, coding_dicts
+
+
+def surrogate_objective(codes, coding_dicts, images, N, lam, batch):
+    vals = []
+    for i, (U, x) in enumerate(zip(codes, images)):
+        D = coding_dicts[i // batch]
+        vals.append(oracle.sample_objective(D, U, oracle.pad_to(np.asarray(x, np.float64), N, N), lam))
+    return float(np.mean(vals))
+
+
+# --- FFT building block ------------------------------------------------------
+
+@pytest.mark.parametrize("N", [64, 128])
+def test_fft_building_block_matches_numpy(N):
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    learner = pkg.OCSC(2, 3, 1.0, 1.0, fft_size=N)
+    rng = np.random.default_rng(N)
+    x = rng.standard_normal((3, N, N)).astype(np.float32)   # odd count: unpaired last plane
+    X = learner.fft2_r2c(torch.from_numpy(x).cuda()).cpu().numpy()
+    ref = np.fft.rfft2(x.astype(np.float64))
+    assert rel(X, ref) < 2e-6
+    back = learner.fft2_c2r(torch.from_numpy(ref.astype(np.complex64)).cuda()).cpu().numpy()
+    assert rel(back, x) < 2e-6
+    learner.close()
+
+
+# --- one sample, config-1 sizes ----------------------------------------------
+
+def test_single_sample_code_and_update():
+    _need_gpu()
+    w = WORKLOADS["plain_64_k16"]
+    imgs = [w.image(0)]
+    raw = w.filters0()
+    codes, dicts = run_gpu(imgs, raw, w.K, w.M, w.lam, w.rho, 64, w.Jz, w.Jd, pad=w.pad)
+    ocodes, odicts, _ = run_oracle(imgs, raw, 64, w.lam, w.rho, w.Jz, w.Jd)
+    assert rel(codes[0], ocodes[0]) < REL_TOL
+    assert rel(dicts[0], odicts[0]) < REL_TOL
+    norms = np.sqrt(np.sum(dicts[0].astype(np.float64) ** 2, axis=(1, 2)))
+    assert np.all(norms <= 1 + 1e-6)
+
+
+# --- whole online pass, 20 images 64x64, K=16 ----------------------------------
+
+def test_online_pass_plain_64_k16():
+    _need_gpu()
+    w = WORKLOADS["plain_64_k16"]
+    imgs = [w.image(i) for i in range(w.n_images)]
+    raw = w.filters0()
+    codes, dicts = run_gpu(imgs, raw, w.K, w.M, w.lam, w.rho, 64, w.Jz, w.Jd, pad=w.pad)
+    ocodes, odicts, ocd = run_oracle(imgs, raw, 64, w.lam, w.rho, w.Jz, w.Jd)
+    for t in range(len(imgs)):
+        assert rel(codes[t], ocodes[t]) < REL_TOL, t
+        assert rel(dicts[t], odicts[t]) < REL_TOL, t
+    gcd = [oracle.normalize_filters(raw)] + dicts[:-1]
+    f_gpu = surrogate_objective(codes, gcd, imgs, 64, w.lam, 1)
+    f_orc = surrogate_objective(ocodes, ocd, imgs, 64, w.lam, 1)
+    assert abs(f_gpu - f_orc) / abs(f_orc) < OBJ_TOL
+    xs = [oracle.pad_to(np.asarray(x, np.float64), 64, 64) for x in imgs]
+    F_gpu = oracle.objective(dicts[-1], codes, xs, w.lam)
+    F_orc = oracle.objective(odicts[-1], ocodes, xs, w.lam)
+    assert abs(F_gpu - F_orc) / abs(F_orc) < OBJ_TOL
+
+
+# --- full size: 100x100 in 128x128, K=100 filters 11x11 (sampled) -------------
+
+def test_plain_100in128_k100_first_samples():
+    """The bench workload at its full size: the first two samples and updates
+    of the stream, compared with the oracle sample by sample."""
+    _need_gpu()
+    w = WORKLOADS["plain_100in128_k100"]
+    imgs = [w.image(i) for i in range(2)]
+    raw = w.filters0()
+    codes, dicts = run_gpu(imgs, raw, w.K, w.M, w.lam, w.rho, 128, w.Jz, w.Jd, pad=w.pad)
+    ocodes, odicts, ocd = run_oracle(imgs, raw, 128, w.lam, w.rho, w.Jz, w.Jd)
+    for t in range(2):
+        assert rel(codes[t], ocodes[t]) < REL_TOL, t
+        assert rel(dicts[t], odicts[t]) < REL_TOL, t
+    gcd = [oracle.normalize_filters(raw)] + dicts[:-1]
+    f_gpu = surrogate_objective(codes, gcd, imgs, 128, w.lam, 1)
+    f_orc = surrogate_objective(ocodes, ocd, imgs, 128, w.lam, 1)
+    assert abs(f_gpu - f_orc) / abs(f_orc) < OBJ_TOL
+
+
+# --- edge cases ------------------------------------------------------------------
+
+def _small_images(n, h, w, seed):
+    return [make_image(h, w, seed + i) for i in range(n)]
+
+
+@pytest.mark.parametrize("case", [
+    dict(K=15, M=5, lam=0.5, rho=1.0, Jz=20, Jd=5, n=3, hw=(64, 64), pad=0),      # odd K
+    dict(K=4, M=1, lam=0.2, rho=2.0, Jz=10, Jd=3, n=2, hw=(40, 50), pad=0),       # 1x1 filters, rectangular
+    dict(K=8, M=7, lam=0.0, rho=1.0, Jz=15, Jd=4, n=2, hw=(57, 57), pad=6),       # lambda = 0, zero padding
+    dict(K=6, M=4, lam=1.0, rho=0.5, Jz=1, Jd=1, n=2, hw=(64, 64), pad=0),        # single iterations
+    dict(K=33, M=3, lam=0.3, rho=1.0, Jz=8, Jd=3, n=2, hw=(100, 90), pad=2),      # K > 32, N = 128
+])
+def test_edge_cases_match_oracle(case):
+    _need_gpu()
+    h, wd = case["hw"]
+    imgs = _small_images(case["n"], h, wd, 77)
+    raw = raw_filters(case["K"], case["M"], 5)
+    N = 64 if max(h, wd) + case["pad"] <= 64 else 128
+    codes, dicts = run_gpu(imgs, raw, case["K"], case["M"], case["lam"], case["rho"], N,
+                           case["Jz"], case["Jd"], pad=case["pad"])
+    ocodes, odicts, _ = run_oracle(imgs, raw, N, case["lam"], case["rho"], case["Jz"], case["Jd"])
+    for t in range(case["n"]):
+        assert rel(codes[t], ocodes[t]) < REL_TOL, t
+        assert rel(dicts[t], odicts[t]) < REL_TOL, t
+
+
+def test_minibatch_fold_matches_oracle():
+    _need_gpu()
+    imgs = _small_images(6, 64, 64, 200)
+    raw = raw_filters(12, 6, 9)
+    codes, dicts = run_gpu(imgs, raw, 12, 6, 0.5, 1.0, 64, 20, 6, batch=3, pad=0)
+    ocodes, odicts, _ = run_oracle(imgs, raw, 64, 0.5, 1.0, 20, 6, batch=3)
+    for t in range(6):
+        assert rel(codes[t], ocodes[t]) < REL_TOL
+    for u in range(2):
+        assert rel(dicts[u], odicts[u]) < REL_TOL
+
+
+@pytest.mark.parametrize("flags,gflags,lam,rho", [
+    (dict(warm_start=False), dict(warm_start=0), 0.5, 1.0),
+    (dict(rho_convention="paper"), dict(rho_convention=1), 0.005, 0.01),
+])
+def test_reading_flags_match_oracle(flags, gflags, lam, rho):
+    _need_gpu()
+    imgs = _small_images(3, 64, 64, 300)
+    raw = raw_filters(10, 5, 11)
+    codes, dicts = run_gpu(imgs, raw, 10, 5, lam, rho, 64, 15, 5, pad=0, **gflags)
+    ocodes, odicts, _ = run_oracle(imgs, raw, 64, lam, rho, 15, 5, **flags)
+    for t in range(3):
+        assert rel(codes[t], ocodes[t]) < REL_TOL
+        assert rel(dicts[t], odicts[t]) < REL_TOL
+
+
+def test_deterministic_reruns():
+    _need_gpu()
+    imgs = _small_images(3, 64, 64, 400)
+    raw = raw_filters(16, 8, 13)
+    a = run_gpu(imgs, raw, 16, 8, 1.0, 1.0, 64, 10, 4, pad=0)
+    b = run_gpu(imgs, raw, 16, 8, 1.0, 1.0, 64, 10, 4, pad=0)
+    for x, y in zip(a[0] + a[1], b[0] + b[1]):
+        assert np.array_equal(x, y)
+
+
+# --- host-side error handling (no kernel ever sees a bad argument) -------------
+
+def test_error_statuses():
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    with pytest.raises(pkg.OCSCError) as e:
+        pkg.OCSC(0, 3, 1.0, 1.0)
+    assert e.value.status == 6
+    with pytest.raises(pkg.OCSCError) as e:
+        pkg.OCSC(4, 3, 1.0, 0.0)
+    assert e.value.status == 1
+    learner = pkg.OCSC(4, 3, 1.0, 1.0, fft_size=64, pad=0, max_batch=1)
+    with pytest.raises(pkg.OCSCError) as e:      # 100x100 does not map to N = 64
+        learner.code([torch.zeros((100, 100), device="cuda")])
+    assert e.value.status == 6
+    learner.code([torch.zeros((64, 64), device="cuda")])
+    with pytest.raises(pkg.OCSCError) as e:      # pending would exceed max_batch
+        learner.code([torch.zeros((64, 64), device="cuda")])
+    assert e.value.status == 5
+    with pytest.raises(pkg.OCSCError) as e:      # infeasible filters without normalisation
+        learner.set_dict(np.full((4, 3, 3), 2.0, np.float32), normalize=False)
+    assert e.value.status == 1
+    learner.update_dict()
+    learner.sync()
+    learner.close()
