@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the OCSC hot path on GB300.
+
+Workload: the plain online pass at paper-like scale -- 100x100 synthetic
+images zero-padded to a 128x128 circular domain, K = 100 filters 11x11,
+lambda = rho = 1, mini-batch 1, 50 code-ADMM and 10 dictionary-ADMM iterations
+per sample.  One step = one sample through the whole hot path: FFT, code ADMM,
+history fold, FP64 per-frequency Cholesky, DictOCSC.  Metric: images/s.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): each rank runs an independent OCSC stream on its own GPU
+(replicas; the online dictionary is one sequential state, so the method has no
+data-parallel split without changing it).  Time = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "plain_100in128_k100"
+METRIC = "OCSC images/s, plain online pass (100x100 in 128x128, K=100, 11x11, B=1)"
+UNIT = "images/s"
+
+# FP64 arithmetic peak of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2070 MHz.
+SMS = 152
+FP64_FMA_PER_CLK_SM = 2
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+
+# DRAM bytes per fold_factor launch from an ncu capture of this workload
+# (profiles/fold_factor_plain_100in128_k100.md), valid only while the kernel
+# source is the one captured (sha1 of dict_update.cu).
+TRAFFIC_CAPTURE = {"bytes": 351.823360e6 + 626.167552e6,
+                   "source_sha1": "b12b1216483b55dd30401973b0e9148cf900b9c7"}
+
+
+def captured_traffic():
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_1706_06972_gb300", "csrc", "dict_update.cu")
+    with open(path, "rb") as f:
+        sha = hashlib.sha1(f.read()).hexdigest()
+    return TRAFFIC_CAPTURE["bytes"] if sha == TRAFFIC_CAPTURE["source_sha1"] else None
+
+
+def fold_factor_fp64_flops(K: int, F: int) -> float:
+    """Algorithmic FP64 flops of one fold_factor launch (all F frequencies):
+    right-looking complex Cholesky (K^3/6 complex MACs + column scaling) and the
+    two triangular solves for g, at 8 flops per complex MAC."""
+    chol = 8.0 * (K - 1) * K * (K + 1) / 6.0 + 1.0 * K * (K - 1)
+    solves = 8.0 * K * (K - 1)
+    return F * (chol + solves)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", gpu_id],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(self.NAMES, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# oracle legs (CPU baseline and reference arm): FP64 oracle, one thread
+# ---------------------------------------------------------------------------
+
+def _oracle_child(n_images: int, first: int) -> None:
+    """Run in a subprocess: time the oracle on images first..first+n-1."""
+    import numpy as np
+
+    import oracle
+    from workloads import WORKLOADS
+
+    w = WORKLOADS[WORKLOAD]
+    st = oracle.init_state(w.filters0().astype(np.float64), 128, 128, w.lam, w.rho)
+    times = []
+    for i in range(first, first + n_images):
+        img = w.image(i)
+        t0 = time.perf_counter()
+        res = oracle.code(st, img, w.Jz)
+        oracle.update_dict(st, [res], w.Jd)
+        times.append(time.perf_counter() - t0)
+    print(json.dumps({"seconds": times}))
+
+
+def run_oracle(n_images: int, first: int = 0) -> list:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-child", str(n_images),
+                          str(first)], capture_output=True, text=True, env=env, cwd=ROOT)
+    if res.returncode != 0:
+        raise RuntimeError(f"oracle leg failed:\n{res.stderr[-2000:]}")
+    return json.loads(res.stdout.strip().splitlines()[-1])["seconds"]
+
+
+def config_dict(extra=None):
+    from workloads import WORKLOADS
+
+    w = WORKLOADS[WORKLOAD]
+    c = {"workload": WORKLOAD, "images": "100x100 zero-padded to 128x128 (FFT 128)",
+         "n_images_stream": w.n_images, "K": w.K, "filter": f"{w.M}x{w.M}", "lambda": w.lam,
+         "rho": w.rho, "batch": w.batch, "Jz": w.Jz, "Jd": w.Jd,
+         "l2": "no flush: each step streams the 336 MB history and writes the 336 MB factor (> 129 MB L2)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# multi-rank helpers
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        if device is not None and dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def reference_arm(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    budget_s = 150.0
+    first = run_oracle(1, 0)
+    steps = max(1, min(args.steps, int(budget_s // max(first[0], 1e-3))))
+    times = first if steps == 1 else first + run_oracle(steps - 1, 1)
+    total = sum(times)
+    value = steps / total
+    sample = f"first {steps} image(s) of the {WORKLOAD} stream, code + dictionary update each"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": 0, "ms_per_step": 1e3 * total / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict({"reference": "FP64 NumPy oracle of the paper's Algorithm 3, one host thread"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def ours_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl")
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_1706_06972_gb300 import build as _build
+
+    if rank == 0:
+        _build.build()
+    barrier(dev)
+    import paper_1706_06972_gb300 as pkg
+    from workloads import WORKLOADS
+
+    w = WORKLOADS[WORKLOAD]
+    N = 128
+    K, W, E = args.steps, args.warmup, args.e2e_steps
+    base = rank * (W + K + E)
+    imgs = [w.image(base + i) for i in range(W + K + E)]
+    x_dev = [torch.from_numpy(im).to(dev) for im in imgs[:W + K]]
+    x_host = [torch.from_numpy(im).pin_memory() for im in imgs[W + K:]]
+    stream = torch.cuda.current_stream(dev)
+    learner = pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_size=N, pad=w.pad, Jz=w.Jz,
+                       Jd=w.Jd, max_batch=1)
+    learner.set_dict(w.filters0(), normalize=True)
+    u_dev = torch.empty((w.K, N, N), device=dev, dtype=torch.float32)
+
+    for i in range(W):
+        learner.code([x_dev[i]], out=[u_dev])
+        learner.update_dict()
+    learner.sync()
+    torch.cuda.synchronize(dev)
+    barrier(dev)
+
+    learner.profile(["fold_factor"])
+    learner.profile_read(["fold_factor"])
+    c0 = learner.counters()
+    gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    barrier(dev)
+    ev0.record(stream)
+    for i in range(W, W + K):
+        learner.code([x_dev[i]], out=[u_dev])
+        learner.update_dict()
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    barrier(dev)
+    t_local = ev0.elapsed_time(ev1) / 1e3
+    t_max = max_over_ranks(t_local, dev)
+    c1 = learner.counters()
+    prof = learner.profile_read(["fold_factor"])["fold_factor"]
+    learner.profile([])
+    learner.sync()
+
+    # Per-kernel breakdown on a few extra steps (context only, not the headline).
+    breakdown = {}
+    if args.breakdown_steps > 0:
+        learner.profile()
+        learner.profile_read()
+        for i in range(args.breakdown_steps):
+            learner.code([x_dev[W + (i % max(K, 1))]], out=[u_dev])
+            learner.update_dict()
+        rd = learner.profile_read()
+        learner.profile([])
+        tot = sum(v[0] for v in rd.values()) or 1.0
+        breakdown = {k: {"ms_per_step": v[0] / args.breakdown_steps, "launches_per_step": v[1] / args.breakdown_steps,
+                         "share": v[0] / tot} for k, v in rd.items()}
+
+    # End to end through the public API with host buffers.
+    e2e = None
+    if E > 0:
+        xd = torch.empty((imgs[0].shape[0], imgs[0].shape[1]), device=dev, dtype=torch.float32)
+        u_host = torch.empty((w.K, N, N), dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize(dev)
+        barrier(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(E):
+            xd.copy_(x_host[i], non_blocking=True)
+            learner.code([xd], out=[u_dev])
+            learner.update_dict()
+            u_host.copy_(u_dev, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        te = max_over_ranks(e0.elapsed_time(e1) / 1e3, dev)
+        e2e = {"value": world * E / te, "unit": UNIT, "h2d_bytes_per_step": int(xd.numel() * 4),
+               "d2h_bytes_per_step": int(u_host.numel() * 4), "steps": E}
+    learner.close()
+
+    if rank != 0:
+        return
+    value = world * K / t_max
+    F = N * (N // 2 + 1)
+    flops = fold_factor_fp64_flops(w.K, F)
+    avg_s = prof[0] / 1e3 / max(prof[1], 1)
+    achieved = flops / avg_s / 1e12
+    roofline = {"kernel": "fold_factor (FP64 per-frequency Cholesky)", "bound": "alu",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": args.traffic if args.traffic is not None else captured_traffic(),
+                "peak_note": "FP64 pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (derived)",
+                "launches": prof[1], "avg_ms": avg_s * 1e3, "flops_per_launch": flops}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        secs = run_oracle(1, 0)
+        cpu = {"value": 1.0 / secs[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"image 0 of {WORKLOAD}: code (50 it) + dictionary update (10 it), FP64 NumPy, 1 thread",
+               "seconds": secs[0]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": 1e3 * t_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": int(c1["kernel_launches"] - c0["kernel_launches"]),
+        "kernel_breakdown": breakdown,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    if len(sys.argv) > 1 and sys.argv[1] == "--oracle-child":
+        _oracle_child(int(sys.argv[2]), int(sys.argv[3]))
+        return
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--breakdown-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per fold_factor launch from an ncu capture of this kernel")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        ours_arm(args)
+
+
+if __name__ == "__main__":
+    main()

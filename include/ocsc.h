@@ -145,6 +145,41 @@ ocsc_status ocsc_sync(ocsc_ctx *ctx);
  * this thread when ctx is NULL (never NULL). */
 const char *ocsc_last_error(const ocsc_ctx *ctx);
 
+/* Kernel classes for ocsc_profile / ocsc_profile_read. */
+typedef enum {
+  OCSC_K_IMAGE_SPECTRUM = 0, /* x~ = F(pad x) */
+  OCSC_K_CODE_RESID = 1,     /* per-frequency residual of the Z~-step */
+  OCSC_K_CODE_PLANE = 2,     /* fused code-ADMM iteration per filter pair */
+  OCSC_K_FOLD_FACTOR = 3,    /* history fold + FP64 Cholesky per frequency */
+  OCSC_K_DSTEP = 4,          /* D-row solve of eq. (sub_d_sol) */
+  OCSC_K_VSTEP_COLS = 5,     /* pruned inverse DFT along the first axis */
+  OCSC_K_VSTEP_PROJECT = 6,  /* Proposition 2 projection, V^, dual update */
+  OCSC_K_DICT_NORMS = 7,     /* |D~(p,:)|^2 of the coding dictionary */
+  OCSC_K_COUNT = 8
+} ocsc_kernel;
+
+typedef struct {
+  uint64_t kernel_launches; /* kernels launched by this context so far */
+  uint64_t samples_coded;   /* samples passed to ocsc_code */
+  uint64_t dict_updates;    /* completed ocsc_update_dict calls that folded samples */
+} ocsc_counters;
+
+/* Counters of ctx (host-side bookkeeping; no synchronisation). */
+ocsc_status ocsc_get_counters(const ocsc_ctx *ctx, ocsc_counters *out);
+
+/*
+ * Enable CUDA-event timing of every launch of the kernel classes whose bit
+ * (1 << ocsc_kernel) is set in mask (0 disables).  Events are recorded on
+ * ctx's stream immediately before and after each launch.
+ */
+ocsc_status ocsc_profile(ocsc_ctx *ctx, unsigned mask);
+
+/*
+ * Total device time (ms) and number of timed launches of one kernel class
+ * since the last read; clears that class's records.  Synchronises.
+ */
+ocsc_status ocsc_profile_read(ocsc_ctx *ctx, int kernel, double *total_ms, uint64_t *launches);
+
 /*
  * Building block: forward 2D DFT (the F of Sec. II-C, unnormalised) of
  * `planes` real N x N float planes x (DEVICE, contiguous) into half spectra

@@ -38,6 +38,14 @@ class ocsc_opts(ctypes.Structure):
     ]
 
 
+class ocsc_counters(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_uint64), ("samples_coded", ctypes.c_uint64),
+                ("dict_updates", ctypes.c_uint64)]
+
+
+KERNELS = ("image_spectrum", "code_resid", "code_plane", "fold_factor", "dstep", "vstep_cols",
+           "vstep_project", "dict_norms")
+
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _PROTOS = {
@@ -53,6 +61,9 @@ _PROTOS = {
     "ocsc_set_dict": (_I, [_P, _P, _I]),
     "ocsc_sync": (_I, [_P]),
     "ocsc_last_error": (ctypes.c_char_p, [_P]),
+    "ocsc_get_counters": (_I, [_P, ctypes.POINTER(ocsc_counters)]),
+    "ocsc_profile": (_I, [_P, ctypes.c_uint]),
+    "ocsc_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
     "ocsc_fft2_r2c": (_I, [_P, _P, _P, _I]),
     "ocsc_fft2_c2r": (_I, [_P, _P, _P, _I]),
 }
@@ -142,6 +153,23 @@ def ocsc_last_error(ctx) -> str:
     return m.decode() if m else ""
 
 
+def ocsc_get_counters(ctx) -> ocsc_counters:
+    c = ocsc_counters()
+    _check(ctx, lib().ocsc_get_counters(ctx, ctypes.byref(c)))
+    return c
+
+
+def ocsc_profile(ctx, mask: int) -> None:
+    _check(ctx, lib().ocsc_profile(ctx, mask))
+
+
+def ocsc_profile_read(ctx, kernel: int):
+    ms = ctypes.c_double()
+    n = ctypes.c_uint64()
+    _check(ctx, lib().ocsc_profile_read(ctx, kernel, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
 def ocsc_fft2_r2c(ctx, x_ptr: int, X_ptr: int, planes: int) -> None:
     _check(ctx, lib().ocsc_fft2_r2c(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(X_ptr), planes))
 
@@ -225,6 +253,22 @@ class OCSC:
 
     def sync(self):
         ocsc_sync(self.ctx)
+
+    def counters(self) -> dict:
+        c = ocsc_get_counters(self.ctx)
+        return {"kernel_launches": c.kernel_launches, "samples_coded": c.samples_coded,
+                "dict_updates": c.dict_updates}
+
+    def profile(self, kernels=KERNELS):
+        """Time every launch of the named kernel classes with CUDA events."""
+        mask = 0
+        for k in kernels:
+            mask |= 1 << KERNELS.index(k)
+        ocsc_profile(self.ctx, mask)
+
+    def profile_read(self, kernels=KERNELS) -> dict:
+        """{kernel: (total ms, launches)} since the last read (synchronises)."""
+        return {k: ocsc_profile_read(self.ctx, KERNELS.index(k)) for k in kernels}
 
     def fft2_r2c(self, x):
         torch = self._torch

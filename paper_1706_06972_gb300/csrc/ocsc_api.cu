@@ -46,6 +46,11 @@ struct ocsc_ctx {
   uint64_t version = 0;
   std::string msg;
   std::vector<void *> allocs;
+  // bookkeeping and optional per-kernel event timing
+  ocsc_counters counters{};
+  unsigned prof_mask = 0;
+  std::vector<cudaEvent_t> prof_ev[OCSC_K_COUNT];  // start/stop pairs
+  size_t prof_used[OCSC_K_COUNT] = {};
 };
 
 namespace {
@@ -103,6 +108,29 @@ double uniform01(uint64_t seed, uint64_t i) {
   return ((double)(splitmix64(seed ^ splitmix64(i)) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
 }
 
+// Launch one kernel through `fn`, counting it and, when its class is being
+// profiled, bracketing it with events on the context's stream.
+template <typename Fn>
+cudaError_t timed(ocsc_ctx *c, int id, Fn &&fn) {
+  c->counters.kernel_launches++;
+  if (!(c->prof_mask & (1u << id))) return fn();
+  auto &ev = c->prof_ev[id];
+  size_t &used = c->prof_used[id];
+  while (used + 2 > ev.size()) {
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    ev.push_back(e);
+  }
+  cudaError_t err = cudaEventRecord(ev[used], c->stream);
+  if (err != cudaSuccess) return err;
+  err = fn();
+  if (err != cudaSuccess) return err;
+  err = cudaEventRecord(ev[used + 1], c->stream);
+  used += 2;
+  return err;
+}
+
 ocsc_status upload_dict(ocsc_ctx *c, const float *D_host, int normalize) {
   const int MM = c->M * c->M;
   std::vector<float> Dn((size_t)c->K * MM);
@@ -117,7 +145,7 @@ ocsc_status upload_dict(ocsc_ctx *c, const float *D_host, int normalize) {
   }
   cudaError_t e = cudaMemcpyAsync(c->V, Dn.data(), Dn.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "upload filters");
-  e = launch_vstep_project(1, c->K, c->N, c->M, nullptr, c->V, c->Vh, c->th, nullptr, c->tw, c->stream);
+  e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_vstep_project(1, c->K, c->N, c->M, nullptr, c->V, c->Vh, c->th, nullptr, c->tw, c->stream); });
   if (e != cudaSuccess) return cuda_fail(c, e, "filter spectrum");
   e = cudaMemsetAsync(c->th, 0, (size_t)c->K * c->F * sizeof(float2), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "reset dual");
@@ -125,7 +153,7 @@ ocsc_status upload_dict(ocsc_ctx *c, const float *D_host, int normalize) {
   // return_feasible = 0.
   e = cudaMemcpyAsync(c->Dcur, c->Vh, (size_t)c->K * c->F * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "seed D~");
-  e = launch_dict_norms(c->K, c->F, c->Vh, c->dn, c->stream);
+  e = timed(c, OCSC_K_DICT_NORMS, [&] { return launch_dict_norms(c->K, c->F, c->Vh, c->dn, c->stream); });
   if (e != cudaSuccess) return cuda_fail(c, e, "dictionary norms");
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "set_dict sync");
@@ -168,6 +196,8 @@ void ocsc_destroy(ocsc_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   for (void *p : ctx->allocs) cudaFree(p);
+  for (auto &v : ctx->prof_ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
   delete ctx;
 }
 
@@ -273,7 +303,7 @@ ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, c
     }
     const int slot = c->pending + s0;
     float2 *xh = c->xhp + (size_t)slot * c->F;
-    cudaError_t e = launch_image_spectrum(c->N, bt, c->tw, xh, c->stream);
+    cudaError_t e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(c->N, bt, c->tw, xh, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "image spectrum");
     CodeIter it{};
     it.K = c->K;
@@ -287,14 +317,17 @@ ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, c
     for (int t = 0; t < c->opts.Jz; ++t) {
       it.first = t == 0;
       it.last = t == c->opts.Jz - 1;
-      e = launch_code_resid(c->N, bt.n, c->K, (float)c->rho, it.first, it.Dh, c->dn, xh, it.What,
-                            c->r + (size_t)slot * c->F, c->stream);
+      e = timed(c, OCSC_K_CODE_RESID, [&] {
+        return launch_code_resid(c->N, bt.n, c->K, (float)c->rho, it.first, it.Dh, c->dn, xh, it.What,
+                                 c->r + (size_t)slot * c->F, c->stream);
+      });
       if (e != cudaSuccess) return cuda_fail(c, e, "code_resid");
-      e = launch_code_plane(c->N, it, bt, c->tw, c->stream);
+      e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(c->N, it, bt, c->tw, c->stream); });
       if (e != cudaSuccess) return cuda_fail(c, e, "code_plane");
     }
   }
   c->pending += n;
+  c->counters.samples_coded += n;
   return OCSC_OK;
 }
 
@@ -326,21 +359,22 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
   fa.L = c->L;
   fa.g = c->g;
   fa.err = c->err;
-  e = launch_fold_factor(fa, c->stream);
+  e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_factor(fa, c->stream); });
   if (e != cudaSuccess) return cuda_fail(c, e, "fold_factor");
   for (int t = 0; t < c->opts.Jd; ++t) {
-    e = launch_dstep(c->K, c->F, (float)rho_eff, c->L, c->g, c->Vh, c->th, c->Dcur, c->E, c->stream);
+    e = timed(c, OCSC_K_DSTEP, [&] { return launch_dstep(c->K, c->F, (float)rho_eff, c->L, c->g, c->Vh, c->th, c->Dcur, c->E, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "dstep");
-    e = launch_vstep_cols(c->K, c->N, c->M, c->E, c->tw, c->Y, c->stream);
+    e = timed(c, OCSC_K_VSTEP_COLS, [&] { return launch_vstep_cols(c->K, c->N, c->M, c->E, c->tw, c->Y, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "vstep_cols");
-    e = launch_vstep_project(0, c->K, c->N, c->M, c->Y, c->V, c->Vh, c->th, c->Dcur, c->tw, c->stream);
+    e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_vstep_project(0, c->K, c->N, c->M, c->Y, c->V, c->Vh, c->th, c->Dcur, c->tw, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "vstep_project");
   }
-  e = launch_dict_norms(c->K, c->F, c->opts.return_feasible ? c->Vh : c->Dcur, c->dn, c->stream);
+  e = timed(c, OCSC_K_DICT_NORMS, [&] { return launch_dict_norms(c->K, c->F, c->opts.return_feasible ? c->Vh : c->Dcur, c->dn, c->stream); });
   if (e != cudaSuccess) return cuda_fail(c, e, "dict_norms");
   c->n_seen += B;
   c->pending = 0;
   c->version += 1;
+  c->counters.dict_updates += 1;
   return OCSC_OK;
 }
 
@@ -374,15 +408,48 @@ ocsc_status ocsc_sync(ocsc_ctx *c) {
 ocsc_status ocsc_fft2_r2c(ocsc_ctx *c, const float *x, float *X, int planes) {
   if (!c) return OCSC_EINVAL;
   if (!x || !X || planes < 0) return fail(c, OCSC_EINVAL, "fft2_r2c: bad arguments");
-  cudaError_t e = launch_fft2(c->N, 0, x, X, planes, c->tw, c->stream);
+  cudaError_t e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(c->N, 0, x, X, planes, c->tw, c->stream); });
   return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "fft2_r2c");
 }
 
 ocsc_status ocsc_fft2_c2r(ocsc_ctx *c, const float *X, float *x, int planes) {
   if (!c) return OCSC_EINVAL;
   if (!x || !X || planes < 0) return fail(c, OCSC_EINVAL, "fft2_c2r: bad arguments");
-  cudaError_t e = launch_fft2(c->N, 1, X, x, planes, c->tw, c->stream);
+  cudaError_t e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(c->N, 1, X, x, planes, c->tw, c->stream); });
   return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "fft2_c2r");
+}
+
+ocsc_status ocsc_get_counters(const ocsc_ctx *c, ocsc_counters *out) {
+  if (!c || !out) return OCSC_EINVAL;
+  *out = c->counters;
+  return OCSC_OK;
+}
+
+ocsc_status ocsc_profile(ocsc_ctx *c, unsigned mask) {
+  if (!c) return OCSC_EINVAL;
+  c->prof_mask = mask & ((1u << OCSC_K_COUNT) - 1u);
+  return OCSC_OK;
+}
+
+ocsc_status ocsc_profile_read(ocsc_ctx *c, int kernel, double *total_ms, uint64_t *launches) {
+  if (!c) return OCSC_EINVAL;
+  if (kernel < 0 || kernel >= OCSC_K_COUNT || !total_ms || !launches)
+    return fail(c, OCSC_EINVAL, "profile_read: bad arguments");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "profile_read sync");
+  double ms = 0;
+  auto &ev = c->prof_ev[kernel];
+  const size_t used = c->prof_used[kernel];
+  for (size_t i = 0; i + 1 < used; i += 2) {
+    float t = 0;
+    e = cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "profile_read elapsed");
+    ms += t;
+  }
+  *total_ms = ms;
+  *launches = used / 2;
+  c->prof_used[kernel] = 0;
+  return OCSC_OK;
 }
 
 }  // extern "C"

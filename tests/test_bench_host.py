@@ -1,0 +1,71 @@
+"""Host-side logic of bench.py on CPU: multi-rank aggregation over gloo
+(world size 2) and the algorithmic FLOP count of the FP64 factor kernel."""
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t = bench.max_over_ranks(1.5 + rank)   # rank 1 is the slow one
+    bench.barrier()
+    q.put((rank, t, bench.dist_env()))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_world2():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[1] for o in out] == [2.5, 2.5]
+    assert out[0][2] == (2, 0, 0) and out[1][2] == (2, 1, 1)
+
+
+def test_single_process_aggregation_is_identity():
+    assert bench.max_over_ranks(3.25) == 3.25
+
+
+def _count_fold_factor_flops(K):
+    """Count the kernel's FP64 operations by walking its loops (8 flops per
+    complex multiply-add, 2 per complex-by-real scaling)."""
+    f = 0
+    for j in range(K):
+        f += 2 * (K - j - 1)                 # column scaling by 1/L_jj
+        n = K - j - 1
+        f += 8 * n * (n + 1) // 2            # trailing update
+    f += 8 * K * (K - 1) // 2                # forward substitution for g
+    f += 8 * K * (K - 1) // 2                # backward substitution for g
+    return f
+
+
+@pytest.mark.parametrize("K", [1, 2, 16, 100])
+def test_fold_factor_flop_count(K):
+    assert bench.fold_factor_fp64_flops(K, 1) == pytest.approx(_count_fold_factor_flops(K))
+
+
+def test_fp64_peak_is_derived_from_unit_counts():
+    assert bench.FP64_PEAK_TFLOPS == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
