@@ -192,6 +192,41 @@ ocsc_status ocsc_fft2_r2c(ocsc_ctx *ctx, const float *x, float *X, int planes);
  * input half spectra must be those of real planes (Hermitian symmetric). */
 ocsc_status ocsc_fft2_c2r(ocsc_ctx *ctx, const float *X, float *x, int planes);
 
+/* Size of the fixed device array used by ocsc_code_noalloc (32 MiB). */
+#define OCSC_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * Allocation-free coding of one image.  The paper has no counterpart: this is
+ * a deployment variant of ocsc_code for callers that must not allocate device
+ * memory while they run -- for instance a plug-in whose host application has
+ * reserved all device memory through its own allocator, a latency-critical
+ * pipeline that cannot absorb the device-wide synchronisation cudaMalloc and
+ * cudaFree may cause, or a service that must not fail at run time for lack of
+ * memory.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * It codes the H x W image x (DEVICE floats, zero-padded at the end of both
+ * axes to N x N, N in {64, 128}, H, W <= N) against the K filters D (DEVICE,
+ * K x M x M floats, M <= 16, used as given) with Jz code-ADMM iterations of
+ * ocsc_code's kernels, and writes the sparse code U (DEVICE, K x N x N floats,
+ * caller-owned) -- the same result ocsc_code gives for that image and
+ * dictionary.  Work is enqueued on cuda_stream (a cudaStream_t; NULL = legacy
+ * default stream); the call is asynchronous.  err (nullable, err_len bytes)
+ * receives a message on failure.
+ *
+ * Scratch lives in one file-scope device array of OCSC_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading the library holds until the process exits.  The scratch
+ * needed is about K * (3 N (N/2+1) * 8 + N * N * 4) bytes (K <= 125 at N = 128,
+ * K <= 128 at N = 64); larger requests return OCSC_EUNSUPPORTED without
+ * touching the device.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current.  All calls
+ * share the array and it keeps the last call's contents (nothing needs to start
+ * at zero); calls whose work overlaps on the GPU -- on different streams or from
+ * different host threads -- race on it and must be serialised by the caller.
+ */
+ocsc_status ocsc_code_noalloc(const float *x, int H, int W, const float *D, int K, int M, int N,
+                              double lambda, double rho, int Jz, float *u, void *cuda_stream,
+                              char *err, size_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,8 @@ _PROTOS = {
     "ocsc_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
     "ocsc_fft2_r2c": (_I, [_P, _P, _P, _I]),
     "ocsc_fft2_c2r": (_I, [_P, _P, _P, _I]),
+    "ocsc_code_noalloc": (_I, [_P, _I, _I, _P, _I, _I, _I, ctypes.c_double, ctypes.c_double, _I, _P,
+                               _P, ctypes.c_char_p, ctypes.c_size_t]),
 }
 EXPORTED = tuple(_PROTOS)
 
@@ -176,6 +178,19 @@ def ocsc_fft2_r2c(ctx, x_ptr: int, X_ptr: int, planes: int) -> None:
 
 def ocsc_fft2_c2r(ctx, X_ptr: int, x_ptr: int, planes: int) -> None:
     _check(ctx, lib().ocsc_fft2_c2r(ctx, ctypes.c_void_p(X_ptr), ctypes.c_void_p(x_ptr), planes))
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def ocsc_code_noalloc(x_ptr: int, H: int, W: int, D_ptr: int, K: int, M: int, N: int, lam: float,
+                      rho: float, Jz: int, u_ptr: int, stream: int = 0) -> None:
+    """Code one image without any device allocation (see include/ocsc.h)."""
+    buf = ctypes.create_string_buffer(512)
+    st = lib().ocsc_code_noalloc(ctypes.c_void_p(x_ptr), H, W, ctypes.c_void_p(D_ptr), K, M, N, lam,
+                                 rho, Jz, ctypes.c_void_p(u_ptr), ctypes.c_void_p(stream), buf, 512)
+    if st != 0:
+        raise OCSCError(st, buf.value.decode())
 
 
 # --- torch convenience wrapper --------------------------------------------------

@@ -1,0 +1,152 @@
+// Allocation-free coding entry point (ocsc_code_noalloc).
+//
+// Some callers cannot allocate device memory when they code an image: a plug-in
+// whose host application has already reserved the whole device through its own
+// allocator, a latency-sensitive pipeline that cannot afford the device-wide
+// synchronisation that cudaMalloc / cudaFree can imply while other streams run,
+// or a deployment that must not fail at run time for lack of memory and so
+// takes everything it needs when the library is loaded.  For them this file
+// keeps the scratch of one coding call in a fixed file-scope device array and
+// runs the same kernels as ocsc_code on it.  The caller still provides the
+// image, the filters and the output buffer.
+//
+// The array below is part of the library image: every GPU that loads the
+// library holds OCSC_NOALLOC_SCRATCH_BYTES of it until the process exits.  All
+// calls share it and it keeps whatever the last call left there; nothing has to
+// start at zero because the first ADMM iteration reads no earlier state.  Two
+// calls whose work overlaps on the GPU (other streams, other host threads)
+// overwrite each other's scratch: serialise them.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <vector>
+
+#include "../../include/ocsc.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace ocsc;
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[OCSC_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+void *g_scratch_addr[kMaxDevices] = {};  // device address of the array, per device
+std::mutex g_scratch_mu;
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Carve {
+  size_t tw, Dh, dn, xh, r, What, Zp, Gam, total;
+};
+
+Carve carve(int K, int N) {
+  const size_t F = (size_t)N * (N / 2 + 1), P = (size_t)N * N;
+  Carve c{};
+  size_t o = 0;
+  c.tw = o;   o += up256(N * sizeof(float2));
+  c.Dh = o;   o += up256(K * F * sizeof(float2));
+  c.dn = o;   o += up256(F * sizeof(float));
+  c.xh = o;   o += up256(F * sizeof(float2));
+  c.r = o;    o += up256(F * sizeof(float2));
+  c.What = o; o += up256(K * F * sizeof(float2));
+  c.Zp = o;   o += up256(K * F * sizeof(float2));
+  c.Gam = o;  o += up256(K * P * sizeof(float));
+  c.total = o;
+  return c;
+}
+
+ocsc_status say(char *err, size_t len, ocsc_status s, const char *fmt, ...) {
+  if (err && len > 0) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(err, len, fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+}  // namespace
+
+extern "C" ocsc_status ocsc_code_noalloc(const float *x, int H, int W, const float *D, int K, int M,
+                                         int N, double lambda, double rho, int Jz, float *u,
+                                         void *cuda_stream, char *err, size_t err_len) {
+  if (err && err_len > 0) err[0] = '\0';
+  if (!x || !D || !u) return say(err, err_len, OCSC_EINVAL, "null image, filter or output pointer");
+  if (N != 64 && N != 128) return say(err, err_len, OCSC_EUNSUPPORTED, "N=%d: only 64 or 128", N);
+  if (H <= 0 || W <= 0 || H > N || W > N)
+    return say(err, err_len, OCSC_EINVAL, "image %dx%d does not fit the %dx%d domain", H, W, N, N);
+  if (K <= 0 || K > 128 || M <= 0 || M > 16 || M > N)
+    return say(err, err_len, OCSC_EUNSUPPORTED, "K=%d, M=%d outside 1..128 and 1..16", K, M);
+  if (!(lambda >= 0) || !(rho > 0) || Jz < 1)
+    return say(err, err_len, OCSC_EINVAL, "need lambda >= 0, rho > 0, Jz >= 1");
+  const Carve cv = carve(K, N);
+  if (cv.total > (size_t)OCSC_NOALLOC_SCRATCH_BYTES)
+    return say(err, err_len, OCSC_EUNSUPPORTED,
+               "K=%d at N=%d needs %zu bytes of scratch; the fixed array holds %zu", K, N, cv.total,
+               (size_t)OCSC_NOALLOC_SCRATCH_BYTES);
+
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return say(err, err_len, OCSC_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return say(err, err_len, OCSC_EUNSUPPORTED, "device %d", dev);
+  unsigned char *base = nullptr;
+  {
+    // First call on this device: look up the array's device address (host code
+    // only sees a host-side stand-in for the symbol).
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess)
+        return say(err, err_len, OCSC_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      g_scratch_addr[dev] = p;
+    }
+    base = static_cast<unsigned char *>(g_scratch_addr[dev]);
+  }
+
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int F = N * (N / 2 + 1);
+  float2 *tw = reinterpret_cast<float2 *>(base + cv.tw);
+  float2 *Dh = reinterpret_cast<float2 *>(base + cv.Dh);
+  float *dn = reinterpret_cast<float *>(base + cv.dn);
+  float2 *xh = reinterpret_cast<float2 *>(base + cv.xh);
+  float2 *r = reinterpret_cast<float2 *>(base + cv.r);
+
+  std::vector<float2> twh(N);
+  for (int m = 0; m < N; ++m) {
+    const double a = -2.0 * M_PI * (double)m / (double)N;
+    twh[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  e = cudaMemcpyAsync(tw, twh.data(), N * sizeof(float2), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return say(err, err_len, OCSC_ECUDA, "twiddles: %s", cudaGetErrorString(e));
+  // D~ = F(pad D) and |D~(p,:)|^2, then the same code-ADMM launches as ocsc_code.
+  e = launch_vstep_project(1, K, N, M, nullptr, const_cast<float *>(D), Dh, nullptr, nullptr, tw, s);
+  if (e == cudaSuccess) e = launch_dict_norms(K, F, Dh, dn, s);
+  ImgBatch b{};
+  b.n = 1;
+  b.x[0] = x;
+  b.u[0] = u;
+  b.H[0] = H;
+  b.W[0] = W;
+  if (e == cudaSuccess) e = launch_image_spectrum(N, b, tw, xh, s);
+  CodeIter it{};
+  it.K = K;
+  it.F = F;
+  it.thr = (float)(lambda / rho);
+  it.Dh = Dh;
+  it.r = r;
+  it.What = reinterpret_cast<float2 *>(base + cv.What);
+  it.Gam = reinterpret_cast<float *>(base + cv.Gam);
+  it.Zp = reinterpret_cast<float2 *>(base + cv.Zp);
+  for (int t = 0; t < Jz && e == cudaSuccess; ++t) {
+    it.first = t == 0;
+    it.last = t == Jz - 1;
+    e = launch_code_resid(N, 1, K, (float)rho, it.first, Dh, dn, xh, it.What, r, s);
+    if (e == cudaSuccess) e = launch_code_plane(N, it, b, tw, s);
+  }
+  if (e != cudaSuccess) return say(err, err_len, OCSC_ECUDA, "launch: %s", cudaGetErrorString(e));
+  return OCSC_OK;
+}
