@@ -40,8 +40,8 @@ FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM bytes per fold_factor launch from an ncu capture of this workload
 # (profiles/fold_factor_plain_100in128_k100.md), valid only while the kernel
 # source is the one captured (sha1 of dict_update.cu).
-TRAFFIC_CAPTURE = {"bytes": 351.823360e6 + 626.167552e6,
-                   "source_sha1": "b12b1216483b55dd30401973b0e9148cf900b9c7"}
+TRAFFIC_CAPTURE = {"bytes": 350.745856e6 + 625.610240e6,
+                   "source_sha1": "3e10f509a7572bf5ed2e5c571dc6a38ef4e95b49"}
 
 
 def captured_traffic():
@@ -56,9 +56,10 @@ def captured_traffic():
 def fold_factor_fp64_flops(K: int, F: int) -> float:
     """Algorithmic FP64 flops of one fold_factor launch (all F frequencies):
     right-looking complex Cholesky (K^3/6 complex MACs + column scaling) and the
-    two triangular solves for g, at 8 flops per complex MAC."""
+    forward substitution of the right-hand side carried along, at 8 flops per
+    complex MAC.  The FP32 work of the kernel (fold, X = L^-1) is not counted."""
     chol = 8.0 * (K - 1) * K * (K + 1) / 6.0 + 1.0 * K * (K - 1)
-    solves = 8.0 * K * (K - 1)
+    solves = 8.0 * K * (K - 1) / 2.0
     return F * (chol + solves)
 
 

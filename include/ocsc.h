@@ -11,9 +11,10 @@
  *                       new codes into the per-frequency history A^p, b^p
  *                       (Sec. III-B, eqs. (A_update), (B_update)), then
  *                       DictOCSC (Algorithm 2): the D-row solve of eq.
- *                       (sub_d_sol) with C^p = (A^p + rho I)^-1 held as an FP64
- *                       Cholesky factor, the support + unit-ball projection of
- *                       Proposition 2 and the scaled dual update.
+ *                       (sub_d_sol) with C^p = (A^p + rho I)^-1 = X^H X, X the
+ *                       inverse of an FP64 Cholesky factor, the support +
+ *                       unit-ball projection of Proposition 2 and the scaled
+ *                       dual update.
  *   ocsc_get_dict    -- the filters D_t (Algorithm 3, last loop).
  *
  * Conventions (shared by every call):
@@ -150,12 +151,13 @@ typedef enum {
   OCSC_K_IMAGE_SPECTRUM = 0, /* x~ = F(pad x) */
   OCSC_K_CODE_RESID = 1,     /* per-frequency residual of the Z~-step */
   OCSC_K_CODE_PLANE = 2,     /* fused code-ADMM iteration per filter pair */
-  OCSC_K_FOLD_FACTOR = 3,    /* history fold + FP64 Cholesky per frequency */
+  OCSC_K_FOLD_FACTOR = 3,    /* history fold + FP64 Cholesky + FP32 L^-1 per frequency */
   OCSC_K_DSTEP = 4,          /* D-row solve of eq. (sub_d_sol) */
   OCSC_K_VSTEP_COLS = 5,     /* pruned inverse DFT along the first axis */
-  OCSC_K_VSTEP_PROJECT = 6,  /* Proposition 2 projection, V^, dual update */
+  OCSC_K_VSTEP_PROJECT = 6,  /* Proposition 2 projection of the support */
   OCSC_K_DICT_NORMS = 7,     /* |D~(p,:)|^2 of the coding dictionary */
-  OCSC_K_COUNT = 8
+  OCSC_K_VSTEP_SPECTRUM = 8, /* V^ = F(pad V) and the dual update */
+  OCSC_K_COUNT = 9
 } ocsc_kernel;
 
 typedef struct {
@@ -215,8 +217,8 @@ ocsc_status ocsc_fft2_c2r(ocsc_ctx *ctx, const float *X, float *x, int planes);
  *
  * Scratch lives in one file-scope device array of OCSC_NOALLOC_SCRATCH_BYTES
  * that every GPU loading the library holds until the process exits.  The scratch
- * needed is about K * (3 N (N/2+1) * 8 + N * N * 4) bytes (K <= 125 at N = 128,
- * K <= 128 at N = 64); larger requests return OCSC_EUNSUPPORTED without
+ * needed is about K * ((3 N + 16) (N/2+1) * 8 + N * N * 4) bytes (K <= 122 at
+ * N = 128, K <= 128 at N = 64); larger requests return OCSC_EUNSUPPORTED without
  * touching the device.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current.  All calls
  * share the array and it keeps the last call's contents (nothing needs to start

@@ -44,7 +44,7 @@ class ocsc_counters(ctypes.Structure):
 
 
 KERNELS = ("image_spectrum", "code_resid", "code_plane", "fold_factor", "dstep", "vstep_cols",
-           "vstep_project", "dict_norms")
+           "vstep_project", "dict_norms", "vstep_spectrum")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int

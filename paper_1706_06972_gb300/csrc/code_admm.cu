@@ -72,6 +72,7 @@ __global__ void code_resid_kernel(int K, int F, float rho, int first,
   float2 s = make_float2(0.f, 0.f);
   if (!first && p < F) {
     const float2 *w = What + (size_t)img * K * F;
+#pragma unroll 4
     for (int k = ty; k < K; k += 8) s = cadd(s, cmul(Dh[(size_t)k * F + p], w[(size_t)k * F + p]));
   }
   part[ty][tx] = s;

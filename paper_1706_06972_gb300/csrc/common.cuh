@@ -26,14 +26,20 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 // Offset of column j: j*K - j*(j-1)/2.
 __host__ __device__ __forceinline__ int tri_off(int j, int K) { return j * (2 * K - j + 1) / 2; }
 __host__ __device__ __forceinline__ int tri_size(int K) { return K * (K + 1) / 2; }
+// Per-frequency stride of packed complex-FP32 matrices in global memory: the
+// triangle rounded up to an even element count, so every frequency starts on a
+// 16-byte boundary.
+__host__ __device__ __forceinline__ int tri_stride(int K) { return (tri_size(K) + 1) & ~1; }
 
 // Inverse of tri_off: packed index t -> (i, j) with i >= j.
 __device__ __forceinline__ void tri_ij(int t, int K, int &i, int &j) {
   const float kf = 2.0f * K + 1.0f;
   int jj = (int)floorf(0.5f * (kf - sqrtf(fmaxf(kf * kf - 8.0f * (float)t, 0.0f))));
   jj = max(0, min(jj, K - 1));
-  while (jj > 0 && tri_off(jj, K) > t) --jj;
-  while (jj < K - 1 && tri_off(jj + 1, K) <= t) ++jj;
+  // The float estimate is off by at most one column (all operands are exact
+  // integers below 2^24 and sqrtf is correctly rounded).
+  if (jj < K - 1 && tri_off(jj + 1, K) <= t) ++jj;
+  else if (jj > 0 && tri_off(jj, K) > t) --jj;
   j = jj;
   i = t - tri_off(jj, K) + jj;
 }

@@ -6,42 +6,77 @@
 // solve of eq. (sub_d_sol) is d = (w A^p + rho I)^-1 (w b^p + rho (v^ - theta^)).
 // Its matrix is fixed during the Jd ADMM iterations, so it is factored once per
 // update: fold_factor folds the pending codes into A and b, forms w A + rho I in
-// FP64 in shared memory, factors it by Cholesky in FP64 and stores L (FP32,
-// reciprocal diagonal) together with g = (w A + rho I)^-1 (w b) computed in
-// FP64.  Each ADMM iteration then solves with L in FP32 (dstep), forms the V
-// update of Proposition 2 from a pruned inverse DFT restricted to the M x M
-// support (vstep_cols, vstep_project), and updates the scaled dual.
+// FP64 in shared memory, factors it by Cholesky in FP64 (L), and alongside it
+// computes X = L^-1 in FP32 and y = L^-1 (w b) from the FP64 sweep.  Each ADMM
+// iteration then applies d = X^H (y + rho X (v^ - theta^)) in FP32 (dstep),
+// forms the V update of Proposition 2 from a pruned inverse DFT restricted to
+// the M x M support (vstep_cols, vstep_project, vstep_spectrum), and updates
+// the scaled dual.
 #include "common.cuh"
 #include "launch.h"
 
 namespace ocsc {
 
-__device__ __forceinline__ double2 dcmul_sub(double2 acc, double2 a, double2 b_conj_src) {
-  // acc - a * conj(b)
-  acc.x -= a.x * b_conj_src.x + a.y * b_conj_src.y;
-  acc.y -= a.y * b_conj_src.x - a.x * b_conj_src.y;
-  return acc;
+// acc -= a * conj(b) as four FP64 FMAs.
+__device__ __forceinline__ void cfms_conj(double2 &acc, double2 a, double2 b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(-a.y, b.x, acc.y);
+  acc.y = fma(a.x, b.y, acc.y);
+}
+// acc -= a * b as four FP64 FMAs.
+__device__ __forceinline__ void cfms(double2 &acc, double2 a, double2 b) {
+  acc.x = fma(-a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
 }
 
 constexpr int kFoldThreads = 256;
 constexpr int kFoldChunk = 16;  // samples staged in shared memory at once
 
 // One CTA per frequency p.
+//
+// 1-2. Fold the pending codes into the FP32 running means A^p, b^p and form
+//      M = w A + rho I, y = w b in FP64.
+// 3.   Right-looking FP64 Cholesky on the packed lower triangle, with y carried
+//      as an extra column (forward substitution: y <- L^-1 w b).  One step
+//      behind it, the same threads run the right-looking forward substitution
+//      of L X = I in FP32 (X = L^-1): after column s of L is final, row s of X
+//      is scaled by 1/L_ss and every X_ic with i > s, c <= s gets
+//      X_ic -= L_is X_sc.  The FP32 update of step s runs in the same phase as
+//      the FP64 trailing update of step s+1, on the other pipe, and writes only
+//      slots of columns <= s, whose FP64 values are no longer read: the low 8
+//      bytes of such a slot then hold X_ic.  L's column s (FP32 copy) and X's
+//      row s are kept in small buffers so those reads are broadcasts.
+// 4.   Store X (FP32, packed lower) and y (FP32).
+//
+// Shared memory: M [T] double2, y [K] double2, invd [K] double, Lcol [2][K]
+// float2, Xrow [K] float2, zs / xs (a chunk of pending codes).  During the
+// fold each M slot first holds the FP32 running sum of conj(z_i) z_j in its low
+// 8 bytes.
 __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int K = a.K, F = a.F, B = a.B;
   const int T = tri_size(K);
   double2 *M = reinterpret_cast<double2 *>(fsm);                 // [T]
-  double2 *rhs = M + T;                                          // [K]
-  float2 *zs = reinterpret_cast<float2 *>(rhs + K);              // [kFoldChunk][K]
+  double2 *y = M + T;                                            // [K]
+  double *invd = reinterpret_cast<double *>(y + K);              // [K]
+  float2 *Lcol = reinterpret_cast<float2 *>(invd + K);           // [2][K]
+  float2 *Xrow = Lcol + 2 * K;                                   // [K]
+  float2 *zs = Xrow + K;                                         // [kFoldChunk][K]
   float2 *xs = zs + kFoldChunk * K;                              // [kFoldChunk]
+  float2 *S = reinterpret_cast<float2 *>(M);                     // FP32 sums, stride 2
+  float2 *XS = reinterpret_cast<float2 *>(M);                    // X_ic at slot t: XS[2 t]
   const int p = blockIdx.x;
   const int tid = threadIdx.x;
 
-  for (int t = tid; t < T; t += kFoldThreads) M[t] = make_double2(0.0, 0.0);
-  for (int i = tid; i < K; i += kFoldThreads) rhs[i] = make_double2(0.0, 0.0);
+  for (int t = tid; t < T; t += kFoldThreads) S[2 * t] = make_float2(0.f, 0.f);
+  float2 sb[(128 + kFoldThreads - 1) / kFoldThreads];
+#pragma unroll
+  for (int m = 0; m < (128 + kFoldThreads - 1) / kFoldThreads; ++m) sb[m] = make_float2(0.f, 0.f);
 
-  // 1. Sum over the pending samples of conj(z_i) z_j and x~ conj(z_i).
+  // 1. FP32 sums over the pending samples of conj(z_i) z_j and x~ conj(z_i).
   for (int c0 = 0; c0 < B; c0 += kFoldChunk) {
     const int nb = min(kFoldChunk, B - c0);
     __syncthreads();
@@ -54,271 +89,284 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
     for (int t = tid; t < T; t += kFoldThreads) {
       int i, j;
       tri_ij(t, K, i, j);
-      float2 acc = make_float2(0.f, 0.f);
+      float2 acc = S[2 * t];
       for (int s = 0; s < nb; ++s) acc = cadd(acc, cconjmul(zs[s * K + i], zs[s * K + j]));
-      M[t].x += (double)acc.x;
-      M[t].y += (double)acc.y;
+      S[2 * t] = acc;
     }
-    for (int i = tid; i < K; i += kFoldThreads) {
-      float2 acc = make_float2(0.f, 0.f);
-      for (int s = 0; s < nb; ++s) acc = cadd(acc, cmulc(xs[s], zs[s * K + i]));
-      rhs[i].x += (double)acc.x;
-      rhs[i].y += (double)acc.y;
+#pragma unroll
+    for (int m = 0; m < (128 + kFoldThreads - 1) / kFoldThreads; ++m) {
+      const int i = tid + m * kFoldThreads;
+      if (i < K)
+        for (int s = 0; s < nb; ++s) sb[m] = cadd(sb[m], cmulc(xs[s], zs[s * K + i]));
     }
   }
   __syncthreads();
 
-  // 2. Running means (FP32 storage) and the FP64 matrix w A + rho I.
-  float2 *Ap = a.A + (size_t)p * T;
+  // 2. Running means in FP32 (stored), and M = w A + rho I, y = w b in FP64.
+  float2 *Ap = a.A + (size_t)p * tri_stride(K);
+  const float alpha = (float)a.alpha, beta = (float)a.beta;
   for (int t = tid; t < T; t += kFoldThreads) {
     int i, j;
     tri_ij(t, K, i, j);
     const float2 old = a.first ? make_float2(0.f, 0.f) : Ap[t];
-    const float2 nw = make_float2((float)(a.alpha * old.x + a.beta * M[t].x),
-                                  (float)(a.alpha * old.y + a.beta * M[t].y));
+    const float2 sum = S[2 * t];
+    const float2 nw = make_float2(fmaf(alpha, old.x, beta * sum.x), fmaf(alpha, old.y, beta * sum.y));
     Ap[t] = nw;
-    M[t] = make_double2(a.w * nw.x + (i == j ? a.rho_eff : 0.0), i == j ? 0.0 : a.w * nw.y);
+    M[t] = (i == j) ? make_double2(a.w * (double)nw.x + a.rho_eff, 0.0)
+                    : make_double2(a.w * (double)nw.x, a.w * (double)nw.y);
   }
-  for (int i = tid; i < K; i += kFoldThreads) {
-    const float2 old = a.first ? make_float2(0.f, 0.f) : a.b[(size_t)i * F + p];
-    const float2 nw = make_float2((float)(a.alpha * old.x + a.beta * rhs[i].x),
-                                  (float)(a.alpha * old.y + a.beta * rhs[i].y));
-    a.b[(size_t)i * F + p] = nw;
-    rhs[i] = make_double2(a.w * nw.x, a.w * nw.y);
+#pragma unroll
+  for (int m = 0; m < (128 + kFoldThreads - 1) / kFoldThreads; ++m) {
+    const int i = tid + m * kFoldThreads;
+    if (i < K) {
+      const float2 old = a.first ? make_float2(0.f, 0.f) : a.b[(size_t)i * F + p];
+      const float2 nw = make_float2(fmaf(alpha, old.x, beta * sb[m].x), fmaf(alpha, old.y, beta * sb[m].y));
+      a.b[(size_t)i * F + p] = nw;
+      y[i] = make_double2(a.w * (double)nw.x, a.w * (double)nw.y);
+    }
   }
   __syncthreads();
 
-  // 3. Right-looking Cholesky in FP64 on the packed lower triangle.
-  for (int j = 0; j < K; ++j) {
-    const int oj = tri_off(j, K);
-    double piv = M[oj].x;
+  // 3. Cholesky (FP64) with the FP32 inverse one step behind.
+  if (tid == 0) {
+    double piv = M[0].x;
     if (!(piv > 0.0)) {
-      if (tid == 0) atomicOr(a.err, ERR_PIVOT);
+      atomicOr(a.err, ERR_PIVOT);
       piv = a.rho_eff > 0.0 ? a.rho_eff : 1.0;
     }
-    const double ljj = sqrt(piv);
-    const double inv = 1.0 / ljj;
-    for (int i = j + 1 + tid; i < K; i += kFoldThreads) {
-      M[oj + i - j].x *= inv;
-      M[oj + i - j].y *= inv;
-    }
-    __syncthreads();
-    if (tid == 0) M[oj] = make_double2(ljj, 0.0);
-    const int n = K - j - 1;
-    const int nt = tri_size(n);
-    for (int u = tid; u < nt; u += kFoldThreads) {
-      int ii, kk;
-      tri_ij(u, n, ii, kk);
-      const int i = j + 1 + ii, k = j + 1 + kk;
-      const double2 lij = M[oj + i - j];
-      const double2 lkj = M[oj + k - j];
-      const int dst = tri_off(k, K) + i - k;
-      M[dst] = dcmul_sub(M[dst], lij, lkj);
-    }
-    __syncthreads();
-  }
-
-  // 4. g = L^-H L^-1 (w b) in FP64 by one warp (column-oriented substitutions).
-  if (tid < 32) {
-    const int lane = tid;
-    for (int j = 0; j < K; ++j) {
-      const int oj = tri_off(j, K);
-      if (lane == 0) {
-        const double inv = 1.0 / M[oj].x;
-        rhs[j].x *= inv;
-        rhs[j].y *= inv;
-      }
-      __syncwarp();
-      const double2 yj = rhs[j];
-      for (int i = j + 1 + lane; i < K; i += 32) {
-        const double2 l = M[oj + i - j];
-        rhs[i].x -= l.x * yj.x - l.y * yj.y;
-        rhs[i].y -= l.x * yj.y + l.y * yj.x;
-      }
-      __syncwarp();
-    }
-    for (int j = K - 1; j >= 0; --j) {
-      const int oj = tri_off(j, K);
-      if (lane == 0) {
-        const double inv = 1.0 / M[oj].x;
-        rhs[j].x *= inv;
-        rhs[j].y *= inv;
-      }
-      __syncwarp();
-      const double2 xj = rhs[j];
-      for (int i = lane; i < j; i += 32) {
-        const double2 l = M[tri_off(i, K) + j - i];   // L_ji; L^H_ij = conj(L_ji)
-        rhs[i].x -= l.x * xj.x + l.y * xj.y;
-        rhs[i].y -= l.x * xj.y - l.y * xj.x;
-      }
-      __syncwarp();
-    }
+    const double l = sqrt(piv);
+    M[0] = make_double2(l, 0.0);
+    invd[0] = 1.0 / l;
   }
   __syncthreads();
-
-  // 5. Store L (FP32, reciprocal diagonal) and g.
-  float2 *Lp = a.L + (size_t)p * T;
-  for (int t = tid; t < T; t += kFoldThreads) {
-    int i, j;
-    tri_ij(t, K, i, j);
-    const double2 v = M[t];
-    Lp[t] = (i == j) ? make_float2((float)(1.0 / v.x), 0.f) : make_float2((float)v.x, (float)v.y);
+  for (int j = 0; j <= K; ++j) {
+    // --- scale phase: column j of L (FP64 + FP32 copy), row j-1 of X.
+    if (j < K) {
+      const int oj = tri_off(j, K);
+      const double inv = invd[j];
+      float2 *lc = Lcol + (j & 1) * K;
+      for (int i = j + 1 + tid; i < K; i += kFoldThreads) {
+        double2 v = M[oj + i - j];
+        v.x *= inv;
+        v.y *= inv;
+        M[oj + i - j] = v;
+        lc[i] = make_float2((float)v.x, (float)v.y);
+      }
+      if (tid == 0) {
+        y[j].x *= inv;
+        y[j].y *= inv;
+      }
+    }
+    if (j >= 1) {
+      const int s1 = j - 1;                 // X row s1 is final up to its scaling
+      const float is = (float)invd[s1];
+      for (int c = tid; c <= s1; c += kFoldThreads) {
+        const int slot = tri_off(c, K) + s1 - c;
+        const float2 xv = (c == s1) ? make_float2(is, 0.f)
+                                    : make_float2(XS[2 * slot].x * is, XS[2 * slot].y * is);
+        Xrow[c] = xv;
+        XS[2 * slot] = xv;
+      }
+    }
+    __syncthreads();
+    // --- update phase: FP64 trailing update of step j, FP32 X update of step j-1.
+    if (j < K) {
+      const int oj = tri_off(j, K);
+      const int n = K - j - 1;
+      const int nt = tri_size(n);
+      const double2 yj = y[j];
+      if (tid == 0 && nt > 0) {  // element (j+1, j+1) also finishes the next pivot
+        const int d1 = tri_off(j + 1, K);
+        const double2 l = M[oj + 1];
+        double2 v = M[d1];
+        cfms_conj(v, l, l);
+        double piv = v.x;
+        if (!(piv > 0.0)) {
+          atomicOr(a.err, ERR_PIVOT);
+          piv = a.rho_eff > 0.0 ? a.rho_eff : 1.0;
+        }
+        const double lj = sqrt(piv);
+        M[d1] = make_double2(lj, 0.0);
+        invd[j + 1] = 1.0 / lj;
+      }
+      for (int u = 1 + tid; u < nt; u += 2 * kFoldThreads) {
+        const int u2 = u + kFoldThreads;
+        int ii, kk, ii2 = 0, kk2 = 0;
+        tri_ij(u, n, ii, kk);
+        const bool two = u2 < nt;
+        if (two) tri_ij(u2, n, ii2, kk2);
+        const int dst = tri_off(j + 1 + kk, K) + ii - kk;
+        double2 v = M[dst];
+        const double2 lij = M[oj + 1 + ii], lkj = M[oj + 1 + kk];
+        int dst2 = dst;
+        double2 v2 = v, lij2 = lij, lkj2 = lkj;
+        if (two) {
+          dst2 = tri_off(j + 1 + kk2, K) + ii2 - kk2;
+          v2 = M[dst2];
+          lij2 = M[oj + 1 + ii2];
+          lkj2 = M[oj + 1 + kk2];
+        }
+        cfms_conj(v, lij, lkj);
+        cfms_conj(v2, lij2, lkj2);
+        M[dst] = v;
+        if (two) M[dst2] = v2;
+      }
+      for (int u = tid; u < n; u += kFoldThreads) {
+        const int i = j + 1 + u;
+        double2 v = y[i];
+        cfms(v, M[oj + i - j], yj);
+        y[i] = v;
+      }
+    }
+    if (j >= 1) {
+      // X_ic -= L_i,s1 X_s1,c for i > s1, c <= s1 (i fastest); column s1 of X
+      // starts here (its entries below the diagonal were zero).
+      const int s1 = j - 1, rows = K - j;
+      const float2 *lc = Lcol + (s1 & 1) * K;
+      for (int e = tid; e < rows * j; e += kFoldThreads) {
+        const int c = e / rows, i = j + e % rows;
+        const float2 l = lc[i], xs1 = Xrow[c];
+        const int slot = tri_off(c, K) + i - c;
+        float2 v = (c == s1) ? make_float2(0.f, 0.f) : XS[2 * slot];
+        v.x -= l.x * xs1.x - l.y * xs1.y;
+        v.y -= l.x * xs1.y + l.y * xs1.x;
+        XS[2 * slot] = v;
+      }
+    }
+    __syncthreads();
   }
+
+  // 4. Store X = L^-1 (FP32) and y = L^-1 (w b) (FP32).
+  float2 *Xp = a.L + (size_t)p * tri_stride(K);
+  for (int t = tid; t < T; t += kFoldThreads) Xp[t] = XS[2 * t];
   for (int i = tid; i < K; i += kFoldThreads)
-    a.g[(size_t)i * F + p] = make_float2((float)rhs[i].x, (float)rhs[i].y);
+    a.g[(size_t)i * F + p] = make_float2((float)y[i].x, (float)y[i].y);
 }
 
-// D-row step: d = g + rho L^-H L^-1 (v^ - theta^); one warp per frequency, the
-// factor of that frequency staged in shared memory.  Also writes E = d + theta^.
-template <int NR>
-__global__ void dstep_kernel(int K, int F, float rho_eff, const float2 *__restrict__ L,
-                             const float2 *__restrict__ g, const float2 *__restrict__ Vh,
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// D-row step of eq. (sub_d_sol): d = (w A + rho I)^-1 (w b + rho (v^ - theta^))
+// = X^H (y + rho X r) with X = L^-1, y = L^-1 (w b) and r = v^ - theta^: two
+// triangular matrix-vector products per frequency, no sequential dependency.
+// One CTA per frequency, thread i owns row i: the first product
+// t_i = y_i + rho sum_{j<=i} X_ij r_j takes i+1 terms and the second
+// d_i = sum_{k>=i} conj(X_ki) t_k takes K-i, so every thread does K+1 terms.
+// X is staged in shared memory with 16-byte cp.async copies (the per-frequency
+// stride is even, so sources are 16-byte aligned).  Also writes E = d + theta^.
+__global__ void dstep_kernel(int K, int F, float rho_eff, const float2 *__restrict__ X,
+                             const float2 *__restrict__ yb, const float2 *__restrict__ Vh,
                              const float2 *__restrict__ th, float2 *__restrict__ Dcur,
                              float2 *__restrict__ E) {
-  extern __shared__ float2 dsm[];
-  const int T = tri_size(K);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
-  const int p = blockIdx.x * wpb + warp;
-  if (p >= F) return;
-  float2 *sL = dsm + (size_t)warp * T;
-  const float2 *Lp = L + (size_t)p * T;
-  for (int t = lane; t < T; t += 32) sL[t] = Lp[t];
-  float2 y[NR];
-#pragma unroll
-  for (int m = 0; m < NR; ++m) {
-    const int i = lane + 32 * m;
-    if (i < K) {
-      const float2 v = Vh[(size_t)i * F + p], t = th[(size_t)i * F + p];
-      y[m] = make_float2(rho_eff * (v.x - t.x), rho_eff * (v.y - t.y));
-    } else {
-      y[m] = make_float2(0.f, 0.f);
-    }
+  extern __shared__ __align__(16) float2 dsm[];
+  const int TS = tri_stride(K);
+  float2 *sX = dsm;
+  float2 *sr = sX + TS;
+  float2 *st = sr + K;
+  const int p = blockIdx.x, i = threadIdx.x;
+  const float4 *g4 = reinterpret_cast<const float4 *>(X + (size_t)p * TS);
+  float4 *s4 = reinterpret_cast<float4 *>(sX);
+  for (int c = i; c < TS / 2; c += blockDim.x) cp_async16(s4 + c, g4 + c);
+  float2 thi = make_float2(0.f, 0.f), yi = make_float2(0.f, 0.f);
+  if (i < K) {
+    const size_t o = (size_t)i * F + p;
+    const float2 v = Vh[o];
+    thi = th[o];
+    yi = yb[o];
+    sr[i] = make_float2(v.x - thi.x, v.y - thi.y);
   }
-  __syncwarp();
-  // Forward: L y' = y.
-  for (int j = 0; j < K; ++j) {
-    const int oj = tri_off(j, K);
-    float2 mine = y[0];
-#pragma unroll
-    for (int m = 1; m < NR; ++m)
-      if ((j >> 5) == m) mine = y[m];
-    float2 yj;
-    yj.x = __shfl_sync(0xffffffffu, mine.x, j & 31);
-    yj.y = __shfl_sync(0xffffffffu, mine.y, j & 31);
-    const float invd = sL[oj].x;
-    yj.x *= invd;
-    yj.y *= invd;
-#pragma unroll
-    for (int m = 0; m < NR; ++m) {
-      const int i = lane + 32 * m;
-      if (i == j) y[m] = yj;
-      if (i > j && i < K) {
-        const float2 l = sL[oj + i - j];
-        y[m].x -= l.x * yj.x - l.y * yj.y;
-        y[m].y -= l.x * yj.y + l.y * yj.x;
-      }
+  cp_async_wait_all();
+  __syncthreads();
+  if (i < K) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int j = 0; j <= i; ++j) {
+      const float2 x = sX[tri_off(j, K) + i - j], rj = sr[j];
+      acc.x += x.x * rj.x - x.y * rj.y;
+      acc.y += x.x * rj.y + x.y * rj.x;
     }
+    st[i] = make_float2(yi.x + rho_eff * acc.x, yi.y + rho_eff * acc.y);
   }
-  // Backward: L^H x = y'.
-  for (int j = K - 1; j >= 0; --j) {
-    float2 mine = y[0];
-#pragma unroll
-    for (int m = 1; m < NR; ++m)
-      if ((j >> 5) == m) mine = y[m];
-    float2 xj;
-    xj.x = __shfl_sync(0xffffffffu, mine.x, j & 31);
-    xj.y = __shfl_sync(0xffffffffu, mine.y, j & 31);
-    const float invd = sL[tri_off(j, K)].x;
-    xj.x *= invd;
-    xj.y *= invd;
-#pragma unroll
-    for (int m = 0; m < NR; ++m) {
-      const int i = lane + 32 * m;
-      if (i == j) y[m] = xj;
-      if (i < j) {
-        const float2 l = sL[tri_off(i, K) + j - i];
-        y[m].x -= l.x * xj.x + l.y * xj.y;
-        y[m].y -= l.x * xj.y - l.y * xj.x;
-      }
+  __syncthreads();
+  if (i < K) {
+    const float2 *col = sX + tri_off(i, K) - i;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = i; k < K; ++k) {
+      const float2 x = col[k], tk = st[k];
+      acc.x += x.x * tk.x + x.y * tk.y;
+      acc.y += x.x * tk.y - x.y * tk.x;
     }
-  }
-#pragma unroll
-  for (int m = 0; m < NR; ++m) {
-    const int i = lane + 32 * m;
-    if (i < K) {
-      const size_t o = (size_t)i * F + p;
-      const float2 d = cadd(g[o], y[m]);
-      Dcur[o] = d;
-      E[o] = cadd(d, th[o]);
-    }
+    const size_t o = (size_t)i * F + p;
+    Dcur[o] = acc;
+    E[o] = cadd(acc, thi);
   }
 }
 
 // Pruned inverse DFT along k1, restricted to m1 in [0, M):
 // Y[k][m1][k2] = sum_k1 E[k][k1][k2] exp(+2 pi i k1 m1 / N).
+// Grid (K, ceil(NH/32)), block (32, M): thread (k2, m1).
 constexpr int kMaxM = 16;
 __global__ void vstep_cols_kernel(int K, int N, int M, const float2 *__restrict__ E,
                                   const float2 *__restrict__ tw, float2 *__restrict__ Y) {
+  extern __shared__ float2 s_twc[];
   const int NH = N / 2 + 1, F = N * NH;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= K * NH) return;
-  const int k = idx / NH, k2 = idx % NH;
-  float2 acc[kMaxM];
-#pragma unroll
-  for (int m = 0; m < kMaxM; ++m) acc[m] = make_float2(0.f, 0.f);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  for (int i = tid; i < N; i += 32 * blockDim.y) s_twc[i] = tw[i];
+  __syncthreads();
+  const int k = blockIdx.x, k2 = blockIdx.y * 32 + threadIdx.x, m1 = threadIdx.y;
+  if (k2 >= NH) return;
   const float2 *Ek = E + (size_t)k * F + k2;
-  for (int k1 = 0; k1 < N; ++k1) {
-    const float2 e = Ek[(size_t)k1 * NH];
-#pragma unroll
-    for (int m = 0; m < kMaxM; ++m) {
-      if (m < M) {
-        const float2 w = tw[(k1 * m) & (N - 1)];
-        acc[m] = cadd(acc[m], cmulc(e, w));
-      }
-    }
+  float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+  for (int k1 = 0; k1 < N; k1 += 2) {
+    acc0 = cadd(acc0, cmulc(Ek[(size_t)k1 * NH], s_twc[(k1 * m1) & (N - 1)]));
+    acc1 = cadd(acc1, cmulc(Ek[(size_t)(k1 + 1) * NH], s_twc[((k1 + 1) * m1) & (N - 1)]));
   }
-#pragma unroll
-  for (int m = 0; m < kMaxM; ++m)
-    if (m < M) Y[((size_t)k * M + m) * NH + k2] = acc[m];
+  Y[((size_t)k * M + m1) * NH + k2] = cadd(acc0, acc1);
 }
 
 // One CTA per filter k.  mode 0: alpha = H(F^-1(E)) from Y, V = alpha /
-// max(||alpha||, 1) (Proposition 2), V^ = F(pad V), theta^ += D~ - V^.
-// mode 1: V^ = F(pad V) for a given V.
+// max(||alpha||, 1) (Proposition 2).  mode 1: V given.  Both: the partial
+// forward DFT Tm(m1, k2) = sum_m2 V(m1, m2) W^(k2 m2) for the spectrum kernel.
 constexpr int kProjThreads = 256;
 __global__ void __launch_bounds__(kProjThreads)
     vstep_project_kernel(int mode, int K, int N, int M, const float2 *__restrict__ Y,
-                         float *__restrict__ V, float2 *__restrict__ Vh, float2 *__restrict__ th,
-                         const float2 *__restrict__ Dcur, const float2 *__restrict__ tw) {
+                         float *__restrict__ V, const float2 *__restrict__ tw, float2 *__restrict__ Tm) {
   extern __shared__ __align__(16) unsigned char psm[];
-  const int NH = N / 2 + 1, F = N * NH, MM = M * M;
-  float *alpha = reinterpret_cast<float *>(psm);          // [M*M]
-  float *red = alpha + kMaxM * kMaxM;                      // [32]
-  float2 *Tm = reinterpret_cast<float2 *>(red + 32);       // [M][NH]
+  const int NH = N / 2 + 1, MM = M * M;
+  float2 *s_tw = reinterpret_cast<float2 *>(psm);          // [N]
+  float *alpha = reinterpret_cast<float *>(s_tw + N);      // [kMaxM * kMaxM]
+  float *red = alpha + kMaxM * kMaxM;                       // [32]
   const int k = blockIdx.x, tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = kProjThreads / 32;
+  for (int i = tid; i < N; i += kProjThreads) s_tw[i] = tw[i];
+  __syncthreads();
   if (mode == 0) {
     const float invP = 1.0f / (float)(N * N);
-    float ss = 0.f;
-    for (int e = tid; e < MM; e += kProjThreads) {
+    for (int e = warp; e < MM; e += nwarps) {
       const int m1 = e / M, m2 = e % M;
       const float2 *Yr = Y + ((size_t)k * M + m1) * NH;
       float s = 0.f;
-      for (int k2 = 0; k2 < NH; ++k2) {
-        const float2 y = Yr[k2];
-        const float2 w = tw[(k2 * m2) & (N - 1)];
+      for (int k2 = lane; k2 < NH; k2 += 32) {
+        const float2 yv = Yr[k2];
+        const float2 w = s_tw[(k2 * m2) & (N - 1)];
         const float c = (k2 == 0 || k2 == N / 2) ? 1.f : 2.f;
-        s += c * (y.x * w.x + y.y * w.y);
+        s += c * (yv.x * w.x + yv.y * w.y);
       }
-      s *= invP;
-      alpha[e] = s;
-      ss += s * s;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) alpha[e] = s * invP;
     }
+    __syncthreads();
+    float ss = 0.f;
+    for (int e = tid; e < MM; e += kProjThreads) ss += alpha[e] * alpha[e];
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if ((tid & 31) == 0) red[tid >> 5] = ss;
+    if (lane == 0) red[warp] = ss;
     __syncthreads();
     if (tid < 32) {
-      float v = tid < kProjThreads / 32 ? red[tid] : 0.f;
+      float v = tid < nwarps ? red[tid] : 0.f;
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
       if (tid == 0) red[0] = v;
     }
@@ -333,30 +381,42 @@ __global__ void __launch_bounds__(kProjThreads)
     for (int e = tid; e < MM; e += kProjThreads) alpha[e] = V[(size_t)k * MM + e];
   }
   __syncthreads();
-  // Tm(m1, k2) = sum_m2 V(m1, m2) W^(k2 m2)
   for (int e = tid; e < M * NH; e += kProjThreads) {
     const int m1 = e / NH, k2 = e % NH;
     float2 acc = make_float2(0.f, 0.f);
     for (int m2 = 0; m2 < M; ++m2) {
-      const float2 w = tw[(k2 * m2) & (N - 1)];
+      const float2 w = s_tw[(k2 * m2) & (N - 1)];
       const float v = alpha[m1 * M + m2];
       acc.x += v * w.x;
       acc.y += v * w.y;
     }
-    Tm[e] = acc;
+    Tm[(size_t)k * M * NH + e] = acc;
   }
+}
+
+// V^(k1, k2) = sum_m1 Tm(m1, k2) W^(k1 m1) over the half spectrum; mode 0 also
+// updates the dual theta^ += D~ - V^.  Grid (K, ceil(F/256)).
+__global__ void __launch_bounds__(256)
+    vstep_spectrum_kernel(int mode, int K, int N, int M, const float2 *__restrict__ Tm,
+                          const float2 *__restrict__ tw, float2 *__restrict__ Vh, float2 *__restrict__ th,
+                          const float2 *__restrict__ Dcur) {
+  __shared__ float2 s_tw[512];
+  const int NH = N / 2 + 1, F = N * NH;
+  for (int i = threadIdx.x; i < N; i += 256) s_tw[i] = tw[i];
   __syncthreads();
-  for (int p = tid; p < F; p += kProjThreads) {
-    const int k1 = p / NH, k2 = p % NH;
-    float2 acc = make_float2(0.f, 0.f);
-    for (int m1 = 0; m1 < M; ++m1) acc = cadd(acc, cmul(Tm[m1 * NH + k2], tw[(k1 * m1) & (N - 1)]));
-    const size_t o = (size_t)k * F + p;
-    Vh[o] = acc;
-    if (mode == 0) {
-      const float2 d = Dcur[o];
-      const float2 t = th[o];
-      th[o] = make_float2(t.x + d.x - acc.x, t.y + d.y - acc.y);
-    }
+  const int k = blockIdx.x;
+  const int p = blockIdx.y * 256 + threadIdx.x;
+  if (p >= F) return;
+  const int k1 = p / NH, k2 = p % NH;
+  const float2 *T = Tm + (size_t)k * M * NH + k2;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int m1 = 0; m1 < M; ++m1) acc = cadd(acc, cmul(T[(size_t)m1 * NH], s_tw[(k1 * m1) & (N - 1)]));
+  const size_t o = (size_t)k * F + p;
+  Vh[o] = acc;
+  if (mode == 0) {
+    const float2 d = Dcur[o];
+    const float2 t = th[o];
+    th[o] = make_float2(t.x + d.x - acc.x, t.y + d.y - acc.y);
   }
 }
 
@@ -376,8 +436,8 @@ __global__ void dict_norms_kernel(int K, int F, const float2 *__restrict__ Dh, f
 // ---------------------------------------------------------------------------
 
 size_t fold_smem_bytes(int K) {
-  return (size_t)tri_size(K) * sizeof(double2) + (size_t)K * sizeof(double2) +
-         (size_t)kFoldChunk * K * sizeof(float2) + kFoldChunk * sizeof(float2);
+  return (size_t)tri_size(K) * sizeof(double2) + (size_t)K * sizeof(double2) + (size_t)K * sizeof(double) +
+         (size_t)3 * K * sizeof(float2) + (size_t)kFoldChunk * K * sizeof(float2) + kFoldChunk * sizeof(float2);
 }
 
 cudaError_t launch_fold_factor(const FoldArgs &a, cudaStream_t s) {
@@ -388,43 +448,40 @@ cudaError_t launch_fold_factor(const FoldArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int NR>
-static cudaError_t dstep_n(int K, int F, float rho_eff, const float2 *L, const float2 *g,
-                           const float2 *Vh, const float2 *th, float2 *Dcur, float2 *E, cudaStream_t s) {
-  const size_t per = (size_t)tri_size(K) * sizeof(float2);
-  int wpb = (int)((200u * 1024u) / per);
-  wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
-  const size_t sm = per * wpb;
-  cudaError_t e = cudaFuncSetAttribute(dstep_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  dstep_kernel<NR><<<(F + wpb - 1) / wpb, 32 * wpb, sm, s>>>(K, F, rho_eff, L, g, Vh, th, Dcur, E);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *L, const float2 *g,
+cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const float2 *yb,
                          const float2 *Vh, const float2 *th, float2 *Dcur, float2 *E,
                          cudaStream_t s) {
-  if (K <= 32) return dstep_n<1>(K, F, rho_eff, L, g, Vh, th, Dcur, E, s);
-  if (K <= 64) return dstep_n<2>(K, F, rho_eff, L, g, Vh, th, Dcur, E, s);
-  if (K <= 128) return dstep_n<4>(K, F, rho_eff, L, g, Vh, th, Dcur, E, s);
-  if (K <= 256) return dstep_n<8>(K, F, rho_eff, L, g, Vh, th, Dcur, E, s);
-  return cudaErrorInvalidValue;
+  if (K > 256) return cudaErrorInvalidValue;
+  const size_t sm = ((size_t)tri_stride(K) + 2 * (size_t)K) * sizeof(float2);
+  cudaError_t e = cudaFuncSetAttribute(dstep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const int threads = (K + 31) / 32 * 32;
+  dstep_kernel<<<F, threads, sm, s>>>(K, F, rho_eff, X, yb, Vh, th, Dcur, E);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_vstep_cols(int K, int N, int M, const float2 *E, const float2 *tw, float2 *Y,
                               cudaStream_t s) {
-  if (M > kMaxM) return cudaErrorInvalidValue;
-  const int total = K * (N / 2 + 1);
-  vstep_cols_kernel<<<(total + 127) / 128, 128, 0, s>>>(K, N, M, E, tw, Y);
+  if (M > kMaxM || N > 512) return cudaErrorInvalidValue;
+  dim3 grid(K, (N / 2 + 1 + 31) / 32), block(32, M);
+  vstep_cols_kernel<<<grid, block, N * sizeof(float2), s>>>(K, N, M, E, tw, Y);
   return cudaGetLastError();
 }
 
 cudaError_t launch_vstep_project(int mode, int K, int N, int M, const float2 *Y, float *V,
-                                 float2 *Vh, float2 *th, const float2 *Dcur, const float2 *tw,
-                                 cudaStream_t s) {
-  if (M > kMaxM) return cudaErrorInvalidValue;
-  const size_t sm = (kMaxM * kMaxM + 32) * sizeof(float) + (size_t)M * (N / 2 + 1) * sizeof(float2);
-  vstep_project_kernel<<<K, kProjThreads, sm, s>>>(mode, K, N, M, Y, V, Vh, th, Dcur, tw);
+                                 const float2 *tw, float2 *Tm, cudaStream_t s) {
+  if (M > kMaxM || N > 512) return cudaErrorInvalidValue;
+  const size_t sm = N * sizeof(float2) + (kMaxM * kMaxM + 32) * sizeof(float);
+  vstep_project_kernel<<<K, kProjThreads, sm, s>>>(mode, K, N, M, Y, V, tw, Tm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vstep_spectrum(int mode, int K, int N, int M, const float2 *Tm, const float2 *tw,
+                                  float2 *Vh, float2 *th, const float2 *Dcur, cudaStream_t s) {
+  if (M > kMaxM || N > 512) return cudaErrorInvalidValue;
+  const int F = N * (N / 2 + 1);
+  dim3 grid(K, (F + 255) / 256);
+  vstep_spectrum_kernel<<<grid, 256, 0, s>>>(mode, K, N, M, Tm, tw, Vh, th, Dcur);
   return cudaGetLastError();
 }
 

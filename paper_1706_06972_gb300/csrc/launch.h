@@ -46,20 +46,24 @@ struct FoldArgs {
   float2 *b;            // [K][F]
   const float2 *Zp;     // [B][K][F]
   const float2 *xh;     // [B][F]
-  float2 *L;            // [F][K(K+1)/2] Cholesky factor, diagonal holds 1/L_jj
-  float2 *g;            // [K][F]  (w A + rho I)^-1 (w b)
+  float2 *L;            // [F][stride] X = L^-1 of the FP64 Cholesky factor, FP32
+  float2 *g;            // [K][F]  y = L^-1 (w b)
   int *err;
 };
 cudaError_t launch_fold_factor(const FoldArgs &a, cudaStream_t s);
-cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *L, const float2 *g,
+// d = X^H (y + rho X (v^ - theta^)) with X = L^-1, y = L^-1 (w b).
+cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const float2 *yb,
                          const float2 *Vh, const float2 *th, float2 *Dcur, float2 *E,
                          cudaStream_t s);
 cudaError_t launch_vstep_cols(int K, int N, int M, const float2 *E, const float2 *tw, float2 *Y,
                               cudaStream_t s);
-// mode 0: V-step from Y (projection, Vh, dual update); mode 1: Vh from given V.
+// mode 0: Proposition 2 projection of alpha from Y into V; mode 1: V given.
+// Both write the partial DFT Tm [K][M][N/2+1] used by launch_vstep_spectrum.
 cudaError_t launch_vstep_project(int mode, int K, int N, int M, const float2 *Y, float *V,
-                                 float2 *Vh, float2 *th, const float2 *Dcur, const float2 *tw,
-                                 cudaStream_t s);
+                                 const float2 *tw, float2 *Tm, cudaStream_t s);
+// V^ = F(pad V) from Tm; mode 0 also theta^ += D~ - V^.
+cudaError_t launch_vstep_spectrum(int mode, int K, int N, int M, const float2 *Tm, const float2 *tw,
+                                  float2 *Vh, float2 *th, const float2 *Dcur, cudaStream_t s);
 cudaError_t launch_dict_norms(int K, int F, const float2 *Dh, float *dn, cudaStream_t s);
 
 }  // namespace ocsc

@@ -39,7 +39,7 @@ std::mutex g_scratch_mu;
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Carve {
-  size_t tw, Dh, dn, xh, r, What, Zp, Gam, total;
+  size_t tw, Tm, Dh, dn, xh, r, What, Zp, Gam, total;
 };
 
 Carve carve(int K, int N) {
@@ -47,6 +47,7 @@ Carve carve(int K, int N) {
   Carve c{};
   size_t o = 0;
   c.tw = o;   o += up256(N * sizeof(float2));
+  c.Tm = o;   o += up256((size_t)K * 16 * (N / 2 + 1) * sizeof(float2));
   c.Dh = o;   o += up256(K * F * sizeof(float2));
   c.dn = o;   o += up256(F * sizeof(float));
   c.xh = o;   o += up256(F * sizeof(float2));
@@ -123,7 +124,9 @@ extern "C" ocsc_status ocsc_code_noalloc(const float *x, int H, int W, const flo
   e = cudaMemcpyAsync(tw, twh.data(), N * sizeof(float2), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return say(err, err_len, OCSC_ECUDA, "twiddles: %s", cudaGetErrorString(e));
   // D~ = F(pad D) and |D~(p,:)|^2, then the same code-ADMM launches as ocsc_code.
-  e = launch_vstep_project(1, K, N, M, nullptr, const_cast<float *>(D), Dh, nullptr, nullptr, tw, s);
+  float2 *Tm = reinterpret_cast<float2 *>(base + cv.Tm);
+  e = launch_vstep_project(1, K, N, M, nullptr, const_cast<float *>(D), tw, Tm, s);
+  if (e == cudaSuccess) e = launch_vstep_spectrum(1, K, N, M, Tm, tw, Dh, nullptr, nullptr, s);
   if (e == cudaSuccess) e = launch_dict_norms(K, F, Dh, dn, s);
   ImgBatch b{};
   b.n = 1;

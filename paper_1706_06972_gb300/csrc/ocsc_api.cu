@@ -26,12 +26,13 @@ struct ocsc_ctx {
   float2 *Dcur = nullptr;   // [K][F] D~_{t,tau}
   float2 *E = nullptr;      // [K][F] D~ + theta^
   float2 *Y = nullptr;      // [K][M][NH]
+  float2 *Tm = nullptr;     // [K][M][NH] partial DFT of V
   float *dn = nullptr;      // [F] |D~(p,:)|^2 of the coding dictionary
   // history and factor
   float2 *A = nullptr;      // [F][T]
   float2 *b = nullptr;      // [K][F]
-  float2 *L = nullptr;      // [F][T]
-  float2 *g = nullptr;      // [K][F]
+  float2 *L = nullptr;      // [F][T] X = L^-1 (FP32) of the FP64 factor
+  float2 *g = nullptr;      // [K][F] y = L^-1 (w b)
   // pending samples
   float2 *Zp = nullptr;     // [max_batch][K][F]
   float2 *xhp = nullptr;    // [max_batch][F]
@@ -145,7 +146,9 @@ ocsc_status upload_dict(ocsc_ctx *c, const float *D_host, int normalize) {
   }
   cudaError_t e = cudaMemcpyAsync(c->V, Dn.data(), Dn.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "upload filters");
-  e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_vstep_project(1, c->K, c->N, c->M, nullptr, c->V, c->Vh, c->th, nullptr, c->tw, c->stream); });
+  e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_vstep_project(1, c->K, c->N, c->M, nullptr, c->V, c->tw, c->Tm, c->stream); });
+  if (e == cudaSuccess)
+    e = timed(c, OCSC_K_VSTEP_SPECTRUM, [&] { return launch_vstep_spectrum(1, c->K, c->N, c->M, c->Tm, c->tw, c->Vh, nullptr, nullptr, c->stream); });
   if (e != cudaSuccess) return cuda_fail(c, e, "filter spectrum");
   e = cudaMemsetAsync(c->th, 0, (size_t)c->K * c->F * sizeof(float2), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "reset dual");
@@ -243,8 +246,9 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
   if ((st = dalloc(c, &c->V, (size_t)K * c->M * c->M)) ||
       (st = dalloc(c, &c->Vh, KF)) || (st = dalloc(c, &c->th, KF)) || (st = dalloc(c, &c->Dcur, KF)) ||
       (st = dalloc(c, &c->E, KF)) || (st = dalloc(c, &c->Y, (size_t)K * c->M * c->NH)) ||
-      (st = dalloc(c, &c->dn, (size_t)c->F)) || (st = dalloc(c, &c->A, (size_t)c->F * c->T)) ||
-      (st = dalloc(c, &c->b, KF)) || (st = dalloc(c, &c->L, (size_t)c->F * c->T)) ||
+      (st = dalloc(c, &c->Tm, (size_t)K * c->M * c->NH)) ||
+      (st = dalloc(c, &c->dn, (size_t)c->F)) || (st = dalloc(c, &c->A, (size_t)c->F * tri_stride(K))) ||
+      (st = dalloc(c, &c->b, KF)) || (st = dalloc(c, &c->L, (size_t)c->F * tri_stride(K))) ||
       (st = dalloc(c, &c->g, KF)) || (st = dalloc(c, &c->Zp, B * KF)) ||
       (st = dalloc(c, &c->xhp, B * c->F)) || (st = dalloc(c, &c->What, B * KF)) ||
       (st = dalloc(c, &c->Gam, B * K * c->P)) || (st = dalloc(c, &c->r, B * c->F)) ||
@@ -366,8 +370,10 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
     if (e != cudaSuccess) return cuda_fail(c, e, "dstep");
     e = timed(c, OCSC_K_VSTEP_COLS, [&] { return launch_vstep_cols(c->K, c->N, c->M, c->E, c->tw, c->Y, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "vstep_cols");
-    e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_vstep_project(0, c->K, c->N, c->M, c->Y, c->V, c->Vh, c->th, c->Dcur, c->tw, c->stream); });
+    e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_vstep_project(0, c->K, c->N, c->M, c->Y, c->V, c->tw, c->Tm, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "vstep_project");
+    e = timed(c, OCSC_K_VSTEP_SPECTRUM, [&] { return launch_vstep_spectrum(0, c->K, c->N, c->M, c->Tm, c->tw, c->Vh, c->th, c->Dcur, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "vstep_spectrum");
   }
   e = timed(c, OCSC_K_DICT_NORMS, [&] { return launch_dict_norms(c->K, c->F, c->opts.return_feasible ? c->Vh : c->Dcur, c->dn, c->stream); });
   if (e != cudaSuccess) return cuda_fail(c, e, "dict_norms");

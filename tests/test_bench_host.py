@@ -57,8 +57,7 @@ def _count_fold_factor_flops(K):
         f += 2 * (K - j - 1)                 # column scaling by 1/L_jj
         n = K - j - 1
         f += 8 * n * (n + 1) // 2            # trailing update
-    f += 8 * K * (K - 1) // 2                # forward substitution for g
-    f += 8 * K * (K - 1) // 2                # backward substitution for g
+    f += 8 * K * (K - 1) // 2                # forward substitution of y
     return f
 
 
