@@ -219,6 +219,74 @@ def reference_arm(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+def test_objective(pkg, learner, w, dev, n_test=8):
+    """Mean objective of eq. (ocsc0) on held-out images coded with the current
+    dictionary (samples are dropped, not folded)."""
+    import torch
+
+    vals = []
+    for i in range(n_test):
+        x = torch.from_numpy(w.image(1_000_000 + i)).to(dev)
+        u = learner.code([x])
+        vals.append(learner.objective([x], u)[0])
+        learner.drop_pending()
+    return sum(vals) / len(vals)
+
+
+def batched_leg(pkg, w, dev, stream, args):
+    """Mini-batch B = 64 on the same workload: throughput, and the held-out
+    objective after the same images against the plain B = 1 path."""
+    import torch
+
+    B = args.batch
+    N = 128
+    mk = lambda bsz: pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_size=N, pad=w.pad, Jz=w.Jz,
+                              Jd=w.Jd, max_batch=max(bsz, 1))
+    # throughput
+    lb = mk(B)
+    lb.set_dict(w.filters0(), normalize=True)
+    base = 2_000_000
+    nb = args.batched_steps
+    xs = [torch.from_numpy(w.image(base + i)).to(dev) for i in range(B * (nb + 1))]
+    us = [torch.empty((w.K, N, N), device=dev) for _ in range(B)]
+    lb.code(xs[:B], out=us)
+    lb.update_dict()
+    lb.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for t in range(1, nb + 1):
+        lb.code(xs[t * B:(t + 1) * B], out=us)
+        lb.update_dict()
+    e1.record(stream)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    lb.close()
+    out = {"batch": B, "steps": nb, "value": B * nb / secs, "unit": UNIT, "ms_per_batch": 1e3 * secs / nb}
+    # same images, plain vs batched, then the held-out objective
+    if args.quality_images > 0:
+        n = args.quality_images // B * B
+        train = [torch.from_numpy(w.image(3_000_000 + i)).to(dev) for i in range(n)]
+        lp = mk(1)
+        lp.set_dict(w.filters0(), normalize=True)
+        for x in train:
+            lp.code([x], want_codes=False)
+            lp.update_dict()
+        f_plain = test_objective(pkg, lp, w, dev)
+        lp.close()
+        lq = mk(B)
+        lq.set_dict(w.filters0(), normalize=True)
+        for t in range(0, n, B):
+            lq.code(train[t:t + B], want_codes=False)
+            lq.update_dict()
+        f_batch = test_objective(pkg, lq, w, dev)
+        lq.close()
+        out.update({"quality_train_images": n, "test_objective_plain": f_plain,
+                    "test_objective_batched": f_batch, "objective_gap": (f_batch - f_plain) / abs(f_plain),
+                    "test_images": 8})
+    return out
+
+
 def ours_arm(args):
     import numpy as np
     import torch
@@ -321,6 +389,7 @@ def ours_arm(args):
         e2e = {"value": world * E / te, "unit": UNIT, "h2d_bytes_per_step": int(xd.numel() * 4),
                "d2h_bytes_per_step": int(u_host.numel() * 4), "steps": E}
     learner.close()
+    batched = batched_leg(pkg, w, dev, stream, args) if args.batched_steps > 0 else None
 
     if rank != 0:
         return
@@ -349,6 +418,7 @@ def ours_arm(args):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(c1["kernel_launches"] - c0["kernel_launches"]),
         "kernel_breakdown": breakdown,
+        "batched": batched,
     }
     print(json.dumps(line))
 
@@ -365,6 +435,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--breakdown-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=64, help="mini-batch of the batched leg")
+    ap.add_argument("--batched-steps", type=int, default=4, help="timed batches of the batched leg (0: skip)")
+    ap.add_argument("--quality-images", type=int, default=256,
+                    help="images for the plain-vs-batched held-out objective (0: skip)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per fold_factor launch from an ncu capture of this kernel")
     args = ap.parse_args()

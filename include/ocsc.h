@@ -146,6 +146,26 @@ ocsc_status ocsc_sync(ocsc_ctx *ctx);
  * this thread when ctx is NULL (never NULL). */
 const char *ocsc_last_error(const ocsc_ctx *ctx);
 
+/*
+ * Forget the samples coded since the last ocsc_update_dict without folding them
+ * into the history (for coding held-out or served samples against a fixed
+ * dictionary).  Host-side bookkeeping only.
+ */
+ocsc_status ocsc_drop_pending(ocsc_ctx *ctx);
+
+/*
+ * Objective of eq. (ocsc0) per sample against the current coding dictionary:
+ * out_host[i] = 1/2 ||x_i - sum_k D_k (*) U_i,k||^2 + lambda ||U_i||_1, with the
+ * convolution circular on the padded N x N domain and x_i zero-padded as in
+ * ocsc_code.  x, H, W are as in ocsc_code; u[i] is a DEVICE pointer to the
+ * K x N x N codes (for instance those ocsc_code wrote).  The residual norm is
+ * taken in the frequency domain by Parseval's identity (Sec. II-C); sums are
+ * FP64 and deterministic.  out_host is a HOST array of n doubles.
+ * Synchronises.
+ */
+ocsc_status ocsc_objective(ocsc_ctx *ctx, int n, const float *const *x, const int *H, const int *W,
+                           const float *const *u, double *out_host);
+
 /* Kernel classes for ocsc_profile / ocsc_profile_read. */
 typedef enum {
   OCSC_K_IMAGE_SPECTRUM = 0, /* x~ = F(pad x) */

@@ -61,6 +61,9 @@ _PROTOS = {
     "ocsc_set_dict": (_I, [_P, _P, _I]),
     "ocsc_sync": (_I, [_P]),
     "ocsc_last_error": (ctypes.c_char_p, [_P]),
+    "ocsc_drop_pending": (_I, [_P]),
+    "ocsc_objective": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                            ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double)]),
     "ocsc_get_counters": (_I, [_P, ctypes.POINTER(ocsc_counters)]),
     "ocsc_profile": (_I, [_P, ctypes.c_uint]),
     "ocsc_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
@@ -153,6 +156,18 @@ def ocsc_sync(ctx) -> None:
 def ocsc_last_error(ctx) -> str:
     m = lib().ocsc_last_error(ctx)
     return m.decode() if m else ""
+
+
+def ocsc_drop_pending(ctx) -> None:
+    _check(ctx, lib().ocsc_drop_pending(ctx))
+
+
+def ocsc_objective(ctx, x_ptrs, H, W, u_ptrs):
+    n = len(x_ptrs)
+    out = (ctypes.c_double * n)()
+    _check(ctx, lib().ocsc_objective(ctx, n, (_P * n)(*x_ptrs), (_I * n)(*H), (_I * n)(*W),
+                                     (_P * n)(*u_ptrs), out))
+    return list(out)
 
 
 def ocsc_get_counters(ctx) -> ocsc_counters:
@@ -268,6 +283,16 @@ class OCSC:
 
     def sync(self):
         ocsc_sync(self.ctx)
+
+    def drop_pending(self):
+        ocsc_drop_pending(self.ctx)
+
+    def objective(self, images, codes):
+        """Per-sample objective of eq. (ocsc0) against the current dictionary."""
+        xs = [im.contiguous() for im in images]
+        us = [u.contiguous() for u in codes]
+        return ocsc_objective(self.ctx, [im.data_ptr() for im in xs], [im.shape[0] for im in xs],
+                              [im.shape[1] for im in xs], [u.data_ptr() for u in us])
 
     def counters(self) -> dict:
         c = ocsc_get_counters(self.ctx)

@@ -66,4 +66,13 @@ cudaError_t launch_vstep_spectrum(int mode, int K, int N, int M, const float2 *T
                                   float2 *Vh, float2 *th, const float2 *Dcur, cudaStream_t s);
 cudaError_t launch_dict_norms(int K, int F, const float2 *Dh, float *dn, cudaStream_t s);
 
+// Objective of one sample: out = 1/2 ||x - sum_k D_k (*) U_k||^2 + lam ||U||_1
+// from its spectrum xh, the code spectra Uh [K][F] and the codes u [K][N][N].
+// `partial` holds objective_partials(N) doubles of scratch.
+constexpr int kObjL1Blocks = 256;
+int objective_partials(int N);
+cudaError_t launch_objective(int K, int N, double lam, const float2 *Dh, const float2 *xh,
+                             const float2 *Uh, const float *u, double *partial, double *out,
+                             cudaStream_t s);
+
 }  // namespace ocsc

@@ -41,6 +41,10 @@ struct ocsc_ctx {
   float *Gam = nullptr;     // [max_batch][K][P]
   float2 *r = nullptr;      // [max_batch][F]
   float2 *tw = nullptr;     // [N] twiddles
+  // objective evaluation scratch
+  float2 *obj_xh = nullptr;  // [F]
+  double *obj_part = nullptr;
+  double *obj_out = nullptr; // [kObjChunk]
   int *err = nullptr;       // device error word
   long long n_seen = 0;
   int pending = 0;
@@ -56,6 +60,7 @@ struct ocsc_ctx {
 
 namespace {
 
+constexpr int kObjChunk = 64;
 thread_local std::string g_init_error = "no error";
 
 ocsc_status fail(ocsc_ctx *c, ocsc_status s, const char *fmt, ...) {
@@ -252,7 +257,10 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
       (st = dalloc(c, &c->g, KF)) || (st = dalloc(c, &c->Zp, B * KF)) ||
       (st = dalloc(c, &c->xhp, B * c->F)) || (st = dalloc(c, &c->What, B * KF)) ||
       (st = dalloc(c, &c->Gam, B * K * c->P)) || (st = dalloc(c, &c->r, B * c->F)) ||
-      (st = dalloc(c, &c->tw, (size_t)c->N)) || (st = dalloc(c, &c->err, 1)))
+      (st = dalloc(c, &c->tw, (size_t)c->N)) || (st = dalloc(c, &c->err, 1)) ||
+      (st = dalloc(c, &c->obj_xh, (size_t)c->F)) ||
+      (st = dalloc(c, &c->obj_part, (size_t)objective_partials(c->N))) ||
+      (st = dalloc(c, &c->obj_out, (size_t)kObjChunk)))
     return bail(st);
   std::vector<float2> tw(c->N);
   for (int m = 0; m < c->N; ++m) {
@@ -423,6 +431,52 @@ ocsc_status ocsc_fft2_c2r(ocsc_ctx *c, const float *X, float *x, int planes) {
   if (!x || !X || planes < 0) return fail(c, OCSC_EINVAL, "fft2_c2r: bad arguments");
   cudaError_t e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(c->N, 1, X, x, planes, c->tw, c->stream); });
   return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "fft2_c2r");
+}
+
+ocsc_status ocsc_drop_pending(ocsc_ctx *c) {
+  if (!c) return OCSC_EINVAL;
+  c->pending = 0;
+  return OCSC_OK;
+}
+
+ocsc_status ocsc_objective(ocsc_ctx *c, int n, const float *const *x, const int *H, const int *W,
+                           const float *const *u, double *out_host) {
+  if (!c) return OCSC_EINVAL;
+  if (n < 0 || (n > 0 && (!x || !H || !W || !u || !out_host)))
+    return fail(c, OCSC_EINVAL, "ocsc_objective: bad arguments");
+  for (int i = 0; i < n; ++i) {
+    if (!x[i] || !u[i] || H[i] <= 0 || W[i] <= 0) return fail(c, OCSC_EINVAL, "ocsc_objective: sample %d invalid", i);
+    if (padded_side(H[i] > W[i] ? H[i] : W[i], c->opts.pad) != c->N)
+      return fail(c, OCSC_EUNSUPPORTED, "sample %d does not map to FFT size %d", i, c->N);
+  }
+  const float2 *Dh = c->opts.return_feasible ? c->Vh : c->Dcur;
+  float2 *Uh = c->What;  // coding workspace of slot 0, idle between ocsc_code calls
+  for (int s0 = 0; s0 < n; s0 += kObjChunk) {
+    const int m = n - s0 < kObjChunk ? n - s0 : kObjChunk;
+    for (int i = 0; i < m; ++i) {
+      ImgBatch bt{};
+      bt.n = 1;
+      bt.x[0] = x[s0 + i];
+      bt.u[0] = nullptr;
+      bt.H[0] = H[s0 + i];
+      bt.W[0] = W[s0 + i];
+      cudaError_t e = timed(c, OCSC_K_COUNT, [&] { return launch_image_spectrum(c->N, bt, c->tw, c->obj_xh, c->stream); });
+      if (e == cudaSuccess)
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(c->N, 0, u[s0 + i], reinterpret_cast<float *>(Uh), c->K, c->tw, c->stream); });
+      if (e == cudaSuccess) {
+        c->counters.kernel_launches += 2;  // three kernels in launch_objective
+        e = timed(c, OCSC_K_COUNT, [&] {
+          return launch_objective(c->K, c->N, c->lam, Dh, c->obj_xh, Uh, u[s0 + i], c->obj_part, c->obj_out + i,
+                                  c->stream);
+        });
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "objective");
+    }
+    cudaError_t e = cudaMemcpyAsync(out_host + s0, c->obj_out, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "objective readback");
+  }
+  return OCSC_OK;
 }
 
 ocsc_status ocsc_get_counters(const ocsc_ctx *c, ocsc_counters *out) {

@@ -234,3 +234,41 @@ def test_error_statuses():
     learner.update_dict()
     learner.sync()
     learner.close()
+
+
+# --- objective kernel and mini-batches ------------------------------------------
+
+@pytest.mark.parametrize("name,N", [("plain_64_k16", 64), ("plain_100in128_k100", 128)])
+def test_objective_matches_oracle_evaluation(name, N):
+    """The GPU objective of eq. (ocsc0) equals the oracle's FP64 evaluation of
+    the same dictionary and codes (Parseval on the half spectrum, padding)."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    w = WORKLOADS[name]
+    learner = pkg.OCSC(w.K, w.M, w.lam, w.rho, fft_size=N, pad=w.pad, Jz=10, Jd=w.Jd, max_batch=2)
+    learner.set_dict(w.filters0(), normalize=True)
+    imgs = [w.image(7), w.image(8)]
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    us = learner.code(xs)
+    f_gpu = learner.objective(xs, us)
+    D = learner.get_dict().astype(np.float64)
+    for im, u, fg in zip(imgs, us, f_gpu):
+        fo = oracle.sample_objective(D, u.cpu().numpy().astype(np.float64),
+                                     oracle.pad_to(np.asarray(im, np.float64), N, N), w.lam)
+        assert abs(fg - fo) / abs(fo) < 1e-5
+    learner.drop_pending()
+    learner.code([xs[0]])     # pending was cleared: room again
+    learner.close()
+
+
+def test_larger_minibatch_matches_oracle():
+    _need_gpu()
+    imgs = _small_images(16, 64, 64, 500)
+    raw = raw_filters(24, 7, 17)
+    codes, dicts = run_gpu(imgs, raw, 24, 7, 0.5, 1.0, 64, 20, 6, batch=8, pad=0)
+    ocodes, odicts, _ = run_oracle(imgs, raw, 64, 0.5, 1.0, 20, 6, batch=8)
+    for t in range(16):
+        assert rel(codes[t], ocodes[t]) < REL_TOL
+    for u in range(2):
+        assert rel(dicts[u], odicts[u]) < REL_TOL
