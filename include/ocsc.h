@@ -22,7 +22,7 @@
  *  - Images are square or rectangular H x W; each is zero-padded at the end of
  *    both axes to an N x N FFT domain, N = the smallest supported size
  *    >= max(H, W) + pad.  Convolution is circular on that domain and filters
- *    occupy its top-left M x M corner.  Supported N: 64 and 128.
+ *    occupy its top-left M x M corner.  Supported N: 64, 128, 256 and 512.
  *  - lambda is the l1 weight (beta in the paper); rho is a spatial-domain
  *    ADMM penalty used by both ADMMs (the paper's frequency-domain penalty
  *    rho' of eq. (sub_d_sol) equals rho / P; opts.rho_convention = 1 uses the
@@ -67,8 +67,9 @@ typedef struct {
                          no wrap-around across the image boundary */
   int max_batch;      /* most samples that may be pending between two
                          ocsc_update_dict calls (default 1) */
-  int fft_size;       /* the FFT side N of this context: 64 or 128 (default
-                         128); every image must pad to exactly this size */
+  int fft_size;       /* the FFT side N of this context: 64, 128, 256 or 512
+                         (default 128); every image must pad to exactly this
+                         size */
   int warm_start;     /* 1 (default): V and the dual theta of DictOCSC carry
                          over between updates; 0: restart at 0 each update as
                          Algorithm 2 prints its initialisation */
@@ -90,7 +91,8 @@ void ocsc_default_opts(ocsc_opts *o);
  * splitmix64/Box-Muller generator seeded by opts->seed, each filter scaled to
  * unit l2 norm; ocsc_set_dict replaces it.
  * Allocates all device state (history and factor: 2 * F * K(K+1)/2 * 8 bytes
- * with F = N * (N/2 + 1), N = opts.fft_size).  On failure *out is NULL and
+ * with F = N * (N/2 + 1), N = opts.fft_size; for N >= 256 also a complex
+ * N x N tile per pending sample and filter pair).  On failure *out is NULL and
  * ocsc_last_error(NULL) gives the reason.
  */
 ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double lambda,

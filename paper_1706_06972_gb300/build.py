@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libocsc.so")
-SOURCES = ["code_admm.cu", "dict_update.cu", "objective.cu", "ocsc_api.cu", "noalloc.cu"]
+SOURCES = ["code_admm.cu", "code_large.cu", "dict_update.cu", "objective.cu", "ocsc_api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -38,6 +38,24 @@ cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, cons
 cudaError_t launch_fft2(int N, int inverse, const float *in, float *out, int planes,
                         const float2 *tw, cudaStream_t s);
 
+// FFT sizes 256 and 512: the 2D transforms go through a per-(sample, filter
+// pair) complex tile T[N][N] in global memory (code_large.cu).
+struct LargeIO {
+  float2 *T;              // tiles [n][npairs][N][N]
+  const float2 *spec_in;  // c2r input half spectra [planes][F]
+  float2 *spec_out;       // r2c output [planes][F], or sample spectra [n][F]
+  const float *real_in;   // r2c input planes [planes][N][N]
+  float *real_out;        // c2r output planes [planes][N][N]
+  int planes;             // planes of an r2c / c2r call
+  int images;             // LARGE_ROWS_FWD: 1 = zero-padded images of the ImgBatch
+};
+enum {
+  LARGE_COL_IN_ADMM, LARGE_COL_IN_C2R, LARGE_ROWS_ADMM, LARGE_ROWS_FWD, LARGE_ROWS_C2R,
+  LARGE_COL_OUT_ADMM, LARGE_COL_OUT_R2C, LARGE_COL_OUT_IMAGE
+};
+cudaError_t launch_large(int N, int what, const CodeIter &it, const ImgBatch &b, const LargeIO &io,
+                         int n, int npairs, const float2 *tw, cudaStream_t s);
+
 // Dictionary step.
 struct FoldArgs {
   int K, F, B, first;

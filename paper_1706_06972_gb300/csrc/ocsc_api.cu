@@ -40,6 +40,7 @@ struct ocsc_ctx {
   float2 *What = nullptr;   // [max_batch][K][F]
   float *Gam = nullptr;     // [max_batch][K][P]
   float2 *r = nullptr;      // [max_batch][F]
+  float2 *tiles = nullptr;  // [max_batch][ceil(K/2)][N][N] tiles for N >= 256
   float2 *tw = nullptr;     // [N] twiddles
   // objective evaluation scratch
   float2 *obj_xh = nullptr;  // [F]
@@ -92,11 +93,12 @@ ocsc_status dalloc(ocsc_ctx *c, T **p, size_t count) {
   return OCSC_OK;
 }
 
-bool supported_fft(int n) { return n == 64 || n == 128; }
+bool supported_fft(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
+bool large_fft(int n) { return n >= 256; }
 
 int padded_side(int side, int pad) {
   const int need = side + pad;
-  for (int n : {64, 128})
+  for (int n : {64, 128, 256, 512})
     if (n >= need) return n;
   return -1;
 }
@@ -229,7 +231,7 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
   }
   if (!(lambda >= 0) || !(rho > 0)) { fail(c, OCSC_EINVAL, "need lambda >= 0 and rho > 0"); return bail(OCSC_EINVAL); }
   if (!supported_fft(c->opts.fft_size) || c->opts.fft_size < filter_h) {
-    fail(c, OCSC_EUNSUPPORTED, "fft_size %d not supported (64 or 128)", c->opts.fft_size);
+    fail(c, OCSC_EUNSUPPORTED, "fft_size %d not supported (64, 128, 256 or 512)", c->opts.fft_size);
     return bail(OCSC_EUNSUPPORTED);
   }
   if (c->opts.Jz < 1 || c->opts.Jd < 1 || c->opts.max_batch < 1) {
@@ -261,6 +263,8 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
       (st = dalloc(c, &c->obj_xh, (size_t)c->F)) ||
       (st = dalloc(c, &c->obj_part, (size_t)objective_partials(c->N))) ||
       (st = dalloc(c, &c->obj_out, (size_t)kObjChunk)))
+    return bail(st);
+  if (large_fft(c->N) && (st = dalloc(c, &c->tiles, B * ((K + 1) / 2) * (size_t)c->P)))
     return bail(st);
   std::vector<float2> tw(c->N);
   for (int m = 0; m < c->N; ++m) {
@@ -315,7 +319,20 @@ ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, c
     }
     const int slot = c->pending + s0;
     float2 *xh = c->xhp + (size_t)slot * c->F;
-    cudaError_t e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(c->N, bt, c->tw, xh, c->stream); });
+    const int npairs = (c->K + 1) / 2;
+    LargeIO io{};
+    io.T = c->tiles ? c->tiles + (size_t)slot * npairs * c->P : nullptr;
+    cudaError_t e;
+    if (large_fft(c->N)) {
+      io.spec_out = xh;
+      io.images = 1;
+      CodeIter none{};
+      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(c->N, LARGE_ROWS_FWD, none, bt, io, bt.n, 1, c->tw, c->stream); });
+      if (e == cudaSuccess)
+        e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(c->N, LARGE_COL_OUT_IMAGE, none, bt, io, bt.n, 1, c->tw, c->stream); });
+    } else {
+      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(c->N, bt, c->tw, xh, c->stream); });
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "image spectrum");
     CodeIter it{};
     it.K = c->K;
@@ -334,7 +351,15 @@ ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, c
                                  c->r + (size_t)slot * c->F, c->stream);
       });
       if (e != cudaSuccess) return cuda_fail(c, e, "code_resid");
-      e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(c->N, it, bt, c->tw, c->stream); });
+      if (large_fft(c->N)) {
+        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(c->N, LARGE_COL_IN_ADMM, it, bt, io, bt.n, npairs, c->tw, c->stream); });
+        if (e == cudaSuccess)
+          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(c->N, LARGE_ROWS_ADMM, it, bt, io, bt.n, npairs, c->tw, c->stream); });
+        if (e == cudaSuccess && !it.last)
+          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(c->N, LARGE_COL_OUT_ADMM, it, bt, io, bt.n, npairs, c->tw, c->stream); });
+      } else {
+        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(c->N, it, bt, c->tw, c->stream); });
+      }
       if (e != cudaSuccess) return cuda_fail(c, e, "code_plane");
     }
   }
@@ -419,18 +444,51 @@ ocsc_status ocsc_sync(ocsc_ctx *c) {
   return check_device(c);
 }
 
+// Real 2D FFT building blocks; for N >= 256 they run in chunks of pairs that
+// fit the context's tile buffer.
+static ocsc_status fft2_any(ocsc_ctx *c, int inverse, const float *in, float *out, int planes, const char *name) {
+  if (!large_fft(c->N)) {
+    cudaError_t e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(c->N, inverse, in, out, planes, c->tw, c->stream); });
+    return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, name);
+  }
+  const int cap_pairs = c->opts.max_batch * ((c->K + 1) / 2);
+  const size_t spec = (size_t)c->F * 2, real = (size_t)c->P;  // floats per plane
+  for (int p0 = 0; p0 < planes; p0 += 2 * cap_pairs) {
+    const int np = planes - p0 < 2 * cap_pairs ? planes - p0 : 2 * cap_pairs;
+    LargeIO io{};
+    io.T = c->tiles;
+    io.planes = np;
+    CodeIter none{};
+    ImgBatch b{};
+    cudaError_t e;
+    if (!inverse) {
+      io.real_in = in + (size_t)p0 * real;
+      io.spec_out = reinterpret_cast<float2 *>(out + (size_t)p0 * spec);
+      e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_ROWS_FWD, none, b, io, 1, (np + 1) / 2, c->tw, c->stream); });
+      if (e == cudaSuccess)
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_COL_OUT_R2C, none, b, io, 1, (np + 1) / 2, c->tw, c->stream); });
+    } else {
+      io.spec_in = reinterpret_cast<const float2 *>(in + (size_t)p0 * spec);
+      io.real_out = out + (size_t)p0 * real;
+      e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_COL_IN_C2R, none, b, io, 1, (np + 1) / 2, c->tw, c->stream); });
+      if (e == cudaSuccess)
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_ROWS_C2R, none, b, io, 1, (np + 1) / 2, c->tw, c->stream); });
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, name);
+  }
+  return OCSC_OK;
+}
+
 ocsc_status ocsc_fft2_r2c(ocsc_ctx *c, const float *x, float *X, int planes) {
   if (!c) return OCSC_EINVAL;
   if (!x || !X || planes < 0) return fail(c, OCSC_EINVAL, "fft2_r2c: bad arguments");
-  cudaError_t e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(c->N, 0, x, X, planes, c->tw, c->stream); });
-  return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "fft2_r2c");
+  return fft2_any(c, 0, x, X, planes, "fft2_r2c");
 }
 
 ocsc_status ocsc_fft2_c2r(ocsc_ctx *c, const float *X, float *x, int planes) {
   if (!c) return OCSC_EINVAL;
   if (!x || !X || planes < 0) return fail(c, OCSC_EINVAL, "fft2_c2r: bad arguments");
-  cudaError_t e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(c->N, 1, X, x, planes, c->tw, c->stream); });
-  return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "fft2_c2r");
+  return fft2_any(c, 1, X, x, planes, "fft2_c2r");
 }
 
 ocsc_status ocsc_drop_pending(ocsc_ctx *c) {
@@ -460,9 +518,31 @@ ocsc_status ocsc_objective(ocsc_ctx *c, int n, const float *const *x, const int 
       bt.u[0] = nullptr;
       bt.H[0] = H[s0 + i];
       bt.W[0] = W[s0 + i];
-      cudaError_t e = timed(c, OCSC_K_COUNT, [&] { return launch_image_spectrum(c->N, bt, c->tw, c->obj_xh, c->stream); });
-      if (e == cudaSuccess)
-        e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(c->N, 0, u[s0 + i], reinterpret_cast<float *>(Uh), c->K, c->tw, c->stream); });
+      cudaError_t e = cudaSuccess;
+      if (large_fft(c->N)) {
+        CodeIter none{};
+        LargeIO io{};
+        io.T = c->tiles;
+        io.spec_out = c->obj_xh;
+        io.images = 1;
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_ROWS_FWD, none, bt, io, 1, 1, c->tw, c->stream); });
+        if (e == cudaSuccess)
+          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_COL_OUT_IMAGE, none, bt, io, 1, 1, c->tw, c->stream); });
+        LargeIO jo{};
+        jo.T = c->tiles;
+        jo.real_in = u[s0 + i];
+        jo.spec_out = Uh;
+        jo.planes = c->K;
+        const int np = (c->K + 1) / 2;
+        if (e == cudaSuccess)
+          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_ROWS_FWD, none, bt, jo, 1, np, c->tw, c->stream); });
+        if (e == cudaSuccess)
+          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_COL_OUT_R2C, none, bt, jo, 1, np, c->tw, c->stream); });
+      } else {
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_image_spectrum(c->N, bt, c->tw, c->obj_xh, c->stream); });
+        if (e == cudaSuccess)
+          e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(c->N, 0, u[s0 + i], reinterpret_cast<float *>(Uh), c->K, c->tw, c->stream); });
+      }
       if (e == cudaSuccess) {
         c->counters.kernel_launches += 2;  // three kernels in launch_objective
         e = timed(c, OCSC_K_COUNT, [&] {

@@ -71,7 +71,7 @@ def surrogate_objective(codes, coding_dicts, images, N, lam, batch):
 
 # --- FFT building block ------------------------------------------------------
 
-@pytest.mark.parametrize("N", [64, 128])
+@pytest.mark.parametrize("N", [64, 128, 256, 512])
 def test_fft_building_block_matches_numpy(N):
     _need_gpu()
     import paper_1706_06972_gb300 as pkg
@@ -156,13 +156,15 @@ def _small_images(n, h, w, seed):
     dict(K=8, M=7, lam=0.0, rho=1.0, Jz=15, Jd=4, n=2, hw=(57, 57), pad=6),       # lambda = 0, zero padding
     dict(K=6, M=4, lam=1.0, rho=0.5, Jz=1, Jd=1, n=2, hw=(64, 64), pad=0),        # single iterations
     dict(K=33, M=3, lam=0.3, rho=1.0, Jz=8, Jd=3, n=2, hw=(100, 90), pad=2),      # K > 32, N = 128
+    dict(K=7, M=5, lam=0.5, rho=1.0, Jz=12, Jd=4, n=2, hw=(230, 200), pad=10),    # N = 256, odd K
+    dict(K=4, M=3, lam=0.5, rho=1.0, Jz=8, Jd=3, n=2, hw=(400, 300), pad=10),     # N = 512
 ])
 def test_edge_cases_match_oracle(case):
     _need_gpu()
     h, wd = case["hw"]
     imgs = _small_images(case["n"], h, wd, 77)
     raw = raw_filters(case["K"], case["M"], 5)
-    N = 64 if max(h, wd) + case["pad"] <= 64 else 128
+    N = next(n for n in (64, 128, 256, 512) if n >= max(h, wd) + case["pad"])
     codes, dicts = run_gpu(imgs, raw, case["K"], case["M"], case["lam"], case["rho"], N,
                            case["Jz"], case["Jd"], pad=case["pad"])
     ocodes, odicts, _ = run_oracle(imgs, raw, N, case["lam"], case["rho"], case["Jz"], case["Jd"])
@@ -238,7 +240,8 @@ def test_error_statuses():
 
 # --- objective kernel and mini-batches ------------------------------------------
 
-@pytest.mark.parametrize("name,N", [("plain_64_k16", 64), ("plain_100in128_k100", 128)])
+@pytest.mark.parametrize("name,N", [("plain_64_k16", 64), ("plain_100in128_k100", 128),
+                                    ("batched_mixed_k100", 256), ("batched_mixed_k100", 512)])
 def test_objective_matches_oracle_evaluation(name, N):
     """The GPU objective of eq. (ocsc0) equals the oracle's FP64 evaluation of
     the same dictionary and codes (Parseval on the half spectrum, padding)."""
@@ -248,7 +251,8 @@ def test_objective_matches_oracle_evaluation(name, N):
     w = WORKLOADS[name]
     learner = pkg.OCSC(w.K, w.M, w.lam, w.rho, fft_size=N, pad=w.pad, Jz=10, Jd=w.Jd, max_batch=2)
     learner.set_dict(w.filters0(), normalize=True)
-    imgs = [w.image(7), w.image(8)]
+    side = N // 2 if N >= 256 else None
+    imgs = [w.image(7), w.image(8)] if side is None else [make_image(side, side, 70 + N + i) for i in range(2)]
     xs = [torch.from_numpy(im).cuda() for im in imgs]
     us = learner.code(xs)
     f_gpu = learner.objective(xs, us)
