@@ -340,3 +340,96 @@ def objective(D, Us, x_pads, lam: float) -> float:
     """Eq. (ocsc0): mean over samples of sample_objective."""
     vals = [sample_objective(D, U, x, lam) for U, x in zip(Us, x_pads)]
     return float(np.mean(vals))
+
+
+# ----------------------------------------------------------------------------
+# Uneven image sizes: one spatial dictionary, one frequency grid per size class
+# (reading R16; the paper uses a single P).  Each class c keeps its own history
+# (A_c, b_c, n_c) and scaled dual theta^_c; with w_c = n_c / n the D-row system
+# of class c is (w_c A_c + rho I) d = w_c b_c + rho (v^_c - theta^_c), and the
+# V-step projects the mean over the active classes of H(F_c^-1(D~_c + theta^_c))
+# (consensus form of Proposition 2: every class penalises its own spatial
+# constraint with the same rho).  With one class this is dict_ocsc exactly.
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class SizeClass:
+    n1: int
+    n2: int
+    hist: History
+    thetah: np.ndarray          # [K, n1, n2]
+    Dh: np.ndarray              # [K, n1, n2] coding spectrum of this class
+
+
+@dataclasses.dataclass
+class MultiState:
+    K: int
+    M: int
+    lam: float
+    rho: float
+    V: np.ndarray
+    classes: dict               # (n1, n2) -> SizeClass
+    warm_start: bool = True
+    updates: int = 0
+
+
+def init_multi(raw_filters: np.ndarray, sizes, lam: float, rho: float,
+               warm_start: bool = True) -> MultiState:
+    V = normalize_filters(raw_filters)
+    K = V.shape[0]
+    classes = {}
+    for (n1, n2) in sizes:
+        classes[(n1, n2)] = SizeClass(n1, n2, History.zeros(K, n1, n2),
+                                      np.zeros((K, n1, n2), np.complex128),
+                                      filters_spectrum(V, n1, n2))
+    return MultiState(K=K, M=V.shape[-1], lam=lam, rho=rho, V=V, classes=classes,
+                      warm_start=warm_start)
+
+
+def code_multi(state: MultiState, image: np.ndarray, size, iters: int) -> CodeResult:
+    cls = state.classes[size]
+    x_pad = pad_to(np.asarray(image, dtype=np.float64), cls.n1, cls.n2)
+    return code_admm(x_pad, cls.Dh, state.lam, state.rho, iters)
+
+
+def dict_ocsc_multi(state: MultiState, iters: int):
+    """Consensus DictOCSC over the active size classes (reading R16)."""
+    active = [c for c in state.classes.values() if c.hist.n > 0]
+    n = sum(c.hist.n for c in active)
+    K, M, r = state.K, state.M, state.rho
+    eye = np.eye(K)
+    Cs = []
+    for c in active:
+        w = c.hist.n / n
+        Cs.append((w, np.linalg.inv(w * c.hist.A + r * eye)))
+    V = state.V
+    for _ in range(iters):
+        ds, alphas = [], []
+        for c, (w, C) in zip(active, Cs):
+            Vh = filters_spectrum(V, c.n1, c.n2)
+            rhs = w * c.hist.b + r * np.moveaxis(Vh - c.thetah, 0, -1)
+            d = np.moveaxis(np.einsum("xyij,xyj->xyi", C, rhs), -1, 0)
+            ds.append(d)
+            alphas.append(crop(ifft2(d + c.thetah).real, M))
+        V = project_filters(np.mean(alphas, axis=0))
+        for c, d in zip(active, ds):
+            c.thetah = c.thetah + d - filters_spectrum(V, c.n1, c.n2)
+    return V
+
+
+def update_dict_multi(state: MultiState, results_by_size: dict, iters: int) -> MultiState:
+    """Fold each class's new codes (eqs. A_update, B_update per class) and run
+    the consensus DictOCSC; every class then codes against F_c(pad V)."""
+    for size, res in results_by_size.items():
+        if res:
+            c = state.classes[size]
+            c.hist = fold_history(c.hist, [r.Zh for r in res], [r.xh for r in res])
+    if not state.warm_start:
+        state.V = np.zeros_like(state.V)
+        for c in state.classes.values():
+            c.thetah = np.zeros_like(c.thetah)
+    state.V = dict_ocsc_multi(state, iters)
+    for c in state.classes.values():
+        c.Dh = filters_spectrum(state.V, c.n1, c.n2)
+    state.updates += 1
+    return state

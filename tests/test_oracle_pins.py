@@ -390,3 +390,64 @@ def test_printed_sherman_morrison_recursion_has_decaying_ridge():
     fixed = np.linalg.inv(A + rP * np.eye(K))
     assert np.max(np.abs(C - decaying)) < 1e-10
     assert np.max(np.abs(C - fixed)) > 1e-2
+
+
+# --- size classes (reading R16) ---------------------------------------------------
+
+def test_one_class_consensus_equals_dictocsc():
+    rng = np.random.default_rng(18)
+    K, n, M = 3, 8, 3
+    raw = rng.standard_normal((K, M, M))
+    imgs = [rng.standard_normal((n, n)) for _ in range(3)]
+    single = oracle.init_state(raw, n, n, 0.3, 1.0)
+    multi = oracle.init_multi(raw, [(n, n)], 0.3, 1.0)
+    for im in imgs:
+        rs = oracle.code(single, im, 15)
+        rm = oracle.code_multi(multi, im, (n, n), 15)
+        np.testing.assert_array_equal(rs.U, rm.U)
+        oracle.update_dict(single, [rs], 6)
+        oracle.update_dict_multi(multi, {(n, n): [rm]}, 6)
+        np.testing.assert_allclose(multi.V, single.V, atol=1e-13)
+
+
+def test_two_class_consensus_reaches_pooled_constrained_optimum():
+    """Two FFT sizes: many consensus iterations reach the minimiser of the
+    pooled objective (1/n) sum_i 1/2 ||x_i - sum_k Z_ik (*) V_k||^2 over
+    feasible V, each convolution circular on its sample's own grid."""
+    rng = np.random.default_rng(19)
+    K, M = 2, 2
+    sizes = [(5, 5), (6, 6)]
+    data = {s: [] for s in sizes}
+    for s, cnt in zip(sizes, (2, 3)):
+        for _ in range(cnt):
+            Z = rng.standard_normal((K,) + s) * (rng.random((K,) + s) < 0.6)
+            x = rng.standard_normal(s) * 2
+            data[s].append((Z, x))
+    st = oracle.init_multi(np.ones((K, M, M)), sizes, 0.1, 1.0)
+    for s in sizes:
+        c = st.classes[s]
+        c.hist = oracle.fold_history(c.hist, [oracle.fft2(Z) for Z, _ in data[s]],
+                                     [oracle.fft2(x) for _, x in data[s]])
+    st.V = np.zeros((K, M, M))
+    V = oracle.dict_ocsc_multi(st, 6000)
+    # brute force: projected gradient with dense convolution matrices
+    n_tot = sum(len(v) for v in data.values())
+    G = np.zeros((K * M * M, K * M * M))
+    r = np.zeros(K * M * M)
+    for s in sizes:
+        sup = np.zeros(s, bool)
+        sup[:M, :M] = True
+        for Z, x in data[s]:
+            S = np.hstack([brute.conv_matrix(Z[k], *s)[:, sup.ravel()] for k in range(K)])
+            G += S.T @ S / n_tot
+            r += S.T @ x.ravel() / n_tot
+    L = np.linalg.norm(G, 2)
+    v = np.zeros(K * M * M)
+    for _ in range(30000):
+        v = v - (G @ v - r) / L
+        for k in range(K):
+            seg = v[k * M * M:(k + 1) * M * M]
+            nv = np.linalg.norm(seg)
+            if nv > 1:
+                v[k * M * M:(k + 1) * M * M] = seg / nv
+    np.testing.assert_allclose(V.reshape(-1), v, atol=1e-6)
