@@ -67,9 +67,14 @@ typedef struct {
                          no wrap-around across the image boundary */
   int max_batch;      /* most samples that may be pending between two
                          ocsc_update_dict calls (default 1) */
-  int fft_size;       /* the FFT side N of this context: 64, 128, 256 or 512
-                         (default 128); every image must pad to exactly this
-                         size */
+  int fft_sizes[4];   /* the FFT sides N this context serves, zero-terminated,
+                         each of 64, 128, 256, 512 (default {128, 0, 0, 0}).
+                         Each size is a class with its own history, factor,
+                         dual and coding spectrum of the one shared
+                         dictionary; with several classes the dictionary step
+                         is the consensus DictOCSC over the classes that have
+                         seen samples (class weights n_c / n).  An image goes
+                         to the class of its padded size. */
   int warm_start;     /* 1 (default): V and the dual theta of DictOCSC carry
                          over between updates; 0: restart at 0 each update as
                          Algorithm 2 prints its initialisation */
@@ -90,9 +95,10 @@ void ocsc_default_opts(ocsc_opts *o);
  * Algorithm 3's Gaussian random initialisation: K x M x M N(0,1) draws from a
  * splitmix64/Box-Muller generator seeded by opts->seed, each filter scaled to
  * unit l2 norm; ocsc_set_dict replaces it.
- * Allocates all device state (history and factor: 2 * F * K(K+1)/2 * 8 bytes
- * with F = N * (N/2 + 1), N = opts.fft_size; for N >= 256 also a complex
- * N x N tile per pending sample and filter pair).  On failure *out is NULL and
+ * Allocates all device state per size class (history and factor:
+ * 2 * F * K(K+1)/2 * 8 bytes with F = N * (N/2 + 1); coding workspaces of
+ * about max_batch * K * N^2 * 24 bytes, plus for N >= 256 a complex N x N tile
+ * per pending sample and filter pair).  On failure *out is NULL and
  * ocsc_last_error(NULL) gives the reason.
  */
 ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double lambda,
@@ -110,10 +116,11 @@ ocsc_status ocsc_padded_size(const ocsc_ctx *ctx, int H, int W, int *N);
  * steps).  x[i] is a DEVICE pointer to an H[i] x W[i] float image; u[i] is a
  * DEVICE pointer to a caller-owned K x N x N float buffer that receives the
  * sparse code U_i after the last U-step, or NULL to skip writing it.  x, H, W
- * and u are HOST arrays of length n.  All n images must map to the same N.
+ * and u are HOST arrays of length n.  Every image must map to one of the
+ * context's FFT sizes; images of different sizes may be mixed in one call.
  * The last Z~-step of each sample and its spectrum stay pending inside the
- * library for the next ocsc_update_dict; pending + n must not exceed
- * opts.max_batch (OCSC_ESTATE otherwise).  Asynchronous.
+ * library for the next ocsc_update_dict; per size class, pending + new must
+ * not exceed opts.max_batch (OCSC_ESTATE otherwise).  Asynchronous.
  */
 ocsc_status ocsc_code(ocsc_ctx *ctx, int n, const float *const *x, const int *H,
                       const int *W, float *const *u);
@@ -207,14 +214,14 @@ ocsc_status ocsc_profile_read(ocsc_ctx *ctx, int kernel, double *total_ms, uint6
 /*
  * Building block: forward 2D DFT (the F of Sec. II-C, unnormalised) of
  * `planes` real N x N float planes x (DEVICE, contiguous) into half spectra
- * N x (N/2+1) of interleaved complex float X (DEVICE), N = ctx's fft_size.
- * Enqueued on ctx's stream.
+ * N x (N/2+1) of interleaved complex float X (DEVICE).  N must be one of the
+ * context's FFT sizes.  Enqueued on ctx's stream.
  */
-ocsc_status ocsc_fft2_r2c(ocsc_ctx *ctx, const float *x, float *X, int planes);
+ocsc_status ocsc_fft2_r2c(ocsc_ctx *ctx, int N, const float *x, float *X, int planes);
 
 /* Building block: inverse of ocsc_fft2_r2c, including the 1/P factor.  The
  * input half spectra must be those of real planes (Hermitian symmetric). */
-ocsc_status ocsc_fft2_c2r(ocsc_ctx *ctx, const float *X, float *x, int planes);
+ocsc_status ocsc_fft2_c2r(ocsc_ctx *ctx, int N, const float *X, float *x, int planes);
 
 /* Size of the fixed device array used by ocsc_code_noalloc (32 MiB). */
 #define OCSC_NOALLOC_SCRATCH_BYTES (32u << 20)

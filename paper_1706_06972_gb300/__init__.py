@@ -32,7 +32,7 @@ class OCSCError(RuntimeError):
 class ocsc_opts(ctypes.Structure):
     _fields_ = [
         ("Jz", ctypes.c_int), ("Jd", ctypes.c_int), ("pad", ctypes.c_int),
-        ("max_batch", ctypes.c_int), ("fft_size", ctypes.c_int), ("warm_start", ctypes.c_int),
+        ("max_batch", ctypes.c_int), ("fft_sizes", ctypes.c_int * 4), ("warm_start", ctypes.c_int),
         ("return_feasible", ctypes.c_int), ("rho_convention", ctypes.c_int),
         ("seed", ctypes.c_uint64),
     ]
@@ -67,8 +67,8 @@ _PROTOS = {
     "ocsc_get_counters": (_I, [_P, ctypes.POINTER(ocsc_counters)]),
     "ocsc_profile": (_I, [_P, ctypes.c_uint]),
     "ocsc_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
-    "ocsc_fft2_r2c": (_I, [_P, _P, _P, _I]),
-    "ocsc_fft2_c2r": (_I, [_P, _P, _P, _I]),
+    "ocsc_fft2_r2c": (_I, [_P, _I, _P, _P, _I]),
+    "ocsc_fft2_c2r": (_I, [_P, _I, _P, _P, _I]),
     "ocsc_code_noalloc": (_I, [_P, _I, _I, _P, _I, _I, _I, ctypes.c_double, ctypes.c_double, _I, _P,
                                _P, ctypes.c_char_p, ctypes.c_size_t]),
 }
@@ -187,12 +187,12 @@ def ocsc_profile_read(ctx, kernel: int):
     return ms.value, n.value
 
 
-def ocsc_fft2_r2c(ctx, x_ptr: int, X_ptr: int, planes: int) -> None:
-    _check(ctx, lib().ocsc_fft2_r2c(ctx, ctypes.c_void_p(x_ptr), ctypes.c_void_p(X_ptr), planes))
+def ocsc_fft2_r2c(ctx, N: int, x_ptr: int, X_ptr: int, planes: int) -> None:
+    _check(ctx, lib().ocsc_fft2_r2c(ctx, N, ctypes.c_void_p(x_ptr), ctypes.c_void_p(X_ptr), planes))
 
 
-def ocsc_fft2_c2r(ctx, X_ptr: int, x_ptr: int, planes: int) -> None:
-    _check(ctx, lib().ocsc_fft2_c2r(ctx, ctypes.c_void_p(X_ptr), ctypes.c_void_p(x_ptr), planes))
+def ocsc_fft2_c2r(ctx, N: int, X_ptr: int, x_ptr: int, planes: int) -> None:
+    _check(ctx, lib().ocsc_fft2_c2r(ctx, N, ctypes.c_void_p(X_ptr), ctypes.c_void_p(x_ptr), planes))
 
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
@@ -225,13 +225,21 @@ class OCSC:
         if not torch.cuda.is_available():
             raise RuntimeError("OCSC needs a CUDA GPU; there is no CPU fallback")
         o = ocsc_default_opts()
+        sizes = opts.pop("fft_sizes", None)
+        if "fft_size" in opts:
+            sizes = [opts.pop("fft_size")]
+        if sizes is not None:
+            if not 1 <= len(sizes) <= 4:
+                raise ValueError("one to four FFT sizes")
+            o.fft_sizes = (ctypes.c_int * 4)(*(list(sizes) + [0] * (4 - len(sizes))))
         for k, v in opts.items():
             if not hasattr(o, k):
                 raise TypeError(f"unknown option {k}")
             setattr(o, k, v)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = ocsc_init(K, M, M, lam, rho, o, self.stream.cuda_stream)
-        self.K, self.M, self.N = K, M, o.fft_size
+        self.sizes = [n for n in o.fft_sizes if n]
+        self.K, self.M, self.N = K, M, self.sizes[0]
         self.opts = o
 
     def close(self):
@@ -249,15 +257,18 @@ class OCSC:
         return ocsc_padded_size(self.ctx, H, W)
 
     def code(self, images, out=None, want_codes: bool = True):
-        """Code a list of 2D float32 CUDA tensors; returns [K, N, N] codes."""
+        """Code a list of 2D float32 CUDA tensors; returns [K, N, N] codes
+        (N the padded size of each image)."""
         torch = self._torch
         xs = [im.contiguous() for im in images]
         for im in xs:
             if not (im.is_cuda and im.dtype == torch.float32 and im.dim() == 2):
                 raise ValueError("images must be 2D float32 CUDA tensors")
         if out is None and want_codes:
-            out = [torch.empty((self.K, self.N, self.N), device=im.device, dtype=torch.float32)
-                   for im in xs]
+            out = []
+            for im in xs:
+                n = self.padded_size(im.shape[0], im.shape[1])
+                out.append(torch.empty((self.K, n, n), device=im.device, dtype=torch.float32))
         ocsc_code(self.ctx, [im.data_ptr() for im in xs], [im.shape[0] for im in xs],
                   [im.shape[1] for im in xs], [u.data_ptr() for u in out] if out is not None else None)
         self._keep = xs  # images must outlive the queued work
@@ -313,13 +324,15 @@ class OCSC:
     def fft2_r2c(self, x):
         torch = self._torch
         x = x.contiguous()
-        X = torch.empty((x.shape[0], self.N, self.N // 2 + 1), device=x.device, dtype=torch.complex64)
-        ocsc_fft2_r2c(self.ctx, x.data_ptr(), X.data_ptr(), x.shape[0])
+        N = x.shape[-1]
+        X = torch.empty((x.shape[0], N, N // 2 + 1), device=x.device, dtype=torch.complex64)
+        ocsc_fft2_r2c(self.ctx, N, x.data_ptr(), X.data_ptr(), x.shape[0])
         return X
 
     def fft2_c2r(self, X):
         torch = self._torch
         X = X.contiguous()
-        x = torch.empty((X.shape[0], self.N, self.N), device=X.device, dtype=torch.float32)
-        ocsc_fft2_c2r(self.ctx, X.data_ptr(), x.data_ptr(), X.shape[0])
+        N = X.shape[-2]
+        x = torch.empty((X.shape[0], N, N), device=X.device, dtype=torch.float32)
+        ocsc_fft2_c2r(self.ctx, N, X.data_ptr(), x.data_ptr(), X.shape[0])
         return x

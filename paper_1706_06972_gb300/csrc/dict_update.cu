@@ -328,58 +328,65 @@ __global__ void vstep_cols_kernel(int K, int N, int M, const float2 *__restrict_
   Y[((size_t)k * M + m1) * NH + k2] = cadd(acc0, acc1);
 }
 
-// One CTA per filter k.  mode 0: alpha = H(F^-1(E)) from Y, V = alpha /
-// max(||alpha||, 1) (Proposition 2).  mode 1: V given.  Both: the partial
-// forward DFT Tm(m1, k2) = sum_m2 V(m1, m2) W^(k2 m2) for the spectrum kernel.
+// V-step of Proposition 2 over the active size classes, one CTA per filter k:
+// alpha_c = H(F_c^-1(D~_c + theta^_c)) from each class's Y_c, alpha = mean over
+// classes (with one class, alpha_c itself), V_k = alpha / max(||alpha||, 1).
 constexpr int kProjThreads = 256;
 __global__ void __launch_bounds__(kProjThreads)
-    vstep_project_kernel(int mode, int K, int N, int M, const float2 *__restrict__ Y,
-                         float *__restrict__ V, const float2 *__restrict__ tw, float2 *__restrict__ Tm) {
-  extern __shared__ __align__(16) unsigned char psm[];
-  const int NH = N / 2 + 1, MM = M * M;
-  float2 *s_tw = reinterpret_cast<float2 *>(psm);          // [N]
-  float *alpha = reinterpret_cast<float *>(s_tw + N);      // [kMaxM * kMaxM]
-  float *red = alpha + kMaxM * kMaxM;                       // [32]
+    vstep_project_kernel(int K, int M, AlphaClasses ac, float *__restrict__ V) {
+  __shared__ float alpha[kMaxM * kMaxM];
+  __shared__ float red[32];
+  const int MM = M * M;
   const int k = blockIdx.x, tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31, nwarps = kProjThreads / 32;
-  for (int i = tid; i < N; i += kProjThreads) s_tw[i] = tw[i];
+  for (int e = tid; e < MM; e += kProjThreads) alpha[e] = 0.f;
   __syncthreads();
-  if (mode == 0) {
-    const float invP = 1.0f / (float)(N * N);
+  for (int c = 0; c < ac.C; ++c) {
+    const int N = ac.N[c], NH = N / 2 + 1;
+    const float2 *tw = ac.tw[c];
+    const float scale = 1.0f / ((float)(N * N) * (float)ac.C);
     for (int e = warp; e < MM; e += nwarps) {
       const int m1 = e / M, m2 = e % M;
-      const float2 *Yr = Y + ((size_t)k * M + m1) * NH;
+      const float2 *Yr = ac.Y[c] + ((size_t)k * M + m1) * NH;
       float s = 0.f;
       for (int k2 = lane; k2 < NH; k2 += 32) {
         const float2 yv = Yr[k2];
-        const float2 w = s_tw[(k2 * m2) & (N - 1)];
-        const float c = (k2 == 0 || k2 == N / 2) ? 1.f : 2.f;
-        s += c * (yv.x * w.x + yv.y * w.y);
+        const float2 w = tw[(k2 * m2) & (N - 1)];
+        const float cw = (k2 == 0 || k2 == N / 2) ? 1.f : 2.f;
+        s += cw * (yv.x * w.x + yv.y * w.y);
       }
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) alpha[e] = s * invP;
+      if (lane == 0) alpha[e] += s * scale;
     }
     __syncthreads();
-    float ss = 0.f;
-    for (int e = tid; e < MM; e += kProjThreads) ss += alpha[e] * alpha[e];
-    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-    if (lane == 0) red[warp] = ss;
-    __syncthreads();
-    if (tid < 32) {
-      float v = tid < nwarps ? red[tid] : 0.f;
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (tid == 0) red[0] = v;
-    }
-    __syncthreads();
-    const float scale = 1.0f / fmaxf(sqrtf(red[0]), 1.0f);
-    for (int e = tid; e < MM; e += kProjThreads) {
-      const float v = alpha[e] * scale;
-      alpha[e] = v;
-      V[(size_t)k * MM + e] = v;
-    }
-  } else {
-    for (int e = tid; e < MM; e += kProjThreads) alpha[e] = V[(size_t)k * MM + e];
   }
+  float ss = 0.f;
+  for (int e = tid; e < MM; e += kProjThreads) ss += alpha[e] * alpha[e];
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) red[warp] = ss;
+  __syncthreads();
+  if (tid < 32) {
+    float v = tid < nwarps ? red[tid] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (tid == 0) red[0] = v;
+  }
+  __syncthreads();
+  const float sc = 1.0f / fmaxf(sqrtf(red[0]), 1.0f);
+  for (int e = tid; e < MM; e += kProjThreads) V[(size_t)k * MM + e] = alpha[e] * sc;
+}
+
+// Partial forward DFT of the filters for one size class, one CTA per filter:
+// Tm(m1, k2) = sum_m2 V(m1, m2) W_N^(k2 m2), k2 in [0, N/2].
+__global__ void __launch_bounds__(kProjThreads)
+    vstep_partial_dft_kernel(int K, int N, int M, const float *__restrict__ V,
+                             const float2 *__restrict__ tw, float2 *__restrict__ Tm) {
+  extern __shared__ __align__(16) unsigned char psm[];
+  const int NH = N / 2 + 1, MM = M * M;
+  float2 *s_tw = reinterpret_cast<float2 *>(psm);
+  float *alpha = reinterpret_cast<float *>(s_tw + N);
+  const int k = blockIdx.x, tid = threadIdx.x;
+  for (int i = tid; i < N; i += kProjThreads) s_tw[i] = tw[i];
+  for (int e = tid; e < MM; e += kProjThreads) alpha[e] = V[(size_t)k * MM + e];
   __syncthreads();
   for (int e = tid; e < M * NH; e += kProjThreads) {
     const int m1 = e / NH, k2 = e % NH;
@@ -468,11 +475,17 @@ cudaError_t launch_vstep_cols(int K, int N, int M, const float2 *E, const float2
   return cudaGetLastError();
 }
 
-cudaError_t launch_vstep_project(int mode, int K, int N, int M, const float2 *Y, float *V,
-                                 const float2 *tw, float2 *Tm, cudaStream_t s) {
+cudaError_t launch_vstep_project(int K, int M, const AlphaClasses &ac, float *V, cudaStream_t s) {
+  if (M > kMaxM || ac.C < 1 || ac.C > kMaxClasses) return cudaErrorInvalidValue;
+  vstep_project_kernel<<<K, kProjThreads, 0, s>>>(K, M, ac, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vstep_partial_dft(int K, int N, int M, const float *V, const float2 *tw, float2 *Tm,
+                                     cudaStream_t s) {
   if (M > kMaxM || N > 512) return cudaErrorInvalidValue;
-  const size_t sm = N * sizeof(float2) + (kMaxM * kMaxM + 32) * sizeof(float);
-  vstep_project_kernel<<<K, kProjThreads, sm, s>>>(mode, K, N, M, Y, V, tw, Tm);
+  const size_t sm = N * sizeof(float2) + kMaxM * kMaxM * sizeof(float);
+  vstep_partial_dft_kernel<<<K, kProjThreads, sm, s>>>(K, N, M, V, tw, Tm);
   return cudaGetLastError();
 }
 

@@ -75,10 +75,19 @@ cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const flo
                          cudaStream_t s);
 cudaError_t launch_vstep_cols(int K, int N, int M, const float2 *E, const float2 *tw, float2 *Y,
                               cudaStream_t s);
-// mode 0: Proposition 2 projection of alpha from Y into V; mode 1: V given.
-// Both write the partial DFT Tm [K][M][N/2+1] used by launch_vstep_spectrum.
-cudaError_t launch_vstep_project(int mode, int K, int N, int M, const float2 *Y, float *V,
-                                 const float2 *tw, float2 *Tm, cudaStream_t s);
+// Size classes that take part in one V-step (reading R16).
+constexpr int kMaxClasses = 4;
+struct AlphaClasses {
+  int C;                            // active classes
+  int N[kMaxClasses];               // FFT side of each
+  const float2 *Y[kMaxClasses];     // [K][M][N/2+1] pruned inverse DFT along k1
+  const float2 *tw[kMaxClasses];    // twiddles of each size
+};
+// Proposition 2 on the mean over classes of the support crops: writes V.
+cudaError_t launch_vstep_project(int K, int M, const AlphaClasses &ac, float *V, cudaStream_t s);
+// Partial DFT Tm [K][M][N/2+1] of the filters V for one class size.
+cudaError_t launch_vstep_partial_dft(int K, int N, int M, const float *V, const float2 *tw, float2 *Tm,
+                                     cudaStream_t s);
 // V^ = F(pad V) from Tm; mode 0 also theta^ += D~ - V^.
 cudaError_t launch_vstep_spectrum(int mode, int K, int N, int M, const float2 *Tm, const float2 *tw,
                                   float2 *Vh, float2 *th, const float2 *Dcur, cudaStream_t s);

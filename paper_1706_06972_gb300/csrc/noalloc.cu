@@ -125,7 +125,7 @@ extern "C" ocsc_status ocsc_code_noalloc(const float *x, int H, int W, const flo
   if (e != cudaSuccess) return say(err, err_len, OCSC_ECUDA, "twiddles: %s", cudaGetErrorString(e));
   // D~ = F(pad D) and |D~(p,:)|^2, then the same code-ADMM launches as ocsc_code.
   float2 *Tm = reinterpret_cast<float2 *>(base + cv.Tm);
-  e = launch_vstep_project(1, K, N, M, nullptr, const_cast<float *>(D), tw, Tm, s);
+  e = launch_vstep_partial_dft(K, N, M, D, tw, Tm, s);
   if (e == cudaSuccess) e = launch_vstep_spectrum(1, K, N, M, Tm, tw, Dh, nullptr, nullptr, s);
   if (e == cudaSuccess) e = launch_dict_norms(K, F, Dh, dn, s);
   ImgBatch b{};

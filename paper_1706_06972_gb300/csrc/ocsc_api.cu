@@ -1,6 +1,14 @@
 // C-ABI runtime: context state, allocation and the launch sequences of
 // Algorithm 3 (code, fold, DictOCSC).  All method arithmetic runs in the
-// kernels of code_admm.cu and dict_update.cu; this file only sequences them.
+// kernels of code_admm.cu, code_large.cu, dict_update.cu and objective.cu;
+// this file only sequences them.
+//
+// A context holds one spatial dictionary V and one or more size classes, one
+// per FFT side N.  Each class keeps its own frequency-domain state (history,
+// factor, dual, coding spectrum) and coding workspaces; the dictionary step is
+// the consensus form of DictOCSC over the classes that have seen samples
+// (with a single class it is Algorithm 2 as is).
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -14,25 +22,24 @@
 
 using namespace ocsc;
 
-struct ocsc_ctx {
-  int K = 0, M = 0, N = 0, NH = 0, F = 0, P = 0, T = 0;
-  double lam = 0, rho = 0;
-  ocsc_opts opts{};
-  cudaStream_t stream = nullptr;
-  // dictionary state
-  float *V = nullptr;       // [K][M][M]
+namespace {
+
+struct SizeClass {
+  int N = 0, NH = 0, F = 0, P = 0;
+  float2 *tw = nullptr;     // [N] twiddles
+  // dictionary state in this class's frequency grid
   float2 *Vh = nullptr;     // [K][F] F(pad V)
   float2 *th = nullptr;     // [K][F] scaled dual of DictOCSC
   float2 *Dcur = nullptr;   // [K][F] D~_{t,tau}
   float2 *E = nullptr;      // [K][F] D~ + theta^
-  float2 *Y = nullptr;      // [K][M][NH]
+  float2 *Y = nullptr;      // [K][M][NH] pruned inverse DFT along k1
   float2 *Tm = nullptr;     // [K][M][NH] partial DFT of V
   float *dn = nullptr;      // [F] |D~(p,:)|^2 of the coding dictionary
   // history and factor
-  float2 *A = nullptr;      // [F][T]
+  float2 *A = nullptr;      // [F][stride] packed FP32 history
   float2 *b = nullptr;      // [K][F]
-  float2 *L = nullptr;      // [F][T] X = L^-1 (FP32) of the FP64 factor
-  float2 *g = nullptr;      // [K][F] y = L^-1 (w b)
+  float2 *X = nullptr;      // [F][stride] X = L^-1 (FP32) of the FP64 factor
+  float2 *y = nullptr;      // [K][F] y = L^-1 (w b)
   // pending samples
   float2 *Zp = nullptr;     // [max_batch][K][F]
   float2 *xhp = nullptr;    // [max_batch][F]
@@ -40,19 +47,28 @@ struct ocsc_ctx {
   float2 *What = nullptr;   // [max_batch][K][F]
   float *Gam = nullptr;     // [max_batch][K][P]
   float2 *r = nullptr;      // [max_batch][F]
-  float2 *tiles = nullptr;  // [max_batch][ceil(K/2)][N][N] tiles for N >= 256
-  float2 *tw = nullptr;     // [N] twiddles
-  // objective evaluation scratch
-  float2 *obj_xh = nullptr;  // [F]
-  double *obj_part = nullptr;
-  double *obj_out = nullptr; // [kObjChunk]
-  int *err = nullptr;       // device error word
+  float2 *tiles = nullptr;  // [max_batch][ceil(K/2)][N][N] for N >= 256
+  float2 *obj_xh = nullptr; // [F]
   long long n_seen = 0;
   int pending = 0;
+};
+
+}  // namespace
+
+struct ocsc_ctx {
+  int K = 0, M = 0, T = 0;
+  double lam = 0, rho = 0;
+  ocsc_opts opts{};
+  cudaStream_t stream = nullptr;
+  float *V = nullptr;       // [K][M][M] the spatial filters
+  std::vector<SizeClass> cls;
+  double *obj_part = nullptr;
+  double *obj_out = nullptr;
+  int *err = nullptr;       // device error word
+  long long n_seen = 0;     // samples folded over all classes
   uint64_t version = 0;
   std::string msg;
   std::vector<void *> allocs;
-  // bookkeeping and optional per-kernel event timing
   ocsc_counters counters{};
   unsigned prof_mask = 0;
   std::vector<cudaEvent_t> prof_ev[OCSC_K_COUNT];  // start/stop pairs
@@ -103,6 +119,13 @@ int padded_side(int side, int pad) {
   return -1;
 }
 
+int class_of(const ocsc_ctx *c, int H, int W) {
+  const int n = padded_side(H > W ? H : W, c->opts.pad);
+  for (size_t i = 0; i < c->cls.size(); ++i)
+    if (c->cls[i].N == n) return (int)i;
+  return -1;
+}
+
 // splitmix64 (Steele, Lea & Flood 2014) and Box-Muller for the Gaussian
 // initial filters of Algorithm 3.
 uint64_t splitmix64(uint64_t x) {
@@ -121,7 +144,7 @@ double uniform01(uint64_t seed, uint64_t i) {
 template <typename Fn>
 cudaError_t timed(ocsc_ctx *c, int id, Fn &&fn) {
   c->counters.kernel_launches++;
-  if (!(c->prof_mask & (1u << id))) return fn();
+  if (id >= OCSC_K_COUNT || !(c->prof_mask & (1u << id))) return fn();
   auto &ev = c->prof_ev[id];
   size_t &used = c->prof_used[id];
   while (used + 2 > ev.size()) {
@@ -139,6 +162,18 @@ cudaError_t timed(ocsc_ctx *c, int id, Fn &&fn) {
   return err;
 }
 
+const float2 *coding_spectrum(const ocsc_ctx *c, const SizeClass &s) {
+  return c->opts.return_feasible ? s.Vh : s.Dcur;
+}
+
+// V^_c = F_c(pad V) for one class, without touching its dual.
+cudaError_t class_spectrum(ocsc_ctx *c, SizeClass &s) {
+  cudaError_t e = timed(c, OCSC_K_VSTEP_SPECTRUM, [&] { return launch_vstep_partial_dft(c->K, s.N, c->M, c->V, s.tw, s.Tm, c->stream); });
+  if (e == cudaSuccess)
+    e = timed(c, OCSC_K_VSTEP_SPECTRUM, [&] { return launch_vstep_spectrum(1, c->K, s.N, c->M, s.Tm, s.tw, s.Vh, nullptr, nullptr, c->stream); });
+  return e;
+}
+
 ocsc_status upload_dict(ocsc_ctx *c, const float *D_host, int normalize) {
   const int MM = c->M * c->M;
   std::vector<float> Dn((size_t)c->K * MM);
@@ -153,18 +188,17 @@ ocsc_status upload_dict(ocsc_ctx *c, const float *D_host, int normalize) {
   }
   cudaError_t e = cudaMemcpyAsync(c->V, Dn.data(), Dn.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "upload filters");
-  e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_vstep_project(1, c->K, c->N, c->M, nullptr, c->V, c->tw, c->Tm, c->stream); });
-  if (e == cudaSuccess)
-    e = timed(c, OCSC_K_VSTEP_SPECTRUM, [&] { return launch_vstep_spectrum(1, c->K, c->N, c->M, c->Tm, c->tw, c->Vh, nullptr, nullptr, c->stream); });
-  if (e != cudaSuccess) return cuda_fail(c, e, "filter spectrum");
-  e = cudaMemsetAsync(c->th, 0, (size_t)c->K * c->F * sizeof(float2), c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "reset dual");
-  // D~ = F(pad D) also seeds D~_{t,tau}, the coding dictionary when
-  // return_feasible = 0.
-  e = cudaMemcpyAsync(c->Dcur, c->Vh, (size_t)c->K * c->F * sizeof(float2), cudaMemcpyDeviceToDevice, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "seed D~");
-  e = timed(c, OCSC_K_DICT_NORMS, [&] { return launch_dict_norms(c->K, c->F, c->Vh, c->dn, c->stream); });
-  if (e != cudaSuccess) return cuda_fail(c, e, "dictionary norms");
+  for (SizeClass &s : c->cls) {
+    const size_t kf = (size_t)c->K * s.F * sizeof(float2);
+    e = class_spectrum(c, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.th, 0, kf, c->stream);
+    // D~ = F(pad D) also seeds D~_{t,tau}, the coding dictionary when
+    // return_feasible = 0.
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.Dcur, s.Vh, kf, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+      e = timed(c, OCSC_K_DICT_NORMS, [&] { return launch_dict_norms(c->K, s.F, s.Vh, s.dn, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "set dictionary");
+  }
   e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "set_dict sync");
   return OCSC_OK;
@@ -183,6 +217,34 @@ ocsc_status check_device(ocsc_ctx *c) {
   return OCSC_OK;
 }
 
+ocsc_status alloc_class(ocsc_ctx *c, SizeClass &s, int N) {
+  s.N = N;
+  s.NH = N / 2 + 1;
+  s.F = N * s.NH;
+  s.P = N * N;
+  const int K = c->K, M = c->M;
+  const size_t KF = (size_t)K * s.F, B = (size_t)c->opts.max_batch, TS = (size_t)tri_stride(K);
+  ocsc_status st;
+  if ((st = dalloc(c, &s.tw, (size_t)N)) || (st = dalloc(c, &s.Vh, KF)) || (st = dalloc(c, &s.th, KF)) ||
+      (st = dalloc(c, &s.Dcur, KF)) || (st = dalloc(c, &s.E, KF)) ||
+      (st = dalloc(c, &s.Y, (size_t)K * M * s.NH)) || (st = dalloc(c, &s.Tm, (size_t)K * M * s.NH)) ||
+      (st = dalloc(c, &s.dn, (size_t)s.F)) || (st = dalloc(c, &s.A, (size_t)s.F * TS)) ||
+      (st = dalloc(c, &s.b, KF)) || (st = dalloc(c, &s.X, (size_t)s.F * TS)) || (st = dalloc(c, &s.y, KF)) ||
+      (st = dalloc(c, &s.Zp, B * KF)) || (st = dalloc(c, &s.xhp, B * s.F)) ||
+      (st = dalloc(c, &s.What, B * KF)) || (st = dalloc(c, &s.Gam, B * K * s.P)) ||
+      (st = dalloc(c, &s.r, B * s.F)) || (st = dalloc(c, &s.obj_xh, (size_t)s.F)))
+    return st;
+  if (large_fft(N) && (st = dalloc(c, &s.tiles, B * ((K + 1) / 2) * (size_t)s.P))) return st;
+  std::vector<float2> tw(N);
+  for (int m = 0; m < N; ++m) {
+    const double a = -2.0 * M_PI * (double)m / (double)N;
+    tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  cudaError_t e = cudaMemcpy(s.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(c, e, "upload twiddles");
+  return OCSC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -193,7 +255,8 @@ void ocsc_default_opts(ocsc_opts *o) {
   o->Jd = 10;
   o->pad = -1;
   o->max_batch = 1;
-  o->fft_size = 128;
+  o->fft_sizes[0] = 128;
+  o->fft_sizes[1] = o->fft_sizes[2] = o->fft_sizes[3] = 0;
   o->warm_start = 1;
   o->return_feasible = 1;
   o->rho_convention = 0;
@@ -230,50 +293,43 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
     return bail(OCSC_EUNSUPPORTED);
   }
   if (!(lambda >= 0) || !(rho > 0)) { fail(c, OCSC_EINVAL, "need lambda >= 0 and rho > 0"); return bail(OCSC_EINVAL); }
-  if (!supported_fft(c->opts.fft_size) || c->opts.fft_size < filter_h) {
-    fail(c, OCSC_EUNSUPPORTED, "fft_size %d not supported (64, 128, 256 or 512)", c->opts.fft_size);
-    return bail(OCSC_EUNSUPPORTED);
-  }
   if (c->opts.Jz < 1 || c->opts.Jd < 1 || c->opts.max_batch < 1) {
     fail(c, OCSC_EINVAL, "Jz, Jd and max_batch must be positive");
     return bail(OCSC_EINVAL);
   }
+  std::vector<int> sizes;
+  for (int i = 0; i < 4 && c->opts.fft_sizes[i] != 0; ++i) {
+    const int n = c->opts.fft_sizes[i];
+    if (!supported_fft(n) || n < filter_h) {
+      fail(c, OCSC_EUNSUPPORTED, "fft size %d not supported (64, 128, 256 or 512)", n);
+      return bail(OCSC_EUNSUPPORTED);
+    }
+    for (int m : sizes)
+      if (m == n) { fail(c, OCSC_EINVAL, "fft size %d listed twice", n); return bail(OCSC_EINVAL); }
+    sizes.push_back(n);
+  }
+  if (sizes.empty()) { fail(c, OCSC_EINVAL, "no fft size given"); return bail(OCSC_EINVAL); }
+  if (sizes.size() > 1 && (c->opts.rho_convention != 0 || !c->opts.return_feasible)) {
+    fail(c, OCSC_EUNSUPPORTED, "several size classes need rho_convention = 0 and return_feasible = 1");
+    return bail(OCSC_EUNSUPPORTED);
+  }
   if (c->opts.pad < 0) c->opts.pad = filter_h - 1;
   c->K = K;
   c->M = filter_h;
-  c->N = c->opts.fft_size;
-  c->NH = c->N / 2 + 1;
-  c->F = c->N * c->NH;
-  c->P = c->N * c->N;
   c->T = tri_size(K);
   c->lam = lambda;
   c->rho = rho;
   c->stream = (cudaStream_t)cuda_stream;
-  const size_t KF = (size_t)K * c->F, B = (size_t)c->opts.max_batch;
-  if ((st = dalloc(c, &c->V, (size_t)K * c->M * c->M)) ||
-      (st = dalloc(c, &c->Vh, KF)) || (st = dalloc(c, &c->th, KF)) || (st = dalloc(c, &c->Dcur, KF)) ||
-      (st = dalloc(c, &c->E, KF)) || (st = dalloc(c, &c->Y, (size_t)K * c->M * c->NH)) ||
-      (st = dalloc(c, &c->Tm, (size_t)K * c->M * c->NH)) ||
-      (st = dalloc(c, &c->dn, (size_t)c->F)) || (st = dalloc(c, &c->A, (size_t)c->F * tri_stride(K))) ||
-      (st = dalloc(c, &c->b, KF)) || (st = dalloc(c, &c->L, (size_t)c->F * tri_stride(K))) ||
-      (st = dalloc(c, &c->g, KF)) || (st = dalloc(c, &c->Zp, B * KF)) ||
-      (st = dalloc(c, &c->xhp, B * c->F)) || (st = dalloc(c, &c->What, B * KF)) ||
-      (st = dalloc(c, &c->Gam, B * K * c->P)) || (st = dalloc(c, &c->r, B * c->F)) ||
-      (st = dalloc(c, &c->tw, (size_t)c->N)) || (st = dalloc(c, &c->err, 1)) ||
-      (st = dalloc(c, &c->obj_xh, (size_t)c->F)) ||
-      (st = dalloc(c, &c->obj_part, (size_t)objective_partials(c->N))) ||
-      (st = dalloc(c, &c->obj_out, (size_t)kObjChunk)))
-    return bail(st);
-  if (large_fft(c->N) && (st = dalloc(c, &c->tiles, B * ((K + 1) / 2) * (size_t)c->P)))
-    return bail(st);
-  std::vector<float2> tw(c->N);
-  for (int m = 0; m < c->N; ++m) {
-    const double a = -2.0 * M_PI * (double)m / (double)c->N;
-    tw[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+  int max_partials = 0;
+  c->cls.resize(sizes.size());
+  for (size_t i = 0; i < sizes.size(); ++i) {
+    if ((st = alloc_class(c, c->cls[i], sizes[i])) != OCSC_OK) return bail(st);
+    max_partials = std::max(max_partials, objective_partials(sizes[i]));
   }
-  cudaError_t e = cudaMemcpy(c->tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) { cuda_fail(c, e, "upload twiddles"); return bail(OCSC_ECUDA); }
-  e = cudaMemset(c->err, 0, sizeof(int));
+  if ((st = dalloc(c, &c->V, (size_t)K * c->M * c->M)) || (st = dalloc(c, &c->err, 1)) ||
+      (st = dalloc(c, &c->obj_part, (size_t)max_partials)) || (st = dalloc(c, &c->obj_out, (size_t)kObjChunk)))
+    return bail(st);
+  cudaError_t e = cudaMemset(c->err, 0, sizeof(int));
   if (e != cudaSuccess) { cuda_fail(c, e, "clear error word"); return bail(OCSC_ECUDA); }
   // Algorithm 3: Gaussian random initial filters (normalised in upload_dict).
   std::vector<float> D0((size_t)K * c->M * c->M);
@@ -294,124 +350,170 @@ ocsc_status ocsc_padded_size(const ocsc_ctx *ctx, int H, int W, int *N) {
   return OCSC_OK;
 }
 
-ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, const int *W,
-                      float *const *u) {
-  if (!c) return OCSC_EINVAL;
-  if (n <= 0 || !x || !H || !W) return fail(c, OCSC_EINVAL, "ocsc_code: bad arguments");
-  if (c->pending + n > c->opts.max_batch)
-    return fail(c, OCSC_ESTATE, "ocsc_code: %d pending + %d new exceeds max_batch %d; call ocsc_update_dict",
-                c->pending, n, c->opts.max_batch);
-  for (int i = 0; i < n; ++i) {
-    if (!x[i] || H[i] <= 0 || W[i] <= 0) return fail(c, OCSC_EINVAL, "ocsc_code: image %d invalid", i);
-    const int side = H[i] > W[i] ? H[i] : W[i];
-    if (padded_side(side, c->opts.pad) != c->N)
-      return fail(c, OCSC_EUNSUPPORTED, "image %d (%dx%d, pad %d) does not map to FFT size %d", i, H[i], W[i],
-                  c->opts.pad, c->N);
-  }
+// Code the images of one class (all of the same padded size).
+static ocsc_status code_class(ocsc_ctx *c, SizeClass &s, const std::vector<int> &idx, const float *const *x,
+                              const int *H, const int *W, float *const *u) {
+  const int n = (int)idx.size();
+  const int npairs = (c->K + 1) / 2;
   for (int s0 = 0; s0 < n; s0 += kMaxCallImages) {
     ImgBatch bt{};
     bt.n = n - s0 < kMaxCallImages ? n - s0 : kMaxCallImages;
     for (int i = 0; i < bt.n; ++i) {
-      bt.x[i] = x[s0 + i];
-      bt.u[i] = u ? u[s0 + i] : nullptr;
-      bt.H[i] = H[s0 + i];
-      bt.W[i] = W[s0 + i];
+      const int j = idx[s0 + i];
+      bt.x[i] = x[j];
+      bt.u[i] = u ? u[j] : nullptr;
+      bt.H[i] = H[j];
+      bt.W[i] = W[j];
     }
-    const int slot = c->pending + s0;
-    float2 *xh = c->xhp + (size_t)slot * c->F;
-    const int npairs = (c->K + 1) / 2;
+    const int slot = s.pending + s0;
+    float2 *xh = s.xhp + (size_t)slot * s.F;
     LargeIO io{};
-    io.T = c->tiles ? c->tiles + (size_t)slot * npairs * c->P : nullptr;
+    io.T = s.tiles ? s.tiles + (size_t)slot * npairs * s.P : nullptr;
     cudaError_t e;
-    if (large_fft(c->N)) {
+    if (large_fft(s.N)) {
       io.spec_out = xh;
       io.images = 1;
       CodeIter none{};
-      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(c->N, LARGE_ROWS_FWD, none, bt, io, bt.n, 1, c->tw, c->stream); });
+      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_ROWS_FWD, none, bt, io, bt.n, 1, s.tw, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(c->N, LARGE_COL_OUT_IMAGE, none, bt, io, bt.n, 1, c->tw, c->stream); });
+        e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_COL_OUT_IMAGE, none, bt, io, bt.n, 1, s.tw, c->stream); });
     } else {
-      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(c->N, bt, c->tw, xh, c->stream); });
+      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(s.N, bt, s.tw, xh, c->stream); });
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "image spectrum");
     CodeIter it{};
     it.K = c->K;
-    it.F = c->F;
+    it.F = s.F;
     it.thr = (float)(c->lam / c->rho);
-    it.Dh = c->opts.return_feasible ? c->Vh : c->Dcur;
-    it.r = c->r + (size_t)slot * c->F;
-    it.What = c->What + (size_t)slot * c->K * c->F;
-    it.Gam = c->Gam + (size_t)slot * c->K * c->P;
-    it.Zp = c->Zp + (size_t)slot * c->K * c->F;
+    it.Dh = coding_spectrum(c, s);
+    it.r = s.r + (size_t)slot * s.F;
+    it.What = s.What + (size_t)slot * c->K * s.F;
+    it.Gam = s.Gam + (size_t)slot * c->K * s.P;
+    it.Zp = s.Zp + (size_t)slot * c->K * s.F;
     for (int t = 0; t < c->opts.Jz; ++t) {
       it.first = t == 0;
       it.last = t == c->opts.Jz - 1;
       e = timed(c, OCSC_K_CODE_RESID, [&] {
-        return launch_code_resid(c->N, bt.n, c->K, (float)c->rho, it.first, it.Dh, c->dn, xh, it.What,
-                                 c->r + (size_t)slot * c->F, c->stream);
+        return launch_code_resid(s.N, bt.n, c->K, (float)c->rho, it.first, it.Dh, s.dn, xh, it.What,
+                                 s.r + (size_t)slot * s.F, c->stream);
       });
       if (e != cudaSuccess) return cuda_fail(c, e, "code_resid");
-      if (large_fft(c->N)) {
-        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(c->N, LARGE_COL_IN_ADMM, it, bt, io, bt.n, npairs, c->tw, c->stream); });
+      if (large_fft(s.N)) {
+        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(s.N, LARGE_COL_IN_ADMM, it, bt, io, bt.n, npairs, s.tw, c->stream); });
         if (e == cudaSuccess)
-          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(c->N, LARGE_ROWS_ADMM, it, bt, io, bt.n, npairs, c->tw, c->stream); });
+          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(s.N, LARGE_ROWS_ADMM, it, bt, io, bt.n, npairs, s.tw, c->stream); });
         if (e == cudaSuccess && !it.last)
-          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(c->N, LARGE_COL_OUT_ADMM, it, bt, io, bt.n, npairs, c->tw, c->stream); });
+          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(s.N, LARGE_COL_OUT_ADMM, it, bt, io, bt.n, npairs, s.tw, c->stream); });
       } else {
-        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(c->N, it, bt, c->tw, c->stream); });
+        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(s.N, it, bt, s.tw, c->stream); });
       }
       if (e != cudaSuccess) return cuda_fail(c, e, "code_plane");
     }
   }
-  c->pending += n;
+  s.pending += n;
+  return OCSC_OK;
+}
+
+ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, const int *W,
+                      float *const *u) {
+  if (!c) return OCSC_EINVAL;
+  if (n <= 0 || !x || !H || !W) return fail(c, OCSC_EINVAL, "ocsc_code: bad arguments");
+  std::vector<std::vector<int>> groups(c->cls.size());
+  for (int i = 0; i < n; ++i) {
+    if (!x[i] || H[i] <= 0 || W[i] <= 0) return fail(c, OCSC_EINVAL, "ocsc_code: image %d invalid", i);
+    const int k = class_of(c, H[i], W[i]);
+    if (k < 0)
+      return fail(c, OCSC_EUNSUPPORTED, "image %d (%dx%d, pad %d) maps to no FFT size of this context", i, H[i],
+                  W[i], c->opts.pad);
+    groups[k].push_back(i);
+  }
+  for (size_t k = 0; k < groups.size(); ++k)
+    if (c->cls[k].pending + (int)groups[k].size() > c->opts.max_batch)
+      return fail(c, OCSC_ESTATE, "ocsc_code: %d pending + %d new samples of size %d exceed max_batch %d; "
+                  "call ocsc_update_dict", c->cls[k].pending, (int)groups[k].size(), c->cls[k].N, c->opts.max_batch);
+  for (size_t k = 0; k < groups.size(); ++k) {
+    if (groups[k].empty()) continue;
+    ocsc_status st = code_class(c, c->cls[k], groups[k], x, H, W, u);
+    if (st != OCSC_OK) return st;
+  }
   c->counters.samples_coded += n;
   return OCSC_OK;
 }
 
 ocsc_status ocsc_update_dict(ocsc_ctx *c) {
   if (!c) return OCSC_EINVAL;
-  if (c->pending == 0) return OCSC_OK;
-  const int B = c->pending;
-  const double rho_eff = c->opts.rho_convention == 1 ? c->rho * c->P : c->rho;
-  cudaError_t e;
+  long long fresh = 0;
+  for (const SizeClass &s : c->cls) fresh += s.pending;
+  if (fresh == 0) return OCSC_OK;
+  const long long n_total = c->n_seen + fresh;
+  cudaError_t e = cudaSuccess;
   if (!c->opts.warm_start) {
     e = cudaMemsetAsync(c->V, 0, (size_t)c->K * c->M * c->M * sizeof(float), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->Vh, 0, (size_t)c->K * c->F * sizeof(float2), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->th, 0, (size_t)c->K * c->F * sizeof(float2), c->stream);
+    for (SizeClass &s : c->cls) {
+      const size_t kf = (size_t)c->K * s.F * sizeof(float2);
+      if (e == cudaSuccess) e = cudaMemsetAsync(s.Vh, 0, kf, c->stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(s.th, 0, kf, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "cold start reset");
   }
-  FoldArgs fa{};
-  fa.K = c->K;
-  fa.F = c->F;
-  fa.B = B;
-  fa.first = c->n_seen == 0;
-  fa.alpha = (double)c->n_seen / (double)(c->n_seen + B);
-  fa.beta = 1.0 / (double)(c->n_seen + B);
-  fa.w = 1.0;
-  fa.rho_eff = rho_eff;
-  fa.A = c->A;
-  fa.b = c->b;
-  fa.Zp = c->Zp;
-  fa.xh = c->xhp;
-  fa.L = c->L;
-  fa.g = c->g;
-  fa.err = c->err;
-  e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_factor(fa, c->stream); });
-  if (e != cudaSuccess) return cuda_fail(c, e, "fold_factor");
-  for (int t = 0; t < c->opts.Jd; ++t) {
-    e = timed(c, OCSC_K_DSTEP, [&] { return launch_dstep(c->K, c->F, (float)rho_eff, c->L, c->g, c->Vh, c->th, c->Dcur, c->E, c->stream); });
-    if (e != cudaSuccess) return cuda_fail(c, e, "dstep");
-    e = timed(c, OCSC_K_VSTEP_COLS, [&] { return launch_vstep_cols(c->K, c->N, c->M, c->E, c->tw, c->Y, c->stream); });
-    if (e != cudaSuccess) return cuda_fail(c, e, "vstep_cols");
-    e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_vstep_project(0, c->K, c->N, c->M, c->Y, c->V, c->tw, c->Tm, c->stream); });
-    if (e != cudaSuccess) return cuda_fail(c, e, "vstep_project");
-    e = timed(c, OCSC_K_VSTEP_SPECTRUM, [&] { return launch_vstep_spectrum(0, c->K, c->N, c->M, c->Tm, c->tw, c->Vh, c->th, c->Dcur, c->stream); });
-    if (e != cudaSuccess) return cuda_fail(c, e, "vstep_spectrum");
+  // Fold and factor every class that has samples (its weight w_c changed).
+  std::vector<SizeClass *> active;
+  for (SizeClass &s : c->cls) {
+    const long long nc = s.n_seen + s.pending;
+    if (nc == 0) continue;
+    active.push_back(&s);
+    FoldArgs fa{};
+    fa.K = c->K;
+    fa.F = s.F;
+    fa.B = s.pending;
+    fa.first = s.n_seen == 0;
+    fa.alpha = (double)s.n_seen / (double)nc;
+    fa.beta = 1.0 / (double)nc;
+    fa.w = (double)nc / (double)n_total;
+    fa.rho_eff = c->opts.rho_convention == 1 ? c->rho * s.P : c->rho;
+    fa.A = s.A;
+    fa.b = s.b;
+    fa.Zp = s.Zp;
+    fa.xh = s.xhp;
+    fa.L = s.X;
+    fa.g = s.y;
+    fa.err = c->err;
+    e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_factor(fa, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "fold_factor");
   }
-  e = timed(c, OCSC_K_DICT_NORMS, [&] { return launch_dict_norms(c->K, c->F, c->opts.return_feasible ? c->Vh : c->Dcur, c->dn, c->stream); });
-  if (e != cudaSuccess) return cuda_fail(c, e, "dict_norms");
-  c->n_seen += B;
-  c->pending = 0;
+  AlphaClasses ac{};
+  ac.C = (int)active.size();
+  for (int i = 0; i < ac.C; ++i) {
+    ac.N[i] = active[i]->N;
+    ac.Y[i] = active[i]->Y;
+    ac.tw[i] = active[i]->tw;
+  }
+  for (int t = 0; t < c->opts.Jd; ++t) {
+    for (SizeClass *s : active) {
+      const float rho_eff = (float)(c->opts.rho_convention == 1 ? c->rho * s->P : c->rho);
+      e = timed(c, OCSC_K_DSTEP, [&] { return launch_dstep(c->K, s->F, rho_eff, s->X, s->y, s->Vh, s->th, s->Dcur, s->E, c->stream); });
+      if (e != cudaSuccess) return cuda_fail(c, e, "dstep");
+      e = timed(c, OCSC_K_VSTEP_COLS, [&] { return launch_vstep_cols(c->K, s->N, c->M, s->E, s->tw, s->Y, c->stream); });
+      if (e != cudaSuccess) return cuda_fail(c, e, "vstep_cols");
+    }
+    e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_vstep_project(c->K, c->M, ac, c->V, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "vstep_project");
+    for (SizeClass *s : active) {
+      e = timed(c, OCSC_K_VSTEP_SPECTRUM, [&] { return launch_vstep_partial_dft(c->K, s->N, c->M, c->V, s->tw, s->Tm, c->stream); });
+      if (e == cudaSuccess)
+        e = timed(c, OCSC_K_VSTEP_SPECTRUM, [&] { return launch_vstep_spectrum(0, c->K, s->N, c->M, s->Tm, s->tw, s->Vh, s->th, s->Dcur, c->stream); });
+      if (e != cudaSuccess) return cuda_fail(c, e, "vstep_spectrum");
+    }
+  }
+  for (SizeClass &s : c->cls) {
+    const bool is_active = std::find(active.begin(), active.end(), &s) != active.end();
+    if (!is_active && (e = class_spectrum(c, s)) != cudaSuccess) return cuda_fail(c, e, "class spectrum");
+    e = timed(c, OCSC_K_DICT_NORMS, [&] { return launch_dict_norms(c->K, s.F, coding_spectrum(c, s), s.dn, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "dict_norms");
+    s.n_seen += s.pending;
+    s.pending = 0;
+  }
+  c->n_seen = n_total;
   c->version += 1;
   c->counters.dict_updates += 1;
   return OCSC_OK;
@@ -421,15 +523,11 @@ ocsc_status ocsc_get_dict(ocsc_ctx *c, float *D_host, uint64_t *version) {
   if (!c || !D_host) return c ? fail(c, OCSC_EINVAL, "null output") : OCSC_EINVAL;
   ocsc_status st = check_device(c);
   if (st != OCSC_OK) return st;
-  const size_t bytes = (size_t)c->K * c->M * c->M * sizeof(float);
-  if (c->opts.return_feasible) {
-    cudaError_t e = cudaMemcpy(D_host, c->V, bytes, cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_fail(c, e, "copy filters");
-  } else {
-    // D_t = H(F^-1(D~_t)) with D~_t = D~_{t,J}: the pruned inverse DFT of the
-    // V-step applied to D~ alone, read back without projection.
+  if (!c->opts.return_feasible)
     return fail(c, OCSC_EUNSUPPORTED, "get_dict with return_feasible=0 is not implemented");
-  }
+  const size_t bytes = (size_t)c->K * c->M * c->M * sizeof(float);
+  cudaError_t e = cudaMemcpy(D_host, c->V, bytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy filters");
   if (version) *version = c->version;
   return OCSC_OK;
 }
@@ -444,19 +542,24 @@ ocsc_status ocsc_sync(ocsc_ctx *c) {
   return check_device(c);
 }
 
-// Real 2D FFT building blocks; for N >= 256 they run in chunks of pairs that
-// fit the context's tile buffer.
-static ocsc_status fft2_any(ocsc_ctx *c, int inverse, const float *in, float *out, int planes, const char *name) {
-  if (!large_fft(c->N)) {
-    cudaError_t e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(c->N, inverse, in, out, planes, c->tw, c->stream); });
+// Real 2D FFT building blocks on one class size; for N >= 256 they run in
+// chunks of pairs that fit the class's tile buffer.
+static ocsc_status fft2_any(ocsc_ctx *c, int N, int inverse, const float *in, float *out, int planes,
+                            const char *name) {
+  SizeClass *s = nullptr;
+  for (SizeClass &k : c->cls)
+    if (k.N == N) s = &k;
+  if (!s) return fail(c, OCSC_EUNSUPPORTED, "%s: N=%d is not a size of this context", name, N);
+  if (!large_fft(N)) {
+    cudaError_t e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(N, inverse, in, out, planes, s->tw, c->stream); });
     return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, name);
   }
   const int cap_pairs = c->opts.max_batch * ((c->K + 1) / 2);
-  const size_t spec = (size_t)c->F * 2, real = (size_t)c->P;  // floats per plane
+  const size_t spec = (size_t)s->F * 2, real = (size_t)s->P;  // floats per plane
   for (int p0 = 0; p0 < planes; p0 += 2 * cap_pairs) {
     const int np = planes - p0 < 2 * cap_pairs ? planes - p0 : 2 * cap_pairs;
     LargeIO io{};
-    io.T = c->tiles;
+    io.T = s->tiles;
     io.planes = np;
     CodeIter none{};
     ImgBatch b{};
@@ -464,36 +567,36 @@ static ocsc_status fft2_any(ocsc_ctx *c, int inverse, const float *in, float *ou
     if (!inverse) {
       io.real_in = in + (size_t)p0 * real;
       io.spec_out = reinterpret_cast<float2 *>(out + (size_t)p0 * spec);
-      e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_ROWS_FWD, none, b, io, 1, (np + 1) / 2, c->tw, c->stream); });
+      e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_ROWS_FWD, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_COL_OUT_R2C, none, b, io, 1, (np + 1) / 2, c->tw, c->stream); });
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_COL_OUT_R2C, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
     } else {
       io.spec_in = reinterpret_cast<const float2 *>(in + (size_t)p0 * spec);
       io.real_out = out + (size_t)p0 * real;
-      e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_COL_IN_C2R, none, b, io, 1, (np + 1) / 2, c->tw, c->stream); });
+      e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_COL_IN_C2R, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_ROWS_C2R, none, b, io, 1, (np + 1) / 2, c->tw, c->stream); });
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_ROWS_C2R, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
     }
     if (e != cudaSuccess) return cuda_fail(c, e, name);
   }
   return OCSC_OK;
 }
 
-ocsc_status ocsc_fft2_r2c(ocsc_ctx *c, const float *x, float *X, int planes) {
+ocsc_status ocsc_fft2_r2c(ocsc_ctx *c, int N, const float *x, float *X, int planes) {
   if (!c) return OCSC_EINVAL;
   if (!x || !X || planes < 0) return fail(c, OCSC_EINVAL, "fft2_r2c: bad arguments");
-  return fft2_any(c, 0, x, X, planes, "fft2_r2c");
+  return fft2_any(c, N, 0, x, X, planes, "fft2_r2c");
 }
 
-ocsc_status ocsc_fft2_c2r(ocsc_ctx *c, const float *X, float *x, int planes) {
+ocsc_status ocsc_fft2_c2r(ocsc_ctx *c, int N, const float *X, float *x, int planes) {
   if (!c) return OCSC_EINVAL;
   if (!x || !X || planes < 0) return fail(c, OCSC_EINVAL, "fft2_c2r: bad arguments");
-  return fft2_any(c, 1, X, x, planes, "fft2_c2r");
+  return fft2_any(c, N, 1, X, x, planes, "fft2_c2r");
 }
 
 ocsc_status ocsc_drop_pending(ocsc_ctx *c) {
   if (!c) return OCSC_EINVAL;
-  c->pending = 0;
+  for (SizeClass &s : c->cls) s.pending = 0;
   return OCSC_OK;
 }
 
@@ -502,16 +605,17 @@ ocsc_status ocsc_objective(ocsc_ctx *c, int n, const float *const *x, const int 
   if (!c) return OCSC_EINVAL;
   if (n < 0 || (n > 0 && (!x || !H || !W || !u || !out_host)))
     return fail(c, OCSC_EINVAL, "ocsc_objective: bad arguments");
+  std::vector<int> cl(n);
   for (int i = 0; i < n; ++i) {
     if (!x[i] || !u[i] || H[i] <= 0 || W[i] <= 0) return fail(c, OCSC_EINVAL, "ocsc_objective: sample %d invalid", i);
-    if (padded_side(H[i] > W[i] ? H[i] : W[i], c->opts.pad) != c->N)
-      return fail(c, OCSC_EUNSUPPORTED, "sample %d does not map to FFT size %d", i, c->N);
+    cl[i] = class_of(c, H[i], W[i]);
+    if (cl[i] < 0) return fail(c, OCSC_EUNSUPPORTED, "sample %d maps to no FFT size of this context", i);
   }
-  const float2 *Dh = c->opts.return_feasible ? c->Vh : c->Dcur;
-  float2 *Uh = c->What;  // coding workspace of slot 0, idle between ocsc_code calls
   for (int s0 = 0; s0 < n; s0 += kObjChunk) {
     const int m = n - s0 < kObjChunk ? n - s0 : kObjChunk;
     for (int i = 0; i < m; ++i) {
+      SizeClass &s = c->cls[cl[s0 + i]];
+      float2 *Uh = s.What;  // coding workspace of slot 0, idle between ocsc_code calls
       ImgBatch bt{};
       bt.n = 1;
       bt.x[0] = x[s0 + i];
@@ -519,35 +623,35 @@ ocsc_status ocsc_objective(ocsc_ctx *c, int n, const float *const *x, const int 
       bt.H[0] = H[s0 + i];
       bt.W[0] = W[s0 + i];
       cudaError_t e = cudaSuccess;
-      if (large_fft(c->N)) {
+      if (large_fft(s.N)) {
         CodeIter none{};
         LargeIO io{};
-        io.T = c->tiles;
-        io.spec_out = c->obj_xh;
+        io.T = s.tiles;
+        io.spec_out = s.obj_xh;
         io.images = 1;
-        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_ROWS_FWD, none, bt, io, 1, 1, c->tw, c->stream); });
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_ROWS_FWD, none, bt, io, 1, 1, s.tw, c->stream); });
         if (e == cudaSuccess)
-          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_COL_OUT_IMAGE, none, bt, io, 1, 1, c->tw, c->stream); });
+          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_COL_OUT_IMAGE, none, bt, io, 1, 1, s.tw, c->stream); });
         LargeIO jo{};
-        jo.T = c->tiles;
+        jo.T = s.tiles;
         jo.real_in = u[s0 + i];
         jo.spec_out = Uh;
         jo.planes = c->K;
         const int np = (c->K + 1) / 2;
         if (e == cudaSuccess)
-          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_ROWS_FWD, none, bt, jo, 1, np, c->tw, c->stream); });
+          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_ROWS_FWD, none, bt, jo, 1, np, s.tw, c->stream); });
         if (e == cudaSuccess)
-          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(c->N, LARGE_COL_OUT_R2C, none, bt, jo, 1, np, c->tw, c->stream); });
+          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_COL_OUT_R2C, none, bt, jo, 1, np, s.tw, c->stream); });
       } else {
-        e = timed(c, OCSC_K_COUNT, [&] { return launch_image_spectrum(c->N, bt, c->tw, c->obj_xh, c->stream); });
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_image_spectrum(s.N, bt, s.tw, s.obj_xh, c->stream); });
         if (e == cudaSuccess)
-          e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(c->N, 0, u[s0 + i], reinterpret_cast<float *>(Uh), c->K, c->tw, c->stream); });
+          e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(s.N, 0, u[s0 + i], reinterpret_cast<float *>(Uh), c->K, s.tw, c->stream); });
       }
       if (e == cudaSuccess) {
         c->counters.kernel_launches += 2;  // three kernels in launch_objective
         e = timed(c, OCSC_K_COUNT, [&] {
-          return launch_objective(c->K, c->N, c->lam, Dh, c->obj_xh, Uh, u[s0 + i], c->obj_part, c->obj_out + i,
-                                  c->stream);
+          return launch_objective(c->K, s.N, c->lam, coding_spectrum(c, s), s.obj_xh, Uh, u[s0 + i], c->obj_part,
+                                  c->obj_out + i, c->stream);
         });
       }
       if (e != cudaSuccess) return cuda_fail(c, e, "objective");

@@ -276,3 +276,37 @@ def test_larger_minibatch_matches_oracle():
         assert rel(codes[t], ocodes[t]) < REL_TOL
     for u in range(2):
         assert rel(dicts[u], odicts[u]) < REL_TOL
+
+
+# --- uneven sizes: size classes with the consensus dictionary step --------------
+
+def test_size_classes_match_oracle():
+    """Images of two padded sizes in one learner (reading R16): per-class
+    histories and duals, V-step on the mean of the class crops; one batch
+    leaves the 128 class idle (refactored with its new weight only)."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    K, M, lam, rho, Jz, Jd = 10, 7, 0.5, 1.0, 15, 5
+    sides = [[50, 100, 50], [100, 100], [50]]
+    raw = raw_filters(K, M, 23)
+    learner = pkg.OCSC(K, M, lam, rho, fft_sizes=[64, 128], pad=6, Jz=Jz, Jd=Jd, max_batch=3)
+    learner.set_dict(raw, normalize=True)
+    st = oracle.init_multi(np.asarray(raw, np.float64), [(64, 64), (128, 128)], lam, rho)
+    seed = 900
+    for batch in sides:
+        imgs = [make_image(s, s + 7 if s == 100 else s, seed + i) for i, s in enumerate(batch)]
+        seed += 10
+        us = learner.code([torch.from_numpy(im).cuda() for im in imgs])
+        learner.update_dict()
+        D = learner.get_dict()
+        res = {}
+        for im, u in zip(imgs, us):
+            N = 64 if max(im.shape) + 6 <= 64 else 128
+            r = oracle.code_multi(st, im, (N, N), Jz)
+            res.setdefault((N, N), []).append(r)
+            assert u.shape[-1] == N
+            assert rel(u.cpu().numpy(), r.U) < REL_TOL
+        oracle.update_dict_multi(st, res, Jd)
+        assert rel(D, st.V) < REL_TOL
+    learner.close()
