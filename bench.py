@@ -287,6 +287,44 @@ def batched_leg(pkg, w, dev, stream, args):
     return out
 
 
+def mixed_leg(pkg, dev, stream, args):
+    """Uneven sizes: images of side 64 / 128 / 256 padded by 10 to FFT 128 /
+    256 / 512, K = 100 filters 11x11, mini-batches of 64 mixed images; one
+    learner with three size classes (consensus dictionary step)."""
+    import torch
+    from workloads import WORKLOADS
+
+    w = WORKLOADS["batched_mixed_k100"]
+    B = w.batch
+    learner = pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_sizes=[128, 256, 512], pad=w.pad,
+                       Jz=w.Jz, Jd=w.Jd, max_batch=B)
+    learner.set_dict(w.filters0(), normalize=True)
+    nb = args.mixed_steps
+    xs = [torch.from_numpy(w.image(i)).to(dev) for i in range(B * (nb + 1))]
+    sides = [int(x.shape[0]) for x in xs]
+    learner.code(xs[:B], want_codes=False)
+    learner.update_dict()
+    learner.sync()
+    learner.profile(["fold_factor", "code_plane", "dstep"])
+    learner.profile_read(["fold_factor", "code_plane", "dstep"])
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for t in range(1, nb + 1):
+        learner.code(xs[t * B:(t + 1) * B], want_codes=False)
+        learner.update_dict()
+    e1.record(stream)
+    e1.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    prof = learner.profile_read(["fold_factor", "code_plane", "dstep"])
+    learner.close()
+    timed = sides[B:]
+    return {"workload": "batched_mixed_k100", "batch": B, "steps": nb, "value": B * nb / secs, "unit": UNIT,
+            "ms_per_batch": 1e3 * secs / nb,
+            "sides_in_timed_batches": {str(sd): timed.count(sd) for sd in sorted(set(timed))},
+            "ms_per_batch_by_kernel": {k: v[0] / nb for k, v in prof.items()}}
+
+
 def ours_arm(args):
     import numpy as np
     import torch
@@ -390,6 +428,7 @@ def ours_arm(args):
                "d2h_bytes_per_step": int(u_host.numel() * 4), "steps": E}
     learner.close()
     batched = batched_leg(pkg, w, dev, stream, args) if args.batched_steps > 0 else None
+    mixed = mixed_leg(pkg, dev, stream, args) if args.mixed_steps > 0 else None
 
     if rank != 0:
         return
@@ -419,6 +458,7 @@ def ours_arm(args):
         "gpu_launches": int(c1["kernel_launches"] - c0["kernel_launches"]),
         "kernel_breakdown": breakdown,
         "batched": batched,
+        "mixed_sizes": mixed,
     }
     print(json.dumps(line))
 
@@ -437,6 +477,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=64, help="mini-batch of the batched leg")
     ap.add_argument("--batched-steps", type=int, default=4, help="timed batches of the batched leg (0: skip)")
+    ap.add_argument("--mixed-steps", type=int, default=2,
+                    help="timed batches of the uneven-size leg (0: skip)")
     ap.add_argument("--quality-images", type=int, default=256,
                     help="images for the plain-vs-batched held-out objective (0: skip)")
     ap.add_argument("--traffic", type=float, default=None,
