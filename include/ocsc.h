@@ -175,6 +175,64 @@ ocsc_status ocsc_drop_pending(ocsc_ctx *ctx);
 ocsc_status ocsc_objective(ocsc_ctx *ctx, int n, const float *const *x, const int *H, const int *W,
                            const float *const *u, double *out_host);
 
+/*
+ * Serving: continuous batching of coding requests over one context
+ * (spec serving pattern; each request runs the code ADMM of
+ * Sec. II-C.1 to a residual tolerance instead of a fixed iteration count).
+ *
+ * Requests are admitted in arrival order while a workspace slot of their size
+ * class is free and the sum of the admitted requests' working sets stays within
+ * mem_budget bytes.  Each ocsc_server_step advances every admitted request by
+ * check_every ADMM iterations (requests at different iteration counts share the
+ * same launches), then reduces each request's relative primal residual
+ * |Z - U| / max(|Z|, |U|) and dual residual |U - U_prev| / |Gamma| in a fixed
+ * order and completes the requests whose both residuals are <= tol, or that
+ * reached max_iters.  A completed request's code U is in its output buffer.
+ * With learn = 1 completed requests are folded into the history and DictOCSC
+ * runs after every update_every completions (Algorithm 3 with mini-batches);
+ * a request is coded against the dictionary current at its admission, so its
+ * result does not depend on the other requests in flight.
+ */
+typedef struct ocsc_server ocsc_server;
+
+typedef struct {
+  double tol;          /* relative residual target (default 1e-4) */
+  int check_every;     /* iterations per step and between checks (default 5, >= 2) */
+  int max_iters;       /* iteration cap (default 500) */
+  size_t mem_budget;   /* bytes of in-flight working sets (default 8 GiB) */
+  int update_every;    /* completions between dictionary updates (default 64;
+                          must not exceed the context's max_batch) */
+  int learn;           /* 1 (default): fold completed requests, update the dictionary */
+} ocsc_server_opts;
+
+typedef struct {
+  uint64_t id;           /* the id given at submission */
+  int iters;             /* ADMM iterations run */
+  double primal, dual;   /* relative residuals at completion */
+  uint64_t dict_version; /* dictionary version (ocsc_get_dict) it was coded with */
+} ocsc_served;
+
+void ocsc_server_default_opts(ocsc_server_opts *o);
+
+/* Create a server on ctx (which must outlive it); allocates the slot
+ * workspaces of every size class (at most 64 slots per class, as many as fit
+ * mem_budget). */
+ocsc_status ocsc_server_create(ocsc_server **out, ocsc_ctx *ctx, const ocsc_server_opts *opts);
+void ocsc_server_destroy(ocsc_server *s);
+
+/* Queue one request: x (DEVICE, H x W floats) is coded into u (DEVICE,
+ * K x N x N floats, N its padded size).  Both stay owned by the caller and must
+ * remain valid until the request is reported by ocsc_server_poll. */
+ocsc_status ocsc_server_submit(ocsc_server *s, uint64_t id, const float *x, int H, int W, float *u);
+
+/* One scheduling round (admission, check_every iterations, residual checks,
+ * completions, a due dictionary update).  Synchronises ctx's stream.  Reports
+ * the requests in flight and still queued. */
+ocsc_status ocsc_server_step(ocsc_server *s, int *n_active, int *n_queued);
+
+/* Copy up to max completed requests (completion order) to out; *n = count. */
+ocsc_status ocsc_server_poll(ocsc_server *s, ocsc_served *out, int max, int *n);
+
 /* Kernel classes for ocsc_profile / ocsc_profile_read. */
 typedef enum {
   OCSC_K_IMAGE_SPECTRUM = 0, /* x~ = F(pad x) */

@@ -43,6 +43,16 @@ class ocsc_counters(ctypes.Structure):
                 ("dict_updates", ctypes.c_uint64)]
 
 
+class ocsc_server_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("check_every", ctypes.c_int), ("max_iters", ctypes.c_int),
+                ("mem_budget", ctypes.c_size_t), ("update_every", ctypes.c_int), ("learn", ctypes.c_int)]
+
+
+class ocsc_served(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("iters", ctypes.c_int), ("primal", ctypes.c_double),
+                ("dual", ctypes.c_double), ("dict_version", ctypes.c_uint64)]
+
+
 KERNELS = ("image_spectrum", "code_resid", "code_plane", "fold_factor", "dstep", "vstep_cols",
            "vstep_project", "dict_norms", "vstep_spectrum")
 
@@ -69,6 +79,12 @@ _PROTOS = {
     "ocsc_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
     "ocsc_fft2_r2c": (_I, [_P, _I, _P, _P, _I]),
     "ocsc_fft2_c2r": (_I, [_P, _I, _P, _P, _I]),
+    "ocsc_server_default_opts": (None, [ctypes.POINTER(ocsc_server_opts)]),
+    "ocsc_server_create": (_I, [ctypes.POINTER(_P), _P, ctypes.POINTER(ocsc_server_opts)]),
+    "ocsc_server_destroy": (None, [_P]),
+    "ocsc_server_submit": (_I, [_P, ctypes.c_uint64, _P, _I, _I, _P]),
+    "ocsc_server_step": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "ocsc_server_poll": (_I, [_P, ctypes.POINTER(ocsc_served), _I, ctypes.POINTER(_I)]),
     "ocsc_code_noalloc": (_I, [_P, _I, _I, _P, _I, _I, _I, ctypes.c_double, ctypes.c_double, _I, _P,
                                _P, ctypes.c_char_p, ctypes.c_size_t]),
 }
@@ -336,3 +352,68 @@ class OCSC:
         x = torch.empty((X.shape[0], N, N), device=X.device, dtype=torch.float32)
         ocsc_fft2_c2r(self.ctx, N, X.data_ptr(), x.data_ptr(), X.shape[0])
         return x
+
+
+class Server:
+    """Continuous-batching request server over an :class:`OCSC` learner.
+
+    ``submit`` queues an image (2D float32 CUDA tensor) and returns the output
+    tensor that will hold its code; ``step`` runs one scheduling round; ``poll``
+    returns the completed requests as dicts.  Output tensors and images are
+    kept alive here until their request completes.
+    """
+
+    def __init__(self, learner: "OCSC", **opts):
+        self.learner = learner
+        o = ocsc_server_opts()
+        lib().ocsc_server_default_opts(ctypes.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown server option {k}")
+            setattr(o, k, v)
+        h = ctypes.c_void_p()
+        _check(learner.ctx, lib().ocsc_server_create(ctypes.byref(h), learner.ctx, ctypes.byref(o)))
+        self.h = h
+        self.opts = o
+        self._live = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ocsc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, rid: int, image, out=None):
+        torch = self.learner._torch
+        x = image.contiguous()
+        n = self.learner.padded_size(x.shape[0], x.shape[1])
+        if out is None:
+            out = torch.empty((self.learner.K, n, n), device=x.device, dtype=torch.float32)
+        _check(self.learner.ctx, lib().ocsc_server_submit(self.h, rid, ctypes.c_void_p(x.data_ptr()),
+                                                          x.shape[0], x.shape[1],
+                                                          ctypes.c_void_p(out.data_ptr())))
+        self._live[rid] = (x, out)
+        return out
+
+    def step(self):
+        a, q = _I(), _I()
+        _check(self.learner.ctx, lib().ocsc_server_step(self.h, ctypes.byref(a), ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, max_items: int = 4096):
+        buf = (ocsc_served * max_items)()
+        n = _I()
+        _check(self.learner.ctx, lib().ocsc_server_poll(self.h, buf, max_items, ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            d = buf[i]
+            x, u = self._live.pop(d.id, (None, None))
+            out.append({"id": d.id, "iters": d.iters, "primal": d.primal, "dual": d.dual,
+                        "dict_version": d.dict_version, "code": u})
+        return out
+

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libocsc.so")
-SOURCES = ["code_admm.cu", "code_large.cu", "dict_update.cu", "objective.cu", "ocsc_api.cu", "noalloc.cu"]
+SOURCES = ["code_admm.cu", "code_large.cu", "dict_update.cu", "objective.cu", "ocsc_api.cu", "serve.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
@@ -44,7 +45,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]  # sources and internal headers
     deps.append(os.path.join(ROOT, "include", "ocsc.h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)

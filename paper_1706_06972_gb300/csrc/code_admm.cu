@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(TileThreads<N>::value)
   }
   __syncthreads();
   fft2d_tile<N, NT, false>(tile, s_tw);
-  float2 *out = xh + (size_t)img * F;
+  float2 *out = xh + (size_t)b.slot[img] * F;
   for (int p = threadIdx.x; p < F; p += NT) {
     const int k1 = p / NH, k2 = p % NH;
     out[p] = tile[k1 * PITCH + k2];
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(TileThreads<N>::value)
 }
 
 // r_p = (x~(p) - sum_k D~_k(p) W^_k(p)) / (rho + |d_p|^2); block (32, 8).
-__global__ void code_resid_kernel(int K, int F, float rho, int first,
+__global__ void code_resid_kernel(int K, int F, float rho, int first, int serve, ImgBatch b,
                                   const float2 *__restrict__ Dh, const float *__restrict__ dn,
                                   const float2 *__restrict__ xh, const float2 *__restrict__ What,
                                   float2 *__restrict__ r) {
@@ -69,9 +69,11 @@ __global__ void code_resid_kernel(int K, int F, float rho, int first,
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int p = blockIdx.x * 32 + tx;
   const int img = blockIdx.y;
+  const int slot = b.slot[img];
+  const bool is_first = serve ? b.iter[img] == 0 : first != 0;
   float2 s = make_float2(0.f, 0.f);
-  if (!first && p < F) {
-    const float2 *w = What + (size_t)img * K * F;
+  if (!is_first && p < F) {
+    const float2 *w = What + (size_t)slot * K * F;
 #pragma unroll 4
     for (int k = ty; k < K; k += 8) s = cadd(s, cmul(Dh[(size_t)k * F + p], w[(size_t)k * F + p]));
   }
@@ -81,9 +83,30 @@ __global__ void code_resid_kernel(int K, int F, float rho, int first,
     float2 t = part[0][tx];
 #pragma unroll
     for (int y = 1; y < 8; ++y) t = cadd(t, part[y][tx]);
-    const float2 x = xh[(size_t)img * F + p];
+    const float2 x = xh[(size_t)slot * F + p];
     const float inv = 1.0f / (rho + dn[p]);
-    r[(size_t)img * F + p] = make_float2((x.x - t.x) * inv, (x.y - t.y) * inv);
+    r[(size_t)slot * F + p] = make_float2((x.x - t.x) * inv, (x.y - t.y) * inv);
+  }
+}
+
+// Sum kResidTerms values over a block; thread 0 writes them to out.
+__device__ __forceinline__ void block_sum_terms(float (&v)[kResidTerms], float *out) {
+  __shared__ float red[kResidTerms][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kResidTerms; ++q) {
+    float x = v[q];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[q][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < kResidTerms; ++q) {
+      float x = lane < nw ? red[q][lane] : 0.f;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) out[q] = x;
+    }
   }
 }
 
@@ -101,15 +124,21 @@ __global__ void __launch_bounds__(TileThreads<N>::value)
   const int kb = ka + 1;
   const bool hasb = kb < K;
   const int img = blockIdx.y;
+  const int slot = b.slot[img];
+  const int t = b.iter[img];
+  const bool first = it.serve ? t == 0 : it.first != 0;
+  const bool store_last = it.serve ? (t + 1) % it.check == 0 : it.last != 0;
+  const bool store_prev = it.serve && (t + 2) % it.check == 0;
+  const bool skip_fwd = !it.serve && it.last;
   load_twiddles<N, NT>(s_tw, tw);
 
   const float2 *Da = it.Dh + (size_t)ka * F;
   const float2 *Db = it.Dh + (size_t)(hasb ? kb : ka) * F;
-  const float2 *rr = it.r + (size_t)img * F;
-  float2 *Wa = it.What + ((size_t)img * K + ka) * F;
-  float2 *Wb = it.What + ((size_t)img * K + (hasb ? kb : ka)) * F;
-  float2 *Za = it.Zp + ((size_t)img * K + ka) * F;
-  float2 *Zb = it.Zp + ((size_t)img * K + (hasb ? kb : ka)) * F;
+  const float2 *rr = it.r + (size_t)slot * F;
+  float2 *Wa = it.What + ((size_t)slot * K + ka) * F;
+  float2 *Wb = it.What + ((size_t)slot * K + (hasb ? kb : ka)) * F;
+  float2 *Za = it.Zp + ((size_t)slot * K + ka) * F;
+  float2 *Zb = it.Zp + ((size_t)slot * K + (hasb ? kb : ka)) * F;
 
   // Z~-step for both filters; pack z_a + i z_b over the full spectrum.
   for (int p = threadIdx.x; p < F; p += NT) {
@@ -117,11 +146,11 @@ __global__ void __launch_bounds__(TileThreads<N>::value)
     const float2 rp = rr[p];
     float2 za = cconjmul(Da[p], rp);
     float2 zb = hasb ? cconjmul(Db[p], rp) : make_float2(0.f, 0.f);
-    if (!it.first) {
+    if (!first) {
       za = cadd(za, Wa[p]);
       if (hasb) zb = cadd(zb, Wb[p]);
     }
-    if (it.last) {
+    if (store_last) {
       Za[p] = za;
       if (hasb) Zb[p] = zb;
     }
@@ -136,30 +165,42 @@ __global__ void __launch_bounds__(TileThreads<N>::value)
 
   // Spatial step: U = S(Z + Gamma), Gamma += Z - U, W = U - Gamma.
   const float invP = 1.0f / (float)P;
-  float *Ga = it.Gam + ((size_t)img * K + ka) * P;
-  float *Gb = it.Gam + ((size_t)img * K + (hasb ? kb : ka)) * P;
+  float *Ga = it.Gam + ((size_t)slot * K + ka) * P;
+  float *Gb = it.Gam + ((size_t)slot * K + (hasb ? kb : ka)) * P;
   float *Ua = b.u[img] ? b.u[img] + (size_t)ka * P : nullptr;
   float *Ub = (b.u[img] && hasb) ? b.u[img] + (size_t)kb * P : nullptr;
+  const bool resid = it.serve && store_last;
+  float acc[kResidTerms] = {0.f, 0.f, 0.f, 0.f, 0.f};
   for (int q = threadIdx.x; q < P; q += NT) {
     const int q1 = q / N, q2 = q % N;
     const float2 c = tile[q1 * PITCH + q2];
-    const float ga = it.first ? 0.f : Ga[q];
-    const float gb = (it.first || !hasb) ? 0.f : Gb[q];
-    const float va = c.x * invP + ga;
-    const float vb = c.y * invP + gb;
+    const float ga = first ? 0.f : Ga[q];
+    const float gb = (first || !hasb) ? 0.f : Gb[q];
+    const float za = c.x * invP, zb = c.y * invP;
+    const float va = za + ga;
+    const float vb = zb + gb;
     const float ua = soft_threshold(va, it.thr);
     const float ub = soft_threshold(vb, it.thr);
     const float ga2 = va - ua, gb2 = vb - ub;
+    if (resid) {
+      const float pa = (first || !Ua) ? 0.f : Ua[q];
+      const float pb = (first || !Ub) ? 0.f : Ub[q];
+      acc[0] += (za - ua) * (za - ua) + (hasb ? (zb - ub) * (zb - ub) : 0.f);
+      acc[1] += za * za + (hasb ? zb * zb : 0.f);
+      acc[2] += ua * ua + (hasb ? ub * ub : 0.f);
+      acc[3] += (ua - pa) * (ua - pa) + (hasb ? (ub - pb) * (ub - pb) : 0.f);
+      acc[4] += ga2 * ga2 + (hasb ? gb2 * gb2 : 0.f);
+    }
     Ga[q] = ga2;
     if (hasb) Gb[q] = gb2;
-    if (it.last) {
+    if (store_last || store_prev) {
       if (Ua) Ua[q] = ua;
       if (Ub) Ub[q] = ub;
-    } else {
-      tile[q1 * PITCH + q2] = make_float2(ua - ga2, hasb ? ub - gb2 : 0.f);
     }
+    if (!skip_fwd) tile[q1 * PITCH + q2] = make_float2(ua - ga2, hasb ? ub - gb2 : 0.f);
   }
-  if (it.last) return;
+  if (resid) block_sum_terms(acc, it.resid + ((size_t)slot * gridDim.x + blockIdx.x) * kResidTerms);
+  if (skip_fwd) return;
   __syncthreads();
   fft2d_tile<N, NT, false>(tile, s_tw);
 
@@ -226,9 +267,30 @@ __global__ void __launch_bounds__(TileThreads<N>::value)
   }
 }
 
+// Per-slot residual sums in double, in a fixed order: out[i][q] = sum over the
+// slot's partial groups of partials[slot][g][q].
+__global__ void resid_reduce_kernel(const int *__restrict__ slots, int n, int groups,
+                                    const float *__restrict__ partials, double *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * kResidTerms) return;
+  const int img = i / kResidTerms, q = i % kResidTerms;
+  const float *p = partials + (size_t)slots[img] * groups * kResidTerms + q;
+  double s = 0.0;
+  for (int g = 0; g < groups; ++g) s += (double)p[(size_t)g * kResidTerms];
+  out[i] = s;
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+
+cudaError_t launch_resid_reduce(const int *slots_dev, int n, int groups, const float *partials,
+                                double *out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int total = n * kResidTerms;
+  resid_reduce_kernel<<<(total + 127) / 128, 128, 0, s>>>(slots_dev, n, groups, partials, out);
+  return cudaGetLastError();
+}
 
 template <typename Kern>
 static cudaError_t set_smem(Kern k, size_t bytes) {
@@ -254,12 +316,12 @@ cudaError_t launch_image_spectrum(int N, const ImgBatch &b, const float2 *tw, fl
   }
 }
 
-cudaError_t launch_code_resid(int N, int n, int K, float rho, int first, const float2 *Dh,
-                              const float *dn, const float2 *xh, const float2 *What, float2 *r,
-                              cudaStream_t s) {
+cudaError_t launch_code_resid(int N, const ImgBatch &b, const CodeIter &it, float rho, const float *dn,
+                              const float2 *xh, cudaStream_t s) {
+  if (b.n <= 0) return cudaSuccess;
   const int F = N * (N / 2 + 1);
-  dim3 grid((F + 31) / 32, n), block(32, 8);
-  code_resid_kernel<<<grid, block, 0, s>>>(K, F, rho, first, Dh, dn, xh, What, r);
+  dim3 grid((F + 31) / 32, b.n), block(32, 8);
+  code_resid_kernel<<<grid, block, 0, s>>>(it.K, F, rho, it.first, it.serve, b, it.Dh, dn, xh, it.What, it.r);
   return cudaGetLastError();
 }
 

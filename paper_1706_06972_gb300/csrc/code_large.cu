@@ -37,6 +37,27 @@ size_t large_smem_bytes() {
 
 __device__ __forceinline__ float soft_thr(float v, float t) { return v > t ? v - t : (v < -t ? v + t : 0.0f); }
 
+// Sum kResidTerms values over a block; thread 0 writes them to out.
+__device__ __forceinline__ void block_terms(float (&v)[kResidTerms], float *out) {
+  __shared__ float red[kResidTerms][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < kResidTerms; ++q) {
+    float x = v[q];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) red[q][warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < kResidTerms; ++q) {
+      float x = lane < nw ? red[q][lane] : 0.f;
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) out[q] = x;
+    }
+  }
+}
+
 // Column-block source / destination of line l: half-spectrum column c0 + l for
 // l < CB, mirror column N - (c0 + l - CB) otherwise; -1 when it does not exist.
 template <int N>
@@ -53,7 +74,7 @@ __device__ __forceinline__ int line_column(int c0, int l) {
 // MODE 0: Z~-step of the ADMM; MODE 1: given half spectra Xa, Xb (c2r).
 template <int N, int MODE>
 __global__ void __launch_bounds__(kLargeThreads)
-    large_col_in_kernel(CodeIter it, LargeIO io, const float2 *__restrict__ tw) {
+    large_col_in_kernel(CodeIter it, ImgBatch b, LargeIO io, const float2 *__restrict__ tw) {
   using G = LargeGeom<N>;
   extern __shared__ float2 lsm[];
   float2 *lines = lsm;
@@ -65,6 +86,10 @@ __global__ void __launch_bounds__(kLargeThreads)
   const int npairs = gridDim.y;
   const int K = MODE == 0 ? it.K : io.planes;
   const bool hasb = kb < K;
+  const int slot = MODE == 0 ? b.slot[img] : img;
+  const int t = MODE == 0 ? b.iter[img] : 0;
+  const bool first = it.serve ? t == 0 : it.first != 0;
+  const bool store_last = it.serve ? (t + 1) % it.check == 0 : it.last != 0;
   const float2 *Da = nullptr, *Db = nullptr, *rr = nullptr;
   const float2 *Wa = nullptr, *Wb = nullptr;
   float2 *Za = nullptr, *Zb = nullptr;
@@ -72,11 +97,11 @@ __global__ void __launch_bounds__(kLargeThreads)
   if (MODE == 0) {
     Da = it.Dh + (size_t)ka * G::F;
     Db = it.Dh + (size_t)(hasb ? kb : ka) * G::F;
-    rr = it.r + (size_t)img * G::F;
-    Wa = it.What + ((size_t)img * K + ka) * G::F;
-    Wb = it.What + ((size_t)img * K + (hasb ? kb : ka)) * G::F;
-    Za = it.Zp + ((size_t)img * K + ka) * G::F;
-    Zb = it.Zp + ((size_t)img * K + (hasb ? kb : ka)) * G::F;
+    rr = it.r + (size_t)slot * G::F;
+    Wa = it.What + ((size_t)slot * K + ka) * G::F;
+    Wb = it.What + ((size_t)slot * K + (hasb ? kb : ka)) * G::F;
+    Za = it.Zp + ((size_t)slot * K + ka) * G::F;
+    Zb = it.Zp + ((size_t)slot * K + (hasb ? kb : ka)) * G::F;
   } else {
     Xa = io.spec_in + (size_t)ka * G::F;
     Xb = io.spec_in + (size_t)(hasb ? kb : ka) * G::F;
@@ -91,11 +116,11 @@ __global__ void __launch_bounds__(kLargeThreads)
       const float2 rp = rr[p];
       za = cconjmul(Da[p], rp);
       if (hasb) zb = cconjmul(Db[p], rp);
-      if (!it.first) {
+      if (!first) {
         za = cadd(za, Wa[p]);
         if (hasb) zb = cadd(zb, Wb[p]);
       }
-      if (it.last) {
+      if (store_last) {
         Za[p] = za;
         if (hasb) Zb[p] = zb;
       }
@@ -109,7 +134,7 @@ __global__ void __launch_bounds__(kLargeThreads)
   }
   __syncthreads();
   fft_lines<N, G::NL, true, kLargeThreads>(lines, G::PITCH, s_tw);
-  float2 *T = io.T + ((size_t)img * npairs + pair) * G::P;
+  float2 *T = io.T + ((size_t)slot * npairs + pair) * G::P;
   for (int e = threadIdx.x; e < N * G::NL; e += kLargeThreads) {
     const int q1 = e / G::NL, l = e % G::NL;
     const int col = line_column<N>(c0, l);
@@ -131,7 +156,8 @@ __global__ void __launch_bounds__(kLargeThreads)
   const int q0 = blockIdx.x * G::RB;
   const int pair = blockIdx.y, img = blockIdx.z;
   const int npairs = gridDim.y;
-  float2 *T = io.T + ((size_t)img * npairs + pair) * G::P;
+  const int slot = (MODE == 0 || io.images) ? b.slot[img] : img;
+  float2 *T = io.T + ((size_t)slot * npairs + pair) * G::P;
   if (MODE == 1) {
     if (io.images) {  // sample spectrum: image img, zero-padded, as the real part
       const float *x = b.x[img];
@@ -178,29 +204,47 @@ __global__ void __launch_bounds__(kLargeThreads)
     }
     const int K = it.K, ka = 2 * pair, kb = ka + 1;
     const bool hasb = kb < K;
-    float *Ga = it.Gam + ((size_t)img * K + ka) * G::P;
-    float *Gb = it.Gam + ((size_t)img * K + (hasb ? kb : ka)) * G::P;
+    const int t = b.iter[img];
+    const bool first = it.serve ? t == 0 : it.first != 0;
+    const bool store_last = it.serve ? (t + 1) % it.check == 0 : it.last != 0;
+    const bool store_prev = it.serve && (t + 2) % it.check == 0;
+    const bool skip_fwd = !it.serve && it.last;
+    const bool resid = it.serve && store_last;
+    float *Ga = it.Gam + ((size_t)slot * K + ka) * G::P;
+    float *Gb = it.Gam + ((size_t)slot * K + (hasb ? kb : ka)) * G::P;
     float *Ua = b.u[img] ? b.u[img] + (size_t)ka * G::P : nullptr;
     float *Ub = (b.u[img] && hasb) ? b.u[img] + (size_t)kb * G::P : nullptr;
+    float acc[kResidTerms] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int e = threadIdx.x; e < G::RB * N; e += kLargeThreads) {
       const int rrow = e / N, q2 = e % N;
       const size_t o = (size_t)(q0 + rrow) * N + q2;
       const float2 c = lines[rrow * G::PITCH + q2];
-      const float ga = it.first ? 0.f : Ga[o];
-      const float gb = (it.first || !hasb) ? 0.f : Gb[o];
-      const float va = c.x * invP + ga, vb = c.y * invP + gb;
+      const float ga = first ? 0.f : Ga[o];
+      const float gb = (first || !hasb) ? 0.f : Gb[o];
+      const float za = c.x * invP, zb = c.y * invP;
+      const float va = za + ga, vb = zb + gb;
       const float ua = soft_thr(va, it.thr), ub = soft_thr(vb, it.thr);
       const float ga2 = va - ua, gb2 = vb - ub;
+      if (resid) {
+        const float pa = (first || !Ua) ? 0.f : Ua[o];
+        const float pb = (first || !Ub) ? 0.f : Ub[o];
+        acc[0] += (za - ua) * (za - ua) + (hasb ? (zb - ub) * (zb - ub) : 0.f);
+        acc[1] += za * za + (hasb ? zb * zb : 0.f);
+        acc[2] += ua * ua + (hasb ? ub * ub : 0.f);
+        acc[3] += (ua - pa) * (ua - pa) + (hasb ? (ub - pb) * (ub - pb) : 0.f);
+        acc[4] += ga2 * ga2 + (hasb ? gb2 * gb2 : 0.f);
+      }
       Ga[o] = ga2;
       if (hasb) Gb[o] = gb2;
-      if (it.last) {
+      if (store_last || store_prev) {
         if (Ua) Ua[o] = ua;
         if (Ub) Ub[o] = ub;
-      } else {
-        lines[rrow * G::PITCH + q2] = make_float2(ua - ga2, hasb ? ub - gb2 : 0.f);
       }
+      if (!skip_fwd) lines[rrow * G::PITCH + q2] = make_float2(ua - ga2, hasb ? ub - gb2 : 0.f);
     }
-    if (it.last) return;
+    if (resid)
+      block_terms(acc, it.resid + (((size_t)slot * npairs + pair) * gridDim.x + blockIdx.x) * kResidTerms);
+    if (skip_fwd) return;
     __syncthreads();
     fft_lines<N, G::RB, false, kLargeThreads>(lines, G::PITCH, s_tw);
   }
@@ -214,7 +258,7 @@ __global__ void __launch_bounds__(kLargeThreads)
 // (r2c); MODE 2: the half spectrum of one real plane (sample spectrum).
 template <int N, int MODE>
 __global__ void __launch_bounds__(kLargeThreads)
-    large_col_out_kernel(CodeIter it, LargeIO io, const float2 *__restrict__ tw) {
+    large_col_out_kernel(CodeIter it, ImgBatch b, LargeIO io, const float2 *__restrict__ tw) {
   using G = LargeGeom<N>;
   extern __shared__ float2 lsm[];
   float2 *lines = lsm;
@@ -223,7 +267,8 @@ __global__ void __launch_bounds__(kLargeThreads)
   const int c0 = blockIdx.x * G::CB;
   const int pair = blockIdx.y, img = blockIdx.z;
   const int npairs = gridDim.y;
-  const float2 *T = io.T + ((size_t)img * npairs + pair) * G::P;
+  const int slot = (MODE == 0 || MODE == 2) ? b.slot[img] : img;
+  const float2 *T = io.T + ((size_t)slot * npairs + pair) * G::P;
   constexpr int NLOAD = MODE == 2 ? G::CB : G::NL;
   for (int e = threadIdx.x; e < N * NLOAD; e += kLargeThreads) {
     const int q1 = e / NLOAD, l = e % NLOAD;
@@ -233,7 +278,7 @@ __global__ void __launch_bounds__(kLargeThreads)
   __syncthreads();
   fft_lines<N, NLOAD, false, kLargeThreads>(lines, G::PITCH, s_tw);
   if (MODE == 2) {
-    float2 *out = io.spec_out + (size_t)img * G::F;
+    float2 *out = io.spec_out + (size_t)slot * G::F;
     for (int e = threadIdx.x; e < N * G::CB; e += kLargeThreads) {
       const int k1 = e / G::CB, l = e % G::CB, k2 = c0 + l;
       if (k2 <= N / 2) out[k1 * G::NH + k2] = lines[l * G::PITCH + k1];
@@ -245,8 +290,8 @@ __global__ void __launch_bounds__(kLargeThreads)
   const bool hasb = kb < K;
   float2 *Oa, *Ob;
   if (MODE == 0) {
-    Oa = it.What + ((size_t)img * K + ka) * G::F;
-    Ob = it.What + ((size_t)img * K + (hasb ? kb : ka)) * G::F;
+    Oa = it.What + ((size_t)slot * K + ka) * G::F;
+    Ob = it.What + ((size_t)slot * K + (hasb ? kb : ka)) * G::F;
   } else {
     Oa = io.spec_out + (size_t)ka * G::F;
     Ob = io.spec_out + (size_t)(hasb ? kb : ka) * G::F;
@@ -282,11 +327,11 @@ static cudaError_t large_n(int what, const CodeIter &it, const ImgBatch &b, cons
   switch (what) {
     case LARGE_COL_IN_ADMM:
       if ((e = prep(large_col_in_kernel<N, 0>, sm)) != cudaSuccess) return e;
-      large_col_in_kernel<N, 0><<<gc, kLargeThreads, sm, s>>>(it, io, tw);
+      large_col_in_kernel<N, 0><<<gc, kLargeThreads, sm, s>>>(it, b, io, tw);
       break;
     case LARGE_COL_IN_C2R:
       if ((e = prep(large_col_in_kernel<N, 1>, sm)) != cudaSuccess) return e;
-      large_col_in_kernel<N, 1><<<gc, kLargeThreads, sm, s>>>(it, io, tw);
+      large_col_in_kernel<N, 1><<<gc, kLargeThreads, sm, s>>>(it, b, io, tw);
       break;
     case LARGE_ROWS_ADMM:
       if ((e = prep(large_rows_kernel<N, 0>, sm)) != cudaSuccess) return e;
@@ -302,15 +347,15 @@ static cudaError_t large_n(int what, const CodeIter &it, const ImgBatch &b, cons
       break;
     case LARGE_COL_OUT_ADMM:
       if ((e = prep(large_col_out_kernel<N, 0>, sm)) != cudaSuccess) return e;
-      large_col_out_kernel<N, 0><<<gc, kLargeThreads, sm, s>>>(it, io, tw);
+      large_col_out_kernel<N, 0><<<gc, kLargeThreads, sm, s>>>(it, b, io, tw);
       break;
     case LARGE_COL_OUT_R2C:
       if ((e = prep(large_col_out_kernel<N, 1>, sm)) != cudaSuccess) return e;
-      large_col_out_kernel<N, 1><<<gc, kLargeThreads, sm, s>>>(it, io, tw);
+      large_col_out_kernel<N, 1><<<gc, kLargeThreads, sm, s>>>(it, b, io, tw);
       break;
     case LARGE_COL_OUT_IMAGE:
       if ((e = prep(large_col_out_kernel<N, 2>, sm)) != cudaSuccess) return e;
-      large_col_out_kernel<N, 2><<<gc, kLargeThreads, sm, s>>>(it, io, tw);
+      large_col_out_kernel<N, 2><<<gc, kLargeThreads, sm, s>>>(it, b, io, tw);
       break;
     default:
       return cudaErrorInvalidValue;

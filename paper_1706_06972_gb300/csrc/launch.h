@@ -7,32 +7,47 @@ namespace ocsc {
 
 constexpr int kMaxCallImages = 64;  // images per kernel-parameter batch
 
-// Per-call image table, passed by value as a kernel parameter.
+// Per-call image table, passed by value as a kernel parameter.  Image i of a
+// launch uses workspace slot slot[i] (its spectrum, W^, Gamma, r, Z~ and, for
+// N >= 256, its tiles); iter[i] is its ADMM iteration index when the launch
+// runs in serving mode.
 struct ImgBatch {
   const float *x[kMaxCallImages];  // device images, H x W row-major
   float *u[kMaxCallImages];        // device code outputs K x N x N (or null)
   int H[kMaxCallImages];
   int W[kMaxCallImages];
+  int slot[kMaxCallImages];
+  int iter[kMaxCallImages];
   int n;
 };
 
-// Code-ADMM iteration parameters.
+// Code-ADMM iteration parameters.  Workspace pointers are slot 0 of arrays
+// indexed by ImgBatch::slot.
 struct CodeIter {
   int K, F;
-  int first, last;     // first / last ADMM iteration of this call
+  int first, last;     // batch mode: first / last ADMM iteration of this call
   float thr;           // lambda / rho
   const float2 *Dh;    // [K][F] dictionary spectrum used for coding
-  const float2 *r;     // [n][F] per-frequency residual multipliers
-  float2 *What;        // [n][K][F] F(U - Gamma)
-  float *Gam;          // [n][K][N*N] scaled dual
-  float2 *Zp;          // [n][K][F] last Z~ (written on the last iteration)
+  float2 *r;           // [slots][F] per-frequency residual multipliers
+  float2 *What;        // [slots][K][F] F(U - Gamma)
+  float *Gam;          // [slots][K][N*N] scaled dual
+  float2 *Zp;          // [slots][K][F] last Z~ (written on the last iteration)
+  // Serving mode (serve = 1): every image has its own iteration index; at
+  // iterations t with (t + 1) % check == 0 the kernel stores Z~ and U and
+  // writes its share of the residual sums, at (t + 2) % check == 0 it stores U
+  // (the U_prev of the next check).  The forward transform always runs.
+  int serve, check;
+  float *resid;        // [slots][groups][kResidTerms] partial sums
 };
+constexpr int kResidTerms = 5;  // |Z-U|^2, |Z|^2, |U|^2, |U-U_prev|^2, |Gamma|^2
 
 cudaError_t launch_image_spectrum(int N, const ImgBatch &b, const float2 *tw, float2 *xh,
                                   cudaStream_t s);
-cudaError_t launch_code_resid(int N, int n, int K, float rho, int first, const float2 *Dh,
-                              const float *dn, const float2 *xh, const float2 *What, float2 *r,
-                              cudaStream_t s);
+cudaError_t launch_code_resid(int N, const ImgBatch &b, const CodeIter &it, float rho, const float *dn,
+                              const float2 *xh, cudaStream_t s);
+// Per-slot residual sums (double, fixed order) from `groups` partials per slot.
+cudaError_t launch_resid_reduce(const int *slots_dev, int n, int groups, const float *partials,
+                                double *out, cudaStream_t s);
 cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, const float2 *tw,
                               cudaStream_t s);
 cudaError_t launch_fft2(int N, int inverse, const float *in, float *out, int planes,

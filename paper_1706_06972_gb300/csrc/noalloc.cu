@@ -134,6 +134,8 @@ extern "C" ocsc_status ocsc_code_noalloc(const float *x, int H, int W, const flo
   b.u[0] = u;
   b.H[0] = H;
   b.W[0] = W;
+  b.slot[0] = 0;
+  b.iter[0] = 0;
   if (e == cudaSuccess) e = launch_image_spectrum(N, b, tw, xh, s);
   CodeIter it{};
   it.K = K;
@@ -147,7 +149,7 @@ extern "C" ocsc_status ocsc_code_noalloc(const float *x, int H, int W, const flo
   for (int t = 0; t < Jz && e == cudaSuccess; ++t) {
     it.first = t == 0;
     it.last = t == Jz - 1;
-    e = launch_code_resid(N, 1, K, (float)rho, it.first, Dh, dn, xh, it.What, r, s);
+    e = launch_code_resid(N, b, it, (float)rho, dn, xh, s);
     if (e == cudaSuccess) e = launch_code_plane(N, it, b, tw, s);
   }
   if (e != cudaSuccess) return say(err, err_len, OCSC_ECUDA, "launch: %s", cudaGetErrorString(e));

@@ -16,115 +16,14 @@
 #include <string>
 #include <vector>
 
-#include "../../include/ocsc.h"
-#include "common.cuh"
-#include "launch.h"
+#include "ctx.h"
 
 using namespace ocsc;
 
 namespace {
 
-struct SizeClass {
-  int N = 0, NH = 0, F = 0, P = 0;
-  float2 *tw = nullptr;     // [N] twiddles
-  // dictionary state in this class's frequency grid
-  float2 *Vh = nullptr;     // [K][F] F(pad V)
-  float2 *th = nullptr;     // [K][F] scaled dual of DictOCSC
-  float2 *Dcur = nullptr;   // [K][F] D~_{t,tau}
-  float2 *E = nullptr;      // [K][F] D~ + theta^
-  float2 *Y = nullptr;      // [K][M][NH] pruned inverse DFT along k1
-  float2 *Tm = nullptr;     // [K][M][NH] partial DFT of V
-  float *dn = nullptr;      // [F] |D~(p,:)|^2 of the coding dictionary
-  // history and factor
-  float2 *A = nullptr;      // [F][stride] packed FP32 history
-  float2 *b = nullptr;      // [K][F]
-  float2 *X = nullptr;      // [F][stride] X = L^-1 (FP32) of the FP64 factor
-  float2 *y = nullptr;      // [K][F] y = L^-1 (w b)
-  // pending samples
-  float2 *Zp = nullptr;     // [max_batch][K][F]
-  float2 *xhp = nullptr;    // [max_batch][F]
-  // code workspace
-  float2 *What = nullptr;   // [max_batch][K][F]
-  float *Gam = nullptr;     // [max_batch][K][P]
-  float2 *r = nullptr;      // [max_batch][F]
-  float2 *tiles = nullptr;  // [max_batch][ceil(K/2)][N][N] for N >= 256
-  float2 *obj_xh = nullptr; // [F]
-  long long n_seen = 0;
-  int pending = 0;
-};
-
-}  // namespace
-
-struct ocsc_ctx {
-  int K = 0, M = 0, T = 0;
-  double lam = 0, rho = 0;
-  ocsc_opts opts{};
-  cudaStream_t stream = nullptr;
-  float *V = nullptr;       // [K][M][M] the spatial filters
-  std::vector<SizeClass> cls;
-  double *obj_part = nullptr;
-  double *obj_out = nullptr;
-  int *err = nullptr;       // device error word
-  long long n_seen = 0;     // samples folded over all classes
-  uint64_t version = 0;
-  std::string msg;
-  std::vector<void *> allocs;
-  ocsc_counters counters{};
-  unsigned prof_mask = 0;
-  std::vector<cudaEvent_t> prof_ev[OCSC_K_COUNT];  // start/stop pairs
-  size_t prof_used[OCSC_K_COUNT] = {};
-};
-
-namespace {
-
 constexpr int kObjChunk = 64;
 thread_local std::string g_init_error = "no error";
-
-ocsc_status fail(ocsc_ctx *c, ocsc_status s, const char *fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  if (c) c->msg = buf;
-  return s;
-}
-
-ocsc_status cuda_fail(ocsc_ctx *c, cudaError_t e, const char *where) {
-  return fail(c, OCSC_ECUDA, "%s: %s", where, cudaGetErrorString(e));
-}
-
-template <typename T>
-ocsc_status dalloc(ocsc_ctx *c, T **p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    (void)cudaGetLastError();
-    *p = nullptr;
-    return fail(c, OCSC_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T),
-                cudaGetErrorString(e));
-  }
-  c->allocs.push_back(*p);
-  return OCSC_OK;
-}
-
-bool supported_fft(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
-bool large_fft(int n) { return n >= 256; }
-
-int padded_side(int side, int pad) {
-  const int need = side + pad;
-  for (int n : {64, 128, 256, 512})
-    if (n >= need) return n;
-  return -1;
-}
-
-int class_of(const ocsc_ctx *c, int H, int W) {
-  const int n = padded_side(H > W ? H : W, c->opts.pad);
-  for (size_t i = 0; i < c->cls.size(); ++i)
-    if (c->cls[i].N == n) return (int)i;
-  return -1;
-}
 
 // splitmix64 (Steele, Lea & Flood 2014) and Box-Muller for the Gaussian
 // initial filters of Algorithm 3.
@@ -137,33 +36,6 @@ uint64_t splitmix64(uint64_t x) {
 
 double uniform01(uint64_t seed, uint64_t i) {
   return ((double)(splitmix64(seed ^ splitmix64(i)) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
-}
-
-// Launch one kernel through `fn`, counting it and, when its class is being
-// profiled, bracketing it with events on the context's stream.
-template <typename Fn>
-cudaError_t timed(ocsc_ctx *c, int id, Fn &&fn) {
-  c->counters.kernel_launches++;
-  if (id >= OCSC_K_COUNT || !(c->prof_mask & (1u << id))) return fn();
-  auto &ev = c->prof_ev[id];
-  size_t &used = c->prof_used[id];
-  while (used + 2 > ev.size()) {
-    cudaEvent_t e;
-    cudaError_t err = cudaEventCreate(&e);
-    if (err != cudaSuccess) return err;
-    ev.push_back(e);
-  }
-  cudaError_t err = cudaEventRecord(ev[used], c->stream);
-  if (err != cudaSuccess) return err;
-  err = fn();
-  if (err != cudaSuccess) return err;
-  err = cudaEventRecord(ev[used + 1], c->stream);
-  used += 2;
-  return err;
-}
-
-const float2 *coding_spectrum(const ocsc_ctx *c, const SizeClass &s) {
-  return c->opts.return_feasible ? s.Vh : s.Dcur;
 }
 
 // V^_c = F_c(pad V) for one class, without touching its dual.
@@ -366,19 +238,22 @@ static ocsc_status code_class(ocsc_ctx *c, SizeClass &s, const std::vector<int> 
       bt.W[i] = W[j];
     }
     const int slot = s.pending + s0;
-    float2 *xh = s.xhp + (size_t)slot * s.F;
+    for (int i = 0; i < bt.n; ++i) {
+      bt.slot[i] = slot + i;
+      bt.iter[i] = 0;
+    }
     LargeIO io{};
-    io.T = s.tiles ? s.tiles + (size_t)slot * npairs * s.P : nullptr;
+    io.T = s.tiles;
     cudaError_t e;
     if (large_fft(s.N)) {
-      io.spec_out = xh;
+      io.spec_out = s.xhp;
       io.images = 1;
       CodeIter none{};
       e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_ROWS_FWD, none, bt, io, bt.n, 1, s.tw, c->stream); });
       if (e == cudaSuccess)
         e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_COL_OUT_IMAGE, none, bt, io, bt.n, 1, s.tw, c->stream); });
     } else {
-      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(s.N, bt, s.tw, xh, c->stream); });
+      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(s.N, bt, s.tw, s.xhp, c->stream); });
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "image spectrum");
     CodeIter it{};
@@ -386,17 +261,16 @@ static ocsc_status code_class(ocsc_ctx *c, SizeClass &s, const std::vector<int> 
     it.F = s.F;
     it.thr = (float)(c->lam / c->rho);
     it.Dh = coding_spectrum(c, s);
-    it.r = s.r + (size_t)slot * s.F;
-    it.What = s.What + (size_t)slot * c->K * s.F;
-    it.Gam = s.Gam + (size_t)slot * c->K * s.P;
-    it.Zp = s.Zp + (size_t)slot * c->K * s.F;
+    it.r = s.r;
+    it.What = s.What;
+    it.Gam = s.Gam;
+    it.Zp = s.Zp;
+    it.serve = 0;
+    it.check = 1;
     for (int t = 0; t < c->opts.Jz; ++t) {
       it.first = t == 0;
       it.last = t == c->opts.Jz - 1;
-      e = timed(c, OCSC_K_CODE_RESID, [&] {
-        return launch_code_resid(s.N, bt.n, c->K, (float)c->rho, it.first, it.Dh, s.dn, xh, it.What,
-                                 s.r + (size_t)slot * s.F, c->stream);
-      });
+      e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(s.N, bt, it, (float)c->rho, s.dn, s.xhp, c->stream); });
       if (e != cudaSuccess) return cuda_fail(c, e, "code_resid");
       if (large_fft(s.N)) {
         e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(s.N, LARGE_COL_IN_ADMM, it, bt, io, bt.n, npairs, s.tw, c->stream); });
