@@ -325,6 +325,79 @@ def mixed_leg(pkg, dev, stream, args):
             "ms_per_batch_by_kernel": {k: v[0] / nb for k, v in prof.items()}}
 
 
+def serving_leg(pkg, dev, stream, args):
+    """Continuous batching of single-image requests (side log-uniform in
+    [64, 502], FFT classes 128 / 256 / 512, K = 100, tolerance 1e-4 checked every
+    5 iterations, cap 500, dictionary update every 64 completions, 8 GiB
+    admission budget): saturated throughput, then Poisson arrivals at 25 / 50 /
+    90 % of it with p50 / p99 latency (arrival to completion, host clock)."""
+    import math
+    import random
+
+    import torch
+    from workloads import WORKLOADS
+
+    w = WORKLOADS["serving_k100"]
+    lr = pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_sizes=[128, 256, 512], pad=w.pad,
+                  Jz=50, Jd=w.Jd, max_batch=w.batch)
+    lr.set_dict(w.filters0(), normalize=True)
+    n_req = args.serve_requests
+    loads = (0.25, 0.5, 0.9)
+    total = n_req * (1 + len(loads))
+    xs = [torch.from_numpy(w.image(i)).to(dev) for i in range(total)]
+    outs = []
+    for x in xs:
+        n = lr.padded_size(x.shape[0], x.shape[1])
+        outs.append(torch.empty((w.K, n, n), device=dev))
+    srv = pkg.Server(lr, tol=1e-4, check_every=5, max_iters=w.Jz, update_every=w.batch, learn=1,
+                     mem_budget=8 << 30)
+
+    def run(ids, arrivals):
+        t0 = time.perf_counter()
+        nxt, done, lat, iters = 0, 0, [], []
+        while done < len(ids):
+            now = time.perf_counter() - t0
+            while nxt < len(ids) and arrivals[nxt] <= now:
+                srv.submit(ids[nxt], xs[ids[nxt]], out=outs[ids[nxt]])
+                nxt += 1
+            active, queued = srv.step() if (nxt > done) else (0, 0)
+            t_done = time.perf_counter() - t0
+            for d in srv.poll():
+                k = ids.index(d["id"])
+                lat.append(t_done - arrivals[k])
+                iters.append(d["iters"])
+                done += 1
+            if active == 0 and queued == 0 and nxt < len(ids):
+                wait = arrivals[nxt] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+        return time.perf_counter() - t0, lat, iters
+
+    torch.cuda.synchronize(dev)
+    ids = list(range(n_req))
+    secs, lat, iters = run(ids, [0.0] * n_req)
+    sat = n_req / secs
+    res = {"workload": "serving_k100", "requests_per_load": n_req, "saturated_rps": sat,
+           "saturated_mean_iters": sum(iters) / len(iters), "loads": []}
+    rng = random.Random(5)
+    for j, f in enumerate(loads):
+        lam = f * sat
+        arr, t = [], 0.0
+        for _ in range(n_req):
+            t += rng.expovariate(lam)
+            arr.append(t)
+        ids = list(range(n_req * (j + 1), n_req * (j + 2)))
+        secs, lat, iters = run(ids, arr)
+        lat.sort()
+        p = lambda q: 1e3 * lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)]
+        res["loads"].append({"offered": f, "offered_rps": lam, "achieved_rps": n_req / secs,
+                             "p50_ms": p(0.50), "p99_ms": p(0.99), "mean_iters": sum(iters) / len(iters)})
+    res["dict_version"] = lr.counters()["dict_updates"]
+    srv.close()
+    lr.close()
+    return res
+
+
 def ours_arm(args):
     import numpy as np
     import torch
@@ -429,6 +502,7 @@ def ours_arm(args):
     learner.close()
     batched = batched_leg(pkg, w, dev, stream, args) if args.batched_steps > 0 else None
     mixed = mixed_leg(pkg, dev, stream, args) if args.mixed_steps > 0 else None
+    serving = serving_leg(pkg, dev, stream, args) if args.serve_requests > 0 else None
 
     if rank != 0:
         return
@@ -459,6 +533,7 @@ def ours_arm(args):
         "kernel_breakdown": breakdown,
         "batched": batched,
         "mixed_sizes": mixed,
+        "serving": serving,
     }
     print(json.dumps(line))
 
@@ -479,6 +554,8 @@ def main():
     ap.add_argument("--batched-steps", type=int, default=4, help="timed batches of the batched leg (0: skip)")
     ap.add_argument("--mixed-steps", type=int, default=2,
                     help="timed batches of the uneven-size leg (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=96,
+                    help="requests per load level of the serving leg (0: skip)")
     ap.add_argument("--quality-images", type=int, default=256,
                     help="images for the plain-vs-batched held-out objective (0: skip)")
     ap.add_argument("--traffic", type=float, default=None,
