@@ -500,9 +500,10 @@ def ours_arm(args):
         e2e = {"value": world * E / te, "unit": UNIT, "h2d_bytes_per_step": int(xd.numel() * 4),
                "d2h_bytes_per_step": int(u_host.numel() * 4), "steps": E}
     learner.close()
-    batched = batched_leg(pkg, w, dev, stream, args) if args.batched_steps > 0 else None
-    mixed = mixed_leg(pkg, dev, stream, args) if args.mixed_steps > 0 else None
-    serving = serving_leg(pkg, dev, stream, args) if args.serve_requests > 0 else None
+    legs = set(args.legs.split(","))
+    batched = batched_leg(pkg, w, dev, stream, args) if args.batched_steps > 0 and "batched" in legs else None
+    mixed = mixed_leg(pkg, dev, stream, args) if args.mixed_steps > 0 and "mixed" in legs else None
+    serving = serving_leg(pkg, dev, stream, args) if args.serve_requests > 0 and "serving" in legs else None
 
     if rank != 0:
         return
@@ -538,9 +539,42 @@ def ours_arm(args):
     print(json.dumps(line))
 
 
+PROFILE_CASES = {
+    # name: (K, M, FFT size, images, image side, Jz)
+    "large512": (32, 11, 512, 4, 400, 10),
+    "large256": (32, 11, 256, 8, 200, 10),
+    "code128": (100, 11, 128, 16, 100, 10),
+}
+
+
+def profile_case(name: str) -> None:
+    """A small coding run for ncu captures of one kernel family (a few GB on
+    the device at most, working set still larger than L2)."""
+    import torch
+
+    import paper_1706_06972_gb300 as pkg
+    from paper_1706_06972_gb300 import build as _build
+    from workloads import make_image, raw_filters
+
+    _build.build()
+    K, M, N, n, side, Jz = PROFILE_CASES[name]
+    lr = pkg.OCSC(K, M, 1.0, 1.0, fft_size=N, pad=M - 1, Jz=Jz, Jd=2, max_batch=n)
+    lr.set_dict(raw_filters(K, M, 3), normalize=True)
+    xs = [torch.from_numpy(make_image(side, side, 100 + i)).cuda() for i in range(n)]
+    for rep in range(2):
+        lr.code(xs, want_codes=False)
+        lr.drop_pending()
+    lr.sync()
+    lr.close()
+    print(json.dumps({"profile_case": name, "K": K, "N": N, "images": n, "Jz": Jz, "ok": True}))
+
+
 def main():
     if len(sys.argv) > 1 and sys.argv[1] == "--oracle-child":
         _oracle_child(int(sys.argv[2]), int(sys.argv[3]))
+        return
+    if len(sys.argv) > 2 and sys.argv[1] == "--profile-case":
+        profile_case(sys.argv[2])
         return
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -550,6 +584,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--breakdown-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--legs", default="plain,batched,mixed,serving",
+                    help="comma list of legs to run (profiling runs pick one); the headline needs plain")
     ap.add_argument("--batch", type=int, default=64, help="mini-batch of the batched leg")
     ap.add_argument("--batched-steps", type=int, default=4, help="timed batches of the batched leg (0: skip)")
     ap.add_argument("--mixed-steps", type=int, default=2,
