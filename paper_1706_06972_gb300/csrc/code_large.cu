@@ -1,38 +1,62 @@
 // Code ADMM for FFT sizes whose packed N x N complex plane does not fit one
 // CTA's shared memory (N = 256, 512).  The iteration is the one of
-// code_admm.cu (Sec. II-C.1 problem (fcsc_code), ADMM of Sec. II-B) with the 2D
-// transforms split by dimension around a per-(sample, filter pair) complex tile
-// T[N][N] in global memory:
-//   col_in  : per block of CB half-spectrum columns k2 and their mirrors N-k2,
-//             the Z~-step z = w^ + conj(d) r for both filters of the pair,
-//             packed as z_a + i z_b over the full spectrum, inverse FFT along k1;
-//   rows    : per block of RB rows, inverse FFT along k2, the spatial step
-//             U = S(Z + Gamma), Gamma += Z - U, W = U - Gamma, forward FFT
-//             along the row;
-//   col_out : per column block, forward FFT along k1 and the split of the
-//             packed spectrum into the two half spectra W^_a, W^_b.
-// The same kernels with other modes give the sample spectrum and the batched
-// real 2D FFT building blocks.  Every block uses 64 KB of lines plus twiddles.
+// code_admm.cu (Sec. II-C.1 problem (fcsc_code), ADMM of Sec. II-B):
+//   W^ = F(U - Gamma),  z = w^ + conj(d) r,  r = (x~ - d^T w^) / (rho + |d|^2),
+//   U' = S(Z + Gamma),  Gamma' = Gamma + Z - U'.
+// With g = F^-1(conj(d) r) this is Z = U - Gamma + g, so V := Z + Gamma = U + g,
+// U' = S(V), Gamma' = V - U' and the next W = U' - Gamma' = 2U' - V: the spatial
+// state is U alone, and the spectral side only needs F(W) and produces g.
+// The 2D transforms are split by dimension around a per-(sample, filter pair)
+// complex tile M[k1][q2] in global memory.  Two kernels per iteration:
+//
+//   spectral (one CTA per row pair k1, -k1 of one sample, all filters):
+//     pass 1: M holds the column transform of the packed pair w_a + i w_b;
+//             its forward FFT along q2, split into the two half spectra,
+//             gives s(p) = sum_k D~_k(p) W^_k(p) and
+//             r(p) = (x~(p) - s(p)) / (rho + |d(p)|^2);
+//     pass 2: M <- row inverse of the packed conj(d_a) r + i conj(d_b) r.  On
+//             the iteration whose Z~ is kept, z = w^ + conj(d) r is also
+//             written to the pending spectra.
+//   spatial (one CTA per block of CB columns q2 of one pair of one sample):
+//             the inverse FFT along k1 gives g; V = U + g, U' = S(V),
+//             W = 2U' - V, and the forward FFT along q1 writes M for the next
+//             iteration.  U is stored tiled by column block, so a CTA reads
+//             and writes one contiguous chunk.
+//
+// Rows of spectral CTA i: (i, N - i) for 0 < i < N/2 and (0, N/2) for i = 0;
+// either way the Hermitian mirror (-k1, -k2) of every bin of a row lies in
+// one of the CTA's two rows.  The same kernels in other modes give the sample
+// spectrum and the batched real 2D FFT building blocks.
 #include "fft.cuh"
 #include "launch.h"
 
 namespace ocsc {
 
 constexpr int kLargeThreads = 256;
-template <int N> struct LargeGeom {
-  static constexpr int NH = N / 2 + 1, F = N * NH, P = N * N;
-  static constexpr int CB = 4096 / N;          // half-spectrum columns per column block
-  static constexpr int NL = 2 * CB;            // lines per column block (with mirrors)
-  static constexpr int RB = 8192 / N;          // rows per row block
-  static constexpr int NBLK = (NH + CB - 1) / CB;
-  static constexpr int PITCH = N + 1;
-};
 
 template <int N>
-size_t large_smem_bytes() {
-  using G = LargeGeom<N>;
-  const int lines = G::NL > G::RB ? G::NL : G::RB;
-  return (size_t)lines * G::PITCH * sizeof(float2) + (size_t)N * sizeof(float2);
+struct LargeGeom {
+  static constexpr int NH = N / 2 + 1, F = N * NH, P = N * N;
+  static constexpr int PITCH = N + 2;          // complex elements per shared-memory line
+  static constexpr int CB = 4096 / N;          // spatial CTA: columns per block
+  static constexpr int NCB = N / CB;
+  static constexpr int GP = 2048 / N;          // spectral CTA: filter pairs per stage
+  static constexpr int NL = 2 * GP;            // spectral CTA: lines per stage
+  static constexpr int EPT = (2 * NH + kLargeThreads - 1) / kLargeThreads;  // row bins per thread
+  static constexpr int SPT = N * CB / kLargeThreads;                        // spatial elements per thread
+};
+
+// Spectral CTA: two stage buffers of NL lines (pass 1 is double-buffered)
+// and the twiddles; spatial CTA: its N x CB block and the twiddles.
+template <int N>
+__host__ __device__ constexpr int spec_lines() { return 2 * LargeGeom<N>::NL; }
+template <int N>
+size_t spec_smem_bytes() {
+  return (size_t)spec_lines<N>() * LargeGeom<N>::PITCH * sizeof(float2) + (size_t)N * sizeof(float2);
+}
+template <int N>
+size_t spat_smem_bytes() {
+  return (size_t)N * LargeGeom<N>::CB * sizeof(float2) + (size_t)N * sizeof(float2);
 }
 
 __device__ __forceinline__ float soft_thr(float v, float t) { return v > t ? v - t : (v < -t ? v + t : 0.0f); }
@@ -58,254 +82,464 @@ __device__ __forceinline__ void block_terms(float (&v)[kResidTerms], float *out)
   }
 }
 
-// Column-block source / destination of line l: half-spectrum column c0 + l for
-// l < CB, mirror column N - (c0 + l - CB) otherwise; -1 when it does not exist.
+// ---------------------------------------------------------------------------
+// Spectral kernel
+// ---------------------------------------------------------------------------
+
+// Row r (0 or 1) of spectral CTA i.
 template <int N>
-__device__ __forceinline__ int line_column(int c0, int l) {
-  using G = LargeGeom<N>;
-  if (l < G::CB) {
-    const int k2 = c0 + l;
-    return k2 <= N / 2 ? k2 : -1;
-  }
-  const int k2 = c0 + l - G::CB;
-  return (k2 > 0 && k2 < N / 2) ? N - k2 : -1;
+__device__ __forceinline__ int spec_row(int i, int r) {
+  return r == 0 ? i : (i == 0 ? N / 2 : N - i);
 }
 
-// MODE 0: Z~-step of the ADMM; MODE 1: given half spectra Xa, Xb (c2r).
-template <int N, int MODE>
-__global__ void __launch_bounds__(kLargeThreads)
-    large_col_in_kernel(CodeIter it, ImgBatch b, LargeIO io, const float2 *__restrict__ tw) {
+// Lines 2g + r <- row r of tile j0 + g, for g < ng (16-byte copies).
+template <int N>
+__device__ __forceinline__ void load_rows(float2 *lines, const float2 *tiles, int j0, int ng, int row0,
+                                          int row1) {
   using G = LargeGeom<N>;
-  extern __shared__ float2 lsm[];
-  float2 *lines = lsm;
-  float2 *s_tw = lsm + (G::NL > G::RB ? G::NL : G::RB) * G::PITCH;
-  for (int i = threadIdx.x; i < N; i += kLargeThreads) s_tw[i] = tw[i];
-  const int c0 = blockIdx.x * G::CB;
-  const int pair = blockIdx.y, img = blockIdx.z;
-  const int ka = 2 * pair, kb = ka + 1;
-  const int npairs = gridDim.y;
-  const int K = MODE == 0 ? it.K : io.planes;
-  const bool hasb = kb < K;
-  const int slot = MODE == 0 ? b.slot[img] : img;
-  const int t = MODE == 0 ? b.iter[img] : 0;
-  const bool first = it.serve ? t == 0 : it.first != 0;
-  const bool store_last = it.serve ? (t + 1) % it.check == 0 : it.last != 0;
-  const float2 *Da = nullptr, *Db = nullptr, *rr = nullptr;
-  const float2 *Wa = nullptr, *Wb = nullptr;
-  float2 *Za = nullptr, *Zb = nullptr;
-  const float2 *Xa = nullptr, *Xb = nullptr;
-  if (MODE == 0) {
-    Da = it.Dh + (size_t)ka * G::F;
-    Db = it.Dh + (size_t)(hasb ? kb : ka) * G::F;
-    rr = it.r + (size_t)slot * G::F;
-    Wa = it.What + ((size_t)slot * K + ka) * G::F;
-    Wb = it.What + ((size_t)slot * K + (hasb ? kb : ka)) * G::F;
-    Za = it.Zp + ((size_t)slot * K + ka) * G::F;
-    Zb = it.Zp + ((size_t)slot * K + (hasb ? kb : ka)) * G::F;
-  } else {
-    Xa = io.spec_in + (size_t)ka * G::F;
-    Xb = io.spec_in + (size_t)(hasb ? kb : ka) * G::F;
-  }
-  for (int e = threadIdx.x; e < N * G::CB; e += kLargeThreads) {
-    const int k1 = e / G::CB, l = e % G::CB;
-    const int k2 = c0 + l;
-    if (k2 > N / 2) continue;
-    const int p = k1 * G::NH + k2;
-    float2 za, zb = make_float2(0.f, 0.f);
-    if (MODE == 0) {
-      const float2 rp = rr[p];
-      za = cconjmul(Da[p], rp);
-      if (hasb) zb = cconjmul(Db[p], rp);
-      if (!first) {
-        za = cadd(za, Wa[p]);
-        if (hasb) zb = cadd(zb, Wb[p]);
-      }
-      if (store_last) {
-        Za[p] = za;
-        if (hasb) Zb[p] = zb;
-      }
-    } else {
-      za = Xa[p];
-      if (hasb) zb = Xb[p];
+  constexpr int V = N / 2;  // float4 per row
+  constexpr int TRIPS = G::NL * V / kLargeThreads;
+#pragma unroll
+  for (int s = 0; s < TRIPS; ++s) {
+    const int e = threadIdx.x + s * kLargeThreads;
+    const int line = e / V, c = e % V;
+    if (line < 2 * ng) {
+      const int g = line >> 1, row = (line & 1) ? row1 : row0;
+      const float4 v = *reinterpret_cast<const float4 *>(tiles + (size_t)(j0 + g) * G::P + (size_t)row * N + 2 * c);
+      *reinterpret_cast<float4 *>(lines + line * G::PITCH + 2 * c) = v;
     }
-    lines[l * G::PITCH + k1] = make_float2(za.x - zb.y, za.y + zb.x);
-    if (k2 > 0 && k2 < N / 2)
-      lines[(G::CB + l) * G::PITCH + (N - k1) % N] = make_float2(za.x + zb.y, zb.x - za.y);
-  }
-  __syncthreads();
-  fft_lines<N, G::NL, true, kLargeThreads>(lines, G::PITCH, s_tw);
-  float2 *T = io.T + ((size_t)slot * npairs + pair) * G::P;
-  for (int e = threadIdx.x; e < N * G::NL; e += kLargeThreads) {
-    const int q1 = e / G::NL, l = e % G::NL;
-    const int col = line_column<N>(c0, l);
-    if (col >= 0) T[(size_t)q1 * N + col] = lines[l * G::PITCH + q1];
   }
 }
 
-// MODE 0: spatial ADMM step between the inverse and forward row transforms.
-// MODE 1: real planes (or zero-padded images) in, forward row transforms out.
-// MODE 2: inverse row transforms, real planes out (c2r).
+// load_rows with asynchronous copies (the caller commits and waits).
+template <int N>
+__device__ __forceinline__ void load_rows_async(float2 *lines, const float2 *tiles, int j0, int ng, int row0,
+                                                int row1) {
+  using G = LargeGeom<N>;
+  constexpr int V = N / 2;
+  constexpr int TRIPS = G::NL * V / kLargeThreads;
+#pragma unroll
+  for (int s = 0; s < TRIPS; ++s) {
+    const int e = threadIdx.x + s * kLargeThreads;
+    const int line = e / V, c = e % V;
+    if (line < 2 * ng) {
+      const int g = line >> 1, row = (line & 1) ? row1 : row0;
+      cp_async16(lines + line * G::PITCH + 2 * c, tiles + (size_t)(j0 + g) * G::P + (size_t)row * N + 2 * c);
+    }
+  }
+}
+
+// Rows of tiles j0 + g <- lines 2g + r.
+template <int N>
+__device__ __forceinline__ void store_rows(const float2 *lines, float2 *tiles, int j0, int ng, int row0, int row1) {
+  using G = LargeGeom<N>;
+  constexpr int V = N / 2;
+  constexpr int TRIPS = G::NL * V / kLargeThreads;
+#pragma unroll
+  for (int s = 0; s < TRIPS; ++s) {
+    const int e = threadIdx.x + s * kLargeThreads;
+    const int line = e / V, c = e % V;
+    if (line < 2 * ng) {
+      const int g = line >> 1, row = (line & 1) ? row1 : row0;
+      *reinterpret_cast<float4 *>(tiles + (size_t)(j0 + g) * G::P + (size_t)row * N + 2 * c) =
+          *reinterpret_cast<const float4 *>(lines + line * G::PITCH + 2 * c);
+    }
+  }
+}
+
+// Half spectra wa, wb of the two real planes packed as a + i b, from the
+// packed value P at a bin and Pm at its Hermitian mirror.
+__device__ __forceinline__ void split_pair(float2 P, float2 Pm, float2 &wa, float2 &wb) {
+  wa = make_float2(0.5f * (P.x + Pm.x), 0.5f * (P.y - Pm.y));
+  wb = make_float2(0.5f * (P.y + Pm.y), -0.5f * (P.x - Pm.x));
+}
+
+// Packed za + i zb at (line own, k2) and, for 0 < k2 < N/2, its Hermitian
+// partner conj(za) + i conj(zb) at (line mir, N - k2).
+template <int N>
+__device__ __forceinline__ void put_pair(float2 *lines, int own, int mir, int k2, float2 za, float2 zb) {
+  using G = LargeGeom<N>;
+  lines[own * G::PITCH + k2] = make_float2(za.x - zb.y, za.y + zb.x);
+  if (k2 > 0 && k2 < N / 2) lines[mir * G::PITCH + (N - k2)] = make_float2(za.x + zb.y, zb.x - za.y);
+}
+
+// MODE 0: ADMM partial sums D^T w^ and r (grid: images x N/2 x stages);
+// MODE 4: ADMM row inverse of conj(d) r, and the kept Z~ (grid: images x N/2 x stages);
+// MODE 1: sample spectra from the column-transformed images (grid: images x N/2);
+// MODE 2: half spectra of planes 2j, 2j+1 (r2c; grid: 1 x N/2 x pair stages);
+// MODE 3: packed row inverse of half spectra (c2r; grid: 1 x N/2 x pair stages).
 template <int N, int MODE>
-__global__ void __launch_bounds__(kLargeThreads)
-    large_rows_kernel(CodeIter it, ImgBatch b, LargeIO io, const float2 *__restrict__ tw) {
+__global__ void __launch_bounds__(kLargeThreads, 3)
+    large_spec_kernel(CodeIter it, ImgBatch b, LargeIO io, const float2 *__restrict__ tw) {
   using G = LargeGeom<N>;
   extern __shared__ float2 lsm[];
   float2 *lines = lsm;
-  float2 *s_tw = lsm + (G::NL > G::RB ? G::NL : G::RB) * G::PITCH;
+  float2 *s_tw = lsm + spec_lines<N>() * G::PITCH;
   for (int i = threadIdx.x; i < N; i += kLargeThreads) s_tw[i] = tw[i];
-  const int q0 = blockIdx.x * G::RB;
-  const int pair = blockIdx.y, img = blockIdx.z;
-  const int npairs = gridDim.y;
-  const int slot = (MODE == 0 || io.images) ? b.slot[img] : img;
-  float2 *T = io.T + ((size_t)slot * npairs + pair) * G::P;
+  const int i = blockIdx.y;
+  const int row0 = spec_row<N>(i, 0), row1 = spec_row<N>(i, 1);
+  const bool selfm = i == 0;  // rows 0 and N/2 are their own mirrors
+
   if (MODE == 1) {
-    if (io.images) {  // sample spectrum: image img, zero-padded, as the real part
-      const float *x = b.x[img];
-      const int H = b.H[img], W = b.W[img];
-      for (int e = threadIdx.x; e < G::RB * N; e += kLargeThreads) {
-        const int rrow = e / N, q2 = e % N, q1 = q0 + rrow;
-        const float v = (q1 < H && q2 < W) ? x[(size_t)q1 * W + q2] : 0.f;
-        lines[rrow * G::PITCH + q2] = make_float2(v, 0.f);
-      }
-    } else {          // planes 2 pair and 2 pair + 1 as real and imaginary parts
-      const int pa = 2 * pair, pb = pa + 1;
-      const bool hasb = pb < io.planes;
-      const float *xa = io.real_in + (size_t)pa * G::P;
-      const float *xb = io.real_in + (size_t)pb * G::P;
-      for (int e = threadIdx.x; e < G::RB * N; e += kLargeThreads) {
-        const int rrow = e / N, q2 = e % N;
-        const size_t o = (size_t)(q0 + rrow) * N + q2;
-        lines[rrow * G::PITCH + q2] = make_float2(xa[o], hasb ? xb[o] : 0.f);
-      }
-    }
+    const int slot = b.slot[blockIdx.x];
+    const float2 *tiles = io.T + (size_t)slot * io.tile_pairs * G::P;
+    load_rows<N>(lines, tiles, 0, 1, row0, row1);
     __syncthreads();
-    fft_lines<N, G::RB, false, kLargeThreads>(lines, G::PITCH, s_tw);
-  } else {
-    for (int e = threadIdx.x; e < G::RB * N; e += kLargeThreads) {
-      const int rrow = e / N, q2 = e % N;
-      lines[rrow * G::PITCH + q2] = T[(size_t)(q0 + rrow) * N + q2];
-    }
-    __syncthreads();
-    fft_lines<N, G::RB, true, kLargeThreads>(lines, G::PITCH, s_tw);
-    const float invP = 1.0f / (float)G::P;
-    if (MODE == 2) {
-      const int pa = 2 * pair, pb = pa + 1;
-      const bool hasb = pb < io.planes;
-      float *xa = io.real_out + (size_t)pa * G::P;
-      float *xb = io.real_out + (size_t)pb * G::P;
-      for (int e = threadIdx.x; e < G::RB * N; e += kLargeThreads) {
-        const int rrow = e / N, q2 = e % N;
-        const size_t o = (size_t)(q0 + rrow) * N + q2;
-        const float2 c = lines[rrow * G::PITCH + q2];
-        xa[o] = c.x * invP;
-        if (hasb) xb[o] = c.y * invP;
-      }
-      return;
-    }
-    const int K = it.K, ka = 2 * pair, kb = ka + 1;
-    const bool hasb = kb < K;
-    const int t = b.iter[img];
-    const bool first = it.serve ? t == 0 : it.first != 0;
-    const bool store_last = it.serve ? (t + 1) % it.check == 0 : it.last != 0;
-    const bool store_prev = it.serve && (t + 2) % it.check == 0;
-    const bool skip_fwd = !it.serve && it.last;
-    const bool resid = it.serve && store_last;
-    float *Ga = it.Gam + ((size_t)slot * K + ka) * G::P;
-    float *Gb = it.Gam + ((size_t)slot * K + (hasb ? kb : ka)) * G::P;
-    float *Ua = b.u[img] ? b.u[img] + (size_t)ka * G::P : nullptr;
-    float *Ub = (b.u[img] && hasb) ? b.u[img] + (size_t)kb * G::P : nullptr;
-    float acc[kResidTerms] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int e = threadIdx.x; e < G::RB * N; e += kLargeThreads) {
-      const int rrow = e / N, q2 = e % N;
-      const size_t o = (size_t)(q0 + rrow) * N + q2;
-      const float2 c = lines[rrow * G::PITCH + q2];
-      const float ga = first ? 0.f : Ga[o];
-      const float gb = (first || !hasb) ? 0.f : Gb[o];
-      const float za = c.x * invP, zb = c.y * invP;
-      const float va = za + ga, vb = zb + gb;
-      const float ua = soft_thr(va, it.thr), ub = soft_thr(vb, it.thr);
-      const float ga2 = va - ua, gb2 = vb - ub;
-      if (resid) {
-        const float pa = (first || !Ua) ? 0.f : Ua[o];
-        const float pb = (first || !Ub) ? 0.f : Ub[o];
-        acc[0] += (za - ua) * (za - ua) + (hasb ? (zb - ub) * (zb - ub) : 0.f);
-        acc[1] += za * za + (hasb ? zb * zb : 0.f);
-        acc[2] += ua * ua + (hasb ? ub * ub : 0.f);
-        acc[3] += (ua - pa) * (ua - pa) + (hasb ? (ub - pb) * (ub - pb) : 0.f);
-        acc[4] += ga2 * ga2 + (hasb ? gb2 * gb2 : 0.f);
-      }
-      Ga[o] = ga2;
-      if (hasb) Gb[o] = gb2;
-      if (store_last || store_prev) {
-        if (Ua) Ua[o] = ua;
-        if (Ub) Ub[o] = ub;
-      }
-      if (!skip_fwd) lines[rrow * G::PITCH + q2] = make_float2(ua - ga2, hasb ? ub - gb2 : 0.f);
-    }
-    if (resid)
-      block_terms(acc, it.resid + (((size_t)slot * npairs + pair) * gridDim.x + blockIdx.x) * kResidTerms);
-    if (skip_fwd) return;
-    __syncthreads();
-    fft_lines<N, G::RB, false, kLargeThreads>(lines, G::PITCH, s_tw);
-  }
-  for (int e = threadIdx.x; e < G::RB * N; e += kLargeThreads) {
-    const int rrow = e / N, q2 = e % N;
-    T[(size_t)(q0 + rrow) * N + q2] = lines[rrow * G::PITCH + q2];
-  }
-}
-
-// MODE 0: W^_a, W^_b of the ADMM; MODE 1: half spectra of two real planes
-// (r2c); MODE 2: the half spectrum of one real plane (sample spectrum).
-template <int N, int MODE>
-__global__ void __launch_bounds__(kLargeThreads)
-    large_col_out_kernel(CodeIter it, ImgBatch b, LargeIO io, const float2 *__restrict__ tw) {
-  using G = LargeGeom<N>;
-  extern __shared__ float2 lsm[];
-  float2 *lines = lsm;
-  float2 *s_tw = lsm + (G::NL > G::RB ? G::NL : G::RB) * G::PITCH;
-  for (int i = threadIdx.x; i < N; i += kLargeThreads) s_tw[i] = tw[i];
-  const int c0 = blockIdx.x * G::CB;
-  const int pair = blockIdx.y, img = blockIdx.z;
-  const int npairs = gridDim.y;
-  const int slot = (MODE == 0 || MODE == 2) ? b.slot[img] : img;
-  const float2 *T = io.T + ((size_t)slot * npairs + pair) * G::P;
-  constexpr int NLOAD = MODE == 2 ? G::CB : G::NL;
-  for (int e = threadIdx.x; e < N * NLOAD; e += kLargeThreads) {
-    const int q1 = e / NLOAD, l = e % NLOAD;
-    const int col = line_column<N>(c0, l);
-    lines[l * G::PITCH + q1] = col >= 0 ? T[(size_t)q1 * N + col] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  fft_lines<N, NLOAD, false, kLargeThreads>(lines, G::PITCH, s_tw);
-  if (MODE == 2) {
+    fft_lines<N, G::NL, false, kLargeThreads>(lines, G::PITCH, 1, s_tw);
     float2 *out = io.spec_out + (size_t)slot * G::F;
-    for (int e = threadIdx.x; e < N * G::CB; e += kLargeThreads) {
-      const int k1 = e / G::CB, l = e % G::CB, k2 = c0 + l;
-      if (k2 <= N / 2) out[k1 * G::NH + k2] = lines[l * G::PITCH + k1];
+    for (int e = threadIdx.x; e < 2 * G::NH; e += kLargeThreads) {
+      const int r = e / G::NH, k2 = e % G::NH;
+      out[(size_t)(r ? row1 : row0) * G::NH + k2] = lines[r * G::PITCH + k2];
     }
     return;
   }
-  const int ka = 2 * pair, kb = ka + 1;
-  const int K = MODE == 0 ? it.K : io.planes;
-  const bool hasb = kb < K;
-  float2 *Oa, *Ob;
+
+  if (MODE == 2 || MODE == 3) {
+    const int npairs = (io.planes + 1) / 2;
+    const int j0 = blockIdx.z * G::GP;
+    const int ng = npairs - j0 < G::GP ? npairs - j0 : G::GP;
+    if (MODE == 2) {
+      load_rows<N>(lines, io.T, j0, ng, row0, row1);
+      __syncthreads();
+      fft_lines<N, G::NL, false, kLargeThreads>(lines, G::PITCH, 1, s_tw);
+      for (int e = threadIdx.x; e < 2 * G::NH; e += kLargeThreads) {
+        const int r = e / G::NH, k2 = e % G::NH, mr = selfm ? r : 1 - r;
+        const size_t p = (size_t)(r ? row1 : row0) * G::NH + k2;
+        for (int g = 0; g < ng; ++g) {
+          const int a = 2 * (j0 + g);
+          float2 wa, wb;
+          split_pair(lines[(2 * g + r) * G::PITCH + k2], lines[(2 * g + mr) * G::PITCH + (N - k2) % N], wa, wb);
+          io.spec_out[(size_t)a * G::F + p] = wa;
+          if (a + 1 < io.planes) io.spec_out[(size_t)(a + 1) * G::F + p] = wb;
+        }
+      }
+    } else {
+      for (int e = threadIdx.x; e < 2 * G::NH; e += kLargeThreads) {
+        const int r = e / G::NH, k2 = e % G::NH, mr = selfm ? r : 1 - r;
+        const size_t p = (size_t)(r ? row1 : row0) * G::NH + k2;
+        for (int g = 0; g < ng; ++g) {
+          const int a = 2 * (j0 + g);
+          const float2 za = io.spec_in[(size_t)a * G::F + p];
+          const float2 zb = a + 1 < io.planes ? io.spec_in[(size_t)(a + 1) * G::F + p] : make_float2(0.f, 0.f);
+          put_pair<N>(lines, 2 * g + r, 2 * g + mr, k2, za, zb);
+        }
+      }
+      __syncthreads();
+      fft_lines<N, G::NL, true, kLargeThreads>(lines, G::PITCH, 1, s_tw);
+      store_rows<N>(lines, io.T, j0, ng, row0, row1);
+    }
+    return;
+  }
+
+  // MODE 0 (s = D^T w^ partial sums and r) and MODE 4 (row inverse of
+  // conj(d) r): one CTA per (sample, row pair, stage of GP filter pairs).
+  const int img = blockIdx.x, st = blockIdx.z, S = gridDim.z;
+  const int slot = b.slot[img], t = b.iter[img];
+  const bool first = it.serve ? t == 0 : it.first != 0;
+  const bool keep_z = it.serve ? (t + 1) % it.check == 0 : it.last != 0;
+  const int K = it.K, npairs = (K + 1) / 2;
+  const int j0 = st * G::GP, ng = npairs - j0 < G::GP ? npairs - j0 : G::GP;
+  float2 *tiles = io.T + (size_t)slot * io.tile_pairs * G::P;
+  // D rows of the stage, line ((g * 2 + f) * 2 + r) = row r of filter 2(j0 + g) + f.
+  float2 *dsm = lines + G::NL * G::PITCH;
+  constexpr int DL = 4 * G::NH;  // complex values per filter pair in dsm
+
+  const bool need_w = MODE == 0 ? !first : (keep_z && !first);
+  if (need_w) load_rows_async<N>(lines, tiles, j0, ng, row0, row1);
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int line = warp; line < 4 * ng; line += kLargeThreads / 32) {
+      const int a = 2 * j0 + (line >> 1);
+      if (a >= K) continue;
+      const float2 *src = it.Dh + (size_t)a * G::F + (size_t)((line & 1) ? row1 : row0) * G::NH;
+      float2 *dst = dsm + line * G::NH;
+      for (int k2 = lane; k2 < G::NH; k2 += 32) cp_async8(dst + k2, src + k2);
+    }
+  }
+  cp_async_wait_all();
+
+  // Per bin of this thread: global index pe, shared offsets of the bin (lo)
+  // and of its mirror (lm) in the lines of pair 0, and of the bin in dsm (ld).
+  int pe[G::EPT], lo[G::EPT], lm[G::EPT], ld[G::EPT], kk[G::EPT];
+#pragma unroll
+  for (int q = 0; q < G::EPT; ++q) {
+    const int e = threadIdx.x + q * kLargeThreads;
+    const bool ok = e < 2 * G::NH;
+    const int r = ok ? (e >= G::NH) : 0, k2 = ok ? e - r * G::NH : 0;
+    const int mr = selfm ? r : 1 - r;
+    kk[q] = k2;
+    lo[q] = r * G::PITCH + k2;
+    lm[q] = mr * G::PITCH + ((N - k2) & (N - 1));
+    ld[q] = r * G::NH + k2;
+    pe[q] = ok ? (r ? row1 : row0) * G::NH + k2 : -1;
+  }
+  __syncthreads();
+  if (need_w) fft_lines<N, G::NL, false, kLargeThreads>(lines, G::PITCH, 1, s_tw);
+
   if (MODE == 0) {
-    Oa = it.What + ((size_t)slot * K + ka) * G::F;
-    Ob = it.What + ((size_t)slot * K + (hasb ? kb : ka)) * G::F;
-  } else {
-    Oa = io.spec_out + (size_t)ka * G::F;
-    Ob = io.spec_out + (size_t)(hasb ? kb : ka) * G::F;
+    // Partial sums of this stage, then the last CTA of the row pair adds the
+    // S partials in stage order and forms r (no CTA waits for another).
+    float2 *part = it.part + (size_t)slot * S * G::F;
+#pragma unroll
+    for (int q = 0; q < G::EPT; ++q) {
+      if (pe[q] < 0) continue;
+      float2 acc = make_float2(0.f, 0.f);
+      if (!first) {
+        for (int g = 0; g < ng; ++g) {
+          const bool hasb = 2 * (j0 + g) + 1 < K;
+          float2 wa, wb;
+          split_pair(lines[2 * g * G::PITCH + lo[q]], lines[2 * g * G::PITCH + lm[q]], wa, wb);
+          acc = cadd(acc, cmul(dsm[g * DL + ld[q]], wa));
+          if (hasb) acc = cadd(acc, cmul(dsm[g * DL + 2 * G::NH + ld[q]], wb));
+        }
+      }
+      part[(size_t)st * G::F + pe[q]] = acc;
+    }
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int *cnt = it.cnt + (size_t)slot * (N / 2) + i;
+      const int old = atomicAdd(cnt, 1);
+      s_last = old == S - 1;
+      if (s_last) *cnt = 0;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < G::EPT; ++q) {
+      if (pe[q] < 0) continue;
+      float2 sum = make_float2(0.f, 0.f);
+      for (int u = 0; u < S; ++u) sum = cadd(sum, __ldcg(part + (size_t)u * G::F + pe[q]));
+      const float2 x = it.xh[(size_t)slot * G::F + pe[q]];
+      const float inv = 1.0f / (it.rho + it.dn[pe[q]]);
+      it.r[(size_t)slot * G::F + pe[q]] = make_float2((x.x - sum.x) * inv, (x.y - sum.y) * inv);
+    }
+    return;
   }
-  for (int e = threadIdx.x; e < N * G::CB; e += kLargeThreads) {
-    const int k1 = e / G::CB, l = e % G::CB, k2 = c0 + l;
-    if (k2 > N / 2) continue;
-    const int m1 = (N - k1) % N;
-    const float2 c = lines[l * G::PITCH + k1];
-    const float2 cm = (k2 > 0 && k2 < N / 2) ? lines[(G::CB + l) * G::PITCH + m1] : lines[l * G::PITCH + m1];
-    const int p = k1 * G::NH + k2;
-    Oa[p] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
-    if (hasb) Ob[p] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+
+  // MODE 4: r (from MODE 0, or x~ / (rho + |d|^2) on the first iteration).
+  float2 rr[G::EPT];
+#pragma unroll
+  for (int q = 0; q < G::EPT; ++q) {
+    rr[q] = make_float2(0.f, 0.f);
+    if (pe[q] < 0) continue;
+    if (first) {
+      const float2 x = it.xh[(size_t)slot * G::F + pe[q]];
+      const float inv = 1.0f / (it.rho + it.dn[pe[q]]);
+      rr[q] = make_float2(x.x * inv, x.y * inv);
+    } else {
+      rr[q] = it.r[(size_t)slot * G::F + pe[q]];
+    }
   }
+  if (keep_z) {
+#pragma unroll
+    for (int q = 0; q < G::EPT; ++q) {
+      if (pe[q] < 0) continue;
+      for (int g = 0; g < ng; ++g) {
+        const int a = 2 * (j0 + g);
+        float2 wa = make_float2(0.f, 0.f), wb = wa;
+        if (!first) split_pair(lines[2 * g * G::PITCH + lo[q]], lines[2 * g * G::PITCH + lm[q]], wa, wb);
+        it.Zp[((size_t)slot * K + a) * G::F + pe[q]] = cadd(wa, cconjmul(dsm[g * DL + ld[q]], rr[q]));
+        if (a + 1 < K)
+          it.Zp[((size_t)slot * K + a + 1) * G::F + pe[q]] =
+              cadd(wb, cconjmul(dsm[g * DL + 2 * G::NH + ld[q]], rr[q]));
+      }
+    }
+    // the bins k2 = 0, N/2 of one row are read above as mirrors by the
+    // thread owning the other row
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < G::EPT; ++q) {
+    if (pe[q] < 0) continue;
+    const bool mirrored = kk[q] > 0 && kk[q] < N / 2;
+    for (int g = 0; g < ng; ++g) {
+      const bool hasb = 2 * (j0 + g) + 1 < K;
+      const float2 ca = cconjmul(dsm[g * DL + ld[q]], rr[q]);
+      const float2 cb = hasb ? cconjmul(dsm[g * DL + 2 * G::NH + ld[q]], rr[q]) : make_float2(0.f, 0.f);
+      lines[2 * g * G::PITCH + lo[q]] = make_float2(ca.x - cb.y, ca.y + cb.x);
+      if (mirrored) lines[2 * g * G::PITCH + lm[q]] = make_float2(ca.x + cb.y, cb.x - ca.y);
+    }
+  }
+  __syncthreads();
+  fft_lines<N, G::NL, true, kLargeThreads>(lines, G::PITCH, 1, s_tw);
+  store_rows<N>(lines, tiles, j0, ng, row0, row1);
+}
+
+// ---------------------------------------------------------------------------
+// Spatial kernel
+// ---------------------------------------------------------------------------
+
+// The spatial CTA keeps its block as [q1][l] (CB contiguous complex values
+// per row of the tile), so that a tile row segment is one 16-byte-aligned run
+// in both memories; its column transforms see element q1 of line l at
+// q1 * CB + l.
+// Block <- columns c0 .. c0 + CB - 1 of a tile (asynchronous 16-byte copies;
+// the caller commits and waits).
+template <int N>
+__device__ __forceinline__ void load_cols_async(float2 *blk, const float2 *tile, int c0) {
+  using G = LargeGeom<N>;
+  constexpr int V = G::CB / 2;
+  constexpr int TRIPS = N * V / kLargeThreads;
+#pragma unroll
+  for (int s = 0; s < TRIPS; ++s) {
+    const int e = threadIdx.x + s * kLargeThreads;
+    const int k1 = e / V, c = e % V;
+    cp_async16(blk + k1 * G::CB + 2 * c, tile + (size_t)k1 * N + c0 + 2 * c);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void store_cols(const float2 *blk, float2 *tile, int c0) {
+  using G = LargeGeom<N>;
+  constexpr int V = G::CB / 2;
+  constexpr int TRIPS = N * V / kLargeThreads;
+#pragma unroll
+  for (int s = 0; s < TRIPS; ++s) {
+    const int e = threadIdx.x + s * kLargeThreads;
+    const int k1 = e / V, c = e % V;
+    *reinterpret_cast<float4 *>(tile + (size_t)k1 * N + c0 + 2 * c) =
+        *reinterpret_cast<const float4 *>(blk + k1 * G::CB + 2 * c);
+  }
+}
+
+// MODE 0: spatial ADMM step between the inverse and forward column transforms
+//         (grid: NCB x pairs x images);
+// MODE 1: zero-padded images in, forward column transforms out (grid: NCB x 1 x images);
+// MODE 2: real planes 2j, 2j+1 in, forward column transforms out (grid: NCB x pairs);
+// MODE 3: inverse column transforms, real planes out (c2r; grid: NCB x pairs).
+template <int N, int MODE>
+__global__ void __launch_bounds__(kLargeThreads, 4)
+    large_spat_kernel(CodeIter it, ImgBatch b, LargeIO io, const float2 *__restrict__ tw) {
+  using G = LargeGeom<N>;
+  extern __shared__ float2 lsm[];
+  float2 *blk = lsm;  // [N][CB]
+  float2 *s_tw = lsm + N * G::CB;
+  for (int i = threadIdx.x; i < N; i += kLargeThreads) s_tw[i] = tw[i];
+  const int cb = blockIdx.x, c0 = cb * G::CB;
+  const int pair = blockIdx.y, img = blockIdx.z;
+
+  if (MODE == 1) {
+    const int slot = b.slot[img];
+    float2 *tile = io.T + (size_t)slot * io.tile_pairs * G::P;
+    const float *x = b.x[img];
+    const int H = b.H[img], W = b.W[img];
+#pragma unroll 4
+    for (int s = 0; s < G::SPT; ++s) {
+      const int e = threadIdx.x + s * kLargeThreads;
+      const int q1 = e / G::CB, q2 = c0 + e % G::CB;
+      blk[e] = make_float2((q1 < H && q2 < W) ? x[(size_t)q1 * W + q2] : 0.f, 0.f);
+    }
+    __syncthreads();
+    fft_lines<N, G::CB, false, kLargeThreads>(blk, 1, G::CB, s_tw);
+    store_cols<N>(blk, tile, c0);
+    return;
+  }
+  if (MODE == 2) {
+    const int pa = 2 * pair, pb = pa + 1;
+    const bool hasb = pb < io.planes;
+    const float *xa = io.real_in + (size_t)pa * G::P;
+    const float *xb = io.real_in + (size_t)pb * G::P;
+#pragma unroll 4
+    for (int s = 0; s < G::SPT; ++s) {
+      const int e = threadIdx.x + s * kLargeThreads;
+      const size_t o = (size_t)(e / G::CB) * N + c0 + e % G::CB;
+      blk[e] = make_float2(xa[o], hasb ? xb[o] : 0.f);
+    }
+    __syncthreads();
+    fft_lines<N, G::CB, false, kLargeThreads>(blk, 1, G::CB, s_tw);
+    store_cols<N>(blk, io.T + (size_t)pair * G::P, c0);
+    return;
+  }
+  if (MODE == 3) {
+    load_cols_async<N>(blk, io.T + (size_t)pair * G::P, c0);
+    cp_async_wait_all();
+    __syncthreads();
+    fft_lines<N, G::CB, true, kLargeThreads>(blk, 1, G::CB, s_tw);
+    const int pa = 2 * pair, pb = pa + 1;
+    const bool hasb = pb < io.planes;
+    float *xa = io.real_out + (size_t)pa * G::P;
+    float *xb = io.real_out + (size_t)pb * G::P;
+    const float invP = 1.0f / (float)G::P;
+#pragma unroll 4
+    for (int s = 0; s < G::SPT; ++s) {
+      const int e = threadIdx.x + s * kLargeThreads;
+      const size_t o = (size_t)(e / G::CB) * N + c0 + e % G::CB;
+      const float2 c = blk[e];
+      xa[o] = c.x * invP;
+      if (hasb) xb[o] = c.y * invP;
+    }
+    return;
+  }
+
+  // MODE 0
+  const int K = it.K, npairs = gridDim.y, ka = 2 * pair, kb = ka + 1;
+  const bool hasb = kb < K;
+  const int slot = b.slot[img], t = b.iter[img];
+  const bool first = it.serve ? t == 0 : it.first != 0;
+  const bool store_last = it.serve ? (t + 1) % it.check == 0 : it.last != 0;
+  const bool store_prev = it.serve && (t + 2) % it.check == 0;
+  const bool skip_fwd = !it.serve && it.last;
+  const bool resid = it.serve && store_last;
+  float2 *tile = io.T + ((size_t)slot * io.tile_pairs + pair) * G::P;
+  load_cols_async<N>(blk, tile, c0);
+  cp_async_wait_all();
+  // U of this column block, [q1][l] like blk, contiguous.
+  float *Sa = it.Gam + ((size_t)slot * K + ka) * G::P + (size_t)cb * N * G::CB;
+  float *Sb = it.Gam + ((size_t)slot * K + (hasb ? kb : ka)) * G::P + (size_t)cb * N * G::CB;
+  __syncthreads();
+  fft_lines<N, G::CB, true, kLargeThreads>(blk, 1, G::CB, s_tw);
+  // The code output doubles as the store of Gamma from the iteration before
+  // a residual check (serving), where Z = V - Gamma_prev is needed.
+  float *Ua = b.u[img] ? b.u[img] + (size_t)ka * G::P : nullptr;
+  float *Ub = (b.u[img] && hasb) ? b.u[img] + (size_t)kb * G::P : nullptr;
+  const float invP = 1.0f / (float)G::P;
+  float acc[kResidTerms] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  constexpr int CH = 4;  // state loads in flight per thread
+#pragma unroll 1
+  for (int s0 = 0; s0 < G::SPT; s0 += CH) {
+    float pa[CH], pb[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int e = threadIdx.x + (s0 + u) * kLargeThreads;
+      pa[u] = first ? 0.f : Sa[e];
+      pb[u] = (first || !hasb) ? 0.f : Sb[e];
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const int e = threadIdx.x + (s0 + u) * kLargeThreads;
+      const size_t o = (size_t)(e / G::CB) * N + c0 + e % G::CB;
+      const float2 c = blk[e];
+      const float va = pa[u] + c.x * invP, vb = pb[u] + c.y * invP;
+      const float ua = soft_thr(va, it.thr), ub = soft_thr(vb, it.thr);
+      const float ga = va - ua, gb = vb - ub;
+      if (resid) {
+        const float qa = (first || !Ua) ? 0.f : Ua[o];  // Gamma of the previous iteration
+        const float qb = (first || !Ub) ? 0.f : Ub[o];
+        const float za = va - qa, zb = vb - qb;
+        acc[0] += (za - ua) * (za - ua) + (hasb ? (zb - ub) * (zb - ub) : 0.f);
+        acc[1] += za * za + (hasb ? zb * zb : 0.f);
+        acc[2] += ua * ua + (hasb ? ub * ub : 0.f);
+        acc[3] += (ua - pa[u]) * (ua - pa[u]) + (hasb ? (ub - pb[u]) * (ub - pb[u]) : 0.f);
+        acc[4] += ga * ga + (hasb ? gb * gb : 0.f);
+      }
+      Sa[e] = ua;
+      if (hasb) Sb[e] = ub;
+      if (store_last || store_prev) {
+        if (Ua) Ua[o] = store_last ? ua : ga;
+        if (Ub) Ub[o] = store_last ? ub : gb;
+      }
+      blk[e] = make_float2(2.f * ua - va, hasb ? 2.f * ub - vb : 0.f);
+    }
+  }
+  if (resid)
+    block_terms(acc, it.resid + (((size_t)slot * npairs + pair) * G::NCB + cb) * kResidTerms);
+  if (skip_fwd) return;
+  __syncthreads();
+  fft_lines<N, G::CB, false, kLargeThreads>(blk, 1, G::CB, s_tw);
+  store_cols<N>(blk, tile, c0);
 }
 
 // ---------------------------------------------------------------------------
@@ -317,50 +551,34 @@ static cudaError_t prep(Kern k, size_t sm) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
 }
 
+template <typename Kern>
+static cudaError_t go(Kern k, dim3 grid, size_t sm, const CodeIter &it, const ImgBatch &b, const LargeIO &io,
+                      const float2 *tw, cudaStream_t s) {
+  cudaError_t e = prep(k, sm);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kLargeThreads, sm, s>>>(it, b, io, tw);
+  return cudaGetLastError();
+}
+
 template <int N>
 static cudaError_t large_n(int what, const CodeIter &it, const ImgBatch &b, const LargeIO &io, int n,
                            int npairs, const float2 *tw, cudaStream_t s) {
   using G = LargeGeom<N>;
-  const size_t sm = large_smem_bytes<N>();
-  cudaError_t e = cudaSuccess;
-  const dim3 gc(G::NBLK, npairs, n), gr(N / G::RB, npairs, n);
+  const size_t sp = spec_smem_bytes<N>(), ss = spat_smem_bytes<N>();
+  const int S = (npairs + G::GP - 1) / G::GP;
+  const dim3 gs(n, N / 2), gz(n, N / 2, S), gp(1, N / 2, S);
   switch (what) {
-    case LARGE_COL_IN_ADMM:
-      if ((e = prep(large_col_in_kernel<N, 0>, sm)) != cudaSuccess) return e;
-      large_col_in_kernel<N, 0><<<gc, kLargeThreads, sm, s>>>(it, b, io, tw);
-      break;
-    case LARGE_COL_IN_C2R:
-      if ((e = prep(large_col_in_kernel<N, 1>, sm)) != cudaSuccess) return e;
-      large_col_in_kernel<N, 1><<<gc, kLargeThreads, sm, s>>>(it, b, io, tw);
-      break;
-    case LARGE_ROWS_ADMM:
-      if ((e = prep(large_rows_kernel<N, 0>, sm)) != cudaSuccess) return e;
-      large_rows_kernel<N, 0><<<gr, kLargeThreads, sm, s>>>(it, b, io, tw);
-      break;
-    case LARGE_ROWS_FWD:
-      if ((e = prep(large_rows_kernel<N, 1>, sm)) != cudaSuccess) return e;
-      large_rows_kernel<N, 1><<<gr, kLargeThreads, sm, s>>>(it, b, io, tw);
-      break;
-    case LARGE_ROWS_C2R:
-      if ((e = prep(large_rows_kernel<N, 2>, sm)) != cudaSuccess) return e;
-      large_rows_kernel<N, 2><<<gr, kLargeThreads, sm, s>>>(it, b, io, tw);
-      break;
-    case LARGE_COL_OUT_ADMM:
-      if ((e = prep(large_col_out_kernel<N, 0>, sm)) != cudaSuccess) return e;
-      large_col_out_kernel<N, 0><<<gc, kLargeThreads, sm, s>>>(it, b, io, tw);
-      break;
-    case LARGE_COL_OUT_R2C:
-      if ((e = prep(large_col_out_kernel<N, 1>, sm)) != cudaSuccess) return e;
-      large_col_out_kernel<N, 1><<<gc, kLargeThreads, sm, s>>>(it, b, io, tw);
-      break;
-    case LARGE_COL_OUT_IMAGE:
-      if ((e = prep(large_col_out_kernel<N, 2>, sm)) != cudaSuccess) return e;
-      large_col_out_kernel<N, 2><<<gc, kLargeThreads, sm, s>>>(it, b, io, tw);
-      break;
-    default:
-      return cudaErrorInvalidValue;
+    case LARGE_SPEC_DOT: return go(large_spec_kernel<N, 0>, gz, sp, it, b, io, tw, s);
+    case LARGE_SPEC_Z: return go(large_spec_kernel<N, 4>, gz, sp, it, b, io, tw, s);
+    case LARGE_SPEC_IMAGE: return go(large_spec_kernel<N, 1>, gs, sp, it, b, io, tw, s);
+    case LARGE_SPEC_R2C: return go(large_spec_kernel<N, 2>, gp, sp, it, b, io, tw, s);
+    case LARGE_SPEC_C2R: return go(large_spec_kernel<N, 3>, gp, sp, it, b, io, tw, s);
+    case LARGE_SPAT_ADMM: return go(large_spat_kernel<N, 0>, dim3(G::NCB, npairs, n), ss, it, b, io, tw, s);
+    case LARGE_SPAT_IMAGE: return go(large_spat_kernel<N, 1>, dim3(G::NCB, 1, n), ss, it, b, io, tw, s);
+    case LARGE_SPAT_R2C: return go(large_spat_kernel<N, 2>, dim3(G::NCB, npairs, 1), ss, it, b, io, tw, s);
+    case LARGE_SPAT_C2R: return go(large_spat_kernel<N, 3>, dim3(G::NCB, npairs, 1), ss, it, b, io, tw, s);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_large(int N, int what, const CodeIter &it, const ImgBatch &b, const LargeIO &io,
@@ -370,6 +588,22 @@ cudaError_t launch_large(int N, int what, const CodeIter &it, const ImgBatch &b,
     case 256: return large_n<256>(what, it, b, io, n, npairs, tw, s);
     case 512: return large_n<512>(what, it, b, io, n, npairs, tw, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+int large_stages(int N, int npairs) {
+  switch (N) {
+    case 256: return (npairs + LargeGeom<256>::GP - 1) / LargeGeom<256>::GP;
+    case 512: return (npairs + LargeGeom<512>::GP - 1) / LargeGeom<512>::GP;
+    default: return 0;
+  }
+}
+
+int large_resid_groups(int N, int npairs) {
+  switch (N) {
+    case 256: return npairs * LargeGeom<256>::NCB;
+    case 512: return npairs * LargeGeom<512>::NCB;
+    default: return 0;
   }
 }
 

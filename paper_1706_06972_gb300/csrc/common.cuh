@@ -22,6 +22,27 @@ __device__ __forceinline__ float2 cconjmul(float2 a, float2 b) {
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
+// 16-byte asynchronous global -> shared copy (cp.async.cg: through L2 only),
+// its group commit and the wait for all but PENDING committed groups.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// 8-byte variant (through L1), for sources that are only 8-byte aligned.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  cp_async_commit();
+  cp_async_wait<0>();
+}
+
 // Packed lower triangle, column-major: column j holds rows j..K-1.
 // Offset of column j: j*K - j*(j-1)/2.
 __host__ __device__ __forceinline__ int tri_off(int j, int K) { return j * (2 * K - j + 1) / 2; }

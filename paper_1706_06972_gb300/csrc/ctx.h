@@ -32,9 +32,11 @@ struct SizeClass {
   float2 *xhp = nullptr;    // [max_batch][F]
   // code workspace
   float2 *What = nullptr;   // [max_batch][K][F]
-  float *Gam = nullptr;     // [max_batch][K][P]
+  float *Gam = nullptr;     // [max_batch][K][P] spatial ADMM state (see CodeIter::Gam)
   float2 *r = nullptr;      // [max_batch][F]
   float2 *tiles = nullptr;  // [max_batch][ceil(K/2)][N][N] for N >= 256
+  float2 *part = nullptr;   // [max_batch][stages][F] for N >= 256
+  int *cnt = nullptr;       // [max_batch][N/2] for N >= 256
   float2 *obj_xh = nullptr; // [F]
   long long n_seen = 0;
   int pending = 0;

@@ -243,14 +243,6 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
     a.g[(size_t)i * F + p] = make_float2((float)y[i].x, (float)y[i].y);
 }
 
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
 // D-row step of eq. (sub_d_sol): d = (w A + rho I)^-1 (w b + rho (v^ - theta^))
 // = X^H (y + rho X r) with X = L^-1, y = L^-1 (w b) and r = v^ - theta^: two
 // triangular matrix-vector products per frequency, no sequential dependency.

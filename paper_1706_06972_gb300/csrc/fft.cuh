@@ -151,10 +151,11 @@ template <int N> struct LinePlan;
 template <> struct LinePlan<256> { static constexpr int NP = 2, R0 = 16, R1 = 16, R2 = 1; };
 template <> struct LinePlan<512> { static constexpr int NP = 3, R0 = 8, R1 = 8, R2 = 8; };
 
-// One Stockham radix-R pass over NL lines (line l at buf + l * pitch).
-// Consecutive threads take consecutive lines of the same butterfly index.
+// One Stockham radix-R pass over NL lines; element m of line l is at
+// buf[l * ls + m * es].  Consecutive threads take consecutive lines of the
+// same butterfly index.
 template <int N, int NL, int R, int NS, bool INV, int NT>
-__device__ __forceinline__ void line_pass(float2 *__restrict__ buf, int pitch, const float2 *__restrict__ tw) {
+__device__ __forceinline__ void line_pass(float2 *__restrict__ buf, int ls, int es, const float2 *__restrict__ tw) {
   constexpr int G = NL * (N / R);
   constexpr int PER = (G + NT - 1) / NT;
   float2 v[PER][R];
@@ -166,7 +167,7 @@ __device__ __forceinline__ void line_pass(float2 *__restrict__ buf, int pitch, c
       const int line = g % NL;
       const int j = g / NL;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[gi][r] = buf[line * pitch + j + r * (N / R)];
+      for (int r = 0; r < R; ++r) v[gi][r] = buf[line * ls + (j + r * (N / R)) * es];
       if constexpr (NS > 1) {
         const int jm = j % NS;
 #pragma unroll
@@ -188,20 +189,21 @@ __device__ __forceinline__ void line_pass(float2 *__restrict__ buf, int pitch, c
       const int j = g / NL;
       const int base = (j / NS) * NS * R + (j % NS);
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[line * pitch + base + r * NS] = v[gi][r];
+      for (int r = 0; r < R; ++r) buf[line * ls + (base + r * NS) * es] = v[gi][r];
     }
   }
   __syncthreads();
 }
 
-// Full 1D transform of NL lines of length N (unnormalised).  The caller must
-// have synchronised after filling the lines.
+// Full 1D transform of NL lines of length N (unnormalised), element m of
+// line l at buf[l * ls + m * es].  The caller must have synchronised after
+// filling the lines.
 template <int N, int NL, bool INV, int NT>
-__device__ __forceinline__ void fft_lines(float2 *buf, int pitch, const float2 *tw) {
+__device__ __forceinline__ void fft_lines(float2 *buf, int ls, int es, const float2 *tw) {
   using P = LinePlan<N>;
-  line_pass<N, NL, P::R0, 1, INV, NT>(buf, pitch, tw);
-  line_pass<N, NL, P::R1, P::R0, INV, NT>(buf, pitch, tw);
-  if constexpr (P::NP == 3) line_pass<N, NL, P::R2, P::R0 * P::R1, INV, NT>(buf, pitch, tw);
+  line_pass<N, NL, P::R0, 1, INV, NT>(buf, ls, es, tw);
+  line_pass<N, NL, P::R1, P::R0, INV, NT>(buf, ls, es, tw);
+  if constexpr (P::NP == 3) line_pass<N, NL, P::R2, P::R0 * P::R1, INV, NT>(buf, ls, es, tw);
 }
 
 // Threads per CTA used with an N x N tile.

@@ -30,7 +30,7 @@ struct CodeIter {
   const float2 *Dh;    // [K][F] dictionary spectrum used for coding
   float2 *r;           // [slots][F] per-frequency residual multipliers
   float2 *What;        // [slots][K][F] F(U - Gamma)
-  float *Gam;          // [slots][K][N*N] scaled dual
+  float *Gam;          // [slots][K][N*N] spatial state: Gamma (N <= 128); U tiled by column block (N >= 256)
   float2 *Zp;          // [slots][K][F] last Z~ (written on the last iteration)
   // Serving mode (serve = 1): every image has its own iteration index; at
   // iterations t with (t + 1) % check == 0 the kernel stores Z~ and U and
@@ -38,6 +38,12 @@ struct CodeIter {
   // (the U_prev of the next check).  The forward transform always runs.
   int serve, check;
   float *resid;        // [slots][groups][kResidTerms] partial sums
+  // N >= 256 only: the spectral kernels form r (into `r`) from these.
+  float rho;
+  const float *dn;     // [F] |D~(p,:)|^2 of Dh
+  const float2 *xh;    // [slots][F] sample spectra
+  float2 *part;        // [slots][stages][F] partial sums of D^T w^
+  int *cnt;            // [slots][N/2] arrival counters (zero between launches)
 };
 constexpr int kResidTerms = 5;  // |Z-U|^2, |Z|^2, |U|^2, |U-U_prev|^2, |Gamma|^2
 
@@ -53,23 +59,32 @@ cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, cons
 cudaError_t launch_fft2(int N, int inverse, const float *in, float *out, int planes,
                         const float2 *tw, cudaStream_t s);
 
-// FFT sizes 256 and 512: the 2D transforms go through a per-(sample, filter
-// pair) complex tile T[N][N] in global memory (code_large.cu).
+// FFT sizes 256 and 512 (code_large.cu): per (sample, filter pair) a complex
+// tile M[N][N] in global memory holds the column-transformed packed pair
+// between the spectral (row) and spatial (column) kernels of an iteration.
 struct LargeIO {
-  float2 *T;              // tiles [n][npairs][N][N]
+  float2 *T;              // tiles [slots][tile_pairs][N][N] (r2c / c2r: [pairs][N][N])
   const float2 *spec_in;  // c2r input half spectra [planes][F]
-  float2 *spec_out;       // r2c output [planes][F], or sample spectra [n][F]
+  float2 *spec_out;       // r2c output [planes][F], or sample spectra [slots][F]
   const float *real_in;   // r2c input planes [planes][N][N]
   float *real_out;        // c2r output planes [planes][N][N]
   int planes;             // planes of an r2c / c2r call
-  int images;             // LARGE_ROWS_FWD: 1 = zero-padded images of the ImgBatch
+  int tile_pairs;         // tiles per slot (ceil(K / 2)) for the ADMM and sample-spectrum modes
 };
 enum {
-  LARGE_COL_IN_ADMM, LARGE_COL_IN_C2R, LARGE_ROWS_ADMM, LARGE_ROWS_FWD, LARGE_ROWS_C2R,
-  LARGE_COL_OUT_ADMM, LARGE_COL_OUT_R2C, LARGE_COL_OUT_IMAGE
+  LARGE_SPEC_DOT, LARGE_SPEC_Z, LARGE_SPEC_IMAGE, LARGE_SPEC_R2C, LARGE_SPEC_C2R,
+  LARGE_SPAT_ADMM, LARGE_SPAT_IMAGE, LARGE_SPAT_R2C, LARGE_SPAT_C2R
 };
+// n: images (ADMM, IMAGE modes); npairs: filter pairs (ADMM) or plane pairs (R2C, C2R).
+// An iteration is SPEC_DOT (skipped on a batch's first iteration), SPEC_Z,
+// SPAT_ADMM; a sample spectrum SPAT_IMAGE then
+// SPEC_IMAGE; r2c SPAT_R2C then SPEC_R2C; c2r SPEC_C2R then SPAT_C2R.
 cudaError_t launch_large(int N, int what, const CodeIter &it, const ImgBatch &b, const LargeIO &io,
                          int n, int npairs, const float2 *tw, cudaStream_t s);
+// Stages of filter pairs per spectral CTA row (sizes CodeIter::part).
+int large_stages(int N, int npairs);
+// Residual partial sums per slot written by SPAT_ADMM in serving mode.
+int large_resid_groups(int N, int npairs);
 
 // Dictionary step.
 struct FoldArgs {

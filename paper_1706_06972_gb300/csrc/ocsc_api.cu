@@ -103,10 +103,18 @@ ocsc_status alloc_class(ocsc_ctx *c, SizeClass &s, int N) {
       (st = dalloc(c, &s.dn, (size_t)s.F)) || (st = dalloc(c, &s.A, (size_t)s.F * TS)) ||
       (st = dalloc(c, &s.b, KF)) || (st = dalloc(c, &s.X, (size_t)s.F * TS)) || (st = dalloc(c, &s.y, KF)) ||
       (st = dalloc(c, &s.Zp, B * KF)) || (st = dalloc(c, &s.xhp, B * s.F)) ||
-      (st = dalloc(c, &s.What, B * KF)) || (st = dalloc(c, &s.Gam, B * K * s.P)) ||
+      (st = dalloc(c, &s.What, (large_fft(N) ? 1 : B) * KF)) || (st = dalloc(c, &s.Gam, B * K * s.P)) ||
       (st = dalloc(c, &s.r, B * s.F)) || (st = dalloc(c, &s.obj_xh, (size_t)s.F)))
     return st;
-  if (large_fft(N) && (st = dalloc(c, &s.tiles, B * ((K + 1) / 2) * (size_t)s.P))) return st;
+  if (large_fft(N)) {
+    const int npairs = (K + 1) / 2;
+    if ((st = dalloc(c, &s.tiles, B * npairs * (size_t)s.P)) ||
+        (st = dalloc(c, &s.part, B * large_stages(N, npairs) * (size_t)s.F)) ||
+        (st = dalloc(c, &s.cnt, B * (size_t)(N / 2))))
+      return st;
+    cudaError_t e = cudaMemset(s.cnt, 0, B * (size_t)(N / 2) * sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(c, e, "clear counters");
+  }
   std::vector<float2> tw(N);
   for (int m = 0; m < N; ++m) {
     const double a = -2.0 * M_PI * (double)m / (double)N;
@@ -244,14 +252,14 @@ static ocsc_status code_class(ocsc_ctx *c, SizeClass &s, const std::vector<int> 
     }
     LargeIO io{};
     io.T = s.tiles;
+    io.tile_pairs = npairs;
     cudaError_t e;
     if (large_fft(s.N)) {
       io.spec_out = s.xhp;
-      io.images = 1;
       CodeIter none{};
-      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_ROWS_FWD, none, bt, io, bt.n, 1, s.tw, c->stream); });
+      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_SPAT_IMAGE, none, bt, io, bt.n, 1, s.tw, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_COL_OUT_IMAGE, none, bt, io, bt.n, 1, s.tw, c->stream); });
+        e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_SPEC_IMAGE, none, bt, io, bt.n, 1, s.tw, c->stream); });
     } else {
       e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(s.N, bt, s.tw, s.xhp, c->stream); });
     }
@@ -267,21 +275,28 @@ static ocsc_status code_class(ocsc_ctx *c, SizeClass &s, const std::vector<int> 
     it.Zp = s.Zp;
     it.serve = 0;
     it.check = 1;
+    it.rho = (float)c->rho;
+    it.dn = s.dn;
+    it.xh = s.xhp;
+    it.part = s.part;
+    it.cnt = s.cnt;
     for (int t = 0; t < c->opts.Jz; ++t) {
       it.first = t == 0;
       it.last = t == c->opts.Jz - 1;
-      e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(s.N, bt, it, (float)c->rho, s.dn, s.xhp, c->stream); });
-      if (e != cudaSuccess) return cuda_fail(c, e, "code_resid");
       if (large_fft(s.N)) {
-        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(s.N, LARGE_COL_IN_ADMM, it, bt, io, bt.n, npairs, s.tw, c->stream); });
+        e = cudaSuccess;
+        if (!it.first)
+          e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_large(s.N, LARGE_SPEC_DOT, it, bt, io, bt.n, npairs, s.tw, c->stream); });
         if (e == cudaSuccess)
-          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(s.N, LARGE_ROWS_ADMM, it, bt, io, bt.n, npairs, s.tw, c->stream); });
-        if (e == cudaSuccess && !it.last)
-          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(s.N, LARGE_COL_OUT_ADMM, it, bt, io, bt.n, npairs, s.tw, c->stream); });
+          e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_large(s.N, LARGE_SPEC_Z, it, bt, io, bt.n, npairs, s.tw, c->stream); });
+        if (e == cudaSuccess)
+          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(s.N, LARGE_SPAT_ADMM, it, bt, io, bt.n, npairs, s.tw, c->stream); });
       } else {
-        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(s.N, it, bt, s.tw, c->stream); });
+        e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(s.N, bt, it, (float)c->rho, s.dn, s.xhp, c->stream); });
+        if (e == cudaSuccess)
+          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(s.N, it, bt, s.tw, c->stream); });
       }
-      if (e != cudaSuccess) return cuda_fail(c, e, "code_plane");
+      if (e != cudaSuccess) return cuda_fail(c, e, "code iteration");
     }
   }
   s.pending += n;
@@ -441,15 +456,15 @@ static ocsc_status fft2_any(ocsc_ctx *c, int N, int inverse, const float *in, fl
     if (!inverse) {
       io.real_in = in + (size_t)p0 * real;
       io.spec_out = reinterpret_cast<float2 *>(out + (size_t)p0 * spec);
-      e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_ROWS_FWD, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
+      e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_SPAT_R2C, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_COL_OUT_R2C, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_SPEC_R2C, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
     } else {
       io.spec_in = reinterpret_cast<const float2 *>(in + (size_t)p0 * spec);
       io.real_out = out + (size_t)p0 * real;
-      e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_COL_IN_C2R, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
+      e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_SPEC_C2R, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_ROWS_C2R, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(N, LARGE_SPAT_C2R, none, b, io, 1, (np + 1) / 2, s->tw, c->stream); });
     }
     if (e != cudaSuccess) return cuda_fail(c, e, name);
   }
@@ -502,10 +517,10 @@ ocsc_status ocsc_objective(ocsc_ctx *c, int n, const float *const *x, const int 
         LargeIO io{};
         io.T = s.tiles;
         io.spec_out = s.obj_xh;
-        io.images = 1;
-        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_ROWS_FWD, none, bt, io, 1, 1, s.tw, c->stream); });
+        io.tile_pairs = 1;
+        e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_SPAT_IMAGE, none, bt, io, 1, 1, s.tw, c->stream); });
         if (e == cudaSuccess)
-          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_COL_OUT_IMAGE, none, bt, io, 1, 1, s.tw, c->stream); });
+          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_SPEC_IMAGE, none, bt, io, 1, 1, s.tw, c->stream); });
         LargeIO jo{};
         jo.T = s.tiles;
         jo.real_in = u[s0 + i];
@@ -513,9 +528,9 @@ ocsc_status ocsc_objective(ocsc_ctx *c, int n, const float *const *x, const int 
         jo.planes = c->K;
         const int np = (c->K + 1) / 2;
         if (e == cudaSuccess)
-          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_ROWS_FWD, none, bt, jo, 1, np, s.tw, c->stream); });
+          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_SPAT_R2C, none, bt, jo, 1, np, s.tw, c->stream); });
         if (e == cudaSuccess)
-          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_COL_OUT_R2C, none, bt, jo, 1, np, s.tw, c->stream); });
+          e = timed(c, OCSC_K_COUNT, [&] { return launch_large(s.N, LARGE_SPEC_R2C, none, bt, jo, 1, np, s.tw, c->stream); });
       } else {
         e = timed(c, OCSC_K_COUNT, [&] { return launch_image_spectrum(s.N, bt, s.tw, s.obj_xh, c->stream); });
         if (e == cudaSuccess)

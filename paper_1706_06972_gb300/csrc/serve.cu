@@ -47,7 +47,8 @@ struct ServeClass {
   int nslots = 0;
   size_t ws = 0;  // bytes of one request's working set
   std::vector<Slot> slots;
-  float2 *What = nullptr, *r = nullptr, *xh = nullptr, *Zp = nullptr, *tiles = nullptr;
+  float2 *What = nullptr, *r = nullptr, *xh = nullptr, *Zp = nullptr, *tiles = nullptr, *part = nullptr;
+  int *cnt = nullptr;
   float *Gam = nullptr;
   float *resid = nullptr;     // [nslots][groups][kResidTerms]
   int groups = 0;
@@ -126,11 +127,11 @@ cudaError_t launch_spectra(ocsc_server *s, int k, const std::vector<int> &slots)
       LargeIO io{};
       io.T = q.tiles;
       io.spec_out = q.xh;
-      io.images = 1;
+      io.tile_pairs = (c->K + 1) / 2;
       CodeIter none{};
-      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(cl.N, LARGE_ROWS_FWD, none, b, io, b.n, 1, cl.tw, c->stream); });
+      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(cl.N, LARGE_SPAT_IMAGE, none, b, io, b.n, 1, cl.tw, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(cl.N, LARGE_COL_OUT_IMAGE, none, b, io, b.n, 1, cl.tw, c->stream); });
+        e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(cl.N, LARGE_SPEC_IMAGE, none, b, io, b.n, 1, cl.tw, c->stream); });
     } else {
       e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(cl.N, b, cl.tw, q.xh, c->stream); });
     }
@@ -157,6 +158,11 @@ cudaError_t launch_iteration(ocsc_server *s, int k, int v, const std::vector<int
   it.serve = 1;
   it.check = s->o.check_every;
   it.resid = q.resid;
+  it.rho = (float)c->rho;
+  it.dn = q.dn[v];
+  it.xh = q.xh;
+  it.part = q.part;
+  it.cnt = q.cnt;
   for (size_t s0 = 0; s0 < slots.size(); s0 += kMaxCallImages) {
     ImgBatch b{};
     b.n = (int)std::min<size_t>(kMaxCallImages, slots.size() - s0);
@@ -169,18 +175,20 @@ cudaError_t launch_iteration(ocsc_server *s, int k, int v, const std::vector<int
       b.slot[i] = slots[s0 + i];
       b.iter[i] = sl.iter;
     }
-    cudaError_t e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(cl.N, b, it, (float)c->rho, q.dn[v], q.xh, c->stream); });
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     if (large_fft(cl.N)) {
       LargeIO io{};
       io.T = q.tiles;
-      e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(cl.N, LARGE_COL_IN_ADMM, it, b, io, b.n, npairs, cl.tw, c->stream); });
+      io.tile_pairs = npairs;
+      e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_large(cl.N, LARGE_SPEC_DOT, it, b, io, b.n, npairs, cl.tw, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(cl.N, LARGE_ROWS_ADMM, it, b, io, b.n, npairs, cl.tw, c->stream); });
+        e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_large(cl.N, LARGE_SPEC_Z, it, b, io, b.n, npairs, cl.tw, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(cl.N, LARGE_COL_OUT_ADMM, it, b, io, b.n, npairs, cl.tw, c->stream); });
+        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(cl.N, LARGE_SPAT_ADMM, it, b, io, b.n, npairs, cl.tw, c->stream); });
     } else {
-      e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(cl.N, it, b, cl.tw, c->stream); });
+      e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(cl.N, b, it, (float)c->rho, q.dn[v], q.xh, c->stream); });
+      if (e == cudaSuccess)
+        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(cl.N, it, b, cl.tw, c->stream); });
     }
     if (e != cudaSuccess) return e;
   }
@@ -233,21 +241,31 @@ ocsc_status ocsc_server_create(ocsc_server **out, ocsc_ctx *c, const ocsc_server
     const SizeClass &cl = c->cls[k];
     ServeClass &q = s->sc[k];
     const size_t KF = (size_t)K * cl.F;
-    q.ws = KF * sizeof(float2) * 2 + (size_t)K * cl.P * sizeof(float) * 2 + (size_t)cl.F * sizeof(float2) * 2 +
-           (large_fft(cl.N) ? (size_t)npairs * cl.P * sizeof(float2) : 0);
+    // Per request: Z~, the spatial state, the code U it writes, the sample
+    // spectrum, r, and W^ (N <= 128) or the pair tiles and partial sums (N >= 256).
+    const bool big = large_fft(cl.N);
+    const int stages = big ? large_stages(cl.N, npairs) : 0;
+    q.ws = KF * sizeof(float2) + (size_t)K * cl.P * sizeof(float) * 2 + (size_t)cl.F * sizeof(float2) * 2 +
+           (big ? ((size_t)npairs * cl.P + (size_t)stages * cl.F) * sizeof(float2) : KF * sizeof(float2));
     q.nslots = (int)std::max<size_t>(1, std::min<size_t>(kMaxCallImages, s->o.mem_budget / q.ws));
     q.slots.resize(q.nslots);
-    q.groups = large_fft(cl.N) ? npairs * (cl.N / (8192 / cl.N)) : npairs;
-    const size_t ns = (size_t)q.nslots;
+    q.groups = big ? large_resid_groups(cl.N, npairs) : npairs;
+    const size_t ns = (size_t)q.nslots, nw = big ? 1 : ns;
     ocsc_status st;
-    if ((st = salloc(s, &q.What, ns * KF)) || (st = salloc(s, &q.Zp, ns * KF)) ||
+    if ((st = salloc(s, &q.What, nw * KF)) || (st = salloc(s, &q.Zp, ns * KF)) ||
         (st = salloc(s, &q.Gam, ns * K * (size_t)cl.P)) || (st = salloc(s, &q.r, ns * cl.F)) ||
         (st = salloc(s, &q.xh, ns * cl.F)) || (st = salloc(s, &q.resid, ns * q.groups * kResidTerms)) ||
         (st = salloc(s, &q.d_slots, ns)) || (st = salloc(s, &q.d_res, ns * kResidTerms)) ||
         (st = salloc(s, &q.D[0], KF)) || (st = salloc(s, &q.D[1], KF)) || (st = salloc(s, &q.dn[0], (size_t)cl.F)) ||
         (st = salloc(s, &q.dn[1], (size_t)cl.F)))
       return bail(st);
-    if (large_fft(cl.N) && (st = salloc(s, &q.tiles, ns * npairs * (size_t)cl.P))) return bail(st);
+    if (big) {
+      if ((st = salloc(s, &q.tiles, ns * npairs * (size_t)cl.P)) || (st = salloc(s, &q.part, ns * stages * (size_t)cl.F)) ||
+          (st = salloc(s, &q.cnt, ns * (size_t)(cl.N / 2))))
+        return bail(st);
+      cudaError_t e = cudaMemset(q.cnt, 0, ns * (size_t)(cl.N / 2) * sizeof(int));
+      if (e != cudaSuccess) return bail(cuda_fail(c, e, "server: clear counters"));
+    }
     max_slots = std::max(max_slots, q.nslots);
   }
   if (cudaMallocHost((void **)&s->h_res, (size_t)max_slots * kResidTerms * sizeof(double)) != cudaSuccess ||
