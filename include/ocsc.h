@@ -82,6 +82,14 @@ typedef struct {
                          0: against D~_{t,J} as Algorithm 2 returns it */
   int rho_convention; /* 0 (default): D-row matrix A + rho I; 1: A + rho P I */
   uint64_t seed;      /* seed of the Gaussian initial filters */
+  int precision;      /* history fold (eqs. (A_update), (B_update)):
+                         0 (default): FP32 on the CUDA cores;
+                         1: the K x K sums of conj(z) z^T per frequency on the
+                            tensor cores with BF16 operands and FP32
+                            accumulation, the history kept as a compensated
+                            pair of FP32 words (A + Alo) across the stream;
+                         2: as 1 with each code split into two BF16 words
+                            (hi + lo; products hi hi + hi lo + lo hi). */
 } ocsc_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -147,6 +155,21 @@ ocsc_status ocsc_get_dict(ocsc_ctx *ctx, float *D_host, uint64_t *version);
  * the DictOCSC dual to 0; the history is kept.  Synchronises.
  */
 ocsc_status ocsc_set_dict(ocsc_ctx *ctx, const float *D_host, int normalize);
+
+/*
+ * Checkpoint of the learner between dictionary updates (the paper has no
+ * counterpart; it keeps the state of Algorithm 3 across a restart): the
+ * filters V, and per size class the coding and DictOCSC spectra (V^, theta^,
+ * D~), the history A (packed) and b, |d|^2 and the sample counts.
+ * ocsc_get_state with buf == NULL stores the byte count in *len; otherwise it
+ * copies the state into HOST buf (*len >= that count, set to it on return).
+ * OCSC_ESTATE if samples are pending (call ocsc_update_dict or
+ * ocsc_drop_pending first).  ocsc_set_state loads a state saved by a context
+ * with the same K, filter size, lambda, rho, conventions and FFT sizes
+ * (OCSC_EINVAL otherwise; nothing is changed then).  Both synchronise.
+ */
+ocsc_status ocsc_get_state(ocsc_ctx *ctx, void *buf, size_t *len);
+ocsc_status ocsc_set_state(ocsc_ctx *ctx, const void *buf, size_t len);
 
 /* Block until all work queued on ctx's stream is done; reports device errors. */
 ocsc_status ocsc_sync(ocsc_ctx *ctx);
@@ -236,15 +259,18 @@ ocsc_status ocsc_server_poll(ocsc_server *s, ocsc_served *out, int max, int *n);
 /* Kernel classes for ocsc_profile / ocsc_profile_read. */
 typedef enum {
   OCSC_K_IMAGE_SPECTRUM = 0, /* x~ = F(pad x) */
-  OCSC_K_CODE_RESID = 1,     /* per-frequency residual of the Z~-step */
-  OCSC_K_CODE_PLANE = 2,     /* fused code-ADMM iteration per filter pair */
+  OCSC_K_CODE_RESID = 1,     /* per-frequency residual of the Z~-step (N >= 256:
+                                the spectral row kernels) */
+  OCSC_K_CODE_PLANE = 2,     /* fused code-ADMM iteration per filter pair (N >= 256:
+                                the spatial column kernel) */
   OCSC_K_FOLD_FACTOR = 3,    /* history fold + FP64 Cholesky + FP32 L^-1 per frequency */
   OCSC_K_DSTEP = 4,          /* D-row solve of eq. (sub_d_sol) */
   OCSC_K_VSTEP_COLS = 5,     /* pruned inverse DFT along the first axis */
   OCSC_K_VSTEP_PROJECT = 6,  /* Proposition 2 projection of the support */
   OCSC_K_DICT_NORMS = 7,     /* |D~(p,:)|^2 of the coding dictionary */
   OCSC_K_VSTEP_SPECTRUM = 8, /* V^ = F(pad V) and the dual update */
-  OCSC_K_COUNT = 9
+  OCSC_K_HISTORY_TC = 9,     /* tensor-core history fold (opts.precision > 0) */
+  OCSC_K_COUNT = 10
 } ocsc_kernel;
 
 typedef struct {

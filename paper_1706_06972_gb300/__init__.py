@@ -34,7 +34,7 @@ class ocsc_opts(ctypes.Structure):
         ("Jz", ctypes.c_int), ("Jd", ctypes.c_int), ("pad", ctypes.c_int),
         ("max_batch", ctypes.c_int), ("fft_sizes", ctypes.c_int * 4), ("warm_start", ctypes.c_int),
         ("return_feasible", ctypes.c_int), ("rho_convention", ctypes.c_int),
-        ("seed", ctypes.c_uint64),
+        ("seed", ctypes.c_uint64), ("precision", ctypes.c_int),
     ]
 
 
@@ -54,7 +54,7 @@ class ocsc_served(ctypes.Structure):
 
 
 KERNELS = ("image_spectrum", "code_resid", "code_plane", "fold_factor", "dstep", "vstep_cols",
-           "vstep_project", "dict_norms", "vstep_spectrum")
+           "vstep_project", "dict_norms", "vstep_spectrum", "history_tc")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -72,6 +72,8 @@ _PROTOS = {
     "ocsc_sync": (_I, [_P]),
     "ocsc_last_error": (ctypes.c_char_p, [_P]),
     "ocsc_drop_pending": (_I, [_P]),
+    "ocsc_get_state": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    "ocsc_set_state": (_I, [_P, _P, ctypes.c_size_t]),
     "ocsc_objective": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double)]),
     "ocsc_get_counters": (_I, [_P, ctypes.POINTER(ocsc_counters)]),
@@ -176,6 +178,19 @@ def ocsc_last_error(ctx) -> str:
 
 def ocsc_drop_pending(ctx) -> None:
     _check(ctx, lib().ocsc_drop_pending(ctx))
+
+
+def ocsc_get_state(ctx) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check(ctx, lib().ocsc_get_state(ctx, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(ctx, lib().ocsc_get_state(ctx, buf, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def ocsc_set_state(ctx, state: bytes) -> None:
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(ctx, lib().ocsc_set_state(ctx, buf, len(state)))
 
 
 def ocsc_objective(ctx, x_ptrs, H, W, u_ptrs):
@@ -313,6 +328,14 @@ class OCSC:
 
     def drop_pending(self):
         ocsc_drop_pending(self.ctx)
+
+    def get_state(self) -> bytes:
+        """Checkpoint of the learner (no samples may be pending)."""
+        return ocsc_get_state(self.ctx)
+
+    def set_state(self, state: bytes) -> None:
+        """Load a checkpoint saved by a learner of the same shape and parameters."""
+        ocsc_set_state(self.ctx, state)
 
     def objective(self, images, codes):
         """Per-sample objective of eq. (ocsc0) against the current dictionary."""

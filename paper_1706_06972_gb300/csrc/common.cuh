@@ -66,6 +66,6 @@ __device__ __forceinline__ void tri_ij(int t, int K, int &i, int &j) {
 }
 
 // Device error word bits.
-enum : int { ERR_PIVOT = 1 };
+enum : int { ERR_PIVOT = 1, ERR_TIMEOUT = 2 };
 
 }  // namespace ocsc

@@ -24,6 +24,7 @@ struct SizeClass {
   float *dn = nullptr;      // [F] |D~(p,:)|^2 of the coding dictionary
   // history and factor
   float2 *A = nullptr;      // [F][stride] packed FP32 history
+  float2 *Alo = nullptr;    // [F][stride] its compensation word (precision > 0)
   float2 *b = nullptr;      // [K][F]
   float2 *X = nullptr;      // [F][stride] X = L^-1 (FP32) of the FP64 factor
   float2 *y = nullptr;      // [K][F] y = L^-1 (w b)

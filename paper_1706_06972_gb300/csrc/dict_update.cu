@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   for (int m = 0; m < (128 + kFoldThreads - 1) / kFoldThreads; ++m) sb[m] = make_float2(0.f, 0.f);
 
   // 1. FP32 sums over the pending samples of conj(z_i) z_j and x~ conj(z_i).
-  for (int c0 = 0; c0 < B; c0 += kFoldChunk) {
+  for (int c0 = 0; c0 < (a.prefolded ? 0 : B); c0 += kFoldChunk) {
     const int nb = min(kFoldChunk, B - c0);
     __syncthreads();
     for (int e = tid; e < nb * K; e += kFoldThreads) {
@@ -105,23 +105,38 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   // 2. Running means in FP32 (stored), and M = w A + rho I, y = w b in FP64.
   float2 *Ap = a.A + (size_t)p * tri_stride(K);
   const float alpha = (float)a.alpha, beta = (float)a.beta;
+  const float2 *Lo = a.Alo ? a.Alo + (size_t)p * tri_stride(K) : nullptr;
   for (int t = tid; t < T; t += kFoldThreads) {
     int i, j;
     tri_ij(t, K, i, j);
-    const float2 old = a.first ? make_float2(0.f, 0.f) : Ap[t];
-    const float2 sum = S[2 * t];
-    const float2 nw = make_float2(fmaf(alpha, old.x, beta * sum.x), fmaf(alpha, old.y, beta * sum.y));
-    Ap[t] = nw;
-    M[t] = (i == j) ? make_double2(a.w * (double)nw.x + a.rho_eff, 0.0)
-                    : make_double2(a.w * (double)nw.x, a.w * (double)nw.y);
+    double hx, hy;
+    if (a.prefolded) {  // A (+ its compensation word) already holds the new mean
+      const float2 h = Ap[t];
+      const float2 l = Lo ? Lo[t] : make_float2(0.f, 0.f);
+      hx = (double)h.x + (double)l.x;
+      hy = (double)h.y + (double)l.y;
+    } else {
+      const float2 old = a.first ? make_float2(0.f, 0.f) : Ap[t];
+      const float2 sum = S[2 * t];
+      const float2 nw = make_float2(fmaf(alpha, old.x, beta * sum.x), fmaf(alpha, old.y, beta * sum.y));
+      Ap[t] = nw;
+      hx = nw.x;
+      hy = nw.y;
+    }
+    M[t] = (i == j) ? make_double2(a.w * hx + a.rho_eff, 0.0) : make_double2(a.w * hx, a.w * hy);
   }
 #pragma unroll
   for (int m = 0; m < (128 + kFoldThreads - 1) / kFoldThreads; ++m) {
     const int i = tid + m * kFoldThreads;
     if (i < K) {
-      const float2 old = a.first ? make_float2(0.f, 0.f) : a.b[(size_t)i * F + p];
-      const float2 nw = make_float2(fmaf(alpha, old.x, beta * sb[m].x), fmaf(alpha, old.y, beta * sb[m].y));
-      a.b[(size_t)i * F + p] = nw;
+      float2 nw;
+      if (a.prefolded) {
+        nw = a.b[(size_t)i * F + p];
+      } else {
+        const float2 old = a.first ? make_float2(0.f, 0.f) : a.b[(size_t)i * F + p];
+        nw = make_float2(fmaf(alpha, old.x, beta * sb[m].x), fmaf(alpha, old.y, beta * sb[m].y));
+        a.b[(size_t)i * F + p] = nw;
+      }
       y[i] = make_double2(a.w * (double)nw.x, a.w * (double)nw.y);
     }
   }

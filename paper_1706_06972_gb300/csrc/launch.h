@@ -97,8 +97,27 @@ struct FoldArgs {
   float2 *L;            // [F][stride] X = L^-1 of the FP64 Cholesky factor, FP32
   float2 *g;            // [K][F]  y = L^-1 (w b)
   int *err;
+  // prefolded = 1: A (+ Alo when not null) and b already hold the new means
+  // (tensor-core fold); the kernel only factors.
+  int prefolded;
+  const float2 *Alo;
 };
 cudaError_t launch_fold_factor(const FoldArgs &a, cudaStream_t s);
+
+// Tensor-core history fold (history_tc.cu): A, Alo <- compensated
+// alpha (A + Alo) + beta sum_i conj(z_i) z_i^T with BF16 operands (terms = 1)
+// or split BF16 hi + lo (terms = 3) and FP32 accumulation; b in FP32.
+struct GramArgs {
+  int K, F, B, first, terms, SC;
+  float alpha, beta, keep;  // keep = 1 - alpha = B beta
+  const float2 *Zp;         // [B][K][F]
+  const float2 *xh;         // [B][F]
+  float2 *A, *Alo;          // [F][stride]
+  float2 *b;                // [K][F]
+  int *err;
+};
+int gram_chunk(int K, int B, int terms);
+cudaError_t launch_gram_fold(const GramArgs &a, cudaStream_t s);
 // d = X^H (y + rho X (v^ - theta^)) with X = L^-1, y = L^-1 (w b).
 cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const float2 *yb,
                          const float2 *Vh, const float2 *th, float2 *Dcur, float2 *E,

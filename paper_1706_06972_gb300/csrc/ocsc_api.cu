@@ -86,6 +86,10 @@ ocsc_status check_device(ocsc_ctx *c) {
     cudaMemset(c->err, 0, sizeof(int));
     return fail(c, OCSC_ENUMERIC, "non-positive pivot in the per-frequency Cholesky factorisation");
   }
+  if (h & ERR_TIMEOUT) {
+    cudaMemset(c->err, 0, sizeof(int));
+    return fail(c, OCSC_ETIMEOUT, "a tensor-core history fold gave up waiting for its MMAs");
+  }
   return OCSC_OK;
 }
 
@@ -106,6 +110,11 @@ ocsc_status alloc_class(ocsc_ctx *c, SizeClass &s, int N) {
       (st = dalloc(c, &s.What, (large_fft(N) ? 1 : B) * KF)) || (st = dalloc(c, &s.Gam, B * K * s.P)) ||
       (st = dalloc(c, &s.r, B * s.F)) || (st = dalloc(c, &s.obj_xh, (size_t)s.F)))
     return st;
+  if (c->opts.precision > 0) {
+    if ((st = dalloc(c, &s.Alo, (size_t)s.F * TS))) return st;
+    cudaError_t e = cudaMemset(s.Alo, 0, (size_t)s.F * TS * sizeof(float2));
+    if (e != cudaSuccess) return cuda_fail(c, e, "clear history compensation");
+  }
   if (large_fft(N)) {
     const int npairs = (K + 1) / 2;
     if ((st = dalloc(c, &s.tiles, B * npairs * (size_t)s.P)) ||
@@ -140,6 +149,7 @@ void ocsc_default_opts(ocsc_opts *o) {
   o->warm_start = 1;
   o->return_feasible = 1;
   o->rho_convention = 0;
+  o->precision = 0;
   o->seed = 0x5EEDull;
 }
 
@@ -173,6 +183,10 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
     return bail(OCSC_EUNSUPPORTED);
   }
   if (!(lambda >= 0) || !(rho > 0)) { fail(c, OCSC_EINVAL, "need lambda >= 0 and rho > 0"); return bail(OCSC_EINVAL); }
+  if (c->opts.precision < 0 || c->opts.precision > 2) {
+    fail(c, OCSC_EINVAL, "precision must be 0, 1 or 2");
+    return bail(OCSC_EINVAL);
+  }
   if (c->opts.Jz < 1 || c->opts.Jd < 1 || c->opts.max_batch < 1) {
     fail(c, OCSC_EINVAL, "Jz, Jd and max_batch must be positive");
     return bail(OCSC_EINVAL);
@@ -367,6 +381,31 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
     fa.L = s.X;
     fa.g = s.y;
     fa.err = c->err;
+    if (c->opts.precision > 0) {
+      // Tensor-core fold of the pending codes (compensated), then factor only.
+      if (s.pending > 0) {
+        GramArgs ga{};
+        ga.K = c->K;
+        ga.F = s.F;
+        ga.B = s.pending;
+        ga.first = s.n_seen == 0;
+        ga.terms = c->opts.precision == 2 ? 3 : 1;
+        ga.SC = gram_chunk(c->K, s.pending, ga.terms);
+        ga.alpha = (float)fa.alpha;
+        ga.beta = (float)fa.beta;
+        ga.keep = (float)((double)s.pending / (double)nc);
+        ga.Zp = s.Zp;
+        ga.xh = s.xhp;
+        ga.A = s.A;
+        ga.Alo = s.Alo;
+        ga.b = s.b;
+        ga.err = c->err;
+        e = timed(c, OCSC_K_HISTORY_TC, [&] { return launch_gram_fold(ga, c->stream); });
+        if (e != cudaSuccess) return cuda_fail(c, e, "history fold (tensor cores)");
+      }
+      fa.prefolded = 1;
+      fa.Alo = s.Alo;
+    }
     e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_factor(fa, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "fold_factor");
   }
@@ -424,6 +463,130 @@ ocsc_status ocsc_get_dict(ocsc_ctx *c, float *D_host, uint64_t *version) {
 ocsc_status ocsc_set_dict(ocsc_ctx *c, const float *D_host, int normalize) {
   if (!c || !D_host) return c ? fail(c, OCSC_EINVAL, "null input") : OCSC_EINVAL;
   return upload_dict(c, D_host, normalize);
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint: the learner state between updates (no pending samples).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t kStateMagic = 0x4353434Fu;  // "OCSC"
+constexpr uint32_t kStateFormat = 1;
+
+struct StateHeader {
+  uint32_t magic, format;
+  int32_t K, M, ncls, N[4];
+  int32_t rho_convention, return_feasible, warm_start, precision;
+  double lam, rho;
+  int64_t n_seen;
+  uint64_t version;
+  int64_t class_seen[4];
+};
+
+// Device regions of the state, in file order.
+std::vector<std::pair<void *, size_t>> state_regions(ocsc_ctx *c) {
+  std::vector<std::pair<void *, size_t>> r;
+  const size_t K = (size_t)c->K;
+  r.emplace_back(c->V, K * c->M * c->M * sizeof(float));
+  for (SizeClass &s : c->cls) {
+    const size_t kf = K * s.F * sizeof(float2);
+    r.emplace_back(s.Vh, kf);
+    r.emplace_back(s.th, kf);
+    r.emplace_back(s.Dcur, kf);
+    r.emplace_back(s.b, kf);
+    r.emplace_back(s.A, (size_t)s.F * tri_stride(c->K) * sizeof(float2));
+    if (s.Alo) r.emplace_back(s.Alo, (size_t)s.F * tri_stride(c->K) * sizeof(float2));
+    r.emplace_back(s.dn, (size_t)s.F * sizeof(float));
+  }
+  return r;
+}
+
+size_t state_bytes(ocsc_ctx *c) {
+  size_t n = sizeof(StateHeader);
+  for (auto &p : state_regions(c)) n += p.second;
+  return n;
+}
+
+StateHeader make_header(const ocsc_ctx *c) {
+  StateHeader h{};
+  h.magic = kStateMagic;
+  h.format = kStateFormat;
+  h.K = c->K;
+  h.M = c->M;
+  h.ncls = (int32_t)c->cls.size();
+  for (size_t i = 0; i < c->cls.size(); ++i) {
+    h.N[i] = c->cls[i].N;
+    h.class_seen[i] = c->cls[i].n_seen;
+  }
+  h.rho_convention = c->opts.rho_convention;
+  h.return_feasible = c->opts.return_feasible;
+  h.warm_start = c->opts.warm_start;
+  h.precision = c->opts.precision;
+  h.lam = c->lam;
+  h.rho = c->rho;
+  h.n_seen = c->n_seen;
+  h.version = c->version;
+  return h;
+}
+
+}  // namespace
+
+ocsc_status ocsc_get_state(ocsc_ctx *c, void *buf, size_t *len) {
+  if (!c) return OCSC_EINVAL;
+  if (!len) return fail(c, OCSC_EINVAL, "get_state: null length");
+  const size_t need = state_bytes(c);
+  if (!buf) {
+    *len = need;
+    return OCSC_OK;
+  }
+  if (*len < need) return fail(c, OCSC_EINVAL, "get_state: buffer of %zu bytes, need %zu", *len, need);
+  for (const SizeClass &s : c->cls)
+    if (s.pending) return fail(c, OCSC_ESTATE, "get_state: %d samples of size %d are pending", s.pending, s.N);
+  ocsc_status st = check_device(c);
+  if (st != OCSC_OK) return st;
+  const StateHeader h = make_header(c);
+  char *o = static_cast<char *>(buf);
+  std::memcpy(o, &h, sizeof h);
+  o += sizeof h;
+  for (auto &p : state_regions(c)) {
+    cudaError_t e = cudaMemcpy(o, p.first, p.second, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_state copy");
+    o += p.second;
+  }
+  *len = need;
+  return OCSC_OK;
+}
+
+ocsc_status ocsc_set_state(ocsc_ctx *c, const void *buf, size_t len) {
+  if (!c) return OCSC_EINVAL;
+  if (!buf) return fail(c, OCSC_EINVAL, "set_state: null buffer");
+  const size_t need = state_bytes(c);
+  if (len != need) return fail(c, OCSC_EINVAL, "set_state: %zu bytes, this context's state has %zu", len, need);
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof h);
+  const StateHeader mine = make_header(c);
+  bool same = h.magic == kStateMagic && h.format == kStateFormat && h.K == mine.K && h.M == mine.M &&
+              h.ncls == mine.ncls && h.rho_convention == mine.rho_convention &&
+              h.return_feasible == mine.return_feasible && h.warm_start == mine.warm_start &&
+              h.precision == mine.precision &&
+              h.lam == mine.lam && h.rho == mine.rho;
+  for (int i = 0; same && i < h.ncls; ++i) same = h.N[i] == mine.N[i];
+  if (!same) return fail(c, OCSC_EINVAL, "set_state: the state was saved by a context of another shape or parameters");
+  ocsc_status st = check_device(c);
+  if (st != OCSC_OK) return st;
+  const char *o = static_cast<const char *>(buf) + sizeof h;
+  for (auto &p : state_regions(c)) {
+    cudaError_t e = cudaMemcpy(p.first, o, p.second, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_state copy");
+    o += p.second;
+  }
+  for (size_t i = 0; i < c->cls.size(); ++i) {
+    c->cls[i].n_seen = h.class_seen[i];
+    c->cls[i].pending = 0;
+  }
+  c->n_seen = h.n_seen;
+  c->version = h.version;
+  return OCSC_OK;
 }
 
 ocsc_status ocsc_sync(ocsc_ctx *c) {

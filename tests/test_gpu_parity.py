@@ -310,3 +310,120 @@ def test_size_classes_match_oracle():
         oracle.update_dict_multi(st, res, Jd)
         assert rel(D, st.V) < REL_TOL
     learner.close()
+
+
+# --- checkpoint ------------------------------------------------------------------
+
+def test_checkpoint_resumes_bit_identically():
+    """A learner restored from a checkpoint continues exactly like the one that
+    saved it (two size classes, so every per-class array is in the state)."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    K, M = 8, 5
+    raw = raw_filters(K, M, 61)
+    mk = lambda: pkg.OCSC(K, M, 0.5, 1.0, fft_sizes=[64, 128], pad=4, Jz=8, Jd=3, max_batch=2)
+    a = mk()
+    a.set_dict(raw, normalize=True)
+    imgs = [torch.from_numpy(make_image(s, s, 700 + i)).cuda() for i, s in enumerate([50, 90, 40, 100, 60, 70])]
+    for s in range(0, 4, 2):
+        a.code(imgs[s:s + 2], want_codes=False)
+        a.update_dict()
+    state = a.get_state()
+    b = mk()
+    b.set_state(state)
+    assert np.array_equal(a.get_dict(), b.get_dict())
+    ua = a.code(imgs[4:6])
+    a.update_dict()
+    ub = b.code(imgs[4:6])
+    b.update_dict()
+    for x, y in zip(ua, ub):
+        assert torch.equal(x, y)
+    assert np.array_equal(a.get_dict(), b.get_dict())
+    assert a.get_state() == b.get_state()
+    a.code(imgs[:1], want_codes=False)
+    with pytest.raises(pkg.OCSCError) as e:     # pending samples
+        a.get_state()
+    assert e.value.status == 5
+    c = pkg.OCSC(K, M, 0.5, 1.0, fft_sizes=[64], pad=4, Jz=8, Jd=3, max_batch=2)
+    with pytest.raises(pkg.OCSCError) as e:     # another shape
+        c.set_state(state)
+    assert e.value.status == 1
+    for x in (a, b, c):
+        x.close()
+
+
+# --- tensor-core history fold (precision variants) ----------------------------------
+
+class _StateHeader(__import__("ctypes").Structure):
+    import ctypes as _c
+    _fields_ = [("magic", _c.c_uint32), ("format", _c.c_uint32), ("K", _c.c_int32), ("M", _c.c_int32),
+                ("ncls", _c.c_int32), ("N", _c.c_int32 * 4), ("rho_convention", _c.c_int32),
+                ("return_feasible", _c.c_int32), ("warm_start", _c.c_int32), ("precision", _c.c_int32),
+                ("lam", _c.c_double), ("rho", _c.c_double), ("n_seen", _c.c_int64), ("version", _c.c_uint64),
+                ("class_seen", _c.c_int64 * 4)]
+
+
+def _history_from_state(state, K, M, N, precision):
+    """A = A_hi + A_lo of a one-class state as [F, K, K] (lower triangle)."""
+    import ctypes
+
+    NH = N // 2 + 1
+    F = N * NH
+    T = K * (K + 1) // 2
+    TS = T + (T & 1)
+    off = ctypes.sizeof(_StateHeader) + K * M * M * 4 + 4 * K * F * 8
+    A = np.frombuffer(state, np.complex64, F * TS, off).reshape(F, TS).astype(np.complex128)
+    off += F * TS * 8
+    if precision:
+        A = A + np.frombuffer(state, np.complex64, F * TS, off).reshape(F, TS)
+    full = np.zeros((F, K, K), np.complex128)
+    for j in range(K):
+        o = j * (2 * K - j + 1) // 2
+        full[:, j:, j] = A[:, o:o + K - j]
+    return full
+
+
+# History tolerances from the operand rounding: FP32 codes carry ~1e-6 of the
+# coding path's own error; one BF16 word keeps 8 significant bits (unit
+# roundoff 2^-9 = 2e-3 per factor of every product); the split hi + lo keeps
+# 16 (the dropped lo*lo term and the rounding of lo are ~2^-16 = 1.5e-5).
+@pytest.mark.parametrize("precision,a_tol,d_tol", [(0, 1e-5, 1e-3), (1, 1e-2, 2e-2), (2, 6e-5, 1e-3)])
+def test_history_fold_precision_matches_oracle(precision, a_tol, d_tol):
+    """Two rank-8 folds: the FP32 path, BF16 tensor-core products (1 term)
+    and split-BF16 products (3 terms), each with the history checked against
+    the FP64 oracle's A^p entry by entry (lower triangle) and the dictionary
+    and objective after each update."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    K, M, N, B, lam, rho, Jz, Jd = 24, 5, 64, 8, 0.5, 1.0, 15, 5
+    raw = raw_filters(K, M, 71)
+    imgs = [make_image(60, 60, 1200 + i) for i in range(2 * B)]
+    lr = pkg.OCSC(K, M, lam, rho, fft_size=N, pad=4, Jz=Jz, Jd=Jd, max_batch=B, precision=precision)
+    lr.set_dict(raw, normalize=True)
+    st = oracle.init_state(np.asarray(raw, np.float64), N, N, lam, rho)
+    NH = N // 2 + 1
+    k1, k2 = np.divmod(np.arange(N * NH), NH)
+    codes, coding = [], []
+    for s in range(0, 2 * B, B):
+        coding.append(oracle.published_filters(st))
+        us = lr.code([torch.from_numpy(im).cuda() for im in imgs[s:s + B]])
+        lr.update_dict()
+        D = lr.get_dict()
+        res = [oracle.code(st, im, Jz) for im in imgs[s:s + B]]
+        oracle.update_dict(st, res, Jd)
+        codes.extend(u.cpu().numpy() for u in us)
+        A = _history_from_state(lr.get_state(), K, M, N, precision)
+        Ao = st.hist.A[k1, k2]
+        low = np.tril(np.ones((K, K), bool))
+        a_err = np.linalg.norm((A - Ao)[:, low]) / np.linalg.norm(Ao[:, low])
+        d_err = rel(D, st.V)
+        print(f"precision={precision} update={s // B}: history {a_err:.3e} dictionary {d_err:.3e}")
+        assert a_err < a_tol, (precision, a_err)
+        assert d_err < d_tol
+    fo = surrogate_objective([r.U for r in res], [coding[-1]] * B, imgs[B:], N, lam, B)
+    fg = surrogate_objective(codes[B:], [coding[-1]] * B, imgs[B:], N, lam, B)
+    print(f"precision={precision}: relative objective {abs(fg - fo) / abs(fo):.3e}")
+    assert abs(fg - fo) / abs(fo) < 1e-3
+    lr.close()
