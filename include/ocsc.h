@@ -20,9 +20,10 @@
  * Conventions (shared by every call):
  *  - All image, code and filter arrays are float32, row-major.
  *  - Images are square or rectangular H x W; each is zero-padded at the end of
- *    both axes to an N x N FFT domain, N = the smallest supported size
+ *    both axes to an N x N FFT domain, N = the smallest FFT size of the context
  *    >= max(H, W) + pad.  Convolution is circular on that domain and filters
- *    occupy its top-left M x M corner.  Supported N: 64, 128, 256 and 512.
+ *    occupy its top-left M x M corner.  Supported N: 64, 128, 256, 288 and
+ *    512; an image goes to the smallest size of the context that holds it.
  *  - lambda is the l1 weight (beta in the paper); rho is a spatial-domain
  *    ADMM penalty used by both ADMMs (the paper's frequency-domain penalty
  *    rho' of eq. (sub_d_sol) equals rho / P; opts.rho_convention = 1 uses the
@@ -68,7 +69,8 @@ typedef struct {
   int max_batch;      /* most samples that may be pending between two
                          ocsc_update_dict calls (default 1) */
   int fft_sizes[4];   /* the FFT sides N this context serves, zero-terminated,
-                         each of 64, 128, 256, 512 (default {128, 0, 0, 0}).
+                         each of 64, 128, 256, 288, 512 (default
+                         {128, 0, 0, 0}).
                          Each size is a class with its own history, factor,
                          dual and coding spectrum of the one shared
                          dictionary; with several classes the dictionary step
@@ -97,7 +99,8 @@ void ocsc_default_opts(ocsc_opts *o);
 
 /*
  * Create a context for K filters of filter_h x filter_w (square only:
- * filter_h == filter_w = M, M <= 16; K <= 128), l1 weight lambda >= 0 and
+ * filter_h == filter_w = M, M <= 16; K <= 256; above 128 the factor is
+ * blocked through a global FP64 workspace of one matrix per SM), l1 weight lambda >= 0 and
  * penalty rho > 0.  opts may be NULL (defaults).  cuda_stream is a
  * cudaStream_t (NULL = legacy default stream).  The initial dictionary is
  * Algorithm 3's Gaussian random initialisation: K x M x M N(0,1) draws from a
@@ -116,7 +119,8 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
  * Synchronises ctx's stream first. */
 void ocsc_destroy(ocsc_ctx *ctx);
 
-/* Padded FFT side N for an H x W image under ctx's pad policy. */
+/* Padded FFT side N for an H x W image: the smallest FFT size of ctx that
+ * holds max(H, W) + pad (OCSC_EUNSUPPORTED if none does). */
 ocsc_status ocsc_padded_size(const ocsc_ctx *ctx, int H, int W, int *N);
 
 /*

@@ -1,5 +1,5 @@
 // Code ADMM for FFT sizes whose packed N x N complex plane does not fit one
-// CTA's shared memory (N = 256, 512).  The iteration is the one of
+// CTA's shared memory (N = 256, 288 = 2^5 3^2, 512).  The iteration is the one of
 // code_admm.cu (Sec. II-C.1 problem (fcsc_code), ADMM of Sec. II-B):
 //   W^ = F(U - Gamma),  z = w^ + conj(d) r,  r = (x~ - d^T w^) / (rho + |d|^2),
 //   U' = S(Z + Gamma),  Gamma' = Gamma + Z - U'.
@@ -34,16 +34,26 @@ namespace ocsc {
 
 constexpr int kLargeThreads = 256;
 
+// Columns per spatial CTA (CB, even, dividing N) and filter pairs per spectral
+// stage (GP) for each size.
+template <int N> struct LargeTile;
+template <> struct LargeTile<256> { static constexpr int CB = 16, GP = 8; };
+template <> struct LargeTile<288> { static constexpr int CB = 16, GP = 4; };
+template <> struct LargeTile<512> { static constexpr int CB = 8, GP = 4; };
+
 template <int N>
 struct LargeGeom {
   static constexpr int NH = N / 2 + 1, F = N * NH, P = N * N;
   static constexpr int PITCH = N + 2;          // complex elements per shared-memory line
-  static constexpr int CB = 4096 / N;          // spatial CTA: columns per block
+  static constexpr int CB = LargeTile<N>::CB;  // spatial CTA: columns per block
   static constexpr int NCB = N / CB;
-  static constexpr int GP = 2048 / N;          // spectral CTA: filter pairs per stage
+  static constexpr int GP = LargeTile<N>::GP;  // spectral CTA: filter pairs per stage
   static constexpr int NL = 2 * GP;            // spectral CTA: lines per stage
   static constexpr int EPT = (2 * NH + kLargeThreads - 1) / kLargeThreads;  // row bins per thread
   static constexpr int SPT = N * CB / kLargeThreads;                        // spatial elements per thread
+  static constexpr int CH = SPT % 4 == 0 ? 4 : (SPT % 3 == 0 ? 3 : (SPT % 2 == 0 ? 2 : 1));
+  static_assert(N % CB == 0 && CB % 2 == 0 && N * CB % kLargeThreads == 0, "spatial tiling");
+  static_assert(N * (CB / 2) % kLargeThreads == 0, "spatial copies");
 };
 
 // Spectral CTA: two stage buffers of NL lines (pass 1 is double-buffered)
@@ -98,7 +108,7 @@ __device__ __forceinline__ void load_rows(float2 *lines, const float2 *tiles, in
                                           int row1) {
   using G = LargeGeom<N>;
   constexpr int V = N / 2;  // float4 per row
-  constexpr int TRIPS = G::NL * V / kLargeThreads;
+  constexpr int TRIPS = (G::NL * V + kLargeThreads - 1) / kLargeThreads;
 #pragma unroll
   for (int s = 0; s < TRIPS; ++s) {
     const int e = threadIdx.x + s * kLargeThreads;
@@ -117,7 +127,7 @@ __device__ __forceinline__ void load_rows_async(float2 *lines, const float2 *til
                                                 int row1) {
   using G = LargeGeom<N>;
   constexpr int V = N / 2;
-  constexpr int TRIPS = G::NL * V / kLargeThreads;
+  constexpr int TRIPS = (G::NL * V + kLargeThreads - 1) / kLargeThreads;
 #pragma unroll
   for (int s = 0; s < TRIPS; ++s) {
     const int e = threadIdx.x + s * kLargeThreads;
@@ -134,7 +144,7 @@ template <int N>
 __device__ __forceinline__ void store_rows(const float2 *lines, float2 *tiles, int j0, int ng, int row0, int row1) {
   using G = LargeGeom<N>;
   constexpr int V = N / 2;
-  constexpr int TRIPS = G::NL * V / kLargeThreads;
+  constexpr int TRIPS = (G::NL * V + kLargeThreads - 1) / kLargeThreads;
 #pragma unroll
   for (int s = 0; s < TRIPS; ++s) {
     const int e = threadIdx.x + s * kLargeThreads;
@@ -269,7 +279,7 @@ __global__ void __launch_bounds__(kLargeThreads, 3)
     const int mr = selfm ? r : 1 - r;
     kk[q] = k2;
     lo[q] = r * G::PITCH + k2;
-    lm[q] = mr * G::PITCH + ((N - k2) & (N - 1));
+    lm[q] = mr * G::PITCH + (k2 == 0 ? 0 : N - k2);
     ld[q] = r * G::NH + k2;
     pe[q] = ok ? (r ? row1 : row0) * G::NH + k2 : -1;
   }
@@ -497,7 +507,7 @@ __global__ void __launch_bounds__(kLargeThreads, 4)
   float *Ub = (b.u[img] && hasb) ? b.u[img] + (size_t)kb * G::P : nullptr;
   const float invP = 1.0f / (float)G::P;
   float acc[kResidTerms] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  constexpr int CH = 4;  // state loads in flight per thread
+  constexpr int CH = G::CH;  // state loads in flight per thread
 #pragma unroll 1
   for (int s0 = 0; s0 < G::SPT; s0 += CH) {
     float pa[CH], pb[CH];
@@ -586,6 +596,7 @@ cudaError_t launch_large(int N, int what, const CodeIter &it, const ImgBatch &b,
   if (n <= 0 || npairs <= 0) return cudaSuccess;
   switch (N) {
     case 256: return large_n<256>(what, it, b, io, n, npairs, tw, s);
+    case 288: return large_n<288>(what, it, b, io, n, npairs, tw, s);
     case 512: return large_n<512>(what, it, b, io, n, npairs, tw, s);
     default: return cudaErrorInvalidValue;
   }
@@ -594,6 +605,7 @@ cudaError_t launch_large(int N, int what, const CodeIter &it, const ImgBatch &b,
 int large_stages(int N, int npairs) {
   switch (N) {
     case 256: return (npairs + LargeGeom<256>::GP - 1) / LargeGeom<256>::GP;
+    case 288: return (npairs + LargeGeom<288>::GP - 1) / LargeGeom<288>::GP;
     case 512: return (npairs + LargeGeom<512>::GP - 1) / LargeGeom<512>::GP;
     default: return 0;
   }
@@ -602,6 +614,7 @@ int large_stages(int N, int npairs) {
 int large_resid_groups(int N, int npairs) {
   switch (N) {
     case 256: return npairs * LargeGeom<256>::NCB;
+    case 288: return npairs * LargeGeom<288>::NCB;
     case 512: return npairs * LargeGeom<512>::NCB;
     default: return 0;
   }

@@ -55,6 +55,8 @@ struct ocsc_ctx {
   double *obj_part = nullptr;
   double *obj_out = nullptr;
   int *err = nullptr;       // device error word
+  double2 *work = nullptr;  // K > 128: FP64 factorisation workspace, one matrix per persistent CTA
+  int work_ctas = 0;
   long long n_seen = 0;     // samples folded over all classes
   uint64_t version = 0;
   std::string msg;
@@ -97,21 +99,17 @@ ocsc_status dalloc(ocsc_ctx *c, T **p, size_t count) {
   return OCSC_OK;
 }
 
-inline bool supported_fft(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
+inline bool supported_fft(int n) { return n == 64 || n == 128 || n == 256 || n == 288 || n == 512; }
 inline bool large_fft(int n) { return n >= 256; }
 
-inline int padded_side(int side, int pad) {
-  const int need = side + pad;
-  for (int n : {64, 128, 256, 512})
-    if (n >= need) return n;
-  return -1;
-}
-
+// Class of an H x W image: the smallest FFT size of the context that holds
+// max(H, W) + pad, or -1.
 inline int class_of(const ocsc_ctx *c, int H, int W) {
-  const int n = padded_side(H > W ? H : W, c->opts.pad);
+  const int need = (H > W ? H : W) + c->opts.pad;
+  int best = -1;
   for (size_t i = 0; i < c->cls.size(); ++i)
-    if (c->cls[i].N == n) return (int)i;
-  return -1;
+    if (c->cls[i].N >= need && (best < 0 || c->cls[i].N < c->cls[best].N)) best = (int)i;
+  return best;
 }
 
 // Launch one kernel through `fn`, counting it and, when its class is being
@@ -136,6 +134,10 @@ cudaError_t timed(ocsc_ctx *c, int id, Fn &&fn) {
   used += 2;
   return err;
 }
+
+// K above this uses the dict_big.cu kernels (matrix outside shared memory).
+constexpr int kSmallK = 128;
+inline bool big_k(const ocsc_ctx *c) { return c->K > kSmallK; }
 
 inline const float2 *coding_spectrum(const ocsc_ctx *c, const SizeClass &s) {
   return c->opts.return_feasible ? s.Vh : s.Dcur;

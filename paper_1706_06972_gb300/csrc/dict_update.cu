@@ -329,8 +329,8 @@ __global__ void vstep_cols_kernel(int K, int N, int M, const float2 *__restrict_
   const float2 *Ek = E + (size_t)k * F + k2;
   float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
   for (int k1 = 0; k1 < N; k1 += 2) {
-    acc0 = cadd(acc0, cmulc(Ek[(size_t)k1 * NH], s_twc[(k1 * m1) & (N - 1)]));
-    acc1 = cadd(acc1, cmulc(Ek[(size_t)(k1 + 1) * NH], s_twc[((k1 + 1) * m1) & (N - 1)]));
+    acc0 = cadd(acc0, cmulc(Ek[(size_t)k1 * NH], s_twc[(k1 * m1) % N]));
+    acc1 = cadd(acc1, cmulc(Ek[(size_t)(k1 + 1) * NH], s_twc[((k1 + 1) * m1) % N]));
   }
   Y[((size_t)k * M + m1) * NH + k2] = cadd(acc0, acc1);
 }
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(kProjThreads)
       float s = 0.f;
       for (int k2 = lane; k2 < NH; k2 += 32) {
         const float2 yv = Yr[k2];
-        const float2 w = tw[(k2 * m2) & (N - 1)];
+        const float2 w = tw[(k2 * m2) % N];
         const float cw = (k2 == 0 || k2 == N / 2) ? 1.f : 2.f;
         s += cw * (yv.x * w.x + yv.y * w.y);
       }
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kProjThreads)
     const int m1 = e / NH, k2 = e % NH;
     float2 acc = make_float2(0.f, 0.f);
     for (int m2 = 0; m2 < M; ++m2) {
-      const float2 w = s_tw[(k2 * m2) & (N - 1)];
+      const float2 w = s_tw[(k2 * m2) % N];
       const float v = alpha[m1 * M + m2];
       acc.x += v * w.x;
       acc.y += v * w.y;
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(256)
   const int k1 = p / NH, k2 = p % NH;
   const float2 *T = Tm + (size_t)k * M * NH + k2;
   float2 acc = make_float2(0.f, 0.f);
-  for (int m1 = 0; m1 < M; ++m1) acc = cadd(acc, cmul(T[(size_t)m1 * NH], s_tw[(k1 * m1) & (N - 1)]));
+  for (int m1 = 0; m1 < M; ++m1) acc = cadd(acc, cmul(T[(size_t)m1 * NH], s_tw[(k1 * m1) % N]));
   const size_t o = (size_t)k * F + p;
   Vh[o] = acc;
   if (mode == 0) {

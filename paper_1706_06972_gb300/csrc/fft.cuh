@@ -73,6 +73,58 @@ struct RegDFT<1, INV> {
   static __device__ __forceinline__ void run(float2 *) {}
 };
 
+// 3-point DFT: X0 = a + b + c, X1,2 = a - (b + c)/2 -+ i sqrt(3)/2 (b - c)
+// (forward; the signs of the sine terms flip for the inverse).
+template <bool INV>
+struct RegDFT<3, INV> {
+  static __device__ __forceinline__ void run(float2 *v) {
+    constexpr float h = 0.86602540378443865f;  // sqrt(3) / 2
+    const float2 a = v[0], s = make_float2(v[1].x + v[2].x, v[1].y + v[2].y);
+    const float2 d = make_float2(v[1].x - v[2].x, v[1].y - v[2].y);
+    const float2 t = make_float2(a.x - 0.5f * s.x, a.y - 0.5f * s.y);
+    const float2 r = INV ? make_float2(-h * d.y, h * d.x) : make_float2(h * d.y, -h * d.x);  // -+ i h d
+    v[0] = make_float2(a.x + s.x, a.y + s.y);
+    v[1] = make_float2(t.x + r.x, t.y + r.y);
+    v[2] = make_float2(t.x - r.x, t.y - r.y);
+  }
+};
+
+// 9-point DFT as 3 x 3 (n = n1 + 3 n2, k = k1 + 3 k2): 3-point DFTs over n2,
+// twiddles W9^(n1 k1), 3-point DFTs over n1.  cos and sin of 2 pi m / 9 for
+// m = 1, 2, 4.
+template <bool INV>
+struct RegDFT<9, INV> {
+  static __device__ __forceinline__ float2 tw9(float2 o, float c, float s0) {
+    const float s = INV ? s0 : -s0;  // W9^m = cos - i sin (forward)
+    return make_float2(o.x * c - o.y * s, o.x * s + o.y * c);
+  }
+  static __device__ __forceinline__ void run(float2 *v) {
+    constexpr float c1 = 0.76604444311897804f, s1 = 0.64278760968653933f;
+    constexpr float c2 = 0.17364817766693041f, s2 = 0.98480775301220802f;
+    constexpr float c4 = -0.93969262078590832f, s4 = 0.34202014332566888f;
+    float2 y[3][3];
+#pragma unroll
+    for (int n1 = 0; n1 < 3; ++n1) {
+      y[n1][0] = v[n1];
+      y[n1][1] = v[n1 + 3];
+      y[n1][2] = v[n1 + 6];
+      RegDFT<3, INV>::run(y[n1]);
+    }
+    y[1][1] = tw9(y[1][1], c1, s1);
+    y[1][2] = tw9(y[1][2], c2, s2);
+    y[2][1] = tw9(y[2][1], c2, s2);
+    y[2][2] = tw9(y[2][2], c4, s4);
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+      float2 w[3] = {y[0][k1], y[1][k1], y[2][k1]};
+      RegDFT<3, INV>::run(w);
+      v[k1] = w[0];
+      v[k1 + 3] = w[1];
+      v[k1 + 6] = w[2];
+    }
+  }
+};
+
 // Radix plan per transform length.
 template <int N> struct FFTPlan;
 template <> struct FFTPlan<64> { static constexpr int R0 = 8, R1 = 8; };
@@ -150,6 +202,7 @@ __device__ __forceinline__ void fft2d_tile(float2 *tile, const float2 *tw) {
 template <int N> struct LinePlan;
 template <> struct LinePlan<256> { static constexpr int NP = 2, R0 = 16, R1 = 16, R2 = 1; };
 template <> struct LinePlan<512> { static constexpr int NP = 3, R0 = 8, R1 = 8, R2 = 8; };
+template <> struct LinePlan<288> { static constexpr int NP = 3, R0 = 8, R1 = 4, R2 = 9; };
 
 // One Stockham radix-R pass over NL lines; element m of line l is at
 // buf[l * ls + m * es].  Consecutive threads take consecutive lines of the

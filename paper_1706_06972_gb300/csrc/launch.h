@@ -117,6 +117,15 @@ struct GramArgs {
   int *err;
 };
 int gram_chunk(int K, int B, int terms);
+
+// K > 128 (dict_big.cu): FP32 fold into A, b; blocked FP64 Cholesky of
+// w (A + Alo) + rho I storing L (FP32, in FoldArgs::L) and y = L^-1 (w b);
+// D-step by substitution with L.
+cudaError_t launch_fold_big(const FoldArgs &a, cudaStream_t s);
+size_t factor_big_workspace(int K, int ctas);
+cudaError_t launch_factor_big(const FoldArgs &a, double2 *work, int ctas, cudaStream_t s);
+cudaError_t launch_dstep_big(int K, int F, float rho_eff, const float2 *L, const float2 *yb, const float2 *Vh,
+                             const float2 *th, float2 *Dcur, float2 *E, cudaStream_t s);
 cudaError_t launch_gram_fold(const GramArgs &a, cudaStream_t s);
 // d = X^H (y + rho X (v^ - theta^)) with X = L^-1, y = L^-1 (w b).
 cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const float2 *yb,

@@ -177,7 +177,7 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
     ocsc_destroy(c);
     return s;
   };
-  if (K <= 0 || K > 128) { fail(c, OCSC_EUNSUPPORTED, "K=%d outside 1..128", K); return bail(OCSC_EUNSUPPORTED); }
+  if (K <= 0 || K > 256) { fail(c, OCSC_EUNSUPPORTED, "K=%d outside 1..256", K); return bail(OCSC_EUNSUPPORTED); }
   if (filter_h != filter_w || filter_h <= 0 || filter_h > 16) {
     fail(c, OCSC_EUNSUPPORTED, "filters must be square with side 1..16");
     return bail(OCSC_EUNSUPPORTED);
@@ -195,7 +195,7 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
   for (int i = 0; i < 4 && c->opts.fft_sizes[i] != 0; ++i) {
     const int n = c->opts.fft_sizes[i];
     if (!supported_fft(n) || n < filter_h) {
-      fail(c, OCSC_EUNSUPPORTED, "fft size %d not supported (64, 128, 256 or 512)", n);
+      fail(c, OCSC_EUNSUPPORTED, "fft size %d not supported (64, 128, 256, 288 or 512)", n);
       return bail(OCSC_EUNSUPPORTED);
     }
     for (int m : sizes)
@@ -220,6 +220,13 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
     if ((st = alloc_class(c, c->cls[i], sizes[i])) != OCSC_OK) return bail(st);
     max_partials = std::max(max_partials, objective_partials(sizes[i]));
   }
+  if (K > kSmallK) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+    c->work_ctas = sms;
+    if ((st = dalloc(c, &c->work, factor_big_workspace(K, sms)))) return bail(st);
+  }
   if ((st = dalloc(c, &c->V, (size_t)K * c->M * c->M)) || (st = dalloc(c, &c->err, 1)) ||
       (st = dalloc(c, &c->obj_part, (size_t)max_partials)) || (st = dalloc(c, &c->obj_out, (size_t)kObjChunk)))
     return bail(st);
@@ -238,9 +245,9 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
 
 ocsc_status ocsc_padded_size(const ocsc_ctx *ctx, int H, int W, int *N) {
   if (!ctx || !N || H <= 0 || W <= 0) return OCSC_EINVAL;
-  const int n = padded_side(H > W ? H : W, ctx->opts.pad);
-  if (n < 0) return OCSC_EUNSUPPORTED;
-  *N = n;
+  const int k = class_of(ctx, H, W);
+  if (k < 0) return OCSC_EUNSUPPORTED;
+  *N = ctx->cls[k].N;
   return OCSC_OK;
 }
 
@@ -381,6 +388,10 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
     fa.L = s.X;
     fa.g = s.y;
     fa.err = c->err;
+    if (big_k(c) && c->opts.precision == 0 && s.pending > 0) {
+      e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_big(fa, c->stream); });
+      if (e != cudaSuccess) return cuda_fail(c, e, "history fold (K > 128)");
+    }
     if (c->opts.precision > 0) {
       // Tensor-core fold of the pending codes (compensated), then factor only.
       if (s.pending > 0) {
@@ -406,7 +417,10 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
       fa.prefolded = 1;
       fa.Alo = s.Alo;
     }
-    e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_factor(fa, c->stream); });
+    if (big_k(c))
+      e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_factor_big(fa, c->work, c->work_ctas, c->stream); });
+    else
+      e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_factor(fa, c->stream); });
     if (e != cudaSuccess) return cuda_fail(c, e, "fold_factor");
   }
   AlphaClasses ac{};
@@ -419,7 +433,10 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
   for (int t = 0; t < c->opts.Jd; ++t) {
     for (SizeClass *s : active) {
       const float rho_eff = (float)(c->opts.rho_convention == 1 ? c->rho * s->P : c->rho);
-      e = timed(c, OCSC_K_DSTEP, [&] { return launch_dstep(c->K, s->F, rho_eff, s->X, s->y, s->Vh, s->th, s->Dcur, s->E, c->stream); });
+      e = timed(c, OCSC_K_DSTEP, [&] {
+        return big_k(c) ? launch_dstep_big(c->K, s->F, rho_eff, s->X, s->y, s->Vh, s->th, s->Dcur, s->E, c->stream)
+                        : launch_dstep(c->K, s->F, rho_eff, s->X, s->y, s->Vh, s->th, s->Dcur, s->E, c->stream);
+      });
       if (e != cudaSuccess) return cuda_fail(c, e, "dstep");
       e = timed(c, OCSC_K_VSTEP_COLS, [&] { return launch_vstep_cols(c->K, s->N, c->M, s->E, s->tw, s->Y, c->stream); });
       if (e != cudaSuccess) return cuda_fail(c, e, "vstep_cols");
