@@ -305,8 +305,9 @@ def mixed_leg(pkg, dev, stream, args):
     learner.code(xs[:B], want_codes=False)
     learner.update_dict()
     learner.sync()
-    learner.profile(["fold_factor", "code_plane", "dstep"])
-    learner.profile_read(["fold_factor", "code_plane", "dstep"])
+    kinds = ["image_spectrum", "code_resid", "code_plane", "fold_factor", "dstep"]
+    learner.profile(kinds)
+    learner.profile_read(kinds)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -316,13 +317,67 @@ def mixed_leg(pkg, dev, stream, args):
     e1.record(stream)
     e1.synchronize()
     secs = e0.elapsed_time(e1) / 1e3
-    prof = learner.profile_read(["fold_factor", "code_plane", "dstep"])
+    prof = learner.profile_read(kinds)
     learner.close()
     timed = sides[B:]
     return {"workload": "batched_mixed_k100", "batch": B, "steps": nb, "value": B * nb / secs, "unit": UNIT,
             "ms_per_batch": 1e3 * secs / nb,
             "sides_in_timed_batches": {str(sd): timed.count(sd) for sd in sorted(set(timed))},
             "ms_per_batch_by_kernel": {k: v[0] / nb for k, v in prof.items()}}
+
+
+def precision_leg(pkg, dev, stream, args):
+    """Precision variants of the history fold on the full precision workload
+    (256 x 256 images padded by 32 to FFT 288, K = 256 filters 11 x 11,
+    mini-batch 128): throughput of the all-FP32 path and of the BF16
+    tensor-core fold, and how far the BF16 dictionary and objective move from
+    the FP32 path's (the errors of each path against the FP64 oracle are
+    measured by the parity tests)."""
+    import numpy as np
+    import torch
+
+    from workloads import WORKLOADS
+
+    w = WORKLOADS["precision_256_k256"]
+    B, N, nb = w.batch, 288, args.precision_steps
+    xs = [torch.from_numpy(w.image(i)).to(dev) for i in range(B * (nb + 1))]
+    test = [torch.from_numpy(w.image(w.n_images - 1 - i)).to(dev) for i in range(4)]
+    kinds = ["image_spectrum", "code_resid", "code_plane", "history_tc", "fold_factor", "dstep"]
+    out = {"workload": "precision_256_k256", "fft": N, "K": w.K, "batch": B, "steps": nb}
+    dicts, objs = {}, {}
+    for prec in (0, 1):
+        lr = pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_size=N, pad=w.pad, Jz=w.Jz, Jd=w.Jd,
+                      max_batch=B, precision=prec)
+        lr.set_dict(w.filters0(), normalize=True)
+        lr.code(xs[:B], want_codes=False)
+        lr.update_dict()
+        lr.sync()
+        lr.profile(kinds)
+        lr.profile_read(kinds)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(1, nb + 1):
+            lr.code(xs[t * B:(t + 1) * B], want_codes=False)
+            lr.update_dict()
+        e1.record(stream)
+        e1.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        prof = lr.profile_read(kinds)
+        dicts[prec] = lr.get_dict().astype(np.float64)
+        us = lr.code(test)
+        objs[prec] = float(np.mean(lr.objective(test, us)))
+        lr.drop_pending()
+        lr.close()
+        out["fp32" if prec == 0 else "bf16_tc"] = {
+            "value": B * nb / secs, "unit": UNIT, "ms_per_batch": 1e3 * secs / nb,
+            "ms_per_batch_by_kernel": {k: v[0] / nb for k, v in prof.items() if v[1]}}
+        torch.cuda.empty_cache()
+    out["bf16_vs_fp32_full_size"] = {
+        "dictionary_rel": float(np.linalg.norm(dicts[1] - dicts[0]) / np.linalg.norm(dicts[0])),
+        "objective_rel": abs(objs[1] - objs[0]) / abs(objs[0]),
+        "test_images": len(test)}
+    return out
 
 
 def serving_leg(pkg, dev, stream, args):
@@ -504,6 +559,7 @@ def ours_arm(args):
     batched = batched_leg(pkg, w, dev, stream, args) if args.batched_steps > 0 and "batched" in legs else None
     mixed = mixed_leg(pkg, dev, stream, args) if args.mixed_steps > 0 and "mixed" in legs else None
     serving = serving_leg(pkg, dev, stream, args) if args.serve_requests > 0 and "serving" in legs else None
+    precision = precision_leg(pkg, dev, stream, args) if args.precision_steps > 0 and "precision" in legs else None
 
     if rank != 0:
         return
@@ -535,6 +591,7 @@ def ours_arm(args):
         "batched": batched,
         "mixed_sizes": mixed,
         "serving": serving,
+        "precision": precision,
     }
     print(json.dumps(line))
 
@@ -584,7 +641,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--breakdown-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--legs", default="plain,batched,mixed,serving",
+    ap.add_argument("--precision-steps", type=int, default=2,
+                    help="timed batches of 128 per variant in the precision leg (0: skip)")
+    ap.add_argument("--legs", default="plain,batched,mixed,serving,precision",
                     help="comma list of legs to run (profiling runs pick one); the headline needs plain")
     ap.add_argument("--batch", type=int, default=64, help="mini-batch of the batched leg")
     ap.add_argument("--batched-steps", type=int, default=4, help="timed batches of the batched leg (0: skip)")
