@@ -40,8 +40,8 @@ FP64_PEAK_TFLOPS = SMS * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM bytes per fold_factor launch from an ncu capture of this workload
 # (profiles/fold_factor_plain_100in128_k100.md), valid only while the kernel
 # source is the one captured (sha1 of dict_update.cu).
-TRAFFIC_CAPTURE = {"bytes": 350.745856e6 + 625.610240e6,
-                   "source_sha1": "3e10f509a7572bf5ed2e5c571dc6a38ef4e95b49"}
+TRAFFIC_CAPTURE = {"bytes": 350.431488e6 + 625.599744e6,
+                   "source_sha1": "fc10b7fab38f8d2fdbee40f93efccaacb8fcd45e"}
 
 
 def captured_traffic():
@@ -597,10 +597,13 @@ def ours_arm(args):
 
 
 PROFILE_CASES = {
-    # name: (K, M, FFT size, images, image side, Jz)
-    "large512": (32, 11, 512, 4, 400, 10),
-    "large256": (32, 11, 256, 8, 200, 10),
-    "code128": (100, 11, 128, 16, 100, 10),
+    # name: (K, M, FFT size, images, image side, Jz, history precision)
+    "large512": (32, 11, 512, 4, 400, 10, 0),
+    "large256": (32, 11, 256, 8, 200, 10, 0),
+    "code128": (100, 11, 128, 16, 100, 10, 0),
+    # K = 256 dictionary step (tensor-core fold, blocked FP64 factor, substitution
+    # D-step) on the FFT 64 grid: 2112 frequencies, ~1.7 GB of history and factor.
+    "bigk64": (256, 11, 64, 8, 53, 5, 1),
 }
 
 
@@ -614,13 +617,16 @@ def profile_case(name: str) -> None:
     from workloads import make_image, raw_filters
 
     _build.build()
-    K, M, N, n, side, Jz = PROFILE_CASES[name]
-    lr = pkg.OCSC(K, M, 1.0, 1.0, fft_size=N, pad=M - 1, Jz=Jz, Jd=2, max_batch=n)
+    K, M, N, n, side, Jz, prec = PROFILE_CASES[name]
+    lr = pkg.OCSC(K, M, 1.0, 1.0, fft_size=N, pad=M - 1, Jz=Jz, Jd=2, max_batch=n, precision=prec)
     lr.set_dict(raw_filters(K, M, 3), normalize=True)
     xs = [torch.from_numpy(make_image(side, side, 100 + i)).cuda() for i in range(n)]
     for rep in range(2):
         lr.code(xs, want_codes=False)
-        lr.drop_pending()
+        if prec:
+            lr.update_dict()
+        else:
+            lr.drop_pending()
     lr.sync()
     lr.close()
     print(json.dumps({"profile_case": name, "K": K, "N": N, "images": n, "Jz": Jz, "ok": True}))
