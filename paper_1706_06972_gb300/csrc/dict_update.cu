@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
       atomicOr(a.err, ERR_PIVOT);
       piv = a.rho_eff > 0.0 ? a.rho_eff : 1.0;
     }
-    const double l = sqrt(piv);
-    M[0] = make_double2(l, 0.0);
-    invd[0] = 1.0 / l;
+    const double r = rsqrt(piv);  // 1 / L_00; L_00 = piv / sqrt(piv)
+    M[0] = make_double2(piv * r, 0.0);
+    invd[0] = r;
   }
   __syncthreads();
   for (int j = 0; j <= K; ++j) {
@@ -200,31 +200,19 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
           atomicOr(a.err, ERR_PIVOT);
           piv = a.rho_eff > 0.0 ? a.rho_eff : 1.0;
         }
-        const double lj = sqrt(piv);
-        M[d1] = make_double2(lj, 0.0);
-        invd[j + 1] = 1.0 / lj;
+        const double r = rsqrt(piv);
+        M[d1] = make_double2(piv * r, 0.0);
+        invd[j + 1] = r;
       }
-      for (int u = 1 + tid; u < nt; u += 2 * kFoldThreads) {
-        const int u2 = u + kFoldThreads;
-        int ii, kk, ii2 = 0, kk2 = 0;
+      // One element per thread and round: only the last warp of the last
+      // round runs with idle lanes.
+      for (int u = 1 + tid; u < nt; u += kFoldThreads) {
+        int ii, kk;
         tri_ij(u, n, ii, kk);
-        const bool two = u2 < nt;
-        if (two) tri_ij(u2, n, ii2, kk2);
         const int dst = tri_off(j + 1 + kk, K) + ii - kk;
         double2 v = M[dst];
-        const double2 lij = M[oj + 1 + ii], lkj = M[oj + 1 + kk];
-        int dst2 = dst;
-        double2 v2 = v, lij2 = lij, lkj2 = lkj;
-        if (two) {
-          dst2 = tri_off(j + 1 + kk2, K) + ii2 - kk2;
-          v2 = M[dst2];
-          lij2 = M[oj + 1 + ii2];
-          lkj2 = M[oj + 1 + kk2];
-        }
-        cfms_conj(v, lij, lkj);
-        cfms_conj(v2, lij2, lkj2);
+        cfms_conj(v, M[oj + 1 + ii], M[oj + 1 + kk]);
         M[dst] = v;
-        if (two) M[dst2] = v2;
       }
       for (int u = tid; u < n; u += kFoldThreads) {
         const int i = j + 1 + u;
