@@ -92,6 +92,24 @@ typedef struct {
                             pair of FP32 words (A + Alo) across the stream;
                          2: as 1 with each code split into two BF16 words
                             (hi + lo; products hi hi + hi lo + lo hi). */
+  int autotune;       /* 1 (default): at a size class's first use, time the
+                         candidate tile shapes on its own buffers and keep the
+                         fastest: threads per CTA of the FP64 factorisation
+                         (256 or 512), columns per CTA of the N >= 256 spatial
+                         FFT kernel in ocsc_code (8 or 16), samples per chunk
+                         of the tensor-core contraction (32, 64, 128).  Every
+                         candidate performs the same operations in the same
+                         order, so results do not depend on the choice.
+                         0: fixed defaults (256, the size's default, largest
+                         chunk that fits). */
+  int graphs;         /* 1: ocsc_code replays a CUDA graph per chunk shape
+                         (class, image count, first slot, image sizes, codes
+                         requested or not): the second call with a shape
+                         captures the sample spectra and the Jz iterations,
+                         later calls copy their images into library staging
+                         slots and launch the graph (codes are copied out).
+                         Not used while kernels are being profiled.  0
+                         (default): every launch is issued directly. */
 } ocsc_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -174,6 +192,14 @@ ocsc_status ocsc_set_dict(ocsc_ctx *ctx, const float *D_host, int normalize);
  */
 ocsc_status ocsc_get_state(ocsc_ctx *ctx, void *buf, size_t *len);
 ocsc_status ocsc_set_state(ocsc_ctx *ctx, const void *buf, size_t len);
+
+/* Tile shapes in use for FFT size N (0 where not tuned yet or not used). */
+typedef struct {
+  int fold_threads; /* CTA size of the K <= 128 fold + FP64 factorisation */
+  int spat_cb;      /* columns per CTA of the N >= 256 spatial kernel in ocsc_code */
+  int gram_sc;      /* samples per chunk of the tensor-core contraction */
+} ocsc_tuning;
+ocsc_status ocsc_get_tuning(const ocsc_ctx *ctx, int N, ocsc_tuning *out);
 
 /* Block until all work queued on ctx's stream is done; reports device errors. */
 ocsc_status ocsc_sync(ocsc_ctx *ctx);
@@ -281,6 +307,8 @@ typedef struct {
   uint64_t kernel_launches; /* kernels launched by this context so far */
   uint64_t samples_coded;   /* samples passed to ocsc_code */
   uint64_t dict_updates;    /* completed ocsc_update_dict calls that folded samples */
+  uint64_t graph_launches;  /* CUDA graph replays of ocsc_code (opts.graphs); their
+                               kernels are included in kernel_launches */
 } ocsc_counters;
 
 /* Counters of ctx (host-side bookkeeping; no synchronisation). */

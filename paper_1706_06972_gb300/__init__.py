@@ -34,13 +34,18 @@ class ocsc_opts(ctypes.Structure):
         ("Jz", ctypes.c_int), ("Jd", ctypes.c_int), ("pad", ctypes.c_int),
         ("max_batch", ctypes.c_int), ("fft_sizes", ctypes.c_int * 4), ("warm_start", ctypes.c_int),
         ("return_feasible", ctypes.c_int), ("rho_convention", ctypes.c_int),
-        ("seed", ctypes.c_uint64), ("precision", ctypes.c_int),
+        ("seed", ctypes.c_uint64), ("precision", ctypes.c_int), ("autotune", ctypes.c_int),
+        ("graphs", ctypes.c_int),
     ]
+
+
+class ocsc_tuning(ctypes.Structure):
+    _fields_ = [("fold_threads", ctypes.c_int), ("spat_cb", ctypes.c_int), ("gram_sc", ctypes.c_int)]
 
 
 class ocsc_counters(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("samples_coded", ctypes.c_uint64),
-                ("dict_updates", ctypes.c_uint64)]
+                ("dict_updates", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64)]
 
 
 class ocsc_server_opts(ctypes.Structure):
@@ -73,6 +78,7 @@ _PROTOS = {
     "ocsc_last_error": (ctypes.c_char_p, [_P]),
     "ocsc_drop_pending": (_I, [_P]),
     "ocsc_get_state": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    "ocsc_get_tuning": (_I, [_P, _I, _P]),
     "ocsc_set_state": (_I, [_P, _P, ctypes.c_size_t]),
     "ocsc_objective": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double)]),
@@ -186,6 +192,12 @@ def ocsc_get_state(ctx) -> bytes:
     buf = ctypes.create_string_buffer(n.value)
     _check(ctx, lib().ocsc_get_state(ctx, buf, ctypes.byref(n)))
     return buf.raw[: n.value]
+
+
+def ocsc_get_tuning(ctx, N: int) -> dict:
+    t = ocsc_tuning()
+    _check(ctx, lib().ocsc_get_tuning(ctx, N, ctypes.byref(t)))
+    return {"fold_threads": t.fold_threads, "spat_cb": t.spat_cb, "gram_sc": t.gram_sc}
 
 
 def ocsc_set_state(ctx, state: bytes) -> None:
@@ -333,6 +345,10 @@ class OCSC:
         """Checkpoint of the learner (no samples may be pending)."""
         return ocsc_get_state(self.ctx)
 
+    def tuning(self, N: int) -> dict:
+        """Tile shapes the autotuner picked for FFT size N."""
+        return ocsc_get_tuning(self.ctx, N)
+
     def set_state(self, state: bytes) -> None:
         """Load a checkpoint saved by a learner of the same shape and parameters."""
         ocsc_set_state(self.ctx, state)
@@ -347,7 +363,7 @@ class OCSC:
     def counters(self) -> dict:
         c = ocsc_get_counters(self.ctx)
         return {"kernel_launches": c.kernel_launches, "samples_coded": c.samples_coded,
-                "dict_updates": c.dict_updates}
+                "dict_updates": c.dict_updates, "graph_launches": c.graph_launches}
 
     def profile(self, kernels=KERNELS):
         """Time every launch of the named kernel classes with CUDA events."""

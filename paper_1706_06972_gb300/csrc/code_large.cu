@@ -52,21 +52,28 @@ struct LargeGeom {
   static constexpr int EPT = (2 * NH + kLargeThreads - 1) / kLargeThreads;  // row bins per thread
   static constexpr int SPT = N * CB / kLargeThreads;                        // spatial elements per thread
   static constexpr int CH = SPT % 4 == 0 ? 4 : (SPT % 3 == 0 ? 3 : (SPT % 2 == 0 ? 2 : 1));
-  static_assert(N % CB == 0 && CB % 2 == 0 && N * CB % kLargeThreads == 0, "spatial tiling");
-  static_assert(N * (CB / 2) % kLargeThreads == 0, "spatial copies");
 };
 
 // Spectral CTA: two stage buffers of NL lines (pass 1 is double-buffered)
 // and the twiddles; spatial CTA: its N x CB block and the twiddles.
 template <int N>
 __host__ __device__ constexpr int spec_lines() { return 2 * LargeGeom<N>::NL; }
+// Spatial CTA geometry for a block of CB columns (CB even, dividing N).
+template <int N, int CB_>
+struct SpatGeom {
+  static constexpr int CB = CB_, NCB = N / CB, P = N * N;
+  static constexpr int SPT = N * CB / kLargeThreads;  // elements per thread
+  static constexpr int CH = SPT % 4 == 0 ? 4 : (SPT % 3 == 0 ? 3 : (SPT % 2 == 0 ? 2 : 1));
+  static_assert(N % CB == 0 && CB % 2 == 0 && N * CB % kLargeThreads == 0, "spatial tiling");
+};
+
 template <int N>
 size_t spec_smem_bytes() {
   return (size_t)spec_lines<N>() * LargeGeom<N>::PITCH * sizeof(float2) + (size_t)N * sizeof(float2);
 }
-template <int N>
+template <int N, int CB>
 size_t spat_smem_bytes() {
-  return (size_t)N * LargeGeom<N>::CB * sizeof(float2) + (size_t)N * sizeof(float2);
+  return (size_t)N * CB * sizeof(float2) + (size_t)N * sizeof(float2);
 }
 
 __device__ __forceinline__ float soft_thr(float v, float t) { return v > t ? v - t : (v < -t ? v + t : 0.0f); }
@@ -388,30 +395,32 @@ __global__ void __launch_bounds__(kLargeThreads, 3)
 // q1 * CB + l.
 // Block <- columns c0 .. c0 + CB - 1 of a tile (asynchronous 16-byte copies;
 // the caller commits and waits).
-template <int N>
+template <int N, int CB>
 __device__ __forceinline__ void load_cols_async(float2 *blk, const float2 *tile, int c0) {
   using G = LargeGeom<N>;
-  constexpr int V = G::CB / 2;
-  constexpr int TRIPS = N * V / kLargeThreads;
+  using S = SpatGeom<N, CB>;
+  constexpr int V = S::CB / 2;
+  constexpr int TRIPS = (N * V + kLargeThreads - 1) / kLargeThreads;
 #pragma unroll
   for (int s = 0; s < TRIPS; ++s) {
     const int e = threadIdx.x + s * kLargeThreads;
     const int k1 = e / V, c = e % V;
-    cp_async16(blk + k1 * G::CB + 2 * c, tile + (size_t)k1 * N + c0 + 2 * c);
+    if (N * V % kLargeThreads == 0 || e < N * V) cp_async16(blk + k1 * S::CB + 2 * c, tile + (size_t)k1 * N + c0 + 2 * c);
   }
 }
 
-template <int N>
+template <int N, int CB>
 __device__ __forceinline__ void store_cols(const float2 *blk, float2 *tile, int c0) {
   using G = LargeGeom<N>;
-  constexpr int V = G::CB / 2;
-  constexpr int TRIPS = N * V / kLargeThreads;
+  using S = SpatGeom<N, CB>;
+  constexpr int V = S::CB / 2;
+  constexpr int TRIPS = (N * V + kLargeThreads - 1) / kLargeThreads;
 #pragma unroll
   for (int s = 0; s < TRIPS; ++s) {
     const int e = threadIdx.x + s * kLargeThreads;
     const int k1 = e / V, c = e % V;
-    *reinterpret_cast<float4 *>(tile + (size_t)k1 * N + c0 + 2 * c) =
-        *reinterpret_cast<const float4 *>(blk + k1 * G::CB + 2 * c);
+    if (N * V % kLargeThreads == 0 || e < N * V) *reinterpret_cast<float4 *>(tile + (size_t)k1 * N + c0 + 2 * c) =
+        *reinterpret_cast<const float4 *>(blk + k1 * S::CB + 2 * c);
   }
 }
 
@@ -420,15 +429,16 @@ __device__ __forceinline__ void store_cols(const float2 *blk, float2 *tile, int 
 // MODE 1: zero-padded images in, forward column transforms out (grid: NCB x 1 x images);
 // MODE 2: real planes 2j, 2j+1 in, forward column transforms out (grid: NCB x pairs);
 // MODE 3: inverse column transforms, real planes out (c2r; grid: NCB x pairs).
-template <int N, int MODE>
-__global__ void __launch_bounds__(kLargeThreads, 4)
+template <int N, int CB, int MODE>
+__global__ void __launch_bounds__(kLargeThreads, N * CB > 4608 ? 2 : 4)
     large_spat_kernel(CodeIter it, ImgBatch b, LargeIO io, const float2 *__restrict__ tw) {
   using G = LargeGeom<N>;
+  using S = SpatGeom<N, CB>;
   extern __shared__ float2 lsm[];
   float2 *blk = lsm;  // [N][CB]
-  float2 *s_tw = lsm + N * G::CB;
+  float2 *s_tw = lsm + N * S::CB;
   for (int i = threadIdx.x; i < N; i += kLargeThreads) s_tw[i] = tw[i];
-  const int cb = blockIdx.x, c0 = cb * G::CB;
+  const int cb = blockIdx.x, c0 = cb * S::CB;
   const int pair = blockIdx.y, img = blockIdx.z;
 
   if (MODE == 1) {
@@ -437,14 +447,14 @@ __global__ void __launch_bounds__(kLargeThreads, 4)
     const float *x = b.x[img];
     const int H = b.H[img], W = b.W[img];
 #pragma unroll 4
-    for (int s = 0; s < G::SPT; ++s) {
+    for (int s = 0; s < S::SPT; ++s) {
       const int e = threadIdx.x + s * kLargeThreads;
-      const int q1 = e / G::CB, q2 = c0 + e % G::CB;
+      const int q1 = e / S::CB, q2 = c0 + e % S::CB;
       blk[e] = make_float2((q1 < H && q2 < W) ? x[(size_t)q1 * W + q2] : 0.f, 0.f);
     }
     __syncthreads();
-    fft_lines<N, G::CB, false, kLargeThreads>(blk, 1, G::CB, s_tw);
-    store_cols<N>(blk, tile, c0);
+    fft_lines<N, S::CB, false, kLargeThreads>(blk, 1, S::CB, s_tw);
+    store_cols<N, CB>(blk, tile, c0);
     return;
   }
   if (MODE == 2) {
@@ -453,30 +463,30 @@ __global__ void __launch_bounds__(kLargeThreads, 4)
     const float *xa = io.real_in + (size_t)pa * G::P;
     const float *xb = io.real_in + (size_t)pb * G::P;
 #pragma unroll 4
-    for (int s = 0; s < G::SPT; ++s) {
+    for (int s = 0; s < S::SPT; ++s) {
       const int e = threadIdx.x + s * kLargeThreads;
-      const size_t o = (size_t)(e / G::CB) * N + c0 + e % G::CB;
+      const size_t o = (size_t)(e / S::CB) * N + c0 + e % S::CB;
       blk[e] = make_float2(xa[o], hasb ? xb[o] : 0.f);
     }
     __syncthreads();
-    fft_lines<N, G::CB, false, kLargeThreads>(blk, 1, G::CB, s_tw);
-    store_cols<N>(blk, io.T + (size_t)pair * G::P, c0);
+    fft_lines<N, S::CB, false, kLargeThreads>(blk, 1, S::CB, s_tw);
+    store_cols<N, CB>(blk, io.T + (size_t)pair * G::P, c0);
     return;
   }
   if (MODE == 3) {
-    load_cols_async<N>(blk, io.T + (size_t)pair * G::P, c0);
+    load_cols_async<N, CB>(blk, io.T + (size_t)pair * G::P, c0);
     cp_async_wait_all();
     __syncthreads();
-    fft_lines<N, G::CB, true, kLargeThreads>(blk, 1, G::CB, s_tw);
+    fft_lines<N, S::CB, true, kLargeThreads>(blk, 1, S::CB, s_tw);
     const int pa = 2 * pair, pb = pa + 1;
     const bool hasb = pb < io.planes;
     float *xa = io.real_out + (size_t)pa * G::P;
     float *xb = io.real_out + (size_t)pb * G::P;
     const float invP = 1.0f / (float)G::P;
 #pragma unroll 4
-    for (int s = 0; s < G::SPT; ++s) {
+    for (int s = 0; s < S::SPT; ++s) {
       const int e = threadIdx.x + s * kLargeThreads;
-      const size_t o = (size_t)(e / G::CB) * N + c0 + e % G::CB;
+      const size_t o = (size_t)(e / S::CB) * N + c0 + e % S::CB;
       const float2 c = blk[e];
       xa[o] = c.x * invP;
       if (hasb) xb[o] = c.y * invP;
@@ -494,22 +504,22 @@ __global__ void __launch_bounds__(kLargeThreads, 4)
   const bool skip_fwd = !it.serve && it.last;
   const bool resid = it.serve && store_last;
   float2 *tile = io.T + ((size_t)slot * io.tile_pairs + pair) * G::P;
-  load_cols_async<N>(blk, tile, c0);
+  load_cols_async<N, CB>(blk, tile, c0);
   cp_async_wait_all();
   // U of this column block, [q1][l] like blk, contiguous.
-  float *Sa = it.Gam + ((size_t)slot * K + ka) * G::P + (size_t)cb * N * G::CB;
-  float *Sb = it.Gam + ((size_t)slot * K + (hasb ? kb : ka)) * G::P + (size_t)cb * N * G::CB;
+  float *Sa = it.Gam + ((size_t)slot * K + ka) * G::P + (size_t)cb * N * S::CB;
+  float *Sb = it.Gam + ((size_t)slot * K + (hasb ? kb : ka)) * G::P + (size_t)cb * N * S::CB;
   __syncthreads();
-  fft_lines<N, G::CB, true, kLargeThreads>(blk, 1, G::CB, s_tw);
+  fft_lines<N, S::CB, true, kLargeThreads>(blk, 1, S::CB, s_tw);
   // The code output doubles as the store of Gamma from the iteration before
   // a residual check (serving), where Z = V - Gamma_prev is needed.
   float *Ua = b.u[img] ? b.u[img] + (size_t)ka * G::P : nullptr;
   float *Ub = (b.u[img] && hasb) ? b.u[img] + (size_t)kb * G::P : nullptr;
   const float invP = 1.0f / (float)G::P;
   float acc[kResidTerms] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  constexpr int CH = G::CH;  // state loads in flight per thread
+  constexpr int CH = S::CH;  // state loads in flight per thread
 #pragma unroll 1
-  for (int s0 = 0; s0 < G::SPT; s0 += CH) {
+  for (int s0 = 0; s0 < S::SPT; s0 += CH) {
     float pa[CH], pb[CH];
 #pragma unroll
     for (int u = 0; u < CH; ++u) {
@@ -520,7 +530,7 @@ __global__ void __launch_bounds__(kLargeThreads, 4)
 #pragma unroll
     for (int u = 0; u < CH; ++u) {
       const int e = threadIdx.x + (s0 + u) * kLargeThreads;
-      const size_t o = (size_t)(e / G::CB) * N + c0 + e % G::CB;
+      const size_t o = (size_t)(e / S::CB) * N + c0 + e % S::CB;
       const float2 c = blk[e];
       const float va = pa[u] + c.x * invP, vb = pb[u] + c.y * invP;
       const float ua = soft_thr(va, it.thr), ub = soft_thr(vb, it.thr);
@@ -545,11 +555,11 @@ __global__ void __launch_bounds__(kLargeThreads, 4)
     }
   }
   if (resid)
-    block_terms(acc, it.resid + (((size_t)slot * npairs + pair) * G::NCB + cb) * kResidTerms);
+    block_terms(acc, it.resid + (((size_t)slot * npairs + pair) * S::NCB + cb) * kResidTerms);
   if (skip_fwd) return;
   __syncthreads();
-  fft_lines<N, G::CB, false, kLargeThreads>(blk, 1, G::CB, s_tw);
-  store_cols<N>(blk, tile, c0);
+  fft_lines<N, S::CB, false, kLargeThreads>(blk, 1, S::CB, s_tw);
+  store_cols<N, CB>(blk, tile, c0);
 }
 
 // ---------------------------------------------------------------------------
@@ -570,11 +580,31 @@ static cudaError_t go(Kern k, dim3 grid, size_t sm, const CodeIter &it, const Im
   return cudaGetLastError();
 }
 
+template <int N, int CB>
+static cudaError_t spat_n(int what, const CodeIter &it, const ImgBatch &b, const LargeIO &io, int n, int npairs,
+                          const float2 *tw, cudaStream_t s) {
+  constexpr int NCB = N / CB;
+  const size_t ss = spat_smem_bytes<N, CB>();
+  switch (what) {
+    case LARGE_SPAT_ADMM: return go(large_spat_kernel<N, CB, 0>, dim3(NCB, npairs, n), ss, it, b, io, tw, s);
+    case LARGE_SPAT_IMAGE: return go(large_spat_kernel<N, CB, 1>, dim3(NCB, 1, n), ss, it, b, io, tw, s);
+    case LARGE_SPAT_R2C: return go(large_spat_kernel<N, CB, 2>, dim3(NCB, npairs, 1), ss, it, b, io, tw, s);
+    case LARGE_SPAT_C2R: return go(large_spat_kernel<N, CB, 3>, dim3(NCB, npairs, 1), ss, it, b, io, tw, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int N>
 static cudaError_t large_n(int what, const CodeIter &it, const ImgBatch &b, const LargeIO &io, int n,
                            int npairs, const float2 *tw, cudaStream_t s) {
   using G = LargeGeom<N>;
-  const size_t sp = spec_smem_bytes<N>(), ss = spat_smem_bytes<N>();
+  if (what >= LARGE_SPAT_ADMM) {
+    const int cb = io.spat_cb ? io.spat_cb : G::CB;
+    if (cb == 8) return spat_n<N, 8>(what, it, b, io, n, npairs, tw, s);
+    if (cb == 16) return spat_n<N, 16>(what, it, b, io, n, npairs, tw, s);
+    return cudaErrorInvalidValue;
+  }
+  const size_t sp = spec_smem_bytes<N>();
   const int S = (npairs + G::GP - 1) / G::GP;
   const dim3 gs(n, N / 2), gz(n, N / 2, S), gp(1, N / 2, S);
   switch (what) {
@@ -583,10 +613,6 @@ static cudaError_t large_n(int what, const CodeIter &it, const ImgBatch &b, cons
     case LARGE_SPEC_IMAGE: return go(large_spec_kernel<N, 1>, gs, sp, it, b, io, tw, s);
     case LARGE_SPEC_R2C: return go(large_spec_kernel<N, 2>, gp, sp, it, b, io, tw, s);
     case LARGE_SPEC_C2R: return go(large_spec_kernel<N, 3>, gp, sp, it, b, io, tw, s);
-    case LARGE_SPAT_ADMM: return go(large_spat_kernel<N, 0>, dim3(G::NCB, npairs, n), ss, it, b, io, tw, s);
-    case LARGE_SPAT_IMAGE: return go(large_spat_kernel<N, 1>, dim3(G::NCB, 1, n), ss, it, b, io, tw, s);
-    case LARGE_SPAT_R2C: return go(large_spat_kernel<N, 2>, dim3(G::NCB, npairs, 1), ss, it, b, io, tw, s);
-    case LARGE_SPAT_C2R: return go(large_spat_kernel<N, 3>, dim3(G::NCB, npairs, 1), ss, it, b, io, tw, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -599,6 +625,15 @@ cudaError_t launch_large(int N, int what, const CodeIter &it, const ImgBatch &b,
     case 288: return large_n<288>(what, it, b, io, n, npairs, tw, s);
     case 512: return large_n<512>(what, it, b, io, n, npairs, tw, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+int large_default_cb(int N) {
+  switch (N) {
+    case 256: return LargeGeom<256>::CB;
+    case 288: return LargeGeom<288>::CB;
+    case 512: return LargeGeom<512>::CB;
+    default: return 0;
   }
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdarg>
 #include <cstdio>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -41,7 +42,20 @@ struct SizeClass {
   float2 *obj_xh = nullptr; // [F]
   long long n_seen = 0;
   int pending = 0;
+  // tile shapes picked by the autotuner (0 = not tuned yet)
+  int fold_threads = 0, spat_cb = 0, gram_sc = 0;
+  // graph path of ocsc_code: image and code staging per slot (lazily allocated)
+  float *xstage = nullptr;  // [max_batch][N*N]
+  float *ustage = nullptr;  // [max_batch][K][N*N]
 };
+
+// A captured coding graph of one chunk shape.
+struct GraphEntry {
+  std::string key;
+  cudaGraphExec_t exec = nullptr;
+  size_t kernels = 0;  // kernel nodes per replay
+};
+constexpr size_t kMaxGraphs = 32;
 
 }  // namespace ocsc
 
@@ -61,6 +75,9 @@ struct ocsc_ctx {
   uint64_t version = 0;
   std::string msg;
   std::vector<void *> allocs;
+  std::vector<ocsc::GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;  // capture stream of the graph path
+  std::set<std::string> graph_seen;
   ocsc_counters counters{};
   unsigned prof_mask = 0;
   std::vector<cudaEvent_t> prof_ev[OCSC_K_COUNT];  // start/stop pairs
@@ -138,6 +155,32 @@ cudaError_t timed(ocsc_ctx *c, int id, Fn &&fn) {
 // K above this uses the dict_big.cu kernels (matrix outside shared memory).
 constexpr int kSmallK = 128;
 inline bool big_k(const ocsc_ctx *c) { return c->K > kSmallK; }
+
+// Mean duration in ms of reps runs of fn (which enqueues on the context's
+// stream); negative on a launch error.  Used by the autotuner.
+template <typename Fn>
+float time_runs(ocsc_ctx *c, int reps, Fn &&fn) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1.f;
+  }
+  float ms = -1.f;
+  bool ok = cudaEventRecord(e0, c->stream) == cudaSuccess;
+  for (int r = 0; ok && r < reps; ++r) {
+    ok = fn() == cudaSuccess;
+    c->counters.kernel_launches++;
+  }
+  if (ok && cudaEventRecord(e1, c->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+    ms /= (float)reps;
+  else
+    ms = -1.f;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
+}
 
 inline const float2 *coding_spectrum(const ocsc_ctx *c, const SizeClass &s) {
   return c->opts.return_feasible ? s.Vh : s.Dcur;

@@ -32,7 +32,6 @@ __device__ __forceinline__ void cfms(double2 &acc, double2 a, double2 b) {
   acc.y = fma(-a.y, b.x, acc.y);
 }
 
-constexpr int kFoldThreads = 256;
 constexpr int kFoldChunk = 16;  // samples staged in shared memory at once
 
 // One CTA per frequency p.
@@ -55,6 +54,7 @@ constexpr int kFoldChunk = 16;  // samples staged in shared memory at once
 // float2, Xrow [K] float2, zs / xs (a chunk of pending codes).  During the
 // fold each M slot first holds the FP32 running sum of conj(z_i) z_j in its low
 // 8 bytes.
+template <int kFoldThreads>
 __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int K = a.K, F = a.F, B = a.B;
@@ -112,9 +112,12 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
     double hx, hy;
     if (a.prefolded) {  // A (+ its compensation word) already holds the new mean
       const float2 h = Ap[t];
-      const float2 l = Lo ? Lo[t] : make_float2(0.f, 0.f);
-      hx = (double)h.x + (double)l.x;
-      hy = (double)h.y + (double)l.y;
+      hx = h.x;
+      hy = h.y;
+      if (Lo) {
+        hx += (double)Lo[t].x;
+        hy += (double)Lo[t].y;
+      }
     } else {
       const float2 old = a.first ? make_float2(0.f, 0.f) : Ap[t];
       const float2 sum = S[2 * t];
@@ -442,11 +445,20 @@ size_t fold_smem_bytes(int K) {
          (size_t)3 * K * sizeof(float2) + (size_t)kFoldChunk * K * sizeof(float2) + kFoldChunk * sizeof(float2);
 }
 
-cudaError_t launch_fold_factor(const FoldArgs &a, cudaStream_t s) {
+// threads: 256 or 512 (CTA size of the per-frequency factorisation; every
+// entry sees the same operations in the same order either way).
+cudaError_t launch_fold_factor(const FoldArgs &a, int threads, cudaStream_t s) {
   const size_t sm = fold_smem_bytes(a.K);
-  cudaError_t e = cudaFuncSetAttribute(fold_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  fold_factor_kernel<<<a.F, kFoldThreads, sm, s>>>(a);
+  cudaError_t e;
+  if (threads == 512) {
+    e = cudaFuncSetAttribute(fold_factor_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    fold_factor_kernel<512><<<a.F, 512, sm, s>>>(a);
+  } else {
+    e = cudaFuncSetAttribute(fold_factor_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    fold_factor_kernel<256><<<a.F, 256, sm, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

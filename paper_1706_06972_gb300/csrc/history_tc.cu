@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_fold_tc_kernel(GramArgs a)
     if (!ok) break;
 
     // (d) b, on the first pass: per-row partial sums added in a fixed order.
-    if (first_pass) {
+    if (first_pass && !a.dry) {
       bpart[g0 * ROWS + row] = bacc;
       __syncthreads();
       for (int r = tid; r < K; r += kTcThreads) {
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_fold_tc_kernel(GramArgs a)
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int j = cc * 8 + e;
-        if (m >= K || j > m) continue;
+        if (m >= K || j > m || a.dry) continue;
         const size_t t = (size_t)tri_off(j, K) + m - j;
         if (a.first) {
           const float2 h = make_float2(a.beta * re[e], a.beta * im[e]);

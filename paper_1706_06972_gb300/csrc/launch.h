@@ -70,6 +70,8 @@ struct LargeIO {
   float *real_out;        // c2r output planes [planes][N][N]
   int planes;             // planes of an r2c / c2r call
   int tile_pairs;         // tiles per slot (ceil(K / 2)) for the ADMM and sample-spectrum modes
+  int spat_cb;            // columns per spatial CTA, 8 or 16 (0: the size's default; serving
+                          // residual partials assume the default)
 };
 enum {
   LARGE_SPEC_DOT, LARGE_SPEC_Z, LARGE_SPEC_IMAGE, LARGE_SPEC_R2C, LARGE_SPEC_C2R,
@@ -81,6 +83,8 @@ enum {
 // SPEC_IMAGE; r2c SPAT_R2C then SPEC_R2C; c2r SPEC_C2R then SPAT_C2R.
 cudaError_t launch_large(int N, int what, const CodeIter &it, const ImgBatch &b, const LargeIO &io,
                          int n, int npairs, const float2 *tw, cudaStream_t s);
+// Default columns per spatial CTA (the serving residual partials assume it).
+int large_default_cb(int N);
 // Stages of filter pairs per spectral CTA row (sizes CodeIter::part).
 int large_stages(int N, int npairs);
 // Residual partial sums per slot written by SPAT_ADMM in serving mode.
@@ -102,13 +106,14 @@ struct FoldArgs {
   int prefolded;
   const float2 *Alo;
 };
-cudaError_t launch_fold_factor(const FoldArgs &a, cudaStream_t s);
+cudaError_t launch_fold_factor(const FoldArgs &a, int threads, cudaStream_t s);
 
 // Tensor-core history fold (history_tc.cu): A, Alo <- compensated
 // alpha (A + Alo) + beta sum_i conj(z_i) z_i^T with BF16 operands (terms = 1)
 // or split BF16 hi + lo (terms = 3) and FP32 accumulation; b in FP32.
 struct GramArgs {
   int K, F, B, first, terms, SC;
+  int dry;                  // 1: compute the sums but store nothing (timing runs)
   float alpha, beta, keep;  // keep = 1 - alpha = B beta
   const float2 *Zp;         // [B][K][F]
   const float2 *xh;         // [B][F]

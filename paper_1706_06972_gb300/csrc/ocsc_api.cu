@@ -150,6 +150,8 @@ void ocsc_default_opts(ocsc_opts *o) {
   o->return_feasible = 1;
   o->rho_convention = 0;
   o->precision = 0;
+  o->autotune = 1;
+  o->graphs = 0;
   o->seed = 0x5EEDull;
 }
 
@@ -158,6 +160,8 @@ const char *ocsc_last_error(const ocsc_ctx *ctx) { return ctx ? ctx->msg.c_str()
 void ocsc_destroy(ocsc_ctx *ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  for (ocsc::GraphEntry &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   for (void *p : ctx->allocs) cudaFree(p);
   for (auto &v : ctx->prof_ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
@@ -251,11 +255,167 @@ ocsc_status ocsc_padded_size(const ocsc_ctx *ctx, int H, int W, int *N) {
   return OCSC_OK;
 }
 
+// Enqueue the coding of one chunk of images of one class (sample spectra and
+// Jz ADMM iterations) for the images, outputs and slots in bt.
+static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) {
+  const int npairs = (c->K + 1) / 2;
+  LargeIO io{};
+  io.T = s.tiles;
+  io.tile_pairs = npairs;
+  cudaError_t e;
+  if (large_fft(s.N)) {
+    io.spec_out = s.xhp;
+    CodeIter none{};
+    e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_SPAT_IMAGE, none, bt, io, bt.n, 1, s.tw, c->stream); });
+    if (e == cudaSuccess)
+      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_SPEC_IMAGE, none, bt, io, bt.n, 1, s.tw, c->stream); });
+  } else {
+    e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(s.N, bt, s.tw, s.xhp, c->stream); });
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "image spectrum");
+  CodeIter it{};
+  it.K = c->K;
+  it.F = s.F;
+  it.thr = (float)(c->lam / c->rho);
+  it.Dh = coding_spectrum(c, s);
+  it.r = s.r;
+  it.What = s.What;
+  it.Gam = s.Gam;
+  it.Zp = s.Zp;
+  it.serve = 0;
+  it.check = 1;
+  it.rho = (float)c->rho;
+  it.dn = s.dn;
+  it.xh = s.xhp;
+  it.part = s.part;
+  it.cnt = s.cnt;
+  if (large_fft(s.N)) {
+    if (s.spat_cb == 0) {
+      s.spat_cb = large_default_cb(s.N);
+      if (c->opts.autotune) {
+        // Time both spatial tile widths on this call's slots before the first
+        // iteration (which rewrites every tile row and all U it touches).
+        CodeIter tt = it;
+        tt.first = 1;
+        tt.last = 0;
+        float best = -1.f;
+        for (int cb : {8, 16}) {
+          LargeIO tio = io;
+          tio.spat_cb = cb;
+          const float ms = time_runs(c, 2, [&] {
+            return launch_large(s.N, LARGE_SPAT_ADMM, tt, bt, tio, bt.n, npairs, s.tw, c->stream);
+          });
+          if (ms < 0.f) return cuda_fail(c, cudaGetLastError(), "autotune spatial tile");
+          if (best < 0.f || ms < best) {
+            best = ms;
+            s.spat_cb = cb;
+          }
+        }
+      }
+    }
+    io.spat_cb = s.spat_cb;
+  }
+  for (int t = 0; t < c->opts.Jz; ++t) {
+    it.first = t == 0;
+    it.last = t == c->opts.Jz - 1;
+    if (large_fft(s.N)) {
+      e = cudaSuccess;
+      if (!it.first)
+        e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_large(s.N, LARGE_SPEC_DOT, it, bt, io, bt.n, npairs, s.tw, c->stream); });
+      if (e == cudaSuccess)
+        e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_large(s.N, LARGE_SPEC_Z, it, bt, io, bt.n, npairs, s.tw, c->stream); });
+      if (e == cudaSuccess)
+        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(s.N, LARGE_SPAT_ADMM, it, bt, io, bt.n, npairs, s.tw, c->stream); });
+    } else {
+      e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(s.N, bt, it, (float)c->rho, s.dn, s.xhp, c->stream); });
+      if (e == cudaSuccess)
+        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(s.N, it, bt, s.tw, c->stream); });
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "code iteration");
+  }
+  return OCSC_OK;
+}
+
+// Graph path of one chunk: images copied into the class's staging slots, the
+// captured coding graph of this chunk shape replayed, codes copied out.  A
+// shape is captured at its second occurrence (the first runs eagerly, which
+// also autotunes); false = not handled here (caller runs it eagerly).
+static bool graph_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &user, ocsc_status *st) {
+  *st = OCSC_OK;
+  if (!c->opts.graphs || c->prof_mask) return false;
+  bool want_u = false;
+  std::string key = std::to_string(s.N) + ":" + std::to_string(user.n) + ":" + std::to_string(user.slot[0]);
+  for (int i = 0; i < user.n; ++i) {
+    key += ":" + std::to_string(user.H[i]) + "x" + std::to_string(user.W[i]) + (user.u[i] ? "u" : "-");
+    want_u = want_u || user.u[i];
+  }
+  GraphEntry *g = nullptr;
+  for (GraphEntry &ge : c->graphs)
+    if (ge.key == key) g = &ge;
+  if (!g) {
+    if (c->graph_seen.insert(key).second) return false;  // first occurrence: eager
+    if (c->graphs.size() >= kMaxGraphs) return false;
+  }
+  const size_t P = (size_t)s.P, KP = (size_t)c->K * s.P;
+  if (!s.xstage && dalloc(c, &s.xstage, (size_t)c->opts.max_batch * P) != OCSC_OK) return false;
+  if (want_u && !s.ustage && dalloc(c, &s.ustage, (size_t)c->opts.max_batch * KP) != OCSC_OK) return false;
+  ImgBatch st_b = user;
+  for (int i = 0; i < user.n; ++i) {
+    st_b.x[i] = s.xstage + (size_t)user.slot[i] * P;
+    st_b.u[i] = user.u[i] ? s.ustage + (size_t)user.slot[i] * KP : nullptr;
+  }
+  if (!g) {
+    // Capture on a library stream (the context's stream may be the legacy
+    // default stream, which cannot capture); nothing executes during capture.
+    cudaError_t e = cudaSuccess;
+    if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      *st = cuda_fail(c, e, "graph capture");
+      return true;
+    }
+    const uint64_t counted = c->counters.kernel_launches;
+    cudaStream_t user_stream = c->stream;
+    c->stream = c->cap_stream;
+    const ocsc_status es = enqueue_chunk(c, s, st_b);
+    c->stream = user_stream;
+    c->counters.kernel_launches = counted;  // the replay below counts them
+    e = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (es != OCSC_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      *st = es != OCSC_OK ? es : cuda_fail(c, e, "graph capture");
+      return true;
+    }
+    GraphEntry ne;
+    ne.key = key;
+    cudaGraphGetNodes(graph, nullptr, &ne.kernels);
+    e = cudaGraphInstantiate(&ne.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      *st = cuda_fail(c, e, "graph instantiate");
+      return true;
+    }
+    c->graphs.push_back(ne);
+    g = &c->graphs.back();
+  }
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < user.n && e == cudaSuccess; ++i)
+    e = cudaMemcpyAsync(s.xstage + (size_t)user.slot[i] * P, user.x[i], (size_t)user.H[i] * user.W[i] * sizeof(float),
+                        cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, c->stream);
+  for (int i = 0; i < user.n && e == cudaSuccess; ++i)
+    if (user.u[i]) e = cudaMemcpyAsync(user.u[i], st_b.u[i], KP * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+  if (e != cudaSuccess) *st = cuda_fail(c, e, "graph launch");
+  c->counters.graph_launches++;
+  c->counters.kernel_launches += g->kernels;
+  return true;
+}
+
 // Code the images of one class (all of the same padded size).
 static ocsc_status code_class(ocsc_ctx *c, SizeClass &s, const std::vector<int> &idx, const float *const *x,
                               const int *H, const int *W, float *const *u) {
   const int n = (int)idx.size();
-  const int npairs = (c->K + 1) / 2;
   for (int s0 = 0; s0 < n; s0 += kMaxCallImages) {
     ImgBatch bt{};
     bt.n = n - s0 < kMaxCallImages ? n - s0 : kMaxCallImages;
@@ -265,60 +425,12 @@ static ocsc_status code_class(ocsc_ctx *c, SizeClass &s, const std::vector<int> 
       bt.u[i] = u ? u[j] : nullptr;
       bt.H[i] = H[j];
       bt.W[i] = W[j];
-    }
-    const int slot = s.pending + s0;
-    for (int i = 0; i < bt.n; ++i) {
-      bt.slot[i] = slot + i;
+      bt.slot[i] = s.pending + s0 + i;
       bt.iter[i] = 0;
     }
-    LargeIO io{};
-    io.T = s.tiles;
-    io.tile_pairs = npairs;
-    cudaError_t e;
-    if (large_fft(s.N)) {
-      io.spec_out = s.xhp;
-      CodeIter none{};
-      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_SPAT_IMAGE, none, bt, io, bt.n, 1, s.tw, c->stream); });
-      if (e == cudaSuccess)
-        e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_large(s.N, LARGE_SPEC_IMAGE, none, bt, io, bt.n, 1, s.tw, c->stream); });
-    } else {
-      e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(s.N, bt, s.tw, s.xhp, c->stream); });
-    }
-    if (e != cudaSuccess) return cuda_fail(c, e, "image spectrum");
-    CodeIter it{};
-    it.K = c->K;
-    it.F = s.F;
-    it.thr = (float)(c->lam / c->rho);
-    it.Dh = coding_spectrum(c, s);
-    it.r = s.r;
-    it.What = s.What;
-    it.Gam = s.Gam;
-    it.Zp = s.Zp;
-    it.serve = 0;
-    it.check = 1;
-    it.rho = (float)c->rho;
-    it.dn = s.dn;
-    it.xh = s.xhp;
-    it.part = s.part;
-    it.cnt = s.cnt;
-    for (int t = 0; t < c->opts.Jz; ++t) {
-      it.first = t == 0;
-      it.last = t == c->opts.Jz - 1;
-      if (large_fft(s.N)) {
-        e = cudaSuccess;
-        if (!it.first)
-          e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_large(s.N, LARGE_SPEC_DOT, it, bt, io, bt.n, npairs, s.tw, c->stream); });
-        if (e == cudaSuccess)
-          e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_large(s.N, LARGE_SPEC_Z, it, bt, io, bt.n, npairs, s.tw, c->stream); });
-        if (e == cudaSuccess)
-          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_large(s.N, LARGE_SPAT_ADMM, it, bt, io, bt.n, npairs, s.tw, c->stream); });
-      } else {
-        e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(s.N, bt, it, (float)c->rho, s.dn, s.xhp, c->stream); });
-        if (e == cudaSuccess)
-          e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(s.N, it, bt, s.tw, c->stream); });
-      }
-      if (e != cudaSuccess) return cuda_fail(c, e, "code iteration");
-    }
+    ocsc_status st;
+    if (!graph_chunk(c, s, bt, &st)) st = enqueue_chunk(c, s, bt);
+    if (st != OCSC_OK) return st;
   }
   s.pending += n;
   return OCSC_OK;
@@ -401,7 +513,35 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
         ga.B = s.pending;
         ga.first = s.n_seen == 0;
         ga.terms = c->opts.precision == 2 ? 3 : 1;
-        ga.SC = gram_chunk(c->K, s.pending, ga.terms);
+        if (s.gram_sc == 0) {
+          s.gram_sc = gram_chunk(c->K, c->opts.max_batch, ga.terms);
+          if (c->opts.autotune) {
+            // Dry runs (sums without stores) of each chunk size that fits.
+            float best = -1.f;
+            for (int sc : {32, 64, 128}) {
+              if (sc > gram_chunk(c->K, 128, ga.terms)) continue;
+              GramArgs gd = ga;
+              gd.SC = sc;
+              gd.dry = 1;
+              gd.Zp = s.Zp;
+              gd.xh = s.xhp;
+              gd.A = s.A;
+              gd.Alo = s.Alo;
+              gd.b = s.b;
+              gd.err = c->err;
+              gd.F = s.F;
+              gd.K = c->K;
+              gd.B = s.pending;
+              const float t = time_runs(c, 2, [&] { return launch_gram_fold(gd, c->stream); });
+              if (t < 0.f) return cuda_fail(c, cudaGetLastError(), "autotune history fold");
+              if (best < 0.f || t < best) {
+                best = t;
+                s.gram_sc = sc;
+              }
+            }
+          }
+        }
+        ga.SC = s.gram_sc;
         ga.alpha = (float)fa.alpha;
         ga.beta = (float)fa.beta;
         ga.keep = (float)((double)s.pending / (double)nc);
@@ -417,10 +557,26 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
       fa.prefolded = 1;
       fa.Alo = s.Alo;
     }
-    if (big_k(c))
+    if (big_k(c)) {
       e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_factor_big(fa, c->work, c->work_ctas, c->stream); });
-    else
-      e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_factor(fa, c->stream); });
+    } else {
+      const int nt = s.fold_threads ? s.fold_threads : 256;
+      e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_factor(fa, nt, c->stream); });
+      if (e == cudaSuccess && s.fold_threads == 0) {
+        // Autotune the CTA size on this class's own history: factor-only
+        // reruns recompute the same X and y from the folded A and b.
+        s.fold_threads = 256;
+        if (c->opts.autotune) {
+          FoldArgs fp = fa;
+          fp.prefolded = 1;
+          fp.Alo = s.Alo;
+          const float t256 = time_runs(c, 2, [&] { return launch_fold_factor(fp, 256, c->stream); });
+          const float t512 = time_runs(c, 2, [&] { return launch_fold_factor(fp, 512, c->stream); });
+          if (t256 < 0.f || t512 < 0.f) return cuda_fail(c, cudaGetLastError(), "autotune fold_factor");
+          s.fold_threads = t512 < t256 ? 512 : 256;
+        }
+      }
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "fold_factor");
   }
   AlphaClasses ac{};
@@ -604,6 +760,18 @@ ocsc_status ocsc_set_state(ocsc_ctx *c, const void *buf, size_t len) {
   c->n_seen = h.n_seen;
   c->version = h.version;
   return OCSC_OK;
+}
+
+ocsc_status ocsc_get_tuning(const ocsc_ctx *c, int N, ocsc_tuning *out) {
+  if (!c || !out) return OCSC_EINVAL;
+  for (const SizeClass &s : c->cls)
+    if (s.N == N) {
+      out->fold_threads = s.fold_threads;
+      out->spat_cb = s.spat_cb;
+      out->gram_sc = s.gram_sc;
+      return OCSC_OK;
+    }
+  return OCSC_EUNSUPPORTED;
 }
 
 ocsc_status ocsc_sync(ocsc_ctx *c) {

@@ -464,3 +464,56 @@ def test_large_K_factor_matches_oracle(K, precision, a_tol, d_tol):
         assert a_err < a_tol or (precision == 1 and s > 0)
         assert d_err < d_tol
     lr.close()
+
+
+# --- batching machinery: CUDA graphs and the autotuner -----------------------------
+
+def _run_sequence(pkg, graphs, autotune, precision=0):
+    K, M = 10, 5
+    raw = raw_filters(K, M, 81)
+    lr = pkg.OCSC(K, M, 0.5, 1.0, fft_sizes=[64, 256], pad=4, Jz=6, Jd=3, max_batch=2,
+                  graphs=graphs, autotune=autotune, precision=precision)
+    lr.set_dict(raw, normalize=True)
+    codes = []
+    for r in range(4):   # the same chunk shapes every round: captured at round 2
+        xs = [torch.from_numpy(make_image(s, s, 1500 + 10 * r + i)).cuda() for i, s in enumerate([50, 200])]
+        us = lr.code(xs)
+        lr.update_dict()
+        codes.extend(u.cpu().numpy() for u in us)
+    D = lr.get_dict()
+    counters = lr.counters()
+    tun = {N: lr.tuning(N) for N in (64, 256)}
+    lr.close()
+    return codes, D, counters, tun
+
+
+def test_graph_replay_matches_direct_launches():
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    a = _run_sequence(pkg, graphs=0, autotune=0)
+    b = _run_sequence(pkg, graphs=1, autotune=0)
+    for x, y in zip(a[0], b[0]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a[1], b[1])
+    assert a[2]["graph_launches"] == 0 and b[2]["graph_launches"] == 6   # 2 classes x rounds 2, 3, 4
+    assert a[2]["kernel_launches"] == b[2]["kernel_launches"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_tiles_do_not_change_results(precision):
+    """Every tuned tile shape performs the same operations in the same order."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    a = _run_sequence(pkg, graphs=0, autotune=0, precision=precision)
+    b = _run_sequence(pkg, graphs=0, autotune=1, precision=precision)
+    for x, y in zip(a[0], b[0]):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a[1], b[1])
+    t = b[3]
+    print("tuned tiles:", t)
+    assert t[64]["fold_threads"] in (256, 512) and t[256]["fold_threads"] in (256, 512)
+    assert t[256]["spat_cb"] in (8, 16) and t[64]["spat_cb"] == 0
+    if precision:
+        assert t[64]["gram_sc"] in (32, 64, 128)
