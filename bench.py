@@ -241,16 +241,17 @@ def batched_leg(pkg, w, dev, stream, args):
     B = args.batch
     N = 128
     mk = lambda bsz: pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_size=N, pad=w.pad, Jz=w.Jz,
-                              Jd=w.Jd, max_batch=max(bsz, 1))
-    # throughput
+                              Jd=w.Jd, max_batch=max(bsz, 1), graphs=args.graphs)
+    # throughput (two warm-up batches: the second captures the coding graph)
     lb = mk(B)
     lb.set_dict(w.filters0(), normalize=True)
     base = 2_000_000
     nb = args.batched_steps
     xs = [torch.from_numpy(w.image(base + i)).to(dev) for i in range(B * (nb + 1))]
     us = [torch.empty((w.K, N, N), device=dev) for _ in range(B)]
-    lb.code(xs[:B], out=us)
-    lb.update_dict()
+    for _ in range(2):
+        lb.code(xs[:B], out=us)
+        lb.update_dict()
     lb.sync()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -483,7 +484,7 @@ def ours_arm(args):
     x_host = [torch.from_numpy(im).pin_memory() for im in imgs[W + K:]]
     stream = torch.cuda.current_stream(dev)
     learner = pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_size=N, pad=w.pad, Jz=w.Jz,
-                       Jd=w.Jd, max_batch=1)
+                       Jd=w.Jd, max_batch=1, graphs=args.graphs)
     learner.set_dict(w.filters0(), normalize=True)
     u_dev = torch.empty((w.K, N, N), device=dev, dtype=torch.float32)
 
@@ -519,6 +520,7 @@ def ours_arm(args):
     prof = learner.profile_read(["fold_factor"])["fold_factor"]
     learner.profile([])
     learner.sync()
+    tuning = learner.tuning(N)
 
     # Per-kernel breakdown on a few extra steps (context only, not the headline).
     breakdown = {}
@@ -584,7 +586,8 @@ def ours_arm(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": 1e3 * t_max / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU"}),
+        "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                               "graphs": bool(args.graphs), "tuned_tiles": tuning}),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(c1["kernel_launches"] - c0["kernel_launches"]),
         "kernel_breakdown": breakdown,
@@ -647,6 +650,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--breakdown-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--graphs", type=int, default=1,
+                    help="1: ocsc_code replays a CUDA graph per chunk shape (plain and batched legs)")
     ap.add_argument("--precision-steps", type=int, default=2,
                     help="timed batches of 128 per variant in the precision leg (0: skip)")
     ap.add_argument("--legs", default="plain,batched,mixed,serving,precision",

@@ -108,7 +108,7 @@ typedef struct {
                          captures the sample spectra and the Jz iterations,
                          later calls copy their images into library staging
                          slots and launch the graph (codes are copied out).
-                         Not used while kernels are being profiled.  0
+                         Not used while coding kernels are profiled.  0
                          (default): every launch is issued directly. */
 } ocsc_opts;
 

@@ -342,7 +342,9 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
 // also autotunes); false = not handled here (caller runs it eagerly).
 static bool graph_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &user, ocsc_status *st) {
   *st = OCSC_OK;
-  if (!c->opts.graphs || c->prof_mask) return false;
+  constexpr unsigned coding_kinds =
+      (1u << OCSC_K_IMAGE_SPECTRUM) | (1u << OCSC_K_CODE_RESID) | (1u << OCSC_K_CODE_PLANE);
+  if (!c->opts.graphs || (c->prof_mask & coding_kinds)) return false;
   bool want_u = false;
   std::string key = std::to_string(s.N) + ":" + std::to_string(user.n) + ":" + std::to_string(user.slot[0]);
   for (int i = 0; i < user.n; ++i) {
