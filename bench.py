@@ -381,10 +381,14 @@ def precision_leg(pkg, dev, stream, args):
     return out
 
 
+SERVING_CLASSES = (96, 128, 144, 192, 256, 288, 384, 512, 576)
+
+
 def serving_leg(pkg, dev, stream, args):
     """Continuous batching of single-image requests (side log-uniform in
-    [64, 502], FFT classes 128 / 256 / 512, K = 100, tolerance 1e-4 checked every
-    5 iterations, cap 500, dictionary update every 64 completions, 8 GiB
+    [64, 512], FFT class the smallest even 2^a 3^b >= side + 10: 96, 128, 144,
+    192, 256, 288, 384, 512, 576; K = 100, tolerance 1e-4 checked every 5
+    iterations, cap 500, dictionary update every 64 completions, 8 GiB
     admission budget): saturated throughput, then Poisson arrivals at 25 / 50 /
     90 % of it with p50 / p99 latency (arrival to completion, host clock)."""
     import math
@@ -394,7 +398,7 @@ def serving_leg(pkg, dev, stream, args):
     from workloads import WORKLOADS
 
     w = WORKLOADS["serving_k100"]
-    lr = pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_sizes=[128, 256, 512], pad=w.pad,
+    lr = pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_sizes=list(SERVING_CLASSES), pad=w.pad,
                   Jz=50, Jd=w.Jd, max_batch=w.batch)
     lr.set_dict(w.filters0(), normalize=True)
     n_req = args.serve_requests

@@ -22,8 +22,9 @@
  *  - Images are square or rectangular H x W; each is zero-padded at the end of
  *    both axes to an N x N FFT domain, N = the smallest FFT size of the context
  *    >= max(H, W) + pad.  Convolution is circular on that domain and filters
- *    occupy its top-left M x M corner.  Supported N: 64, 128, 256, 288 and
- *    512; an image goes to the smallest size of the context that holds it.
+ *    occupy its top-left M x M corner.  Supported N: 64, 96, 128, 144, 192,
+ *    256, 288, 384, 512, 576 (2^a 3^b); an image goes to the smallest size of
+ *    the context that holds it.
  *  - lambda is the l1 weight (beta in the paper); rho is a spatial-domain
  *    ADMM penalty used by both ADMMs (the paper's frequency-domain penalty
  *    rho' of eq. (sub_d_sol) equals rho / P; opts.rho_convention = 1 uses the
@@ -60,6 +61,8 @@ typedef enum {
   OCSC_ENUMERIC = 7      /* a factorisation met a non-positive pivot */
 } ocsc_status;
 
+#define OCSC_MAX_FFT_SIZES 12
+
 typedef struct {
   int Jz;             /* code-ADMM iterations per sample (default 50) */
   int Jd;             /* dictionary-ADMM iterations per update (default 10) */
@@ -68,9 +71,9 @@ typedef struct {
                          no wrap-around across the image boundary */
   int max_batch;      /* most samples that may be pending between two
                          ocsc_update_dict calls (default 1) */
-  int fft_sizes[4];   /* the FFT sides N this context serves, zero-terminated,
-                         each of 64, 128, 256, 288, 512 (default
-                         {128, 0, 0, 0}).
+  int fft_sizes[OCSC_MAX_FFT_SIZES]; /* the FFT sides N this context serves,
+                         zero-terminated, each of 64, 96, 128, 144, 192, 256,
+                         288, 384, 512, 576 (default {128, 0, ...}).
                          Each size is a class with its own history, factor,
                          dual and coding spectrum of the one shared
                          dictionary; with several classes the dictionary step

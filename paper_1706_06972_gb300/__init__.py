@@ -29,10 +29,13 @@ class OCSCError(RuntimeError):
         self.status = status
 
 
+MAX_FFT_SIZES = 12  # OCSC_MAX_FFT_SIZES
+
+
 class ocsc_opts(ctypes.Structure):
     _fields_ = [
         ("Jz", ctypes.c_int), ("Jd", ctypes.c_int), ("pad", ctypes.c_int),
-        ("max_batch", ctypes.c_int), ("fft_sizes", ctypes.c_int * 4), ("warm_start", ctypes.c_int),
+        ("max_batch", ctypes.c_int), ("fft_sizes", ctypes.c_int * MAX_FFT_SIZES), ("warm_start", ctypes.c_int),
         ("return_feasible", ctypes.c_int), ("rho_convention", ctypes.c_int),
         ("seed", ctypes.c_uint64), ("precision", ctypes.c_int), ("autotune", ctypes.c_int),
         ("graphs", ctypes.c_int),
@@ -274,7 +277,7 @@ class OCSC:
         if sizes is not None:
             if not 1 <= len(sizes) <= 4:
                 raise ValueError("one to four FFT sizes")
-            o.fft_sizes = (ctypes.c_int * 4)(*(list(sizes) + [0] * (4 - len(sizes))))
+            o.fft_sizes = (ctypes.c_int * MAX_FFT_SIZES)(*(list(sizes) + [0] * (MAX_FFT_SIZES - len(sizes))))
         for k, v in opts.items():
             if not hasattr(o, k):
                 raise TypeError(f"unknown option {k}")

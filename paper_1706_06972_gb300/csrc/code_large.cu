@@ -1,5 +1,6 @@
 // Code ADMM for FFT sizes whose packed N x N complex plane does not fit one
-// CTA's shared memory (N = 256, 288 = 2^5 3^2, 512).  The iteration is the one of
+// CTA's shared memory, and for the sizes with a factor 3 (N = 96, 144, 192,
+// 256, 288, 384, 512, 576).  The iteration is the one of
 // code_admm.cu (Sec. II-C.1 problem (fcsc_code), ADMM of Sec. II-B):
 //   W^ = F(U - Gamma),  z = w^ + conj(d) r,  r = (x~ - d^T w^) / (rho + |d|^2),
 //   U' = S(Z + Gamma),  Gamma' = Gamma + Z - U'.
@@ -27,6 +28,8 @@
 // either way the Hermitian mirror (-k1, -k2) of every bin of a row lies in
 // one of the CTA's two rows.  The same kernels in other modes give the sample
 // spectrum and the batched real 2D FFT building blocks.
+#include <type_traits>
+
 #include "fft.cuh"
 #include "launch.h"
 
@@ -37,9 +40,21 @@ constexpr int kLargeThreads = 256;
 // Columns per spatial CTA (CB, even, dividing N) and filter pairs per spectral
 // stage (GP) for each size.
 template <int N> struct LargeTile;
+template <> struct LargeTile<96> { static constexpr int CB = 8, GP = 8; };
+template <> struct LargeTile<144> { static constexpr int CB = 16, GP = 8; };
+template <> struct LargeTile<192> { static constexpr int CB = 16, GP = 8; };
 template <> struct LargeTile<256> { static constexpr int CB = 16, GP = 8; };
 template <> struct LargeTile<288> { static constexpr int CB = 16, GP = 4; };
+template <> struct LargeTile<384> { static constexpr int CB = 8, GP = 4; };
 template <> struct LargeTile<512> { static constexpr int CB = 8, GP = 4; };
+template <> struct LargeTile<576> { static constexpr int CB = 8, GP = 4; };
+
+// Spatial tile widths a size admits: CB even, dividing N, N * CB a multiple of
+// the CTA's thread count.
+template <int N, int CB>
+constexpr bool spat_ok() {
+  return N % CB == 0 && CB % 2 == 0 && (N * CB) % kLargeThreads == 0;
+}
 
 template <int N>
 struct LargeGeom {
@@ -600,8 +615,12 @@ static cudaError_t large_n(int what, const CodeIter &it, const ImgBatch &b, cons
   using G = LargeGeom<N>;
   if (what >= LARGE_SPAT_ADMM) {
     const int cb = io.spat_cb ? io.spat_cb : G::CB;
-    if (cb == 8) return spat_n<N, 8>(what, it, b, io, n, npairs, tw, s);
-    if (cb == 16) return spat_n<N, 16>(what, it, b, io, n, npairs, tw, s);
+    if (cb == 8) {
+      if constexpr (spat_ok<N, 8>()) return spat_n<N, 8>(what, it, b, io, n, npairs, tw, s);
+    }
+    if (cb == 16) {
+      if constexpr (spat_ok<N, 16>()) return spat_n<N, 16>(what, it, b, io, n, npairs, tw, s);
+    }
     return cudaErrorInvalidValue;
   }
   const size_t sp = spec_smem_bytes<N>();
@@ -617,42 +636,50 @@ static cudaError_t large_n(int what, const CodeIter &it, const ImgBatch &b, cons
   }
 }
 
+// Calls f(std::integral_constant<int, N>) for the supported sizes.
+template <typename Fn, typename R>
+static R with_size(int N, R fallback, Fn &&f) {
+  switch (N) {
+    case 96: return f(std::integral_constant<int, 96>());
+    case 144: return f(std::integral_constant<int, 144>());
+    case 192: return f(std::integral_constant<int, 192>());
+    case 256: return f(std::integral_constant<int, 256>());
+    case 288: return f(std::integral_constant<int, 288>());
+    case 384: return f(std::integral_constant<int, 384>());
+    case 512: return f(std::integral_constant<int, 512>());
+    case 576: return f(std::integral_constant<int, 576>());
+    default: return fallback;
+  }
+}
+
 cudaError_t launch_large(int N, int what, const CodeIter &it, const ImgBatch &b, const LargeIO &io,
                          int n, int npairs, const float2 *tw, cudaStream_t s) {
   if (n <= 0 || npairs <= 0) return cudaSuccess;
-  switch (N) {
-    case 256: return large_n<256>(what, it, b, io, n, npairs, tw, s);
-    case 288: return large_n<288>(what, it, b, io, n, npairs, tw, s);
-    case 512: return large_n<512>(what, it, b, io, n, npairs, tw, s);
-    default: return cudaErrorInvalidValue;
-  }
+  return with_size(N, cudaErrorInvalidValue, [&](auto nc) {
+    return large_n<decltype(nc)::value>(what, it, b, io, n, npairs, tw, s);
+  });
 }
 
 int large_default_cb(int N) {
-  switch (N) {
-    case 256: return LargeGeom<256>::CB;
-    case 288: return LargeGeom<288>::CB;
-    case 512: return LargeGeom<512>::CB;
-    default: return 0;
-  }
+  return with_size(N, 0, [](auto nc) { return LargeGeom<decltype(nc)::value>::CB; });
+}
+
+bool large_cb_ok(int N, int cb) {
+  return with_size(N, false, [cb](auto nc) {
+    constexpr int n = decltype(nc)::value;
+    return (cb == 8 && spat_ok<n, 8>()) || (cb == 16 && spat_ok<n, 16>());
+  });
 }
 
 int large_stages(int N, int npairs) {
-  switch (N) {
-    case 256: return (npairs + LargeGeom<256>::GP - 1) / LargeGeom<256>::GP;
-    case 288: return (npairs + LargeGeom<288>::GP - 1) / LargeGeom<288>::GP;
-    case 512: return (npairs + LargeGeom<512>::GP - 1) / LargeGeom<512>::GP;
-    default: return 0;
-  }
+  return with_size(N, 0, [npairs](auto nc) {
+    constexpr int gp = LargeGeom<decltype(nc)::value>::GP;
+    return (npairs + gp - 1) / gp;
+  });
 }
 
 int large_resid_groups(int N, int npairs) {
-  switch (N) {
-    case 256: return npairs * LargeGeom<256>::NCB;
-    case 288: return npairs * LargeGeom<288>::NCB;
-    case 512: return npairs * LargeGeom<512>::NCB;
-    default: return 0;
-  }
+  return with_size(N, 0, [npairs](auto nc) { return npairs * LargeGeom<decltype(nc)::value>::NCB; });
 }
 
 }  // namespace ocsc

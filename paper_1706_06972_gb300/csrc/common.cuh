@@ -68,4 +68,7 @@ __device__ __forceinline__ void tri_ij(int t, int K, int &i, int &j) {
 // Device error word bits.
 enum : int { ERR_PIVOT = 1, ERR_TIMEOUT = 2 };
 
+// Largest FFT side of any size class.
+constexpr int kMaxFFT = 576;
+
 }  // namespace ocsc

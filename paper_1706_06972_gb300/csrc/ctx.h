@@ -116,8 +116,14 @@ ocsc_status dalloc(ocsc_ctx *c, T **p, size_t count) {
   return OCSC_OK;
 }
 
-inline bool supported_fft(int n) { return n == 64 || n == 128 || n == 256 || n == 288 || n == 512; }
-inline bool large_fft(int n) { return n >= 256; }
+// FFT sides: 2^a 3^b with b <= 2.  64 and 128 run the whole-plane kernels of
+// code_admm.cu; every other size the row / column kernels of code_large.cu.
+inline bool supported_fft(int n) {
+  for (int m : {64, 96, 128, 144, 192, 256, 288, 384, 512, 576})
+    if (n == m) return true;
+  return false;
+}
+inline bool large_fft(int n) { return n != 64 && n != 128; }
 
 // Class of an H x W image: the smallest FFT size of the context that holds
 // max(H, W) + pad, or -1.

@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(256)
     vstep_spectrum_kernel(int mode, int K, int N, int M, const float2 *__restrict__ Tm,
                           const float2 *__restrict__ tw, float2 *__restrict__ Vh, float2 *__restrict__ th,
                           const float2 *__restrict__ Dcur) {
-  __shared__ float2 s_tw[512];
+  __shared__ float2 s_tw[kMaxFFT];
   const int NH = N / 2 + 1, F = N * NH;
   for (int i = threadIdx.x; i < N; i += 256) s_tw[i] = tw[i];
   __syncthreads();
@@ -476,7 +476,7 @@ cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const flo
 
 cudaError_t launch_vstep_cols(int K, int N, int M, const float2 *E, const float2 *tw, float2 *Y,
                               cudaStream_t s) {
-  if (M > kMaxM || N > 512) return cudaErrorInvalidValue;
+  if (M > kMaxM || N > kMaxFFT) return cudaErrorInvalidValue;
   dim3 grid(K, (N / 2 + 1 + 31) / 32), block(32, M);
   vstep_cols_kernel<<<grid, block, N * sizeof(float2), s>>>(K, N, M, E, tw, Y);
   return cudaGetLastError();
@@ -490,7 +490,7 @@ cudaError_t launch_vstep_project(int K, int M, const AlphaClasses &ac, float *V,
 
 cudaError_t launch_vstep_partial_dft(int K, int N, int M, const float *V, const float2 *tw, float2 *Tm,
                                      cudaStream_t s) {
-  if (M > kMaxM || N > 512) return cudaErrorInvalidValue;
+  if (M > kMaxM || N > kMaxFFT) return cudaErrorInvalidValue;
   const size_t sm = N * sizeof(float2) + kMaxM * kMaxM * sizeof(float);
   vstep_partial_dft_kernel<<<K, kProjThreads, sm, s>>>(K, N, M, V, tw, Tm);
   return cudaGetLastError();
@@ -498,7 +498,7 @@ cudaError_t launch_vstep_partial_dft(int K, int N, int M, const float *V, const 
 
 cudaError_t launch_vstep_spectrum(int mode, int K, int N, int M, const float2 *Tm, const float2 *tw,
                                   float2 *Vh, float2 *th, const float2 *Dcur, cudaStream_t s) {
-  if (M > kMaxM || N > 512) return cudaErrorInvalidValue;
+  if (M > kMaxM || N > kMaxFFT) return cudaErrorInvalidValue;
   const int F = N * (N / 2 + 1);
   dim3 grid(K, (F + 255) / 256);
   vstep_spectrum_kernel<<<grid, 256, 0, s>>>(mode, K, N, M, Tm, tw, Vh, th, Dcur);

@@ -203,6 +203,11 @@ template <int N> struct LinePlan;
 template <> struct LinePlan<256> { static constexpr int NP = 2, R0 = 16, R1 = 16, R2 = 1; };
 template <> struct LinePlan<512> { static constexpr int NP = 3, R0 = 8, R1 = 8, R2 = 8; };
 template <> struct LinePlan<288> { static constexpr int NP = 3, R0 = 8, R1 = 4, R2 = 9; };
+template <> struct LinePlan<96> { static constexpr int NP = 3, R0 = 8, R1 = 4, R2 = 3; };
+template <> struct LinePlan<144> { static constexpr int NP = 2, R0 = 16, R1 = 9, R2 = 1; };
+template <> struct LinePlan<192> { static constexpr int NP = 3, R0 = 8, R1 = 8, R2 = 3; };
+template <> struct LinePlan<384> { static constexpr int NP = 3, R0 = 8, R1 = 16, R2 = 3; };
+template <> struct LinePlan<576> { static constexpr int NP = 3, R0 = 8, R1 = 8, R2 = 9; };
 
 // One Stockham radix-R pass over NL lines; element m of line l is at
 // buf[l * ls + m * es].  Consecutive threads take consecutive lines of the

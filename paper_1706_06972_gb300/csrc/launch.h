@@ -85,6 +85,7 @@ cudaError_t launch_large(int N, int what, const CodeIter &it, const ImgBatch &b,
                          int n, int npairs, const float2 *tw, cudaStream_t s);
 // Default columns per spatial CTA (the serving residual partials assume it).
 int large_default_cb(int N);
+bool large_cb_ok(int N, int cb);
 // Stages of filter pairs per spectral CTA row (sizes CodeIter::part).
 int large_stages(int N, int npairs);
 // Residual partial sums per slot written by SPAT_ADMM in serving mode.
@@ -139,7 +140,7 @@ cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const flo
 cudaError_t launch_vstep_cols(int K, int N, int M, const float2 *E, const float2 *tw, float2 *Y,
                               cudaStream_t s);
 // Size classes that take part in one V-step (reading R16).
-constexpr int kMaxClasses = 4;
+constexpr int kMaxClasses = 12;
 struct AlphaClasses {
   int C;                            // active classes
   int N[kMaxClasses];               // FFT side of each

@@ -107,22 +107,12 @@ ocsc_status alloc_class(ocsc_ctx *c, SizeClass &s, int N) {
       (st = dalloc(c, &s.dn, (size_t)s.F)) || (st = dalloc(c, &s.A, (size_t)s.F * TS)) ||
       (st = dalloc(c, &s.b, KF)) || (st = dalloc(c, &s.X, (size_t)s.F * TS)) || (st = dalloc(c, &s.y, KF)) ||
       (st = dalloc(c, &s.Zp, B * KF)) || (st = dalloc(c, &s.xhp, B * s.F)) ||
-      (st = dalloc(c, &s.What, (large_fft(N) ? 1 : B) * KF)) || (st = dalloc(c, &s.Gam, B * K * s.P)) ||
-      (st = dalloc(c, &s.r, B * s.F)) || (st = dalloc(c, &s.obj_xh, (size_t)s.F)))
+      (st = dalloc(c, &s.obj_xh, (size_t)s.F)))
     return st;
   if (c->opts.precision > 0) {
     if ((st = dalloc(c, &s.Alo, (size_t)s.F * TS))) return st;
     cudaError_t e = cudaMemset(s.Alo, 0, (size_t)s.F * TS * sizeof(float2));
     if (e != cudaSuccess) return cuda_fail(c, e, "clear history compensation");
-  }
-  if (large_fft(N)) {
-    const int npairs = (K + 1) / 2;
-    if ((st = dalloc(c, &s.tiles, B * npairs * (size_t)s.P)) ||
-        (st = dalloc(c, &s.part, B * large_stages(N, npairs) * (size_t)s.F)) ||
-        (st = dalloc(c, &s.cnt, B * (size_t)(N / 2))))
-      return st;
-    cudaError_t e = cudaMemset(s.cnt, 0, B * (size_t)(N / 2) * sizeof(int));
-    if (e != cudaSuccess) return cuda_fail(c, e, "clear counters");
   }
   std::vector<float2> tw(N);
   for (int m = 0; m < N; ++m) {
@@ -132,6 +122,29 @@ ocsc_status alloc_class(ocsc_ctx *c, SizeClass &s, int N) {
   cudaError_t e = cudaMemcpy(s.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(c, e, "upload twiddles");
   return OCSC_OK;
+}
+
+// The coding workspace of a class (per slot: W^ and r, or the pair tiles and
+// partial sums; the spatial state), allocated at the class's first coding,
+// objective or FFT call, so that a context used only through the server never
+// holds it.
+ocsc_status ensure_code_ws(ocsc_ctx *c, SizeClass &s) {
+  if (s.Gam) return OCSC_OK;
+  const int K = c->K, N = s.N;
+  const size_t KF = (size_t)K * s.F, B = (size_t)c->opts.max_batch;
+  ocsc_status st;
+  if ((st = dalloc(c, &s.What, (large_fft(N) ? 1 : B) * KF)) || (st = dalloc(c, &s.r, B * s.F)))
+    return st;
+  if (large_fft(N)) {
+    const int npairs = (K + 1) / 2;
+    if ((st = dalloc(c, &s.tiles, B * npairs * (size_t)s.P)) ||
+        (st = dalloc(c, &s.part, B * large_stages(N, npairs) * (size_t)s.F)) ||
+        (st = dalloc(c, &s.cnt, B * (size_t)(N / 2))))
+      return st;
+    cudaError_t e = cudaMemset(s.cnt, 0, B * (size_t)(N / 2) * sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(c, e, "clear counters");
+  }
+  return dalloc(c, &s.Gam, B * K * (size_t)s.P);  // last: marks the workspace complete
 }
 
 }  // namespace
@@ -144,8 +157,8 @@ void ocsc_default_opts(ocsc_opts *o) {
   o->Jd = 10;
   o->pad = -1;
   o->max_batch = 1;
+  for (int i = 0; i < OCSC_MAX_FFT_SIZES; ++i) o->fft_sizes[i] = 0;
   o->fft_sizes[0] = 128;
-  o->fft_sizes[1] = o->fft_sizes[2] = o->fft_sizes[3] = 0;
   o->warm_start = 1;
   o->return_feasible = 1;
   o->rho_convention = 0;
@@ -196,10 +209,10 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
     return bail(OCSC_EINVAL);
   }
   std::vector<int> sizes;
-  for (int i = 0; i < 4 && c->opts.fft_sizes[i] != 0; ++i) {
+  for (int i = 0; i < OCSC_MAX_FFT_SIZES && c->opts.fft_sizes[i] != 0; ++i) {
     const int n = c->opts.fft_sizes[i];
     if (!supported_fft(n) || n < filter_h) {
-      fail(c, OCSC_EUNSUPPORTED, "fft size %d not supported (64, 128, 256, 288 or 512)", n);
+      fail(c, OCSC_EUNSUPPORTED, "fft size %d not supported (64, 96, 128, 144, 192, 256, 288, 384, 512, 576)", n);
       return bail(OCSC_EUNSUPPORTED);
     }
     for (int m : sizes)
@@ -300,6 +313,7 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
         tt.last = 0;
         float best = -1.f;
         for (int cb : {8, 16}) {
+          if (!large_cb_ok(s.N, cb)) continue;
           LargeIO tio = io;
           tio.spat_cb = cb;
           const float ms = time_runs(c, 2, [&] {
@@ -418,6 +432,8 @@ static bool graph_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &user, ocsc_st
 static ocsc_status code_class(ocsc_ctx *c, SizeClass &s, const std::vector<int> &idx, const float *const *x,
                               const int *H, const int *W, float *const *u) {
   const int n = (int)idx.size();
+  ocsc_status wst = ensure_code_ws(c, s);
+  if (wst != OCSC_OK) return wst;
   for (int s0 = 0; s0 < n; s0 += kMaxCallImages) {
     ImgBatch bt{};
     bt.n = n - s0 < kMaxCallImages ? n - s0 : kMaxCallImages;
@@ -646,16 +662,16 @@ ocsc_status ocsc_set_dict(ocsc_ctx *c, const float *D_host, int normalize) {
 namespace {
 
 constexpr uint32_t kStateMagic = 0x4353434Fu;  // "OCSC"
-constexpr uint32_t kStateFormat = 1;
+constexpr uint32_t kStateFormat = 2;
 
 struct StateHeader {
   uint32_t magic, format;
-  int32_t K, M, ncls, N[4];
+  int32_t K, M, ncls, N[OCSC_MAX_FFT_SIZES];
   int32_t rho_convention, return_feasible, warm_start, precision;
   double lam, rho;
   int64_t n_seen;
   uint64_t version;
-  int64_t class_seen[4];
+  int64_t class_seen[OCSC_MAX_FFT_SIZES];
 };
 
 // Device regions of the state, in file order.
@@ -789,6 +805,8 @@ static ocsc_status fft2_any(ocsc_ctx *c, int N, int inverse, const float *in, fl
   for (SizeClass &k : c->cls)
     if (k.N == N) s = &k;
   if (!s) return fail(c, OCSC_EUNSUPPORTED, "%s: N=%d is not a size of this context", name, N);
+  ocsc_status wst = ensure_code_ws(c, *s);
+  if (wst != OCSC_OK) return wst;
   if (!large_fft(N)) {
     cudaError_t e = timed(c, OCSC_K_COUNT, [&] { return launch_fft2(N, inverse, in, out, planes, s->tw, c->stream); });
     return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, name);
@@ -854,6 +872,8 @@ ocsc_status ocsc_objective(ocsc_ctx *c, int n, const float *const *x, const int 
     const int m = n - s0 < kObjChunk ? n - s0 : kObjChunk;
     for (int i = 0; i < m; ++i) {
       SizeClass &s = c->cls[cl[s0 + i]];
+      ocsc_status wst = ensure_code_ws(c, s);
+      if (wst != OCSC_OK) return wst;
       float2 *Uh = s.What;  // coding workspace of slot 0, idle between ocsc_code calls
       ImgBatch bt{};
       bt.n = 1;

@@ -71,7 +71,7 @@ def surrogate_objective(codes, coding_dicts, images, N, lam, batch):
 
 # --- FFT building block ------------------------------------------------------
 
-@pytest.mark.parametrize("N", [64, 128, 256, 288, 512])
+@pytest.mark.parametrize("N", [64, 96, 128, 144, 192, 256, 288, 384, 512, 576])
 def test_fft_building_block_matches_numpy(N):
     _need_gpu()
     import paper_1706_06972_gb300 as pkg
@@ -159,13 +159,18 @@ def _small_images(n, h, w, seed):
     dict(K=7, M=5, lam=0.5, rho=1.0, Jz=12, Jd=4, n=2, hw=(230, 200), pad=10),    # N = 256, odd K
     dict(K=4, M=3, lam=0.5, rho=1.0, Jz=8, Jd=3, n=2, hw=(400, 300), pad=10),     # N = 512
     dict(K=9, M=11, lam=1.0, rho=1.0, Jz=10, Jd=4, n=2, hw=(256, 256), pad=32),   # N = 288 = 2^5 3^2
+    dict(K=5, M=5, lam=0.5, rho=1.0, Jz=10, Jd=4, n=2, hw=(80, 70), pad=10),      # N = 96 = 2^5 3
+    dict(K=6, M=5, lam=0.5, rho=1.0, Jz=10, Jd=4, n=2, hw=(130, 120), pad=10),    # N = 144 = 2^4 3^2
+    dict(K=4, M=5, lam=0.5, rho=1.0, Jz=8, Jd=3, n=2, hw=(180, 175), pad=10),     # N = 192 = 2^6 3
+    dict(K=3, M=5, lam=0.5, rho=1.0, Jz=6, Jd=3, n=2, hw=(370, 360), pad=10),     # N = 384 = 2^7 3
+    dict(K=2, M=3, lam=0.5, rho=1.0, Jz=5, Jd=2, n=2, hw=(560, 500), pad=10),     # N = 576 = 2^6 3^2
 ])
 def test_edge_cases_match_oracle(case):
     _need_gpu()
     h, wd = case["hw"]
     imgs = _small_images(case["n"], h, wd, 77)
     raw = raw_filters(case["K"], case["M"], 5)
-    N = next(n for n in (64, 128, 256, 288, 512) if n >= max(h, wd) + case["pad"])
+    N = next(n for n in (64, 96, 128, 144, 192, 256, 288, 384, 512, 576) if n >= max(h, wd) + case["pad"])
     codes, dicts = run_gpu(imgs, raw, case["K"], case["M"], case["lam"], case["rho"], N,
                            case["Jz"], case["Jd"], pad=case["pad"])
     ocodes, odicts, _ = run_oracle(imgs, raw, N, case["lam"], case["rho"], case["Jz"], case["Jd"])
@@ -358,12 +363,13 @@ def test_checkpoint_resumes_bit_identically():
 # --- tensor-core history fold (precision variants) ----------------------------------
 
 class _StateHeader(__import__("ctypes").Structure):
+    """Mirror of the checkpoint header (OCSC_MAX_FFT_SIZES = 12 classes)."""
     import ctypes as _c
     _fields_ = [("magic", _c.c_uint32), ("format", _c.c_uint32), ("K", _c.c_int32), ("M", _c.c_int32),
-                ("ncls", _c.c_int32), ("N", _c.c_int32 * 4), ("rho_convention", _c.c_int32),
+                ("ncls", _c.c_int32), ("N", _c.c_int32 * 12), ("rho_convention", _c.c_int32),
                 ("return_feasible", _c.c_int32), ("warm_start", _c.c_int32), ("precision", _c.c_int32),
                 ("lam", _c.c_double), ("rho", _c.c_double), ("n_seen", _c.c_int64), ("version", _c.c_uint64),
-                ("class_seen", _c.c_int64 * 4)]
+                ("class_seen", _c.c_int64 * 12)]
 
 
 def _history_from_state(state, K, M, N, precision):

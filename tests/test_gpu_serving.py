@@ -63,12 +63,13 @@ def test_result_same_alone_and_in_mix():
     lr.close()
 
 
-def test_served_codes_match_oracle_at_reported_iterations():
+@pytest.mark.parametrize("sizes,sides", [((64, 128), (50, 100, 57)), ((96, 144), (80, 130, 85))])
+def test_served_codes_match_oracle_at_reported_iterations(sizes, sides):
     _need_gpu()
     import paper_1706_06972_gb300 as pkg
 
-    lr, raw = _learner(pkg)
-    imgs = [make_image(s, s, 40 + i) for i, s in enumerate([50, 100, 57])]
+    lr, raw = _learner(pkg, sizes=sizes)
+    imgs = [make_image(s, s, 40 + i) for i, s in enumerate(sides)]
     srv = pkg.Server(lr, learn=0, tol=1e-4, check_every=5, max_iters=200)
     res = _serve_all(srv, [(i, torch.from_numpy(im).cuda()) for i, im in enumerate(imgs)])
     srv.close()
@@ -77,7 +78,7 @@ def test_served_codes_match_oracle_at_reported_iterations():
         d = res[i]
         assert d["iters"] % 5 == 0 and 5 <= d["iters"] <= 200
         assert (d["primal"] <= 1e-4 and d["dual"] <= 1e-4) or d["iters"] == 200
-        N = 64 if max(im.shape) + 7 <= 64 else 128
+        N = sizes[0] if max(im.shape) + 7 <= sizes[0] else sizes[1]
         o = oracle.code_admm(oracle.pad_to(np.asarray(im, np.float64), N, N),
                              oracle.filters_spectrum(D, N, N), 0.5, 1.0, d["iters"])
         u = d["code"].cpu().numpy().astype(np.float64)

@@ -121,11 +121,10 @@ WORKLOADS = {
     # 4096 images of side 64/128/256, padded by 10 to FFT 128/256/512, K=100, B=64.
     "batched_mixed_k100": Workload("batched_mixed_k100", 3, 4096, (64, 128, 256), 10, 100, 11,
                                    1.0, 1.0, 64, 50, 10),
-    # Requests with side log-uniform in [64, 502] (the largest side whose
-    # 10-pixel padding fits FFT 512), K=100 filters 11x11, dictionary update
-    # every 64 completed requests.
+    # Requests with side log-uniform in [64, 512], each padded by 10 to its FFT
+    # class, K=100 filters 11x11, dictionary update every 64 completed requests.
     "serving_k100": Workload("serving_k100", 5, 20000, (), 10, 100, 11, 1.0, 1.0, 64, 500, 10,
-                             side_range=(64, 502)),
+                             side_range=(64, 512)),
     # 2048 images 256x256 padded to FFT 288, K=256, B=128.
     "precision_256_k256": Workload("precision_256_k256", 4, 2048, (256,), 32, 256, 11,
                                    1.0, 1.0, 128, 50, 10),
