@@ -275,8 +275,8 @@ class OCSC:
         if "fft_size" in opts:
             sizes = [opts.pop("fft_size")]
         if sizes is not None:
-            if not 1 <= len(sizes) <= 4:
-                raise ValueError("one to four FFT sizes")
+            if not 1 <= len(sizes) <= MAX_FFT_SIZES:
+                raise ValueError(f"one to {MAX_FFT_SIZES} FFT sizes")
             o.fft_sizes = (ctypes.c_int * MAX_FFT_SIZES)(*(list(sizes) + [0] * (MAX_FFT_SIZES - len(sizes))))
         for k, v in opts.items():
             if not hasattr(o, k):

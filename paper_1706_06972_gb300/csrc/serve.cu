@@ -13,9 +13,12 @@
 //      requests that converged or hit the cap, and frees their slots;
 //   4. with learning on, folds completed requests into the history and runs
 //      DictOCSC after every update_every completions (Algorithm 3).
-// A request is coded against the dictionary current when it was admitted: the
-// engine keeps two coding spectra per class and starts an update only when no
-// request still uses the older one.  Every per-request computation reads only
+// Request work runs on a stream of the server; the dictionary update runs on
+// the context's stream, ordered after the staging of the completed requests
+// only, so it overlaps the coding of the requests in flight.  A request is
+// coded against the dictionary current when it was admitted: the engine keeps
+// two coding spectra per class, starts an update only when no request still
+// uses the older one, and makes the new one current once its copies are done.  Every per-request computation reads only
 // that request's slot and its dictionary version, so a result does not depend
 // on the other requests in flight.
 #include <algorithm>
@@ -74,6 +77,17 @@ struct ocsc_server {
   double *h_res = nullptr;    // pinned [max slots][kResidTerms]
   int *h_slots = nullptr;     // pinned [max slots]
   std::vector<void *> allocs;
+  // Streams: request work runs on `stream`; dictionary updates on the
+  // context's stream (ctx_stream), so an update overlaps the coding of the
+  // requests in flight.  Completed requests are staged into one of two pending
+  // sets per class (set 0 = the context's own buffers) while an update reads
+  // the other; ev_read[set] marks the end of the last update that read it.
+  cudaStream_t stream = nullptr, ctx_stream = nullptr;
+  cudaEvent_t ev_stage = nullptr, ev_pub = nullptr, ev_read[2] = {nullptr, nullptr};
+  int pend_set = 0;
+  std::vector<float2 *> pend_Zp[2], pend_xh[2];
+  bool pub_pending = false;   // a published version is waiting for its event
+  int pub_slot = 0;
 };
 
 namespace {
@@ -211,7 +225,28 @@ void ocsc_server_default_opts(ocsc_server_opts *o) {
 
 void ocsc_server_destroy(ocsc_server *s) {
   if (!s) return;
-  cudaStreamSynchronize(s->ctx->stream);
+  ocsc_ctx *c = s->ctx;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->ctx_stream) c->stream = s->ctx_stream;
+  cudaStreamSynchronize(c->stream);
+  // Give the context back its own pending buffers (with the samples staged in
+  // the server's set, if that one is current).
+  if (!s->pend_Zp[0].empty()) {
+    for (size_t k = 0; k < c->cls.size(); ++k) {
+      SizeClass &cl = c->cls[k];
+      if (s->pend_set == 1 && cl.pending > 0) {
+        cudaMemcpy(s->pend_Zp[0][k], s->pend_Zp[1][k], (size_t)cl.pending * c->K * cl.F * sizeof(float2),
+                   cudaMemcpyDeviceToDevice);
+        cudaMemcpy(s->pend_xh[0][k], s->pend_xh[1][k], (size_t)cl.pending * cl.F * sizeof(float2),
+                   cudaMemcpyDeviceToDevice);
+      }
+      cl.Zp = s->pend_Zp[0][k];
+      cl.xhp = s->pend_xh[0][k];
+    }
+  }
+  for (cudaEvent_t ev : {s->ev_stage, s->ev_pub, s->ev_read[0], s->ev_read[1]})
+    if (ev) cudaEventDestroy(ev);
+  if (s->stream) cudaStreamDestroy(s->stream);
   for (void *p : s->allocs) cudaFree(p);
   if (s->h_res) cudaFreeHost(s->h_res);
   if (s->h_slots) cudaFreeHost(s->h_slots);
@@ -271,7 +306,32 @@ ocsc_status ocsc_server_create(ocsc_server **out, ocsc_ctx *c, const ocsc_server
   if (cudaMallocHost((void **)&s->h_res, (size_t)max_slots * kResidTerms * sizeof(double)) != cudaSuccess ||
       cudaMallocHost((void **)&s->h_slots, (size_t)max_slots * sizeof(int)) != cudaSuccess)
     return bail(fail(c, OCSC_ENOMEM, "server: pinned host buffers"));
-  cudaError_t e = publish(s, 0);
+  if (s->o.learn) {
+    s->pend_Zp[0].resize(c->cls.size());
+    s->pend_Zp[1].resize(c->cls.size());
+    s->pend_xh[0].resize(c->cls.size());
+    s->pend_xh[1].resize(c->cls.size());
+    for (size_t k = 0; k < c->cls.size(); ++k) {
+      SizeClass &cl = c->cls[k];
+      s->pend_Zp[0][k] = cl.Zp;
+      s->pend_xh[0][k] = cl.xhp;
+      ocsc_status st;
+      if ((st = salloc(s, &s->pend_Zp[1][k], (size_t)c->opts.max_batch * K * cl.F)) ||
+          (st = salloc(s, &s->pend_xh[1][k], (size_t)c->opts.max_batch * cl.F)))
+        return bail(st);
+    }
+  }
+  // Request work gets the highest stream priority: while an update's long
+  // FP64 CTAs hold the SMs, freed SMs go to request kernels first.
+  int prio_least = 0, prio_greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, prio_greatest);
+  for (cudaEvent_t *ev : {&s->ev_stage, &s->ev_pub, &s->ev_read[0], &s->ev_read[1]})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "server: stream and events"));
+  s->ctx_stream = c->stream;
+  e = publish(s, 0);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventRecord(s->ev_read[i], c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return bail(cuda_fail(c, e, "server: publish dictionary"));
   *out = s;
@@ -294,10 +354,66 @@ ocsc_status ocsc_server_submit(ocsc_server *s, uint64_t id, const float *x, int 
   return OCSC_OK;
 }
 
+namespace {
+
+// Enqueue a dictionary update on the context's stream after the staging copies
+// of the serving stream, switch the pending set, and (publish) copy the new
+// coding spectra into version slot 1 - cur, marked by ev_pub.
+ocsc_status start_update(ocsc_server *s, bool publish_new) {
+  ocsc_ctx *c = s->ctx;
+  cudaError_t e = cudaEventRecord(s->ev_stage, s->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->ctx_stream, s->ev_stage, 0);
+  if (e != cudaSuccess) return cuda_fail(c, e, "server: order the update after staging");
+  c->stream = s->ctx_stream;
+  ocsc_status st = ocsc_update_dict(c);
+  if (st == OCSC_OK && publish_new) {
+    if ((e = publish(s, 1 - s->cur)) == cudaSuccess) e = cudaEventRecord(s->ev_pub, c->stream);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "server: publish dictionary");
+    s->pub_pending = true;
+    s->pub_slot = 1 - s->cur;
+  }
+  if (st == OCSC_OK && !s->pend_Zp[0].empty()) {
+    // The update read the current pending set; further samples go to the other
+    // one once the update that last read it has finished.
+    if ((e = cudaEventRecord(s->ev_read[s->pend_set], c->stream)) != cudaSuccess)
+      st = cuda_fail(c, e, "server: pending set event");
+    s->pend_set = 1 - s->pend_set;
+    for (size_t k = 0; k < c->cls.size(); ++k) {
+      c->cls[k].Zp = s->pend_Zp[s->pend_set][k];
+      c->cls[k].xhp = s->pend_xh[s->pend_set][k];
+    }
+    if (st == OCSC_OK && (e = cudaStreamWaitEvent(s->stream, s->ev_read[s->pend_set], 0)) != cudaSuccess)
+      st = cuda_fail(c, e, "server: wait for the pending set");
+  }
+  c->stream = s->stream;
+  return st;
+}
+
+}  // namespace
+
+static ocsc_status step_body(ocsc_server *s, int *n_active, int *n_queued);
+
 ocsc_status ocsc_server_step(ocsc_server *s, int *n_active, int *n_queued) {
   if (!s) return OCSC_EINVAL;
   ocsc_ctx *c = s->ctx;
+  // Request work runs on the server's stream for the whole step.
+  struct StreamSwap {
+    ocsc_ctx *c;
+    cudaStream_t saved;
+    ~StreamSwap() { c->stream = saved; }
+  } swap{c, c->stream};
+  c->stream = s->stream;
+  return step_body(s, n_active, n_queued);
+}
+
+static ocsc_status step_body(ocsc_server *s, int *n_active, int *n_queued) {
+  ocsc_ctx *c = s->ctx;
   cudaError_t e = cudaSuccess;
+  // 0. A published dictionary becomes current once its copies are done.
+  if (s->pub_pending && cudaEventQuery(s->ev_pub) == cudaSuccess) {
+    s->cur = s->pub_slot;
+    s->pub_pending = false;
+  }
   // 1. Admission in arrival order.
   std::vector<std::vector<int>> admitted(s->sc.size());
   auto active_count = [&]() {
@@ -374,7 +490,7 @@ ocsc_status ocsc_server_step(ocsc_server *s, int *n_active, int *n_queued) {
         if (s->o.learn) {
           SizeClass &cl = c->cls[k];
           if (cl.pending >= c->opts.max_batch) {
-            ocsc_status st = ocsc_update_dict(c);
+            ocsc_status st = start_update(s, false);
             if (st != OCSC_OK) return st;
           }
           const size_t KF = (size_t)c->K * cl.F;
@@ -395,11 +511,10 @@ ocsc_status ocsc_server_step(ocsc_server *s, int *n_active, int *n_queued) {
   }
   // 4. Dictionary update once enough requests completed and no request still
   //    uses the version slot the new dictionary goes to.
-  if (s->o.learn && s->o.update_every > 0 && s->since_update >= s->o.update_every && s->refs[1 - s->cur] == 0) {
-    ocsc_status st = ocsc_update_dict(c);
+  if (s->o.learn && s->o.update_every > 0 && s->since_update >= s->o.update_every && s->refs[1 - s->cur] == 0 &&
+      !s->pub_pending) {
+    ocsc_status st = start_update(s, true);
     if (st != OCSC_OK) return st;
-    if ((e = publish(s, 1 - s->cur)) != cudaSuccess) return cuda_fail(c, e, "server: publish dictionary");
-    s->cur = 1 - s->cur;
     s->since_update = 0;
   }
   if (n_active) *n_active = active_count();
