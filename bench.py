@@ -220,17 +220,20 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------
 
 def test_objective(pkg, learner, w, dev, n_test=8):
-    """Mean objective of eq. (ocsc0) on held-out images coded with the current
-    dictionary (samples are dropped, not folded)."""
+    """Test-set evaluation of Sec. IV on held-out images coded with the current
+    dictionary (samples are dropped, not folded): mean objective of eq. (ocsc0)
+    and mean PSNR of the reconstruction, the peak being each image's range
+    (max - min; the images are contrast-normalised floats, not 8-bit)."""
     import torch
 
-    vals = []
+    vals, psnrs = [], []
     for i in range(n_test):
         x = torch.from_numpy(w.image(1_000_000 + i)).to(dev)
         u = learner.code([x])
         vals.append(learner.objective([x], u)[0])
+        psnrs.append(learner.psnr([x], u, peak=float(x.max() - x.min()))[0])
         learner.drop_pending()
-    return sum(vals) / len(vals)
+    return sum(vals) / len(vals), sum(psnrs) / len(psnrs)
 
 
 def batched_leg(pkg, w, dev, stream, args):
@@ -273,18 +276,18 @@ def batched_leg(pkg, w, dev, stream, args):
         for x in train:
             lp.code([x], want_codes=False)
             lp.update_dict()
-        f_plain = test_objective(pkg, lp, w, dev)
+        f_plain, p_plain = test_objective(pkg, lp, w, dev)
         lp.close()
         lq = mk(B)
         lq.set_dict(w.filters0(), normalize=True)
         for t in range(0, n, B):
             lq.code(train[t:t + B], want_codes=False)
             lq.update_dict()
-        f_batch = test_objective(pkg, lq, w, dev)
+        f_batch, p_batch = test_objective(pkg, lq, w, dev)
         lq.close()
         out.update({"quality_train_images": n, "test_objective_plain": f_plain,
                     "test_objective_batched": f_batch, "objective_gap": (f_batch - f_plain) / abs(f_plain),
-                    "test_images": 8})
+                    "test_psnr_plain_db": p_plain, "test_psnr_batched_db": p_batch, "test_images": 8})
     return out
 
 

@@ -232,6 +232,22 @@ ocsc_status ocsc_objective(ocsc_ctx *ctx, int n, const float *const *x, const in
                            const float *const *u, double *out_host);
 
 /*
+ * The two terms of the objective separately (evaluation of Sec. IV: the test
+ * set objective and the PSNR of the reconstruction sum_k D_k (*) U_k):
+ * resid2_host[i] = ||x_i - sum_k D_k (*) U_ik||^2 over the padded N x N domain,
+ * l1_host[i] = ||U_i||_1.  Same arguments and rules as ocsc_objective.
+ */
+ocsc_status ocsc_objective_terms(ocsc_ctx *ctx, int n, const float *const *x, const int *H, const int *W,
+                                 const float *const *u, double *resid2_host, double *l1_host);
+
+/*
+ * ||a - b||_2 / ||a||_2 over count floats of two DEVICE arrays (FP64, fixed
+ * summation order; the relative changes of the stopping rule of Sec. IV).
+ * Result in *out_host (0 for count = 0, +inf if a = 0 and b != 0).  Synchronises.
+ */
+ocsc_status ocsc_rel_diff(ocsc_ctx *ctx, const float *a, const float *b, size_t count, double *out_host);
+
+/*
  * Serving: continuous batching of coding requests over one context
  * (spec serving pattern; each request runs the code ADMM of
  * Sec. II-C.1 to a residual tolerance instead of a fixed iteration count).

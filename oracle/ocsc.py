@@ -343,6 +343,40 @@ def objective(D, Us, x_pads, lam: float) -> float:
 
 
 # ----------------------------------------------------------------------------
+# Evaluation of Sec. IV: stopping rule of the online method, test-set PSNR,
+# filter order for display.
+# ----------------------------------------------------------------------------
+
+def rel_change(new: np.ndarray, old: np.ndarray) -> float:
+    """||new - old||_2 / ||new||_2, the relative change of the stopping rule
+    (codes Z_t against the previous pass, dictionary D against the previous
+    update; both must fall below 1e-3)."""
+    new = np.asarray(new, np.float64)
+    d = np.linalg.norm(new - np.asarray(old, np.float64))
+    n = np.linalg.norm(new)
+    return float(d / n) if n > 0 else (0.0 if d == 0 else float("inf"))
+
+
+def psnr(D: np.ndarray, U: np.ndarray, x_pad: np.ndarray, peak: float = 255.0) -> float:
+    """10 log10(peak^2 P / ||x_rec - x||^2), x_rec = sum_k D_k (*) U_k, over the
+    padded P = N1 x N2 domain the model is defined on (the paper averages this
+    over the test set with peak 255 for 8-bit images)."""
+    x_pad = np.asarray(x_pad, np.float64)
+    r = reconstruct(np.asarray(D, np.float64), np.asarray(U, np.float64)) - x_pad
+    return float(10.0 * np.log10(peak * peak * x_pad.size / float(np.sum(r * r))))
+
+
+def filter_order(D: np.ndarray) -> np.ndarray:
+    """Filter indices in ascending order of their sample variance over the M x M
+    entries (unbiased: divided by the entry count minus one), the display order
+    of Sec. IV."""
+    D = np.asarray(D, np.float64).reshape(len(D), -1)
+    mu = D.sum(axis=1) / D.shape[1]
+    var = ((D - mu[:, None]) ** 2).sum(axis=1) / (D.shape[1] - 1)
+    return np.argsort(var, kind="stable")
+
+
+# ----------------------------------------------------------------------------
 # Uneven image sizes: one spatial dictionary, one frequency grid per size class
 # (reading R16; the paper uses a single P).  Each class c keeps its own history
 # (A_c, b_c, n_c) and scaled dual theta^_c; with w_c = n_c / n the D-row system

@@ -85,6 +85,10 @@ _PROTOS = {
     "ocsc_set_state": (_I, [_P, _P, ctypes.c_size_t]),
     "ocsc_objective": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double)]),
+    "ocsc_objective_terms": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                  ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]),
+    "ocsc_rel_diff": (_I, [_P, _P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)]),
     "ocsc_get_counters": (_I, [_P, ctypes.POINTER(ocsc_counters)]),
     "ocsc_profile": (_I, [_P, ctypes.c_uint]),
     "ocsc_profile_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]),
@@ -214,6 +218,30 @@ def ocsc_objective(ctx, x_ptrs, H, W, u_ptrs):
     _check(ctx, lib().ocsc_objective(ctx, n, (_P * n)(*x_ptrs), (_I * n)(*H), (_I * n)(*W),
                                      (_P * n)(*u_ptrs), out))
     return list(out)
+
+
+def ocsc_objective_terms(ctx, x_ptrs, H, W, u_ptrs):
+    n = len(x_ptrs)
+    r2 = (ctypes.c_double * n)()
+    l1 = (ctypes.c_double * n)()
+    _check(ctx, lib().ocsc_objective_terms(ctx, n, (_P * n)(*x_ptrs), (_I * n)(*H), (_I * n)(*W),
+                                           (_P * n)(*u_ptrs), r2, l1))
+    return list(r2), list(l1)
+
+
+def ocsc_rel_diff(ctx, a_ptr: int, b_ptr: int, count: int) -> float:
+    out = ctypes.c_double()
+    _check(ctx, lib().ocsc_rel_diff(ctx, a_ptr, b_ptr, count, ctypes.byref(out)))
+    return out.value
+
+
+def filter_order(D):
+    """Filter indices in ascending order of their sample variance over the
+    M x M entries (the display order of Sec. IV)."""
+    import numpy as np
+
+    flat = np.asarray(D, np.float64).reshape(len(D), -1)
+    return np.argsort(flat.var(axis=1, ddof=1), kind="stable")
 
 
 def ocsc_get_counters(ctx) -> ocsc_counters:
@@ -362,6 +390,57 @@ class OCSC:
         us = [u.contiguous() for u in codes]
         return ocsc_objective(self.ctx, [im.data_ptr() for im in xs], [im.shape[0] for im in xs],
                               [im.shape[1] for im in xs], [u.data_ptr() for u in us])
+
+    def objective_terms(self, images, codes):
+        """(||x - sum_k D_k (*) U_k||^2, ||U||_1) per sample, padded domain."""
+        xs = [im.contiguous() for im in images]
+        us = [u.contiguous() for u in codes]
+        return ocsc_objective_terms(self.ctx, [im.data_ptr() for im in xs], [im.shape[0] for im in xs],
+                                    [im.shape[1] for im in xs], [u.data_ptr() for u in us])
+
+    def psnr(self, images, codes, peak: float = 255.0):
+        """Per-sample 10 log10(peak^2 P / ||x_rec - x||^2) over the padded
+        P = N x N domain (Sec. IV; the paper uses peak 255 for 8-bit images)."""
+        import math
+
+        r2, _ = self.objective_terms(images, codes)
+        return [10.0 * math.log10(peak * peak * u.shape[-1] * u.shape[-2] / v) for u, v in zip(codes, r2)]
+
+    def rel_diff(self, a, b) -> float:
+        """||a - b|| / ||a|| of two float32 CUDA tensors of the same size."""
+        a = a.contiguous()
+        b = b.contiguous()
+        if a.numel() != b.numel():
+            raise ValueError("sizes differ")
+        return ocsc_rel_diff(self.ctx, a.data_ptr(), b.data_ptr(), a.numel())
+
+    def fit(self, images, max_passes: int = 10, tol: float = 1e-3, batch: int = 1):
+        """Online passes over `images` (Algorithm 3 per mini-batch) until the
+        stopping rule of Sec. IV holds: the relative change of the codes of the
+        current mini-batch against the previous pass and of the dictionary
+        against the previous update both below tol.  Returns a dict with the
+        pass and step where it stopped (or max_passes) and the last changes."""
+        import numpy as np
+
+        prev = [None] * len(images)
+        D_old = self.get_dict()
+        last = {"code_change": float("inf"), "dict_change": float("inf")}
+        for p in range(max_passes):
+            for t in range(0, len(images), batch):
+                idx = list(range(t, min(t + batch, len(images))))
+                us = self.code([images[i] for i in idx])
+                self.update_dict()
+                D = self.get_dict().astype(np.float64)
+                dz = max(self.rel_diff(u, prev[i]) if prev[i] is not None else float("inf")
+                         for u, i in zip(us, idx))
+                dd = float(np.linalg.norm(D - D_old) / max(np.linalg.norm(D), 1e-300))
+                for u, i in zip(us, idx):
+                    prev[i] = u
+                D_old = D
+                last = {"code_change": dz, "dict_change": dd}
+                if dz < tol and dd < tol:
+                    return {"stopped": True, "pass": p, "step": t // batch, **last}
+        return {"stopped": False, "pass": max_passes, "step": None, **last}
 
     def counters(self) -> dict:
         c = ocsc_get_counters(self.ctx)

@@ -165,5 +165,9 @@ int objective_partials(int N);
 cudaError_t launch_objective(int K, int N, double lam, const float2 *Dh, const float2 *xh,
                              const float2 *Uh, const float *u, double *partial, double *out,
                              cudaStream_t s);
+// ||a - b|| / ||a|| over count floats (FP64, fixed order); partial holds
+// 2 kObjL1Blocks doubles.
+cudaError_t launch_rel_diff(const float *a, const float *b, size_t count, double *partial, double *out,
+                            cudaStream_t s);
 
 }  // namespace ocsc

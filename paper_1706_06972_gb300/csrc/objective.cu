@@ -62,7 +62,9 @@ __global__ void __launch_bounds__(kObjBlock)
   if (threadIdx.x == 0) partial[blockIdx.x] = t;
 }
 
-// out = a * sum(pa[0..na)) + b * sum(pb[0..nb)), summed in index order.
+// out[0] = a sa / 2 + b sb, out[1] = a sa, out[2] = sb with sa = sum(pa[0..na)),
+// sb = sum(pb[0..nb)), summed in index order: the objective, the squared
+// residual norm ||x - sum_k D_k (*) U_k||^2 and ||U||_1.
 __global__ void objective_final_kernel(const double *__restrict__ pa, int na, double a,
                                        const double *__restrict__ pb, int nb, double b,
                                        double *__restrict__ out) {
@@ -70,7 +72,49 @@ __global__ void objective_final_kernel(const double *__restrict__ pa, int na, do
   double sa = 0.0, sb = 0.0;
   for (int i = 0; i < na; ++i) sa += pa[i];
   for (int i = 0; i < nb; ++i) sb += pb[i];
-  *out = a * sa + b * sb;
+  out[0] = 0.5 * a * sa + b * sb;
+  out[1] = a * sa;
+  out[2] = sb;
+}
+
+// Partial sums of (a - b)^2 and a^2, one pair per block.
+__global__ void __launch_bounds__(kObjBlock)
+    rel_diff_partial_kernel(const float *__restrict__ a, const float *__restrict__ b, size_t count,
+                            double *__restrict__ partial) {
+  __shared__ double red[32];
+  double d = 0.0, n = 0.0;
+  const size_t stride = (size_t)gridDim.x * kObjBlock;
+  for (size_t i = (size_t)blockIdx.x * kObjBlock + threadIdx.x; i < count; i += stride) {
+    const double x = a[i], y = b[i];
+    d += (x - y) * (x - y);
+    n += x * x;
+  }
+  const double td = block_sum(d, red);
+  __syncthreads();
+  const double tn = block_sum(n, red);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = td;
+    partial[2 * blockIdx.x + 1] = tn;
+  }
+}
+
+__global__ void rel_diff_final_kernel(const double *__restrict__ partial, int nb, double *__restrict__ out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double d = 0.0, n = 0.0;
+  for (int i = 0; i < nb; ++i) {
+    d += partial[2 * i];
+    n += partial[2 * i + 1];
+  }
+  *out = n > 0.0 ? sqrt(d / n) : (d > 0.0 ? INFINITY : 0.0);
+}
+
+cudaError_t launch_rel_diff(const float *a, const float *b, size_t count, double *partial, double *out,
+                            cudaStream_t s) {
+  rel_diff_partial_kernel<<<kObjL1Blocks, kObjBlock, 0, s>>>(a, b, count, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  rel_diff_final_kernel<<<1, 32, 0, s>>>(partial, kObjL1Blocks, out);
+  return cudaGetLastError();
 }
 
 int objective_partials(int N) {
@@ -89,7 +133,7 @@ cudaError_t launch_objective(int K, int N, double lam, const float2 *Dh, const f
   l1_partial_kernel<<<kObjL1Blocks, kObjBlock, 0, s>>>(u, (size_t)K * N * N, partial + nr);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  objective_final_kernel<<<1, 32, 0, s>>>(partial, nr, 0.5 / ((double)N * N), partial + nr, kObjL1Blocks, lam,
+  objective_final_kernel<<<1, 32, 0, s>>>(partial, nr, 1.0 / ((double)N * N), partial + nr, kObjL1Blocks, lam,
                                           out);
   return cudaGetLastError();
 }

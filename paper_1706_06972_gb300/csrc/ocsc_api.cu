@@ -245,7 +245,8 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
     if ((st = dalloc(c, &c->work, factor_big_workspace(K, sms)))) return bail(st);
   }
   if ((st = dalloc(c, &c->V, (size_t)K * c->M * c->M)) || (st = dalloc(c, &c->err, 1)) ||
-      (st = dalloc(c, &c->obj_part, (size_t)max_partials)) || (st = dalloc(c, &c->obj_out, (size_t)kObjChunk)))
+      (st = dalloc(c, &c->obj_part, (size_t)std::max(max_partials, 2 * kObjL1Blocks))) ||
+      (st = dalloc(c, &c->obj_out, (size_t)3 * kObjChunk)))
     return bail(st);
   cudaError_t e = cudaMemset(c->err, 0, sizeof(int));
   if (e != cudaSuccess) { cuda_fail(c, e, "clear error word"); return bail(OCSC_ECUDA); }
@@ -857,10 +858,10 @@ ocsc_status ocsc_drop_pending(ocsc_ctx *c) {
   return OCSC_OK;
 }
 
-ocsc_status ocsc_objective(ocsc_ctx *c, int n, const float *const *x, const int *H, const int *W,
-                           const float *const *u, double *out_host) {
+static ocsc_status objective_terms(ocsc_ctx *c, int n, const float *const *x, const int *H, const int *W,
+                                   const float *const *u, double *f_host, double *r2_host, double *l1_host) {
   if (!c) return OCSC_EINVAL;
-  if (n < 0 || (n > 0 && (!x || !H || !W || !u || !out_host)))
+  if (n < 0 || (n > 0 && (!x || !H || !W || !u || !(f_host || r2_host || l1_host))))
     return fail(c, OCSC_EINVAL, "ocsc_objective: bad arguments");
   std::vector<int> cl(n);
   for (int i = 0; i < n; ++i) {
@@ -910,16 +911,50 @@ ocsc_status ocsc_objective(ocsc_ctx *c, int n, const float *const *x, const int 
         c->counters.kernel_launches += 2;  // three kernels in launch_objective
         e = timed(c, OCSC_K_COUNT, [&] {
           return launch_objective(c->K, s.N, c->lam, coding_spectrum(c, s), s.obj_xh, Uh, u[s0 + i], c->obj_part,
-                                  c->obj_out + i, c->stream);
+                                  c->obj_out + 3 * i, c->stream);
         });
       }
       if (e != cudaSuccess) return cuda_fail(c, e, "objective");
     }
-    cudaError_t e = cudaMemcpyAsync(out_host + s0, c->obj_out, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    std::vector<double> h((size_t)3 * m);
+    cudaError_t e = cudaMemcpyAsync(h.data(), c->obj_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "objective readback");
+    for (int i = 0; i < m; ++i) {
+      if (f_host) f_host[s0 + i] = h[3 * i];
+      if (r2_host) r2_host[s0 + i] = h[3 * i + 1];
+      if (l1_host) l1_host[s0 + i] = h[3 * i + 2];
+    }
   }
   return OCSC_OK;
+}
+
+ocsc_status ocsc_objective(ocsc_ctx *c, int n, const float *const *x, const int *H, const int *W,
+                           const float *const *u, double *out_host) {
+  if (!c) return OCSC_EINVAL;
+  if (n > 0 && !out_host) return fail(c, OCSC_EINVAL, "ocsc_objective: bad arguments");
+  return objective_terms(c, n, x, H, W, u, out_host, nullptr, nullptr);
+}
+
+ocsc_status ocsc_objective_terms(ocsc_ctx *c, int n, const float *const *x, const int *H, const int *W,
+                                 const float *const *u, double *resid2_host, double *l1_host) {
+  if (!c) return OCSC_EINVAL;
+  if (n > 0 && (!resid2_host || !l1_host)) return fail(c, OCSC_EINVAL, "ocsc_objective_terms: bad arguments");
+  return objective_terms(c, n, x, H, W, u, nullptr, resid2_host, l1_host);
+}
+
+ocsc_status ocsc_rel_diff(ocsc_ctx *c, const float *a, const float *b, size_t count, double *out_host) {
+  if (!c) return OCSC_EINVAL;
+  if (!a || !b || !out_host) return fail(c, OCSC_EINVAL, "ocsc_rel_diff: bad arguments");
+  if (count == 0) {
+    *out_host = 0.0;
+    return OCSC_OK;
+  }
+  c->counters.kernel_launches += 2;
+  cudaError_t e = launch_rel_diff(a, b, count, c->obj_part, c->obj_out, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, c->obj_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "rel_diff");
 }
 
 ocsc_status ocsc_get_counters(const ocsc_ctx *c, ocsc_counters *out) {

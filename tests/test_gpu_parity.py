@@ -523,3 +523,52 @@ def test_autotuned_tiles_do_not_change_results(precision):
     assert t[256]["spat_cb"] in (8, 16) and t[64]["spat_cb"] == 0
     if precision:
         assert t[64]["gram_sc"] in (32, 64, 128)
+
+
+# --- evaluation of Sec. IV: objective terms, PSNR, relative change, passes ---------
+
+def test_objective_terms_psnr_and_rel_diff_match_oracle():
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    K, M, N, lam = 8, 5, 64, 0.5
+    raw = raw_filters(K, M, 111)
+    lr = pkg.OCSC(K, M, lam, 1.0, fft_sizes=[64, 96], pad=4, Jz=12, Jd=3, max_batch=2)
+    lr.set_dict(raw, normalize=True)
+    imgs = [make_image(s, s, 1600 + i) for i, s in enumerate([60, 80])]
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    us = lr.code(xs)
+    r2, l1 = lr.objective_terms(xs, us)
+    ps = lr.psnr(xs, us, peak=4.0)
+    D = lr.get_dict().astype(np.float64)
+    for im, u, a, b, q in zip(imgs, us, r2, l1, ps):
+        Nn = u.shape[-1]
+        U = u.cpu().numpy().astype(np.float64)
+        xp = oracle.pad_to(np.asarray(im, np.float64), Nn, Nn)
+        r = oracle.reconstruct(D, U) - xp
+        assert abs(a - float(np.sum(r * r))) / float(np.sum(r * r)) < 1e-5
+        assert abs(b - float(np.sum(np.abs(U)))) / float(np.sum(np.abs(U))) < 1e-12
+        assert abs(q - oracle.psnr(D, U, xp, peak=4.0)) < 1e-4
+    v = lr.rel_diff(us[0], 0.75 * us[0])
+    assert abs(v - 0.25) < 1e-7
+    assert abs(lr.rel_diff(us[0], us[0] * 0 + us[0])) == 0.0
+    lr.drop_pending()
+    lr.close()
+
+
+def test_fit_stops_by_the_rule_of_the_paper():
+    """Passes over four images until the codes and the dictionary change by
+    less than tol between passes (a loose tol so that it stops quickly)."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    K, M = 4, 5
+    lr = pkg.OCSC(K, M, 0.5, 1.0, fft_size=64, pad=4, Jz=20, Jd=5, max_batch=2)
+    lr.set_dict(raw_filters(K, M, 121), normalize=True)
+    xs = [torch.from_numpy(make_image(60, 60, 1700 + i)).cuda() for i in range(4)]
+    res = lr.fit(xs, max_passes=40, tol=5e-2, batch=2)
+    assert res["stopped"] and res["pass"] >= 1
+    assert res["code_change"] < 5e-2 and res["dict_change"] < 5e-2
+    order = pkg.filter_order(lr.get_dict())
+    assert sorted(order.tolist()) == list(range(K))
+    lr.close()

@@ -451,3 +451,34 @@ def test_two_class_consensus_reaches_pooled_constrained_optimum():
             if nv > 1:
                 v[k * M * M:(k + 1) * M * M] = seg / nv
     np.testing.assert_allclose(V.reshape(-1), v, atol=1e-6)
+
+
+# --- evaluation of Sec. IV -------------------------------------------------------
+
+def test_psnr_closed_form():
+    """Reconstruction off by a constant c everywhere: ||x_rec - x||^2 = c^2 P, so
+    PSNR = 10 log10(peak^2 / c^2) whatever the image."""
+    rng = np.random.default_rng(3)
+    K, M, n = 3, 3, 16
+    D = rng.standard_normal((K, M, M))
+    U = rng.standard_normal((K, n, n))
+    x_rec = oracle.reconstruct(D, U)
+    c = 0.25
+    val = oracle.psnr(D, U, x_rec - c, peak=2.0)
+    assert abs(val - 10.0 * np.log10(4.0 / c ** 2)) < 1e-9
+
+
+def test_rel_change_closed_form():
+    a = np.arange(1.0, 7.0).reshape(2, 3)
+    assert abs(oracle.rel_change(a, 0.9 * a) - 0.1) < 1e-15
+    assert oracle.rel_change(a, a) == 0.0
+    assert oracle.rel_change(np.zeros(3), np.ones(3)) == float("inf")
+
+
+def test_filter_order_by_variance():
+    """2 x 2 filters: entries 1,2,3,4 have variance 5/3 (mean 2.5, squared
+    deviations 2.25 + 0.25 + 0.25 + 2.25 over 3); constant filters 0."""
+    D = np.stack([np.array([[1.0, 2.0], [3.0, 4.0]]),
+                  np.full((2, 2), 7.0),
+                  np.array([[0.0, 0.0], [0.0, 3.0]])])        # mean 0.75, var (3*0.5625+5.0625)/3 = 2.25
+    assert list(oracle.filter_order(D)) == [1, 0, 2]
