@@ -384,6 +384,50 @@ def precision_leg(pkg, dev, stream, args):
     return out
 
 
+def recursion_leg(pkg, w, dev, stream, args):
+    """The recursion variant of the history (eq. C_update: C^p kept in FP64 and
+    updated in O(K^2) per sample, the ADMM penalty rho / t that matches its
+    decaying ridge) against the per-sample factorisation, both under the
+    paper's rho P, on the headline workload (B = 1): images/s, per-kernel ms
+    per sample (the recursion's fold is timed as fold_factor), and the held-out
+    objective and PSNR after the same samples."""
+    import torch
+
+    W, n = 3, args.recursion_steps
+    xs = [torch.from_numpy(w.image(i)).to(dev) for i in range(W + n)]
+    kinds = ["image_spectrum", "code_resid", "code_plane", "fold_factor", "dstep", "vstep_cols",
+             "vstep_project", "vstep_spectrum", "dict_norms"]
+    out = {"workload": WORKLOAD, "rho_convention": "paper (rho P)", "steps": n}
+    for hist, name in ((0, "factor"), (1, "recursion")):
+        lr = pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_size=128, pad=w.pad, Jz=w.Jz, Jd=w.Jd,
+                      max_batch=1, graphs=args.graphs, history=hist, rho_convention=1)
+        lr.set_dict(w.filters0(), normalize=True)
+        for i in range(W):
+            lr.code([xs[i]], want_codes=False)
+            lr.update_dict()
+        lr.sync()
+        lr.profile(kinds)
+        lr.profile_read(kinds)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(W, W + n):
+            lr.code([xs[i]], want_codes=False)
+            lr.update_dict()
+        e1.record(stream)
+        e1.synchronize()
+        secs = e0.elapsed_time(e1) / 1e3
+        prof = lr.profile_read(kinds)
+        lr.profile([])
+        obj, psnr = test_objective(pkg, lr, w, dev)
+        lr.close()
+        out[name] = {"value": n / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / n,
+                     "ms_per_step_by_kernel": {k: v[0] / n for k, v in prof.items() if v[1]},
+                     "test_objective": obj, "test_psnr_db": psnr, "samples_seen": W + n}
+        torch.cuda.empty_cache()
+    return out
+
+
 SERVING_CLASSES = (96, 128, 144, 192, 256, 288, 384, 512, 576)
 
 
@@ -569,6 +613,7 @@ def ours_arm(args):
     mixed = mixed_leg(pkg, dev, stream, args) if args.mixed_steps > 0 and "mixed" in legs else None
     serving = serving_leg(pkg, dev, stream, args) if args.serve_requests > 0 and "serving" in legs else None
     precision = precision_leg(pkg, dev, stream, args) if args.precision_steps > 0 and "precision" in legs else None
+    recursion = recursion_leg(pkg, w, dev, stream, args) if args.recursion_steps > 0 and "recursion" in legs else None
 
     if rank != 0:
         return
@@ -602,6 +647,7 @@ def ours_arm(args):
         "mixed_sizes": mixed,
         "serving": serving,
         "precision": precision,
+        "recursion": recursion,
     }
     print(json.dumps(line))
 
@@ -661,7 +707,9 @@ def main():
                     help="1: ocsc_code replays a CUDA graph per chunk shape (plain and batched legs)")
     ap.add_argument("--precision-steps", type=int, default=2,
                     help="timed batches of 128 per variant in the precision leg (0: skip)")
-    ap.add_argument("--legs", default="plain,batched,mixed,serving,precision",
+    ap.add_argument("--recursion-steps", type=int, default=40,
+                    help="timed samples of each history variant in the recursion leg (0: skip)")
+    ap.add_argument("--legs", default="plain,batched,mixed,serving,precision,recursion",
                     help="comma list of legs to run (profiling runs pick one); the headline needs plain")
     ap.add_argument("--batch", type=int, default=64, help="mini-batch of the batched leg")
     ap.add_argument("--batched-steps", type=int, default=4, help="timed batches of the batched leg (0: skip)")

@@ -113,6 +113,17 @@ typedef struct {
                          slots and launch the graph (codes are copied out).
                          Not used while coding kernels are profiled.  0
                          (default): every launch is issued directly. */
+  int history;        /* 0 (default): keep A^p and factor w A^p + rho I in FP64
+                         at every update (the C^p definition of eq.
+                         (sub_d_sol)).  1: keep C^p itself and apply the
+                         printed Sherman-Morrison recursion of eq. (C_update)
+                         per folded sample (FP64, O(K^2)); it yields
+                         C_t = (A_t + (rho P / t) I)^-1, a ridge that decays
+                         with the sample count t.  Needs rho_convention 1 (the
+                         printed rho P: with the spatial rho the first C
+                         already has a condition number near |z|^2 / rho and
+                         the rank-one downdates diverge, in FP64 too), one FFT
+                         size, precision 0 and K <= 128. */
 } ocsc_opts;
 
 /* Fill *o with the defaults listed above. */

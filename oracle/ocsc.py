@@ -215,8 +215,35 @@ class DictState:
     Dh_last: np.ndarray     # [K, n1, n2] D~_{t,J} of the last update
 
 
+def sm_fold(C, Zh_list, n: int, r: float):
+    """The printed recursion of eq. (C_update) over a batch of codes in order.
+
+    Sample number t = n + 1, n + 2, ...:
+      t = 1:  C = I / r - conj(z) z^T / (r (r + z^T conj(z)))
+      t > 1:  C = t/(t-1) [C - C conj(z) z^T C / ((t-1) + z^T C conj(z))]
+    with z = Z~(p, :)^T at every frequency and r = rho (rho P under the paper's
+    convention).  C_t = (A_t + (r / t) I)^-1 (reading R3), the inverse of
+    eq. (sub_d_sol) for the penalty rho / t, which DictOCSC then uses (R23).
+    Returns C [n1, n2, K, K].
+    """
+    for i, Zh in enumerate(Zh_list):
+        t = n + 1 + i
+        z = np.moveaxis(Zh, 0, -1)                        # [n1, n2, K]
+        zc = np.conj(z)[..., :, None]                     # conj(z), K x 1
+        zr = z[..., None, :]                              # z^T, 1 x K
+        if t == 1:
+            K = z.shape[-1]
+            nz = np.real(zr @ zc)                         # [n1, n2, 1, 1]
+            C = np.eye(K) / r - (zc @ zr) / (r * (r + nz))
+        else:
+            u = C @ zc                                    # C conj(z)
+            den = (t - 1) + (zr @ u)
+            C = (t / (t - 1)) * (C - (u @ (zr @ C)) / den)
+    return C
+
+
 def dict_ocsc(h: History, V: np.ndarray, thetah: np.ndarray, rho: float, iters: int,
-              rho_convention: str = "spatial"):
+              rho_convention: str = "spatial", C=None):
     """DictOCSC (Algorithm 2) on the current history.
 
     C^p = (A^p + rho I)^-1 (eq. sub_d_sol; rho*P under the paper's convention).
@@ -224,14 +251,16 @@ def dict_ocsc(h: History, V: np.ndarray, thetah: np.ndarray, rho: float, iters: 
         D~(p,:) = C^p (b^p + rho (V^(p) - theta^(p)))       (eq. sub_d_sol)
         V_k     = Prop. 2 projection of H(F^-1(D~_k + theta^_k))
         theta^  = theta^ + D~ - F(V)
-    Returns (V, theta^, D~_{t,J}).
+    Returns (V, theta^, D~_{t,J}).  A given C (the recursion of eq. C_update)
+    replaces the inverse.
     """
     K, M = V.shape[0], V.shape[-1]
     n1, n2 = h.A.shape[0], h.A.shape[1]
     P = n1 * n2
     r = rho * P if rho_convention == "paper" else rho
     eye = np.eye(K)
-    C = np.linalg.inv(h.A + r * eye)                  # [n1, n2, K, K]
+    if C is None:
+        C = np.linalg.inv(h.A + r * eye)              # [n1, n2, K, K]
     Dh = None
     for _ in range(iters):
         Vh = filters_spectrum(V, n1, n2)              # [K, n1, n2]
@@ -264,11 +293,13 @@ class OCSCState:
     return_feasible: bool = True
     rho_convention: str = "spatial"
     updates: int = 0
+    history: str = "factor"     # "recursion": C from eq. (C_update) (variant)
+    C: np.ndarray = None        # [n1, n2, K, K] when history == "recursion"
 
 
 def init_state(raw_filters: np.ndarray, n1: int, n2: int, lam: float, rho: float,
                warm_start: bool = True, return_feasible: bool = True,
-               rho_convention: str = "spatial") -> OCSCState:
+               rho_convention: str = "spatial", history: str = "factor") -> OCSCState:
     """Algorithm 3 initialisation: D~_0 from Gaussian filters (R10), C = b = 0."""
     V = normalize_filters(raw_filters)
     K, M = V.shape[0], V.shape[-1]
@@ -276,7 +307,8 @@ def init_state(raw_filters: np.ndarray, n1: int, n2: int, lam: float, rho: float
                      thetah=np.zeros((K, n1, n2), np.complex128),
                      Dh=filters_spectrum(V, n1, n2),
                      hist=History.zeros(K, n1, n2), warm_start=warm_start,
-                     return_feasible=return_feasible, rho_convention=rho_convention)
+                     return_feasible=return_feasible, rho_convention=rho_convention,
+                     history=history)
 
 
 def code(state: OCSCState, image: np.ndarray, iters: int) -> CodeResult:
@@ -287,13 +319,27 @@ def code(state: OCSCState, image: np.ndarray, iters: int) -> CodeResult:
 
 def update_dict(state: OCSCState, results, iters: int) -> OCSCState:
     """Algorithm 3, history and dictionary steps for a batch of coded samples."""
+    n_before = state.hist.n
     state.hist = fold_history(state.hist, [r.Zh for r in results], [r.xh for r in results])
+    C = None
+    rho_d = state.rho
     if state.warm_start:
         V0, th0 = state.V, state.thetah
     else:
         V0 = np.zeros_like(state.V)
         th0 = np.zeros_like(state.thetah)
-    V, thetah, Dh_last = dict_ocsc(state.hist, V0, th0, state.rho, iters, state.rho_convention)
+    if state.history == "recursion":
+        r = state.rho * state.n1 * state.n2 if state.rho_convention == "paper" else state.rho
+        state.C = sm_fold(state.C, [r_.Zh for r_ in results], n_before, r)
+        C = state.C
+        # Reading R23: C_t = (A_t + (r / t) I)^-1 is the D-row minimiser's
+        # inverse for the penalty rho / t, so the ADMM runs with that penalty;
+        # the scaled dual keeps the unscaled dual rho Theta across updates.
+        t = state.hist.n
+        rho_d = state.rho / t
+        if n_before > 0:
+            th0 = th0 * (t / n_before)
+    V, thetah, Dh_last = dict_ocsc(state.hist, V0, th0, rho_d, iters, state.rho_convention, C=C)
     state.V, state.thetah = V, thetah
     state.Dh = filters_spectrum(V, state.n1, state.n2) if state.return_feasible else Dh_last
     state.updates += 1

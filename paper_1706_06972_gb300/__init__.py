@@ -38,7 +38,7 @@ class ocsc_opts(ctypes.Structure):
         ("max_batch", ctypes.c_int), ("fft_sizes", ctypes.c_int * MAX_FFT_SIZES), ("warm_start", ctypes.c_int),
         ("return_feasible", ctypes.c_int), ("rho_convention", ctypes.c_int),
         ("seed", ctypes.c_uint64), ("precision", ctypes.c_int), ("autotune", ctypes.c_int),
-        ("graphs", ctypes.c_int),
+        ("graphs", ctypes.c_int), ("history", ctypes.c_int),
     ]
 
 

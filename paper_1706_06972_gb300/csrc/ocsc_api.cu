@@ -109,6 +109,7 @@ ocsc_status alloc_class(ocsc_ctx *c, SizeClass &s, int N) {
       (st = dalloc(c, &s.Zp, B * KF)) || (st = dalloc(c, &s.xhp, B * s.F)) ||
       (st = dalloc(c, &s.obj_xh, (size_t)s.F)))
     return st;
+  if (c->opts.history == 1 && (st = dalloc(c, &s.Csm, (size_t)s.F * TS))) return st;
   if (c->opts.precision > 0) {
     if ((st = dalloc(c, &s.Alo, (size_t)s.F * TS))) return st;
     cudaError_t e = cudaMemset(s.Alo, 0, (size_t)s.F * TS * sizeof(float2));
@@ -165,6 +166,7 @@ void ocsc_default_opts(ocsc_opts *o) {
   o->precision = 0;
   o->autotune = 1;
   o->graphs = 0;
+  o->history = 0;
   o->seed = 0x5EEDull;
 }
 
@@ -200,6 +202,15 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
     return bail(OCSC_EUNSUPPORTED);
   }
   if (!(lambda >= 0) || !(rho > 0)) { fail(c, OCSC_EINVAL, "need lambda >= 0 and rho > 0"); return bail(OCSC_EINVAL); }
+  if (c->opts.history < 0 || c->opts.history > 1) {
+    fail(c, OCSC_EINVAL, "history must be 0 or 1");
+    return bail(OCSC_EINVAL);
+  }
+  if (c->opts.history == 1 &&
+      (c->opts.precision != 0 || K > 128 || c->opts.fft_sizes[1] != 0 || c->opts.rho_convention != 1)) {
+    fail(c, OCSC_EUNSUPPORTED, "history = 1 needs rho_convention 1, precision 0, K <= 128 and one FFT size");
+    return bail(OCSC_EUNSUPPORTED);
+  }
   if (c->opts.precision < 0 || c->opts.precision > 2) {
     fail(c, OCSC_EINVAL, "precision must be 0, 1 or 2");
     return bail(OCSC_EINVAL);
@@ -519,6 +530,25 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
     fa.L = s.X;
     fa.g = s.y;
     fa.err = c->err;
+    if (c->opts.history == 1) {
+      SmArgs sa{};
+      sa.K = c->K;
+      sa.F = s.F;
+      sa.B = s.pending;
+      sa.n = (int)s.n_seen;
+      sa.r = fa.rho_eff;
+      sa.alpha = (float)fa.alpha;
+      sa.beta = (float)fa.beta;
+      sa.Zp = s.Zp;
+      sa.xh = s.xhp;
+      sa.C = s.Csm;
+      sa.b = s.b;
+      if (s.pending > 0) {
+        e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_sm_fold(sa, c->stream); });
+        if (e != cudaSuccess) return cuda_fail(c, e, "history recursion");
+      }
+      continue;
+    }
     if (big_k(c) && c->opts.precision == 0 && s.pending > 0) {
       e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_big(fa, c->stream); });
       if (e != cudaSuccess) return cuda_fail(c, e, "history fold (K > 128)");
@@ -609,6 +639,14 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
     for (SizeClass *s : active) {
       const float rho_eff = (float)(c->opts.rho_convention == 1 ? c->rho * s->P : c->rho);
       e = timed(c, OCSC_K_DSTEP, [&] {
+        if (c->opts.history == 1) {
+          // Reading R23: penalty r / n after n folded samples; the scaled dual
+          // keeps rho Theta, so it grows by n / n_before at the first step.
+          const double nc = (double)(s->n_seen + s->pending);
+          const double ths = (t == 0 && s->n_seen > 0) ? nc / (double)s->n_seen : 1.0;
+          return launch_dstep_sm(c->K, s->F, (c->opts.rho_convention == 1 ? c->rho * s->P : c->rho) / nc, ths,
+                                 s->Csm, s->b, s->Vh, s->th, s->Dcur, s->E, c->stream);
+        }
         return big_k(c) ? launch_dstep_big(c->K, s->F, rho_eff, s->X, s->y, s->Vh, s->th, s->Dcur, s->E, c->stream)
                         : launch_dstep(c->K, s->F, rho_eff, s->X, s->y, s->Vh, s->th, s->Dcur, s->E, c->stream);
       });
@@ -668,7 +706,7 @@ constexpr uint32_t kStateFormat = 2;
 struct StateHeader {
   uint32_t magic, format;
   int32_t K, M, ncls, N[OCSC_MAX_FFT_SIZES];
-  int32_t rho_convention, return_feasible, warm_start, precision;
+  int32_t rho_convention, return_feasible, warm_start, precision, history;
   double lam, rho;
   int64_t n_seen;
   uint64_t version;
@@ -688,6 +726,7 @@ std::vector<std::pair<void *, size_t>> state_regions(ocsc_ctx *c) {
     r.emplace_back(s.b, kf);
     r.emplace_back(s.A, (size_t)s.F * tri_stride(c->K) * sizeof(float2));
     if (s.Alo) r.emplace_back(s.Alo, (size_t)s.F * tri_stride(c->K) * sizeof(float2));
+    if (s.Csm) r.emplace_back(s.Csm, (size_t)s.F * tri_stride(c->K) * sizeof(double2));
     r.emplace_back(s.dn, (size_t)s.F * sizeof(float));
   }
   return r;
@@ -714,6 +753,7 @@ StateHeader make_header(const ocsc_ctx *c) {
   h.return_feasible = c->opts.return_feasible;
   h.warm_start = c->opts.warm_start;
   h.precision = c->opts.precision;
+  h.history = c->opts.history;
   h.lam = c->lam;
   h.rho = c->rho;
   h.n_seen = c->n_seen;
@@ -760,7 +800,7 @@ ocsc_status ocsc_set_state(ocsc_ctx *c, const void *buf, size_t len) {
   bool same = h.magic == kStateMagic && h.format == kStateFormat && h.K == mine.K && h.M == mine.M &&
               h.ncls == mine.ncls && h.rho_convention == mine.rho_convention &&
               h.return_feasible == mine.return_feasible && h.warm_start == mine.warm_start &&
-              h.precision == mine.precision &&
+              h.precision == mine.precision && h.history == mine.history &&
               h.lam == mine.lam && h.rho == mine.rho;
   for (int i = 0; same && i < h.ncls; ++i) same = h.N[i] == mine.N[i];
   if (!same) return fail(c, OCSC_EINVAL, "set_state: the state was saved by a context of another shape or parameters");

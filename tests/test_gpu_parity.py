@@ -572,3 +572,51 @@ def test_fit_stops_by_the_rule_of_the_paper():
     order = pkg.filter_order(lr.get_dict())
     assert sorted(order.tolist()) == list(range(K))
     lr.close()
+
+
+# --- recursion variant of the history (eq. C_update, reading R3) ---------------------
+
+# The printed recursion comes with the printed rho P: C_t = (A_t + (rho P / t) I)^-1,
+# and DictOCSC runs with the matching penalty rho / t (reading R23).  (With the
+# spatial rho = 1 the ridge starts at 1 against |z|^2 ~ 1e4 and the oracle's own
+# FP64 recursion loses its accuracy within ten samples.)  C is FP64 on both sides;
+# the FP32 codes and b carry the usual coding error.
+RECURSION_DICT_TOL = REL_TOL
+
+@pytest.mark.parametrize("wname,N,nimg,batch", [("plain_64_k16", 64, 20, 1), ("plain_64_k16", 64, 12, 4),
+                                                ("plain_100in128_k100", 128, 2, 1)])
+def test_recursion_history_matches_oracle(wname, N, nimg, batch):
+    """history = 1: C from the printed Sherman-Morrison recursion (a ridge
+    decaying as rho / t), against the oracle's recursion mode sample by sample."""
+    _need_gpu()
+    w = WORKLOADS[wname]
+    imgs = [w.image(i) for i in range(nimg)]
+    raw = w.filters0()
+    codes, dicts = run_gpu(imgs, raw, w.K, w.M, w.lam, w.rho, N, w.Jz, w.Jd, batch=batch, pad=w.pad, history=1,
+                           rho_convention=1)
+    ocodes, odicts, ocd = run_oracle(imgs, raw, N, w.lam, w.rho, w.Jz, w.Jd, batch=batch, history="recursion",
+                                     rho_convention="paper")
+    derr = [rel(dicts[t], odicts[t]) for t in range(len(dicts))]
+    cerr = [rel(codes[t], ocodes[t]) for t in range(nimg)]
+    gcd = [oracle.normalize_filters(raw)] + dicts[:-1]
+    f_gpu = surrogate_objective(codes, gcd, imgs, N, w.lam, batch)
+    f_orc = surrogate_objective(ocodes, ocd, imgs, N, w.lam, batch)
+    print(f"recursion {wname} B={batch}: dictionary max {max(derr):.2e}, code max {max(cerr):.2e}, "
+          f"objective {abs(f_gpu - f_orc) / abs(f_orc):.2e}; per update {[f'{x:.1e}' for x in derr]}")
+    assert max(derr) < RECURSION_DICT_TOL and max(cerr) < RECURSION_DICT_TOL
+    assert abs(f_gpu - f_orc) / abs(f_orc) < OBJ_TOL
+
+
+def test_recursion_history_rejects_unsupported_setups():
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    with pytest.raises(pkg.OCSCError) as e:
+        pkg.OCSC(8, 5, 0.5, 1.0, fft_sizes=[64, 128], history=1, rho_convention=1)
+    assert e.value.status == 6
+    with pytest.raises(pkg.OCSCError) as e:
+        pkg.OCSC(8, 5, 0.5, 1.0, fft_size=64, history=1, precision=1, rho_convention=1)
+    assert e.value.status == 6
+    with pytest.raises(pkg.OCSCError) as e:
+        pkg.OCSC(8, 5, 0.5, 1.0, fft_size=64, history=1)
+    assert e.value.status == 6

@@ -482,3 +482,78 @@ def test_filter_order_by_variance():
                   np.full((2, 2), 7.0),
                   np.array([[0.0, 0.0], [0.0, 3.0]])])        # mean 0.75, var (3*0.5625+5.0625)/3 = 2.25
     assert list(oracle.filter_order(D)) == [1, 0, 2]
+
+
+def test_oracle_recursion_mode_equals_decaying_ridge_solve():
+    """sm_fold (the recursion variant of the oracle) against the definition it
+    reduces to: C_t = (A_t + (r / t) I)^-1 with A_t the running mean, over a
+    batch fold of 3 samples after 2 earlier ones; and one DictOCSC step with it
+    against the explicit solve."""
+    rng = np.random.default_rng(21)
+    K, n = 3, 4
+    r = 0.7
+    Zs = [rng.standard_normal((K, n, n)) + 1j * rng.standard_normal((K, n, n)) for _ in range(5)]
+    xs = [rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) for _ in range(5)]
+    h = oracle.History.zeros(K, n, n)
+    h = oracle.fold_history(h, Zs[:2], xs[:2])
+    C = oracle.sm_fold(None, Zs[:2], 0, r)
+    h = oracle.fold_history(h, Zs[2:], xs[2:])
+    C = oracle.sm_fold(C, Zs[2:], 2, r)
+    ref = np.linalg.inv(h.A + (r / 5) * np.eye(K))
+    assert np.max(np.abs(C - ref)) < 1e-10
+    V = oracle.normalize_filters(rng.standard_normal((K, 2, 2)))
+    th = np.zeros((K, n, n), complex)
+    _, _, Dh = oracle.dict_ocsc(h, V, th, r, 1, C=C)
+    rhs = h.b + r * np.moveaxis(oracle.filters_spectrum(V, n, n), 0, -1)
+    d = np.linalg.solve(h.A + (r / 5) * np.eye(K), rhs[..., None])[..., 0]
+    assert np.max(np.abs(np.moveaxis(Dh, 0, -1) - d)) < 1e-10
+
+
+def test_printed_recursion_with_the_fixed_penalty_diverges():
+    """Reading R23: with C_t from eq. (C_update) (ridge r / t) but the fixed
+    penalty rho on the right of eq. (sub_d_sol), each DictOCSC iteration scales
+    the components of D~ in the null space of A_t (t < K samples) by about
+    t - 1, so the iteration diverges; with the matching penalty rho / t it is an
+    ADMM and stays bounded."""
+    rng = np.random.default_rng(23)
+    K, n, M, t = 6, 8, 3, 4
+    Zs = [rng.standard_normal((K, n, n)) + 1j * rng.standard_normal((K, n, n)) for _ in range(t)]
+    xs = [rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)) for _ in range(t)]
+    h = oracle.fold_history(oracle.History.zeros(K, n, n), Zs, xs)
+    C = oracle.sm_fold(None, Zs, 0, 1.0)
+    V = oracle.normalize_filters(rng.standard_normal((K, M, M)))
+    th = np.zeros((K, n, n), complex)
+    grow = []
+    for iters in (10, 20):
+        _, _, Dh = oracle.dict_ocsc(h, V, th, 1.0, iters, C=C)
+        grow.append(np.abs(Dh).max())
+    assert grow[1] / grow[0] > (t - 1.5) ** 10           # geometric, ratio ~ t - 1
+    for iters in (10, 20):
+        _, _, Dh = oracle.dict_ocsc(h, V, th, 1.0 / t, iters, C=C)
+        assert np.abs(Dh).max() < 10.0
+
+
+def test_recursion_mode_update_equals_factorised_admm_at_rho_over_t():
+    """Two recursion-mode updates (batches of 2 and 3 samples, paper's rho P)
+    against DictOCSC on np.linalg.inv(A_t + (rho P / t) I), the penalty rho / t
+    and the scaled dual carried as rho Theta (reading R23)."""
+    import types
+
+    rng = np.random.default_rng(24)
+    K, n, M, rho, Jd = 4, 6, 3, 0.05, 4
+    raw = rng.standard_normal((K, M, M))
+    res = [types.SimpleNamespace(Zh=rng.standard_normal((K, n, n)) + 1j * rng.standard_normal((K, n, n)),
+                                 xh=rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+           for _ in range(5)]
+    st = oracle.init_state(raw, n, n, 0.1, rho, rho_convention="paper", history="recursion")
+    h = oracle.History.zeros(K, n, n)
+    V, th = oracle.normalize_filters(raw), np.zeros((K, n, n), complex)
+    for batch in (res[:2], res[2:]):
+        oracle.update_dict(st, batch, Jd)
+        nb = h.n
+        h = oracle.fold_history(h, [r.Zh for r in batch], [r.xh for r in batch])
+        if nb:
+            th = th * (h.n / nb)
+        V, th, _ = oracle.dict_ocsc(h, V, th, rho / h.n, Jd, rho_convention="paper")
+        assert np.max(np.abs(st.V - V)) < 1e-10
+        assert np.max(np.abs(st.thetah - th)) < 1e-10 * max(1.0, np.abs(th).max())
