@@ -653,13 +653,16 @@ def ours_arm(args):
 
 
 PROFILE_CASES = {
-    # name: (K, M, FFT size, images, image side, Jz, history precision)
+    # name: (K, M, FFT size, images, image side, Jz, history precision[, history variant])
     "large512": (32, 11, 512, 4, 400, 10, 0),
     "large256": (32, 11, 256, 8, 200, 10, 0),
     "code128": (100, 11, 128, 16, 100, 10, 0),
     # K = 256 dictionary step (tensor-core fold, blocked FP64 factor, substitution
     # D-step) on the FFT 64 grid: 2112 frequencies, ~1.7 GB of history and factor.
     "bigk64": (256, 11, 64, 8, 53, 5, 1),
+    # Recursion variant of the history (eq. C_update) at the headline sizes:
+    # K = 100, FFT 128, one sample per update; C is 672 MB of double-float.
+    "rec128": (100, 11, 128, 1, 100, 5, 0, 1),
 }
 
 
@@ -673,13 +676,15 @@ def profile_case(name: str) -> None:
     from workloads import make_image, raw_filters
 
     _build.build()
-    K, M, N, n, side, Jz, prec = PROFILE_CASES[name]
-    lr = pkg.OCSC(K, M, 1.0, 1.0, fft_size=N, pad=M - 1, Jz=Jz, Jd=2, max_batch=n, precision=prec)
+    K, M, N, n, side, Jz, prec, *rest = PROFILE_CASES[name]
+    hist = rest[0] if rest else 0
+    lr = pkg.OCSC(K, M, 1.0, 1.0, fft_size=N, pad=M - 1, Jz=Jz, Jd=2, max_batch=n, precision=prec,
+                  history=hist, rho_convention=1 if hist else 0)
     lr.set_dict(raw_filters(K, M, 3), normalize=True)
     xs = [torch.from_numpy(make_image(side, side, 100 + i)).cuda() for i in range(n)]
     for rep in range(2):
         lr.code(xs, want_codes=False)
-        if prec:
+        if prec or hist:
             lr.update_dict()
         else:
             lr.drop_pending()

@@ -26,7 +26,7 @@ struct SizeClass {
   // history and factor
   float2 *A = nullptr;      // [F][stride] packed FP32 history
   float2 *Alo = nullptr;    // [F][stride] its compensation word (precision > 0)
-  double2 *Csm = nullptr;   // [F][stride] C^p of the recursion variant (history = 1), FP64
+  float4 *Csf = nullptr;    // [F][stride] C^p of the recursion variant (history = 1), double-float
   float2 *b = nullptr;      // [K][F]
   float2 *X = nullptr;      // [F][stride] X = L^-1 (FP32) of the FP64 factor
   float2 *y = nullptr;      // [K][F] y = L^-1 (w b)

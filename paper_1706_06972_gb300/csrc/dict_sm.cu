@@ -11,11 +11,17 @@
 // is d = C (b + (r / t) (v^ - theta^)) (reading R23: with r itself on the right
 // the iteration grows by about t - 1 per step in the null space of A_t).
 //
-// sm_fold:  one CTA per frequency; C (packed lower, FP64) in shared memory for
-//           the whole batch; b folded as the running mean in FP32; stores C.
-// dstep_sm: one CTA per frequency, thread i owns row i of the Hermitian product
-//           (FP64); the caller passes r / t.
+// C is kept in double-float (an FP32 pair hi + lo per real number: 16 bytes per
+// complex entry, about 48 significant bits) and all O(K^2) work runs on the
+// FP32 pipe with error-free products (FMA) and sums (Knuth's TwoSum); the
+// per-sample scalars (z^T C conj(z), the scale factors) are FP64.
+// Both kernels take one CTA per frequency with the packed triangle in shared
+// memory, and split every row of the Hermitian product C x over kRowLanes
+// adjacent lanes (columns j = q mod kRowLanes), merged by shuffles in FP64.
+// sm_fold:  C for the whole batch; b folded as the running mean in FP32.
+// dstep_sm: the caller passes r / t.
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "launch.h"
 
 namespace ocsc {
@@ -23,6 +29,7 @@ namespace ocsc {
 namespace {
 
 constexpr int kSmThreads = 256;
+constexpr int kRowLanes = 2;  // lanes per row of a Hermitian product (divides 32)
 
 __device__ __forceinline__ double block_sum_d(double v, double *red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -35,153 +42,177 @@ __device__ __forceinline__ double block_sum_d(double v, double *red) {
   return t;
 }
 
+// Row i of C w over the columns j = q, q + kRowLanes, ... (C Hermitian, packed
+// lower, double-float [re hi, im hi, re lo, im lo]; w double-float likewise):
+// lower entries C_ij (j <= i) sit at tri_off(j) + i - j, upper ones
+// C_ij = conj(C_ji) at tri_off(i) + j - i, and both offsets advance by a fixed
+// rule per step.  Returns the partial (Re, Im) in FP64.
+__device__ __forceinline__ double2 herm_row_part(const float4 *sC, const float4 *sw, int K, int i, int q) {
+  constexpr int L = kRowLanes;
+  int lo = tri_off(q, K) + i - q, up = tri_off(i, K) + q - i;
+  float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f, E0 = 0.f, E1 = 0.f, E2 = 0.f, E3 = 0.f;
+#pragma unroll 2
+  for (int j = q; j < K; j += L) {
+    const bool low = j <= i;
+    const float4 c = sC[low ? lo : up];
+    const float4 w = sw[j];
+    const float yh = low ? c.y : -c.y, yl = low ? c.w : -c.w;
+    df_mac(c.x, c.z, w.x, w.z, S0, E0);    // Re C Re w
+    df_mac(-yh, -yl, w.y, w.w, S1, E1);    // -Im C Im w
+    df_mac(c.x, c.z, w.y, w.w, S2, E2);    // Re C Im w
+    df_mac(yh, yl, w.x, w.z, S3, E3);      // Im C Re w
+    lo += L * (K - j) - L * (L + 1) / 2;   // tri_off(j + L) - tri_off(j) - L
+    up += L;
+  }
+  return make_double2(((double)S0 + (double)S1) + ((double)E0 + (double)E1),
+                      ((double)S2 + (double)S3) + ((double)E2 + (double)E3));
+}
+
+// Sum of a row's kRowLanes partials (adjacent lanes of one warp).
+__device__ __forceinline__ double2 row_merge(double2 v) {
+#pragma unroll
+  for (int o = 1; o < kRowLanes; o <<= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
 }  // namespace
 
-// Shared memory: C [T] double2, z [K] double2, u [K] double2, two partial
-// halves of u [2][K] double2, red [32] double.
+// Shared memory: C [T] float4 (double-float), conj(z) as double-float [K]
+// float4, v = g u [K] float4 (double-float), u [K] double2, red [32] double.
 __global__ void __launch_bounds__(kSmThreads) sm_fold_kernel(SmArgs a) {
   extern __shared__ __align__(16) unsigned char smm[];
   const int K = a.K, F = a.F, T = tri_size(K), TS = tri_stride(K);
-  double2 *Cs = reinterpret_cast<double2 *>(smm);
-  double2 *z = Cs + T;
-  double2 *u = z + K;
-  double2 *uh = u + K;  // [2][K]
-  double *red = reinterpret_cast<double *>(uh + 2 * K);
+  float4 *Cs = reinterpret_cast<float4 *>(smm);
+  float4 *zc = Cs + T;
+  float4 *vv = zc + K;
+  double2 *u = reinterpret_cast<double2 *>(vv + K);
+  double *red = reinterpret_cast<double *>(u + K);
   const int p = blockIdx.x, tid = threadIdx.x;
-  double2 *Cg = a.C + (size_t)p * TS;
+  const int row = tid / kRowLanes, q = tid % kRowLanes, ii = row < K ? row : K - 1;
+  float4 *Cg = a.C + (size_t)p * TS;
   if (a.n > 0)
     for (int t = tid; t < T; t += kSmThreads) Cs[t] = Cg[t];
   float2 bacc = make_float2(0.f, 0.f);
   for (int s = 0; s < a.B; ++s) {
     const double t = (double)(a.n + 1 + s);
+    const bool first = a.n + s == 0;
     __syncthreads();
-    for (int k = tid; k < K; k += kSmThreads) {
-      const float2 v = a.Zp[((size_t)s * K + k) * F + p];
-      z[k] = make_double2(v.x, v.y);
-      if (k == tid) {
-        const float2 x = a.xh[(size_t)s * F + p];
-        bacc = cadd(bacc, cmulc(x, v));  // x~ conj(z)
-      }
+    if (tid < K) {
+      const float2 v = a.Zp[((size_t)s * K + tid) * F + p];
+      zc[tid] = make_float4(v.x, -v.y, 0.f, 0.f);  // conj(z), exact
+      const float2 x = a.xh[(size_t)s * F + p];
+      bacc = cadd(bacc, cmulc(x, v));  // x~ conj(z)
     }
-    if (a.n + s == 0) {  // C_0 = I / r
+    if (first) {  // C_0 = I / r
+      const float4 d = df_split2(1.0 / a.r, 0.0);
       for (int e = tid; e < T; e += kSmThreads) {
         int i, j;
         tri_ij(e, K, i, j);
-        Cs[e] = make_double2(i == j ? 1.0 / a.r : 0.0, 0.0);
+        Cs[e] = i == j ? d : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     __syncthreads();
-    // u = C conj(z): row i split over two threads (columns j even / odd).
-    for (int e = tid; e < 2 * K; e += kSmThreads) {
-      const int i = e >> 1, h = e & 1;
-      double2 acc = make_double2(0.0, 0.0);
-      for (int j = h; j < K; j += 2) {
-        const double2 c = j <= i ? Cs[tri_off(j, K) + i - j] : Cs[tri_off(i, K) + j - i];
-        const double cy = j <= i ? c.y : -c.y;  // C_ij = conj(C_ji) above the diagonal
-        const double2 zc = make_double2(z[j].x, -z[j].y);
-        acc.x = fma(c.x, zc.x, acc.x);
-        acc.x = fma(-cy, zc.y, acc.x);
-        acc.y = fma(c.x, zc.y, acc.y);
-        acc.y = fma(cy, zc.x, acc.y);
-      }
-      uh[h * K + i] = acc;
-    }
-    __syncthreads();
+    // u = C conj(z)
+    const double2 ui = row_merge(herm_row_part(Cs, zc, K, ii, q));
+    if (row < K && q == 0) u[row] = ui;
     double part = 0.0;
-    for (int i = tid; i < K; i += kSmThreads) {
-      const double2 ui = make_double2(uh[i].x + uh[K + i].x, uh[i].y + uh[K + i].y);
-      u[i] = ui;
-      part += z[i].x * ui.x - z[i].y * ui.y;  // Re(z_i u_i): z^T C conj(z) is real
-    }
+    __syncthreads();
+    if (tid < K) part = (double)zc[tid].x * u[tid].x + (double)zc[tid].y * u[tid].y;  // Re(z_i u_i), real
     const double zu = block_sum_d(part, red);
-    const bool first = a.n + s == 0;
     const double den = first ? 1.0 + zu : (t - 1.0) + zu;
     const double sc = first ? 1.0 : t / (t - 1.0);
-    const double inv = 1.0 / den;
+    // C <- sc C - v v^H with v = g u, g^2 = sc / den.
+    const double g = sqrt(sc / den);
+    if (tid < K) vv[tid] = df_split2(g * u[tid].x, g * u[tid].y);
+    __syncthreads();
+    const float sch = (float)sc, scl = (float)(sc - (double)sch);
     for (int e = tid; e < T; e += kSmThreads) {
       int i, j;
       tri_ij(e, K, i, j);
-      const double2 ui = u[i], uj = u[j];
-      double2 c = Cs[e];
-      // c - u_i conj(u_j) / den
-      c.x -= (ui.x * uj.x + ui.y * uj.y) * inv;
-      c.y -= (ui.y * uj.x - ui.x * uj.y) * inv;
-      Cs[e] = make_double2(sc * c.x, sc * c.y);
+      const float4 vi = vv[i], vj = vv[j], c = Cs[e];
+      // Re: sc Re c - (Re vi Re vj + Im vi Im vj);  Im: sc Im c - (Im vi Re vj - Re vi Im vj)
+      float Sr, Er, Si, Ei;
+      df_mul(c.x, c.z, sch, scl, Sr, Er);
+      df_mac(-vi.x, -vi.z, vj.x, vj.z, Sr, Er);
+      df_mac(-vi.y, -vi.w, vj.y, vj.w, Sr, Er);
+      df_mul(c.y, c.w, sch, scl, Si, Ei);
+      df_mac(-vi.y, -vi.w, vj.x, vj.z, Si, Ei);
+      df_mac(vi.x, vi.z, vj.y, vj.w, Si, Ei);
+      const float2 nr = two_sum(Sr, Er), ni = two_sum(Si, Ei);
+      Cs[e] = make_float4(nr.x, ni.x, nr.y, ni.y);
     }
   }
   __syncthreads();
   for (int t = tid; t < T; t += kSmThreads) Cg[t] = Cs[t];
-  for (int k = tid; k < K; k += kSmThreads) {
-    float2 *bp = a.b + (size_t)k * F + p;
+  if (tid < K) {
+    float2 *bp = a.b + (size_t)tid * F + p;
     const float2 old = a.n == 0 ? make_float2(0.f, 0.f) : *bp;
     *bp = make_float2(fmaf(a.alpha, old.x, a.beta * bacc.x), fmaf(a.alpha, old.y, a.beta * bacc.y));
   }
 }
 
-// d = C (b + r (v^ - theta^)) with C Hermitian (packed lower, FP64), in FP64:
-// C_t's ridge decays as r / t, so its condition number grows with t and an FP32
-// product would lose accuracy; also E = d + theta^.  ths != 1 rescales theta^
+// d = C (b + r (v^ - theta^)) with C Hermitian (packed lower, double-float);
+// w = b + r (v^ - theta^) is formed in FP64 and split the same way.  C_t's
+// ridge decays as r / t, so its condition number grows with t and a plain FP32
+// product would lose accuracy.  Also E = d + theta^; ths != 1 rescales theta^
 // first (stored back: the scaled dual after a change of penalty).
-__global__ void dstep_sm_kernel(int K, int F, double r, double ths, const double2 *__restrict__ C,
-                                const float2 *__restrict__ b, const float2 *__restrict__ Vh,
-                                float2 *__restrict__ th, float2 *__restrict__ Dcur,
-                                float2 *__restrict__ E) {
-  extern __shared__ __align__(16) double2 dsm_s[];
+__global__ void __launch_bounds__(kRowLanes * 128) dstep_sm_kernel(int K, int F, double r, double ths,
+                                                                   const float4 *__restrict__ Cf,
+                                                                   const float2 *__restrict__ b,
+                                                                   const float2 *__restrict__ Vh,
+                                                                   float2 *__restrict__ th,
+                                                                   float2 *__restrict__ Dcur,
+                                                                   float2 *__restrict__ E) {
+  extern __shared__ __align__(16) float4 dsm_s[];
   const int TS = tri_stride(K);
-  double2 *sC = dsm_s;
-  double2 *sw = sC + TS;
-  const int p = blockIdx.x, i = threadIdx.x;
-  const double2 *g = C + (size_t)p * TS;
-  for (int c = i; c < TS; c += blockDim.x) cp_async16(sC + c, g + c);
+  float4 *sC = dsm_s;
+  float4 *sw = sC + TS;
+  const int p = blockIdx.x, tid = threadIdx.x;
+  const int row = tid / kRowLanes, q = tid % kRowLanes, ii = row < K ? row : K - 1;
+  const float4 *g = Cf + (size_t)p * TS;
+  for (int c = tid; c < TS; c += blockDim.x) cp_async16(sC + c, g + c);
+  cp_async_commit();
   float2 thi = make_float2(0.f, 0.f);
-  if (i < K) {
-    const size_t o = (size_t)i * F + p;
+  const size_t o = (size_t)row * F + p;
+  if (row < K && q == 0) {
     const float2 v = Vh[o], bb = b[o];
     thi = th[o];
     if (ths != 1.0) {
       thi = make_float2((float)(ths * thi.x), (float)(ths * thi.y));
       th[o] = thi;
     }
-    sw[i] = make_double2((double)bb.x + r * ((double)v.x - thi.x), (double)bb.y + r * ((double)v.y - thi.y));
+    sw[row] = df_split2((double)bb.x + r * ((double)v.x - thi.x), (double)bb.y + r * ((double)v.y - thi.y));
   }
   cp_async_wait_all();
   __syncthreads();
-  if (i < K) {
-    double2 acc = make_double2(0.0, 0.0);
-    for (int j = 0; j < K; ++j) {
-      const bool low = j <= i;
-      const double2 c = low ? sC[tri_off(j, K) + i - j] : sC[tri_off(i, K) + j - i];
-      const double cy = low ? c.y : -c.y;
-      const double2 w = sw[j];
-      acc.x = fma(c.x, w.x, acc.x);
-      acc.x = fma(-cy, w.y, acc.x);
-      acc.y = fma(c.x, w.y, acc.y);
-      acc.y = fma(cy, w.x, acc.y);
-    }
-    const size_t o = (size_t)i * F + p;
-    const float2 d = make_float2((float)acc.x, (float)acc.y);
-    Dcur[o] = d;
-    E[o] = cadd(d, thi);
+  const double2 d = row_merge(herm_row_part(sC, sw, K, ii, q));  // idle lanes redo row K - 1
+  if (row < K && q == 0) {
+    const float2 df = make_float2((float)d.x, (float)d.y);
+    Dcur[o] = df;
+    E[o] = cadd(df, thi);
   }
 }
 
 cudaError_t launch_sm_fold(const SmArgs &a, cudaStream_t s) {
   if (a.K < 1 || a.K > 128) return cudaErrorInvalidValue;
   const int T = tri_size(a.K);
-  const size_t sm = ((size_t)T + 4 * a.K) * sizeof(double2) + 32 * sizeof(double);
+  const size_t sm = ((size_t)T + 2 * a.K) * sizeof(float4) + a.K * sizeof(double2) + 32 * sizeof(double);
   cudaError_t e = cudaFuncSetAttribute(sm_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   sm_fold_kernel<<<a.F, kSmThreads, sm, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_dstep_sm(int K, int F, double r, double ths, const double2 *C, const float2 *b,
+cudaError_t launch_dstep_sm(int K, int F, double r, double ths, const float4 *Cf, const float2 *b,
                             const float2 *Vh, float2 *th, float2 *Dcur, float2 *E, cudaStream_t s) {
-  if (K > 128) return cudaErrorInvalidValue;
-  const size_t sm = ((size_t)tri_stride(K) + K) * sizeof(double2);
+  if (K < 1 || K > 128) return cudaErrorInvalidValue;
+  const size_t sm = ((size_t)tri_stride(K) + K) * sizeof(float4);
   cudaError_t e = cudaFuncSetAttribute(dstep_sm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dstep_sm_kernel<<<F, 128, sm, s>>>(K, F, r, ths, C, b, Vh, th, Dcur, E);
+  dstep_sm_kernel<<<F, (kRowLanes * K + 31) / 32 * 32, sm, s>>>(K, F, r, ths, Cf, b, Vh, th, Dcur, E);
   return cudaGetLastError();
 }
 

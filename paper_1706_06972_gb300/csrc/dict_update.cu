@@ -6,61 +6,49 @@
 // solve of eq. (sub_d_sol) is d = (w A^p + rho I)^-1 (w b^p + rho (v^ - theta^)).
 // Its matrix is fixed during the Jd ADMM iterations, so it is factored once per
 // update: fold_factor folds the pending codes into A and b, forms w A + rho I in
-// FP64 in shared memory, factors it by Cholesky in FP64 (L), and alongside it
-// computes X = L^-1 in FP32 and y = L^-1 (w b) from the FP64 sweep.  Each ADMM
+// double-float (two FP32 words, about 48 bits; dfloat.cuh) in shared memory,
+// factors it by Cholesky in that arithmetic (L) on the FP32 pipe, and alongside
+// it computes X = L^-1 in FP32 and y = L^-1 (w b) from the same sweep.  Each ADMM
 // iteration then applies d = X^H (y + rho X (v^ - theta^)) in FP32 (dstep),
 // forms the V update of Proposition 2 from a pruned inverse DFT restricted to
 // the M x M support (vstep_cols, vstep_project, vstep_spectrum), and updates
 // the scaled dual.
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "launch.h"
 
 namespace ocsc {
-
-// acc -= a * conj(b) as four FP64 FMAs.
-__device__ __forceinline__ void cfms_conj(double2 &acc, double2 a, double2 b) {
-  acc.x = fma(-a.x, b.x, acc.x);
-  acc.x = fma(-a.y, b.y, acc.x);
-  acc.y = fma(-a.y, b.x, acc.y);
-  acc.y = fma(a.x, b.y, acc.y);
-}
-// acc -= a * b as four FP64 FMAs.
-__device__ __forceinline__ void cfms(double2 &acc, double2 a, double2 b) {
-  acc.x = fma(-a.x, b.x, acc.x);
-  acc.x = fma(a.y, b.y, acc.x);
-  acc.y = fma(-a.x, b.y, acc.y);
-  acc.y = fma(-a.y, b.x, acc.y);
-}
 
 constexpr int kFoldChunk = 16;  // samples staged in shared memory at once
 
 // One CTA per frequency p.
 //
 // 1-2. Fold the pending codes into the FP32 running means A^p, b^p and form
-//      M = w A + rho I, y = w b in FP64.
-// 3.   Right-looking FP64 Cholesky on the packed lower triangle, with y carried
-//      as an extra column (forward substitution: y <- L^-1 w b).  One step
-//      behind it, the same threads run the right-looking forward substitution
-//      of L X = I in FP32 (X = L^-1): after column s of L is final, row s of X
-//      is scaled by 1/L_ss and every X_ic with i > s, c <= s gets
-//      X_ic -= L_is X_sc.  The FP32 update of step s runs in the same phase as
-//      the FP64 trailing update of step s+1, on the other pipe, and writes only
-//      slots of columns <= s, whose FP64 values are no longer read: the low 8
-//      bytes of such a slot then hold X_ic.  L's column s (FP32 copy) and X's
-//      row s are kept in small buffers so those reads are broadcasts.
+//      M = w A + rho I, y = w b in double-float.
+// 3.   Right-looking double-float Cholesky on the packed lower triangle, with
+//      y carried as an extra column (forward substitution: y <- L^-1 w b); the
+//      pivots 1 / sqrt(.) are taken in FP64.  One step behind it, the same
+//      threads run the right-looking forward substitution of L X = I in FP32
+//      (X = L^-1): after column s of L is final, row s of X is scaled by
+//      1/L_ss and every X_ic with i > s, c <= s gets X_ic -= L_is X_sc.  The
+//      FP32 update of step s runs in the same phase as the trailing update of
+//      step s+1 and writes only slots of columns <= s, whose double-float
+//      values are no longer read: the first 8 bytes of such a slot then hold
+//      X_ic.  L's column s (FP32 copy) and X's row s are kept in small buffers
+//      so those reads are broadcasts.
 // 4.   Store X (FP32, packed lower) and y (FP32).
 //
-// Shared memory: M [T] double2, y [K] double2, invd [K] double, Lcol [2][K]
-// float2, Xrow [K] float2, zs / xs (a chunk of pending codes).  During the
-// fold each M slot first holds the FP32 running sum of conj(z_i) z_j in its low
-// 8 bytes.
+// Shared memory: M [T] float4, y [K] float4 (double-float), invd [K] double,
+// Lcol [2][K] float2, Xrow [K] float2, zs / xs (a chunk of pending codes).
+// During the fold each M slot first holds the FP32 running sum of
+// conj(z_i) z_j in its first 8 bytes.
 template <int kFoldThreads>
 __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int K = a.K, F = a.F, B = a.B;
   const int T = tri_size(K);
-  double2 *M = reinterpret_cast<double2 *>(fsm);                 // [T]
-  double2 *y = M + T;                                            // [K]
+  float4 *M = reinterpret_cast<float4 *>(fsm);                   // [T] double-float
+  float4 *y = M + T;                                             // [K] double-float
   double *invd = reinterpret_cast<double *>(y + K);              // [K]
   float2 *Lcol = reinterpret_cast<float2 *>(invd + K);           // [2][K]
   float2 *Xrow = Lcol + 2 * K;                                   // [K]
@@ -102,7 +90,8 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   }
   __syncthreads();
 
-  // 2. Running means in FP32 (stored), and M = w A + rho I, y = w b in FP64.
+  // 2. Running means in FP32 (stored), and M = w A + rho I, y = w b in
+  //    double-float.
   float2 *Ap = a.A + (size_t)p * tri_stride(K);
   const float alpha = (float)a.alpha, beta = (float)a.beta;
   const float2 *Lo = a.Alo ? a.Alo + (size_t)p * tri_stride(K) : nullptr;
@@ -126,7 +115,7 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
       hx = nw.x;
       hy = nw.y;
     }
-    M[t] = (i == j) ? make_double2(a.w * hx + a.rho_eff, 0.0) : make_double2(a.w * hx, a.w * hy);
+    M[t] = (i == j) ? df_split2(a.w * hx + a.rho_eff, 0.0) : df_split2(a.w * hx, a.w * hy);
   }
 #pragma unroll
   for (int m = 0; m < (128 + kFoldThreads - 1) / kFoldThreads; ++m) {
@@ -140,39 +129,49 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
         nw = make_float2(fmaf(alpha, old.x, beta * sb[m].x), fmaf(alpha, old.y, beta * sb[m].y));
         a.b[(size_t)i * F + p] = nw;
       }
-      y[i] = make_double2(a.w * (double)nw.x, a.w * (double)nw.y);
+      y[i] = df_split2(a.w * (double)nw.x, a.w * (double)nw.y);
     }
   }
   __syncthreads();
 
-  // 3. Cholesky (FP64) with the FP32 inverse one step behind.
+  // 3. Cholesky (double-float) with the FP32 inverse one step behind.  Slots
+  //    of M and y hold unnormalised pairs (S, E) while they are being updated
+  //    and are normalised when they become entries of L (scale phase).
   if (tid == 0) {
-    double piv = M[0].x;
+    double piv = df_val(M[0].x, M[0].z);
     if (!(piv > 0.0)) {
       atomicOr(a.err, ERR_PIVOT);
       piv = a.rho_eff > 0.0 ? a.rho_eff : 1.0;
     }
     const double r = rsqrt(piv);  // 1 / L_00; L_00 = piv / sqrt(piv)
-    M[0] = make_double2(piv * r, 0.0);
+    M[0] = df_split2(piv * r, 0.0);
     invd[0] = r;
   }
   __syncthreads();
   for (int j = 0; j <= K; ++j) {
-    // --- scale phase: column j of L (FP64 + FP32 copy), row j-1 of X.
+    // --- scale phase: column j of L (double-float + FP32 copy), row j-1 of X.
     if (j < K) {
       const int oj = tri_off(j, K);
-      const double inv = invd[j];
+      const float2 inv = df_of(invd[j]);
       float2 *lc = Lcol + (j & 1) * K;
       for (int i = j + 1 + tid; i < K; i += kFoldThreads) {
-        double2 v = M[oj + i - j];
-        v.x *= inv;
-        v.y *= inv;
-        M[oj + i - j] = v;
-        lc[i] = make_float2((float)v.x, (float)v.y);
+        const float4 v = M[oj + i - j];
+        const float2 vr = two_sum(v.x, v.z), vi = two_sum(v.y, v.w);
+        float Sr, Er, Si, Ei;
+        df_mul(vr.x, vr.y, inv.x, inv.y, Sr, Er);
+        df_mul(vi.x, vi.y, inv.x, inv.y, Si, Ei);
+        const float2 lr = two_sum(Sr, Er), li = two_sum(Si, Ei);
+        M[oj + i - j] = make_float4(lr.x, li.x, lr.y, li.y);
+        lc[i] = make_float2(lr.x, li.x);
       }
       if (tid == 0) {
-        y[j].x *= inv;
-        y[j].y *= inv;
+        const float4 v = y[j];
+        const float2 vr = two_sum(v.x, v.z), vi = two_sum(v.y, v.w);
+        float Sr, Er, Si, Ei;
+        df_mul(vr.x, vr.y, inv.x, inv.y, Sr, Er);
+        df_mul(vi.x, vi.y, inv.x, inv.y, Si, Ei);
+        const float2 yr = two_sum(Sr, Er), yi = two_sum(Si, Ei);
+        y[j] = make_float4(yr.x, yi.x, yr.y, yi.y);
       }
     }
     if (j >= 1) {
@@ -187,40 +186,48 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
       }
     }
     __syncthreads();
-    // --- update phase: FP64 trailing update of step j, FP32 X update of step j-1.
+    // --- update phase: trailing update of step j, FP32 X update of step j-1.
     if (j < K) {
       const int oj = tri_off(j, K);
       const int n = K - j - 1;
       const int nt = tri_size(n);
-      const double2 yj = y[j];
+      const float4 yj = y[j];
       if (tid == 0 && nt > 0) {  // element (j+1, j+1) also finishes the next pivot
         const int d1 = tri_off(j + 1, K);
-        const double2 l = M[oj + 1];
-        double2 v = M[d1];
-        cfms_conj(v, l, l);
-        double piv = v.x;
+        const float4 l = M[oj + 1], v = M[d1];
+        const double lx = df_val(l.x, l.z), ly = df_val(l.y, l.w);
+        double piv = df_val(v.x, v.z) - (lx * lx + ly * ly);
         if (!(piv > 0.0)) {
           atomicOr(a.err, ERR_PIVOT);
           piv = a.rho_eff > 0.0 ? a.rho_eff : 1.0;
         }
         const double r = rsqrt(piv);
-        M[d1] = make_double2(piv * r, 0.0);
+        M[d1] = df_split2(piv * r, 0.0);
         invd[j + 1] = r;
       }
       // One element per thread and round: only the last warp of the last
-      // round runs with idle lanes.
+      // round runs with idle lanes.  M_ik -= L_ij conj(L_kj).
       for (int u = 1 + tid; u < nt; u += kFoldThreads) {
         int ii, kk;
         tri_ij(u, n, ii, kk);
         const int dst = tri_off(j + 1 + kk, K) + ii - kk;
-        double2 v = M[dst];
-        cfms_conj(v, M[oj + 1 + ii], M[oj + 1 + kk]);
+        const float4 li = M[oj + 1 + ii], lk = M[oj + 1 + kk];
+        float4 v = M[dst];
+        df_mac(-li.x, -li.z, lk.x, lk.z, v.x, v.z);  // Re: - Re li Re lk - Im li Im lk
+        df_mac(-li.y, -li.w, lk.y, lk.w, v.x, v.z);
+        df_mac(-li.y, -li.w, lk.x, lk.z, v.y, v.w);  // Im: - Im li Re lk + Re li Im lk
+        df_mac(li.x, li.z, lk.y, lk.w, v.y, v.w);
         M[dst] = v;
       }
+      // y_i -= L_ij y_j.
       for (int u = tid; u < n; u += kFoldThreads) {
         const int i = j + 1 + u;
-        double2 v = y[i];
-        cfms(v, M[oj + i - j], yj);
+        const float4 l = M[oj + i - j];
+        float4 v = y[i];
+        df_mac(-l.x, -l.z, yj.x, yj.z, v.x, v.z);  // Re: - Re l Re y + Im l Im y
+        df_mac(l.y, l.w, yj.y, yj.w, v.x, v.z);
+        df_mac(-l.x, -l.z, yj.y, yj.w, v.y, v.w);  // Im: - Re l Im y - Im l Re y
+        df_mac(-l.y, -l.w, yj.x, yj.z, v.y, v.w);
         y[i] = v;
       }
     }
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   float2 *Xp = a.L + (size_t)p * tri_stride(K);
   for (int t = tid; t < T; t += kFoldThreads) Xp[t] = XS[2 * t];
   for (int i = tid; i < K; i += kFoldThreads)
-    a.g[(size_t)i * F + p] = make_float2((float)y[i].x, (float)y[i].y);
+    a.g[(size_t)i * F + p] = make_float2(y[i].x + y[i].z, y[i].y + y[i].w);
 }
 
 // D-row step of eq. (sub_d_sol): d = (w A + rho I)^-1 (w b + rho (v^ - theta^))

@@ -131,13 +131,14 @@ struct SmArgs {
   float alpha, beta;    // running mean of b: n/(n+B), 1/(n+B)
   const float2 *Zp;     // [B][K][F]
   const float2 *xh;     // [B][F]
-  double2 *C;           // [F][stride] C = (A + (r/t) I)^-1, packed lower, FP64
+  float4 *C;            // [F][stride] C = (A + (r/t) I)^-1, packed lower, double-float
+                        // (re hi, im hi, re lo, im lo)
   float2 *b;            // [K][F]
 };
 cudaError_t launch_sm_fold(const SmArgs &a, cudaStream_t s);
 // r is the penalty matching C's ridge; ths != 1 first rescales theta^ in place
 // (the scaled dual carried across a change of penalty).
-cudaError_t launch_dstep_sm(int K, int F, double r, double ths, const double2 *C, const float2 *b,
+cudaError_t launch_dstep_sm(int K, int F, double r, double ths, const float4 *Cf, const float2 *b,
                             const float2 *Vh, float2 *th, float2 *Dcur, float2 *E, cudaStream_t s);
 
 // K > 128 (dict_big.cu): FP32 fold into A, b; blocked FP64 Cholesky of

@@ -109,7 +109,7 @@ ocsc_status alloc_class(ocsc_ctx *c, SizeClass &s, int N) {
       (st = dalloc(c, &s.Zp, B * KF)) || (st = dalloc(c, &s.xhp, B * s.F)) ||
       (st = dalloc(c, &s.obj_xh, (size_t)s.F)))
     return st;
-  if (c->opts.history == 1 && (st = dalloc(c, &s.Csm, (size_t)s.F * TS))) return st;
+  if (c->opts.history == 1 && (st = dalloc(c, &s.Csf, (size_t)s.F * TS))) return st;
   if (c->opts.precision > 0) {
     if ((st = dalloc(c, &s.Alo, (size_t)s.F * TS))) return st;
     cudaError_t e = cudaMemset(s.Alo, 0, (size_t)s.F * TS * sizeof(float2));
@@ -541,7 +541,7 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
       sa.beta = (float)fa.beta;
       sa.Zp = s.Zp;
       sa.xh = s.xhp;
-      sa.C = s.Csm;
+      sa.C = s.Csf;
       sa.b = s.b;
       if (s.pending > 0) {
         e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_sm_fold(sa, c->stream); });
@@ -645,7 +645,7 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
           const double nc = (double)(s->n_seen + s->pending);
           const double ths = (t == 0 && s->n_seen > 0) ? nc / (double)s->n_seen : 1.0;
           return launch_dstep_sm(c->K, s->F, (c->opts.rho_convention == 1 ? c->rho * s->P : c->rho) / nc, ths,
-                                 s->Csm, s->b, s->Vh, s->th, s->Dcur, s->E, c->stream);
+                                 s->Csf, s->b, s->Vh, s->th, s->Dcur, s->E, c->stream);
         }
         return big_k(c) ? launch_dstep_big(c->K, s->F, rho_eff, s->X, s->y, s->Vh, s->th, s->Dcur, s->E, c->stream)
                         : launch_dstep(c->K, s->F, rho_eff, s->X, s->y, s->Vh, s->th, s->Dcur, s->E, c->stream);
@@ -726,7 +726,7 @@ std::vector<std::pair<void *, size_t>> state_regions(ocsc_ctx *c) {
     r.emplace_back(s.b, kf);
     r.emplace_back(s.A, (size_t)s.F * tri_stride(c->K) * sizeof(float2));
     if (s.Alo) r.emplace_back(s.Alo, (size_t)s.F * tri_stride(c->K) * sizeof(float2));
-    if (s.Csm) r.emplace_back(s.Csm, (size_t)s.F * tri_stride(c->K) * sizeof(double2));
+    if (s.Csf) r.emplace_back(s.Csf, (size_t)s.F * tri_stride(c->K) * sizeof(float4));
     r.emplace_back(s.dn, (size_t)s.F * sizeof(float));
   }
   return r;
