@@ -653,7 +653,7 @@ def ours_arm(args):
 
 
 PROFILE_CASES = {
-    # name: (K, M, FFT size, images, image side, Jz, history precision[, history variant])
+    # name: (K, M, FFT size, images, image side, Jz, history precision[, history variant[, update]])
     "large512": (32, 11, 512, 4, 400, 10, 0),
     "large256": (32, 11, 256, 8, 200, 10, 0),
     "code128": (100, 11, 128, 16, 100, 10, 0),
@@ -663,6 +663,8 @@ PROFILE_CASES = {
     # Recursion variant of the history (eq. C_update) at the headline sizes:
     # K = 100, FFT 128, one sample per update; C is 672 MB of double-float.
     "rec128": (100, 11, 128, 1, 100, 5, 0, 1),
+    # The factorisation (fold_factor) at the headline sizes: K = 100, FFT 128.
+    "fold128": (100, 11, 128, 1, 100, 5, 0, 0, 1),
 }
 
 
@@ -678,13 +680,14 @@ def profile_case(name: str) -> None:
     _build.build()
     K, M, N, n, side, Jz, prec, *rest = PROFILE_CASES[name]
     hist = rest[0] if rest else 0
+    upd = prec or hist or (len(rest) > 1 and rest[1])
     lr = pkg.OCSC(K, M, 1.0, 1.0, fft_size=N, pad=M - 1, Jz=Jz, Jd=2, max_batch=n, precision=prec,
                   history=hist, rho_convention=1 if hist else 0)
     lr.set_dict(raw_filters(K, M, 3), normalize=True)
     xs = [torch.from_numpy(make_image(side, side, 100 + i)).cuda() for i in range(n)]
     for rep in range(2):
         lr.code(xs, want_codes=False)
-        if prec or hist:
+        if upd:
             lr.update_dict()
         else:
             lr.drop_pending()

@@ -31,23 +31,34 @@ namespace {
 constexpr int kSmThreads = 256;
 constexpr int kRowLanes = 2;  // lanes per row of a Hermitian product (divides 32)
 
-__device__ __forceinline__ double block_sum_d(double v, double *red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// (S, E) + (S2, E2) as an unnormalised pair.
+__device__ __forceinline__ void df_acc(float &S, float &E, float S2, float E2) {
+  const float2 s = two_sum(S, S2);
+  S = s.x;
+  E = (E + E2) + s.y;
+}
+
+// Block-wide sum of an unnormalised pair, in a fixed order, returned to every
+// thread normalised.
+__device__ __forceinline__ float2 block_sum_df(float S, float E, float2 *red) {
+  for (int o = 16; o > 0; o >>= 1)
+    df_acc(S, E, __shfl_xor_sync(0xffffffffu, S, o), __shfl_xor_sync(0xffffffffu, E, o));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
-  if (lane == 0) red[warp] = v;
+  if (lane == 0) red[warp] = make_float2(S, E);
   __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];  // fixed order, every thread
-  return t;
+  float tS = 0.f, tE = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) df_acc(tS, tE, red[w].x, red[w].y);
+  return two_sum(tS, tE);
 }
 
 // Row i of C w over the columns j = q, q + kRowLanes, ... (C Hermitian, packed
 // lower, double-float [re hi, im hi, re lo, im lo]; w double-float likewise):
 // lower entries C_ij (j <= i) sit at tri_off(j) + i - j, upper ones
 // C_ij = conj(C_ji) at tri_off(i) + j - i, and both offsets advance by a fixed
-// rule per step.  Returns the partial (Re, Im) in FP64.
-__device__ __forceinline__ double2 herm_row_part(const float4 *sC, const float4 *sw, int K, int i, int q) {
+// rule per step.  Returns the partial as unnormalised pairs (S re, E re, S im,
+// E im).
+__device__ __forceinline__ float4 herm_row_part(const float4 *sC, const float4 *sw, int K, int i, int q) {
   constexpr int L = kRowLanes;
   int lo = tri_off(q, K) + i - q, up = tri_off(i, K) + q - i;
   float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f, E0 = 0.f, E1 = 0.f, E2 = 0.f, E3 = 0.f;
@@ -64,32 +75,39 @@ __device__ __forceinline__ double2 herm_row_part(const float4 *sC, const float4 
     lo += L * (K - j) - L * (L + 1) / 2;   // tri_off(j + L) - tri_off(j) - L
     up += L;
   }
-  return make_double2(((double)S0 + (double)S1) + ((double)E0 + (double)E1),
-                      ((double)S2 + (double)S3) + ((double)E2 + (double)E3));
+  df_acc(S0, E0, S1, E1);
+  df_acc(S2, E2, S3, E3);
+  return make_float4(S0, E0, S2, E2);
 }
 
-// Sum of a row's kRowLanes partials (adjacent lanes of one warp).
-__device__ __forceinline__ double2 row_merge(double2 v) {
+// Sum of a row's kRowLanes partials (adjacent lanes of one warp), normalised:
+// (re hi, im hi, re lo, im lo).
+__device__ __forceinline__ float4 row_merge(float4 v) {
 #pragma unroll
   for (int o = 1; o < kRowLanes; o <<= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    const float a = __shfl_xor_sync(0xffffffffu, v.x, o), b = __shfl_xor_sync(0xffffffffu, v.y, o);
+    const float c = __shfl_xor_sync(0xffffffffu, v.z, o), d = __shfl_xor_sync(0xffffffffu, v.w, o);
+    df_acc(v.x, v.y, a, b);
+    df_acc(v.z, v.w, c, d);
   }
-  return v;
+  const float2 re = two_sum(v.x, v.y), im = two_sum(v.z, v.w);
+  return make_float4(re.x, im.x, re.y, im.y);
 }
 
 }  // namespace
 
 // Shared memory: C [T] float4 (double-float), conj(z) as double-float [K]
-// float4, v = g u [K] float4 (double-float), u [K] double2, red [32] double.
+// float4, v = g u [K] float4, u [K] float4 (double-float), red [32] float2,
+// scalars [4] float2.
 __global__ void __launch_bounds__(kSmThreads) sm_fold_kernel(SmArgs a) {
   extern __shared__ __align__(16) unsigned char smm[];
   const int K = a.K, F = a.F, T = tri_size(K), TS = tri_stride(K);
   float4 *Cs = reinterpret_cast<float4 *>(smm);
   float4 *zc = Cs + T;
   float4 *vv = zc + K;
-  double2 *u = reinterpret_cast<double2 *>(vv + K);
-  double *red = reinterpret_cast<double *>(u + K);
+  float4 *u = vv + K;
+  float2 *red = reinterpret_cast<float2 *>(u + K);
+  float2 *scal = red + 32;  // g, sc (double-float), set by thread 0
   const int p = blockIdx.x, tid = threadIdx.x;
   const int row = tid / kRowLanes, q = tid % kRowLanes, ii = row < K ? row : K - 1;
   float4 *Cg = a.C + (size_t)p * TS;
@@ -97,7 +115,6 @@ __global__ void __launch_bounds__(kSmThreads) sm_fold_kernel(SmArgs a) {
     for (int t = tid; t < T; t += kSmThreads) Cs[t] = Cg[t];
   float2 bacc = make_float2(0.f, 0.f);
   for (int s = 0; s < a.B; ++s) {
-    const double t = (double)(a.n + 1 + s);
     const bool first = a.n + s == 0;
     __syncthreads();
     if (tid < K) {
@@ -107,7 +124,7 @@ __global__ void __launch_bounds__(kSmThreads) sm_fold_kernel(SmArgs a) {
       bacc = cadd(bacc, cmulc(x, v));  // x~ conj(z)
     }
     if (first) {  // C_0 = I / r
-      const float4 d = df_split2(1.0 / a.r, 0.0);
+      const float4 d = make_float4(a.rinv.x, 0.f, a.rinv.y, 0.f);
       for (int e = tid; e < T; e += kSmThreads) {
         int i, j;
         tri_ij(e, K, i, j);
@@ -116,29 +133,46 @@ __global__ void __launch_bounds__(kSmThreads) sm_fold_kernel(SmArgs a) {
     }
     __syncthreads();
     // u = C conj(z)
-    const double2 ui = row_merge(herm_row_part(Cs, zc, K, ii, q));
+    const float4 ui = row_merge(herm_row_part(Cs, zc, K, ii, q));
     if (row < K && q == 0) u[row] = ui;
-    double part = 0.0;
     __syncthreads();
-    if (tid < K) part = (double)zc[tid].x * u[tid].x + (double)zc[tid].y * u[tid].y;  // Re(z_i u_i), real
-    const double zu = block_sum_d(part, red);
-    const double den = first ? 1.0 + zu : (t - 1.0) + zu;
-    const double sc = first ? 1.0 : t / (t - 1.0);
-    // C <- sc C - v v^H with v = g u, g^2 = sc / den.
-    const double g = sqrt(sc / den);
-    if (tid < K) vv[tid] = df_split2(g * u[tid].x, g * u[tid].y);
+    // z^T C conj(z) = sum_i Re(z_i u_i), real.
+    float Sz = 0.f, Ez = 0.f;
+    if (tid < K) {
+      const float4 uz = u[tid], z4 = zc[tid];
+      df_mac(z4.x, 0.f, uz.x, uz.z, Sz, Ez);
+      df_mac(z4.y, 0.f, uz.y, uz.w, Sz, Ez);
+    }
+    const float2 zu = block_sum_df(Sz, Ez, red);
+    // C <- sc C - v v^H with v = g u, g^2 = sc / den (one thread, FP64).
+    if (tid == 0) {
+      const double t = (double)(a.n + 1 + s), zud = df_val(zu.x, zu.y);
+      const double den = first ? 1.0 + zud : (t - 1.0) + zud;
+      const double sc = first ? 1.0 : t / (t - 1.0);
+      scal[0] = df_of(sqrt(sc / den));
+      scal[1] = df_of(sc);
+    }
     __syncthreads();
-    const float sch = (float)sc, scl = (float)(sc - (double)sch);
+    const float2 g = scal[0], sc = scal[1];
+    if (tid < K) {
+      const float4 uz = u[tid];
+      float Sr, Er, Si, Ei;
+      df_mul(uz.x, uz.z, g.x, g.y, Sr, Er);
+      df_mul(uz.y, uz.w, g.x, g.y, Si, Ei);
+      const float2 vr = two_sum(Sr, Er), vi = two_sum(Si, Ei);
+      vv[tid] = make_float4(vr.x, vi.x, vr.y, vi.y);
+    }
+    __syncthreads();
     for (int e = tid; e < T; e += kSmThreads) {
       int i, j;
       tri_ij(e, K, i, j);
       const float4 vi = vv[i], vj = vv[j], c = Cs[e];
       // Re: sc Re c - (Re vi Re vj + Im vi Im vj);  Im: sc Im c - (Im vi Re vj - Re vi Im vj)
       float Sr, Er, Si, Ei;
-      df_mul(c.x, c.z, sch, scl, Sr, Er);
+      df_mul(c.x, c.z, sc.x, sc.y, Sr, Er);
       df_mac(-vi.x, -vi.z, vj.x, vj.z, Sr, Er);
       df_mac(-vi.y, -vi.w, vj.y, vj.w, Sr, Er);
-      df_mul(c.y, c.w, sch, scl, Si, Ei);
+      df_mul(c.y, c.w, sc.x, sc.y, Si, Ei);
       df_mac(-vi.y, -vi.w, vj.x, vj.z, Si, Ei);
       df_mac(vi.x, vi.z, vj.y, vj.w, Si, Ei);
       const float2 nr = two_sum(Sr, Er), ni = two_sum(Si, Ei);
@@ -155,11 +189,12 @@ __global__ void __launch_bounds__(kSmThreads) sm_fold_kernel(SmArgs a) {
 }
 
 // d = C (b + r (v^ - theta^)) with C Hermitian (packed lower, double-float);
-// w = b + r (v^ - theta^) is formed in FP64 and split the same way.  C_t's
-// ridge decays as r / t, so its condition number grows with t and a plain FP32
-// product would lose accuracy.  Also E = d + theta^; ths != 1 rescales theta^
-// first (stored back: the scaled dual after a change of penalty).
-__global__ void __launch_bounds__(kRowLanes * 128) dstep_sm_kernel(int K, int F, double r, double ths,
+// w = b + r (v^ - theta^) is formed in double-float from the FP32 inputs and
+// r = (r hi, r lo).  C_t's ridge decays as r / t, so its condition number
+// grows with t and a plain FP32 product would lose accuracy.  Also
+// E = d + theta^; ths != 1 rescales theta^ first (stored back: the scaled dual
+// after a change of penalty).
+__global__ void __launch_bounds__(kRowLanes * 128) dstep_sm_kernel(int K, int F, float2 r, float ths,
                                                                    const float4 *__restrict__ Cf,
                                                                    const float2 *__restrict__ b,
                                                                    const float2 *__restrict__ Vh,
@@ -180,17 +215,25 @@ __global__ void __launch_bounds__(kRowLanes * 128) dstep_sm_kernel(int K, int F,
   if (row < K && q == 0) {
     const float2 v = Vh[o], bb = b[o];
     thi = th[o];
-    if (ths != 1.0) {
-      thi = make_float2((float)(ths * thi.x), (float)(ths * thi.y));
+    if (ths != 1.f) {
+      thi = make_float2(ths * thi.x, ths * thi.y);
       th[o] = thi;
     }
-    sw[row] = df_split2((double)bb.x + r * ((double)v.x - thi.x), (double)bb.y + r * ((double)v.y - thi.y));
+    // b + r (v - theta), each part exact until the final rounding to a pair.
+    const float2 dr = two_sum(v.x, -thi.x), di = two_sum(v.y, -thi.y);
+    float Sr, Er, Si, Ei;
+    df_mul(dr.x, dr.y, r.x, r.y, Sr, Er);
+    df_mul(di.x, di.y, r.x, r.y, Si, Ei);
+    df_acc(Sr, Er, bb.x, 0.f);
+    df_acc(Si, Ei, bb.y, 0.f);
+    const float2 wr = two_sum(Sr, Er), wi = two_sum(Si, Ei);
+    sw[row] = make_float4(wr.x, wi.x, wr.y, wi.y);
   }
   cp_async_wait_all();
   __syncthreads();
-  const double2 d = row_merge(herm_row_part(sC, sw, K, ii, q));  // idle lanes redo row K - 1
+  const float4 d = row_merge(herm_row_part(sC, sw, K, ii, q));  // idle lanes redo row K - 1
   if (row < K && q == 0) {
-    const float2 df = make_float2((float)d.x, (float)d.y);
+    const float2 df = make_float2(d.x + d.z, d.y + d.w);
     Dcur[o] = df;
     E[o] = cadd(df, thi);
   }
@@ -199,7 +242,7 @@ __global__ void __launch_bounds__(kRowLanes * 128) dstep_sm_kernel(int K, int F,
 cudaError_t launch_sm_fold(const SmArgs &a, cudaStream_t s) {
   if (a.K < 1 || a.K > 128) return cudaErrorInvalidValue;
   const int T = tri_size(a.K);
-  const size_t sm = ((size_t)T + 2 * a.K) * sizeof(float4) + a.K * sizeof(double2) + 32 * sizeof(double);
+  const size_t sm = ((size_t)T + 3 * a.K) * sizeof(float4) + 36 * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(sm_fold_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   sm_fold_kernel<<<a.F, kSmThreads, sm, s>>>(a);
@@ -212,7 +255,9 @@ cudaError_t launch_dstep_sm(int K, int F, double r, double ths, const float4 *Cf
   const size_t sm = ((size_t)tri_stride(K) + K) * sizeof(float4);
   cudaError_t e = cudaFuncSetAttribute(dstep_sm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  dstep_sm_kernel<<<F, (kRowLanes * K + 31) / 32 * 32, sm, s>>>(K, F, r, ths, Cf, b, Vh, th, Dcur, E);
+  const float rh = (float)r;
+  const float2 rf = make_float2(rh, (float)(r - (double)rh));
+  dstep_sm_kernel<<<F, (kRowLanes * K + 31) / 32 * 32, sm, s>>>(K, F, rf, (float)ths, Cf, b, Vh, th, Dcur, E);
   return cudaGetLastError();
 }
 

@@ -38,7 +38,7 @@ constexpr int kFoldChunk = 16;  // samples staged in shared memory at once
 //      so those reads are broadcasts.
 // 4.   Store X (FP32, packed lower) and y (FP32).
 //
-// Shared memory: M [T] float4, y [K] float4 (double-float), invd [K] double,
+// Shared memory: M [T] float4, y [K] float4 (double-float), invf [K] float2,
 // Lcol [2][K] float2, Xrow [K] float2, zs / xs (a chunk of pending codes).
 // During the fold each M slot first holds the FP32 running sum of
 // conj(z_i) z_j in its first 8 bytes.
@@ -49,8 +49,8 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   const int T = tri_size(K);
   float4 *M = reinterpret_cast<float4 *>(fsm);                   // [T] double-float
   float4 *y = M + T;                                             // [K] double-float
-  double *invd = reinterpret_cast<double *>(y + K);              // [K]
-  float2 *Lcol = reinterpret_cast<float2 *>(invd + K);           // [2][K]
+  float2 *invf = reinterpret_cast<float2 *>(y + K);              // [K] 1 / L_jj, double-float
+  float2 *Lcol = invf + K;                                       // [2][K]
   float2 *Xrow = Lcol + 2 * K;                                   // [K]
   float2 *zs = Xrow + K;                                         // [kFoldChunk][K]
   float2 *xs = zs + kFoldChunk * K;                              // [kFoldChunk]
@@ -95,27 +95,32 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   float2 *Ap = a.A + (size_t)p * tri_stride(K);
   const float alpha = (float)a.alpha, beta = (float)a.beta;
   const float2 *Lo = a.Alo ? a.Alo + (size_t)p * tri_stride(K) : nullptr;
+  const float2 wf = df_of(a.w), rf = df_of(a.rho_eff);
   for (int t = tid; t < T; t += kFoldThreads) {
     int i, j;
     tri_ij(t, K, i, j);
-    double hx, hy;
+    float2 hf, lf = make_float2(0.f, 0.f);
     if (a.prefolded) {  // A (+ its compensation word) already holds the new mean
-      const float2 h = Ap[t];
-      hx = h.x;
-      hy = h.y;
-      if (Lo) {
-        hx += (double)Lo[t].x;
-        hy += (double)Lo[t].y;
-      }
+      hf = Ap[t];
+      if (Lo) lf = Lo[t];
     } else {
       const float2 old = a.first ? make_float2(0.f, 0.f) : Ap[t];
       const float2 sum = S[2 * t];
-      const float2 nw = make_float2(fmaf(alpha, old.x, beta * sum.x), fmaf(alpha, old.y, beta * sum.y));
-      Ap[t] = nw;
-      hx = nw.x;
-      hy = nw.y;
+      hf = make_float2(fmaf(alpha, old.x, beta * sum.x), fmaf(alpha, old.y, beta * sum.y));
+      Ap[t] = hf;
     }
-    M[t] = (i == j) ? df_split2(a.w * hx + a.rho_eff, 0.0) : df_split2(a.w * hx, a.w * hy);
+    // w (h + lo) in FP32 pairs (the FP64 pipe is kept for the pivots).
+    float Sr, Er, Si, Ei;
+    df_mul(hf.x, lf.x, wf.x, wf.y, Sr, Er);
+    df_mul(hf.y, lf.y, wf.x, wf.y, Si, Ei);
+    if (i == j) {
+      const float2 s2 = two_sum(Sr, rf.x);
+      Sr = s2.x;
+      Er += s2.y + rf.y;
+      Si = 0.f;
+      Ei = 0.f;
+    }
+    M[t] = make_float4(Sr, Si, Er, Ei);
   }
 #pragma unroll
   for (int m = 0; m < (128 + kFoldThreads - 1) / kFoldThreads; ++m) {
@@ -129,7 +134,10 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
         nw = make_float2(fmaf(alpha, old.x, beta * sb[m].x), fmaf(alpha, old.y, beta * sb[m].y));
         a.b[(size_t)i * F + p] = nw;
       }
-      y[i] = df_split2(a.w * (double)nw.x, a.w * (double)nw.y);
+      float Sr, Er, Si, Ei;
+      df_mul(nw.x, 0.f, wf.x, wf.y, Sr, Er);
+      df_mul(nw.y, 0.f, wf.x, wf.y, Si, Ei);
+      y[i] = make_float4(Sr, Si, Er, Ei);
     }
   }
   __syncthreads();
@@ -145,14 +153,14 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
     }
     const double r = rsqrt(piv);  // 1 / L_00; L_00 = piv / sqrt(piv)
     M[0] = df_split2(piv * r, 0.0);
-    invd[0] = r;
+    invf[0] = df_of(r);
   }
   __syncthreads();
   for (int j = 0; j <= K; ++j) {
     // --- scale phase: column j of L (double-float + FP32 copy), row j-1 of X.
     if (j < K) {
       const int oj = tri_off(j, K);
-      const float2 inv = df_of(invd[j]);
+      const float2 inv = invf[j];
       float2 *lc = Lcol + (j & 1) * K;
       for (int i = j + 1 + tid; i < K; i += kFoldThreads) {
         const float4 v = M[oj + i - j];
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
     }
     if (j >= 1) {
       const int s1 = j - 1;                 // X row s1 is final up to its scaling
-      const float is = (float)invd[s1];
+      const float is = invf[s1].x;
       for (int c = tid; c <= s1; c += kFoldThreads) {
         const int slot = tri_off(c, K) + s1 - c;
         const float2 xv = (c == s1) ? make_float2(is, 0.f)
@@ -203,21 +211,35 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
         }
         const double r = rsqrt(piv);
         M[d1] = df_split2(piv * r, 0.0);
-        invd[j + 1] = r;
+        invf[j + 1] = df_of(r);
       }
-      // One element per thread and round: only the last warp of the last
-      // round runs with idle lanes.  M_ik -= L_ij conj(L_kj).
-      for (int u = 1 + tid; u < nt; u += kFoldThreads) {
-        int ii, kk;
-        tri_ij(u, n, ii, kk);
-        const int dst = tri_off(j + 1 + kk, K) + ii - kk;
-        const float4 li = M[oj + 1 + ii], lk = M[oj + 1 + kk];
-        float4 v = M[dst];
-        df_mac(-li.x, -li.z, lk.x, lk.z, v.x, v.z);  // Re: - Re li Re lk - Im li Im lk
-        df_mac(-li.y, -li.w, lk.y, lk.w, v.x, v.z);
-        df_mac(-li.y, -li.w, lk.x, lk.z, v.y, v.w);  // Im: - Im li Re lk + Re li Im lk
-        df_mac(li.x, li.z, lk.y, lk.w, v.y, v.w);
-        M[dst] = v;
+      // M_ik -= L_ij conj(L_kj) over the trailing triangle (ii >= kk in [0, n),
+      // rows j+1+ii, columns j+1+kk), folded into a rectangle: row r holds
+      // column kk = r (c < n - r: ii = r + c) followed by column n - 1 - r
+      // (ii = c - 1); for odd n the middle row holds only its first part.  A
+      // warp takes a rectangle row, its lanes the entries, so every packed
+      // offset is a per-row base plus c.  Element (0, 0), the next pivot, is
+      // done above.
+      {
+        const int warp = tid >> 5, lane = tid & 31, R = (n + 1) / 2;
+        for (int r = warp; r < R; r += kFoldThreads / 32) {
+          const int cut = n - r, len = (2 * r + 1 == n) ? cut : n + 1, kb = n - 1 - r;
+          const int dsta = tri_off(j + 1 + r, K), dstb = tri_off(j + 1 + kb, K) - cut;
+          const int lia = oj + 1 + r, lib = oj;  // L row offsets: + c
+          for (int c = lane; c < len; c += 32) {
+            if (r == 0 && c == 0) continue;
+            const bool first = c < cut;
+            const float4 lk = M[first ? oj + 1 + r : oj + 1 + kb];
+            const float4 li = M[(first ? lia : lib) + c];
+            const int dst = (first ? dsta : dstb) + c;
+            float4 v = M[dst];
+            df_mac(-li.x, -li.z, lk.x, lk.z, v.x, v.z);  // Re: - Re li Re lk - Im li Im lk
+            df_mac(-li.y, -li.w, lk.y, lk.w, v.x, v.z);
+            df_mac(-li.y, -li.w, lk.x, lk.z, v.y, v.w);  // Im: - Im li Re lk + Re li Im lk
+            df_mac(li.x, li.z, lk.y, lk.w, v.y, v.w);
+            M[dst] = v;
+          }
+        }
       }
       // y_i -= L_ij y_j.
       for (int u = tid; u < n; u += kFoldThreads) {
@@ -232,18 +254,32 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
       }
     }
     if (j >= 1) {
-      // X_ic -= L_i,s1 X_s1,c for i > s1, c <= s1 (i fastest); column s1 of X
-      // starts here (its entries below the diagonal were zero).
-      const int s1 = j - 1, rows = K - j;
+      // X_ic -= L_i,s1 X_s1,c for i > s1, c <= s1; column s1 of X starts here
+      // (its entries below the diagonal were zero).  A warp takes columns c,
+      // its lanes the rows i, whose L entries stay in registers.
+      const int s1 = j - 1;
       const float2 *lc = Lcol + (s1 & 1) * K;
-      for (int e = tid; e < rows * j; e += kFoldThreads) {
-        const int c = e / rows, i = j + e % rows;
-        const float2 l = lc[i], xs1 = Xrow[c];
-        const int slot = tri_off(c, K) + i - c;
-        float2 v = (c == s1) ? make_float2(0.f, 0.f) : XS[2 * slot];
-        v.x -= l.x * xs1.x - l.y * xs1.y;
-        v.y -= l.x * xs1.y + l.y * xs1.x;
-        XS[2 * slot] = v;
+      const int warp = tid >> 5, lane = tid & 31;
+      float2 lreg[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int i = j + lane + 32 * m;
+        lreg[m] = i < K ? lc[i] : make_float2(0.f, 0.f);
+      }
+      for (int c = warp; c <= s1; c += kFoldThreads / 32) {
+        const float2 xs1 = Xrow[c];
+        const int base = tri_off(c, K) - c;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int i = j + lane + 32 * m;
+          if (i < K) {
+            const float2 l = lreg[m];
+            float2 v = (c == s1) ? make_float2(0.f, 0.f) : XS[2 * (base + i)];
+            v.x -= l.x * xs1.x - l.y * xs1.y;
+            v.y -= l.x * xs1.y + l.y * xs1.x;
+            XS[2 * (base + i)] = v;
+          }
+        }
       }
     }
     __syncthreads();

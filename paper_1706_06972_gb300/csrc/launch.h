@@ -128,6 +128,7 @@ int gram_chunk(int K, int B, int terms);
 struct SmArgs {
   int K, F, B, n;       // pending samples B folded after n earlier ones
   double r;             // ridge of the first sample: rho (rho P under the paper's convention)
+  float2 rinv;          // 1 / r as a double-float pair
   float alpha, beta;    // running mean of b: n/(n+B), 1/(n+B)
   const float2 *Zp;     // [B][K][F]
   const float2 *xh;     // [B][F]

@@ -537,6 +537,11 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
       sa.B = s.pending;
       sa.n = (int)s.n_seen;
       sa.r = fa.rho_eff;
+      {
+        const double ri = 1.0 / fa.rho_eff;
+        const float rh = (float)ri;
+        sa.rinv = make_float2(rh, (float)(ri - (double)rh));
+      }
       sa.alpha = (float)fa.alpha;
       sa.beta = (float)fa.beta;
       sa.Zp = s.Zp;
