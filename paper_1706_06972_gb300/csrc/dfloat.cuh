@@ -37,6 +37,19 @@ __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, f
   E = fmaf(ah, bl, fmaf(al, bh, fmaf(ah, bh, -S)));
 }
 
+// (S, E) + (S2, E2) as an unnormalised pair.
+__device__ __forceinline__ void df_acc(float &S, float &E, float S2, float E2) {
+  const float2 s = two_sum(S, S2);
+  S = s.x;
+  E = (E + E2) + s.y;
+}
+
+// v += w for complex unnormalised pairs (re S, im S, re E, im E).
+__device__ __forceinline__ void df_acc2(float4 &v, const float4 &w) {
+  df_acc(v.x, v.z, w.x, w.z);
+  df_acc(v.y, v.w, w.y, w.w);
+}
+
 // S + E as a normalised pair (hi, lo), valid for any S, E.
 __device__ __forceinline__ float2 df_norm(float S, float E) { return two_sum(S, E); }
 

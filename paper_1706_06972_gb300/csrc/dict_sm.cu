@@ -31,13 +31,6 @@ namespace {
 constexpr int kSmThreads = 256;
 constexpr int kRowLanes = 2;  // lanes per row of a Hermitian product (divides 32)
 
-// (S, E) + (S2, E2) as an unnormalised pair.
-__device__ __forceinline__ void df_acc(float &S, float &E, float S2, float E2) {
-  const float2 s = two_sum(S, S2);
-  S = s.x;
-  E = (E + E2) + s.y;
-}
-
 // Block-wide sum of an unnormalised pair, in a fixed order, returned to every
 // thread normalised.
 __device__ __forceinline__ float2 block_sum_df(float S, float E, float2 *red) {

@@ -20,28 +20,273 @@
 namespace ocsc {
 
 constexpr int kFoldChunk = 16;  // samples staged in shared memory at once
+constexpr int kPanel = 4;       // columns per Cholesky panel
+
+// 1 / sqrt(p) for p = ph + pl > 0 as a pair: the FP32 estimate r0 (a few
+// ulp) refined by one Newton step r0 (1 + e / 2), e = 1 - p r0^2 formed in
+// double-float, which squares the relative error.
+__device__ __forceinline__ float2 df_rsqrt(float ph, float pl) {
+  const float r0 = rsqrtf(ph);
+  float S, E;
+  df_mul(r0, 0.f, r0, 0.f, S, E);
+  const float2 q = two_sum(S, E);
+  df_mul(ph, pl, q.x, q.y, S, E);
+  const float2 pr = two_sum(S, E);
+  const float2 e1 = two_sum(1.f, -pr.x);
+  const float e = e1.x + (e1.y - pr.y);
+  return two_sum(r0, 0.5f * r0 * e);
+}
+
+// Normalised pair product (v re, v im) x r for a complex pair v (possibly
+// unnormalised) and a real pair r.
+__device__ __forceinline__ float4 df_scale(float4 v, float2 r) {
+  const float2 vr = two_sum(v.x, v.z), vi = two_sum(v.y, v.w);
+  float Sr, Er, Si, Ei;
+  df_mul(vr.x, vr.y, r.x, r.y, Sr, Er);
+  df_mul(vi.x, vi.y, r.x, r.y, Si, Ei);
+  const float2 a = two_sum(Sr, Er), b = two_sum(Si, Ei);
+  return make_float4(a.x, b.x, a.y, b.y);
+}
+
+// v -= l conj(m) (complex pairs; v unnormalised).
+__device__ __forceinline__ void df_sub_lconjm(float4 &v, const float4 &l, const float4 &m) {
+  df_mac(-l.x, -l.z, m.x, m.z, v.x, v.z);  // Re: - Re l Re m - Im l Im m
+  df_mac(-l.y, -l.w, m.y, m.w, v.x, v.z);
+  df_mac(-l.y, -l.w, m.x, m.z, v.y, v.w);  // Im: - Im l Re m + Re l Im m
+  df_mac(l.x, l.z, m.y, m.w, v.y, v.w);
+}
+
+// v -= l m (complex pairs; v unnormalised).
+__device__ __forceinline__ void df_sub_lm(float4 &v, const float4 &l, const float4 &m) {
+  df_mac(-l.x, -l.z, m.x, m.z, v.x, v.z);  // Re: - Re l Re m + Im l Im m
+  df_mac(l.y, l.w, m.y, m.w, v.x, v.z);
+  df_mac(-l.x, -l.z, m.y, m.w, v.y, v.w);  // Im: - Re l Im m - Im l Re m
+  df_mac(-l.y, -l.w, m.x, m.z, v.y, v.w);
+}
+
+// Factor panel pb (columns j0 .. j0+nb-1, all rows below) by one warp: pivot,
+// scaling of the column (kept in registers and as an FP32 copy in Lb), y, and
+// the update of the panel's later columns; lanes take rows j+1+lane+32m.
+__device__ __forceinline__ void fold_panel(float4 *M, float4 *y, float2 *invf, float2 *Lb, int K, int pb,
+                                           int lane, int *err, float rho_fb) {
+  const int j0 = pb * kPanel, nb = min(kPanel, K - j0);
+  float2 *Lq = Lb + (pb % 3) * kPanel * K;
+  for (int q = 0; q < nb; ++q) {
+    const int mrows = (K - j0 - q - 1 + 31) / 32;  // row slots j+1+lane+32m below K
+    const int j = j0 + q, oj = tri_off(j, K);
+    const float4 d = M[oj];
+    float2 pv = two_sum(d.x, d.z);
+    if (!(pv.x > 0.f)) {
+      if (lane == 0) atomicOr(err, ERR_PIVOT);
+      pv = make_float2(rho_fb, 0.f);
+    }
+    const float2 r = df_rsqrt(pv.x, pv.y);
+    float S, E;
+    df_mul(pv.x, pv.y, r.x, r.y, S, E);
+    const float2 ljj = two_sum(S, E);  // L_jj = p / sqrt(p)
+    float4 l[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = j + 1 + lane + 32 * m;
+      if (m >= mrows) break;
+      if (i < K) {
+        l[m] = df_scale(M[oj + i - j], r);
+        M[oj + i - j] = l[m];
+        Lq[q * K + i] = make_float2(l[m].x, l[m].y);
+      }
+    }
+    const float4 yj = df_scale(y[j], r);
+    __syncwarp();
+    if (lane == 0) {
+      M[oj] = make_float4(ljj.x, 0.f, ljj.y, 0.f);
+      invf[j] = r;
+      y[j] = yj;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = j + 1 + lane + 32 * m;
+      if (m >= mrows) break;
+      if (i < K) {
+        float4 v = y[i];
+        df_sub_lm(v, l[m], yj);
+        y[i] = v;
+      }
+    }
+    for (int qp = q + 1; qp < nb; ++qp) {
+      const int jp = j0 + qp, ojp = tri_off(jp, K);
+      const float4 lj = M[oj + jp - j];  // L_{jp, j}, scaled above by its row's lane
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int i = j + 1 + lane + 32 * m;
+        if (m >= mrows) break;
+        if (i >= jp && i < K) {
+          float4 v = M[ojp + i - jp];
+          df_sub_lconjm(v, l[m], lj);
+          M[ojp + i - jp] = v;
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Rank-nb update of the trailing triangle (rows / columns from j1 = j0 + nb)
+// by panel columns j0 .. j0+nb-1, over rectangle rows r0, r0 + rs, ... < rend;
+// the lanes of the calling warp take the entries.
+// second = false: only the first part of each row (column r itself).
+__device__ __forceinline__ void fold_trail(float4 *M, int K, int j0, int nb, int r0, int rs, int rend, int lane,
+                                           bool second) {
+  const int j1 = j0 + nb, n = K - j1;
+  int cq[kPanel];  // cq[q] + ii: slot of L_{j1+ii, j0+q}
+#pragma unroll
+  for (int q = 0; q < kPanel; ++q) cq[q] = q < nb ? tri_off(j0 + q, K) - j0 - q + j1 : 0;
+  for (int r = r0; r < rend; r += rs) {
+    const int cut = n - r, len = (2 * r + 1 == n) ? cut : n + 1, kb = n - 1 - r;
+    const int dsta = tri_off(j1 + r, K), dstb = tri_off(j1 + kb, K) - cut;
+    float4 lka[kPanel], lkb[kPanel];
+#pragma unroll
+    for (int q = 0; q < kPanel; ++q) {
+      lka[q] = q < nb ? M[cq[q] + r] : make_float4(0.f, 0.f, 0.f, 0.f);
+      lkb[q] = q < nb ? M[cq[q] + kb] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    int c = lane;
+    // Column r: entry ii = r + c; then column n-1-r: ii = c - 1.
+    for (; c < cut; c += 32) {
+      const int dst = dsta + c, ii = r + c;
+      float4 v = M[dst], w = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < kPanel; ++q)
+        if (q < nb) df_sub_lconjm((q & 1) ? w : v, M[cq[q] + ii], lka[q]);
+      df_acc2(v, w);
+      M[dst] = v;
+    }
+    if (!second) continue;
+    for (; c < len; c += 32) {
+      const int dst = dstb + c, ii = c - 1;
+      float4 v = M[dst], w = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < kPanel; ++q)
+        if (q < nb) df_sub_lconjm((q & 1) ? w : v, M[cq[q] + ii], lkb[q]);
+      df_acc2(v, w);
+      M[dst] = v;
+    }
+  }
+}
+
+// The same update over rectangle rows [r0, R) as one flat index space
+// u = (r - r0) (n + 1) + c shared by `nt` threads (index t), each stepping u by
+// nt with an incremental (r, c); every lane has an entry in every pass but the
+// last.  The middle row of an odd n has only its first part; the first parts
+// of rows r < skip (done elsewhere) are skipped.
+__device__ __forceinline__ void fold_trail_flat(float4 *M, int K, int j0, int nb, int r0, int t, int nt, int skip) {
+  const int j1 = j0 + nb, n = K - j1, R = (n + 1) / 2, W = n + 1;
+  if (r0 >= R) return;
+  int cq[kPanel];
+#pragma unroll
+  for (int q = 0; q < kPanel; ++q) cq[q] = q < nb ? tri_off(j0 + q, K) - j0 - q + j1 : 0;
+  const int total = (R - r0) * W, dr = nt / W, dc = nt % W;
+  int r = r0 + t / W, c = t % W;
+  for (int u = t; u < total; u += nt) {
+    const int cut = n - r;
+    if ((c < cut && r >= skip) || (c >= cut && 2 * r + 1 != n)) {
+      const bool first = c < cut;
+      const int kk = first ? r : n - 1 - r, ii = first ? r + c : c - 1;
+      const int dst = tri_off(j1 + kk, K) + ii - kk;
+      float4 v = M[dst], w = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < kPanel; ++q)
+        if (q < nb) df_sub_lconjm((q & 1) ? w : v, M[cq[q] + ii], M[cq[q] + kk]);
+      df_acc2(v, w);
+      M[dst] = v;
+    }
+    c += dc;
+    r += dr;
+    if (c >= W) {
+      c -= W;
+      ++r;
+    }
+  }
+}
+
+// Forward substitution L X = I for the pivots of panel pb (FP32, L from the
+// panel's FP32 copy): for each column c <= j0 + nb - 1 taken by the calling
+// warp (c0, c0 + cs, ...), rows i >= j0 in registers (lane + 32 m): for every
+// pivot s of the panel, X_sc *= 1 / L_ss (X_ss = 1 / L_ss when c = s), then
+// X_ic -= L_is X_sc for i > s.
+__device__ __forceinline__ void fold_xpanel(float2 *XS, const float2 *Lb, const float2 *invf, int K, int pb,
+                                            int c0, int cs, int lane) {
+  const int j0 = pb * kPanel, nb = min(kPanel, K - j0), mrows = (K - j0 + 31) / 32;
+  const float2 *Lq = Lb + (pb % 3) * kPanel * K;
+  float2 lr[kPanel][4];
+#pragma unroll
+  for (int q = 0; q < kPanel; ++q)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = j0 + lane + 32 * m;
+      lr[q][m] = (q < nb && i > j0 + q && i < K) ? Lq[q * K + i] : make_float2(0.f, 0.f);
+    }
+  for (int c = c0; c < j0 + nb; c += cs) {
+    const int base = tri_off(c, K) - c;
+    float2 x[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = j0 + lane + 32 * m;
+      x[m] = (c < j0 && i < K) ? XS[2 * (base + i)] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < kPanel; ++q) {
+      const int s = j0 + q;
+      if (q >= nb || c > s) continue;
+      const float is = invf[s].x;
+      const float2 own = (c == s) ? make_float2(is, 0.f) : make_float2(x[0].x * is, x[0].y * is);
+      const float2 xs = make_float2(__shfl_sync(0xffffffffu, own.x, q), __shfl_sync(0xffffffffu, own.y, q));
+      if (lane == q) x[0] = xs;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if (m >= mrows) break;
+        const float2 l = lr[q][m];  // zero unless row j0 + lane + 32 m > s
+        x[m].x -= l.x * xs.x - l.y * xs.y;
+        x[m].y -= l.x * xs.y + l.y * xs.x;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int i = j0 + lane + 32 * m;
+      if (i < K && i >= c) XS[2 * (base + i)] = x[m];
+    }
+  }
+}
+
 
 // One CTA per frequency p.
 //
 // 1-2. Fold the pending codes into the FP32 running means A^p, b^p and form
 //      M = w A + rho I, y = w b in double-float.
-// 3.   Right-looking double-float Cholesky on the packed lower triangle, with
-//      y carried as an extra column (forward substitution: y <- L^-1 w b); the
-//      pivots 1 / sqrt(.) are taken in FP64.  One step behind it, the same
-//      threads run the right-looking forward substitution of L X = I in FP32
-//      (X = L^-1): after column s of L is final, row s of X is scaled by
-//      1/L_ss and every X_ic with i > s, c <= s gets X_ic -= L_is X_sc.  The
-//      FP32 update of step s runs in the same phase as the trailing update of
-//      step s+1 and writes only slots of columns <= s, whose double-float
-//      values are no longer read: the first 8 bytes of such a slot then hold
-//      X_ic.  L's column s (FP32 copy) and X's row s are kept in small buffers
-//      so those reads are broadcasts.
+// 3.   Blocked right-looking double-float Cholesky on the packed lower
+//      triangle in panels of kPanel columns, with y carried along (forward
+//      substitution y <- L^-1 w b), and X = L^-1 in FP32 one panel behind.
+//      Per panel b, in one phase between two barriers:
+//        warp 0    applies panel b's rank-kPanel update to the columns of panel
+//                  b+1 (and the columns paired with them, below), then factors
+//                  panel b+1 (fold_panel: pivots 1/sqrt by an FP32 estimate and
+//                  one double-float Newton step, column scaling, the update
+//                  inside the panel, y);
+//        warps 1.. apply panel b's update to the rest of the trailing triangle
+//                  (fold_trail) and run the forward substitution L X = I for
+//                  the pivots of panel b-1 (fold_xpanel), a warp per column of
+//                  X with its rows in registers.
+//      The trailing triangle is folded into a rectangle (row r: column r, then
+//      column n-1-r) whose rows go to warps and entries to lanes, so every
+//      packed offset is a per-row base plus the lane's index.  X_ic is written
+//      into the first 8 bytes of slot (i, c) once column c of L is no longer
+//      read; panel b's columns are kept as FP32 copies (three buffers: panels
+//      b-1 for X, b and b+1 in flight).
 // 4.   Store X (FP32, packed lower) and y (FP32).
 //
 // Shared memory: M [T] float4, y [K] float4 (double-float), invf [K] float2,
-// Lcol [2][K] float2, Xrow [K] float2, zs / xs (a chunk of pending codes).
-// During the fold each M slot first holds the FP32 running sum of
-// conj(z_i) z_j in its first 8 bytes.
+// Lb [3][kPanel][K] float2, zs / xs (a chunk of pending codes).  During the
+// fold each M slot first holds the FP32 running sum of conj(z_i) z_j in its
+// first 8 bytes.
 template <int kFoldThreads>
 __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
@@ -50,9 +295,8 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   float4 *M = reinterpret_cast<float4 *>(fsm);                   // [T] double-float
   float4 *y = M + T;                                             // [K] double-float
   float2 *invf = reinterpret_cast<float2 *>(y + K);              // [K] 1 / L_jj, double-float
-  float2 *Lcol = invf + K;                                       // [2][K]
-  float2 *Xrow = Lcol + 2 * K;                                   // [K]
-  float2 *zs = Xrow + K;                                         // [kFoldChunk][K]
+  float2 *Lb = invf + K;                                         // [3][kPanel][K]
+  float2 *zs = Lb + 3 * kPanel * K;                              // [kFoldChunk][K]
   float2 *xs = zs + kFoldChunk * K;                              // [kFoldChunk]
   float2 *S = reinterpret_cast<float2 *>(M);                     // FP32 sums, stride 2
   float2 *XS = reinterpret_cast<float2 *>(M);                    // X_ic at slot t: XS[2 t]
@@ -142,148 +386,31 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   }
   __syncthreads();
 
-  // 3. Cholesky (double-float) with the FP32 inverse one step behind.  Slots
-  //    of M and y hold unnormalised pairs (S, E) while they are being updated
-  //    and are normalised when they become entries of L (scale phase).
-  if (tid == 0) {
-    double piv = df_val(M[0].x, M[0].z);
-    if (!(piv > 0.0)) {
-      atomicOr(a.err, ERR_PIVOT);
-      piv = a.rho_eff > 0.0 ? a.rho_eff : 1.0;
-    }
-    const double r = rsqrt(piv);  // 1 / L_00; L_00 = piv / sqrt(piv)
-    M[0] = df_split2(piv * r, 0.0);
-    invf[0] = df_of(r);
-  }
+  // 3. Blocked Cholesky (double-float), y alongside, X = L^-1 one panel behind.
+  const int warp = tid >> 5, lane = tid & 31, nwarps = kFoldThreads / 32;
+  const float rho_fb = a.rho_eff > 0.0 ? (float)a.rho_eff : 1.f;
+  const int nblk = (K + kPanel - 1) / kPanel;
+  if (warp == 0) fold_panel(M, y, invf, Lb, K, 0, lane, a.err, rho_fb);
   __syncthreads();
-  for (int j = 0; j <= K; ++j) {
-    // --- scale phase: column j of L (double-float + FP32 copy), row j-1 of X.
-    if (j < K) {
-      const int oj = tri_off(j, K);
-      const float2 inv = invf[j];
-      float2 *lc = Lcol + (j & 1) * K;
-      for (int i = j + 1 + tid; i < K; i += kFoldThreads) {
-        const float4 v = M[oj + i - j];
-        const float2 vr = two_sum(v.x, v.z), vi = two_sum(v.y, v.w);
-        float Sr, Er, Si, Ei;
-        df_mul(vr.x, vr.y, inv.x, inv.y, Sr, Er);
-        df_mul(vi.x, vi.y, inv.x, inv.y, Si, Ei);
-        const float2 lr = two_sum(Sr, Er), li = two_sum(Si, Ei);
-        M[oj + i - j] = make_float4(lr.x, li.x, lr.y, li.y);
-        lc[i] = make_float2(lr.x, li.x);
-      }
-      if (tid == 0) {
-        const float4 v = y[j];
-        const float2 vr = two_sum(v.x, v.z), vi = two_sum(v.y, v.w);
-        float Sr, Er, Si, Ei;
-        df_mul(vr.x, vr.y, inv.x, inv.y, Sr, Er);
-        df_mul(vi.x, vi.y, inv.x, inv.y, Si, Ei);
-        const float2 yr = two_sum(Sr, Er), yi = two_sum(Si, Ei);
-        y[j] = make_float4(yr.x, yi.x, yr.y, yi.y);
-      }
-    }
-    if (j >= 1) {
-      const int s1 = j - 1;                 // X row s1 is final up to its scaling
-      const float is = invf[s1].x;
-      for (int c = tid; c <= s1; c += kFoldThreads) {
-        const int slot = tri_off(c, K) + s1 - c;
-        const float2 xv = (c == s1) ? make_float2(is, 0.f)
-                                    : make_float2(XS[2 * slot].x * is, XS[2 * slot].y * is);
-        Xrow[c] = xv;
-        XS[2 * slot] = xv;
-      }
-    }
-    __syncthreads();
-    // --- update phase: trailing update of step j, FP32 X update of step j-1.
-    if (j < K) {
-      const int oj = tri_off(j, K);
-      const int n = K - j - 1;
-      const int nt = tri_size(n);
-      const float4 yj = y[j];
-      if (tid == 0 && nt > 0) {  // element (j+1, j+1) also finishes the next pivot
-        const int d1 = tri_off(j + 1, K);
-        const float4 l = M[oj + 1], v = M[d1];
-        const double lx = df_val(l.x, l.z), ly = df_val(l.y, l.w);
-        double piv = df_val(v.x, v.z) - (lx * lx + ly * ly);
-        if (!(piv > 0.0)) {
-          atomicOr(a.err, ERR_PIVOT);
-          piv = a.rho_eff > 0.0 ? a.rho_eff : 1.0;
-        }
-        const double r = rsqrt(piv);
-        M[d1] = df_split2(piv * r, 0.0);
-        invf[j + 1] = df_of(r);
-      }
-      // M_ik -= L_ij conj(L_kj) over the trailing triangle (ii >= kk in [0, n),
-      // rows j+1+ii, columns j+1+kk), folded into a rectangle: row r holds
-      // column kk = r (c < n - r: ii = r + c) followed by column n - 1 - r
-      // (ii = c - 1); for odd n the middle row holds only its first part.  A
-      // warp takes a rectangle row, its lanes the entries, so every packed
-      // offset is a per-row base plus c.  Element (0, 0), the next pivot, is
-      // done above.
-      {
-        const int warp = tid >> 5, lane = tid & 31, R = (n + 1) / 2;
-        for (int r = warp; r < R; r += kFoldThreads / 32) {
-          const int cut = n - r, len = (2 * r + 1 == n) ? cut : n + 1, kb = n - 1 - r;
-          const int dsta = tri_off(j + 1 + r, K), dstb = tri_off(j + 1 + kb, K) - cut;
-          const int lia = oj + 1 + r, lib = oj;  // L row offsets: + c
-          for (int c = lane; c < len; c += 32) {
-            if (r == 0 && c == 0) continue;
-            const bool first = c < cut;
-            const float4 lk = M[first ? oj + 1 + r : oj + 1 + kb];
-            const float4 li = M[(first ? lia : lib) + c];
-            const int dst = (first ? dsta : dstb) + c;
-            float4 v = M[dst];
-            df_mac(-li.x, -li.z, lk.x, lk.z, v.x, v.z);  // Re: - Re li Re lk - Im li Im lk
-            df_mac(-li.y, -li.w, lk.y, lk.w, v.x, v.z);
-            df_mac(-li.y, -li.w, lk.x, lk.z, v.y, v.w);  // Im: - Im li Re lk + Re li Im lk
-            df_mac(li.x, li.z, lk.y, lk.w, v.y, v.w);
-            M[dst] = v;
-          }
-        }
-      }
-      // y_i -= L_ij y_j.
-      for (int u = tid; u < n; u += kFoldThreads) {
-        const int i = j + 1 + u;
-        const float4 l = M[oj + i - j];
-        float4 v = y[i];
-        df_mac(-l.x, -l.z, yj.x, yj.z, v.x, v.z);  // Re: - Re l Re y + Im l Im y
-        df_mac(l.y, l.w, yj.y, yj.w, v.x, v.z);
-        df_mac(-l.x, -l.z, yj.y, yj.w, v.y, v.w);  // Im: - Re l Im y - Im l Re y
-        df_mac(-l.y, -l.w, yj.x, yj.z, v.y, v.w);
-        y[i] = v;
-      }
-    }
-    if (j >= 1) {
-      // X_ic -= L_i,s1 X_s1,c for i > s1, c <= s1; column s1 of X starts here
-      // (its entries below the diagonal were zero).  A warp takes columns c,
-      // its lanes the rows i, whose L entries stay in registers.
-      const int s1 = j - 1;
-      const float2 *lc = Lcol + (s1 & 1) * K;
-      const int warp = tid >> 5, lane = tid & 31;
-      float2 lreg[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int i = j + lane + 32 * m;
-        lreg[m] = i < K ? lc[i] : make_float2(0.f, 0.f);
-      }
-      for (int c = warp; c <= s1; c += kFoldThreads / 32) {
-        const float2 xs1 = Xrow[c];
-        const int base = tri_off(c, K) - c;
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const int i = j + lane + 32 * m;
-          if (i < K) {
-            const float2 l = lreg[m];
-            float2 v = (c == s1) ? make_float2(0.f, 0.f) : XS[2 * (base + i)];
-            v.x -= l.x * xs1.x - l.y * xs1.y;
-            v.y -= l.x * xs1.y + l.y * xs1.x;
-            XS[2 * (base + i)] = v;
-          }
-        }
-      }
+  for (int b = 0; b < nblk; ++b) {
+    const int j0 = b * kPanel, nb = min(kPanel, K - j0), n = K - j0 - nb;
+    const int nb2 = min(kPanel, n), R = (n + 1) / 2, rw = min(nb2, R);
+    // For n >= 2 kPanel the next panel's columns are exactly the first parts
+    // of rectangle rows r < kPanel (warp 0) and the flat pool takes the rest;
+    // below that warp 0 takes the whole (small) triangle.
+    const bool small = n < 2 * kPanel;
+    if (warp == 0) {
+      fold_trail(M, K, j0, nb, 0, 1, small ? R : rw, lane, small);
+      __syncwarp();
+      if (nb2 > 0) fold_panel(M, y, invf, Lb, K, b + 1, lane, a.err, rho_fb);
+    } else {
+      if (!small) fold_trail_flat(M, K, j0, nb, 0, tid - 32, kFoldThreads - 32, rw);
+      if (b >= 1) fold_xpanel(XS, Lb, invf, K, b - 1, warp - 1, nwarps - 1, lane);
     }
     __syncthreads();
   }
+  fold_xpanel(XS, Lb, invf, K, nblk - 1, warp, nwarps, lane);
+  __syncthreads();
 
   // 4. Store X = L^-1 (FP32) and y = L^-1 (w b) (FP32).
   float2 *Xp = a.L + (size_t)p * tri_stride(K);
@@ -484,8 +611,8 @@ __global__ void dict_norms_kernel(int K, int F, const float2 *__restrict__ Dh, f
 // ---------------------------------------------------------------------------
 
 size_t fold_smem_bytes(int K) {
-  return (size_t)tri_size(K) * sizeof(double2) + (size_t)K * sizeof(double2) + (size_t)K * sizeof(double) +
-         (size_t)3 * K * sizeof(float2) + (size_t)kFoldChunk * K * sizeof(float2) + kFoldChunk * sizeof(float2);
+  return (size_t)(tri_size(K) + K) * sizeof(float4) + (size_t)(1 + 3 * kPanel) * K * sizeof(float2) +
+         (size_t)kFoldChunk * K * sizeof(float2) + kFoldChunk * sizeof(float2);
 }
 
 // threads: 256 or 512 (CTA size of the per-frequency factorisation; every
