@@ -179,6 +179,22 @@ def test_edge_cases_match_oracle(case):
         assert rel(dicts[t], odicts[t]) < REL_TOL, t
 
 
+@pytest.mark.parametrize("K", [1, 3, 5, 127, 128])
+def test_factor_panel_edges_match_oracle(K):
+    """The per-frequency factorisation works on panels of 4 columns with the
+    next panel factored ahead: K = 1 (a single pivot), 3 and 5 (ragged last
+    panel; trailing triangles smaller than two panels), 127 and 128 (ragged or
+    full last panel at the largest in-shared-memory size).  Two updates."""
+    _need_gpu()
+    imgs = _small_images(2, 56, 56, 700 + K)
+    raw = raw_filters(K, 5, 900 + K)
+    codes, dicts = run_gpu(imgs, raw, K, 5, 0.5, 1.0, 64, 8, 4, pad=0)
+    ocodes, odicts, _ = run_oracle(imgs, raw, 64, 0.5, 1.0, 8, 4)
+    for t in range(2):
+        assert rel(codes[t], ocodes[t]) < REL_TOL, t
+        assert rel(dicts[t], odicts[t]) < REL_TOL, t
+
+
 def test_minibatch_fold_matches_oracle():
     _need_gpu()
     imgs = _small_images(6, 64, 64, 200)
