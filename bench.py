@@ -44,8 +44,8 @@ FP32_PEAK_TFLOPS = SMS * FP32_LANES_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM bytes per fold_factor launch from an ncu capture of this workload
 # (profiles/fold_factor_plain_100in128_k100.md), valid only while the kernel
 # source is the one captured (sha1 of dict_update.cu).
-TRAFFIC_CAPTURE = {"bytes": 350.972928e6 + 625.112064e6,
-                   "source_sha1": "3eccb4240cd24706366610a8f8c13817712ef07e"}
+TRAFFIC_CAPTURE = {"bytes": 350.423040e6 + 625.118720e6,
+                   "source_sha1": "5aace13e6608b8694365c38ae4152e912b1af9d3"}
 
 
 def captured_traffic():

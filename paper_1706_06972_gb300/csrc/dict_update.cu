@@ -56,6 +56,15 @@ __device__ __forceinline__ void df_sub_lconjm(float4 &v, const float4 &l, const 
   df_mac(l.x, l.z, m.y, m.w, v.y, v.w);
 }
 
+// w = -l conj(m) (complex pairs, unnormalised): the first product of each
+// part needs no TwoSum.
+__device__ __forceinline__ void df_neg_lconjm(float4 &w, const float4 &l, const float4 &m) {
+  df_mul(-l.x, -l.z, m.x, m.z, w.x, w.z);  // Re: - Re l Re m
+  df_mac(-l.y, -l.w, m.y, m.w, w.x, w.z);  //     - Im l Im m
+  df_mul(-l.y, -l.w, m.x, m.z, w.y, w.w);  // Im: - Im l Re m
+  df_mac(l.x, l.z, m.y, m.w, w.y, w.w);    //     + Re l Im m
+}
+
 // v -= l m (complex pairs; v unnormalised).
 __device__ __forceinline__ void df_sub_lm(float4 &v, const float4 &l, const float4 &m) {
   df_mac(-l.x, -l.z, m.x, m.z, v.x, v.z);  // Re: - Re l Re m + Im l Im m
@@ -130,6 +139,19 @@ __device__ __forceinline__ void fold_panel(float4 *M, float4 *y, float2 *invf, f
   }
 }
 
+// One trailing entry v - sum_q L_{ii, q} conj(L_{kk, q}) over the panel's nb
+// columns (nb >= 1), in two independent chains (q even / odd) merged at the end.
+__device__ __forceinline__ float4 trail_entry(float4 v, const float4 *M, const int (&cq)[kPanel], int ii,
+                                              const float4 (&lk)[kPanel], int nb) {
+  float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+  df_sub_lconjm(v, M[cq[0] + ii], lk[0]);
+  if (nb > 1) df_neg_lconjm(w, M[cq[1] + ii], lk[1]);
+  if (nb > 2) df_sub_lconjm(v, M[cq[2] + ii], lk[2]);
+  if (nb > 3) df_sub_lconjm(w, M[cq[3] + ii], lk[3]);
+  df_acc2(v, w);
+  return v;
+}
+
 // Rank-nb update of the trailing triangle (rows / columns from j1 = j0 + nb)
 // by panel columns j0 .. j0+nb-1, over rectangle rows r0, r0 + rs, ... < rend;
 // the lanes of the calling warp take the entries.
@@ -153,22 +175,12 @@ __device__ __forceinline__ void fold_trail(float4 *M, int K, int j0, int nb, int
     // Column r: entry ii = r + c; then column n-1-r: ii = c - 1.
     for (; c < cut; c += 32) {
       const int dst = dsta + c, ii = r + c;
-      float4 v = M[dst], w = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int q = 0; q < kPanel; ++q)
-        if (q < nb) df_sub_lconjm((q & 1) ? w : v, M[cq[q] + ii], lka[q]);
-      df_acc2(v, w);
-      M[dst] = v;
+      M[dst] = trail_entry(M[dst], M, cq, ii, lka, nb);
     }
     if (!second) continue;
     for (; c < len; c += 32) {
       const int dst = dstb + c, ii = c - 1;
-      float4 v = M[dst], w = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int q = 0; q < kPanel; ++q)
-        if (q < nb) df_sub_lconjm((q & 1) ? w : v, M[cq[q] + ii], lkb[q]);
-      df_acc2(v, w);
-      M[dst] = v;
+      M[dst] = trail_entry(M[dst], M, cq, ii, lkb, nb);
     }
   }
 }
@@ -192,12 +204,10 @@ __device__ __forceinline__ void fold_trail_flat(float4 *M, int K, int j0, int nb
       const bool first = c < cut;
       const int kk = first ? r : n - 1 - r, ii = first ? r + c : c - 1;
       const int dst = tri_off(j1 + kk, K) + ii - kk;
-      float4 v = M[dst], w = make_float4(0.f, 0.f, 0.f, 0.f);
+      float4 lk[kPanel];
 #pragma unroll
-      for (int q = 0; q < kPanel; ++q)
-        if (q < nb) df_sub_lconjm((q & 1) ? w : v, M[cq[q] + ii], M[cq[q] + kk]);
-      df_acc2(v, w);
-      M[dst] = v;
+      for (int q = 0; q < kPanel; ++q) lk[q] = q < nb ? M[cq[q] + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
+      M[dst] = trail_entry(M[dst], M, cq, ii, lk, nb);
     }
     c += dc;
     r += dr;
@@ -476,22 +486,35 @@ __global__ void dstep_kernel(int K, int F, float rho_eff, const float2 *__restri
 
 // Pruned inverse DFT along k1, restricted to m1 in [0, M):
 // Y[k][m1][k2] = sum_k1 E[k][k1][k2] exp(+2 pi i k1 m1 / N).
-// Grid (K, ceil(NH/32)), block (32, M): thread (k2, m1).
+// Grid (K, ceil(NH/32)), block (32, M): the block first stages its N x 32
+// column block of E in shared memory (coalesced rows of 32 bins), then thread
+// (k2, m1) sums over k1 from there.
 constexpr int kMaxM = 16;
 __global__ void vstep_cols_kernel(int K, int N, int M, const float2 *__restrict__ E,
                                   const float2 *__restrict__ tw, float2 *__restrict__ Y) {
-  extern __shared__ float2 s_twc[];
+  extern __shared__ float2 s_twc[];  // [N] twiddles, then [N][32] column block
+  float2 *s_e = s_twc + N;
   const int NH = N / 2 + 1, F = N * NH;
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  for (int i = tid; i < N; i += 32 * blockDim.y) s_twc[i] = tw[i];
-  __syncthreads();
+  const int tid = threadIdx.y * 32 + threadIdx.x, nthr = 32 * blockDim.y;
+  for (int i = tid; i < N; i += nthr) s_twc[i] = tw[i];
   const int k = blockIdx.x, k2 = blockIdx.y * 32 + threadIdx.x, m1 = threadIdx.y;
+  const float2 *Ek = E + (size_t)k * F + blockIdx.y * 32;
+  const int ncol = min(32, NH - blockIdx.y * 32);
+  for (int e = tid; e < N * 32; e += nthr) {
+    const int k1 = e >> 5, c = e & 31;
+    s_e[e] = c < ncol ? Ek[(size_t)k1 * NH + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
   if (k2 >= NH) return;
-  const float2 *Ek = E + (size_t)k * F + k2;
   float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+  int ph = 0;  // (k1 m1) mod N
   for (int k1 = 0; k1 < N; k1 += 2) {
-    acc0 = cadd(acc0, cmulc(Ek[(size_t)k1 * NH], s_twc[(k1 * m1) % N]));
-    acc1 = cadd(acc1, cmulc(Ek[(size_t)(k1 + 1) * NH], s_twc[((k1 + 1) * m1) % N]));
+    acc0 = cadd(acc0, cmulc(s_e[k1 * 32 + threadIdx.x], s_twc[ph]));
+    ph += m1;
+    if (ph >= N) ph -= N;
+    acc1 = cadd(acc1, cmulc(s_e[(k1 + 1) * 32 + threadIdx.x], s_twc[ph]));
+    ph += m1;
+    if (ph >= N) ph -= N;
   }
   Y[((size_t)k * M + m1) * NH + k2] = cadd(acc0, acc1);
 }
@@ -648,7 +671,12 @@ cudaError_t launch_vstep_cols(int K, int N, int M, const float2 *E, const float2
                               cudaStream_t s) {
   if (M > kMaxM || N > kMaxFFT) return cudaErrorInvalidValue;
   dim3 grid(K, (N / 2 + 1 + 31) / 32), block(32, M);
-  vstep_cols_kernel<<<grid, block, N * sizeof(float2), s>>>(K, N, M, E, tw, Y);
+  const size_t sm = (size_t)N * 33 * sizeof(float2);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(vstep_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  vstep_cols_kernel<<<grid, block, sm, s>>>(K, N, M, E, tw, Y);
   return cudaGetLastError();
 }
 
