@@ -12,7 +12,9 @@
  *                       (Sec. III-B, eqs. (A_update), (B_update)), then
  *                       DictOCSC (Algorithm 2): the D-row solve of eq.
  *                       (sub_d_sol) with C^p = (A^p + rho I)^-1 = X^H X, X the
- *                       inverse of an FP64 Cholesky factor, the support +
+ *                       inverse of the Cholesky factor (computed in
+ *                       double-float, FP32 hi + lo pairs, ~48 significant
+ *                       bits; FP64 for K > 128), the support +
  *                       unit-ball projection of Proposition 2 and the scaled
  *                       dual update.
  *   ocsc_get_dict    -- the filters D_t (Algorithm 3, last loop).
@@ -97,7 +99,7 @@ typedef struct {
                             (hi + lo; products hi hi + hi lo + lo hi). */
   int autotune;       /* 1 (default): at a size class's first use, time the
                          candidate tile shapes on its own buffers and keep the
-                         fastest: threads per CTA of the FP64 factorisation
+                         fastest: threads per CTA of the factorisation
                          (256 or 512), columns per CTA of the N >= 256 spatial
                          FFT kernel in ocsc_code (8 or 16), samples per chunk
                          of the tensor-core contraction (32, 64, 128).  Every
@@ -113,13 +115,15 @@ typedef struct {
                          slots and launch the graph (codes are copied out).
                          Not used while coding kernels are profiled.  0
                          (default): every launch is issued directly. */
-  int history;        /* 0 (default): keep A^p and factor w A^p + rho I in FP64
-                         at every update (the C^p definition of eq.
-                         (sub_d_sol)).  1: keep C^p itself and apply the
+  int history;        /* 0 (default): keep A^p and factor w A^p + rho I at
+                         every update (the C^p definition of eq. (sub_d_sol)).
+                         1: keep C^p itself (double-float) and apply the
                          printed Sherman-Morrison recursion of eq. (C_update)
-                         per folded sample (FP64, O(K^2)); it yields
+                         per folded sample (O(K^2)); it yields
                          C_t = (A_t + (rho P / t) I)^-1, a ridge that decays
-                         with the sample count t.  Needs rho_convention 1 (the
+                         with the sample count t, and DictOCSC then runs with
+                         the matching penalty rho / t (the scaled dual carried
+                         as rho Theta across updates).  Needs rho_convention 1 (the
                          printed rho P: with the spatial rho the first C
                          already has a condition number near |z|^2 / rho and
                          the rank-one downdates diverge, in FP64 too), one FFT
@@ -209,7 +213,7 @@ ocsc_status ocsc_set_state(ocsc_ctx *ctx, const void *buf, size_t len);
 
 /* Tile shapes in use for FFT size N (0 where not tuned yet or not used). */
 typedef struct {
-  int fold_threads; /* CTA size of the K <= 128 fold + FP64 factorisation */
+  int fold_threads; /* CTA size of the K <= 128 fold + factorisation */
   int spat_cb;      /* columns per CTA of the N >= 256 spatial kernel in ocsc_code */
   int gram_sc;      /* samples per chunk of the tensor-core contraction */
 } ocsc_tuning;
@@ -323,7 +327,9 @@ typedef enum {
                                 the spectral row kernels) */
   OCSC_K_CODE_PLANE = 2,     /* fused code-ADMM iteration per filter pair (N >= 256:
                                 the spatial column kernel) */
-  OCSC_K_FOLD_FACTOR = 3,    /* history fold + FP64 Cholesky + FP32 L^-1 per frequency */
+  OCSC_K_FOLD_FACTOR = 3,    /* history fold + Cholesky (double-float; FP64 for K > 128)
+                                + FP32 L^-1 per frequency; with history = 1 the
+                                Sherman-Morrison fold */
   OCSC_K_DSTEP = 4,          /* D-row solve of eq. (sub_d_sol) */
   OCSC_K_VSTEP_COLS = 5,     /* pruned inverse DFT along the first axis */
   OCSC_K_VSTEP_PROJECT = 6,  /* Proposition 2 projection of the support */

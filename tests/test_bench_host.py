@@ -1,5 +1,5 @@
 """Host-side logic of bench.py on CPU: multi-rank aggregation over gloo
-(world size 2) and the algorithmic FLOP count of the FP64 factor kernel."""
+(world size 2) and the algorithmic FLOP counts of the factor kernel."""
 import os
 import socket
 
@@ -68,3 +68,29 @@ def test_fold_factor_flop_count(K):
 
 def test_fp64_peak_is_derived_from_unit_counts():
     assert bench.FP64_PEAK_TFLOPS == pytest.approx(152 * 2 * 2 * 2.07e9 / 1e12)
+
+
+def test_fp32_peak_is_derived_from_unit_counts():
+    assert bench.FP32_PEAK_TFLOPS == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+
+
+def _count_fold_factor_df_flops(K):
+    """Walk the factorisation column by column: every trailing entry of step
+    j takes one double-float complex multiply-subtract (4 error-free real
+    multiply-accumulates of 1 FMUL + 3 FFMA + 8 FADD = 15 flops), so does
+    every row of the right-hand side below j; the column scaling is 32 flops
+    per entry; X = L^-1 takes one FP32 complex MAC (8 flops) per entry of the
+    forward substitution."""
+    f = 0
+    for j in range(K):
+        n = K - j - 1
+        f += 60 * n * (n + 1) // 2           # trailing update, pairs
+        f += 60 * n                          # y_i -= L_ij y_j, pairs
+        f += 32 * n                          # L_ij = M_ij / L_jj
+        f += 8 * n * (j + 1)                 # X_ic -= L_ij X_jc, c <= j
+    return f
+
+
+@pytest.mark.parametrize("K", [1, 2, 16, 100])
+def test_fold_factor_df_flop_count(K):
+    assert bench.fold_factor_df_flops(K, 1) == pytest.approx(_count_fold_factor_df_flops(K))

@@ -4,8 +4,10 @@ All GPU work goes through the C ABI (libocsc.so via the ctypes binding).
 Tolerances come from FP32 arithmetic: FFTs of N x N planes carry a relative
 error of a few eps32 * log2(N^2) (eps32 = 6e-8), and the ADMM iterates
 propagate it through Jz = 50 code iterations and Jd = 10 dictionary
-iterations; the dictionary solve adds the FP32 triangular solves with the FP64
-Cholesky factor, whose error grows with the condition number of A + rho I.
+iterations; the dictionary solve adds the FP32 triangular products with the
+inverse of the Cholesky factor (factored in double-float, FP32 hi + lo pairs
+of ~48 bits; FP64 for K > 128), whose error grows with the condition number of
+A + rho I.
 The bars below are those of the method statement: relative objective 1e-4 on
 the FP32 path, and norm-relative code / dictionary errors 1e-3.
 """
@@ -595,8 +597,9 @@ def test_fit_stops_by_the_rule_of_the_paper():
 # The printed recursion comes with the printed rho P: C_t = (A_t + (rho P / t) I)^-1,
 # and DictOCSC runs with the matching penalty rho / t (reading R23).  (With the
 # spatial rho = 1 the ridge starts at 1 against |z|^2 ~ 1e4 and the oracle's own
-# FP64 recursion loses its accuracy within ten samples.)  C is FP64 on both sides;
-# the FP32 codes and b carry the usual coding error.
+# FP64 recursion loses its accuracy within ten samples.)  C is double-float on the
+# GPU (~48 bits) and FP64 in the oracle; the FP32 codes and b carry the usual
+# coding error.
 RECURSION_DICT_TOL = REL_TOL
 
 @pytest.mark.parametrize("wname,N,nimg,batch", [("plain_64_k16", 64, 20, 1), ("plain_64_k16", 64, 12, 4),
