@@ -499,7 +499,7 @@ def _run_sequence(pkg, graphs, autotune, precision=0):
                   graphs=graphs, autotune=autotune, precision=precision)
     lr.set_dict(raw, normalize=True)
     codes = []
-    for r in range(4):   # the same chunk shapes every round: captured at round 2
+    for r in range(4):   # the same chunk shapes every pass: captured at the second pass
         xs = [torch.from_numpy(make_image(s, s, 1500 + 10 * r + i)).cuda() for i, s in enumerate([50, 200])]
         us = lr.code(xs)
         lr.update_dict()
