@@ -181,6 +181,18 @@ def test_edge_cases_match_oracle(case):
         assert rel(dicts[t], odicts[t]) < REL_TOL, t
 
 
+def test_fold_of_more_samples_than_one_chunk_matches_oracle():
+    """A mini-batch of 20 samples: the fold stages pending codes in chunks of
+    16, so the running sums cross a chunk boundary before the factorisation."""
+    _need_gpu()
+    imgs = _small_images(20, 48, 48, 1700)
+    raw = raw_filters(12, 5, 1701)
+    codes, dicts = run_gpu(imgs, raw, 12, 5, 0.5, 1.0, 64, 8, 4, batch=20, pad=0)
+    ocodes, odicts, _ = run_oracle(imgs, raw, 64, 0.5, 1.0, 8, 4, batch=20)
+    assert max(rel(codes[t], ocodes[t]) for t in range(20)) < REL_TOL
+    assert rel(dicts[0], odicts[0]) < REL_TOL
+
+
 @pytest.mark.parametrize("K", [1, 3, 5, 127, 128])
 def test_factor_panel_edges_match_oracle(K):
     """The per-frequency factorisation works on panels of 4 columns with the
