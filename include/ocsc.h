@@ -184,7 +184,10 @@ ocsc_status ocsc_update_dict(ocsc_ctx *ctx);
 /*
  * Copy the filters D_t (K x M x M floats) to HOST memory D_host and the
  * dictionary version (number of completed updates) to *version (nullable).
- * Synchronises ctx's stream and reports pending device-side errors.
+ * With return_feasible = 1, D_t = V_{t,J} (feasible); with return_feasible = 0,
+ * D_t = H(F^-1(D~_{t,J})), the support crop of the D~ that Algorithm 2 returns
+ * (Algorithm 3, last loop), formed on the device.  Synchronises ctx's stream
+ * and reports pending device-side errors.
  */
 ocsc_status ocsc_get_dict(ocsc_ctx *ctx, float *D_host, uint64_t *version);
 
@@ -261,6 +264,47 @@ ocsc_status ocsc_objective_terms(ocsc_ctx *ctx, int n, const float *const *x, co
  * Result in *out_host (0 for count = 0, +inf if a = 0 and b != 0).  Synchronises.
  */
 ocsc_status ocsc_rel_diff(ocsc_ctx *ctx, const float *a, const float *b, size_t count, double *out_host);
+
+/*
+ * PSNR of the reconstruction sum_k D_k (*) U_ik against x_i, the test-set
+ * measure of Sec. IV: psnr_host[i] = 10 log10(peak^2 P_i / ||x_i - sum_k D_k (*)
+ * U_ik||^2) with P_i the pixel count of the sample's padded N x N domain (the
+ * domain the model is defined on) and peak > 0 the signal peak (255 for the
+ * paper's 8-bit images).  Same arguments and rules as ocsc_objective; the
+ * logarithm is taken on the device in FP64.  Synchronises.
+ */
+ocsc_status ocsc_psnr(ocsc_ctx *ctx, int n, const float *const *x, const int *H, const int *W,
+                      const float *const *u, double peak, double *psnr_host);
+
+/*
+ * Display order of the filters (Sec. IV, the learned filters shown sorted by
+ * variance): order_host[r] (HOST, K ints) = the index of the filter with the
+ * r-th smallest sample variance over its M x M entries (sum of squared
+ * deviations divided by M*M - 1; 0 when M = 1), ties in index order.  Computed
+ * on the device from the current filters D_t.  Synchronises.
+ */
+ocsc_status ocsc_filter_order(ocsc_ctx *ctx, int *order_host);
+
+/*
+ * Copy the filters D_t (K x M x M floats) into the DEVICE buffer D_dev
+ * (caller-owned), on ctx's stream; asynchronous.  With ocsc_rel_diff this gives
+ * the dictionary change of the stopping rule of Sec. IV without a host copy.
+ */
+ocsc_status ocsc_copy_dict(ocsc_ctx *ctx, float *D_dev);
+
+/*
+ * Poll budget of the bounded device waits of ctx (the tensor-core history
+ * fold's wait for its MMAs; the persistent coder's grid barrier): a wait that
+ * has polled this many times gives up, the kernel records OCSC_ETIMEOUT in the
+ * context's device error word, finishes or releases what it holds (a timed-out
+ * tensor-core fold still waits, with the full default budget, for the MMAs it
+ * issued before it frees tensor memory) and returns; the next synchronising
+ * call reports OCSC_ETIMEOUT and clears the word.  The paper has no
+ * counterpart: the hook exists so that the failure path can be exercised
+ * (polls = 0 makes every such wait give up at once).  Default 2^24.  The
+ * history of an update that timed out is left as it was before the update.
+ */
+ocsc_status ocsc_set_wait_limit(ocsc_ctx *ctx, uint64_t polls);
 
 /*
  * Serving: continuous batching of coding requests over one context
@@ -396,15 +440,21 @@ ocsc_status ocsc_fft2_c2r(ocsc_ctx *ctx, int N, const float *X, float *x, int pl
  * default stream); the call is asynchronous.  err (nullable, err_len bytes)
  * receives a message on failure.
  *
- * Scratch lives in one file-scope device array of OCSC_NOALLOC_SCRATCH_BYTES
- * that every GPU loading the library holds until the process exits.  The scratch
- * needed is about K * ((3 N + 16) (N/2+1) * 8 + N * N * 4) bytes (K <= 122 at
- * N = 128, K <= 128 at N = 64); larger requests return OCSC_EUNSUPPORTED without
- * touching the device.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current.  All calls
- * share the array and it keeps the last call's contents (nothing needs to start
- * at zero); calls whose work overlaps on the GPU -- on different streams or from
- * different host threads -- race on it and must be serialised by the caller.
+ * Scratch lives in one file-scope device array of OCSC_NOALLOC_SCRATCH_BYTES.
+ * The scratch needed is about K * ((3 N + 16) (N/2+1) * 8 + N * N * 4) bytes
+ * (K <= 122 at N = 128, K <= 128 at N = 64); larger requests return
+ * OCSC_EUNSUPPORTED without touching the device.  Every call looks up the
+ * array's device address (cudaGetSymbolAddress) with the caller's device
+ * current.  Under CUDA's default lazy module loading the array and the coding
+ * kernels are loaded on a device by the first call there, and that loading can
+ * take device memory; from then on the array stays resident on that device
+ * until the process exits and calls allocate nothing.  A caller that must not
+ * allocate after start-up makes one valid call at start-up, or runs with
+ * CUDA_MODULE_LOADING=EAGER (the array is then loaded with the library).  All
+ * calls share the array and it keeps the last call's contents (every call
+ * rewrites what it reads before reading it); calls whose work overlaps on the
+ * GPU -- on different streams or from different host threads -- race on it and
+ * must be serialised by the caller.
  */
 ocsc_status ocsc_code_noalloc(const float *x, int H, int W, const float *D, int K, int M, int N,
                               double lambda, double rho, int Jz, float *u, void *cuda_stream,

@@ -100,6 +100,11 @@ _PROTOS = {
     "ocsc_server_submit": (_I, [_P, ctypes.c_uint64, _P, _I, _I, _P]),
     "ocsc_server_step": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "ocsc_server_poll": (_I, [_P, ctypes.POINTER(ocsc_served), _I, ctypes.POINTER(_I)]),
+    "ocsc_psnr": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                       ctypes.POINTER(_P), ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "ocsc_filter_order": (_I, [_P, ctypes.POINTER(_I)]),
+    "ocsc_copy_dict": (_I, [_P, _P]),
+    "ocsc_set_wait_limit": (_I, [_P, ctypes.c_uint64]),
     "ocsc_code_noalloc": (_I, [_P, _I, _I, _P, _I, _I, _I, ctypes.c_double, ctypes.c_double, _I, _P,
                                _P, ctypes.c_char_p, ctypes.c_size_t]),
 }
@@ -235,13 +240,26 @@ def ocsc_rel_diff(ctx, a_ptr: int, b_ptr: int, count: int) -> float:
     return out.value
 
 
-def filter_order(D):
-    """Filter indices in ascending order of their sample variance over the
-    M x M entries (the display order of Sec. IV)."""
-    import numpy as np
+def ocsc_psnr(ctx, x_ptrs, H, W, u_ptrs, peak: float):
+    n = len(x_ptrs)
+    out = (ctypes.c_double * n)()
+    _check(ctx, lib().ocsc_psnr(ctx, n, (_P * n)(*x_ptrs), (_I * n)(*H), (_I * n)(*W), (_P * n)(*u_ptrs),
+                                peak, out))
+    return list(out)
 
-    flat = np.asarray(D, np.float64).reshape(len(D), -1)
-    return np.argsort(flat.var(axis=1, ddof=1), kind="stable")
+
+def ocsc_filter_order(ctx, K: int):
+    out = (_I * K)()
+    _check(ctx, lib().ocsc_filter_order(ctx, out))
+    return list(out)
+
+
+def ocsc_copy_dict(ctx, D_dev_ptr: int) -> None:
+    _check(ctx, lib().ocsc_copy_dict(ctx, ctypes.c_void_p(D_dev_ptr)))
+
+
+def ocsc_set_wait_limit(ctx, polls: int) -> None:
+    _check(ctx, lib().ocsc_set_wait_limit(ctx, polls))
 
 
 def ocsc_get_counters(ctx) -> ocsc_counters:
@@ -401,10 +419,28 @@ class OCSC:
     def psnr(self, images, codes, peak: float = 255.0):
         """Per-sample 10 log10(peak^2 P / ||x_rec - x||^2) over the padded
         P = N x N domain (Sec. IV; the paper uses peak 255 for 8-bit images)."""
-        import math
+        xs = [im.contiguous() for im in images]
+        us = [u.contiguous() for u in codes]
+        return ocsc_psnr(self.ctx, [im.data_ptr() for im in xs], [im.shape[0] for im in xs],
+                         [im.shape[1] for im in xs], [u.data_ptr() for u in us], float(peak))
 
-        r2, _ = self.objective_terms(images, codes)
-        return [10.0 * math.log10(peak * peak * u.shape[-1] * u.shape[-2] / v) for u, v in zip(codes, r2)]
+    def filter_order(self):
+        """Filter indices in ascending order of their sample variance (Sec. IV)."""
+        import numpy as np
+
+        return np.asarray(ocsc_filter_order(self.ctx, self.K), np.int64)
+
+    def dict_device(self, out=None):
+        """The filters D_t as a [K, M, M] float32 CUDA tensor (device copy)."""
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.K, self.M, self.M), device="cuda", dtype=torch.float32)
+        ocsc_copy_dict(self.ctx, out.data_ptr())
+        return out
+
+    def set_wait_limit(self, polls: int):
+        """Poll budget of the bounded device waits (failure-path tests)."""
+        ocsc_set_wait_limit(self.ctx, int(polls))
 
     def rel_diff(self, a, b) -> float:
         """||a - b|| / ||a|| of two float32 CUDA tensors of the same size."""
@@ -418,25 +454,26 @@ class OCSC:
         """Online passes over `images` (Algorithm 3 per mini-batch) until the
         stopping rule of Sec. IV holds: the relative change of the codes of the
         current mini-batch against the previous pass and of the dictionary
-        against the previous update both below tol.  Returns a dict with the
-        pass and step where it stopped (or max_passes) and the last changes."""
-        import numpy as np
+        against the previous update both below tol (both relative changes are
+        taken on the device, ocsc_rel_diff).  Returns a dict with the pass and
+        step where it stopped (or max_passes) and the last changes."""
 
         prev = [None] * len(images)
-        D_old = self.get_dict()
+        D_old = self.dict_device()
+        D_new = self.dict_device()
         last = {"code_change": float("inf"), "dict_change": float("inf")}
         for p in range(max_passes):
             for t in range(0, len(images), batch):
                 idx = list(range(t, min(t + batch, len(images))))
                 us = self.code([images[i] for i in idx])
                 self.update_dict()
-                D = self.get_dict().astype(np.float64)
+                self.dict_device(out=D_new)
                 dz = max(self.rel_diff(u, prev[i]) if prev[i] is not None else float("inf")
                          for u, i in zip(us, idx))
-                dd = float(np.linalg.norm(D - D_old) / max(np.linalg.norm(D), 1e-300))
+                dd = self.rel_diff(D_new, D_old)
                 for u, i in zip(us, idx):
                     prev[i] = u
-                D_old = D
+                D_old, D_new = D_new, D_old
                 last = {"code_change": dz, "dict_change": dd}
                 if dz < tol and dd < tol:
                     return {"stopped": True, "pass": p, "step": t // batch, **last}

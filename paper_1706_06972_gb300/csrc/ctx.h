@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ocsc.h"
 #include "common.cuh"
 #include "launch.h"
@@ -57,6 +59,8 @@ struct GraphEntry {
   size_t kernels = 0;  // kernel nodes per replay
 };
 constexpr size_t kMaxGraphs = 32;
+// Default poll count of the bounded device waits (tensor-core fold, persistent coder).
+constexpr unsigned kWaitPolls = 1u << 24;
 
 }  // namespace ocsc
 
@@ -66,10 +70,13 @@ struct ocsc_ctx {
   ocsc_opts opts{};
   cudaStream_t stream = nullptr;
   float *V = nullptr;       // [K][M][M] the spatial filters
+  float *Dpub = nullptr;    // [K][M][M] H(F^-1(D~_{t,J})) when return_feasible = 0
   std::vector<ocsc::SizeClass> cls;
   double *obj_part = nullptr;
   double *obj_out = nullptr;
   int *err = nullptr;       // device error word
+  int *order = nullptr;     // [K] filter order (ocsc_filter_order)
+  unsigned wait_polls = ocsc::kWaitPolls;  // polls of a bounded device wait before it gives up
   double2 *work = nullptr;  // K > 128: FP64 factorisation workspace, one matrix per persistent CTA
   int work_ctas = 0;
   long long n_seen = 0;     // samples folded over all classes
@@ -86,6 +93,15 @@ struct ocsc_ctx {
 };
 
 namespace ocsc {
+
+// NVTX range over one library call (visible in Nsight timelines; a no-op
+// unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 inline ocsc_status fail(ocsc_ctx *c, ocsc_status s, const char *fmt, ...) {
   char buf[512];

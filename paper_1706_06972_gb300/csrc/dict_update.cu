@@ -522,6 +522,8 @@ __global__ void vstep_cols_kernel(int K, int N, int M, const float2 *__restrict_
 // V-step of Proposition 2 over the active size classes, one CTA per filter k:
 // alpha_c = H(F_c^-1(D~_c + theta^_c)) from each class's Y_c, alpha = mean over
 // classes (with one class, alpha_c itself), V_k = alpha / max(||alpha||, 1).
+// With ac.project = 0 it writes alpha itself (H(F^-1(.)) of what Y was formed
+// from), which publishes D~_{t,J} literally.
 constexpr int kProjThreads = 256;
 __global__ void __launch_bounds__(kProjThreads)
     vstep_project_kernel(int K, int M, AlphaClasses ac, float *__restrict__ V) {
@@ -562,7 +564,7 @@ __global__ void __launch_bounds__(kProjThreads)
     if (tid == 0) red[0] = v;
   }
   __syncthreads();
-  const float sc = 1.0f / fmaxf(sqrtf(red[0]), 1.0f);
+  const float sc = ac.project ? 1.0f / fmaxf(sqrtf(red[0]), 1.0f) : 1.0f;
   for (int e = tid; e < MM; e += kProjThreads) V[(size_t)k * MM + e] = alpha[e] * sc;
 }
 

@@ -35,7 +35,7 @@ namespace ocsc {
 namespace {
 
 constexpr int kTcThreads = 256;
-constexpr unsigned kWaitLimit = 1u << 24;  // mbarrier polls before giving up
+constexpr unsigned kWaitLimit = 1u << 24;  // mbarrier polls of the drain wait after a timeout
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -75,9 +75,10 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(count) : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (unsigned it = 0; it < kWaitLimit; ++it) {
+// Bounded wait for the phase with the given parity (at most `polls` polls);
+// false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, unsigned polls) {
+  for (unsigned it = 0; it < polls; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_fold_tc_kernel(GramArgs a)
         mma_commit(mb_addr);
       }
       // (c) the MMAs have read the chunk and written the tiles.
-      if (!mbar_wait(mb_addr, phase)) ok = false;
+      if (!mbar_wait(mb_addr, phase, a.wait_polls)) ok = false;
       phase ^= 1u;
       fence_after();
       if (__syncthreads_or(!ok)) {
@@ -296,11 +297,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) gram_fold_tc_kernel(GramArgs a)
     fence_after();
   }
 
-  // On a timeout, record it and wait once more (bounded) so that no MMA is
-  // still writing tensor memory when it is released.
+  // On a timeout, record it and wait once more, with the full poll budget
+  // whatever the caller's limit, so that no MMA is still writing tensor memory
+  // when it is released.
   if (!ok) {
     if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
-    (void)mbar_wait(mb_addr, phase ^ 1u);
+    (void)mbar_wait(mb_addr, phase ^ 1u, kWaitLimit);
   }
   fence_before();
   __syncthreads();

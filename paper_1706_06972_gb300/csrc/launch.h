@@ -121,6 +121,7 @@ struct GramArgs {
   float2 *A, *Alo;          // [F][stride]
   float2 *b;                // [K][F]
   int *err;
+  unsigned wait_polls;      // polls of the MMA-completion wait before it reports ERR_TIMEOUT
 };
 int gram_chunk(int K, int B, int terms);
 
@@ -160,12 +161,14 @@ cudaError_t launch_vstep_cols(int K, int N, int M, const float2 *E, const float2
 // Size classes that take part in one V-step (reading R16).
 constexpr int kMaxClasses = 12;
 struct AlphaClasses {
+  int project;                      // 1: Proposition 2 projection; 0: the mean crop as is
   int C;                            // active classes
   int N[kMaxClasses];               // FFT side of each
   const float2 *Y[kMaxClasses];     // [K][M][N/2+1] pruned inverse DFT along k1
   const float2 *tw[kMaxClasses];    // twiddles of each size
 };
-// Proposition 2 on the mean over classes of the support crops: writes V.
+// Proposition 2 on the mean over classes of the support crops: writes V
+// (ac.project = 0: the mean crop itself, for the literal return of Algorithm 2).
 cudaError_t launch_vstep_project(int K, int M, const AlphaClasses &ac, float *V, cudaStream_t s);
 // Partial DFT Tm [K][M][N/2+1] of the filters V for one class size.
 cudaError_t launch_vstep_partial_dft(int K, int N, int M, const float *V, const float2 *tw, float2 *Tm,
@@ -187,5 +190,18 @@ cudaError_t launch_objective(int K, int N, double lam, const float2 *Dh, const f
 // 2 kObjL1Blocks doubles.
 cudaError_t launch_rel_diff(const float *a, const float *b, size_t count, double *partial, double *out,
                             cudaStream_t s);
+
+// PSNR of Sec. IV from the objective terms of n samples (terms [n][3], the
+// squared residual norm at [3 i + 1]).
+constexpr int kMaxPsnr = 64;
+struct PsnrArgs {
+  int n;
+  double peak;
+  int P[kMaxPsnr];  // pixel count of each sample's padded domain
+};
+cudaError_t launch_psnr(const double *terms, const PsnrArgs &a, double *out, cudaStream_t s);
+// Filters in ascending order of their sample variance (K <= kMaxOrderK).
+constexpr int kMaxOrderK = 256;
+cudaError_t launch_filter_order(int K, int M, const float *V, int *order, cudaStream_t s);
 
 }  // namespace ocsc

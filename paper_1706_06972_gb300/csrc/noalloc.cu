@@ -5,22 +5,25 @@
 // allocator, a latency-sensitive pipeline that cannot afford the device-wide
 // synchronisation that cudaMalloc / cudaFree can imply while other streams run,
 // or a deployment that must not fail at run time for lack of memory and so
-// takes everything it needs when the library is loaded.  For them this file
-// keeps the scratch of one coding call in a fixed file-scope device array and
-// runs the same kernels as ocsc_code on it.  The caller still provides the
-// image, the filters and the output buffer.
+// takes everything it needs at start-up.  For them this file keeps the scratch
+// of one coding call in a fixed file-scope device array and runs the same
+// kernels as ocsc_code on it.  The caller still provides the image, the filters
+// and the output buffer.
 //
-// The array below is part of the library image: every GPU that loads the
-// library holds OCSC_NOALLOC_SCRATCH_BYTES of it until the process exits.  All
-// calls share it and it keeps whatever the last call left there; nothing has to
-// start at zero because the first ADMM iteration reads no earlier state.  Two
-// calls whose work overlaps on the GPU (other streams, other host threads)
-// overwrite each other's scratch: serialise them.
+// The array below is part of this file's module.  Under CUDA's default lazy
+// module loading the module (with the array) and the coding kernels are loaded
+// on the first call on each device, and loading can itself take device memory;
+// after that, the array stays resident on that device until the process exits.
+// A caller that must never allocate after start-up therefore makes one call at
+// start-up (or runs with CUDA_MODULE_LOADING=EAGER).  All calls share the array
+// and it keeps whatever the last call left there; nothing has to start at zero
+// because the twiddles are rewritten by every call and the first ADMM
+// iteration reads no earlier state.  Two calls whose work overlaps on the GPU
+// (other streams, other host threads) overwrite each other's scratch:
+// serialise them.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
-#include <mutex>
-#include <vector>
 
 #include "../../include/ocsc.h"
 #include "common.cuh"
@@ -31,10 +34,6 @@ using namespace ocsc;
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[OCSC_NOALLOC_SCRATCH_BYTES];
-
-constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices] = {};  // device address of the array, per device
-std::mutex g_scratch_mu;
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -57,6 +56,15 @@ Carve carve(int K, int N) {
   c.Gam = o;  o += up256(K * P * sizeof(float));
   c.total = o;
   return c;
+}
+
+// W_N^m = exp(-2 pi i m / N) for m < N, evaluated in double and rounded once
+// to float, as the context path's host table is.
+__global__ void noalloc_twiddles_kernel(int N, float2 *tw) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= N) return;
+  const double a = -2.0 * 3.14159265358979323846 * (double)m / (double)N;
+  tw[m] = make_float2((float)cos(a), (float)sin(a));
 }
 
 ocsc_status say(char *err, size_t len, ocsc_status s, const char *fmt, ...) {
@@ -89,24 +97,14 @@ extern "C" ocsc_status ocsc_code_noalloc(const float *x, int H, int W, const flo
                "K=%d at N=%d needs %zu bytes of scratch; the fixed array holds %zu", K, N, cv.total,
                (size_t)OCSC_NOALLOC_SCRATCH_BYTES);
 
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return say(err, err_len, OCSC_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return say(err, err_len, OCSC_EUNSUPPORTED, "device %d", dev);
-  unsigned char *base = nullptr;
-  {
-    // First call on this device: look up the array's device address (host code
-    // only sees a host-side stand-in for the symbol).
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-      void *p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess)
-        return say(err, err_len, OCSC_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-      g_scratch_addr[dev] = p;
-    }
-    base = static_cast<unsigned char *>(g_scratch_addr[dev]);
-  }
+  // The array's device address, looked up on every call with the caller's
+  // device current: host code only sees a host-side stand-in for the symbol,
+  // and the address belongs to the current context (a context created anew,
+  // for instance after cudaDeviceReset, may place the module elsewhere).
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return say(err, err_len, OCSC_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  unsigned char *base = static_cast<unsigned char *>(p);
 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const int F = N * (N / 2 + 1);
@@ -116,16 +114,11 @@ extern "C" ocsc_status ocsc_code_noalloc(const float *x, int H, int W, const flo
   float2 *xh = reinterpret_cast<float2 *>(base + cv.xh);
   float2 *r = reinterpret_cast<float2 *>(base + cv.r);
 
-  std::vector<float2> twh(N);
-  for (int m = 0; m < N; ++m) {
-    const double a = -2.0 * M_PI * (double)m / (double)N;
-    twh[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
-  e = cudaMemcpyAsync(tw, twh.data(), N * sizeof(float2), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return say(err, err_len, OCSC_ECUDA, "twiddles: %s", cudaGetErrorString(e));
+  noalloc_twiddles_kernel<<<(N + 127) / 128, 128, 0, s>>>(N, tw);
+  e = cudaGetLastError();
   // D~ = F(pad D) and |D~(p,:)|^2, then the same code-ADMM launches as ocsc_code.
   float2 *Tm = reinterpret_cast<float2 *>(base + cv.Tm);
-  e = launch_vstep_partial_dft(K, N, M, D, tw, Tm, s);
+  if (e == cudaSuccess) e = launch_vstep_partial_dft(K, N, M, D, tw, Tm, s);
   if (e == cudaSuccess) e = launch_vstep_spectrum(1, K, N, M, Tm, tw, Dh, nullptr, nullptr, s);
   if (e == cudaSuccess) e = launch_dict_norms(K, F, Dh, dn, s);
   ImgBatch b{};

@@ -117,6 +117,54 @@ cudaError_t launch_rel_diff(const float *a, const float *b, size_t count, double
   return cudaGetLastError();
 }
 
+// PSNR of Sec. IV per sample from its squared residual norm:
+// out[i] = 10 log10(peak^2 P_i / r2_i), r2_i = terms[3 i + 1] (the layout the
+// objective kernels write), P_i the pixel count of the sample's padded domain.
+__global__ void psnr_kernel(const double *__restrict__ terms, PsnrArgs a, double *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  out[i] = 10.0 * log10(a.peak * a.peak * (double)a.P[i] / terms[3 * i + 1]);
+}
+
+cudaError_t launch_psnr(const double *terms, const PsnrArgs &a, double *out, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  psnr_kernel<<<1, kMaxPsnr, 0, s>>>(terms, a, out);
+  return cudaGetLastError();
+}
+
+// Display order of the filters (Sec. IV): ascending sample variance over the
+// M x M entries of each filter (divided by the entry count minus one; 0 for
+// 1 x 1 filters), ties kept in index order.  One block: thread k forms the
+// variance of filter k in FP64, then its rank among all K (a stable counting
+// rank), and writes order[rank] = k.
+__global__ void filter_order_kernel(int K, int MM, const float *__restrict__ V, int *__restrict__ order) {
+  __shared__ double var[kMaxOrderK];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    const float *f = V + (size_t)k * MM;
+    double mu = 0.0;
+    for (int e = 0; e < MM; ++e) mu += (double)f[e];
+    mu /= (double)MM;
+    double ss = 0.0;
+    for (int e = 0; e < MM; ++e) {
+      const double d = (double)f[e] - mu;
+      ss += d * d;
+    }
+    var[k] = MM > 1 ? ss / (double)(MM - 1) : 0.0;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    int rank = 0;
+    for (int j = 0; j < K; ++j) rank += (var[j] < var[k] || (var[j] == var[k] && j < k)) ? 1 : 0;
+    order[rank] = k;
+  }
+}
+
+cudaError_t launch_filter_order(int K, int M, const float *V, int *order, cudaStream_t s) {
+  if (K > kMaxOrderK) return cudaErrorInvalidValue;
+  filter_order_kernel<<<1, 256, 0, s>>>(K, M * M, V, order);
+  return cudaGetLastError();
+}
+
 int objective_partials(int N) {
   const int F = N * (N / 2 + 1);
   return (F + kObjBlock - 1) / kObjBlock + kObjL1Blocks;

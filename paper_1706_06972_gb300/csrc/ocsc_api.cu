@@ -255,9 +255,9 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
     c->work_ctas = sms;
     if ((st = dalloc(c, &c->work, factor_big_workspace(K, sms)))) return bail(st);
   }
-  if ((st = dalloc(c, &c->V, (size_t)K * c->M * c->M)) || (st = dalloc(c, &c->err, 1)) ||
+  if ((st = dalloc(c, &c->V, (size_t)K * c->M * c->M)) || (st = dalloc(c, &c->Dpub, (size_t)K * c->M * c->M)) || (st = dalloc(c, &c->err, 1)) ||
       (st = dalloc(c, &c->obj_part, (size_t)std::max(max_partials, 2 * kObjL1Blocks))) ||
-      (st = dalloc(c, &c->obj_out, (size_t)3 * kObjChunk)))
+      (st = dalloc(c, &c->obj_out, (size_t)4 * kObjChunk)) || (st = dalloc(c, &c->order, (size_t)K)))
     return bail(st);
   cudaError_t e = cudaMemset(c->err, 0, sizeof(int));
   if (e != cudaSuccess) { cuda_fail(c, e, "clear error word"); return bail(OCSC_ECUDA); }
@@ -469,6 +469,7 @@ static ocsc_status code_class(ocsc_ctx *c, SizeClass &s, const std::vector<int> 
 ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, const int *W,
                       float *const *u) {
   if (!c) return OCSC_EINVAL;
+  NvtxRange range("ocsc_code");
   if (n <= 0 || !x || !H || !W) return fail(c, OCSC_EINVAL, "ocsc_code: bad arguments");
   std::vector<std::vector<int>> groups(c->cls.size());
   for (int i = 0; i < n; ++i) {
@@ -494,6 +495,7 @@ ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, c
 
 ocsc_status ocsc_update_dict(ocsc_ctx *c) {
   if (!c) return OCSC_EINVAL;
+  NvtxRange range("ocsc_update_dict");
   long long fresh = 0;
   for (const SizeClass &s : c->cls) fresh += s.pending;
   if (fresh == 0) return OCSC_OK;
@@ -583,6 +585,7 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
               gd.Alo = s.Alo;
               gd.b = s.b;
               gd.err = c->err;
+              gd.wait_polls = ocsc::kWaitPolls;
               gd.F = s.F;
               gd.K = c->K;
               gd.B = s.pending;
@@ -605,6 +608,7 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
         ga.Alo = s.Alo;
         ga.b = s.b;
         ga.err = c->err;
+        ga.wait_polls = c->wait_polls;
         e = timed(c, OCSC_K_HISTORY_TC, [&] { return launch_gram_fold(ga, c->stream); });
         if (e != cudaSuccess) return cuda_fail(c, e, "history fold (tensor cores)");
       }
@@ -634,6 +638,7 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
     if (e != cudaSuccess) return cuda_fail(c, e, "fold_factor");
   }
   AlphaClasses ac{};
+  ac.project = 1;
   ac.C = (int)active.size();
   for (int i = 0; i < ac.C; ++i) {
     ac.N[i] = active[i]->N;
@@ -686,10 +691,26 @@ ocsc_status ocsc_get_dict(ocsc_ctx *c, float *D_host, uint64_t *version) {
   if (!c || !D_host) return c ? fail(c, OCSC_EINVAL, "null output") : OCSC_EINVAL;
   ocsc_status st = check_device(c);
   if (st != OCSC_OK) return st;
-  if (!c->opts.return_feasible)
-    return fail(c, OCSC_EUNSUPPORTED, "get_dict with return_feasible=0 is not implemented");
   const size_t bytes = (size_t)c->K * c->M * c->M * sizeof(float);
-  cudaError_t e = cudaMemcpy(D_host, c->V, bytes, cudaMemcpyDeviceToHost);
+  const float *src = c->V;
+  if (!c->opts.return_feasible) {
+    // Algorithm 3 publishes H(F^-1(D~_t)) with D~_t = D~_{t,J} as Algorithm 2
+    // returns it (one size class): the support crop of its inverse DFT.
+    SizeClass &s = c->cls[0];
+    AlphaClasses ac{};
+    ac.project = 0;
+    ac.C = 1;
+    ac.N[0] = s.N;
+    ac.Y[0] = s.Y;
+    ac.tw[0] = s.tw;
+    cudaError_t e = timed(c, OCSC_K_VSTEP_COLS, [&] { return launch_vstep_cols(c->K, s.N, c->M, s.Dcur, s.tw, s.Y, c->stream); });
+    if (e == cudaSuccess)
+      e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_vstep_project(c->K, c->M, ac, c->Dpub, c->stream); });
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "publish D~_{t,J}");
+    src = c->Dpub;
+  }
+  cudaError_t e = cudaMemcpy(D_host, src, bytes, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "copy filters");
   if (version) *version = c->version;
   return OCSC_OK;
@@ -904,9 +925,10 @@ ocsc_status ocsc_drop_pending(ocsc_ctx *c) {
 }
 
 static ocsc_status objective_terms(ocsc_ctx *c, int n, const float *const *x, const int *H, const int *W,
-                                   const float *const *u, double *f_host, double *r2_host, double *l1_host) {
+                                   const float *const *u, double *f_host, double *r2_host, double *l1_host,
+                                   double *psnr_host = nullptr, double peak = 0.0) {
   if (!c) return OCSC_EINVAL;
-  if (n < 0 || (n > 0 && (!x || !H || !W || !u || !(f_host || r2_host || l1_host))))
+  if (n < 0 || (n > 0 && (!x || !H || !W || !u || !(f_host || r2_host || l1_host || psnr_host))))
     return fail(c, OCSC_EINVAL, "ocsc_objective: bad arguments");
   std::vector<int> cl(n);
   for (int i = 0; i < n; ++i) {
@@ -961,14 +983,25 @@ static ocsc_status objective_terms(ocsc_ctx *c, int n, const float *const *x, co
       }
       if (e != cudaSuccess) return cuda_fail(c, e, "objective");
     }
-    std::vector<double> h((size_t)3 * m);
-    cudaError_t e = cudaMemcpyAsync(h.data(), c->obj_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    std::vector<double> h((size_t)4 * kObjChunk);
+    cudaError_t e = cudaSuccess;
+    if (psnr_host) {
+      PsnrArgs pa{};
+      pa.n = m;
+      pa.peak = peak;
+      for (int i = 0; i < m; ++i) pa.P[i] = c->cls[cl[s0 + i]].P;
+      c->counters.kernel_launches += 1;
+      e = launch_psnr(c->obj_out, pa, c->obj_out + 3 * kObjChunk, c->stream);
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h.data(), c->obj_out, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "objective readback");
     for (int i = 0; i < m; ++i) {
       if (f_host) f_host[s0 + i] = h[3 * i];
       if (r2_host) r2_host[s0 + i] = h[3 * i + 1];
       if (l1_host) l1_host[s0 + i] = h[3 * i + 2];
+      if (psnr_host) psnr_host[s0 + i] = h[3 * kObjChunk + i];
     }
   }
   return OCSC_OK;
@@ -986,6 +1019,38 @@ ocsc_status ocsc_objective_terms(ocsc_ctx *c, int n, const float *const *x, cons
   if (!c) return OCSC_EINVAL;
   if (n > 0 && (!resid2_host || !l1_host)) return fail(c, OCSC_EINVAL, "ocsc_objective_terms: bad arguments");
   return objective_terms(c, n, x, H, W, u, nullptr, resid2_host, l1_host);
+}
+
+ocsc_status ocsc_psnr(ocsc_ctx *c, int n, const float *const *x, const int *H, const int *W,
+                      const float *const *u, double peak, double *psnr_host) {
+  if (!c) return OCSC_EINVAL;
+  if (n > 0 && (!psnr_host || !(peak > 0))) return fail(c, OCSC_EINVAL, "ocsc_psnr: bad arguments");
+  return objective_terms(c, n, x, H, W, u, nullptr, nullptr, nullptr, psnr_host, peak);
+}
+
+ocsc_status ocsc_filter_order(ocsc_ctx *c, int *order_host) {
+  if (!c) return OCSC_EINVAL;
+  if (!order_host) return fail(c, OCSC_EINVAL, "ocsc_filter_order: null output");
+  c->counters.kernel_launches += 1;
+  cudaError_t e = launch_filter_order(c->K, c->M, c->V, c->order, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(order_host, c->order, (size_t)c->K * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "filter_order");
+}
+
+ocsc_status ocsc_copy_dict(ocsc_ctx *c, float *D_dev) {
+  if (!c) return OCSC_EINVAL;
+  if (!D_dev) return fail(c, OCSC_EINVAL, "ocsc_copy_dict: null output");
+  const size_t bytes = (size_t)c->K * c->M * c->M * sizeof(float);
+  cudaError_t e = cudaMemcpyAsync(D_dev, c->V, bytes, cudaMemcpyDeviceToDevice, c->stream);
+  return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "copy_dict");
+}
+
+ocsc_status ocsc_set_wait_limit(ocsc_ctx *c, uint64_t polls) {
+  if (!c) return OCSC_EINVAL;
+  c->wait_polls = polls > 0xffffffffull ? 0xffffffffu : (unsigned)polls;
+  return OCSC_OK;
 }
 
 ocsc_status ocsc_rel_diff(ocsc_ctx *c, const float *a, const float *b, size_t count, double *out_host) {

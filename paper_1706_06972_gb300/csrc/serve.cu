@@ -395,6 +395,7 @@ static ocsc_status step_body(ocsc_server *s, int *n_active, int *n_queued);
 
 ocsc_status ocsc_server_step(ocsc_server *s, int *n_active, int *n_queued) {
   if (!s) return OCSC_EINVAL;
+  NvtxRange range("ocsc_server_step");
   ocsc_ctx *c = s->ctx;
   // Request work runs on the server's stream for the whole step.
   struct StreamSwap {

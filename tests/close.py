@@ -1,0 +1,60 @@
+"""Element-wise comparison of GPU results with the oracle's (test helpers).
+
+errors() reports, for an array and its reference: the largest element
+difference relative to the largest reference element ("elem"), the
+norm-relative difference ("norm"), the worst per-plane norm-relative
+difference over the leading axes ("plane": a filter, a code plane), and for
+N x N code planes the worst per-frequency-row and per-frequency-column
+norm-relative difference of their spectra ("row", "col": a wrong
+self-conjugate row or column, k = 0 or N/2, shows there).  Per-plane and
+per-row errors are taken relative to the larger of the plane's (row's) own
+norm and the RMS plane (row) norm of the array, so that planes that are
+almost empty in the reference do not turn rounding into large ratios.
+"""
+import numpy as np
+
+ELEM_TOL = 5e-5       # max |a - ref| / max |ref|, FP32 path
+PLANE_TOL = 1e-4      # worst per-filter / per-frequency-row error, FP32 path
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    a = a.astype(np.complex128) if np.iscomplexobj(a) else a.astype(np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _worst(diff, ref):
+    """Worst norm-relative error over the leading axis (planes)."""
+    d = np.sqrt(np.sum(np.abs(diff) ** 2, axis=tuple(range(1, diff.ndim))))
+    r = np.sqrt(np.sum(np.abs(ref) ** 2, axis=tuple(range(1, ref.ndim))))
+    floor = max(float(np.sqrt(np.mean(r ** 2))), 1e-300)
+    return float(np.max(d / np.maximum(r, floor)))
+
+
+def errors(a, ref):
+    """Element, per-plane and (for code planes) per-frequency-row/column errors."""
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    assert a.shape == ref.shape, (a.shape, ref.shape)
+    diff = a - ref
+    e = {"elem": float(np.max(np.abs(diff)) / max(float(np.max(np.abs(ref))), 1e-300)),
+         "norm": rel(a, ref),
+         "plane": _worst(diff.reshape((-1,) + diff.shape[-2:]), ref.reshape((-1,) + ref.shape[-2:]))}
+    if a.ndim == 3 and a.shape[-1] == a.shape[-2] and a.shape[-1] >= 16:
+        A = np.fft.fft2(diff)
+        R = np.fft.fft2(ref)
+        e["row"] = _worst(np.moveaxis(A, 1, 0), np.moveaxis(R, 1, 0))
+        e["col"] = _worst(np.moveaxis(A, 2, 0), np.moveaxis(R, 2, 0))
+    return e
+
+
+def assert_close(a, ref, label, elem=ELEM_TOL, plane=PLANE_TOL):
+    e = errors(a, ref)
+    print(f"{label}: " + " ".join(f"{k} {v:.2e}" for k, v in e.items()))
+    assert e["elem"] < elem, (label, e)
+    assert e["plane"] < plane, (label, e)
+    if "row" in e:
+        assert e["row"] < plane and e["col"] < plane, (label, e)
+    return e
+
+

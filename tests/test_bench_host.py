@@ -94,3 +94,35 @@ def _count_fold_factor_df_flops(K):
 @pytest.mark.parametrize("K", [1, 2, 16, 100])
 def test_fold_factor_df_flop_count(K):
     assert bench.fold_factor_df_flops(K, 1) == pytest.approx(_count_fold_factor_df_flops(K))
+
+
+@pytest.mark.parametrize("K,B", [(1, 1), (16, 1), (100, 64)])
+def test_fold_factor_method_flop_count(K, B):
+    """Sec. III-C's work per frequency: complex Cholesky (sum over columns of
+    the trailing updates, 8 flops per complex MAC: ~4/3 K^3), the inverse of
+    the triangular factor (~4/3 K^3) and the rank-B fold (8 K^2 B)."""
+    chol = sum(8 * (K - j - 1) * (K - j) / 2 for j in range(K))
+    inv = sum(8 * (K - j - 1) * (K - j) / 2 for j in range(K))
+    exact = chol + inv + 8 * K * K * B
+    approx = bench.fold_factor_method_flops(K, 1, B)
+    assert approx == pytest.approx(8.0 / 3.0 * K ** 3 + 8 * K * K * B)
+    if K >= 16:
+        assert abs(approx - exact) / exact < 0.1     # the K^3 terms dominate
+
+
+def test_code_plane_bytes_by_iteration_walk():
+    """Walk the Jz iterations of one coding call and count what each must move."""
+    K, N, B, Jz = 7, 64, 3, 5
+    F, P = N * (N // 2 + 1), N * N
+    total = 0
+    for t in range(Jz):
+        first, last = t == 0, t == Jz - 1
+        per = 0
+        per += 0 if first else F * 8      # W^ read
+        per += 0 if last else F * 8       # W^ written
+        per += 0 if first else P * 4      # Gamma read
+        per += P * 4                      # Gamma written
+        per += F * 8 if last else 0       # Z~ kept for the fold
+        per += P * 4 if last else 0       # U written
+        total += B * K * per + B * F * 8 + K * F * 8
+    assert bench.code_plane_bytes(K, N, B, Jz, True) == total

@@ -1,38 +1,44 @@
 """Parity of the CUDA path with the FP64 oracle on the same seeded inputs.
 
 All GPU work goes through the C ABI (libocsc.so via the ctypes binding).
+Comparisons are element by element (assert_close): the largest element
+difference relative to the largest reference element, the worst per-filter
+(per-plane) norm-relative difference, and for N x N code planes the worst
+per-frequency-row and per-frequency-column norm-relative difference of their
+spectra (a wrong self-conjugate row or column, k = 0 or N/2, shows there).
+Per-plane and per-row errors are taken relative to the larger of the plane's
+(row's) own norm and the array's RMS plane (row) norm, so that planes that
+are almost empty in the reference do not turn rounding into large ratios.
+
 Tolerances come from FP32 arithmetic: FFTs of N x N planes carry a relative
 error of a few eps32 * log2(N^2) (eps32 = 6e-8), and the ADMM iterates
-propagate it through Jz = 50 code iterations and Jd = 10 dictionary
-iterations; the dictionary solve adds the FP32 triangular products with the
-inverse of the Cholesky factor (factored in double-float, FP32 hi + lo pairs
-of ~48 bits; FP64 for K > 128), whose error grows with the condition number of
-A + rho I.
-The bars below are those of the method statement: relative objective 1e-4 on
-the FP32 path, and norm-relative code / dictionary errors 1e-3.
+propagate it through Jz code iterations and Jd dictionary iterations; the
+dictionary solve adds the FP32 triangular products with the inverse of the
+Cholesky factor (factored in double-float, FP32 hi + lo pairs of ~48 bits;
+FP64 for K > 128), whose error grows with the condition number of A + rho I.
+Measured element errors of the FP32 path are ~1e-6 (codes) to ~3e-6
+(dictionary) after a few updates; ELEM_TOL / PLANE_TOL keep a margin of about
+20 over the worst case seen.  The objective bars are those of the method
+statement: relative objective 1e-4 on the FP32 path, 1e-3 on the BF16
+tensor-core history path.
 """
 import numpy as np
 import pytest
 
 import oracle
+from tests.close import ELEM_TOL, PLANE_TOL, _worst, assert_close, errors, rel
 from workloads import WORKLOADS, make_image, raw_filters
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-OBJ_TOL = 1e-4      # relative objective, FP32 path
-REL_TOL = 1e-3      # norm-relative code and dictionary errors
+OBJ_TOL = 1e-4        # relative objective, FP32 path
+OBJ_TOL_BF16 = 1e-3   # relative objective, BF16 tensor-core history path
 
 
 def _need_gpu():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-
-
-def rel(a, b):
-    a = np.asarray(a)
-    a = a.astype(np.complex128) if np.iscomplexobj(a) else a.astype(np.float64)
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def run_gpu(images, raw, K, M, lam, rho, N, Jz, Jd, batch=1, normalize=True, **opts):
@@ -71,6 +77,16 @@ def surrogate_objective(codes, coding_dicts, images, N, lam, batch):
     return float(np.mean(vals))
 
 
+def compare_runs(gpu, orc, label, elem=ELEM_TOL, plane=PLANE_TOL):
+    """Codes and dictionaries of a GPU run against the oracle's, element by
+    element; returns the worst element errors."""
+    codes, dicts = gpu
+    ocodes, odicts = orc[0], orc[1]
+    wc = max(assert_close(codes[t], ocodes[t], f"{label} code {t}", elem, plane)["elem"] for t in range(len(codes)))
+    wd = max(assert_close(dicts[u], odicts[u], f"{label} dict {u}", elem, plane)["elem"] for u in range(len(dicts)))
+    return wc, wd
+
+
 # --- FFT building block ------------------------------------------------------
 
 @pytest.mark.parametrize("N", [64, 96, 128, 144, 192, 256, 288, 384, 512, 576])
@@ -83,9 +99,13 @@ def test_fft_building_block_matches_numpy(N):
     x = rng.standard_normal((3, N, N)).astype(np.float32)   # odd count: unpaired last plane
     X = learner.fft2_r2c(torch.from_numpy(x).cuda()).cpu().numpy()
     ref = np.fft.rfft2(x.astype(np.float64))
-    assert rel(X, ref) < 2e-6
+    err = float(np.max(np.abs(X - ref)) / np.max(np.abs(ref)))
+    assert err < 1e-6 and rel(X, ref) < 2e-6, err
+    # every frequency row and column of the half spectrum separately
+    assert _worst(np.moveaxis(X - ref, 1, 0), np.moveaxis(ref, 1, 0)) < 2e-6
+    assert _worst(np.moveaxis(X - ref, 2, 0), np.moveaxis(ref, 2, 0)) < 2e-6
     back = learner.fft2_c2r(torch.from_numpy(ref.astype(np.complex64)).cuda()).cpu().numpy()
-    assert rel(back, x) < 2e-6
+    assert float(np.max(np.abs(back - x)) / np.max(np.abs(x))) < 1e-6
     learner.close()
 
 
@@ -96,11 +116,10 @@ def test_single_sample_code_and_update():
     w = WORKLOADS["plain_64_k16"]
     imgs = [w.image(0)]
     raw = w.filters0()
-    codes, dicts = run_gpu(imgs, raw, w.K, w.M, w.lam, w.rho, 64, w.Jz, w.Jd, pad=w.pad)
-    ocodes, odicts, _ = run_oracle(imgs, raw, 64, w.lam, w.rho, w.Jz, w.Jd)
-    assert rel(codes[0], ocodes[0]) < REL_TOL
-    assert rel(dicts[0], odicts[0]) < REL_TOL
-    norms = np.sqrt(np.sum(dicts[0].astype(np.float64) ** 2, axis=(1, 2)))
+    gpu = run_gpu(imgs, raw, w.K, w.M, w.lam, w.rho, 64, w.Jz, w.Jd, pad=w.pad)
+    orc = run_oracle(imgs, raw, 64, w.lam, w.rho, w.Jz, w.Jd)
+    compare_runs(gpu, orc, "plain_64_k16 one sample")
+    norms = np.sqrt(np.sum(gpu[1][0].astype(np.float64) ** 2, axis=(1, 2)))
     assert np.all(norms <= 1 + 1e-6)
 
 
@@ -113,12 +132,11 @@ def test_online_pass_plain_64_k16():
     raw = w.filters0()
     codes, dicts = run_gpu(imgs, raw, w.K, w.M, w.lam, w.rho, 64, w.Jz, w.Jd, pad=w.pad)
     ocodes, odicts, ocd = run_oracle(imgs, raw, 64, w.lam, w.rho, w.Jz, w.Jd)
-    for t in range(len(imgs)):
-        assert rel(codes[t], ocodes[t]) < REL_TOL, t
-        assert rel(dicts[t], odicts[t]) < REL_TOL, t
+    compare_runs((codes, dicts), (ocodes, odicts), "plain_64_k16 pass")
     gcd = [oracle.normalize_filters(raw)] + dicts[:-1]
     f_gpu = surrogate_objective(codes, gcd, imgs, 64, w.lam, 1)
     f_orc = surrogate_objective(ocodes, ocd, imgs, 64, w.lam, 1)
+    print(f"plain_64_k16 pass: relative surrogate objective {abs(f_gpu - f_orc) / abs(f_orc):.2e}")
     assert abs(f_gpu - f_orc) / abs(f_orc) < OBJ_TOL
     xs = [oracle.pad_to(np.asarray(x, np.float64), 64, 64) for x in imgs]
     F_gpu = oracle.objective(dicts[-1], codes, xs, w.lam)
@@ -137,13 +155,82 @@ def test_plain_100in128_k100_first_samples():
     raw = w.filters0()
     codes, dicts = run_gpu(imgs, raw, w.K, w.M, w.lam, w.rho, 128, w.Jz, w.Jd, pad=w.pad)
     ocodes, odicts, ocd = run_oracle(imgs, raw, 128, w.lam, w.rho, w.Jz, w.Jd)
-    for t in range(2):
-        assert rel(codes[t], ocodes[t]) < REL_TOL, t
-        assert rel(dicts[t], odicts[t]) < REL_TOL, t
+    compare_runs((codes, dicts), (ocodes, odicts), "plain_100in128_k100")
     gcd = [oracle.normalize_filters(raw)] + dicts[:-1]
     f_gpu = surrogate_objective(codes, gcd, imgs, 128, w.lam, 1)
     f_orc = surrogate_objective(ocodes, ocd, imgs, 128, w.lam, 1)
     assert abs(f_gpu - f_orc) / abs(f_orc) < OBJ_TOL
+
+
+def test_batched_headline_step_matches_oracle():
+    """The bench's headline step shape: K = 100 filters 11 x 11 on 100 x 100
+    images in 128 x 128, mini-batch 4 (the fold is rank 4), Jz = 50, Jd = 10."""
+    _need_gpu()
+    w = WORKLOADS["plain_100in128_k100"]
+    imgs = [w.image(40 + i) for i in range(4)]
+    raw = w.filters0()
+    gpu = run_gpu(imgs, raw, w.K, w.M, w.lam, w.rho, 128, w.Jz, w.Jd, batch=4, pad=w.pad)
+    orc = run_oracle(imgs, raw, 128, w.lam, w.rho, w.Jz, w.Jd, batch=4)
+    compare_runs(gpu, orc, "plain_100in128_k100 B=4")
+
+
+@pytest.mark.parametrize("rho", [0.1, 0.02])
+def test_small_rho_conditioning_stress(rho):
+    """The factorisation of w A + rho I in double-float with X = L^-1 stored in
+    FP32, at a small spatial penalty: A from two samples has rank two, so the
+    matrix has K - 2 eigenvalues equal to rho and two of order |z|^2, a
+    condition number up to ~|z|^2 / rho.  lambda = rho keeps the threshold
+    lambda / rho = 1.  K = 100 filters 11 x 11 on 100 x 100 in 128 x 128."""
+    _need_gpu()
+    w = WORKLOADS["plain_100in128_k100"]
+    imgs = [w.image(60 + i) for i in range(2)]
+    raw = w.filters0()
+    Jz, Jd = 30, 10
+    codes, dicts = run_gpu(imgs, raw, w.K, w.M, rho, rho, 128, Jz, Jd, pad=w.pad)
+    ocodes, odicts, ocd = run_oracle(imgs, raw, 128, rho, rho, Jz, Jd)
+    compare_runs((codes, dicts), (ocodes, odicts), f"small rho {rho}", elem=STRESS_ELEM_TOL,
+                 plane=STRESS_PLANE_TOL)
+    gcd = [oracle.normalize_filters(raw)] + dicts[:-1]
+    f_gpu = surrogate_objective(codes, gcd, imgs, 128, rho, 1)
+    f_orc = surrogate_objective(ocodes, ocd, imgs, 128, rho, 1)
+    print(f"small rho {rho}: relative objective {abs(f_gpu - f_orc) / abs(f_orc):.2e}")
+    assert abs(f_gpu - f_orc) / abs(f_orc) < OBJ_TOL
+
+
+STRESS_ELEM_TOL = 5e-4
+STRESS_PLANE_TOL = 1e-3
+
+
+# --- coding at the N >= 256 sizes with many filter pairs per spectral row --------
+
+@pytest.mark.parametrize("K,N,side,Jz", [(100, 256, 200, 10), (34, 512, 400, 8)])
+def test_large_grid_coding_with_many_stages(K, N, side, Jz):
+    """The spectral row kernels of N >= 256 split the filter pairs into stages
+    (8 pairs per stage at N = 256, 4 at N = 512) whose partial sums the last
+    CTA of a row adds in order: K = 100 at N = 256 has 7 stages (the last with
+    2 pairs), K = 34 at N = 512 has 5 (the last with 1 pair).  Codes of two
+    samples against the same dictionary, element by element."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    M, lam, rho = 11, 1.0, 1.0
+    raw = raw_filters(K, M, 500 + K)
+    imgs = [make_image(side, side, 1800 + N + i) for i in range(2)]
+    lr = pkg.OCSC(K, M, lam, rho, fft_size=N, pad=10, Jz=Jz, Jd=2, max_batch=2)
+    lr.set_dict(raw, normalize=True)
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    us = lr.code(xs)
+    f_gpu = lr.objective(xs, us)
+    lr.drop_pending()
+    lr.close()
+    D = oracle.normalize_filters(np.asarray(raw, np.float64))
+    Dh = oracle.filters_spectrum(D, N, N)
+    for i, im in enumerate(imgs):
+        o = oracle.code_admm(oracle.pad_to(np.asarray(im, np.float64), N, N), Dh, lam, rho, Jz)
+        u = us[i].cpu().numpy()
+        assert_close(u, o.U, f"K={K} N={N} code {i}")
+        fo = oracle.sample_objective(D, o.U, oracle.pad_to(np.asarray(im, np.float64), N, N), lam)
+        assert abs(f_gpu[i] - fo) / abs(fo) < OBJ_TOL
 
 
 # --- edge cases ------------------------------------------------------------------
@@ -166,6 +253,7 @@ def _small_images(n, h, w, seed):
     dict(K=4, M=5, lam=0.5, rho=1.0, Jz=8, Jd=3, n=2, hw=(180, 175), pad=10),     # N = 192 = 2^6 3
     dict(K=3, M=5, lam=0.5, rho=1.0, Jz=6, Jd=3, n=2, hw=(370, 360), pad=10),     # N = 384 = 2^7 3
     dict(K=2, M=3, lam=0.5, rho=1.0, Jz=5, Jd=2, n=2, hw=(560, 500), pad=10),     # N = 576 = 2^6 3^2
+    dict(K=1, M=3, lam=0.5, rho=1.0, Jz=6, Jd=3, n=2, hw=(64, 64), pad=0),        # K = 1: one unpaired plane
 ])
 def test_edge_cases_match_oracle(case):
     _need_gpu()
@@ -173,12 +261,10 @@ def test_edge_cases_match_oracle(case):
     imgs = _small_images(case["n"], h, wd, 77)
     raw = raw_filters(case["K"], case["M"], 5)
     N = next(n for n in (64, 96, 128, 144, 192, 256, 288, 384, 512, 576) if n >= max(h, wd) + case["pad"])
-    codes, dicts = run_gpu(imgs, raw, case["K"], case["M"], case["lam"], case["rho"], N,
-                           case["Jz"], case["Jd"], pad=case["pad"])
-    ocodes, odicts, _ = run_oracle(imgs, raw, N, case["lam"], case["rho"], case["Jz"], case["Jd"])
-    for t in range(case["n"]):
-        assert rel(codes[t], ocodes[t]) < REL_TOL, t
-        assert rel(dicts[t], odicts[t]) < REL_TOL, t
+    gpu = run_gpu(imgs, raw, case["K"], case["M"], case["lam"], case["rho"], N,
+                  case["Jz"], case["Jd"], pad=case["pad"])
+    orc = run_oracle(imgs, raw, N, case["lam"], case["rho"], case["Jz"], case["Jd"])
+    compare_runs(gpu, orc, f"edge K={case['K']} M={case['M']} N={N}")
 
 
 def test_fold_of_more_samples_than_one_chunk_matches_oracle():
@@ -187,53 +273,51 @@ def test_fold_of_more_samples_than_one_chunk_matches_oracle():
     _need_gpu()
     imgs = _small_images(20, 48, 48, 1700)
     raw = raw_filters(12, 5, 1701)
-    codes, dicts = run_gpu(imgs, raw, 12, 5, 0.5, 1.0, 64, 8, 4, batch=20, pad=0)
-    ocodes, odicts, _ = run_oracle(imgs, raw, 64, 0.5, 1.0, 8, 4, batch=20)
-    assert max(rel(codes[t], ocodes[t]) for t in range(20)) < REL_TOL
-    assert rel(dicts[0], odicts[0]) < REL_TOL
+    gpu = run_gpu(imgs, raw, 12, 5, 0.5, 1.0, 64, 8, 4, batch=20, pad=0)
+    orc = run_oracle(imgs, raw, 64, 0.5, 1.0, 8, 4, batch=20)
+    compare_runs(gpu, orc, "fold of 20")
 
 
 @pytest.mark.parametrize("K", [1, 3, 5, 127, 128])
 def test_factor_panel_edges_match_oracle(K):
-    """The per-frequency factorisation works on panels of 4 columns with the
+    """The per-frequency factorisation works on panels of columns with the
     next panel factored ahead: K = 1 (a single pivot), 3 and 5 (ragged last
     panel; trailing triangles smaller than two panels), 127 and 128 (ragged or
     full last panel at the largest in-shared-memory size).  Two updates."""
     _need_gpu()
     imgs = _small_images(2, 56, 56, 700 + K)
     raw = raw_filters(K, 5, 900 + K)
-    codes, dicts = run_gpu(imgs, raw, K, 5, 0.5, 1.0, 64, 8, 4, pad=0)
-    ocodes, odicts, _ = run_oracle(imgs, raw, 64, 0.5, 1.0, 8, 4)
-    for t in range(2):
-        assert rel(codes[t], ocodes[t]) < REL_TOL, t
-        assert rel(dicts[t], odicts[t]) < REL_TOL, t
+    gpu = run_gpu(imgs, raw, K, 5, 0.5, 1.0, 64, 8, 4, pad=0)
+    orc = run_oracle(imgs, raw, 64, 0.5, 1.0, 8, 4)
+    compare_runs(gpu, orc, f"panel edges K={K}")
 
 
 def test_minibatch_fold_matches_oracle():
     _need_gpu()
     imgs = _small_images(6, 64, 64, 200)
     raw = raw_filters(12, 6, 9)
-    codes, dicts = run_gpu(imgs, raw, 12, 6, 0.5, 1.0, 64, 20, 6, batch=3, pad=0)
-    ocodes, odicts, _ = run_oracle(imgs, raw, 64, 0.5, 1.0, 20, 6, batch=3)
-    for t in range(6):
-        assert rel(codes[t], ocodes[t]) < REL_TOL
-    for u in range(2):
-        assert rel(dicts[u], odicts[u]) < REL_TOL
+    gpu = run_gpu(imgs, raw, 12, 6, 0.5, 1.0, 64, 20, 6, batch=3, pad=0)
+    orc = run_oracle(imgs, raw, 64, 0.5, 1.0, 20, 6, batch=3)
+    compare_runs(gpu, orc, "mini-batch 3")
 
 
 @pytest.mark.parametrize("flags,gflags,lam,rho", [
     (dict(warm_start=False), dict(warm_start=0), 0.5, 1.0),
     (dict(rho_convention="paper"), dict(rho_convention=1), 0.005, 0.01),
+    (dict(return_feasible=False), dict(return_feasible=0), 0.5, 1.0),
+    (dict(return_feasible=False, warm_start=False), dict(return_feasible=0, warm_start=0), 0.5, 1.0),
 ])
 def test_reading_flags_match_oracle(flags, gflags, lam, rho):
+    """The literal readings of Algorithm 2: cold start of V and theta at every
+    update (R6), the printed rho P (R2), and the literal return of D~_{t,J}
+    (R7: the codes of the next samples are computed against D~_{t,J} and the
+    published filters are H(F^-1(D~_{t,J})))."""
     _need_gpu()
     imgs = _small_images(3, 64, 64, 300)
     raw = raw_filters(10, 5, 11)
-    codes, dicts = run_gpu(imgs, raw, 10, 5, lam, rho, 64, 15, 5, pad=0, **gflags)
-    ocodes, odicts, _ = run_oracle(imgs, raw, 64, lam, rho, 15, 5, **flags)
-    for t in range(3):
-        assert rel(codes[t], ocodes[t]) < REL_TOL
-        assert rel(dicts[t], odicts[t]) < REL_TOL
+    gpu = run_gpu(imgs, raw, 10, 5, lam, rho, 64, 15, 5, pad=0, **gflags)
+    orc = run_oracle(imgs, raw, 64, lam, rho, 15, 5, **flags)
+    compare_runs(gpu, orc, f"flags {gflags}")
 
 
 def test_deterministic_reruns():
@@ -307,45 +391,46 @@ def test_larger_minibatch_matches_oracle():
     _need_gpu()
     imgs = _small_images(16, 64, 64, 500)
     raw = raw_filters(24, 7, 17)
-    codes, dicts = run_gpu(imgs, raw, 24, 7, 0.5, 1.0, 64, 20, 6, batch=8, pad=0)
-    ocodes, odicts, _ = run_oracle(imgs, raw, 64, 0.5, 1.0, 20, 6, batch=8)
-    for t in range(16):
-        assert rel(codes[t], ocodes[t]) < REL_TOL
-    for u in range(2):
-        assert rel(dicts[u], odicts[u]) < REL_TOL
+    gpu = run_gpu(imgs, raw, 24, 7, 0.5, 1.0, 64, 20, 6, batch=8, pad=0)
+    orc = run_oracle(imgs, raw, 64, 0.5, 1.0, 20, 6, batch=8)
+    compare_runs(gpu, orc, "mini-batch 8")
 
 
 # --- uneven sizes: size classes with the consensus dictionary step --------------
 
-def test_size_classes_match_oracle():
+@pytest.mark.parametrize("warm_start", [1, 0])
+def test_size_classes_match_oracle(warm_start):
     """Images of two padded sizes in one learner (reading R16): per-class
     histories and duals, V-step on the mean of the class crops; one batch
-    leaves the 128 class idle (refactored with its new weight only)."""
+    leaves the 128 class idle (refactored with its new weight only).  With
+    warm_start = 0 every update restarts V and every class's dual at 0."""
     _need_gpu()
     import paper_1706_06972_gb300 as pkg
 
     K, M, lam, rho, Jz, Jd = 10, 7, 0.5, 1.0, 15, 5
     sides = [[50, 100, 50], [100, 100], [50]]
     raw = raw_filters(K, M, 23)
-    learner = pkg.OCSC(K, M, lam, rho, fft_sizes=[64, 128], pad=6, Jz=Jz, Jd=Jd, max_batch=3)
+    learner = pkg.OCSC(K, M, lam, rho, fft_sizes=[64, 128], pad=6, Jz=Jz, Jd=Jd, max_batch=3,
+                       warm_start=warm_start)
     learner.set_dict(raw, normalize=True)
-    st = oracle.init_multi(np.asarray(raw, np.float64), [(64, 64), (128, 128)], lam, rho)
+    st = oracle.init_multi(np.asarray(raw, np.float64), [(64, 64), (128, 128)], lam, rho,
+                           warm_start=bool(warm_start))
     seed = 900
-    for batch in sides:
+    for b, batch in enumerate(sides):
         imgs = [make_image(s, s + 7 if s == 100 else s, seed + i) for i, s in enumerate(batch)]
         seed += 10
         us = learner.code([torch.from_numpy(im).cuda() for im in imgs])
         learner.update_dict()
         D = learner.get_dict()
         res = {}
-        for im, u in zip(imgs, us):
+        for i, (im, u) in enumerate(zip(imgs, us)):
             N = 64 if max(im.shape) + 6 <= 64 else 128
             r = oracle.code_multi(st, im, (N, N), Jz)
             res.setdefault((N, N), []).append(r)
             assert u.shape[-1] == N
-            assert rel(u.cpu().numpy(), r.U) < REL_TOL
+            assert_close(u.cpu().numpy(), r.U, f"classes ws={warm_start} batch {b} code {i} N={N}")
         oracle.update_dict_multi(st, res, Jd)
-        assert rel(D, st.V) < REL_TOL
+        assert_close(D, st.V, f"classes ws={warm_start} dict {b}")
     learner.close()
 
 
@@ -398,8 +483,8 @@ class _StateHeader(__import__("ctypes").Structure):
     _fields_ = [("magic", _c.c_uint32), ("format", _c.c_uint32), ("K", _c.c_int32), ("M", _c.c_int32),
                 ("ncls", _c.c_int32), ("N", _c.c_int32 * 12), ("rho_convention", _c.c_int32),
                 ("return_feasible", _c.c_int32), ("warm_start", _c.c_int32), ("precision", _c.c_int32),
-                ("lam", _c.c_double), ("rho", _c.c_double), ("n_seen", _c.c_int64), ("version", _c.c_uint64),
-                ("class_seen", _c.c_int64 * 12)]
+                ("history", _c.c_int32), ("lam", _c.c_double), ("rho", _c.c_double), ("n_seen", _c.c_int64),
+                ("version", _c.c_uint64), ("class_seen", _c.c_int64 * 12)]
 
 
 def _history_from_state(state, K, M, N, precision):
@@ -422,83 +507,127 @@ def _history_from_state(state, K, M, N, precision):
     return full
 
 
-# History tolerances from the operand rounding: FP32 codes carry ~1e-6 of the
-# coding path's own error; one BF16 word keeps 8 significant bits (unit
-# roundoff 2^-9 = 2e-3 per factor of every product); the split hi + lo keeps
-# 16 (the dropped lo*lo term and the rounding of lo are ~2^-16 = 1.5e-5).
-@pytest.mark.parametrize("precision,a_tol,d_tol", [(0, 1e-5, 1e-3), (1, 1e-2, 2e-2), (2, 6e-5, 1e-3)])
-def test_history_fold_precision_matches_oracle(precision, a_tol, d_tol):
-    """Two rank-8 folds: the FP32 path, BF16 tensor-core products (1 term)
-    and split-BF16 products (3 terms), each with the history checked against
-    the FP64 oracle's A^p entry by entry (lower triangle) and the dictionary
-    and objective after each update."""
-    _need_gpu()
+_ORACLE_CACHE = {}
+
+
+def _precision_oracle(K, M, N, B, lam, rho, Jz, Jd, seed_f, seed_i):
+    """Two rank-B updates of the oracle; the history after each, codes, the
+    dictionary after each update and the dictionary each batch was coded
+    against (cached: the precision variants share it)."""
+    key = (K, M, N, B, lam, rho, Jz, Jd, seed_f, seed_i)
+    if key not in _ORACLE_CACHE:
+        raw = raw_filters(K, M, seed_f)
+        imgs = [make_image(60, 60, seed_i + i) for i in range(2 * B)]
+        st = oracle.init_state(np.asarray(raw, np.float64), N, N, lam, rho)
+        NH = N // 2 + 1
+        k1, k2 = np.divmod(np.arange(N * NH), NH)
+        out = {"raw": raw, "imgs": imgs, "hist": [], "codes": [], "dicts": [], "coding": []}
+        for s in range(0, 2 * B, B):
+            out["coding"].append(oracle.published_filters(st))
+            res = [oracle.code(st, im, Jz) for im in imgs[s:s + B]]
+            oracle.update_dict(st, res, Jd)
+            out["codes"].extend(r.U for r in res)
+            out["dicts"].append(st.V.copy())
+            out["hist"].append(st.hist.A[k1, k2].copy())
+        _ORACLE_CACHE.clear()
+        _ORACLE_CACHE[key] = out
+    return _ORACLE_CACHE[key]
+
+
+# Tolerances of the history fold variants, from the operand rounding: FP32
+# codes carry ~1e-6 of the coding path's own error; one BF16 word keeps 8
+# significant bits (unit roundoff 2^-9 = 2e-3 per factor of every product);
+# the split hi + lo keeps 16 (the dropped lo*lo term and the rounding of lo are
+# ~2^-16 = 1.5e-5).  The BF16 error of the first fold moves the dictionary,
+# which moves the next batch's codes, so later errors compound: the method
+# statement bounds the BF16 path by its relative objective (1e-3).
+PRECISION_TOL = {
+    # precision: (history, element / plane bar of codes and dictionary, objective)
+    0: (1e-5, (ELEM_TOL, PLANE_TOL), OBJ_TOL),
+    1: (1e-2, (1e-1, 2e-1), OBJ_TOL_BF16),
+    2: (6e-5, (1e-3, 2e-3), OBJ_TOL_BF16),
+}
+
+
+def _precision_case(K, precision, M, N, B, Jz, Jd, seed_f, seed_i):
     import paper_1706_06972_gb300 as pkg
 
-    K, M, N, B, lam, rho, Jz, Jd = 24, 5, 64, 8, 0.5, 1.0, 15, 5
-    raw = raw_filters(K, M, 71)
-    imgs = [make_image(60, 60, 1200 + i) for i in range(2 * B)]
+    lam, rho = 0.5, 1.0
+    o = _precision_oracle(K, M, N, B, lam, rho, Jz, Jd, seed_f, seed_i)
+    h_tol, (e_tol, p_tol), f_tol = PRECISION_TOL[precision]
     lr = pkg.OCSC(K, M, lam, rho, fft_size=N, pad=4, Jz=Jz, Jd=Jd, max_batch=B, precision=precision)
-    lr.set_dict(raw, normalize=True)
-    st = oracle.init_state(np.asarray(raw, np.float64), N, N, lam, rho)
-    NH = N // 2 + 1
-    k1, k2 = np.divmod(np.arange(N * NH), NH)
-    codes, coding = [], []
-    for s in range(0, 2 * B, B):
-        coding.append(oracle.published_filters(st))
-        us = lr.code([torch.from_numpy(im).cuda() for im in imgs[s:s + B]])
-        lr.update_dict()
-        D = lr.get_dict()
-        res = [oracle.code(st, im, Jz) for im in imgs[s:s + B]]
-        oracle.update_dict(st, res, Jd)
-        codes.extend(u.cpu().numpy() for u in us)
-        A = _history_from_state(lr.get_state(), K, M, N, precision)
-        Ao = st.hist.A[k1, k2]
-        low = np.tril(np.ones((K, K), bool))
-        a_err = np.linalg.norm((A - Ao)[:, low]) / np.linalg.norm(Ao[:, low])
-        d_err = rel(D, st.V)
-        print(f"precision={precision} update={s // B}: history {a_err:.3e} dictionary {d_err:.3e}")
-        assert a_err < a_tol, (precision, a_err)
-        assert d_err < d_tol
-    fo = surrogate_objective([r.U for r in res], [coding[-1]] * B, imgs[B:], N, lam, B)
-    fg = surrogate_objective(codes[B:], [coding[-1]] * B, imgs[B:], N, lam, B)
-    print(f"precision={precision}: relative objective {abs(fg - fo) / abs(fo):.3e}")
-    assert abs(fg - fo) / abs(fo) < 1e-3
-    lr.close()
-
-
-@pytest.mark.parametrize("K,precision,a_tol,d_tol", [(136, 0, 1e-5, 1e-3), (136, 2, 6e-5, 1e-3),
-                                                     (256, 0, 1e-5, 1e-3), (256, 1, 1e-2, 3e-2)])
-def test_large_K_factor_matches_oracle(K, precision, a_tol, d_tol):
-    """K > 128: blocked FP64 Cholesky through the global workspace, D-step by
-    substitution, FP32 or tensor-core fold (two 128-row blocks).  With one
-    BF16 word per operand the history bound applies to the first fold only:
-    later codes are computed against a dictionary that already differs from
-    the oracle's by the BF16 error, and the difference compounds."""
-    _need_gpu()
-    import paper_1706_06972_gb300 as pkg
-
-    M, N, B, lam, rho, Jz, Jd = 5, 64, 4, 0.5, 1.0, 8, 4
-    raw = raw_filters(K, M, 91)
-    imgs = [make_image(60, 60, 1400 + i) for i in range(2 * B)]
-    lr = pkg.OCSC(K, M, lam, rho, fft_size=N, pad=4, Jz=Jz, Jd=Jd, max_batch=B, precision=precision)
-    lr.set_dict(raw, normalize=True)
-    st = oracle.init_state(np.asarray(raw, np.float64), N, N, lam, rho)
-    NH = N // 2 + 1
-    k1, k2 = np.divmod(np.arange(N * NH), NH)
+    lr.set_dict(o["raw"], normalize=True)
     low = np.tril(np.ones((K, K), bool))
-    for s in range(0, 2 * B, B):
-        lr.code([torch.from_numpy(im).cuda() for im in imgs[s:s + B]], want_codes=False)
+    codes, report = [], []
+    for u, s in enumerate(range(0, 2 * B, B)):
+        us = lr.code([torch.from_numpy(im).cuda() for im in o["imgs"][s:s + B]])
         lr.update_dict()
         D = lr.get_dict()
-        oracle.update_dict(st, [oracle.code(st, im, Jz) for im in imgs[s:s + B]], Jd)
+        codes.extend(x.cpu().numpy() for x in us)
         A = _history_from_state(lr.get_state(), K, M, N, precision)
-        Ao = st.hist.A[k1, k2]
+        Ao = o["hist"][u]
         a_err = np.linalg.norm((A - Ao)[:, low]) / np.linalg.norm(Ao[:, low])
-        d_err = rel(D, st.V)
-        print(f"K={K} precision={precision} update={s // B}: history {a_err:.3e} dictionary {d_err:.3e}")
-        assert a_err < a_tol or (precision == 1 and s > 0)
-        assert d_err < d_tol
+        d = assert_close(D, o["dicts"][u], f"K={K} precision={precision} dictionary {u}", e_tol, p_tol)
+        print(f"K={K} precision={precision} update {u}: history {a_err:.3e}")
+        report.append((a_err, d["norm"]))
+        assert a_err < h_tol or (precision == 1 and u > 0), a_err
+    lr.close()
+    cerr = [assert_close(codes[t], o["codes"][t], f"K={K} precision={precision} code {t}", e_tol, p_tol)["norm"]
+            for t in range(2 * B)]
+    imgs = o["imgs"]
+    fo = surrogate_objective(o["codes"][B:], [o["coding"][1]] * B, imgs[B:], N, lam, B)
+    fg = surrogate_objective(codes[B:], [o["coding"][1]] * B, imgs[B:], N, lam, B)
+    f_err = abs(fg - fo) / abs(fo)
+    print(f"K={K} precision={precision} vs FP64 oracle: relative objective {f_err:.3e}, dictionary "
+          f"{max(r[1] for r in report):.3e}, code {max(cerr):.3e} (norm-relative, worst)")
+    assert f_err < f_tol
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_history_fold_precision_matches_oracle(precision):
+    """Two rank-8 folds at K = 24: the FP32 path, BF16 tensor-core products
+    (1 term) and split-BF16 products (3 terms), each with the history checked
+    against the FP64 oracle's A^p entry by entry (lower triangle), and the
+    dictionary, the codes and the objective against the oracle's."""
+    _need_gpu()
+    _precision_case(24, precision, 5, 64, 8, 15, 5, 71, 1200)
+
+
+@pytest.mark.parametrize("K,precision", [(136, 0), (136, 2), (256, 0), (256, 1), (256, 2)])
+def test_large_K_factor_matches_oracle(K, precision):
+    """K > 128: blocked FP64 Cholesky through the global workspace, D-step by
+    substitution, FP32 or tensor-core fold (two 128-row blocks); K = 256 is the
+    precision workload's filter count.  Relative objective, dictionary error
+    and code error against the FP64 oracle per result."""
+    _need_gpu()
+    _precision_case(K, precision, 5, 64, 4, 8, 4, 91, 1400)
+
+
+def test_tensor_core_fold_timeout_is_reported_and_context_recovers():
+    """The tensor-core fold waits for its MMAs with a bounded poll loop.  With
+    the poll budget at 0 every CTA gives up at once: it records the timeout,
+    drains its own MMAs with the full budget, frees its tensor memory and
+    returns; the next synchronising call reports OCSC_ETIMEOUT.  With the
+    default budget restored the same context folds and factors again."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    K, M, N, B = 24, 5, 64, 4
+    lr = pkg.OCSC(K, M, 0.5, 1.0, fft_size=N, pad=4, Jz=6, Jd=3, max_batch=B, precision=1)
+    lr.set_dict(raw_filters(K, M, 7), normalize=True)
+    xs = [torch.from_numpy(make_image(60, 60, 2100 + i)).cuda() for i in range(2 * B)]
+    lr.code(xs[:B], want_codes=False)
+    lr.set_wait_limit(0)
+    lr.update_dict()
+    with pytest.raises(pkg.OCSCError) as e:
+        lr.sync()
+    assert e.value.status == 4
+    lr.set_wait_limit(1 << 24)
+    lr.sync()                                     # the error word was cleared
+    lr.code(xs[B:], want_codes=False)
+    lr.update_dict()
+    D = lr.get_dict()
+    assert np.all(np.isfinite(D)) and np.all(np.sqrt(np.sum(D.astype(np.float64) ** 2, axis=(1, 2))) <= 1 + 1e-6)
     lr.close()
 
 
@@ -599,8 +728,29 @@ def test_fit_stops_by_the_rule_of_the_paper():
     res = lr.fit(xs, max_passes=40, tol=5e-2, batch=2)
     assert res["stopped"] and res["pass"] >= 1
     assert res["code_change"] < 5e-2 and res["dict_change"] < 5e-2
-    order = pkg.filter_order(lr.get_dict())
-    assert sorted(order.tolist()) == list(range(K))
+    lr.close()
+
+
+def test_filter_order_matches_oracle_on_a_learned_dictionary():
+    """The display order of Sec. IV (ascending filter variance), computed on
+    the device, equals the oracle's on the same learned filters."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    K, M = 24, 7
+    lr = pkg.OCSC(K, M, 0.5, 1.0, fft_size=64, pad=6, Jz=15, Jd=5, max_batch=2)
+    lr.set_dict(raw_filters(K, M, 131), normalize=True)
+    for t in range(3):
+        lr.code([torch.from_numpy(make_image(58, 58, 1750 + 2 * t + i)).cuda() for i in range(2)],
+                want_codes=False)
+        lr.update_dict()
+    D = lr.get_dict()
+    order = lr.filter_order()
+    assert np.array_equal(order, oracle.filter_order(D.astype(np.float64)))
+    # ties keep index order: equal filters
+    same = np.tile(D[:1], (K, 1, 1))
+    lr.set_dict(same, normalize=False)
+    assert np.array_equal(lr.filter_order(), np.arange(K))
     lr.close()
 
 
@@ -612,7 +762,7 @@ def test_fit_stops_by_the_rule_of_the_paper():
 # FP64 recursion loses its accuracy within ten samples.)  C is double-float on the
 # GPU (~48 bits) and FP64 in the oracle; the FP32 codes and b carry the usual
 # coding error.
-RECURSION_DICT_TOL = REL_TOL
+RECURSION_DICT_TOL = 1e-3
 
 @pytest.mark.parametrize("wname,N,nimg,batch", [("plain_64_k16", 64, 20, 1), ("plain_64_k16", 64, 12, 4),
                                                 ("plain_100in128_k100", 128, 2, 1)])
@@ -627,8 +777,10 @@ def test_recursion_history_matches_oracle(wname, N, nimg, batch):
                            rho_convention=1)
     ocodes, odicts, ocd = run_oracle(imgs, raw, N, w.lam, w.rho, w.Jz, w.Jd, batch=batch, history="recursion",
                                      rho_convention="paper")
-    derr = [rel(dicts[t], odicts[t]) for t in range(len(dicts))]
-    cerr = [rel(codes[t], ocodes[t]) for t in range(nimg)]
+    derr = [assert_close(dicts[t], odicts[t], f"recursion {wname} B={batch} dict {t}")["norm"]
+            for t in range(len(dicts))]
+    cerr = [assert_close(codes[t], ocodes[t], f"recursion {wname} B={batch} code {t}")["norm"]
+            for t in range(nimg)]
     gcd = [oracle.normalize_filters(raw)] + dicts[:-1]
     f_gpu = surrogate_objective(codes, gcd, imgs, N, w.lam, batch)
     f_orc = surrogate_objective(ocodes, ocd, imgs, N, w.lam, batch)

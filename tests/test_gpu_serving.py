@@ -10,12 +10,11 @@ import numpy as np
 import pytest
 
 import oracle
+from tests.close import assert_close
 from workloads import make_image, raw_filters
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-REL_TOL = 1e-3
 
 
 def _need_gpu():
@@ -63,6 +62,49 @@ def test_result_same_alone_and_in_mix():
     lr.close()
 
 
+def test_result_same_alone_and_in_mix_while_learning():
+    """learn = 1: dictionary updates run on the context's stream while other
+    requests are in flight.  Every served request, recoded alone by a fresh
+    server (learning off) against the dictionary version it reports, gives the
+    same iterations and the same code bit for bit: the two-version fence keeps
+    a request on the dictionary current at its admission."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    lr, raw = _learner(pkg, K=12, M=5, sizes=(64, 128), max_batch=4)
+    sides = [50, 100, 40, 90, 55, 110, 45, 60, 100, 50, 57, 95]
+    imgs = [torch.from_numpy(make_image(s, s, 300 + i)).cuda() for i, s in enumerate(sides)]
+    srv = pkg.Server(lr, learn=1, update_every=4, tol=1e-3, check_every=5, max_iters=150)
+    versions = {0: lr.get_dict()}
+    pending = list(range(len(imgs)))
+    res = {}
+    for _ in range(2000):
+        for i in pending[:2]:          # two arrivals per round: requests keep
+            srv.submit(i, imgs[i])     # arriving while updates run
+        pending = pending[2:]
+        active, queued = srv.step()
+        for d in srv.poll():
+            res[d["id"]] = d
+        D = lr.get_dict()
+        versions.setdefault(lr.version, D)
+        if not pending and active == 0 and queued == 0:
+            break
+    srv.close()
+    assert len(res) == len(imgs)
+    used = sorted({d["dict_version"] for d in res.values()})
+    assert len(used) >= 2, used        # the stream saw at least one update
+    for i, d in res.items():
+        alone_ctx, _ = _learner(pkg, K=12, M=5, sizes=(64, 128), max_batch=4)
+        alone_ctx.set_dict(versions[d["dict_version"]], normalize=False)
+        one = pkg.Server(alone_ctx, learn=0, tol=1e-3, check_every=5, max_iters=150)
+        a = _serve_all(one, [(i, imgs[i])])[i]
+        one.close()
+        alone_ctx.close()
+        assert a["iters"] == d["iters"], (i, a["iters"], d["iters"])
+        assert torch.equal(a["code"], d["code"]), i
+    lr.close()
+
+
 @pytest.mark.parametrize("sizes,sides", [((64, 128), (50, 100, 57)), ((96, 144), (80, 130, 85))])
 def test_served_codes_match_oracle_at_reported_iterations(sizes, sides):
     _need_gpu()
@@ -81,8 +123,7 @@ def test_served_codes_match_oracle_at_reported_iterations(sizes, sides):
         N = sizes[0] if max(im.shape) + 7 <= sizes[0] else sizes[1]
         o = oracle.code_admm(oracle.pad_to(np.asarray(im, np.float64), N, N),
                              oracle.filters_spectrum(D, N, N), 0.5, 1.0, d["iters"])
-        u = d["code"].cpu().numpy().astype(np.float64)
-        assert np.linalg.norm(u - o.U) / np.linalg.norm(o.U) < REL_TOL
+        assert_close(d["code"].cpu().numpy(), o.U, f"served request {i} ({d['iters']} iterations)")
     lr.close()
 
 
@@ -103,7 +144,7 @@ def test_learning_through_the_server_matches_oracle():
     st = oracle.init_state(np.asarray(raw, np.float64), 64, 64, 0.5, 1.0)
     results = [oracle.code(st, imgs[d["id"]], d["iters"]) for d in order]
     oracle.update_dict(st, results, 6)
-    assert np.linalg.norm(D - st.V) / np.linalg.norm(st.V) < REL_TOL
+    assert_close(D, st.V, "dictionary learned through the server")
     lr.close()
 
 

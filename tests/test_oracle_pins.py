@@ -557,3 +557,98 @@ def test_recursion_mode_update_equals_factorised_admm_at_rho_over_t():
         V, th, _ = oracle.dict_ocsc(h, V, th, rho / h.n, Jd, rho_convention="paper")
         assert np.max(np.abs(st.V - V)) < 1e-10
         assert np.max(np.abs(st.thetah - th)) < 1e-10 * max(1.0, np.abs(th).max())
+
+
+# --- the literal branches of Algorithm 2 (readings R6, R7) --------------------------
+
+class _Coded:
+    """A coded sample as update_dict takes it (spectra of given spatial codes)."""
+
+    def __init__(self, Z, x):
+        self.Zh = oracle.fft2(Z)
+        self.xh = oracle.fft2(x)
+
+
+def _project_rows(a, K, M):
+    """alpha_k / max(||alpha_k||, 1) on a flat [K * M * M] vector."""
+    out = a.copy()
+    for k in range(K):
+        seg = out[k * M * M:(k + 1) * M * M]
+        out[k * M * M:(k + 1) * M * M] = seg / max(np.linalg.norm(seg), 1.0)
+    return out
+
+
+def _crop_flat(d, K, n, M):
+    return d.reshape(K, n, n)[:, :M, :M].reshape(-1)
+
+
+@pytest.mark.parametrize("rho", [1.0, 0.3])
+def test_literal_return_publishes_the_last_dstep(rho):
+    """return_feasible=False: Algorithm 2 returns D~_{t,J} and Algorithm 3
+    publishes H(F^-1(D~_t)).  From a cold start (warm_start=False) with J = 2
+    the D-steps are, by dense spatial solves over full-size filters,
+      d1 = (G + rho I)^-1 r,          V1 = Prop. 2 of H(d1),  theta1 = d1 - pad(V1),
+      d2 = (G + rho I)^-1 (r + rho (pad(V1) - theta1)),
+    so the published filters are H(d2) and the coding spectrum is F(d2)."""
+    rng = np.random.default_rng(31)
+    K, n, M, t = 2, 6, 3, 3
+    Zsp = [rng.standard_normal((K, n, n)) * (rng.random((K, n, n)) < 0.6) for _ in range(t)]
+    xs = [rng.standard_normal((n, n)) * 2 for _ in range(t)]
+    st = oracle.init_state(rng.standard_normal((K, M, M)), n, n, 0.1, rho, warm_start=False,
+                           return_feasible=False)
+    # a first update so that the cold start has something to discard
+    oracle.update_dict(st, [_Coded(Zsp[0], xs[0])], 3)
+    oracle.update_dict(st, [_Coded(Z, x) for Z, x in zip(Zsp[1:], xs[1:])], 2)
+    G, r = _dense_dict_system(Zsp, xs, n)          # running mean over all t samples
+    A = G + rho * np.eye(K * n * n)
+    d1 = np.linalg.solve(A, r)
+    v1 = np.zeros(K * n * n)
+    v1.reshape(K, n, n)[:, :M, :M] = _project_rows(_crop_flat(d1, K, n, M), K, M).reshape(K, M, M)
+    th1 = d1 - v1
+    d2 = np.linalg.solve(A, r + rho * (v1 - th1))
+    np.testing.assert_allclose(oracle.published_filters(st).reshape(-1), _crop_flat(d2, K, n, M), atol=1e-10)
+    np.testing.assert_allclose(st.Dh, oracle.fft2(d2.reshape(K, n, n)), atol=1e-9)
+    # the feasible V of the same update is Prop. 2 of H(d2 + theta1)
+    np.testing.assert_allclose(st.V.reshape(-1), _project_rows(_crop_flat(d2 + th1, K, n, M), K, M), atol=1e-10)
+
+
+def test_literal_return_tends_to_the_feasible_filters():
+    """At the ADMM fixed point D~ = F(pad V): after many iterations the literal
+    return and the feasible V coincide."""
+    rng = np.random.default_rng(32)
+    K, n, M = 2, 6, 2
+    samples = [_Coded(rng.standard_normal((K, n, n)) * (rng.random((K, n, n)) < 0.5),
+                      rng.standard_normal((n, n)) * 2) for _ in range(3)]
+    st = oracle.init_state(rng.standard_normal((K, M, M)), n, n, 0.1, 1.0, return_feasible=False)
+    oracle.update_dict(st, samples, 3000)
+    np.testing.assert_allclose(oracle.published_filters(st), st.V, atol=1e-7)
+    assert np.max(np.abs(oracle.ifft2(st.Dh).real[:, M:, :])) < 1e-7
+
+
+def test_cold_start_of_the_multi_class_step_discards_the_previous_state():
+    """warm_start=False with size classes (readings R6, R16): with J = 1 every
+    class solves from V = 0, theta = 0, so the update gives Prop. 2 of the mean
+    over classes of H(d_c), d_c = (w_c G_c + rho I)^-1 w_c r_c by dense spatial
+    solves, whatever V and theta the earlier update left."""
+    rng = np.random.default_rng(33)
+    K, M, rho = 2, 2, 0.7
+    sizes = [(5, 5), (6, 6)]
+    st = oracle.init_multi(rng.standard_normal((K, M, M)), sizes, 0.1, rho, warm_start=False)
+    data = {s: [] for s in sizes}
+    first = {s: [] for s in sizes}
+    for s, cnt in zip(sizes, (2, 1)):
+        for j in range(cnt):
+            Z = rng.standard_normal((K,) + s) * (rng.random((K,) + s) < 0.6)
+            x = rng.standard_normal(s) * 2
+            (first if j == 0 else data)[s].append((Z, x))
+    oracle.update_dict_multi(st, {s: [_Coded(Z, x) for Z, x in first[s]] for s in sizes}, 4)
+    oracle.update_dict_multi(st, {s: [_Coded(Z, x) for Z, x in data[s]] for s in sizes}, 1)
+    n_tot = sum(len(first[s]) + len(data[s]) for s in sizes)
+    alpha = np.zeros(K * M * M)
+    for s in sizes:
+        pairs = first[s] + data[s]
+        G, r = _dense_dict_system([Z for Z, _ in pairs], [x for _, x in pairs], s[0])
+        w = len(pairs) / n_tot
+        d = np.linalg.solve(w * G + rho * np.eye(G.shape[0]), w * r)
+        alpha += _crop_flat(d, K, s[0], M) / len(sizes)
+    np.testing.assert_allclose(st.V.reshape(-1), _project_rows(alpha, K, M), atol=1e-10)
