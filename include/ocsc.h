@@ -101,8 +101,9 @@ typedef struct {
                          candidate tile shapes on its own buffers and keep the
                          fastest: threads per CTA of the factorisation
                          (256 or 512), columns per CTA of the N >= 256 spatial
-                         FFT kernel in ocsc_code (8 or 16), samples per chunk
-                         of the tensor-core contraction (32, 64, 128).  Every
+                         FFT kernel in ocsc_code (8 or 16), CTAs per SM of the
+                         N <= 128 coding plane kernel (2 or 3), samples per
+                         chunk of the tensor-core contraction (32, 64, 128).  Every
                          candidate performs the same operations in the same
                          order, so results do not depend on the choice.
                          0: fixed defaults (256, the size's default, largest
@@ -163,7 +164,8 @@ ocsc_status ocsc_padded_size(const ocsc_ctx *ctx, int H, int W, int *N);
  * Code n samples against the current dictionary (Algorithm 3, FFT and code
  * steps).  x[i] is a DEVICE pointer to an H[i] x W[i] float image; u[i] is a
  * DEVICE pointer to a caller-owned K x N x N float buffer that receives the
- * sparse code U_i after the last U-step, or NULL to skip writing it.  x, H, W
+ * sparse code U_i after the last U-step, or NULL to skip writing it (8-byte
+ * aligned, as cudaMalloc and torch allocations are; OCSC_EINVAL otherwise).  x, H, W
  * and u are HOST arrays of length n.  Every image must map to one of the
  * context's FFT sizes; images of different sizes may be mixed in one call.
  * The last Z~-step of each sample and its spectrum stay pending inside the
@@ -219,6 +221,8 @@ typedef struct {
   int fold_threads; /* CTA size of the K <= 128 fold + factorisation */
   int spat_cb;      /* columns per CTA of the N >= 256 spatial kernel in ocsc_code */
   int gram_sc;      /* samples per chunk of the tensor-core contraction */
+  int plane_ctas;   /* CTAs per SM the N <= 128 coding plane kernel's register
+                       budget is sized for (2 or 3) */
 } ocsc_tuning;
 ocsc_status ocsc_get_tuning(const ocsc_ctx *ctx, int N, ocsc_tuning *out);
 
@@ -352,7 +356,7 @@ ocsc_status ocsc_server_create(ocsc_server **out, ocsc_ctx *ctx, const ocsc_serv
 void ocsc_server_destroy(ocsc_server *s);
 
 /* Queue one request: x (DEVICE, H x W floats) is coded into u (DEVICE,
- * K x N x N floats, N its padded size).  Both stay owned by the caller and must
+ * K x N x N floats, N its padded size, 8-byte aligned).  Both stay owned by the caller and must
  * remain valid until the request is reported by ocsc_server_poll. */
 ocsc_status ocsc_server_submit(ocsc_server *s, uint64_t id, const float *x, int H, int W, float *u);
 
@@ -435,7 +439,7 @@ ocsc_status ocsc_fft2_c2r(ocsc_ctx *ctx, int N, const float *X, float *x, int pl
  * axes to N x N, N in {64, 128}, H, W <= N) against the K filters D (DEVICE,
  * K x M x M floats, M <= 16, used as given) with Jz code-ADMM iterations of
  * ocsc_code's kernels, and writes the sparse code U (DEVICE, K x N x N floats,
- * caller-owned) -- the same result ocsc_code gives for that image and
+ * 8-byte aligned, caller-owned) -- the same result ocsc_code gives for that image and
  * dictionary.  Work is enqueued on cuda_stream (a cudaStream_t; NULL = legacy
  * default stream); the call is asynchronous.  err (nullable, err_len bytes)
  * receives a message on failure.

@@ -43,7 +43,8 @@ class ocsc_opts(ctypes.Structure):
 
 
 class ocsc_tuning(ctypes.Structure):
-    _fields_ = [("fold_threads", ctypes.c_int), ("spat_cb", ctypes.c_int), ("gram_sc", ctypes.c_int)]
+    _fields_ = [("fold_threads", ctypes.c_int), ("spat_cb", ctypes.c_int), ("gram_sc", ctypes.c_int),
+                ("plane_ctas", ctypes.c_int)]
 
 
 class ocsc_counters(ctypes.Structure):
@@ -209,7 +210,8 @@ def ocsc_get_state(ctx) -> bytes:
 def ocsc_get_tuning(ctx, N: int) -> dict:
     t = ocsc_tuning()
     _check(ctx, lib().ocsc_get_tuning(ctx, N, ctypes.byref(t)))
-    return {"fold_threads": t.fold_threads, "spat_cb": t.spat_cb, "gram_sc": t.gram_sc}
+    return {"fold_threads": t.fold_threads, "spat_cb": t.spat_cb, "gram_sc": t.gram_sc,
+            "plane_ctas": t.plane_ctas}
 
 
 def ocsc_set_state(ctx, state: bytes) -> None:

@@ -13,12 +13,12 @@
 // only coupling across frequencies is the FFT of each filter plane.  So each
 // iteration is two kernels:
 //   code_resid  -- r_p for every (sample, p): reduce d_k w^_k over k;
-//   code_plane  -- one CTA per (sample, pair of filters): build z for both
-//                  filters, pack them as one complex plane z_a + i z_b, inverse
-//                  2D FFT in shared memory, shrink + dual update in registers,
-//                  forward FFT of W = U - Gamma, split back into the two half
-//                  spectra.  Gamma is the only spatial array that goes to
-//                  global memory.
+//   code_plane  -- one CTA per (sample, filter): build z on the half
+//                  spectrum in shared memory, real inverse 2D FFT (column
+//                  transforms, then half-length transforms of the packed
+//                  rows), shrink + dual update on pairs of pixels, forward
+//                  real 2D FFT of W = U - Gamma back to the half spectrum.
+//                  Gamma is the only spatial array that goes to global memory.
 #include "fft.cuh"
 #include "launch.h"
 
@@ -110,19 +110,36 @@ __device__ __forceinline__ void block_sum_terms(float (&v)[kResidTerms], float *
   }
 }
 
-// One fused ADMM iteration for filters (a, a+1) of one sample.
-template <int N>
-__global__ void __launch_bounds__(TileThreads<N>::value)
+// One fused ADMM iteration for filter k of one sample, on its half spectrum.
+//
+// The tile holds the N x (N/2 + 1) half spectrum exactly as it lies in global
+// memory (pitch N/2 + 1), 67.5 KB at N = 128, so two or three CTAs share an SM
+// and one CTA's loads and stores overlap another's transforms.  The real 2D
+// inverse runs as N/2 column transforms of length N (the columns k2 = 0 and
+// k2 = N/2 are Hermitian in k1, so their inverses are real and travel packed
+// as one complex column c0 + i cN/2), then per row the half-length complex
+// inverse of the packed row: for a real row x with half spectrum X[0..N/2],
+// h[m] = x[2m] + i x[2m+1] has the N/2-point spectrum
+//   H[k] = (X[k] + conj X[N/2-k]) + i W_N^-k (X[k] - conj X[N/2-k])
+// (times 2 against the 1/N-normalised split, which keeps the scale of an
+// unnormalised length-N inverse).  The forward transform reverses the steps:
+// half-length row transforms of h, the split
+//   X[k] = (H[k] + conj H[N/2-k]) / 2 + W_N^k (H[k] - conj H[N/2-k]) / (2i),
+// X[0] and X[N/2] real (packed as one complex column), N/2 column transforms.
+//
+// MINB is the number of CTAs per SM the register budget is sized for (2: no
+// spills; 3: a few spilled registers, more overlap); both perform the same
+// operations in the same order.
+template <int N, int MINB>
+__global__ void __launch_bounds__(HalfPlan<N>::NT, MINB)
     code_plane_kernel(CodeIter it, ImgBatch b, const float2 *__restrict__ tw) {
-  constexpr int NT = TileThreads<N>::value, PITCH = tile_pitch<N>(), NH = N / 2 + 1;
+  constexpr int NT = HalfPlan<N>::NT, NH = N / 2 + 1, H = N / 2, Q = H / 2 + 1;
   constexpr int F = N * NH, P = N * N;
   extern __shared__ float2 smem[];
-  float2 *tile = smem;
-  float2 *s_tw = smem + N * PITCH;
+  float2 *tile = smem;      // [N][NH]
+  float2 *s_tw = smem + F;  // [N]
   const int K = it.K;
-  const int ka = 2 * blockIdx.x;
-  const int kb = ka + 1;
-  const bool hasb = kb < K;
+  const int k = blockIdx.x;
   const int img = blockIdx.y;
   const int slot = b.slot[img];
   const int t = b.iter[img];
@@ -132,85 +149,132 @@ __global__ void __launch_bounds__(TileThreads<N>::value)
   const bool skip_fwd = !it.serve && it.last;
   load_twiddles<N, NT>(s_tw, tw);
 
-  const float2 *Da = it.Dh + (size_t)ka * F;
-  const float2 *Db = it.Dh + (size_t)(hasb ? kb : ka) * F;
+  const float2 *Dk = it.Dh + (size_t)k * F;
   const float2 *rr = it.r + (size_t)slot * F;
-  float2 *Wa = it.What + ((size_t)slot * K + ka) * F;
-  float2 *Wb = it.What + ((size_t)slot * K + (hasb ? kb : ka)) * F;
-  float2 *Za = it.Zp + ((size_t)slot * K + ka) * F;
-  float2 *Zb = it.Zp + ((size_t)slot * K + (hasb ? kb : ka)) * F;
+  float2 *Wk = it.What + ((size_t)slot * K + k) * F;
+  float2 *Zk = it.Zp + ((size_t)slot * K + k) * F;
 
-  // Z~-step for both filters; pack z_a + i z_b over the full spectrum.
+  // 1. Z~-step z = w^ + conj(d) r_p over the half spectrum; the thread of
+  //    column 0 also takes column N/2 of its row and packs the two.
   for (int p = threadIdx.x; p < F; p += NT) {
-    const int k1 = p / NH, k2 = p % NH;
-    const float2 rp = rr[p];
-    float2 za = cconjmul(Da[p], rp);
-    float2 zb = hasb ? cconjmul(Db[p], rp) : make_float2(0.f, 0.f);
-    if (!first) {
-      za = cadd(za, Wa[p]);
-      if (hasb) zb = cadd(zb, Wb[p]);
+    const int k1 = p / NH, k2 = p - k1 * NH;
+    if (k2 == H) continue;
+    float2 z = cconjmul(Dk[p], rr[p]);
+    if (!first) z = cadd(z, Wk[p]);
+    if (store_last) Zk[p] = z;
+    if (k2 == 0) {
+      const int ph = p + H;
+      float2 zh = cconjmul(Dk[ph], rr[ph]);
+      if (!first) zh = cadd(zh, Wk[ph]);
+      if (store_last) Zk[ph] = zh;
+      z = make_float2(z.x - zh.y, z.y + zh.x);  // z0 + i zN/2
     }
-    if (store_last) {
-      Za[p] = za;
-      if (hasb) Zb[p] = zb;
-    }
-    tile[k1 * PITCH + k2] = make_float2(za.x - zb.y, za.y + zb.x);
-    if (k2 > 0 && k2 < N / 2) {
-      const int m1 = (N - k1) & (N - 1);
-      tile[m1 * PITCH + (N - k2)] = make_float2(za.x + zb.y, zb.x - za.y);
+    tile[p] = z;
+  }
+  __syncthreads();
+
+  // 2. Inverse transforms along k1 (length N) of the N/2 columns.
+  half_cols<N, true>(tile, s_tw);
+
+  // 3. Per row, the half-length spectrum of the packed real row.
+  for (int q = threadIdx.x; q < N * Q; q += NT) {
+    const int n1 = q / Q, kk = q - n1 * Q;
+    float2 *row = tile + n1 * NH;
+    if (kk == 0) {
+      const float2 c = row[0];  // (X[0], X[N/2]), both real
+      row[0] = make_float2(c.x + c.y, c.x - c.y);
+    } else {
+      const int kq = H - kk;
+      const float2 a = row[kk], c = row[kq];
+      const float2 wa = make_float2(s_tw[kk].x, -s_tw[kk].y);  // W_N^-k
+      const float2 wc = make_float2(s_tw[kq].x, -s_tw[kq].y);
+      // H[k] = (a + conj c) + i W^-k (a - conj c)
+      const float2 da = cmul(wa, make_float2(a.x - c.x, a.y + c.y));
+      row[kk] = make_float2(a.x + c.x - da.y, a.y - c.y + da.x);
+      if (kq != kk) {
+        const float2 dc = cmul(wc, make_float2(c.x - a.x, c.y + a.y));
+        row[kq] = make_float2(c.x + a.x - dc.y, c.y - a.y + dc.x);
+      }
     }
   }
   __syncthreads();
-  fft2d_tile<N, NT, true>(tile, s_tw);
 
-  // Spatial step: U = S(Z + Gamma), Gamma += Z - U, W = U - Gamma.
+  // 4. Inverse transforms of the packed rows (length N/2): P (z[2m] + i z[2m+1]).
+  half_rows<N, true>(tile, s_tw);
+
+  // 5. Spatial step on pairs of pixels (2m, 2m+1) of row n1:
+  //    U = S(Z + Gamma), Gamma += Z - U, W = U - Gamma.
   const float invP = 1.0f / (float)P;
-  float *Ga = it.Gam + ((size_t)slot * K + ka) * P;
-  float *Gb = it.Gam + ((size_t)slot * K + (hasb ? kb : ka)) * P;
-  float *Ua = b.u[img] ? b.u[img] + (size_t)ka * P : nullptr;
-  float *Ub = (b.u[img] && hasb) ? b.u[img] + (size_t)kb * P : nullptr;
+  float *Gk = it.Gam + ((size_t)slot * K + k) * P;
+  float *Uk = b.u[img] ? b.u[img] + (size_t)k * P : nullptr;
   const bool resid = it.serve && store_last;
   float acc[kResidTerms] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int q = threadIdx.x; q < P; q += NT) {
-    const int q1 = q / N, q2 = q % N;
-    const float2 c = tile[q1 * PITCH + q2];
-    const float ga = first ? 0.f : Ga[q];
-    const float gb = (first || !hasb) ? 0.f : Gb[q];
+  for (int q = threadIdx.x; q < N * H; q += NT) {
+    const int n1 = q / H, m = q - n1 * H;
+    const float2 c = tile[n1 * NH + m];
+    const int o = n1 * N + 2 * m;
+    const float2 g = first ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2 *>(Gk + o);
     const float za = c.x * invP, zb = c.y * invP;
-    const float va = za + ga;
-    const float vb = zb + gb;
-    const float ua = soft_threshold(va, it.thr);
-    const float ub = soft_threshold(vb, it.thr);
-    const float ga2 = va - ua, gb2 = vb - ub;
+    const float va = za + g.x, vb = zb + g.y;
+    const float ua = soft_threshold(va, it.thr), ub = soft_threshold(vb, it.thr);
+    const float ga = va - ua, gb = vb - ub;
     if (resid) {
-      const float pa = (first || !Ua) ? 0.f : Ua[q];
-      const float pb = (first || !Ub) ? 0.f : Ub[q];
-      acc[0] += (za - ua) * (za - ua) + (hasb ? (zb - ub) * (zb - ub) : 0.f);
-      acc[1] += za * za + (hasb ? zb * zb : 0.f);
-      acc[2] += ua * ua + (hasb ? ub * ub : 0.f);
-      acc[3] += (ua - pa) * (ua - pa) + (hasb ? (ub - pb) * (ub - pb) : 0.f);
-      acc[4] += ga2 * ga2 + (hasb ? gb2 * gb2 : 0.f);
+      const float2 pu = (first || !Uk) ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2 *>(Uk + o);
+      acc[0] += (za - ua) * (za - ua) + (zb - ub) * (zb - ub);
+      acc[1] += za * za + zb * zb;
+      acc[2] += ua * ua + ub * ub;
+      acc[3] += (ua - pu.x) * (ua - pu.x) + (ub - pu.y) * (ub - pu.y);
+      acc[4] += ga * ga + gb * gb;
     }
-    Ga[q] = ga2;
-    if (hasb) Gb[q] = gb2;
-    if (store_last || store_prev) {
-      if (Ua) Ua[q] = ua;
-      if (Ub) Ub[q] = ub;
-    }
-    if (!skip_fwd) tile[q1 * PITCH + q2] = make_float2(ua - ga2, hasb ? ub - gb2 : 0.f);
+    *reinterpret_cast<float2 *>(Gk + o) = make_float2(ga, gb);
+    if ((store_last || store_prev) && Uk) *reinterpret_cast<float2 *>(Uk + o) = make_float2(ua, ub);
+    if (!skip_fwd) tile[n1 * NH + m] = make_float2(ua - ga, ub - gb);
   }
   if (resid) block_sum_terms(acc, it.resid + ((size_t)slot * gridDim.x + blockIdx.x) * kResidTerms);
   if (skip_fwd) return;
   __syncthreads();
-  fft2d_tile<N, NT, false>(tile, s_tw);
 
-  // Split the packed spectrum into the two half spectra W^_a, W^_b.
+  // 6. Forward transforms of the packed rows h[m] = w[2m] + i w[2m+1].
+  half_rows<N, false>(tile, s_tw);
+
+  // 7. Split each row's H into the half spectrum X[0..N/2] of its real row;
+  //    X[0] and X[N/2] are real and stay packed in element 0.
+  for (int q = threadIdx.x; q < N * Q; q += NT) {
+    const int n1 = q / Q, kk = q - n1 * Q;
+    float2 *row = tile + n1 * NH;
+    if (kk == 0) {
+      const float2 h = row[0];
+      row[0] = make_float2(h.x + h.y, h.x - h.y);  // (X[0], X[N/2])
+    } else {
+      const int kq = H - kk;
+      const float2 a = row[kk], c = row[kq];
+      // X[k] = (a + conj c) / 2 + W^k (a - conj c) / (2i)
+      const float2 ea = cmul(s_tw[kk], make_float2(a.y + c.y, c.x - a.x));  // W^k (a - conj c) / i
+      row[kk] = make_float2(0.5f * (a.x + c.x + ea.x), 0.5f * (a.y - c.y + ea.y));
+      if (kq != kk) {
+        const float2 ec = cmul(s_tw[kq], make_float2(c.y + a.y, a.x - c.x));
+        row[kq] = make_float2(0.5f * (c.x + a.x + ec.x), 0.5f * (c.y - a.y + ec.y));
+      }
+    }
+  }
+  __syncthreads();
+
+  // 8. Forward transforms along n1 of the N/2 columns.
+  half_cols<N, false>(tile, s_tw);
+
+  // 9. W^ to global memory; columns 0 and N/2 unpacked from element 0:
+  //    C = X0^ + i XN/2^ with both columns Hermitian in k1.
   for (int p = threadIdx.x; p < F; p += NT) {
-    const int k1 = p / NH, k2 = p % NH;
-    const float2 c = tile[k1 * PITCH + k2];
-    const float2 cm = tile[((N - k1) & (N - 1)) * PITCH + ((N - k2) & (N - 1))];
-    Wa[p] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
-    if (hasb) Wb[p] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+    const int k1 = p / NH, k2 = p - k1 * NH;
+    float2 v;
+    if (k2 == 0 || k2 == H) {
+      const float2 c = tile[k1 * NH], cm = tile[((N - k1) & (N - 1)) * NH];
+      v = k2 == 0 ? make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y))
+                  : make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+    } else {
+      v = tile[p];
+    }
+    Wk[p] = v;
   }
 }
 
@@ -325,23 +389,26 @@ cudaError_t launch_code_resid(int N, const ImgBatch &b, const CodeIter &it, floa
   return cudaGetLastError();
 }
 
-template <int N>
+template <int N, int MINB>
 static cudaError_t code_plane_n(const CodeIter &it, const ImgBatch &b, const float2 *tw,
                                 cudaStream_t s) {
-  const size_t sm = tile_smem_bytes<N>();
-  cudaError_t e = set_smem(code_plane_kernel<N>, sm);
+  const size_t sm = half_smem_bytes<N>();
+  cudaError_t e = set_smem(code_plane_kernel<N, MINB>, sm);
   if (e != cudaSuccess) return e;
-  dim3 grid((it.K + 1) / 2, b.n);
-  code_plane_kernel<N><<<grid, TileThreads<N>::value, sm, s>>>(it, b, tw);
+  dim3 grid(it.K, b.n);
+  code_plane_kernel<N, MINB><<<grid, HalfPlan<N>::NT, sm, s>>>(it, b, tw);
   return cudaGetLastError();
 }
 
+int plane_resid_groups(int K) { return K; }
+
 cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, const float2 *tw,
-                              cudaStream_t s) {
+                              cudaStream_t s, int ctas) {
   if (b.n <= 0) return cudaSuccess;
+  const bool three = ctas == 3;
   switch (N) {
-    case 64: return code_plane_n<64>(it, b, tw, s);
-    case 128: return code_plane_n<128>(it, b, tw, s);
+    case 64: return three ? code_plane_n<64, 3>(it, b, tw, s) : code_plane_n<64, 2>(it, b, tw, s);
+    case 128: return three ? code_plane_n<128, 3>(it, b, tw, s) : code_plane_n<128, 2>(it, b, tw, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -264,6 +264,88 @@ __device__ __forceinline__ void fft_lines(float2 *buf, int ls, int es, const flo
   if constexpr (P::NP == 3) line_pass<N, NL, P::R2, P::R0 * P::R1, INV, NT>(buf, ls, es, tw);
 }
 
+// ---------------------------------------------------------------------------
+// Half-spectrum tile of one real N x N plane: N rows of NH = N/2 + 1 complex
+// elements at pitch NH (element (k1, k2) at k1 * NH + k2 -- the global layout
+// of a half spectrum).  Columns are transformed with length N, rows (the
+// packed real row of the r2c / c2r step) with length N/2.  A pitch of NH
+// (= 1 mod 16 for N = 64, 128) keeps 64-bit accesses conflict-free both when
+// consecutive threads take consecutive columns of one row and when they take
+// consecutive rows of one column.
+// ---------------------------------------------------------------------------
+
+// One Stockham radix-R pass of length LEN over LINES lines: element m of line
+// l at buf[l * LS + m * ES]; twiddles W_LEN^x = tw[x * TWS] from the table of
+// size LEN * TWS.  Consecutive threads take consecutive lines of the same
+// butterfly index.  Every group is held in registers across the barrier
+// between the reads and the in-place writes.
+template <int LEN, int LINES, int R, int NS, bool INV, int LS, int ES, int NT, int TWS>
+__device__ __forceinline__ void half_pass(float2 *__restrict__ buf, const float2 *__restrict__ tw) {
+  constexpr int G = LINES * (LEN / R);
+  static_assert(G % NT == 0, "threads must divide the butterfly groups");
+  constexpr int PER = G / NT;
+  float2 v[PER][R];
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int gi = 0; gi < PER; ++gi) {
+    const int g = tid + gi * NT;
+    const int line = g % LINES;
+    const int j = g / LINES;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[gi][r] = buf[line * LS + (j + r * (LEN / R)) * ES];
+    if constexpr (NS > 1) {
+      const int jm = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = tw[((r * jm * (LEN / (NS * R))) % LEN) * TWS];
+        if (INV) w.y = -w.y;
+        v[gi][r] = cmul(v[gi][r], w);
+      }
+    }
+    RegDFT<R, INV>::run(v[gi]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int gi = 0; gi < PER; ++gi) {
+    const int g = tid + gi * NT;
+    const int line = g % LINES;
+    const int j = g / LINES;
+    const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[line * LS + (base + r * NS) * ES] = v[gi][r];
+  }
+  __syncthreads();
+}
+
+// Radix plans of the half-spectrum tile: columns (length N) and rows (N/2).
+template <int N> struct HalfPlan;
+template <> struct HalfPlan<64> { static constexpr int C0 = 8, C1 = 8, R0 = 8, R1 = 4, NT = 128; };
+template <> struct HalfPlan<128> { static constexpr int C0 = 16, C1 = 8, R0 = 8, R1 = 8, NT = 256; };
+
+// Transform of the N/2 columns k2 < N/2 (length N, along k1); column N/2 is
+// carried packed in column 0 by the caller.
+template <int N, bool INV>
+__device__ __forceinline__ void half_cols(float2 *tile, const float2 *tw) {
+  using P = HalfPlan<N>;
+  constexpr int NH = N / 2 + 1;
+  half_pass<N, N / 2, P::C0, 1, INV, 1, NH, P::NT, 1>(tile, tw);
+  half_pass<N, N / 2, P::C1, P::C0, INV, 1, NH, P::NT, 1>(tile, tw);
+}
+
+// Transform of the N rows (length N/2, elements 0 .. N/2 - 1 of each row).
+template <int N, bool INV>
+__device__ __forceinline__ void half_rows(float2 *tile, const float2 *tw) {
+  using P = HalfPlan<N>;
+  constexpr int NH = N / 2 + 1;
+  half_pass<N / 2, N, P::R0, 1, INV, NH, 1, P::NT, 2>(tile, tw);
+  half_pass<N / 2, N, P::R1, P::R0, INV, NH, 1, P::NT, 2>(tile, tw);
+}
+
+template <int N>
+__host__ __device__ constexpr size_t half_smem_bytes() {
+  return (size_t)N * (N / 2 + 1) * sizeof(float2) + (size_t)N * sizeof(float2);
+}
+
 // Threads per CTA used with an N x N tile.
 template <int N> struct TileThreads;
 template <> struct TileThreads<64> { static constexpr int value = 256; };

@@ -54,8 +54,12 @@ cudaError_t launch_code_resid(int N, const ImgBatch &b, const CodeIter &it, floa
 // Per-slot residual sums (double, fixed order) from `groups` partials per slot.
 cudaError_t launch_resid_reduce(const int *slots_dev, int n, int groups, const float *partials,
                                 double *out, cudaStream_t s);
+// ctas: CTAs per SM the kernel's register budget is sized for (2 or 3; the
+// results are the same).
 cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, const float2 *tw,
-                              cudaStream_t s);
+                              cudaStream_t s, int ctas = 2);
+// Residual partial sums per slot written by code_plane in serving mode (one per CTA).
+int plane_resid_groups(int K);
 cudaError_t launch_fft2(int N, int inverse, const float *in, float *out, int planes,
                         const float2 *tw, cudaStream_t s);
 

@@ -340,6 +340,25 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
       }
     }
     io.spat_cb = s.spat_cb;
+  } else if (s.plane_ctas == 0) {
+    s.plane_ctas = 2;
+    if (c->opts.autotune) {
+      // Time both register budgets of the plane kernel on this call's slots
+      // before the first iteration (which rewrites all of W^ and Gamma it
+      // touches; the timing runs read stale multipliers r, harmlessly).
+      CodeIter tt = it;
+      tt.first = 1;
+      tt.last = 0;
+      float best = -1.f;
+      for (int ctas : {2, 3}) {
+        const float ms = time_runs(c, 2, [&] { return launch_code_plane(s.N, tt, bt, s.tw, c->stream, ctas); });
+        if (ms < 0.f) return cuda_fail(c, cudaGetLastError(), "autotune coding plane");
+        if (best < 0.f || ms < best) {
+          best = ms;
+          s.plane_ctas = ctas;
+        }
+      }
+    }
   }
   for (int t = 0; t < c->opts.Jz; ++t) {
     it.first = t == 0;
@@ -355,7 +374,7 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
     } else {
       e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(s.N, bt, it, (float)c->rho, s.dn, s.xhp, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(s.N, it, bt, s.tw, c->stream); });
+        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(s.N, it, bt, s.tw, c->stream, s.plane_ctas); });
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "code iteration");
   }
@@ -474,6 +493,8 @@ ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, c
   std::vector<std::vector<int>> groups(c->cls.size());
   for (int i = 0; i < n; ++i) {
     if (!x[i] || H[i] <= 0 || W[i] <= 0) return fail(c, OCSC_EINVAL, "ocsc_code: image %d invalid", i);
+    if (u && u[i] && reinterpret_cast<uintptr_t>(u[i]) % 8 != 0)
+      return fail(c, OCSC_EINVAL, "ocsc_code: code buffer %d is not 8-byte aligned", i);
     const int k = class_of(c, H[i], W[i]);
     if (k < 0)
       return fail(c, OCSC_EUNSUPPORTED, "image %d (%dx%d, pad %d) maps to no FFT size of this context", i, H[i],
@@ -853,6 +874,7 @@ ocsc_status ocsc_get_tuning(const ocsc_ctx *c, int N, ocsc_tuning *out) {
     if (s.N == N) {
       out->fold_threads = s.fold_threads;
       out->spat_cb = s.spat_cb;
+      out->plane_ctas = s.plane_ctas;
       out->gram_sc = s.gram_sc;
       return OCSC_OK;
     }

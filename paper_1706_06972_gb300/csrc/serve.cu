@@ -202,7 +202,7 @@ cudaError_t launch_iteration(ocsc_server *s, int k, int v, const std::vector<int
     } else {
       e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(cl.N, b, it, (float)c->rho, q.dn[v], q.xh, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(cl.N, it, b, cl.tw, c->stream); });
+        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(cl.N, it, b, cl.tw, c->stream, cl.plane_ctas ? cl.plane_ctas : 2); });
     }
     if (e != cudaSuccess) return e;
   }
@@ -284,7 +284,7 @@ ocsc_status ocsc_server_create(ocsc_server **out, ocsc_ctx *c, const ocsc_server
            (big ? ((size_t)npairs * cl.P + (size_t)stages * cl.F) * sizeof(float2) : KF * sizeof(float2));
     q.nslots = (int)std::max<size_t>(1, std::min<size_t>(kMaxCallImages, s->o.mem_budget / q.ws));
     q.slots.resize(q.nslots);
-    q.groups = big ? large_resid_groups(cl.N, npairs) : npairs;
+    q.groups = big ? large_resid_groups(cl.N, npairs) : plane_resid_groups(c->K);
     const size_t ns = (size_t)q.nslots, nw = big ? 1 : ns;
     ocsc_status st;
     if ((st = salloc(s, &q.What, nw * KF)) || (st = salloc(s, &q.Zp, ns * KF)) ||
@@ -341,6 +341,8 @@ ocsc_status ocsc_server_create(ocsc_server **out, ocsc_ctx *c, const ocsc_server
 ocsc_status ocsc_server_submit(ocsc_server *s, uint64_t id, const float *x, int H, int W, float *u) {
   if (!s) return OCSC_EINVAL;
   if (!x || !u || H <= 0 || W <= 0) return fail(s->ctx, OCSC_EINVAL, "server_submit: bad arguments");
+  if (reinterpret_cast<uintptr_t>(u) % 8 != 0)
+    return fail(s->ctx, OCSC_EINVAL, "server_submit: the code buffer must be 8-byte aligned");
   const int k = class_of(s->ctx, H, W);
   if (k < 0) return fail(s->ctx, OCSC_EUNSUPPORTED, "server_submit: %dx%d maps to no FFT size of this context", H, W);
   Request r;

@@ -13,8 +13,18 @@ almost empty in the reference do not turn rounding into large ratios.
 """
 import numpy as np
 
-ELEM_TOL = 5e-5       # max |a - ref| / max |ref|, FP32 path
-PLANE_TOL = 1e-4      # worst per-filter / per-frequency-row error, FP32 path
+# Bars of the FP32 path, from the worst errors measured on GB300 with a margin
+# of about 3.  Codes computed against the same dictionary on both sides (the
+# first mini-batch, or coding-only cases): worst element 5.7e-6 and plane /
+# row 1.0e-5 (K = 34 at N = 512, K = 100 at N = 128).  Codes after a
+# dictionary update and the dictionaries themselves: the FP32 coding error of
+# the folded samples (~1e-6) passes through the dictionary step, whose
+# sensitivity to its input codes grows as the penalty falls; worst element
+# 9.8e-5 and plane 9.6e-5 (N = 384 after one update).
+CODE_ELEM_TOL = 2e-5   # max |a - ref| / max |ref|, same dictionary on both sides
+CODE_PLANE_TOL = 3e-5  # worst per-plane / per-frequency-row error, same dictionary
+ELEM_TOL = 3e-4        # after dictionary updates
+PLANE_TOL = 3e-4
 
 
 def rel(a, b):
@@ -48,7 +58,11 @@ def errors(a, ref):
     return e
 
 
-def assert_close(a, ref, label, elem=ELEM_TOL, plane=PLANE_TOL):
+def assert_close(a, ref, label, elem=ELEM_TOL, plane=PLANE_TOL, allow_zero=False):
+    """errors(a, ref) within the bars; a reference that is all zero (a code
+    the threshold has emptied) would make the comparison vacuous, so it fails
+    unless allow_zero."""
+    assert allow_zero or np.any(np.asarray(ref) != 0), f"{label}: the reference is all zero"
     e = errors(a, ref)
     print(f"{label}: " + " ".join(f"{k} {v:.2e}" for k, v in e.items()))
     assert e["elem"] < elem, (label, e)

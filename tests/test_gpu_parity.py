@@ -26,7 +26,7 @@ import numpy as np
 import pytest
 
 import oracle
-from tests.close import ELEM_TOL, PLANE_TOL, _worst, assert_close, errors, rel
+from tests.close import CODE_ELEM_TOL, CODE_PLANE_TOL, ELEM_TOL, PLANE_TOL, _worst, assert_close, errors, rel
 from workloads import WORKLOADS, make_image, raw_filters
 
 torch = pytest.importorskip("torch")
@@ -77,12 +77,19 @@ def surrogate_objective(codes, coding_dicts, images, N, lam, batch):
     return float(np.mean(vals))
 
 
-def compare_runs(gpu, orc, label, elem=ELEM_TOL, plane=PLANE_TOL):
+def compare_runs(gpu, orc, label, elem=ELEM_TOL, plane=PLANE_TOL, batch=1):
     """Codes and dictionaries of a GPU run against the oracle's, element by
-    element; returns the worst element errors."""
+    element: the first mini-batch's codes (same initial dictionary on both
+    sides) at the coding bars, later codes and the dictionaries at the bars
+    after updates.  Returns the worst element errors."""
     codes, dicts = gpu
     ocodes, odicts = orc[0], orc[1]
-    wc = max(assert_close(codes[t], ocodes[t], f"{label} code {t}", elem, plane)["elem"] for t in range(len(codes)))
+    wc = 0.0
+    for t in range(len(codes)):
+        tight = t < batch and elem == ELEM_TOL
+        e = assert_close(codes[t], ocodes[t], f"{label} code {t}", CODE_ELEM_TOL if tight else elem,
+                         CODE_PLANE_TOL if tight else plane)
+        wc = max(wc, e["elem"])
     wd = max(assert_close(dicts[u], odicts[u], f"{label} dict {u}", elem, plane)["elem"] for u in range(len(dicts)))
     return wc, wd
 
@@ -171,16 +178,24 @@ def test_batched_headline_step_matches_oracle():
     raw = w.filters0()
     gpu = run_gpu(imgs, raw, w.K, w.M, w.lam, w.rho, 128, w.Jz, w.Jd, batch=4, pad=w.pad)
     orc = run_oracle(imgs, raw, 128, w.lam, w.rho, w.Jz, w.Jd, batch=4)
-    compare_runs(gpu, orc, "plain_100in128_k100 B=4")
+    compare_runs(gpu, orc, "plain_100in128_k100 B=4", batch=4)
 
 
 @pytest.mark.parametrize("rho", [0.1, 0.02])
 def test_small_rho_conditioning_stress(rho):
-    """The factorisation of w A + rho I in double-float with X = L^-1 stored in
-    FP32, at a small spatial penalty: A from two samples has rank two, so the
-    matrix has K - 2 eigenvalues equal to rho and two of order |z|^2, a
-    condition number up to ~|z|^2 / rho.  lambda = rho keeps the threshold
-    lambda / rho = 1.  K = 100 filters 11 x 11 on 100 x 100 in 128 x 128."""
+    """A small spatial penalty: A from one sample has rank one, so w A + rho I
+    has K - 1 eigenvalues equal to rho and one of order |z|^2, a condition
+    number up to ~|z|^2 / rho (1.2e4 at rho = 0.1, 6.6e4 at 0.02 here).
+    lambda = rho keeps the threshold lambda / rho = 1.  K = 100 filters 11 x 11
+    on 100 x 100 in 128 x 128.
+
+    The dictionary step is then ill-conditioned with respect to its input
+    codes: feeding the oracle's own Z~ rounded to FP32 into its fold moves its
+    dictionary by delta (measured here; the FP32 storage of X = L^-1 alone
+    moves it by ~2e-6, far less).  The GPU's FP32 coding carries ~20 times that
+    rounding, so its dictionary and the next sample's codes are held to
+    100 delta; the first sample's codes (same initial dictionary) to the coding
+    bars, and the objective to the method statement's 1e-4."""
     _need_gpu()
     w = WORKLOADS["plain_100in128_k100"]
     imgs = [w.image(60 + i) for i in range(2)]
@@ -188,17 +203,27 @@ def test_small_rho_conditioning_stress(rho):
     Jz, Jd = 30, 10
     codes, dicts = run_gpu(imgs, raw, w.K, w.M, rho, rho, 128, Jz, Jd, pad=w.pad)
     ocodes, odicts, ocd = run_oracle(imgs, raw, 128, rho, rho, Jz, Jd)
-    compare_runs((codes, dicts), (ocodes, odicts), f"small rho {rho}", elem=STRESS_ELEM_TOL,
-                 plane=STRESS_PLANE_TOL)
+    # the oracle with its first sample's Z~ rounded to FP32 before the fold
+    st = oracle.init_state(np.asarray(raw, np.float64), 128, 128, rho, rho)
+    r0 = oracle.code(st, imgs[0], Jz)
+    r0.Zh = r0.Zh.astype(np.complex64).astype(np.complex128)
+    oracle.update_dict(st, [r0], Jd)
+    r1 = oracle.code(st, imgs[1], Jz)
+    d_dict = errors(st.V, odicts[0])
+    d_code = errors(r1.U, ocodes[1])
+    print(f"small rho {rho}: FP32 rounding of the folded codes moves the oracle's dictionary by "
+          f"elem {d_dict['elem']:.2e} plane {d_dict['plane']:.2e} and the next code by elem "
+          f"{d_code['elem']:.2e} plane {d_code['plane']:.2e}")
+    assert_close(codes[0], ocodes[0], f"small rho {rho} code 0", CODE_ELEM_TOL, CODE_PLANE_TOL)
+    assert_close(dicts[0], odicts[0], f"small rho {rho} dict 0", max(ELEM_TOL, 100 * d_dict["elem"]),
+                 max(PLANE_TOL, 100 * d_dict["plane"]))
+    assert_close(codes[1], ocodes[1], f"small rho {rho} code 1", max(ELEM_TOL, 100 * d_code["elem"]),
+                 max(PLANE_TOL, 100 * max(d_code["plane"], d_code.get("row", 0), d_code.get("col", 0))))
     gcd = [oracle.normalize_filters(raw)] + dicts[:-1]
     f_gpu = surrogate_objective(codes, gcd, imgs, 128, rho, 1)
     f_orc = surrogate_objective(ocodes, ocd, imgs, 128, rho, 1)
     print(f"small rho {rho}: relative objective {abs(f_gpu - f_orc) / abs(f_orc):.2e}")
     assert abs(f_gpu - f_orc) / abs(f_orc) < OBJ_TOL
-
-
-STRESS_ELEM_TOL = 5e-4
-STRESS_PLANE_TOL = 1e-3
 
 
 # --- coding at the N >= 256 sizes with many filter pairs per spectral row --------
@@ -213,7 +238,7 @@ def test_large_grid_coding_with_many_stages(K, N, side, Jz):
     _need_gpu()
     import paper_1706_06972_gb300 as pkg
 
-    M, lam, rho = 11, 1.0, 1.0
+    M, lam, rho = 11, 0.1, 1.0
     raw = raw_filters(K, M, 500 + K)
     imgs = [make_image(side, side, 1800 + N + i) for i in range(2)]
     lr = pkg.OCSC(K, M, lam, rho, fft_size=N, pad=10, Jz=Jz, Jd=2, max_batch=2)
@@ -228,7 +253,7 @@ def test_large_grid_coding_with_many_stages(K, N, side, Jz):
     for i, im in enumerate(imgs):
         o = oracle.code_admm(oracle.pad_to(np.asarray(im, np.float64), N, N), Dh, lam, rho, Jz)
         u = us[i].cpu().numpy()
-        assert_close(u, o.U, f"K={K} N={N} code {i}")
+        assert_close(u, o.U, f"K={K} N={N} code {i}", CODE_ELEM_TOL, CODE_PLANE_TOL)
         fo = oracle.sample_objective(D, o.U, oracle.pad_to(np.asarray(im, np.float64), N, N), lam)
         assert abs(f_gpu[i] - fo) / abs(fo) < OBJ_TOL
 
@@ -243,7 +268,7 @@ def _small_images(n, h, w, seed):
     dict(K=15, M=5, lam=0.5, rho=1.0, Jz=20, Jd=5, n=3, hw=(64, 64), pad=0),      # odd K
     dict(K=4, M=1, lam=0.2, rho=2.0, Jz=10, Jd=3, n=2, hw=(40, 50), pad=0),       # 1x1 filters, rectangular
     dict(K=8, M=7, lam=0.0, rho=1.0, Jz=15, Jd=4, n=2, hw=(57, 57), pad=6),       # lambda = 0, zero padding
-    dict(K=6, M=4, lam=1.0, rho=0.5, Jz=1, Jd=1, n=2, hw=(64, 64), pad=0),        # single iterations
+    dict(K=6, M=4, lam=0.02, rho=0.5, Jz=1, Jd=1, n=2, hw=(64, 64), pad=0),       # single iterations
     dict(K=33, M=3, lam=0.3, rho=1.0, Jz=8, Jd=3, n=2, hw=(100, 90), pad=2),      # K > 32, N = 128
     dict(K=7, M=5, lam=0.5, rho=1.0, Jz=12, Jd=4, n=2, hw=(230, 200), pad=10),    # N = 256, odd K
     dict(K=4, M=3, lam=0.5, rho=1.0, Jz=8, Jd=3, n=2, hw=(400, 300), pad=10),     # N = 512
@@ -275,7 +300,7 @@ def test_fold_of_more_samples_than_one_chunk_matches_oracle():
     raw = raw_filters(12, 5, 1701)
     gpu = run_gpu(imgs, raw, 12, 5, 0.5, 1.0, 64, 8, 4, batch=20, pad=0)
     orc = run_oracle(imgs, raw, 64, 0.5, 1.0, 8, 4, batch=20)
-    compare_runs(gpu, orc, "fold of 20")
+    compare_runs(gpu, orc, "fold of 20", batch=20)
 
 
 @pytest.mark.parametrize("K", [1, 3, 5, 127, 128])
@@ -287,8 +312,8 @@ def test_factor_panel_edges_match_oracle(K):
     _need_gpu()
     imgs = _small_images(2, 56, 56, 700 + K)
     raw = raw_filters(K, 5, 900 + K)
-    gpu = run_gpu(imgs, raw, K, 5, 0.5, 1.0, 64, 8, 4, pad=0)
-    orc = run_oracle(imgs, raw, 64, 0.5, 1.0, 8, 4)
+    gpu = run_gpu(imgs, raw, K, 5, 0.05, 1.0, 64, 8, 4, pad=0)
+    orc = run_oracle(imgs, raw, 64, 0.05, 1.0, 8, 4)
     compare_runs(gpu, orc, f"panel edges K={K}")
 
 
@@ -298,7 +323,7 @@ def test_minibatch_fold_matches_oracle():
     raw = raw_filters(12, 6, 9)
     gpu = run_gpu(imgs, raw, 12, 6, 0.5, 1.0, 64, 20, 6, batch=3, pad=0)
     orc = run_oracle(imgs, raw, 64, 0.5, 1.0, 20, 6, batch=3)
-    compare_runs(gpu, orc, "mini-batch 3")
+    compare_runs(gpu, orc, "mini-batch 3", batch=3)
 
 
 @pytest.mark.parametrize("flags,gflags,lam,rho", [
@@ -393,7 +418,7 @@ def test_larger_minibatch_matches_oracle():
     raw = raw_filters(24, 7, 17)
     gpu = run_gpu(imgs, raw, 24, 7, 0.5, 1.0, 64, 20, 6, batch=8, pad=0)
     orc = run_oracle(imgs, raw, 64, 0.5, 1.0, 20, 6, batch=8)
-    compare_runs(gpu, orc, "mini-batch 8")
+    compare_runs(gpu, orc, "mini-batch 8", batch=8)
 
 
 # --- uneven sizes: size classes with the consensus dictionary step --------------
@@ -549,10 +574,10 @@ PRECISION_TOL = {
 }
 
 
-def _precision_case(K, precision, M, N, B, Jz, Jd, seed_f, seed_i):
+def _precision_case(K, precision, M, N, B, Jz, Jd, seed_f, seed_i, lam=0.5):
     import paper_1706_06972_gb300 as pkg
 
-    lam, rho = 0.5, 1.0
+    rho = 1.0
     o = _precision_oracle(K, M, N, B, lam, rho, Jz, Jd, seed_f, seed_i)
     h_tol, (e_tol, p_tol), f_tol = PRECISION_TOL[precision]
     lr = pkg.OCSC(K, M, lam, rho, fft_size=N, pad=4, Jz=Jz, Jd=Jd, max_batch=B, precision=precision)
@@ -600,7 +625,7 @@ def test_large_K_factor_matches_oracle(K, precision):
     precision workload's filter count.  Relative objective, dictionary error
     and code error against the FP64 oracle per result."""
     _need_gpu()
-    _precision_case(K, precision, 5, 64, 4, 8, 4, 91, 1400)
+    _precision_case(K, precision, 5, 64, 4, 8, 4, 91, 1400, lam=0.05)
 
 
 def test_tensor_core_fold_timeout_is_reported_and_context_recovers():
@@ -680,6 +705,7 @@ def test_autotuned_tiles_do_not_change_results(precision):
     print("tuned tiles:", t)
     assert t[64]["fold_threads"] in (256, 512) and t[256]["fold_threads"] in (256, 512)
     assert t[256]["spat_cb"] in (8, 16) and t[64]["spat_cb"] == 0
+    assert t[64]["plane_ctas"] in (2, 3) and t[256]["plane_ctas"] == 0
     if precision:
         assert t[64]["gram_sc"] in (32, 64, 128)
 

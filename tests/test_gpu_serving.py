@@ -78,10 +78,17 @@ def test_result_same_alone_and_in_mix_while_learning():
     versions = {0: lr.get_dict()}
     pending = list(range(len(imgs)))
     res = {}
+    seen_updates = 0
+    for i in pending[:6]:              # a first wave; its completions trigger an update
+        srv.submit(i, imgs[i])
+    pending = pending[6:]
     for _ in range(2000):
-        for i in pending[:2]:          # two arrivals per round: requests keep
-            srv.submit(i, imgs[i])     # arriving while updates run
-        pending = pending[2:]
+        updates = lr.counters()["dict_updates"]
+        if updates > seen_updates and pending:   # later waves arrive while the
+            seen_updates = updates               # earlier requests and the
+            for i in pending[:3]:                # update are still in flight
+                srv.submit(i, imgs[i])
+            pending = pending[3:]
         active, queued = srv.step()
         for d in srv.poll():
             res[d["id"]] = d
