@@ -96,7 +96,15 @@ typedef struct {
                             accumulation, the history kept as a compensated
                             pair of FP32 words (A + Alo) across the stream;
                          2: as 1 with each code split into two BF16 words
-                            (hi + lo; products hi hi + hi lo + lo hi). */
+                            (hi + lo; products hi hi + hi lo + lo hi);
+                         3: the products conj(z_i) z_j and x~ conj(z_i) split
+                            exactly and summed in double-float (FP32 pairs),
+                            the running means A + Alo and b + blo kept as
+                            pairs (K <= 128).  A and b then stay exact
+                            functions of the same FP32 codes; with the
+                            separately rounded FP32 products of 0 the solve's
+                            forward error grows like u cond(w A + rho I)
+                            (u = 2^-24), which matters at small rho. */
   int autotune;       /* 1 (default): at a size class's first use, time the
                          candidate tile shapes on its own buffers and keep the
                          fastest: threads per CTA of the factorisation
@@ -164,7 +172,7 @@ ocsc_status ocsc_padded_size(const ocsc_ctx *ctx, int H, int W, int *N);
  * Code n samples against the current dictionary (Algorithm 3, FFT and code
  * steps).  x[i] is a DEVICE pointer to an H[i] x W[i] float image; u[i] is a
  * DEVICE pointer to a caller-owned K x N x N float buffer that receives the
- * sparse code U_i after the last U-step, or NULL to skip writing it (8-byte
+ * sparse code U_i after the last U-step, or NULL to skip writing it (16-byte
  * aligned, as cudaMalloc and torch allocations are; OCSC_EINVAL otherwise).  x, H, W
  * and u are HOST arrays of length n.  Every image must map to one of the
  * context's FFT sizes; images of different sizes may be mixed in one call.
@@ -356,7 +364,7 @@ ocsc_status ocsc_server_create(ocsc_server **out, ocsc_ctx *ctx, const ocsc_serv
 void ocsc_server_destroy(ocsc_server *s);
 
 /* Queue one request: x (DEVICE, H x W floats) is coded into u (DEVICE,
- * K x N x N floats, N its padded size, 8-byte aligned).  Both stay owned by the caller and must
+ * K x N x N floats, N its padded size, 16-byte aligned).  Both stay owned by the caller and must
  * remain valid until the request is reported by ocsc_server_poll. */
 ocsc_status ocsc_server_submit(ocsc_server *s, uint64_t id, const float *x, int H, int W, float *u);
 
@@ -439,7 +447,7 @@ ocsc_status ocsc_fft2_c2r(ocsc_ctx *ctx, int N, const float *X, float *x, int pl
  * axes to N x N, N in {64, 128}, H, W <= N) against the K filters D (DEVICE,
  * K x M x M floats, M <= 16, used as given) with Jz code-ADMM iterations of
  * ocsc_code's kernels, and writes the sparse code U (DEVICE, K x N x N floats,
- * 8-byte aligned, caller-owned) -- the same result ocsc_code gives for that image and
+ * 16-byte aligned, caller-owned) -- the same result ocsc_code gives for that image and
  * dictionary.  Work is enqueued on cuda_stream (a cudaStream_t; NULL = legacy
  * default stream); the call is asynchronous.  err (nullable, err_len bytes)
  * receives a message on failure.

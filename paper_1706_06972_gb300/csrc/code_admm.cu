@@ -135,9 +135,9 @@ __global__ void __launch_bounds__(HalfPlan<N>::NT, MINB)
     code_plane_kernel(CodeIter it, ImgBatch b, const float2 *__restrict__ tw) {
   constexpr int NT = HalfPlan<N>::NT, NH = N / 2 + 1, H = N / 2, Q = H / 2 + 1;
   constexpr int F = N * NH, P = N * N;
-  extern __shared__ float2 smem[];
-  float2 *tile = smem;      // [N][NH]
-  float2 *s_tw = smem + F;  // [N]
+  extern __shared__ __align__(16) float4 hsmem[];
+  float2 *tile = reinterpret_cast<float2 *>(hsmem);  // [N][NH]
+  float2 *s_tw = tile + F;                           // [N]
   const int K = it.K;
   const int k = blockIdx.x;
   const int img = blockIdx.y;
@@ -154,22 +154,56 @@ __global__ void __launch_bounds__(HalfPlan<N>::NT, MINB)
   float2 *Wk = it.What + ((size_t)slot * K + k) * F;
   float2 *Zk = it.Zp + ((size_t)slot * K + k) * F;
 
-  // 1. Z~-step z = w^ + conj(d) r_p over the half spectrum; the thread of
-  //    column 0 also takes column N/2 of its row and packs the two.
-  for (int p = threadIdx.x; p < F; p += NT) {
-    const int k1 = p / NH, k2 = p - k1 * NH;
-    if (k2 == H) continue;
-    float2 z = cconjmul(Dk[p], rr[p]);
-    if (!first) z = cadd(z, Wk[p]);
-    if (store_last) Zk[p] = z;
-    if (k2 == 0) {
-      const int ph = p + H;
-      float2 zh = cconjmul(Dk[ph], rr[ph]);
-      if (!first) zh = cadd(zh, Wk[ph]);
-      if (store_last) Zk[ph] = zh;
-      z = make_float2(z.x - zh.y, z.y + zh.x);  // z0 + i zN/2
+  // 1. Z~-step z = w^ + conj(d) r_p over the half spectrum.  W^ of this
+  //    filter comes into the tile (its global layout) by 16-byte asynchronous
+  //    copies, all in flight at once; D~ and r are read two bins per 16-byte
+  //    load, four loads deep per thread.  Then columns 0 and N/2 are packed as
+  //    z0 + i zN/2 in column 0.
+  constexpr int F2 = F / 2;  // bin pairs (F is even)
+  if (!first) {
+    const float4 *src = reinterpret_cast<const float4 *>(Wk);
+    float4 *dst = reinterpret_cast<float4 *>(tile);
+    for (int c = threadIdx.x; c < F2; c += NT) cp_async16(dst + c, src + c);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  {
+    const float4 *D4 = reinterpret_cast<const float4 *>(Dk);
+    const float4 *R4 = reinterpret_cast<const float4 *>(rr);
+    float4 *Z4 = reinterpret_cast<float4 *>(Zk);
+    float4 *T4 = reinterpret_cast<float4 *>(tile);
+    constexpr int U = 4;
+    for (int c0 = threadIdx.x; c0 < F2; c0 += U * NT) {
+      float4 dv[U], rv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = c0 + u * NT;
+        if (c < F2) {
+          dv[u] = D4[c];
+          rv[u] = R4[c];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int c = c0 + u * NT;
+        if (c >= F2) break;
+        float2 z0 = cconjmul(make_float2(dv[u].x, dv[u].y), make_float2(rv[u].x, rv[u].y));
+        float2 z1 = cconjmul(make_float2(dv[u].z, dv[u].w), make_float2(rv[u].z, rv[u].w));
+        if (!first) {
+          const float4 w = T4[c];
+          z0 = cadd(z0, make_float2(w.x, w.y));
+          z1 = cadd(z1, make_float2(w.z, w.w));
+        }
+        const float4 zz = make_float4(z0.x, z0.y, z1.x, z1.y);
+        if (store_last) Z4[c] = zz;
+        T4[c] = zz;
+      }
     }
-    tile[p] = z;
+  }
+  __syncthreads();
+  for (int k1 = threadIdx.x; k1 < N; k1 += NT) {
+    const float2 z0 = tile[k1 * NH], zh = tile[k1 * NH + H];
+    tile[k1 * NH] = make_float2(z0.x - zh.y, z0.y + zh.x);  // z0 + i zN/2
   }
   __syncthreads();
 
@@ -202,33 +236,64 @@ __global__ void __launch_bounds__(HalfPlan<N>::NT, MINB)
   // 4. Inverse transforms of the packed rows (length N/2): P (z[2m] + i z[2m+1]).
   half_rows<N, true>(tile, s_tw);
 
-  // 5. Spatial step on pairs of pixels (2m, 2m+1) of row n1:
-  //    U = S(Z + Gamma), Gamma += Z - U, W = U - Gamma.
+  // 5. Spatial step on groups of four pixels 4j .. 4j+3 of row n1 (tile
+  //    elements 2j, 2j+1): U = S(Z + Gamma), Gamma += Z - U, W = U - Gamma.
+  //    Gamma (and, for the serving residual, the previous U) are read four
+  //    16-byte loads deep per thread before use.
   const float invP = 1.0f / (float)P;
   float *Gk = it.Gam + ((size_t)slot * K + k) * P;
   float *Uk = b.u[img] ? b.u[img] + (size_t)k * P : nullptr;
   const bool resid = it.serve && store_last;
+  const bool wantu = (store_last || store_prev) && Uk;
   float acc[kResidTerms] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int q = threadIdx.x; q < N * H; q += NT) {
-    const int n1 = q / H, m = q - n1 * H;
-    const float2 c = tile[n1 * NH + m];
-    const int o = n1 * N + 2 * m;
-    const float2 g = first ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2 *>(Gk + o);
-    const float za = c.x * invP, zb = c.y * invP;
-    const float va = za + g.x, vb = zb + g.y;
-    const float ua = soft_threshold(va, it.thr), ub = soft_threshold(vb, it.thr);
-    const float ga = va - ua, gb = vb - ub;
-    if (resid) {
-      const float2 pu = (first || !Uk) ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2 *>(Uk + o);
-      acc[0] += (za - ua) * (za - ua) + (zb - ub) * (zb - ub);
-      acc[1] += za * za + zb * zb;
-      acc[2] += ua * ua + ub * ub;
-      acc[3] += (ua - pu.x) * (ua - pu.x) + (ub - pu.y) * (ub - pu.y);
-      acc[4] += ga * ga + gb * gb;
+  {
+    constexpr int Q4 = N * N / 4, J = N / 4, U = 4;
+    float4 *G4 = reinterpret_cast<float4 *>(Gk);
+    float4 *U4 = reinterpret_cast<float4 *>(Uk);
+    for (int q0 = threadIdx.x; q0 < Q4; q0 += U * NT) {
+      float4 gv[U], pv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + u * NT;
+        gv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        pv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (q < Q4) {
+          if (!first) gv[u] = G4[q];
+          if (resid && !first && Uk) pv[u] = U4[q];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int q = q0 + u * NT;
+        if (q >= Q4) break;
+        const int n1 = q / J, j = q - n1 * J;
+        float2 *tp = tile + n1 * NH + 2 * j;
+        const float2 c0 = tp[0], c1 = tp[1];
+        const float z[4] = {c0.x * invP, c0.y * invP, c1.x * invP, c1.y * invP};
+        const float g[4] = {gv[u].x, gv[u].y, gv[u].z, gv[u].w};
+        const float pu[4] = {pv[u].x, pv[u].y, pv[u].z, pv[u].w};
+        float un[4], gn[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float v = z[e] + g[e];
+          un[e] = soft_threshold(v, it.thr);
+          gn[e] = v - un[e];
+          if (resid) {
+            acc[0] += (z[e] - un[e]) * (z[e] - un[e]);
+            acc[1] += z[e] * z[e];
+            acc[2] += un[e] * un[e];
+            acc[3] += (un[e] - pu[e]) * (un[e] - pu[e]);
+            acc[4] += gn[e] * gn[e];
+          }
+        }
+        G4[q] = make_float4(gn[0], gn[1], gn[2], gn[3]);
+        if (wantu) U4[q] = make_float4(un[0], un[1], un[2], un[3]);
+        if (!skip_fwd) {
+          tp[0] = make_float2(un[0] - gn[0], un[1] - gn[1]);
+          tp[1] = make_float2(un[2] - gn[2], un[3] - gn[3]);
+        }
+      }
     }
-    *reinterpret_cast<float2 *>(Gk + o) = make_float2(ga, gb);
-    if ((store_last || store_prev) && Uk) *reinterpret_cast<float2 *>(Uk + o) = make_float2(ua, ub);
-    if (!skip_fwd) tile[n1 * NH + m] = make_float2(ua - ga, ub - gb);
   }
   if (resid) block_sum_terms(acc, it.resid + ((size_t)slot * gridDim.x + blockIdx.x) * kResidTerms);
   if (skip_fwd) return;

@@ -30,6 +30,7 @@ struct SizeClass {
   float2 *Alo = nullptr;    // [F][stride] its compensation word (precision > 0)
   float4 *Csf = nullptr;    // [F][stride] C^p of the recursion variant (history = 1), double-float
   float2 *b = nullptr;      // [K][F]
+  float2 *blo = nullptr;    // [K][F] its compensation word (precision 3)
   float2 *X = nullptr;      // [F][stride] X = L^-1 (FP32) of the FP64 factor
   float2 *y = nullptr;      // [K][F] y = L^-1 (w b)
   // pending samples

@@ -297,7 +297,35 @@ __device__ __forceinline__ void fold_xpanel(float2 *XS, const float2 *Lb, const 
 // Lb [3][kPanel][K] float2, zs / xs (a chunk of pending codes).  During the
 // fold each M slot first holds the FP32 running sum of conj(z_i) z_j in its
 // first 8 bytes.
-template <int kFoldThreads>
+// DF (history precision 3): the products conj(z_i) z_j and x~ conj(z_i) are
+// split exactly and summed in double-float, and the running means of A and b
+// are kept as FP32 pairs (A + Alo, b + blo) updated in double-float, so that A
+// and b stay exact functions of the same FP32 codes: with separately rounded
+// products their rounding differs along directions that only rho damps, a
+// forward error of order u cond(w A + rho I).
+__device__ __forceinline__ void df_acc_cconjmul(float4 &v, float2 a, float2 b) {  // v += conj(a) b
+  df_mac(a.x, 0.f, b.x, 0.f, v.x, v.z);
+  df_mac(a.y, 0.f, b.y, 0.f, v.x, v.z);
+  df_mac(a.x, 0.f, b.y, 0.f, v.y, v.w);
+  df_mac(-a.y, 0.f, b.x, 0.f, v.y, v.w);
+}
+__device__ __forceinline__ void df_acc_cmulc(float4 &v, float2 a, float2 b) {  // v += a conj(b)
+  df_mac(a.x, 0.f, b.x, 0.f, v.x, v.z);
+  df_mac(a.y, 0.f, b.y, 0.f, v.x, v.z);
+  df_mac(a.y, 0.f, b.x, 0.f, v.y, v.w);
+  df_mac(-a.x, 0.f, b.y, 0.f, v.y, v.w);
+}
+// alpha (oh + ol) + beta (S + E) as a normalised pair, all in double-float.
+__device__ __forceinline__ float2 df_blend(float oh, float ol, float S, float E, float2 al, float2 be) {
+  const float2 s = two_sum(S, E);
+  float P1, E1, P2, E2;
+  df_mul(oh, ol, al.x, al.y, P1, E1);
+  df_mul(s.x, s.y, be.x, be.y, P2, E2);
+  df_acc(P1, E1, P2, E2);
+  return two_sum(P1, E1);
+}
+
+template <int kFoldThreads, bool DF>
 __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int K = a.K, F = a.F, B = a.B;
@@ -313,10 +341,17 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   const int p = blockIdx.x;
   const int tid = threadIdx.x;
 
-  for (int t = tid; t < T; t += kFoldThreads) S[2 * t] = make_float2(0.f, 0.f);
-  float2 sb[(128 + kFoldThreads - 1) / kFoldThreads];
+  constexpr int MR = (128 + kFoldThreads - 1) / kFoldThreads;
+  for (int t = tid; t < T; t += kFoldThreads) {
+    if (DF) M[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    else S[2 * t] = make_float2(0.f, 0.f);
+  }
+  float2 sb[MR];
+  float4 sbd[DF ? MR : 1];
 #pragma unroll
-  for (int m = 0; m < (128 + kFoldThreads - 1) / kFoldThreads; ++m) sb[m] = make_float2(0.f, 0.f);
+  for (int m = 0; m < MR; ++m) sb[m] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int m = 0; m < (DF ? MR : 1); ++m) sbd[m] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   // 1. FP32 sums over the pending samples of conj(z_i) z_j and x~ conj(z_i).
   for (int c0 = 0; c0 < (a.prefolded ? 0 : B); c0 += kFoldChunk) {
@@ -331,15 +366,25 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
     for (int t = tid; t < T; t += kFoldThreads) {
       int i, j;
       tri_ij(t, K, i, j);
-      float2 acc = S[2 * t];
-      for (int s = 0; s < nb; ++s) acc = cadd(acc, cconjmul(zs[s * K + i], zs[s * K + j]));
-      S[2 * t] = acc;
+      if (DF) {
+        float4 acc = M[t];
+        for (int s = 0; s < nb; ++s) df_acc_cconjmul(acc, zs[s * K + i], zs[s * K + j]);
+        M[t] = acc;
+      } else {
+        float2 acc = S[2 * t];
+        for (int s = 0; s < nb; ++s) acc = cadd(acc, cconjmul(zs[s * K + i], zs[s * K + j]));
+        S[2 * t] = acc;
+      }
     }
 #pragma unroll
-    for (int m = 0; m < (128 + kFoldThreads - 1) / kFoldThreads; ++m) {
+    for (int m = 0; m < MR; ++m) {
       const int i = tid + m * kFoldThreads;
-      if (i < K)
-        for (int s = 0; s < nb; ++s) sb[m] = cadd(sb[m], cmulc(xs[s], zs[s * K + i]));
+      if (i < K) {
+        if (DF)
+          for (int s = 0; s < nb; ++s) df_acc_cmulc(sbd[m], xs[s], zs[s * K + i]);
+        else
+          for (int s = 0; s < nb; ++s) sb[m] = cadd(sb[m], cmulc(xs[s], zs[s * K + i]));
+      }
     }
   }
   __syncthreads();
@@ -348,8 +393,9 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   //    double-float.
   float2 *Ap = a.A + (size_t)p * tri_stride(K);
   const float alpha = (float)a.alpha, beta = (float)a.beta;
-  const float2 *Lo = a.Alo ? a.Alo + (size_t)p * tri_stride(K) : nullptr;
+  float2 *Lo = a.Alo ? a.Alo + (size_t)p * tri_stride(K) : nullptr;
   const float2 wf = df_of(a.w), rf = df_of(a.rho_eff);
+  const float2 ald = df_of(a.alpha), bed = df_of(a.beta);
   for (int t = tid; t < T; t += kFoldThreads) {
     int i, j;
     tri_ij(t, K, i, j);
@@ -357,6 +403,16 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
     if (a.prefolded) {  // A (+ its compensation word) already holds the new mean
       hf = Ap[t];
       if (Lo) lf = Lo[t];
+    } else if (DF) {
+      const float2 oh = a.first ? make_float2(0.f, 0.f) : Ap[t];
+      const float2 ol = a.first ? make_float2(0.f, 0.f) : Lo[t];
+      const float4 sum = M[t];
+      const float2 nr = df_blend(oh.x, ol.x, sum.x, sum.z, ald, bed);
+      const float2 ni = df_blend(oh.y, ol.y, sum.y, sum.w, ald, bed);
+      hf = make_float2(nr.x, ni.x);
+      lf = make_float2(nr.y, ni.y);
+      Ap[t] = hf;
+      Lo[t] = lf;
     } else {
       const float2 old = a.first ? make_float2(0.f, 0.f) : Ap[t];
       const float2 sum = S[2 * t];
@@ -380,17 +436,29 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   for (int m = 0; m < (128 + kFoldThreads - 1) / kFoldThreads; ++m) {
     const int i = tid + m * kFoldThreads;
     if (i < K) {
-      float2 nw;
+      float2 nw, nl = make_float2(0.f, 0.f);
+      const size_t o = (size_t)i * F + p;
       if (a.prefolded) {
-        nw = a.b[(size_t)i * F + p];
+        nw = a.b[o];
+        if (a.blo) nl = a.blo[o];
+      } else if (DF) {
+        const float2 oh = a.first ? make_float2(0.f, 0.f) : a.b[o];
+        const float2 ol = a.first ? make_float2(0.f, 0.f) : a.blo[o];
+        const float4 sum = sbd[DF ? m : 0];
+        const float2 nr = df_blend(oh.x, ol.x, sum.x, sum.z, ald, bed);
+        const float2 ni = df_blend(oh.y, ol.y, sum.y, sum.w, ald, bed);
+        nw = make_float2(nr.x, ni.x);
+        nl = make_float2(nr.y, ni.y);
+        a.b[o] = nw;
+        a.blo[o] = nl;
       } else {
-        const float2 old = a.first ? make_float2(0.f, 0.f) : a.b[(size_t)i * F + p];
+        const float2 old = a.first ? make_float2(0.f, 0.f) : a.b[o];
         nw = make_float2(fmaf(alpha, old.x, beta * sb[m].x), fmaf(alpha, old.y, beta * sb[m].y));
-        a.b[(size_t)i * F + p] = nw;
+        a.b[o] = nw;
       }
       float Sr, Er, Si, Ei;
-      df_mul(nw.x, 0.f, wf.x, wf.y, Sr, Er);
-      df_mul(nw.y, 0.f, wf.x, wf.y, Si, Ei);
+      df_mul(nw.x, nl.x, wf.x, wf.y, Sr, Er);
+      df_mul(nw.y, nl.y, wf.x, wf.y, Si, Ei);
       y[i] = make_float4(Sr, Si, Er, Ei);
     }
   }
@@ -642,19 +710,20 @@ size_t fold_smem_bytes(int K) {
 
 // threads: 256 or 512 (CTA size of the per-frequency factorisation; every
 // entry sees the same operations in the same order either way).
+template <int NTH, bool DF>
+static cudaError_t fold_factor_n(const FoldArgs &a, size_t sm, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(fold_factor_kernel<NTH, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  fold_factor_kernel<NTH, DF><<<a.F, NTH, sm, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fold_factor(const FoldArgs &a, int threads, cudaStream_t s) {
   const size_t sm = fold_smem_bytes(a.K);
-  cudaError_t e;
-  if (threads == 512) {
-    e = cudaFuncSetAttribute(fold_factor_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    fold_factor_kernel<512><<<a.F, 512, sm, s>>>(a);
-  } else {
-    e = cudaFuncSetAttribute(fold_factor_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    fold_factor_kernel<256><<<a.F, 256, sm, s>>>(a);
-  }
-  return cudaGetLastError();
+  if (a.dfold && !a.prefolded && (!a.Alo || !a.blo)) return cudaErrorInvalidValue;
+  const bool df = a.dfold && !a.prefolded;
+  if (threads == 512) return df ? fold_factor_n<512, true>(a, sm, s) : fold_factor_n<512, false>(a, sm, s);
+  return df ? fold_factor_n<256, true>(a, sm, s) : fold_factor_n<256, false>(a, sm, s);
 }
 
 cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const float2 *yb,

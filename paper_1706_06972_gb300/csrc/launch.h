@@ -106,10 +106,14 @@ struct FoldArgs {
   float2 *L;            // [F][stride] X = L^-1 of the FP64 Cholesky factor, FP32
   float2 *g;            // [K][F]  y = L^-1 (w b)
   int *err;
-  // prefolded = 1: A (+ Alo when not null) and b already hold the new means
-  // (tensor-core fold); the kernel only factors.
+  // prefolded = 1: A (+ Alo when not null) and b (+ blo when not null) already
+  // hold the new means (tensor-core fold); the kernel only factors.
   int prefolded;
-  const float2 *Alo;
+  float2 *Alo;          // [F][stride] compensation word of A (precision > 0)
+  // dfold = 1 (history precision 3): products and running means in
+  // double-float, A + Alo and b + blo kept as FP32 pairs.
+  int dfold;
+  float2 *blo;          // [K][F] compensation word of b (precision 3)
 };
 cudaError_t launch_fold_factor(const FoldArgs &a, int threads, cudaStream_t s);
 

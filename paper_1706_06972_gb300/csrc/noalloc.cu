@@ -84,8 +84,8 @@ extern "C" ocsc_status ocsc_code_noalloc(const float *x, int H, int W, const flo
                                          void *cuda_stream, char *err, size_t err_len) {
   if (err && err_len > 0) err[0] = '\0';
   if (!x || !D || !u) return say(err, err_len, OCSC_EINVAL, "null image, filter or output pointer");
-  if (reinterpret_cast<uintptr_t>(u) % 8 != 0)
-    return say(err, err_len, OCSC_EINVAL, "the code buffer must be 8-byte aligned");
+  if (reinterpret_cast<uintptr_t>(u) % 16 != 0)
+    return say(err, err_len, OCSC_EINVAL, "the code buffer must be 16-byte aligned");
   if (N != 64 && N != 128) return say(err, err_len, OCSC_EUNSUPPORTED, "N=%d: only 64 or 128", N);
   if (H <= 0 || W <= 0 || H > N || W > N)
     return say(err, err_len, OCSC_EINVAL, "image %dx%d does not fit the %dx%d domain", H, W, N, N);

@@ -115,6 +115,11 @@ ocsc_status alloc_class(ocsc_ctx *c, SizeClass &s, int N) {
     cudaError_t e = cudaMemset(s.Alo, 0, (size_t)s.F * TS * sizeof(float2));
     if (e != cudaSuccess) return cuda_fail(c, e, "clear history compensation");
   }
+  if (c->opts.precision == 3) {
+    if ((st = dalloc(c, &s.blo, KF))) return st;
+    cudaError_t e = cudaMemset(s.blo, 0, KF * sizeof(float2));
+    if (e != cudaSuccess) return cuda_fail(c, e, "clear history compensation");
+  }
   std::vector<float2> tw(N);
   for (int m = 0; m < N; ++m) {
     const double a = -2.0 * M_PI * (double)m / (double)N;
@@ -211,9 +216,13 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
     fail(c, OCSC_EUNSUPPORTED, "history = 1 needs rho_convention 1, precision 0, K <= 128 and one FFT size");
     return bail(OCSC_EUNSUPPORTED);
   }
-  if (c->opts.precision < 0 || c->opts.precision > 2) {
-    fail(c, OCSC_EINVAL, "precision must be 0, 1 or 2");
+  if (c->opts.precision < 0 || c->opts.precision > 3) {
+    fail(c, OCSC_EINVAL, "precision must be 0, 1, 2 or 3");
     return bail(OCSC_EINVAL);
+  }
+  if (c->opts.precision == 3 && K > kSmallK) {
+    fail(c, OCSC_EUNSUPPORTED, "precision 3 (double-float history) needs K <= %d", kSmallK);
+    return bail(OCSC_EUNSUPPORTED);
   }
   if (c->opts.Jz < 1 || c->opts.Jd < 1 || c->opts.max_batch < 1) {
     fail(c, OCSC_EINVAL, "Jz, Jd and max_batch must be positive");
@@ -493,8 +502,8 @@ ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, c
   std::vector<std::vector<int>> groups(c->cls.size());
   for (int i = 0; i < n; ++i) {
     if (!x[i] || H[i] <= 0 || W[i] <= 0) return fail(c, OCSC_EINVAL, "ocsc_code: image %d invalid", i);
-    if (u && u[i] && reinterpret_cast<uintptr_t>(u[i]) % 8 != 0)
-      return fail(c, OCSC_EINVAL, "ocsc_code: code buffer %d is not 8-byte aligned", i);
+    if (u && u[i] && reinterpret_cast<uintptr_t>(u[i]) % 16 != 0)
+      return fail(c, OCSC_EINVAL, "ocsc_code: code buffer %d is not 16-byte aligned", i);
     const int k = class_of(c, H[i], W[i]);
     if (k < 0)
       return fail(c, OCSC_EUNSUPPORTED, "image %d (%dx%d, pad %d) maps to no FFT size of this context", i, H[i],
@@ -581,7 +590,13 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
       e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_big(fa, c->stream); });
       if (e != cudaSuccess) return cuda_fail(c, e, "history fold (K > 128)");
     }
-    if (c->opts.precision > 0) {
+    if (c->opts.precision == 3) {
+      // Double-float fold inside the factorisation kernel.
+      fa.dfold = 1;
+      fa.Alo = s.Alo;
+      fa.blo = s.blo;
+    }
+    if (c->opts.precision == 1 || c->opts.precision == 2) {
       // Tensor-core fold of the pending codes (compensated), then factor only.
       if (s.pending > 0) {
         GramArgs ga{};
@@ -649,6 +664,7 @@ ocsc_status ocsc_update_dict(ocsc_ctx *c) {
           FoldArgs fp = fa;
           fp.prefolded = 1;
           fp.Alo = s.Alo;
+          fp.blo = s.blo;
           const float t256 = time_runs(c, 2, [&] { return launch_fold_factor(fp, 256, c->stream); });
           const float t512 = time_runs(c, 2, [&] { return launch_fold_factor(fp, 512, c->stream); });
           if (t256 < 0.f || t512 < 0.f) return cuda_fail(c, cudaGetLastError(), "autotune fold_factor");
@@ -773,6 +789,7 @@ std::vector<std::pair<void *, size_t>> state_regions(ocsc_ctx *c) {
     r.emplace_back(s.b, kf);
     r.emplace_back(s.A, (size_t)s.F * tri_stride(c->K) * sizeof(float2));
     if (s.Alo) r.emplace_back(s.Alo, (size_t)s.F * tri_stride(c->K) * sizeof(float2));
+    if (s.blo) r.emplace_back(s.blo, kf);
     if (s.Csf) r.emplace_back(s.Csf, (size_t)s.F * tri_stride(c->K) * sizeof(float4));
     r.emplace_back(s.dn, (size_t)s.F * sizeof(float));
   }

@@ -341,8 +341,8 @@ ocsc_status ocsc_server_create(ocsc_server **out, ocsc_ctx *c, const ocsc_server
 ocsc_status ocsc_server_submit(ocsc_server *s, uint64_t id, const float *x, int H, int W, float *u) {
   if (!s) return OCSC_EINVAL;
   if (!x || !u || H <= 0 || W <= 0) return fail(s->ctx, OCSC_EINVAL, "server_submit: bad arguments");
-  if (reinterpret_cast<uintptr_t>(u) % 8 != 0)
-    return fail(s->ctx, OCSC_EINVAL, "server_submit: the code buffer must be 8-byte aligned");
+  if (reinterpret_cast<uintptr_t>(u) % 16 != 0)
+    return fail(s->ctx, OCSC_EINVAL, "server_submit: the code buffer must be 16-byte aligned");
   const int k = class_of(s->ctx, H, W);
   if (k < 0) return fail(s->ctx, OCSC_EUNSUPPORTED, "server_submit: %dx%d maps to no FFT size of this context", H, W);
   Request r;
