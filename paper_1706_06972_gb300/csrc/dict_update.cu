@@ -185,36 +185,56 @@ __device__ __forceinline__ void fold_trail(float4 *M, int K, int j0, int nb, int
   }
 }
 
-// The same update over rectangle rows [r0, R) as one flat index space
-// u = (r - r0) (n + 1) + c shared by `nt` threads (index t), each stepping u by
-// nt with an incremental (r, c); every lane has an entry in every pass but the
-// last.  The middle row of an odd n has only its first part; the first parts
-// of rows r < skip (done elsewhere) are skipped.
-__device__ __forceinline__ void fold_trail_flat(float4 *M, int K, int j0, int nb, int r0, int t, int nt, int skip) {
-  const int j1 = j0 + nb, n = K - j1, R = (n + 1) / 2, W = n + 1;
-  if (r0 >= R) return;
-  int cq[kPanel];
+// The same rank-nb update over the trailing entries (ii, kk) with
+// o <= kk <= ii < n (local coordinates of the trailing triangle, whose first
+// row and column are j1 = j0 + nb), by 2 x 2 tiles of that sub-triangle:
+// tile (ti, tk), ti >= tk, holds rows o + 2 ti (+1) and columns o + 2 tk (+1),
+// and thread t of nt takes tiles t, t + nt, ... in packed lower-triangular
+// order (consecutive threads: consecutive row tiles of one column tile, whose
+// L values they share).  A tile loads the nb panel entries of its two rows
+// and two columns once for its (up to) four entries, and updates the four in
+// independent double-float chains.
+__device__ __forceinline__ void fold_trail_tiles(float4 *M, int K, int j0, int nb, int o, int t, int nt) {
+  const int j1 = j0 + nb, n = K - j1, m = n - o;
+  if (m <= 0) return;
+  const int mt = (m + 1) / 2, ntiles = mt * (mt + 1) / 2;
+  int cq[kPanel];  // cq[q] + ii: slot of L_{j1+ii, j0+q}
 #pragma unroll
   for (int q = 0; q < kPanel; ++q) cq[q] = q < nb ? tri_off(j0 + q, K) - j0 - q + j1 : 0;
-  const int total = (R - r0) * W, dr = nt / W, dc = nt % W;
-  int r = r0 + t / W, c = t % W;
-  for (int u = t; u < total; u += nt) {
-    const int cut = n - r;
-    if ((c < cut && r >= skip) || (c >= cut && 2 * r + 1 != n)) {
-      const bool first = c < cut;
-      const int kk = first ? r : n - 1 - r, ii = first ? r + c : c - 1;
-      const int dst = tri_off(j1 + kk, K) + ii - kk;
-      float4 lk[kPanel];
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int u = t; u < ntiles; u += nt) {
+    int ti, tk;
+    tri_ij(u, mt, ti, tk);
+    const int r0 = o + 2 * ti, c0 = o + 2 * tk;
+    const bool r1 = r0 + 1 < n, c1 = c0 + 1 < n;
+    const bool e01 = c1 && ti > tk;  // entry (r0, c0 + 1) lies below the diagonal
+    float4 lr0[kPanel], lr1[kPanel], lc0[kPanel], lc1[kPanel];
 #pragma unroll
-      for (int q = 0; q < kPanel; ++q) lk[q] = q < nb ? M[cq[q] + kk] : make_float4(0.f, 0.f, 0.f, 0.f);
-      M[dst] = trail_entry(M[dst], M, cq, ii, lk, nb);
+    for (int q = 0; q < kPanel; ++q) {
+      const bool ok = q < nb;
+      lr0[q] = ok ? M[cq[q] + r0] : zero;
+      lr1[q] = ok && r1 ? M[cq[q] + r0 + 1] : zero;
+      lc0[q] = ok ? M[cq[q] + c0] : zero;
+      lc1[q] = ok && c1 ? M[cq[q] + c0 + 1] : zero;
     }
-    c += dc;
-    r += dr;
-    if (c >= W) {
-      c -= W;
-      ++r;
+    const int s0 = tri_off(j1 + c0, K) + r0 - c0;          // (r0, c0); (r0 + 1, c0) follows it
+    const int s1 = c1 ? tri_off(j1 + c0 + 1, K) + r0 - c0 - 1 : 0;  // (r0, c0 + 1); (r0 + 1, c0 + 1) follows
+    float4 v00 = M[s0];
+    float4 v10 = r1 ? M[s0 + 1] : zero;
+    float4 v01 = e01 ? M[s1] : zero;
+    float4 v11 = r1 && c1 ? M[s1 + 1] : zero;
+#pragma unroll
+    for (int q = 0; q < kPanel; ++q) {
+      if (q >= nb) break;
+      df_sub_lconjm(v00, lr0[q], lc0[q]);
+      df_sub_lconjm(v10, lr1[q], lc0[q]);
+      df_sub_lconjm(v01, lr0[q], lc1[q]);
+      df_sub_lconjm(v11, lr1[q], lc1[q]);
     }
+    M[s0] = v00;
+    if (r1) M[s0 + 1] = v10;
+    if (e01) M[s1] = v01;
+    if (r1 && c1) M[s1 + 1] = v11;
   }
 }
 
@@ -282,7 +302,8 @@ __device__ __forceinline__ void fold_xpanel(float2 *XS, const float2 *Lb, const 
 //                  one double-float Newton step, column scaling, the update
 //                  inside the panel, y);
 //        warps 1.. apply panel b's update to the rest of the trailing triangle
-//                  (fold_trail) and run the forward substitution L X = I for
+//                  (fold_trail_tiles, 2 x 2 register tiles) and run the
+//                  forward substitution L X = I for
 //                  the pivots of panel b-1 (fold_xpanel), a warp per column of
 //                  X with its rows in registers.
 //      The trailing triangle is folded into a rectangle (row r: column r, then
@@ -482,7 +503,7 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
       __syncwarp();
       if (nb2 > 0) fold_panel(M, y, invf, Lb, K, b + 1, lane, a.err, rho_fb);
     } else {
-      if (!small) fold_trail_flat(M, K, j0, nb, 0, tid - 32, kFoldThreads - 32, rw);
+      if (!small) fold_trail_tiles(M, K, j0, nb, rw, tid - 32, kFoldThreads - 32);
       if (b >= 1) fold_xpanel(XS, Lb, invf, K, b - 1, warp - 1, nwarps - 1, lane);
     }
     __syncthreads();
