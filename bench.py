@@ -414,6 +414,28 @@ def hbm_entry(name, bytes_per_launch, avg_s, launches, peak, peak_note):
             "avg_ms": avg_s * 1e3, "launches": launches, "traffic": captured_traffic(name)}
 
 
+def persistent_leg(pkg, w, dev, stream, args):
+    """The headline step (mini-batch 64 on the headline workload) with the
+    persistent coder: the 50 code-ADMM iterations of each mini-batch in one
+    cooperative launch instead of 100 launches; images/s beside the headline's
+    per-iteration launches, on the same images."""
+    import torch
+
+    B, W, n = args.batch, 2, args.persistent_steps
+    xs = [torch.from_numpy(w.image(i)).to(dev) for i in range((W + n) * B)]
+    lr = make_learner(pkg, w, stream, B, persistent=1)
+    lr.set_dict(w.filters0(), normalize=True)
+    run_steps(lr, xs, B, 0, W)
+    lr.sync()
+    lr.profile(["persist"])
+    lr.profile_read(["persist"])
+    secs = event_time(stream, lambda: run_steps(lr, xs, B, W, n))
+    ms, launches = lr.profile_read(["persist"])["persist"]
+    lr.close()
+    return {"batch": B, "steps": n, "value": B * n / secs, "unit": UNIT, "ms_per_step": 1e3 * secs / n,
+            "persist_ms_per_launch": ms / max(launches, 1), "launches": launches}
+
+
 def fixed_objective_leg(pkg, w, dev, stream, args):
     """"At fixed objective" (Sec. IV's test objective on held-out images): a
     plain learner (mini-batch 1) trains on n images; its held-out objective is
@@ -450,40 +472,40 @@ def fixed_objective_leg(pkg, w, dev, stream, args):
 def mixed_leg(pkg, dev, stream, args):
     """Uneven sizes: images of side 64 / 128 / 256 padded by 10 to FFT 128 /
     256 / 512, K = 100 filters 11x11, mini-batches of 64 mixed images; one
-    learner with three size classes (consensus dictionary step)."""
+    learner with three size classes (consensus dictionary step).  Three ways of
+    issuing the coding of a mini-batch, timed on the same batches: per-iteration
+    launches, the same replayed from CUDA graphs, and the persistent coder (all
+    Jz iterations of the mini-batch in one cooperative launch)."""
     import torch
     from workloads import WORKLOADS
 
     w = WORKLOADS["batched_mixed_k100"]
     B = w.batch
-    learner = pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_sizes=[128, 256, 512], pad=w.pad,
-                       Jz=w.Jz, Jd=w.Jd, max_batch=B)
-    learner.set_dict(w.filters0(), normalize=True)
     nb = args.mixed_steps
-    xs = [torch.from_numpy(w.image(i)).to(dev) for i in range(B * (nb + 1))]
+    xs = [torch.from_numpy(w.image(i)).to(dev) for i in range(B * (nb + 2))]
     sides = [int(x.shape[0]) for x in xs]
-    learner.code(xs[:B], want_codes=False)
-    learner.update_dict()
-    learner.sync()
-    kinds = ["image_spectrum", "code_resid", "code_plane", "fold_factor", "dstep"]
-    learner.profile(kinds)
-    learner.profile_read(kinds)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for t in range(1, nb + 1):
-        learner.code(xs[t * B:(t + 1) * B], want_codes=False)
-        learner.update_dict()
-    e1.record(stream)
-    e1.synchronize()
-    secs = e0.elapsed_time(e1) / 1e3
-    prof = learner.profile_read(kinds)
-    learner.close()
-    timed = sides[B:]
-    return {"workload": "batched_mixed_k100", "batch": B, "steps": nb, "value": B * nb / secs, "unit": UNIT,
-            "ms_per_batch": 1e3 * secs / nb,
-            "sides_in_timed_batches": {str(sd): timed.count(sd) for sd in sorted(set(timed))},
-            "ms_per_batch_by_kernel": {k: v[0] / nb for k, v in prof.items()}}
+    kinds = ["image_spectrum", "code_resid", "code_plane", "fold_factor", "dstep", "persist"]
+    out = {"workload": "batched_mixed_k100", "batch": B, "steps": nb}
+    for name, opts in (("per_iteration", {}), ("graphs", {"graphs": 1}), ("persistent", {"persistent": 1})):
+        learner = pkg.OCSC(w.K, w.M, w.lam, w.rho, stream=stream, fft_sizes=[128, 256, 512], pad=w.pad,
+                           Jz=w.Jz, Jd=w.Jd, max_batch=B, **opts)
+        learner.set_dict(w.filters0(), normalize=True)
+        for t in range(2):   # the second batch captures the graphs of the graph variant
+            learner.code(xs[t * B:(t + 1) * B], want_codes=False)
+            learner.update_dict()
+        learner.sync()
+        if name != "graphs":
+            learner.profile(kinds)
+            learner.profile_read(kinds)
+        secs = event_time(stream, lambda: run_steps(learner, xs, B, 2, nb))
+        prof = learner.profile_read(kinds) if name != "graphs" else {}
+        learner.close()
+        out[name] = {"value": B * nb / secs, "unit": UNIT, "ms_per_batch": 1e3 * secs / nb,
+                     "ms_per_batch_by_kernel": {k: v[0] / nb for k, v in prof.items() if v[1]}}
+    timed = sides[2 * B:]
+    out["value"] = out["persistent"]["value"]
+    out["sides_in_timed_batches"] = {str(sd): timed.count(sd) for sd in sorted(set(timed))}
+    return out
 
 
 def precision_leg(pkg, dev, stream, args):
@@ -775,6 +797,7 @@ def ours_arm(args):
     legs = set(args.legs.split(","))
     plain = plain_leg(pkg, w, dev, stream, args) if "plain" in legs and args.plain_steps > 0 else None
     fixed = fixed_objective_leg(pkg, w, dev, stream, args) if "fixed" in legs and args.quality_images > 0 else None
+    persist = persistent_leg(pkg, w, dev, stream, args) if "persistent" in legs and args.persistent_steps > 0 else None
     mixed = mixed_leg(pkg, dev, stream, args) if args.mixed_steps > 0 and "mixed" in legs else None
     serving = serving_leg(pkg, dev, stream, args) if args.serve_requests > 0 and "serving" in legs else None
     precision = precision_leg(pkg, dev, stream, args) if args.precision_steps > 0 and "precision" in legs else None
@@ -822,6 +845,7 @@ def ours_arm(args):
         "plain_path": plain,
         "vs_plain_path": (value / plain["value"]) if plain else None,
         "fixed_objective": fixed,
+        "persistent_coder": persist,
         "rooflines": rooflines,
         "kernel_breakdown": breakdown,
         "mixed_sizes": mixed,
@@ -901,7 +925,9 @@ def main():
                     help="timed batches of 128 per variant in the precision leg (0: skip)")
     ap.add_argument("--recursion-steps", type=int, default=40,
                     help="timed samples of each history variant in the recursion leg (0: skip)")
-    ap.add_argument("--legs", default="plain,fixed,mixed,serving,precision,recursion",
+    ap.add_argument("--persistent-steps", type=int, default=10,
+                    help="timed mini-batches of the persistent-coder leg (0: skip)")
+    ap.add_argument("--legs", default="plain,fixed,persistent,mixed,serving,precision,recursion",
                     help="comma list of the extra legs to run besides the headline")
     ap.add_argument("--mixed-steps", type=int, default=2,
                     help="timed batches of the uneven-size leg (0: skip)")

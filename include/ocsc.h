@@ -137,6 +137,16 @@ typedef struct {
                          already has a condition number near |z|^2 / rho and
                          the rank-one downdates diverge, in FP64 too), one FFT
                          size, precision 0 and K <= 128. */
+  int persistent;     /* 1: ocsc_code runs all Jz iterations of the images of
+                         FFT sizes 64, 128, 256 and 512 in one cooperative
+                         launch per chunk of up to 64 images (sizes may be
+                         mixed in one launch), after their sample spectra:
+                         every CTA of a co-resident grid walks the units of
+                         the per-iteration kernels, three intervals per
+                         iteration separated by a bounded grid barrier.  Codes
+                         are identical to those of the per-iteration launches.
+                         Other sizes take the per-iteration path.  0 (default):
+                         per-iteration launches. */
 } ocsc_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -391,8 +401,9 @@ typedef enum {
   OCSC_K_VSTEP_PROJECT = 6,  /* Proposition 2 projection of the support */
   OCSC_K_DICT_NORMS = 7,     /* |D~(p,:)|^2 of the coding dictionary */
   OCSC_K_VSTEP_SPECTRUM = 8, /* V^ = F(pad V) and the dual update */
-  OCSC_K_HISTORY_TC = 9,     /* tensor-core history fold (opts.precision > 0) */
-  OCSC_K_COUNT = 10
+  OCSC_K_HISTORY_TC = 9,     /* tensor-core history fold (opts.precision 1 or 2) */
+  OCSC_K_PERSIST = 10,       /* persistent coder: all Jz iterations of a chunk (opts.persistent) */
+  OCSC_K_COUNT = 11
 } ocsc_kernel;
 
 typedef struct {

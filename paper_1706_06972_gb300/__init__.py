@@ -38,7 +38,7 @@ class ocsc_opts(ctypes.Structure):
         ("max_batch", ctypes.c_int), ("fft_sizes", ctypes.c_int * MAX_FFT_SIZES), ("warm_start", ctypes.c_int),
         ("return_feasible", ctypes.c_int), ("rho_convention", ctypes.c_int),
         ("seed", ctypes.c_uint64), ("precision", ctypes.c_int), ("autotune", ctypes.c_int),
-        ("graphs", ctypes.c_int), ("history", ctypes.c_int),
+        ("graphs", ctypes.c_int), ("history", ctypes.c_int), ("persistent", ctypes.c_int),
     ]
 
 
@@ -63,7 +63,7 @@ class ocsc_served(ctypes.Structure):
 
 
 KERNELS = ("image_spectrum", "code_resid", "code_plane", "fold_factor", "dstep", "vstep_cols",
-           "vstep_project", "dict_norms", "vstep_spectrum", "history_tc")
+           "vstep_project", "dict_norms", "vstep_spectrum", "history_tc", "persist")
 
 _P = ctypes.c_void_p
 _I = ctypes.c_int

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libocsc.so")
 SOURCES = ["code_admm.cu", "code_large.cu", "dict_update.cu", "objective.cu", "ocsc_api.cu", "serve.cu",
-           "noalloc.cu", "history_tc.cu", "dict_big.cu", "dict_sm.cu"]
+           "noalloc.cu", "history_tc.cu", "dict_big.cu", "dict_sm.cu", "persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -76,6 +76,7 @@ struct ocsc_ctx {
   double *obj_part = nullptr;
   double *obj_out = nullptr;
   int *err = nullptr;       // device error word
+  unsigned *bar = nullptr;  // [2] grid barrier of the persistent coder
   int *order = nullptr;     // [K] filter order (ocsc_filter_order)
   unsigned wait_polls = ocsc::kWaitPolls;  // polls of a bounded device wait before it gives up
   double2 *work = nullptr;  // K > 128: FP64 factorisation workspace, one matrix per persistent CTA

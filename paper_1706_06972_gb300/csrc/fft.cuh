@@ -319,7 +319,7 @@ __device__ __forceinline__ void half_pass(float2 *__restrict__ buf, const float2
 
 // Radix plans of the half-spectrum tile: columns (length N) and rows (N/2).
 template <int N> struct HalfPlan;
-template <> struct HalfPlan<64> { static constexpr int C0 = 8, C1 = 8, R0 = 8, R1 = 4, NT = 128; };
+template <> struct HalfPlan<64> { static constexpr int C0 = 8, C1 = 8, R0 = 8, R1 = 4, NT = 256; };
 template <> struct HalfPlan<128> { static constexpr int C0 = 16, C1 = 8, R0 = 8, R1 = 8, NT = 256; };
 
 // Transform of the N/2 columns k2 < N/2 (length N, along k1); column N/2 is

@@ -199,6 +199,40 @@ cudaError_t launch_objective(int K, int N, double lam, const float2 *Dh, const f
 cudaError_t launch_rel_diff(const float *a, const float *b, size_t count, double *partial, double *out,
                             cudaStream_t s);
 
+// Persistent coder (persist.cu): all Jz code-ADMM iterations of up to
+// kMaxCallImages images of FFT sizes 64, 128, 256 and 512 in one cooperative
+// launch.  Per iteration three intervals of units separated by a grid
+// barrier: (A) the residual r of the Z~-step (N <= 128) and the partial sums
+// D^T w^ (N >= 256, not on the first iteration); (B) the plane iteration
+// (N <= 128) and the row inverse of conj(d) r (N >= 256); (C) the spatial
+// column step (N >= 256).  Every unit is the body of the corresponding
+// per-iteration kernel, so the results are those of the launches it replaces.
+constexpr int kMaxPersistClasses = 4;
+constexpr int kPersistThreads = 256;
+struct PersistClass {
+  int N;           // FFT side (64, 128, 256 or 512)
+  int n0, n;       // images n0 .. n0 + n - 1 of PersistArgs::b
+  int S;           // N >= 256: stages of filter pairs of the spectral units
+  int cb;          // N >= 256: columns per spatial unit (8 or 16)
+  CodeIter it;     // the class's workspaces (first / last are set per iteration)
+  LargeIO io;      // N >= 256: the pair tiles
+  const float2 *tw;
+};
+struct PersistArgs {
+  ImgBatch b;
+  int ncls, Jz, K;
+  PersistClass c[kMaxPersistClasses];
+  unsigned *bar;   // [2] arrivals and generation of the grid barrier, zero at launch
+  int *err;        // device error word: ERR_TIMEOUT when a barrier wait gave up
+  unsigned polls;  // polls of one barrier wait
+};
+bool persist_size_ok(int N);
+size_t persist_smem_bytes(const PersistArgs &a);
+// CTAs of one cooperative launch with `smem` bytes of dynamic shared memory
+// (all co-resident), or a negative CUDA error.
+int persist_grid(size_t smem);
+cudaError_t launch_persist(const PersistArgs &a, int grid, size_t smem, cudaStream_t s);
+
 // PSNR of Sec. IV from the objective terms of n samples (terms [n][3], the
 // squared residual norm at [3 i + 1]).
 constexpr int kMaxPsnr = 64;

@@ -88,7 +88,11 @@ ocsc_status check_device(ocsc_ctx *c) {
   }
   if (h & ERR_TIMEOUT) {
     cudaMemset(c->err, 0, sizeof(int));
-    return fail(c, OCSC_ETIMEOUT, "a tensor-core history fold gave up waiting for its MMAs");
+    // A persistent launch that gave up may have left the arrival counters of
+    // the N >= 256 spectral units part-way; they must start at zero.
+    for (SizeClass &s : c->cls)
+      if (s.cnt) cudaMemset(s.cnt, 0, (size_t)c->opts.max_batch * (s.N / 2) * sizeof(int));
+    return fail(c, OCSC_ETIMEOUT, "a bounded device wait gave up (tensor-core history fold or persistent coder barrier)");
   }
   return OCSC_OK;
 }
@@ -172,6 +176,7 @@ void ocsc_default_opts(ocsc_opts *o) {
   o->autotune = 1;
   o->graphs = 0;
   o->history = 0;
+  o->persistent = 0;
   o->seed = 0x5EEDull;
 }
 
@@ -264,7 +269,7 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
     c->work_ctas = sms;
     if ((st = dalloc(c, &c->work, factor_big_workspace(K, sms)))) return bail(st);
   }
-  if ((st = dalloc(c, &c->V, (size_t)K * c->M * c->M)) || (st = dalloc(c, &c->Dpub, (size_t)K * c->M * c->M)) || (st = dalloc(c, &c->err, 1)) ||
+  if ((st = dalloc(c, &c->V, (size_t)K * c->M * c->M)) || (st = dalloc(c, &c->Dpub, (size_t)K * c->M * c->M)) || (st = dalloc(c, &c->err, 1)) || (st = dalloc(c, &c->bar, 2)) ||
       (st = dalloc(c, &c->obj_part, (size_t)std::max(max_partials, 2 * kObjL1Blocks))) ||
       (st = dalloc(c, &c->obj_out, (size_t)4 * kObjChunk)) || (st = dalloc(c, &c->order, (size_t)K)))
     return bail(st);
@@ -291,11 +296,11 @@ ocsc_status ocsc_padded_size(const ocsc_ctx *ctx, int H, int W, int *N) {
 
 // Enqueue the coding of one chunk of images of one class (sample spectra and
 // Jz ADMM iterations) for the images, outputs and slots in bt.
-static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) {
-  const int npairs = (c->K + 1) / 2;
+// Sample spectra x~ = F(pad x) of the images in bt into their slots.
+static ocsc_status enqueue_spectra(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) {
   LargeIO io{};
   io.T = s.tiles;
-  io.tile_pairs = npairs;
+  io.tile_pairs = (c->K + 1) / 2;
   cudaError_t e;
   if (large_fft(s.N)) {
     io.spec_out = s.xhp;
@@ -306,7 +311,11 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
   } else {
     e = timed(c, OCSC_K_IMAGE_SPECTRUM, [&] { return launch_image_spectrum(s.N, bt, s.tw, s.xhp, c->stream); });
   }
-  if (e != cudaSuccess) return cuda_fail(c, e, "image spectrum");
+  return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "image spectrum");
+}
+
+// Code-ADMM parameters and workspaces of a class (batch mode).
+static CodeIter class_iter(const ocsc_ctx *c, const SizeClass &s) {
   CodeIter it{};
   it.K = c->K;
   it.F = s.F;
@@ -323,6 +332,18 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
   it.xh = s.xhp;
   it.part = s.part;
   it.cnt = s.cnt;
+  return it;
+}
+
+static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) {
+  const int npairs = (c->K + 1) / 2;
+  LargeIO io{};
+  io.T = s.tiles;
+  io.tile_pairs = npairs;
+  cudaError_t e;
+  ocsc_status sst = enqueue_spectra(c, s, bt);
+  if (sst != OCSC_OK) return sst;
+  CodeIter it = class_iter(c, s);
   if (large_fft(s.N)) {
     if (s.spat_cb == 0) {
       s.spat_cb = large_default_cb(s.N);
@@ -494,6 +515,82 @@ static ocsc_status code_class(ocsc_ctx *c, SizeClass &s, const std::vector<int> 
   return OCSC_OK;
 }
 
+// Persistent path: the images of the classes in pcls (each of FFT size 64,
+// 128, 256 or 512), in chunks of at most kMaxCallImages ordered by class; per
+// chunk the sample spectra of each class, then one cooperative launch running
+// all Jz iterations of every image of the chunk.
+static ocsc_status code_persistent(ocsc_ctx *c, const std::vector<int> &pcls,
+                                   const std::vector<std::vector<int>> &groups, const float *const *x,
+                                   const int *H, const int *W, float *const *u) {
+  std::vector<std::pair<int, int>> all;  // (class, image index)
+  for (int k : pcls) {
+    SizeClass &s = c->cls[k];
+    ocsc_status st = ensure_code_ws(c, s);
+    if (st != OCSC_OK) return st;
+    if (large_fft(s.N) && s.spat_cb == 0) s.spat_cb = large_default_cb(s.N);
+    for (int j : groups[k]) all.emplace_back(k, j);
+  }
+  std::vector<int> used(c->cls.size(), 0);
+  for (size_t s0 = 0; s0 < all.size(); s0 += kMaxCallImages) {
+    const int m = (int)std::min<size_t>(kMaxCallImages, all.size() - s0);
+    PersistArgs pa{};
+    pa.b.n = m;
+    pa.Jz = c->opts.Jz;
+    pa.K = c->K;
+    pa.bar = c->bar;
+    pa.err = c->err;
+    pa.polls = c->wait_polls;
+    for (int i = 0; i < m; ++i) {
+      const int k = all[s0 + i].first, j = all[s0 + i].second;
+      SizeClass &s = c->cls[k];
+      pa.b.x[i] = x[j];
+      pa.b.u[i] = u ? u[j] : nullptr;
+      pa.b.H[i] = H[j];
+      pa.b.W[i] = W[j];
+      pa.b.slot[i] = s.pending + used[k]++;
+      pa.b.iter[i] = 0;
+      if (pa.ncls == 0 || pa.c[pa.ncls - 1].N != s.N) {
+        PersistClass &pc = pa.c[pa.ncls++];
+        pc.N = s.N;
+        pc.n0 = i;
+        pc.n = 0;
+        pc.it = class_iter(c, s);
+        pc.tw = s.tw;
+        pc.io.T = s.tiles;
+        pc.io.tile_pairs = (c->K + 1) / 2;
+        pc.io.spat_cb = s.spat_cb;
+        pc.cb = s.spat_cb;
+        pc.S = large_fft(s.N) ? large_stages(s.N, (c->K + 1) / 2) : 0;
+      }
+      pa.c[pa.ncls - 1].n++;
+    }
+    for (int q = 0; q < pa.ncls; ++q) {
+      const PersistClass &pc = pa.c[q];
+      ImgBatch bt{};
+      bt.n = pc.n;
+      for (int i = 0; i < pc.n; ++i) {
+        bt.x[i] = pa.b.x[pc.n0 + i];
+        bt.u[i] = pa.b.u[pc.n0 + i];
+        bt.H[i] = pa.b.H[pc.n0 + i];
+        bt.W[i] = pa.b.W[pc.n0 + i];
+        bt.slot[i] = pa.b.slot[pc.n0 + i];
+      }
+      SizeClass *sp = nullptr;
+      for (SizeClass &sc : c->cls)
+        if (sc.N == pc.N) sp = &sc;
+      ocsc_status st = enqueue_spectra(c, *sp, bt);
+      if (st != OCSC_OK) return st;
+    }
+    const size_t smem = persist_smem_bytes(pa);
+    const int grid = persist_grid(smem);
+    if (grid <= 0) return cuda_fail(c, grid < 0 ? (cudaError_t)(-grid) : cudaErrorInvalidConfiguration, "persistent coder occupancy");
+    cudaError_t e = timed(c, OCSC_K_PERSIST, [&] { return launch_persist(pa, grid, smem, c->stream); });
+    if (e != cudaSuccess) return cuda_fail(c, e, "persistent coder launch");
+  }
+  for (int k : pcls) c->cls[k].pending += (int)groups[k].size();
+  return OCSC_OK;
+}
+
 ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, const int *W,
                       float *const *u) {
   if (!c) return OCSC_EINVAL;
@@ -514,9 +611,18 @@ ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, c
     if (c->cls[k].pending + (int)groups[k].size() > c->opts.max_batch)
       return fail(c, OCSC_ESTATE, "ocsc_code: %d pending + %d new samples of size %d exceed max_batch %d; "
                   "call ocsc_update_dict", c->cls[k].pending, (int)groups[k].size(), c->cls[k].N, c->opts.max_batch);
+  std::vector<int> pcls;  // classes coded by the persistent launch
   for (size_t k = 0; k < groups.size(); ++k) {
     if (groups[k].empty()) continue;
+    if (c->opts.persistent && persist_size_ok(c->cls[k].N)) {
+      pcls.push_back((int)k);
+      continue;
+    }
     ocsc_status st = code_class(c, c->cls[k], groups[k], x, H, W, u);
+    if (st != OCSC_OK) return st;
+  }
+  if (!pcls.empty()) {
+    ocsc_status st = code_persistent(c, pcls, groups, x, H, W, u);
     if (st != OCSC_OK) return st;
   }
   c->counters.samples_coded += n;

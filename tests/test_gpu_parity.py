@@ -845,3 +845,79 @@ def test_recursion_history_rejects_unsupported_setups():
     with pytest.raises(pkg.OCSCError) as e:
         pkg.OCSC(8, 5, 0.5, 1.0, fft_size=64, history=1)
     assert e.value.status == 6
+
+
+# --- persistent coder: all Jz iterations in one cooperative launch ------------------
+
+def _mixed_run(pkg, persistent, sides, K=11, Jz=6, Jd=3, wait_polls=None):
+    M = 5
+    lr = pkg.OCSC(K, M, 0.3, 1.0, fft_sizes=[64, 128, 256, 512], pad=10, Jz=Jz, Jd=Jd, max_batch=len(sides),
+                  persistent=persistent)
+    lr.set_dict(raw_filters(K, M, 2400), normalize=True)
+    imgs = [torch.from_numpy(make_image(s, s, 2410 + i)).cuda() for i, s in enumerate(sides)]
+    if wait_polls is not None:
+        lr.set_wait_limit(wait_polls)
+    us = lr.code(imgs)
+    return lr, imgs, us
+
+
+def test_persistent_coder_equals_per_iteration_launches():
+    """Images of FFT sizes 64, 128, 256 and 512 coded in one cooperative launch
+    per chunk give the same codes, bit for bit, as the per-iteration kernels
+    (the launch runs their bodies as units), and the same dictionary after the
+    update; odd K exercises the unpaired last filter."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    sides = [40, 100, 200, 60, 400, 110]
+    a, _, ua = _mixed_run(pkg, 0, sides)
+    b, _, ub = _mixed_run(pkg, 1, sides)
+    for x, y in zip(ua, ub):
+        assert torch.equal(x, y)
+    a.update_dict()
+    b.update_dict()
+    assert np.array_equal(a.get_dict(), b.get_dict())
+    assert b.counters()["kernel_launches"] < a.counters()["kernel_launches"]
+    a.close()
+    b.close()
+
+
+def test_persistent_coder_matches_oracle_on_mixed_sizes():
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    sides = [50, 110, 230, 420]
+    K, M, Jz = 11, 5, 8
+    lr, imgs, us = _mixed_run(pkg, 1, sides, K=K, Jz=Jz)
+    D = oracle.normalize_filters(raw_filters(K, M, 2400).astype(np.float64))
+    for im, u in zip(imgs, us):
+        N = u.shape[-1]
+        o = oracle.code_admm(oracle.pad_to(im.cpu().numpy().astype(np.float64), N, N),
+                             oracle.filters_spectrum(D, N, N), 0.3, 1.0, Jz)
+        assert_close(u.cpu().numpy(), o.U, f"persistent N={N}", CODE_ELEM_TOL, CODE_PLANE_TOL)
+    lr.close()
+
+
+def test_persistent_barrier_timeout_is_reported_and_context_recovers():
+    """The grid barrier waits with a bounded poll loop.  With the poll budget
+    at 0 a CTA that arrives before the last one gives up at once, records the
+    timeout and returns, and every other CTA returns at its next barrier; the
+    next synchronising call reports OCSC_ETIMEOUT.  With the default budget the
+    same context codes again, and its codes equal a fresh context's."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    sides = [100, 200]
+    lr, imgs, _ = _mixed_run(pkg, 1, sides, wait_polls=0)
+    with pytest.raises(pkg.OCSCError) as e:
+        lr.sync()
+    assert e.value.status == 4
+    lr.drop_pending()
+    lr.set_wait_limit(1 << 24)
+    us = lr.code(imgs)
+    lr.sync()
+    ref, _, ur = _mixed_run(pkg, 1, sides)
+    for x, y in zip(us, ur):
+        assert torch.equal(x, y)
+    lr.close()
+    ref.close()
