@@ -214,7 +214,7 @@ struct PersistClass {
   int n0, n;       // images n0 .. n0 + n - 1 of PersistArgs::b
   int S;           // N >= 256: stages of filter pairs of the spectral units
   int cb;          // N >= 256: columns per spatial unit (8 or 16)
-  CodeIter it;     // the class's workspaces (first / last are set per iteration)
+  CodeIter it[3];  // the class's workspaces, for the first, a middle and the last iteration
   LargeIO io;      // N >= 256: the pair tiles
   const float2 *tw;
 };

@@ -554,7 +554,11 @@ static ocsc_status code_persistent(ocsc_ctx *c, const std::vector<int> &pcls,
         pc.N = s.N;
         pc.n0 = i;
         pc.n = 0;
-        pc.it = class_iter(c, s);
+        for (int v = 0; v < 3; ++v) {
+          pc.it[v] = class_iter(c, s);
+          pc.it[v].first = v == 0;
+          pc.it[v].last = v == 2 || c->opts.Jz == 1;
+        }
         pc.tw = s.tw;
         pc.io.T = s.tiles;
         pc.io.tile_pairs = (c->K + 1) / 2;

@@ -120,9 +120,7 @@ __global__ void __launch_bounds__(kPersistThreads, 2) code_persist_kernel(const 
         int c = 0, v = u;
         while (v >= cnt[c]) v -= cnt[c++];
         const PersistClass &pc = a.c[c];
-        CodeIter it = pc.it;
-        it.first = t == 0;
-        it.last = t == a.Jz - 1;
+        const CodeIter &it = pc.it[t == 0 ? 0 : (t == a.Jz - 1 ? 2 : 1)];
         __syncthreads();  // the previous unit's shared memory is free
         switch (pc.N) {
           case 64: small_unit<64>(a, pc, it, phase, v, psm); break;
