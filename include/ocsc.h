@@ -147,6 +147,14 @@ typedef struct {
                          are identical to those of the per-iteration launches.
                          Other sizes take the per-iteration path.  0 (default):
                          per-iteration launches. */
+  int band_lo, band_hi; /* 0, 0 (default): the context solves every frequency.
+                         0 <= band_lo < band_hi <= N (one FFT size, an even row
+                         count): a band context, which keeps the history and
+                         factor of the frequencies of rows k1 in
+                         [band_lo, band_hi) only and updates its dictionary
+                         through the ocsc_band_* calls (frequency-band
+                         sharding of the dictionary step).  Needs history 0,
+                         precision 0 or 3, K <= 128, return_feasible 1. */
 } ocsc_opts;
 
 /* Fill *o with the defaults listed above. */
@@ -327,6 +335,50 @@ ocsc_status ocsc_copy_dict(ocsc_ctx *ctx, float *D_dev);
  * history of an update that timed out is left as it was before the update.
  */
 ocsc_status ocsc_set_wait_limit(ocsc_ctx *ctx, uint64_t polls);
+
+/*
+ * Frequency-band sharding of the dictionary step.  Proposition 1 (Sec. III-B)
+ * decouples the D-row systems of eq. (sub_d_sol) per frequency, so the
+ * history, its factorisation and the D~-step split by frequency band; only the
+ * V-step of Proposition 2 couples the bands, through the support crop
+ * H(F^-1(D~ + theta^)), which is a sum over frequencies.  With G contexts (one
+ * per GPU, each a band context owning rows [band_lo, band_hi) of k1; the bands
+ * cover 0 .. N once) one update of Algorithm 2 is:
+ *   1. every context codes its own samples (ocsc_code) and exports each band's
+ *      rows of their Z~ and x~ (ocsc_band_export); the caller moves them to the
+ *      band owners (an all-to-all) and concatenates them in one global sample
+ *      order (the order of the fold);
+ *   2. every context folds the B samples of the mini-batch into its band and
+ *      factors it (ocsc_band_fold);
+ *   3. Jd times: ocsc_band_dict_step writes the band's share of the support
+ *      sums alpha (K x M x M floats); the caller adds the G shares in a fixed
+ *      order (an all-reduce of K M^2 floats) and passes the sum to every
+ *      context's ocsc_band_project (last = 1 on the last iteration, which also
+ *      publishes the new dictionary and its coding spectrum);
+ *   4. every context drops its pending samples (ocsc_drop_pending).
+ * All contexts then hold the same filters D_t.  All calls are asynchronous on
+ * the context's stream; Z_dev, x_dev, alpha_dev are DEVICE buffers owned by the
+ * caller.  Errors: OCSC_ESTATE when ctx is not a band context (band_fold,
+ * band_dict_step, band_project) or nothing has been folded yet
+ * (band_dict_step); OCSC_EINVAL for bad arguments.
+ *
+ * ocsc_band_export: the pending samples' Z~ rows k1 in [k1_lo, k1_hi) as
+ *   [pending][K][(k1_hi - k1_lo)(N/2 + 1)] complex floats (interleaved) into
+ *   Z_dev, their x~ rows as [pending][(k1_hi - k1_lo)(N/2 + 1)] into x_dev.
+ *   Any context may export any band.
+ * ocsc_band_fold: fold B samples, given in that layout for this context's
+ *   band, in order (eqs. (A_update), (B_update), the running mean over all
+ *   samples seen), then factor the band (eq. (sub_d_sol)).
+ * ocsc_band_dict_step: the D~-step of the band, then alpha_dev[k][m1][m2] =
+ *   (1/P) sum over the band's frequencies of the inverse-DFT terms of
+ *   D~ + theta^ on the M x M support.
+ * ocsc_band_project: V = Proposition 2 of alpha_dev, then V^ = F(pad V) and
+ *   the scaled dual on the band.
+ */
+ocsc_status ocsc_band_export(ocsc_ctx *ctx, int k1_lo, int k1_hi, float *Z_dev, float *x_dev);
+ocsc_status ocsc_band_fold(ocsc_ctx *ctx, int B, const float *Z_dev, const float *x_dev);
+ocsc_status ocsc_band_dict_step(ocsc_ctx *ctx, float *alpha_dev);
+ocsc_status ocsc_band_project(ocsc_ctx *ctx, const float *alpha_dev, int last);
 
 /*
  * Serving: continuous batching of coding requests over one context

@@ -39,6 +39,7 @@ class ocsc_opts(ctypes.Structure):
         ("return_feasible", ctypes.c_int), ("rho_convention", ctypes.c_int),
         ("seed", ctypes.c_uint64), ("precision", ctypes.c_int), ("autotune", ctypes.c_int),
         ("graphs", ctypes.c_int), ("history", ctypes.c_int), ("persistent", ctypes.c_int),
+        ("band_lo", ctypes.c_int), ("band_hi", ctypes.c_int),
     ]
 
 
@@ -106,6 +107,10 @@ _PROTOS = {
     "ocsc_filter_order": (_I, [_P, ctypes.POINTER(_I)]),
     "ocsc_copy_dict": (_I, [_P, _P]),
     "ocsc_set_wait_limit": (_I, [_P, ctypes.c_uint64]),
+    "ocsc_band_export": (_I, [_P, _I, _I, _P, _P]),
+    "ocsc_band_fold": (_I, [_P, _I, _P, _P]),
+    "ocsc_band_dict_step": (_I, [_P, _P]),
+    "ocsc_band_project": (_I, [_P, _P, _I]),
     "ocsc_code_noalloc": (_I, [_P, _I, _I, _P, _I, _I, _I, ctypes.c_double, ctypes.c_double, _I, _P,
                                _P, ctypes.c_char_p, ctypes.c_size_t]),
 }
@@ -439,6 +444,44 @@ class OCSC:
             out = torch.empty((self.K, self.M, self.M), device="cuda", dtype=torch.float32)
         ocsc_copy_dict(self.ctx, out.data_ptr())
         return out
+
+    # --- frequency-band sharding of the dictionary step (see bands.py) ---------
+
+    def band_rows(self):
+        """(k1_lo, k1_hi) of this band context."""
+        return self.opts.band_lo, self.opts.band_hi
+
+    def band_export(self, k1_lo: int, k1_hi: int, n: int):
+        """The n pending samples' Z~ and x~ rows k1 in [k1_lo, k1_hi) as complex64
+        CUDA tensors [n, K, rows * (N/2+1)] and [n, rows * (N/2+1)]."""
+        torch = self._torch
+        fb = (k1_hi - k1_lo) * (self.N // 2 + 1)
+        Z = torch.empty((n, self.K, fb), device="cuda", dtype=torch.complex64)
+        x = torch.empty((n, fb), device="cuda", dtype=torch.complex64)
+        _check(self.ctx, lib().ocsc_band_export(self.ctx, k1_lo, k1_hi, ctypes.c_void_p(Z.data_ptr()),
+                                                ctypes.c_void_p(x.data_ptr())))
+        return Z, x
+
+    def band_fold(self, Z, x):
+        """Fold a mini-batch's band rows (global sample order) and factor the band."""
+        Z = Z.contiguous()
+        x = x.contiguous()
+        self._keep_band = (Z, x)
+        _check(self.ctx, lib().ocsc_band_fold(self.ctx, Z.shape[0], ctypes.c_void_p(Z.data_ptr()),
+                                              ctypes.c_void_p(x.data_ptr())))
+
+    def band_dict_step(self, out=None):
+        """The band's share of the support sums alpha [K, M, M] (float32 CUDA)."""
+        torch = self._torch
+        if out is None:
+            out = torch.empty((self.K, self.M, self.M), device="cuda", dtype=torch.float32)
+        _check(self.ctx, lib().ocsc_band_dict_step(self.ctx, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def band_project(self, alpha, last: bool):
+        alpha = alpha.contiguous()
+        self._keep_alpha = alpha
+        _check(self.ctx, lib().ocsc_band_project(self.ctx, ctypes.c_void_p(alpha.data_ptr()), int(last)))
 
     def set_wait_limit(self, polls: int):
         """Poll budget of the bounded device waits (failure-path tests)."""

@@ -16,6 +16,7 @@ namespace ocsc {
 
 struct SizeClass {
   int N = 0, NH = 0, F = 0, P = 0;
+  int p0 = 0, Fb = 0;       // frequencies p0 .. p0 + Fb - 1 of the history (a band context: its band)
   float2 *tw = nullptr;     // [N] twiddles
   // dictionary state in this class's frequency grid
   float2 *Vh = nullptr;     // [K][F] F(pad V)

@@ -359,7 +359,10 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   float2 *xs = zs + kFoldChunk * K;                              // [kFoldChunk]
   float2 *S = reinterpret_cast<float2 *>(M);                     // FP32 sums, stride 2
   float2 *XS = reinterpret_cast<float2 *>(M);                    // X_ic at slot t: XS[2 t]
-  const int p = blockIdx.x;
+  // Frequency p of the class's grid (a band context factors rows p0 .. of
+  // its own band; its history and factor arrays hold the band only).
+  const int p = blockIdx.x + a.p0, pl = blockIdx.x;
+  const int zF = a.zF ? a.zF : F, zp = p - a.zp0;
   const int tid = threadIdx.x;
 
   constexpr int MR = (128 + kFoldThreads - 1) / kFoldThreads;
@@ -380,9 +383,9 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
     __syncthreads();
     for (int e = tid; e < nb * K; e += kFoldThreads) {
       const int s = e / K, k = e % K;
-      zs[s * K + k] = a.Zp[((size_t)(c0 + s) * K + k) * F + p];
+      zs[s * K + k] = a.Zp[((size_t)(c0 + s) * K + k) * zF + zp];
     }
-    for (int s = tid; s < nb; s += kFoldThreads) xs[s] = a.xh[(size_t)(c0 + s) * F + p];
+    for (int s = tid; s < nb; s += kFoldThreads) xs[s] = a.xh[(size_t)(c0 + s) * zF + zp];
     __syncthreads();
     for (int t = tid; t < T; t += kFoldThreads) {
       int i, j;
@@ -412,9 +415,9 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
 
   // 2. Running means in FP32 (stored), and M = w A + rho I, y = w b in
   //    double-float.
-  float2 *Ap = a.A + (size_t)p * tri_stride(K);
+  float2 *Ap = a.A + (size_t)pl * tri_stride(K);
   const float alpha = (float)a.alpha, beta = (float)a.beta;
-  float2 *Lo = a.Alo ? a.Alo + (size_t)p * tri_stride(K) : nullptr;
+  float2 *Lo = a.Alo ? a.Alo + (size_t)pl * tri_stride(K) : nullptr;
   const float2 wf = df_of(a.w), rf = df_of(a.rho_eff);
   const float2 ald = df_of(a.alpha), bed = df_of(a.beta);
   for (int t = tid; t < T; t += kFoldThreads) {
@@ -512,7 +515,7 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   __syncthreads();
 
   // 4. Store X = L^-1 (FP32) and y = L^-1 (w b) (FP32).
-  float2 *Xp = a.L + (size_t)p * tri_stride(K);
+  float2 *Xp = a.L + (size_t)pl * tri_stride(K);
   for (int t = tid; t < T; t += kFoldThreads) Xp[t] = XS[2 * t];
   for (int i = tid; i < K; i += kFoldThreads)
     a.g[(size_t)i * F + p] = make_float2(y[i].x + y[i].z, y[i].y + y[i].w);
@@ -529,14 +532,14 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
 __global__ void dstep_kernel(int K, int F, float rho_eff, const float2 *__restrict__ X,
                              const float2 *__restrict__ yb, const float2 *__restrict__ Vh,
                              const float2 *__restrict__ th, float2 *__restrict__ Dcur,
-                             float2 *__restrict__ E) {
+                             float2 *__restrict__ E, int p0) {
   extern __shared__ __align__(16) float2 dsm[];
   const int TS = tri_stride(K);
   float2 *sX = dsm;
   float2 *sr = sX + TS;
   float2 *st = sr + K;
-  const int p = blockIdx.x, i = threadIdx.x;
-  const float4 *g4 = reinterpret_cast<const float4 *>(X + (size_t)p * TS);
+  const int p = blockIdx.x + p0, i = threadIdx.x;  // X holds frequencies p0 .. only
+  const float4 *g4 = reinterpret_cast<const float4 *>(X + (size_t)blockIdx.x * TS);
   float4 *s4 = reinterpret_cast<float4 *>(sX);
   for (int c = i; c < TS / 2; c += blockDim.x) cp_async16(s4 + c, g4 + c);
   float2 thi = make_float2(0.f, 0.f), yi = make_float2(0.f, 0.f);
@@ -579,25 +582,27 @@ __global__ void dstep_kernel(int K, int F, float rho_eff, const float2 *__restri
 // column block of E in shared memory (coalesced rows of 32 bins), then thread
 // (k2, m1) sums over k1 from there.
 constexpr int kMaxM = 16;
+// Rows k1 in [k1_lo, k1_hi) only (an even count): the whole range, or the
+// band of a band context, whose sums over bands add up to the full one.
 __global__ void vstep_cols_kernel(int K, int N, int M, const float2 *__restrict__ E,
-                                  const float2 *__restrict__ tw, float2 *__restrict__ Y) {
-  extern __shared__ float2 s_twc[];  // [N] twiddles, then [N][32] column block
+                                  const float2 *__restrict__ tw, float2 *__restrict__ Y, int k1_lo, int k1_hi) {
+  extern __shared__ float2 s_twc[];  // [N] twiddles, then [rows][32] column block
   float2 *s_e = s_twc + N;
-  const int NH = N / 2 + 1, F = N * NH;
+  const int NH = N / 2 + 1, F = N * NH, rows = k1_hi - k1_lo;
   const int tid = threadIdx.y * 32 + threadIdx.x, nthr = 32 * blockDim.y;
   for (int i = tid; i < N; i += nthr) s_twc[i] = tw[i];
   const int k = blockIdx.x, k2 = blockIdx.y * 32 + threadIdx.x, m1 = threadIdx.y;
-  const float2 *Ek = E + (size_t)k * F + blockIdx.y * 32;
+  const float2 *Ek = E + (size_t)k * F + (size_t)k1_lo * NH + blockIdx.y * 32;
   const int ncol = min(32, NH - blockIdx.y * 32);
-  for (int e = tid; e < N * 32; e += nthr) {
+  for (int e = tid; e < rows * 32; e += nthr) {
     const int k1 = e >> 5, c = e & 31;
     s_e[e] = c < ncol ? Ek[(size_t)k1 * NH + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   if (k2 >= NH) return;
   float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
-  int ph = 0;  // (k1 m1) mod N
-  for (int k1 = 0; k1 < N; k1 += 2) {
+  int ph = (k1_lo * m1) % N;  // (k1 m1) mod N
+  for (int k1 = 0; k1 < rows; k1 += 2) {
     acc0 = cadd(acc0, cmulc(s_e[k1 * 32 + threadIdx.x], s_twc[ph]));
     ph += m1;
     if (ph >= N) ph -= N;
@@ -688,7 +693,7 @@ __global__ void __launch_bounds__(kProjThreads)
 __global__ void __launch_bounds__(256)
     vstep_spectrum_kernel(int mode, int K, int N, int M, const float2 *__restrict__ Tm,
                           const float2 *__restrict__ tw, float2 *__restrict__ Vh, float2 *__restrict__ th,
-                          const float2 *__restrict__ Dcur) {
+                          const float2 *__restrict__ Dcur, int p0, int p1) {
   __shared__ float2 s_tw[kMaxFFT];
   const int NH = N / 2 + 1, F = N * NH;
   for (int i = threadIdx.x; i < N; i += 256) s_tw[i] = tw[i];
@@ -702,11 +707,38 @@ __global__ void __launch_bounds__(256)
   for (int m1 = 0; m1 < M; ++m1) acc = cadd(acc, cmul(T[(size_t)m1 * NH], s_tw[(k1 * m1) % N]));
   const size_t o = (size_t)k * F + p;
   Vh[o] = acc;
-  if (mode == 0) {
+  if (mode == 0 && p >= p0 && p < p1) {  // the dual lives on the frequencies this context solves
     const float2 d = Dcur[o];
     const float2 t = th[o];
     th[o] = make_float2(t.x + d.x - acc.x, t.y + d.y - acc.y);
   }
+}
+
+// Proposition 2 on given support sums: V_k = alpha_k / max(||alpha_k||, 1)
+// (the band path: alpha is the sum over the bands of their partial crops).
+__global__ void __launch_bounds__(kProjThreads)
+    project_alpha_kernel(int K, int MM, const float *__restrict__ alpha, float *__restrict__ V) {
+  __shared__ float red[32];
+  const int k = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = kProjThreads / 32;
+  const float *a = alpha + (size_t)k * MM;
+  float ss = 0.f;
+  for (int e = tid; e < MM; e += kProjThreads) ss += a[e] * a[e];
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  if (lane == 0) red[warp] = ss;
+  __syncthreads();
+  if (tid < 32) {
+    float v = tid < nwarps ? red[tid] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (tid == 0) red[0] = v;
+  }
+  __syncthreads();
+  const float sc = 1.0f / fmaxf(sqrtf(red[0]), 1.0f);
+  for (int e = tid; e < MM; e += kProjThreads) V[(size_t)k * MM + e] = a[e] * sc;
+}
+
+cudaError_t launch_project_alpha(int K, int M, const float *alpha, float *V, cudaStream_t s) {
+  project_alpha_kernel<<<K, kProjThreads, 0, s>>>(K, M * M, alpha, V);
+  return cudaGetLastError();
 }
 
 __global__ void dict_norms_kernel(int K, int F, const float2 *__restrict__ Dh, float *__restrict__ dn) {
@@ -735,7 +767,7 @@ template <int NTH, bool DF>
 static cudaError_t fold_factor_n(const FoldArgs &a, size_t sm, cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(fold_factor_kernel<NTH, DF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  fold_factor_kernel<NTH, DF><<<a.F, NTH, sm, s>>>(a);
+  fold_factor_kernel<NTH, DF><<<a.nF ? a.nF : a.F, NTH, sm, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -749,26 +781,28 @@ cudaError_t launch_fold_factor(const FoldArgs &a, int threads, cudaStream_t s) {
 
 cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const float2 *yb,
                          const float2 *Vh, const float2 *th, float2 *Dcur, float2 *E,
-                         cudaStream_t s) {
+                         cudaStream_t s, int p0, int nF) {
   if (K > 256) return cudaErrorInvalidValue;
   const size_t sm = ((size_t)tri_stride(K) + 2 * (size_t)K) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(dstep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int threads = (K + 31) / 32 * 32;
-  dstep_kernel<<<F, threads, sm, s>>>(K, F, rho_eff, X, yb, Vh, th, Dcur, E);
+  dstep_kernel<<<nF ? nF : F, threads, sm, s>>>(K, F, rho_eff, X, yb, Vh, th, Dcur, E, p0);
   return cudaGetLastError();
 }
 
 cudaError_t launch_vstep_cols(int K, int N, int M, const float2 *E, const float2 *tw, float2 *Y,
-                              cudaStream_t s) {
+                              cudaStream_t s, int k1_lo, int k1_hi) {
   if (M > kMaxM || N > kMaxFFT) return cudaErrorInvalidValue;
+  if (k1_hi == 0) k1_hi = N;
+  if (k1_lo < 0 || k1_hi > N || k1_lo >= k1_hi || (k1_hi - k1_lo) % 2) return cudaErrorInvalidValue;
   dim3 grid(K, (N / 2 + 1 + 31) / 32), block(32, M);
   const size_t sm = (size_t)N * 33 * sizeof(float2);
   if (sm > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(vstep_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  vstep_cols_kernel<<<grid, block, sm, s>>>(K, N, M, E, tw, Y);
+  vstep_cols_kernel<<<grid, block, sm, s>>>(K, N, M, E, tw, Y, k1_lo, k1_hi);
   return cudaGetLastError();
 }
 
@@ -787,11 +821,11 @@ cudaError_t launch_vstep_partial_dft(int K, int N, int M, const float *V, const 
 }
 
 cudaError_t launch_vstep_spectrum(int mode, int K, int N, int M, const float2 *Tm, const float2 *tw,
-                                  float2 *Vh, float2 *th, const float2 *Dcur, cudaStream_t s) {
+                                  float2 *Vh, float2 *th, const float2 *Dcur, cudaStream_t s, int p0, int p1) {
   if (M > kMaxM || N > kMaxFFT) return cudaErrorInvalidValue;
   const int F = N * (N / 2 + 1);
   dim3 grid(K, (F + 255) / 256);
-  vstep_spectrum_kernel<<<grid, 256, 0, s>>>(mode, K, N, M, Tm, tw, Vh, th, Dcur);
+  vstep_spectrum_kernel<<<grid, 256, 0, s>>>(mode, K, N, M, Tm, tw, Vh, th, Dcur, p0, p1 ? p1 : F);
   return cudaGetLastError();
 }
 

@@ -114,6 +114,10 @@ struct FoldArgs {
   // double-float, A + Alo and b + blo kept as FP32 pairs.
   int dfold;
   float2 *blo;          // [K][F] compensation word of b (precision 3)
+  // Band contexts: frequencies p0 .. p0 + nF - 1 (nF = 0: all F); A, Alo and
+  // L hold these frequencies only; Zp and xh have row stride zF (0: F) and
+  // start at frequency zp0.
+  int p0, nF, zF, zp0;
 };
 cudaError_t launch_fold_factor(const FoldArgs &a, int threads, cudaStream_t s);
 
@@ -161,11 +165,13 @@ cudaError_t launch_dstep_big(int K, int F, float rho_eff, const float2 *L, const
                              const float2 *th, float2 *Dcur, float2 *E, cudaStream_t s);
 cudaError_t launch_gram_fold(const GramArgs &a, cudaStream_t s);
 // d = X^H (y + rho X (v^ - theta^)) with X = L^-1, y = L^-1 (w b).
+// p0, nF: the frequencies solved (a band context; X holds them only); nF = 0: all.
 cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const float2 *yb,
                          const float2 *Vh, const float2 *th, float2 *Dcur, float2 *E,
-                         cudaStream_t s);
+                         cudaStream_t s, int p0 = 0, int nF = 0);
+// Rows k1 in [k1_lo, k1_hi) (k1_hi = 0: all N; an even count).
 cudaError_t launch_vstep_cols(int K, int N, int M, const float2 *E, const float2 *tw, float2 *Y,
-                              cudaStream_t s);
+                              cudaStream_t s, int k1_lo = 0, int k1_hi = 0);
 // Size classes that take part in one V-step (reading R16).
 constexpr int kMaxClasses = 12;
 struct AlphaClasses {
@@ -182,8 +188,12 @@ cudaError_t launch_vstep_project(int K, int M, const AlphaClasses &ac, float *V,
 cudaError_t launch_vstep_partial_dft(int K, int N, int M, const float *V, const float2 *tw, float2 *Tm,
                                      cudaStream_t s);
 // V^ = F(pad V) from Tm; mode 0 also theta^ += D~ - V^.
+// The dual is updated on frequencies [p0, p1) only (p1 = 0: all).
 cudaError_t launch_vstep_spectrum(int mode, int K, int N, int M, const float2 *Tm, const float2 *tw,
-                                  float2 *Vh, float2 *th, const float2 *Dcur, cudaStream_t s);
+                                  float2 *Vh, float2 *th, const float2 *Dcur, cudaStream_t s, int p0 = 0,
+                                  int p1 = 0);
+// Proposition 2 on the support sums alpha [K][M][M] (writes V).
+cudaError_t launch_project_alpha(int K, int M, const float *alpha, float *V, cudaStream_t s);
 cudaError_t launch_dict_norms(int K, int F, const float2 *Dh, float *dn, cudaStream_t s);
 
 // Objective of one sample: out = 1/2 ||x - sum_k D_k (*) U_k||^2 + lam ||U||_1

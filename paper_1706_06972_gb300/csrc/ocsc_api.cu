@@ -102,21 +102,25 @@ ocsc_status alloc_class(ocsc_ctx *c, SizeClass &s, int N) {
   s.NH = N / 2 + 1;
   s.F = N * s.NH;
   s.P = N * N;
+  // A band context keeps the history and factor of its own rows only.
+  s.p0 = c->opts.band_hi > 0 ? c->opts.band_lo * s.NH : 0;
+  s.Fb = c->opts.band_hi > 0 ? (c->opts.band_hi - c->opts.band_lo) * s.NH : s.F;
   const int K = c->K, M = c->M;
   const size_t KF = (size_t)K * s.F, B = (size_t)c->opts.max_batch, TS = (size_t)tri_stride(K);
+  const size_t FT = (size_t)s.Fb * TS;
   ocsc_status st;
   if ((st = dalloc(c, &s.tw, (size_t)N)) || (st = dalloc(c, &s.Vh, KF)) || (st = dalloc(c, &s.th, KF)) ||
       (st = dalloc(c, &s.Dcur, KF)) || (st = dalloc(c, &s.E, KF)) ||
       (st = dalloc(c, &s.Y, (size_t)K * M * s.NH)) || (st = dalloc(c, &s.Tm, (size_t)K * M * s.NH)) ||
-      (st = dalloc(c, &s.dn, (size_t)s.F)) || (st = dalloc(c, &s.A, (size_t)s.F * TS)) ||
-      (st = dalloc(c, &s.b, KF)) || (st = dalloc(c, &s.X, (size_t)s.F * TS)) || (st = dalloc(c, &s.y, KF)) ||
+      (st = dalloc(c, &s.dn, (size_t)s.F)) || (st = dalloc(c, &s.A, FT)) ||
+      (st = dalloc(c, &s.b, KF)) || (st = dalloc(c, &s.X, FT)) || (st = dalloc(c, &s.y, KF)) ||
       (st = dalloc(c, &s.Zp, B * KF)) || (st = dalloc(c, &s.xhp, B * s.F)) ||
       (st = dalloc(c, &s.obj_xh, (size_t)s.F)))
     return st;
   if (c->opts.history == 1 && (st = dalloc(c, &s.Csf, (size_t)s.F * TS))) return st;
   if (c->opts.precision > 0) {
-    if ((st = dalloc(c, &s.Alo, (size_t)s.F * TS))) return st;
-    cudaError_t e = cudaMemset(s.Alo, 0, (size_t)s.F * TS * sizeof(float2));
+    if ((st = dalloc(c, &s.Alo, FT))) return st;
+    cudaError_t e = cudaMemset(s.Alo, 0, FT * sizeof(float2));
     if (e != cudaSuccess) return cuda_fail(c, e, "clear history compensation");
   }
   if (c->opts.precision == 3) {
@@ -177,6 +181,8 @@ void ocsc_default_opts(ocsc_opts *o) {
   o->graphs = 0;
   o->history = 0;
   o->persistent = 0;
+  o->band_lo = 0;
+  o->band_hi = 0;
   o->seed = 0x5EEDull;
 }
 
@@ -245,6 +251,15 @@ ocsc_status ocsc_init(ocsc_ctx **out, int K, int filter_h, int filter_w, double 
     sizes.push_back(n);
   }
   if (sizes.empty()) { fail(c, OCSC_EINVAL, "no fft size given"); return bail(OCSC_EINVAL); }
+  if (c->opts.band_hi != 0) {
+    const int N = sizes[0], lo = c->opts.band_lo, hi = c->opts.band_hi;
+    if (sizes.size() != 1 || lo < 0 || hi > N || lo >= hi || (hi - lo) % 2 || c->opts.history != 0 ||
+        (c->opts.precision != 0 && c->opts.precision != 3) || K > kSmallK || !c->opts.return_feasible) {
+      fail(c, OCSC_EUNSUPPORTED, "a band context needs one FFT size N, 0 <= band_lo < band_hi <= N with an "
+           "even row count, history 0, precision 0 or 3, K <= %d and return_feasible 1", kSmallK);
+      return bail(OCSC_EUNSUPPORTED);
+    }
+  }
   if (sizes.size() > 1 && (c->opts.rho_convention != 0 || !c->opts.return_feasible)) {
     fail(c, OCSC_EUNSUPPORTED, "several size classes need rho_convention = 0 and return_feasible = 1");
     return bail(OCSC_EUNSUPPORTED);
@@ -636,6 +651,8 @@ ocsc_status ocsc_code(ocsc_ctx *c, int n, const float *const *x, const int *H, c
 ocsc_status ocsc_update_dict(ocsc_ctx *c) {
   if (!c) return OCSC_EINVAL;
   NvtxRange range("ocsc_update_dict");
+  if (c->opts.band_hi != 0)
+    return fail(c, OCSC_ESTATE, "a band context updates its dictionary through the ocsc_band_* calls");
   long long fresh = 0;
   for (const SizeClass &s : c->cls) fresh += s.pending;
   if (fresh == 0) return OCSC_OK;
@@ -897,8 +914,8 @@ std::vector<std::pair<void *, size_t>> state_regions(ocsc_ctx *c) {
     r.emplace_back(s.th, kf);
     r.emplace_back(s.Dcur, kf);
     r.emplace_back(s.b, kf);
-    r.emplace_back(s.A, (size_t)s.F * tri_stride(c->K) * sizeof(float2));
-    if (s.Alo) r.emplace_back(s.Alo, (size_t)s.F * tri_stride(c->K) * sizeof(float2));
+    r.emplace_back(s.A, (size_t)s.Fb * tri_stride(c->K) * sizeof(float2));
+    if (s.Alo) r.emplace_back(s.Alo, (size_t)s.Fb * tri_stride(c->K) * sizeof(float2));
     if (s.blo) r.emplace_back(s.blo, kf);
     if (s.Csf) r.emplace_back(s.Csf, (size_t)s.F * tri_stride(c->K) * sizeof(float4));
     r.emplace_back(s.dn, (size_t)s.F * sizeof(float));
@@ -1214,6 +1231,129 @@ ocsc_status ocsc_rel_diff(ocsc_ctx *c, const float *a, const float *b, size_t co
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, c->obj_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "rel_diff");
+}
+
+// ---------------------------------------------------------------------------
+// Frequency-band sharding of the dictionary step (Prop. 1 decouples the
+// D-row systems per frequency): a band context folds, factors and solves the
+// frequencies of its k1 rows only; the caller moves the codes' band rows to
+// their owners and sums the support crops over the bands.
+// ---------------------------------------------------------------------------
+
+static ocsc_status band_ctx(ocsc_ctx *c, const char *what) {
+  if (c->opts.band_hi == 0) return fail(c, OCSC_ESTATE, "%s: not a band context (opts.band_hi = 0)", what);
+  return OCSC_OK;
+}
+
+ocsc_status ocsc_band_export(ocsc_ctx *c, int k1_lo, int k1_hi, float *Z_dev, float *x_dev) {
+  if (!c) return OCSC_EINVAL;
+  SizeClass &s = c->cls[0];
+  if (c->cls.size() != 1 || k1_lo < 0 || k1_hi > s.N || k1_lo >= k1_hi || !Z_dev || !x_dev)
+    return fail(c, OCSC_EINVAL, "band_export: bad arguments");
+  const size_t row = (size_t)s.NH * sizeof(float2), w = (size_t)(k1_hi - k1_lo) * row, F8 = (size_t)s.F * sizeof(float2);
+  if (s.pending == 0) return OCSC_OK;
+  cudaError_t e = cudaMemcpy2DAsync(Z_dev, w, s.Zp + (size_t)k1_lo * s.NH, F8, w, (size_t)s.pending * c->K,
+                                    cudaMemcpyDeviceToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(x_dev, w, s.xhp + (size_t)k1_lo * s.NH, F8, w, (size_t)s.pending, cudaMemcpyDeviceToDevice,
+                          c->stream);
+  return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "band_export");
+}
+
+ocsc_status ocsc_band_fold(ocsc_ctx *c, int B, const float *Z_dev, const float *x_dev) {
+  if (!c) return OCSC_EINVAL;
+  ocsc_status st = band_ctx(c, "band_fold");
+  if (st != OCSC_OK) return st;
+  if (B < 1 || !Z_dev || !x_dev) return fail(c, OCSC_EINVAL, "band_fold: bad arguments");
+  SizeClass &s = c->cls[0];
+  cudaError_t e = cudaSuccess;
+  if (!c->opts.warm_start) {
+    e = cudaMemsetAsync(c->V, 0, (size_t)c->K * c->M * c->M * sizeof(float), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.Vh, 0, (size_t)c->K * s.F * sizeof(float2), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.th, 0, (size_t)c->K * s.F * sizeof(float2), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "band cold start");
+  }
+  const long long nc = s.n_seen + B;
+  FoldArgs fa{};
+  fa.K = c->K;
+  fa.F = s.F;
+  fa.B = B;
+  fa.first = s.n_seen == 0;
+  fa.alpha = (double)s.n_seen / (double)nc;
+  fa.beta = 1.0 / (double)nc;
+  fa.w = 1.0;
+  fa.rho_eff = c->opts.rho_convention == 1 ? c->rho * s.P : c->rho;
+  fa.A = s.A;
+  fa.b = s.b;
+  fa.Zp = reinterpret_cast<const float2 *>(Z_dev);
+  fa.xh = reinterpret_cast<const float2 *>(x_dev);
+  fa.L = s.X;
+  fa.g = s.y;
+  fa.err = c->err;
+  fa.p0 = s.p0;
+  fa.nF = s.Fb;
+  fa.zF = s.Fb;
+  fa.zp0 = s.p0;
+  if (c->opts.precision == 3) {
+    fa.dfold = 1;
+    fa.Alo = s.Alo;
+    fa.blo = s.blo;
+  }
+  const int nt = s.fold_threads ? s.fold_threads : 256;
+  e = timed(c, OCSC_K_FOLD_FACTOR, [&] { return launch_fold_factor(fa, nt, c->stream); });
+  if (e != cudaSuccess) return cuda_fail(c, e, "band fold_factor");
+  s.n_seen = nc;
+  c->n_seen += B;
+  return OCSC_OK;
+}
+
+ocsc_status ocsc_band_dict_step(ocsc_ctx *c, float *alpha_dev) {
+  if (!c) return OCSC_EINVAL;
+  ocsc_status st = band_ctx(c, "band_dict_step");
+  if (st != OCSC_OK) return st;
+  if (!alpha_dev) return fail(c, OCSC_EINVAL, "band_dict_step: null output");
+  if (c->cls[0].n_seen == 0) return fail(c, OCSC_ESTATE, "band_dict_step: nothing folded yet");
+  SizeClass &s = c->cls[0];
+  const float rho_eff = (float)(c->opts.rho_convention == 1 ? c->rho * s.P : c->rho);
+  cudaError_t e = timed(c, OCSC_K_DSTEP, [&] {
+    return launch_dstep(c->K, s.F, rho_eff, s.X, s.y, s.Vh, s.th, s.Dcur, s.E, c->stream, s.p0, s.Fb);
+  });
+  if (e == cudaSuccess)
+    e = timed(c, OCSC_K_VSTEP_COLS, [&] {
+      return launch_vstep_cols(c->K, s.N, c->M, s.E, s.tw, s.Y, c->stream, c->opts.band_lo, c->opts.band_hi);
+    });
+  AlphaClasses ac{};
+  ac.project = 0;
+  ac.C = 1;
+  ac.N[0] = s.N;
+  ac.Y[0] = s.Y;
+  ac.tw[0] = s.tw;
+  if (e == cudaSuccess)
+    e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_vstep_project(c->K, c->M, ac, alpha_dev, c->stream); });
+  return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "band_dict_step");
+}
+
+ocsc_status ocsc_band_project(ocsc_ctx *c, const float *alpha_dev, int last) {
+  if (!c) return OCSC_EINVAL;
+  ocsc_status st = band_ctx(c, "band_project");
+  if (st != OCSC_OK) return st;
+  if (!alpha_dev) return fail(c, OCSC_EINVAL, "band_project: null input");
+  SizeClass &s = c->cls[0];
+  cudaError_t e = timed(c, OCSC_K_VSTEP_PROJECT, [&] { return launch_project_alpha(c->K, c->M, alpha_dev, c->V, c->stream); });
+  if (e == cudaSuccess)
+    e = timed(c, OCSC_K_VSTEP_SPECTRUM, [&] { return launch_vstep_partial_dft(c->K, s.N, c->M, c->V, s.tw, s.Tm, c->stream); });
+  if (e == cudaSuccess)
+    e = timed(c, OCSC_K_VSTEP_SPECTRUM, [&] {
+      return launch_vstep_spectrum(0, c->K, s.N, c->M, s.Tm, s.tw, s.Vh, s.th, s.Dcur, c->stream, s.p0, s.p0 + s.Fb);
+    });
+  if (e == cudaSuccess && last) {
+    e = timed(c, OCSC_K_DICT_NORMS, [&] { return launch_dict_norms(c->K, s.F, s.Vh, s.dn, c->stream); });
+    if (e == cudaSuccess) {
+      c->version += 1;
+      c->counters.dict_updates += 1;
+    }
+  }
+  return e == cudaSuccess ? OCSC_OK : cuda_fail(c, e, "band_project");
 }
 
 ocsc_status ocsc_get_counters(const ocsc_ctx *c, ocsc_counters *out) {

@@ -921,3 +921,62 @@ def test_persistent_barrier_timeout_is_reported_and_context_recovers():
         assert torch.equal(x, y)
     lr.close()
     ref.close()
+
+
+# --- frequency-band sharding of the dictionary step (Prop. 1) ------------------------
+
+@pytest.mark.parametrize("G", [2, 3])
+def test_band_sharded_dictionary_step_matches_oracle(G):
+    """G band contexts on one GPU, each owning a band of k1 rows (history and
+    factor of its frequencies only); each codes one sample per update, the band
+    rows go to their owners, and the support sums are added in context order
+    (bands.band_update_local).  Two updates against the oracle's mini-batch of
+    G samples; every context ends with the same filters."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+    from paper_1706_06972_gb300.bands import band_partition, band_update_local
+
+    K, M, N, lam, rho, Jz, Jd = 12, 5, 64, 0.3, 1.0, 10, 5
+    raw = raw_filters(K, M, 2500)
+    lrs = [pkg.OCSC(K, M, lam, rho, fft_size=N, pad=4, Jz=Jz, Jd=Jd, max_batch=2, band_lo=lo, band_hi=hi)
+           for lo, hi in band_partition(N, G)]
+    for lr in lrs:
+        lr.set_dict(raw, normalize=True)
+    st = oracle.init_state(np.asarray(raw, np.float64), N, N, lam, rho)
+    for u in range(2):
+        imgs = [make_image(60, 60, 2510 + 10 * u + g) for g in range(G)]
+        codes = [lrs[g].code([torch.from_numpy(imgs[g]).cuda()])[0].cpu().numpy() for g in range(G)]
+        res = [oracle.code(st, im, Jz) for im in imgs]
+        for g in range(G):
+            tight = u == 0
+            assert_close(codes[g], res[g].U, f"bands G={G} update {u} code {g}",
+                         CODE_ELEM_TOL if tight else ELEM_TOL, CODE_PLANE_TOL if tight else PLANE_TOL)
+        band_update_local(lrs, [1] * G, Jd)
+        oracle.update_dict(st, res, Jd)
+        Ds = [lr.get_dict() for lr in lrs]
+        for D in Ds[1:]:
+            assert np.array_equal(D, Ds[0])
+        assert_close(Ds[0], st.V, f"bands G={G} dict {u}")
+    for lr in lrs:
+        lr.close()
+
+
+def test_band_context_rejects_the_whole_update_and_bad_bands():
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    lr = pkg.OCSC(8, 5, 0.3, 1.0, fft_size=64, pad=4, band_lo=0, band_hi=32)
+    lr.code([torch.from_numpy(make_image(60, 60, 1)).cuda()], want_codes=False)
+    with pytest.raises(pkg.OCSCError) as e:
+        lr.update_dict()
+    assert e.value.status == 5
+    lr.close()
+    for lo, hi in ((0, 31), (10, 10), (0, 66)):
+        with pytest.raises(pkg.OCSCError) as e:
+            pkg.OCSC(8, 5, 0.3, 1.0, fft_size=64, band_lo=lo, band_hi=hi)
+        assert e.value.status == 6
+    full = pkg.OCSC(8, 5, 0.3, 1.0, fft_size=64)
+    with pytest.raises(pkg.OCSCError) as e:
+        full.band_dict_step()
+    assert e.value.status == 5
+    full.close()
