@@ -58,15 +58,22 @@ def hbm_peak():
         return HBM_FALLBACK_GBS, "of fallback (6.8 TB/s, one earlier GB300 measurement)"
 
 
-# DRAM bytes per launch from ncu captures (profiles/), valid only while the
-# kernel's source file is the one captured (sha1 of the file).
+# DRAM bytes from ncu captures (profiles/), per unit of work, valid only while
+# the kernel's source file is the one captured (sha1 of the file).
+#   code_plane: the code128 profile case (16 images of the headline workload
+#   per launch, a middle iteration) -> bytes per image; traffic grows in
+#   proportion to the images of a launch (one CTA per image and filter).
+#   fold_factor: the fold128 profile case (the headline workload's factor at
+#   mini-batch 1) -> bytes per launch at B = 1.
 TRAFFIC_CAPTURES = {
-    "fold_factor": {"bytes": 350.423040e6 + 625.118720e6, "file": "dict_update.cu",
-                    "source_sha1": "5aace13e6608b8694365c38ae4152e912b1af9d3"},
+    "code_plane": {"bytes": (230526208 + 174130432) / 16, "per": "image", "file": "plane_bodies.cuh",
+                   "source_sha1": "91d52c571e078fb1834344eddc8e7d35eb34140d"},
+    "fold_factor": {"bytes": 350429440 + 625175552, "per": "launch at mini-batch 1", "file": "dict_update.cu",
+                    "source_sha1": "ea40f8f4e12ac24d0ea48bd233bddb9396a7d2aa"},
 }
 
 
-def captured_traffic(kernel):
+def captured_traffic(kernel, units=1):
     import hashlib
 
     cap = TRAFFIC_CAPTURES.get(kernel)
@@ -75,7 +82,7 @@ def captured_traffic(kernel):
     path = os.path.join(ROOT, "paper_1706_06972_gb300", "csrc", cap["file"])
     with open(path, "rb") as f:
         sha = hashlib.sha1(f.read()).hexdigest()
-    return cap["bytes"] if sha == cap["source_sha1"] else None
+    return cap["bytes"] * units if sha == cap["source_sha1"] else None
 
 
 def fold_factor_fp64_flops(K: int, F: int) -> float:
@@ -397,7 +404,7 @@ def alu_roofline(K, F, B, avg_s, launches):
     achieved = meth / avg_s / 1e12
     return {"kernel": "fold_factor (per-frequency fold + Cholesky in double-float on the FP32 pipe + FP32 L^-1)",
             "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": captured_traffic("fold_factor"),
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": captured_traffic("fold_factor") if B == 1 else None,
             "peak_note": "FP32 pipe, derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz (no driver measurement; "
                          f"an FMA probe measured {FP32_PROBE_TFLOPS} TFLOP/s at ~1.98 GHz)",
             "work": "method flops (8/3) K^3 F + 8 K^2 B F (Cholesky + triangular inverse + fold)",
@@ -407,11 +414,11 @@ def alu_roofline(K, F, B, avg_s, launches):
                                  "note": "FP32 flops of the double-float instruction stream executed"}}
 
 
-def hbm_entry(name, bytes_per_launch, avg_s, launches, peak, peak_note):
+def hbm_entry(name, bytes_per_launch, avg_s, launches, peak, peak_note, traffic=None):
     achieved = bytes_per_launch / avg_s / 1e9
     return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_note": peak_note, "bytes_per_launch": bytes_per_launch,
-            "avg_ms": avg_s * 1e3, "launches": launches, "traffic": captured_traffic(name)}
+            "avg_ms": avg_s * 1e3, "launches": launches, "traffic": traffic}
 
 
 def persistent_leg(pkg, w, dev, stream, args):
@@ -812,7 +819,7 @@ def ours_arm(args):
     ms, n = prof["code_plane"]
     if n:
         rooflines["code_plane"] = hbm_entry("code_plane", code_plane_bytes(w.K, N, B, w.Jz, False) / w.Jz,
-                                            ms / 1e3 / n, n, peak, peak_note)
+                                            ms / 1e3 / n, n, peak, peak_note, captured_traffic("code_plane", B))
     ms, n = prof["fold_factor"]
     if n:
         rooflines["fold_factor"] = alu_roofline(w.K, F, B, ms / 1e3 / n, n)
