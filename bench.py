@@ -800,6 +800,7 @@ def ours_arm(args):
         te = max_over_ranks(event_time(stream, e2e_steps), dev)
         e2e = {"value": world * B * E / te, "unit": UNIT, "h2d_bytes_per_step": int(B * host[0].numel() * 4),
                "d2h_bytes_per_step": int(D_host.numel() * 4), "steps": E}
+    tuned = learner.tuning(N)  # launch shapes the autotuner chose
     learner.close()
     legs = set(args.legs.split(","))
     plain = plain_leg(pkg, w, dev, stream, args) if "plain" in legs and args.plain_steps > 0 else None
@@ -846,7 +847,7 @@ def ours_arm(args):
         "ms_per_step": 1e3 * t_max / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f32x2", "data": "synthetic",
         "config": config_dict({"parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                               "graphs": False, "tuned_tiles": None}),
+                               "graphs": False, "tuned": tuned}),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(c1["kernel_launches"] - c0["kernel_launches"]),
         "plain_path": plain,
@@ -876,6 +877,8 @@ PROFILE_CASES = {
     "rec128": (100, 11, 128, 1, 100, 5, 0, 1),
     # The factorisation (fold_factor) at the headline sizes: K = 100, FFT 128.
     "fold128": (100, 11, 128, 1, 100, 5, 0, 0, 1),
+    # The same with the headline's mini-batch of 64 samples folded per update.
+    "fold128b64": (100, 11, 128, 64, 100, 2, 0, 0, 1),
 }
 
 

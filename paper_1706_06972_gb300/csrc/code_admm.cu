@@ -19,6 +19,15 @@
 //                  rows), shrink + dual update on pairs of pixels, forward
 //                  real 2D FFT of W = U - Gamma back to the half spectrum.
 //                  Gamma is the only spatial array that goes to global memory.
+//                  Every pass moves the whole tile through registers, so the
+//                  kernel is fused to as few passes as the transforms allow:
+//                  the column packing rides on the first column pass, the
+//                  last pass of each transform is done in place without a
+//                  barrier, and for N = 128 the c2r split rides on the first
+//                  row pass, the spatial step sits between the last inverse
+//                  and the first forward row pass on each thread's registers,
+//                  the r2c split rides on the last row pass and the last
+//                  column pass stores W^ to global memory itself.
 #include "plane_bodies.cuh"
 
 namespace ocsc {
@@ -61,12 +70,12 @@ __global__ void code_resid_kernel(int K, int F, float rho, int first, int serve,
 // One fused ADMM iteration for filter k of one sample (grid: K x images).
 // MINB is the number of CTAs per SM the register budget is sized for (2: no
 // spills; 3: a few spilled registers, more overlap); both perform the same
-// operations in the same order.
-template <int N, int MINB>
+// operations in the same order.  SERVE selects the serving form of the body.
+template <int N, int MINB, bool SERVE>
 __global__ void __launch_bounds__(HalfPlan<N>::NT, MINB)
     code_plane_kernel(CodeIter it, ImgBatch b, const float2 *__restrict__ tw) {
   extern __shared__ __align__(16) float4 hsmem[];
-  code_plane_body<N>(it, b, tw, blockIdx.x, blockIdx.y, hsmem);
+  code_plane_body<N, SERVE>(it, b, tw, blockIdx.x, blockIdx.y, hsmem);
 }
 
 // Building block: batched real 2D FFT (pairs of planes share one complex FFT).
@@ -175,20 +184,24 @@ cudaError_t launch_code_resid(int N, const ImgBatch &b, const CodeIter &it, floa
                               const float2 *xh, cudaStream_t s) {
   if (b.n <= 0) return cudaSuccess;
   const int F = N * (N / 2 + 1);
-  dim3 grid((F + 31) / 32, b.n), block(32, 8);
+  dim3 grid((F + kResidBins - 1) / kResidBins, b.n), block(32, 8);
   code_resid_kernel<<<grid, block, 0, s>>>(it.K, F, rho, it.first, it.serve, b, it.Dh, dn, xh, it.What, it.r);
   return cudaGetLastError();
 }
 
-template <int N, int MINB>
-static cudaError_t code_plane_n(const CodeIter &it, const ImgBatch &b, const float2 *tw,
-                                cudaStream_t s) {
+template <int N, int MINB, bool SERVE>
+static cudaError_t code_plane_nms(const CodeIter &it, const ImgBatch &b, const float2 *tw, cudaStream_t s) {
   const size_t sm = half_smem_bytes<N>();
-  cudaError_t e = set_smem(code_plane_kernel<N, MINB>, sm);
+  cudaError_t e = set_smem(code_plane_kernel<N, MINB, SERVE>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid(it.K, b.n);
-  code_plane_kernel<N, MINB><<<grid, HalfPlan<N>::NT, sm, s>>>(it, b, tw);
+  code_plane_kernel<N, MINB, SERVE><<<grid, HalfPlan<N>::NT, sm, s>>>(it, b, tw);
   return cudaGetLastError();
+}
+
+template <int N, int MINB>
+static cudaError_t code_plane_n(const CodeIter &it, const ImgBatch &b, const float2 *tw, cudaStream_t s) {
+  return it.serve ? code_plane_nms<N, MINB, true>(it, b, tw, s) : code_plane_nms<N, MINB, false>(it, b, tw, s);
 }
 
 int plane_resid_groups(int K) { return K; }

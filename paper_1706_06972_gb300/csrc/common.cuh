@@ -43,6 +43,12 @@ __device__ __forceinline__ void cp_async_wait_all() {
   cp_async_wait<0>();
 }
 
+// Hint that `bytes` (a multiple of 16) from the 16-byte aligned gmem be
+// brought into L2 (cp.async.bulk.prefetch: no completion, no ordering).
+__device__ __forceinline__ void prefetch_l2(const void *gmem, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
+}
+
 // Packed lower triangle, column-major: column j holds rows j..K-1.
 // Offset of column j: j*K - j*(j-1)/2.
 __host__ __device__ __forceinline__ int tri_off(int j, int K) { return j * (2 * K - j + 1) / 2; }

@@ -296,8 +296,10 @@ __device__ __forceinline__ void fold_xpanel(float2 *XS, const float2 *Lb, const 
 //      triangle in panels of kPanel columns, with y carried along (forward
 //      substitution y <- L^-1 w b), and X = L^-1 in FP32 one panel behind.
 //      Per panel b, in one phase between two barriers:
-//        warp 0    applies panel b's rank-kPanel update to the columns of panel
-//                  b+1 (and the columns paired with them, below), then factors
+//        warps 0..kPanel-1 apply panel b's rank-kPanel update to the columns
+//                  of panel b+1, one column each (warp 0 alone, with the
+//                  columns paired with them, once the trailing triangle is
+//                  small), and meet at a named barrier; warp 0 then factors
 //                  panel b+1 (fold_panel: pivots 1/sqrt by an FP32 estimate and
 //                  one double-float Newton step, column scaling, the update
 //                  inside the panel, y);
@@ -346,8 +348,14 @@ __device__ __forceinline__ float2 df_blend(float oh, float ol, float S, float E,
   return two_sum(P1, E1);
 }
 
+// Barrier `id` (not 0, which __syncthreads uses) over the first `count`
+// threads of the block, a multiple of 32.
+__device__ __forceinline__ void named_barrier_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 template <int kFoldThreads, bool DF>
-__global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
+__global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_kernel(FoldArgs a) {
   extern __shared__ __align__(16) unsigned char fsm[];
   const int K = a.K, F = a.F, B = a.B;
   const int T = tri_size(K);
@@ -378,6 +386,7 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
   for (int m = 0; m < (DF ? MR : 1); ++m) sbd[m] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   // 1. FP32 sums over the pending samples of conj(z_i) z_j and x~ conj(z_i).
+  const int mt = (K + 1) / 2, ntile = mt * (mt + 1) / 2;
   for (int c0 = 0; c0 < (a.prefolded ? 0 : B); c0 += kFoldChunk) {
     const int nb = min(kFoldChunk, B - c0);
     __syncthreads();
@@ -387,17 +396,48 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
     }
     for (int s = tid; s < nb; s += kFoldThreads) xs[s] = a.xh[(size_t)(c0 + s) * zF + zp];
     __syncthreads();
-    for (int t = tid; t < T; t += kFoldThreads) {
-      int i, j;
-      tri_ij(t, K, i, j);
+    // 2 x 2 tiles of the lower triangle (rows i0, i0 + 1, columns j0, j0 + 1):
+    // the four codes of a sample are loaded once for the tile's four entries.
+    // Entries outside the triangle (above the diagonal of a diagonal tile,
+    // or index K for odd K) are computed from zeros and not stored.
+    for (int u = tid; u < ntile; u += kFoldThreads) {
+      int ti, tj;
+      tri_ij(u, mt, ti, tj);
+      const int i0 = 2 * ti, j0 = 2 * tj;
+      const bool hi = i0 + 1 < K, hj = j0 + 1 < K, e01 = hj && ti > tj;
+      const int t00 = tri_off(j0, K) + i0 - j0;                    // (i0 + 1, j0) follows it
+      const int t01 = hj ? tri_off(j0 + 1, K) + i0 - j0 - 1 : 0;   // (i0 + 1, j0 + 1) follows it
+      const float2 zero = make_float2(0.f, 0.f);
       if (DF) {
-        float4 acc = M[t];
-        for (int s = 0; s < nb; ++s) df_acc_cconjmul(acc, zs[s * K + i], zs[s * K + j]);
-        M[t] = acc;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 a00 = M[t00], a10 = hi ? M[t00 + 1] : z4, a01 = e01 ? M[t01] : z4, a11 = hi && hj ? M[t01 + 1] : z4;
+        for (int s = 0; s < nb; ++s) {
+          const float2 zi0 = zs[s * K + i0], zi1 = hi ? zs[s * K + i0 + 1] : zero;
+          const float2 zj0 = zs[s * K + j0], zj1 = hj ? zs[s * K + j0 + 1] : zero;
+          df_acc_cconjmul(a00, zi0, zj0);
+          df_acc_cconjmul(a10, zi1, zj0);
+          df_acc_cconjmul(a01, zi0, zj1);
+          df_acc_cconjmul(a11, zi1, zj1);
+        }
+        M[t00] = a00;
+        if (hi) M[t00 + 1] = a10;
+        if (e01) M[t01] = a01;
+        if (hi && hj) M[t01 + 1] = a11;
       } else {
-        float2 acc = S[2 * t];
-        for (int s = 0; s < nb; ++s) acc = cadd(acc, cconjmul(zs[s * K + i], zs[s * K + j]));
-        S[2 * t] = acc;
+        float2 a00 = S[2 * t00], a10 = hi ? S[2 * (t00 + 1)] : zero, a01 = e01 ? S[2 * t01] : zero;
+        float2 a11 = hi && hj ? S[2 * (t01 + 1)] : zero;
+        for (int s = 0; s < nb; ++s) {
+          const float2 zi0 = zs[s * K + i0], zi1 = hi ? zs[s * K + i0 + 1] : zero;
+          const float2 zj0 = zs[s * K + j0], zj1 = hj ? zs[s * K + j0 + 1] : zero;
+          a00 = cadd(a00, cconjmul(zi0, zj0));
+          a10 = cadd(a10, cconjmul(zi1, zj0));
+          a01 = cadd(a01, cconjmul(zi0, zj1));
+          a11 = cadd(a11, cconjmul(zi1, zj1));
+        }
+        S[2 * t00] = a00;
+        if (hi) S[2 * (t00 + 1)] = a10;
+        if (e01) S[2 * t01] = a01;
+        if (hi && hj) S[2 * (t01 + 1)] = a11;
       }
     }
 #pragma unroll
@@ -501,13 +541,27 @@ __global__ void __launch_bounds__(kFoldThreads) fold_factor_kernel(FoldArgs a) {
     // of rectangle rows r < kPanel (warp 0) and the flat pool takes the rest;
     // below that warp 0 takes the whole (small) triangle.
     const bool small = n < 2 * kPanel;
-    if (warp == 0) {
-      fold_trail(M, K, j0, nb, 0, 1, small ? R : rw, lane, small);
-      __syncwarp();
-      if (nb2 > 0) fold_panel(M, y, invf, Lb, K, b + 1, lane, a.err, rho_fb);
+    if (small) {
+      if (warp == 0) {
+        fold_trail(M, K, j0, nb, 0, 1, R, lane, true);
+        __syncwarp();
+        if (nb2 > 0) fold_panel(M, y, invf, Lb, K, b + 1, lane, a.err, rho_fb);
+      } else if (b >= 1) {
+        fold_xpanel(XS, Lb, invf, K, b - 1, warp - 1, nwarps - 1, lane);
+      }
     } else {
-      if (!small) fold_trail_tiles(M, K, j0, nb, rw, tid - 32, kFoldThreads - 32);
-      if (b >= 1) fold_xpanel(XS, Lb, invf, K, b - 1, warp - 1, nwarps - 1, lane);
+      // Here nb2 = rw = kPanel: warps 0 .. kPanel-1 update one column of the
+      // next panel each and meet at a named barrier before warp 0 factors it.
+      if (warp < kPanel) {
+        fold_trail(M, K, j0, nb, warp, kPanel, rw, lane, false);
+        named_barrier_sync(1, kPanel * 32);
+      }
+      if (warp == 0) {
+        fold_panel(M, y, invf, Lb, K, b + 1, lane, a.err, rho_fb);
+      } else {
+        fold_trail_tiles(M, K, j0, nb, rw, tid - 32, kFoldThreads - 32);
+        if (b >= 1) fold_xpanel(XS, Lb, invf, K, b - 1, warp - 1, nwarps - 1, lane);
+      }
     }
     __syncthreads();
   }

@@ -284,8 +284,35 @@ __device__ __forceinline__ void half_pass(float2 *__restrict__ buf, const float2
   constexpr int G = LINES * (LEN / R);
   static_assert(G % NT == 0, "threads must divide the butterfly groups");
   constexpr int PER = G / NT;
-  float2 v[PER][R];
   const int tid = threadIdx.x;
+  if constexpr (NS * R == LEN) {
+    // The last pass writes each group's outputs onto its own inputs
+    // (j + r LEN / R), so a group is finished before the next is loaded and
+    // no barrier separates the loads from the stores.
+#pragma unroll
+    for (int gi = 0; gi < PER; ++gi) {
+      const int g = tid + gi * NT;
+      const int line = g % LINES;
+      const int j = g / LINES;
+      float2 u[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) u[r] = buf[line * LS + (j + r * NS) * ES];
+      if constexpr (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = tw[((r * j) % LEN) * TWS];
+          if (INV) w.y = -w.y;
+          u[r] = cmul(u[r], w);
+        }
+      }
+      RegDFT<R, INV>::run(u);
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[line * LS + (j + r * NS) * ES] = u[r];
+    }
+    __syncthreads();
+    return;
+  }
+  float2 v[PER][R];
 #pragma unroll
   for (int gi = 0; gi < PER; ++gi) {
     const int g = tid + gi * NT;

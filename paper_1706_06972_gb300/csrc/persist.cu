@@ -63,7 +63,7 @@ __device__ __forceinline__ int units_of(const PersistClass &c, int phase, int t,
   const int npairs = (K + 1) / 2;
   if (c.N <= 128) {
     const int F = c.N * (c.N / 2 + 1);
-    if (phase == 0) return c.n * ((F + 31) / 32);
+    if (phase == 0) return c.n * ((F + kResidBins - 1) / kResidBins);
     if (phase == 1) return c.n * K;
     return 0;
   }
@@ -77,12 +77,12 @@ __device__ __forceinline__ int units_of(const PersistClass &c, int phase, int t,
 template <int N>
 __device__ __noinline__ void small_unit(const PersistArgs &a, const PersistClass &c, const CodeIter &it,
                                            int phase, int v, float4 *psm) {
-  constexpr int F = N * (N / 2 + 1), NB = (F + 31) / 32;
+  constexpr int F = N * (N / 2 + 1), NB = (F + kResidBins - 1) / kResidBins;
   if (phase == 0) {
     code_resid_body(it.K, F, it.rho, it.first, 0, a.b, it.Dh, it.dn, it.xh, it.What, it.r, v % NB, c.n0 + v / NB,
                     threadIdx.x & 31, threadIdx.x >> 5);
   } else {
-    code_plane_body<N>(it, a.b, c.tw, v % it.K, c.n0 + v / it.K, psm);
+    code_plane_body<N, false>(it, a.b, c.tw, v % it.K, c.n0 + v / it.K, psm);
   }
 }
 
@@ -175,9 +175,12 @@ int persist_grid(size_t smem) {
 
 cudaError_t launch_persist(const PersistArgs &a, int grid, size_t smem, cudaStream_t s) {
   if (grid <= 0 || a.ncls < 1 || a.ncls > kMaxPersistClasses) return cudaErrorInvalidValue;
-  for (int i = 0; i < a.ncls; ++i)
+  for (int i = 0; i < a.ncls; ++i) {
     if (!persist_size_ok(a.c[i].N) || (a.c[i].N > 128 && a.c[i].cb != 8 && a.c[i].cb != 16))
       return cudaErrorInvalidValue;
+    for (const CodeIter &it : a.c[i].it)
+      if (it.serve) return cudaErrorInvalidValue;  // batch coding only
+  }
   cudaError_t e = cudaFuncSetAttribute(code_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), s);

@@ -39,31 +39,57 @@ __device__ __forceinline__ void block_sum_terms(float (&v)[kResidTerms], float *
   }
 }
 
-// r_p = (x~(p) - sum_k D~_k(p) W^_k(p)) / (rho + |d_p|^2) for 32 bins
-// pb * 32 .. of image img; 256 threads as (32 bins) x (8 filter lanes).
+// r_p = (x~(p) - sum_k D~_k(p) W^_k(p)) / (rho + |d_p|^2) for the 64 bins
+// pb * 64 .. of image img (F is even); 256 threads as (32 bin pairs) x
+// (8 filter lanes): lane ty sums the filters k = ty, ty + 8, ... of two
+// adjacent bins from 16-byte loads, and the lanes' sums are added in order.
+constexpr int kResidBins = 64;
+
 __device__ __forceinline__ void code_resid_body(int K, int F, float rho, int first, int serve, const ImgBatch &b,
                                                 const float2 *__restrict__ Dh, const float *__restrict__ dn,
                                                 const float2 *__restrict__ xh, const float2 *__restrict__ What,
                                                 float2 *__restrict__ r, int pb, int img, int tx, int ty) {
-  __shared__ float2 part[8][33];
-  const int p = pb * 32 + tx;
+  __shared__ float4 part[8][33];
+  const int F2 = F / 2, q = pb * 32 + tx;  // bins 2q, 2q + 1
   const int slot = b.slot[img];
   const bool is_first = serve ? b.iter[img] == 0 : first != 0;
-  float2 s = make_float2(0.f, 0.f);
-  if (!is_first && p < F) {
-    const float2 *w = What + (size_t)slot * K * F;
-#pragma unroll 4
-    for (int k = ty; k < K; k += 8) s = cadd(s, cmul(Dh[(size_t)k * F + p], w[(size_t)k * F + p]));
-  }
-  part[ty][tx] = s;
-  __syncthreads();
-  if (ty == 0 && p < F) {
-    float2 t = part[0][tx];
+  float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+  if (!is_first && q < F2) {
+    const float4 *w = reinterpret_cast<const float4 *>(What + (size_t)slot * K * F);
+    const float4 *D = reinterpret_cast<const float4 *>(Dh);
+    constexpr int U = 4;  // loads in flight per operand
+    for (int k0 = ty; k0 < K; k0 += 8 * U) {
+      float4 d[U], v[U];
 #pragma unroll
-    for (int y = 1; y < 8; ++y) t = cadd(t, part[y][tx]);
-    const float2 x = xh[(size_t)slot * F + p];
-    const float inv = 1.0f / (rho + dn[p]);
-    r[(size_t)slot * F + p] = make_float2((x.x - t.x) * inv, (x.y - t.y) * inv);
+      for (int u = 0; u < U; ++u) {
+        const int k = k0 + 8 * u;
+        if (k < K) {
+          d[u] = D[(size_t)k * F2 + q];
+          v[u] = w[(size_t)k * F2 + q];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (k0 + 8 * u >= K) break;
+        s0 = cadd(s0, cmul(make_float2(d[u].x, d[u].y), make_float2(v[u].x, v[u].y)));
+        s1 = cadd(s1, cmul(make_float2(d[u].z, d[u].w), make_float2(v[u].z, v[u].w)));
+      }
+    }
+  }
+  part[ty][tx] = make_float4(s0.x, s0.y, s1.x, s1.y);
+  __syncthreads();
+  if (ty == 0 && q < F2) {
+    float4 t = part[0][tx];
+#pragma unroll
+    for (int y = 1; y < 8; ++y) {
+      const float4 u = part[y][tx];
+      t = make_float4(t.x + u.x, t.y + u.y, t.z + u.z, t.w + u.w);
+    }
+    const float4 x = reinterpret_cast<const float4 *>(xh + (size_t)slot * F)[q];
+    const float2 dd = reinterpret_cast<const float2 *>(dn)[q];
+    const float i0 = 1.0f / (rho + dd.x), i1 = 1.0f / (rho + dd.y);
+    reinterpret_cast<float4 *>(r + (size_t)slot * F)[q] =
+        make_float4((x.x - t.x) * i0, (x.y - t.y) * i0, (x.z - t.z) * i1, (x.w - t.w) * i1);
   }
 }
 
@@ -84,7 +110,307 @@ __device__ __forceinline__ void code_resid_body(int K, int F, float rho, int fir
 //   X[k] = (H[k] + conj H[N/2-k]) / 2 + W_N^k (H[k] - conj H[N/2-k]) / (2i),
 // X[0] and X[N/2] real (packed as one complex column), N/2 column transforms.
 //
+// The split of a packed real row and its inverse (the plane kernel's
+// header explains them): with a = X[k], c = X[N/2 - k] of a real row's half
+// spectrum, the half-length spectrum of h[m] = x[2m] + i x[2m+1] is
+// H[k] = (a + conj c) + i W_N^-k (a - conj c); with a = H[k], c = H[N/2 - k],
+// X[k] = (a + conj c) / 2 + W_N^k (a - conj c) / (2i).
+__device__ __forceinline__ float2 split_c2r(float2 a, float2 c, const float2 *s_tw, int k) {
+  const float2 w = make_float2(s_tw[k].x, -s_tw[k].y);
+  const float2 d = cmul(w, make_float2(a.x - c.x, a.y + c.y));
+  return make_float2(a.x + c.x - d.y, a.y - c.y + d.x);
+}
+__device__ __forceinline__ float2 split_r2c(float2 a, float2 c, const float2 *s_tw, int k) {
+  const float2 e = cmul(s_tw[k], make_float2(a.y + c.y, c.x - a.x));
+  return make_float2(0.5f * (a.x + c.x + e.x), 0.5f * (a.y - c.y + e.y));
+}
+
+// First inverse column pass (radix C0, no twiddles) over the Z~ tile, with
+// columns 0 and N/2 packed as z0 + i zN/2 where the thread of column 0 loads
+// them.
 template <int N>
+__device__ __forceinline__ void cols_inv_first_packed(float2 *tile) {
+  using P = HalfPlan<N>;
+  constexpr int NT = P::NT, NH = N / 2 + 1, H = N / 2, R = P::C0, LINES = N / 2, STEP = N / R;
+  constexpr int G = LINES * STEP, PER = G / NT;
+  static_assert(G % NT == 0, "threads must divide the butterfly groups");
+  float2 v[PER][R];
+#pragma unroll
+  for (int gi = 0; gi < PER; ++gi) {
+    const int g = threadIdx.x + gi * NT, c = g % LINES, j = g / LINES;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int p = (j + r * STEP) * NH + c;
+      float2 z = tile[p];
+      if (c == 0) {
+        const float2 zh = tile[p + H];
+        z = make_float2(z.x - zh.y, z.y + zh.x);
+      }
+      v[gi][r] = z;
+    }
+    RegDFT<R, true>::run(v[gi]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int gi = 0; gi < PER; ++gi) {
+    const int g = threadIdx.x + gi * NT, c = g % LINES, j = g / LINES;
+#pragma unroll
+    for (int r = 0; r < R; ++r) tile[(j * R + r) * NH + c] = v[gi][r];
+  }
+  __syncthreads();
+}
+
+// N = 128: rows of 64 points by two radix-8 passes.  A thread takes one row
+// and four of its eight butterfly groups (group j holds elements j + 8r):
+// threads 0..127 groups 0, 4, 1, 7 and threads 128..255 groups 2, 6, 3, 5, so
+// that every element's mirror 64 - k (group 8 - j, element 7 - r; group 0:
+// element 8 - r, element 0 the packed pair) is in the same thread.  The first
+// inverse pass then applies the c2r split where it loads, and the last
+// forward pass the r2c split where it stores.
+template <bool FWD>
+__device__ __forceinline__ float2 split_dir(float2 a, float2 c, const float2 *s_tw, int k) {
+  return FWD ? split_r2c(a, c, s_tw, k) : split_c2r(a, c, s_tw, k);
+}
+
+// The split of two groups a (group ga) and b (group 8 - ga) that mirror each
+// other; with self set, a and b are groups 0 and 4, each its own mirror.
+template <bool FWD>
+__device__ __forceinline__ void rows128_split_pair(float2 (&a)[8], float2 (&b)[8], int ga, int gb, bool self,
+                                                   const float2 *s_tw) {
+  float2 na[8], nb[8];
+  if (self) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      na[r] = r == 0 ? make_float2(a[0].x + a[0].y, a[0].x - a[0].y)  // (X[0], X[N/2]) <-> H[0]
+                     : split_dir<FWD>(a[r], a[8 - r], s_tw, 8 * r);
+      nb[r] = split_dir<FWD>(b[r], b[7 - r], s_tw, 4 + 8 * r);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      na[r] = split_dir<FWD>(a[r], b[7 - r], s_tw, ga + 8 * r);
+      nb[r] = split_dir<FWD>(b[r], a[7 - r], s_tw, gb + 8 * r);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    a[r] = na[r];
+    b[r] = nb[r];
+  }
+}
+
+// First inverse row pass (radix 8, no twiddles) with the c2r split folded in.
+__device__ __forceinline__ void rows128_inv_first(float2 *tile, const float2 *s_tw) {
+  constexpr int NH = 65;
+  const int row = threadIdx.x & 127, half = threadIdx.x >> 7;
+  const int g0 = half ? 2 : 0, g1 = half ? 6 : 4, g2 = half ? 3 : 1, g3 = half ? 5 : 7;
+  float2 *rw = tile + row * NH;
+  float2 a[8], b[8], c[8], d[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    a[r] = rw[g0 + 8 * r];
+    b[r] = rw[g1 + 8 * r];
+    c[r] = rw[g2 + 8 * r];
+    d[r] = rw[g3 + 8 * r];
+  }
+  rows128_split_pair<false>(a, b, g0, g1, half == 0, s_tw);
+  rows128_split_pair<false>(c, d, g2, g3, false, s_tw);
+  RegDFT<8, true>::run(a);
+  RegDFT<8, true>::run(b);
+  RegDFT<8, true>::run(c);
+  RegDFT<8, true>::run(d);
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    rw[8 * g0 + r] = a[r];
+    rw[8 * g1 + r] = b[r];
+    rw[8 * g2 + r] = c[r];
+    rw[8 * g3 + r] = d[r];
+  }
+  __syncthreads();
+}
+
+// Second forward row pass (twiddles W_64^(n j)) with the r2c split folded in.
+// Group j takes Y_n[j] (n = 0 .. 7), which the first pass left at 8j + n,
+// and yields X[j + 8k], stored at 8j + k: the packed rows leave this pass with
+// element k of the half spectrum at place 8 (k mod 8) + k / 8 (place 0 still
+// holds (X[0], X[N/2])).  Each group's outputs land on its own inputs' places,
+// so no barrier separates the loads from the stores and each mirror pair is
+// finished before the next is loaded.
+__device__ __forceinline__ void rows128_fwd_last(float2 *tile, const float2 *s_tw) {
+  constexpr int NH = 65;
+  const int row = threadIdx.x & 127, half = threadIdx.x >> 7;
+  float2 *rw = tile + row * NH;
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {  // the mirror pairs (g0, g1) and (g2, g3), one at a time
+    const int ga = pr == 0 ? (half ? 2 : 0) : (half ? 3 : 1);
+    const int gb = pr == 0 ? (half ? 6 : 4) : (half ? 5 : 7);
+    float2 a[8], b[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      a[r] = rw[8 * ga + r];
+      b[r] = rw[8 * gb + r];
+    }
+#pragma unroll
+    for (int r = 1; r < 8; ++r) {  // W_64^(r j) = W_128^(2 r j)
+      a[r] = cmul(a[r], s_tw[((r * ga) % 64) * 2]);
+      b[r] = cmul(b[r], s_tw[((r * gb) % 64) * 2]);
+    }
+    RegDFT<8, false>::run(a);
+    RegDFT<8, false>::run(b);
+    rows128_split_pair<true>(a, b, ga, gb, pr == 0 && half == 0, s_tw);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      rw[8 * ga + r] = a[r];
+      rw[8 * gb + r] = b[r];
+    }
+  }
+  __syncthreads();
+}
+
+// The spatial step of one pixel: u = S(z + gamma), gamma' = z + gamma - u;
+// returns u - gamma' (the next iteration's w) and, for the serving residual,
+// adds the five terms of the stopping test (pu: the previous u).
+__device__ __forceinline__ float spatial_px(float z, float &g, float pu, float thr, bool resid,
+                                            float (&acc)[kResidTerms], float &u) {
+  const float v = z + g;
+  u = soft_threshold(v, thr);
+  g = v - u;
+  if (resid) {
+    acc[0] += (z - u) * (z - u);
+    acc[1] += z * z;
+    acc[2] += u * u;
+    acc[3] += (u - pu) * (u - pu);
+    acc[4] += g * g;
+  }
+  return u - g;
+}
+
+// N = 128: the second inverse row pass (radix 8, twiddles W_64^-(r j)), the
+// spatial step and the first forward row pass (radix 8, no twiddles) on one
+// thread's registers, in place.  Thread t takes row t mod 128 and groups
+// j = 4h .. 4h + 3 (h = t / 128), two at a time; the inverse pass leaves
+// h[m] = (z[2m], z[2m+1]), m = j + 8r, in slot r of group j, so slot r of the
+// pair (j, j + 1) is pixels 16r + 2j .. 16r + 2j + 3 of the row.  The forward
+// pass transforms the same group (elements j + 8 n1, over n1) and writes its
+// outputs Y_j[k1] back to the places j + 8 k1 it read, leaving the
+// transposition of the 8 x 8 split to the next pass.  Gamma is kept in the
+// matching order, pixel 8c + e of row n1 at ((2c + e / 4) 128 + n1) 4 + e % 4,
+// so that a warp's 16-byte loads are 512 contiguous bytes; U keeps the image
+// layout.  Returns after the spatial step when skip_fwd is set.
+__device__ __forceinline__ void rows128_spatial(float2 *tile, const float2 *s_tw, float *__restrict__ Gk,
+                                                float *__restrict__ Uk, float thr, bool first, bool resid,
+                                                bool wantu, bool skip_fwd, float (&acc)[kResidTerms]) {
+  constexpr int NH = 65;
+  constexpr float invP = 1.0f / (128.0f * 128.0f);
+  const int row = threadIdx.x & 127, h = threadIdx.x >> 7;
+  float2 *rw = tile + row * NH;
+  float4 *G4 = reinterpret_cast<float4 *>(Gk);
+  float4 *U4 = reinterpret_cast<float4 *>(Uk);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {
+    const int ja = 4 * h + 2 * pr, jb = ja + 1;
+    float2 a[8], b[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      a[r] = rw[ja + 8 * r];
+      b[r] = rw[jb + 8 * r];
+    }
+#pragma unroll
+    for (int r = 1; r < 8; ++r) {
+      a[r] = cmul(a[r], cconj(s_tw[((r * ja) % 64) * 2]));
+      b[r] = cmul(b[r], cconj(s_tw[((r * jb) % 64) * 2]));
+    }
+    RegDFT<8, true>::run(a);
+    RegDFT<8, true>::run(b);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int gi = (2 * (2 * r + h) + pr) * 128 + row;  // pixels 16r + 8h + 4pr .. + 3
+      const int ui = row * 32 + 4 * r + 2 * h + pr;
+      float4 g = first ? zero : G4[gi];
+      const float4 pu = resid && !first && Uk ? U4[ui] : zero;
+      float4 u;
+      a[r] = make_float2(spatial_px(a[r].x * invP, g.x, pu.x, thr, resid, acc, u.x),
+                         spatial_px(a[r].y * invP, g.y, pu.y, thr, resid, acc, u.y));
+      b[r] = make_float2(spatial_px(b[r].x * invP, g.z, pu.z, thr, resid, acc, u.z),
+                         spatial_px(b[r].y * invP, g.w, pu.w, thr, resid, acc, u.w));
+      G4[gi] = g;
+      if (wantu) U4[ui] = u;
+    }
+    if (skip_fwd) continue;
+    RegDFT<8, false>::run(a);
+    RegDFT<8, false>::run(b);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      rw[ja + 8 * r] = a[r];
+      rw[jb + 8 * r] = b[r];
+    }
+  }
+  if (!skip_fwd) __syncthreads();
+}
+
+// N = 128: the last forward column pass (radix 8 after radix 16, twiddles
+// W_128^(r j)) stores W^ straight from registers.  Group j of a column holds
+// rows j + 16r, in natural order, and its mirror rows 128 - k1 are group
+// 16 - j, element 7 - r (group 0: element 8 - r); threads 64q .. 64q + 63 take
+// the group pairs (0, 8), (4, 12) (q = 0) or (q, 16 - q), (8 - q, 8 + q), so
+// the thread of column 0, which unpacks X0^ and XN/2^ from the packed column,
+// holds every row's mirror.  The pass is in place and the last, so each pair
+// is transformed and stored before the next is loaded.
+__device__ __forceinline__ void unpack_cols0(float2 *__restrict__ Wk, float2 c, float2 cm, int k1) {
+  constexpr int NH = 65, H = 64;
+  Wk[k1 * NH] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
+  Wk[k1 * NH + H] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
+}
+
+__device__ __forceinline__ void cols128_fwd_last_store(const float2 *tile, const float2 *s_tw,
+                                                       float2 *__restrict__ Wk) {
+  constexpr int NH = 65, S = 16;
+  const int c = threadIdx.x & 63, q = threadIdx.x >> 6;
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {  // the mirror pairs, one at a time
+    const int ja = pr == 0 ? q : (q == 0 ? 4 : 8 - q);
+    const int jb = pr == 0 ? (q == 0 ? 8 : 16 - q) : (q == 0 ? 12 : 8 + q);
+    float2 a[8], b[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      a[r] = tile[(ja + S * r) * NH + c];
+      b[r] = tile[(jb + S * r) * NH + c];
+    }
+#pragma unroll
+    for (int r = 1; r < 8; ++r) {
+      a[r] = cmul(a[r], s_tw[(r * ja) % 128]);
+      b[r] = cmul(b[r], s_tw[(r * jb) % 128]);
+    }
+    RegDFT<8, false>::run(a);
+    RegDFT<8, false>::run(b);
+    if (c != 0) {
+      const int k2 = (c >> 3) + 8 * (c & 7);  // the tile's columns are in the rows' pass order
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        Wk[(ja + S * r) * NH + k2] = a[r];
+        Wk[(jb + S * r) * NH + k2] = b[r];
+      }
+    } else if (pr == 0 && q == 0) {  // groups 0 and 8, each its own mirror
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        unpack_cols0(Wk, a[r], a[(8 - r) & 7], S * r);
+        unpack_cols0(Wk, b[r], b[7 - r], 8 + S * r);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        unpack_cols0(Wk, a[r], b[7 - r], ja + S * r);
+        unpack_cols0(Wk, b[r], a[7 - r], jb + S * r);
+      }
+    }
+  }
+}
+
+// SERVE: the serving form (per-slot iteration counters, the stopping test's
+// residual terms every `check` iterations); the batch form has it.serve = 0.
+template <int N, bool SERVE>
 __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBatch &b, const float2 *__restrict__ tw,
                                                 int k, int img, float4 *hsmem) {
   constexpr int NT = HalfPlan<N>::NT, NH = N / 2 + 1, H = N / 2, Q = H / 2 + 1;
@@ -94,30 +420,32 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
   const int K = it.K;
   const int slot = b.slot[img];
   const int t = b.iter[img];
-  const bool first = it.serve ? t == 0 : it.first != 0;
-  const bool store_last = it.serve ? (t + 1) % it.check == 0 : it.last != 0;
-  const bool store_prev = it.serve && (t + 2) % it.check == 0;
-  const bool skip_fwd = !it.serve && it.last;
-  load_twiddles<N, NT>(s_tw, tw);
-
+  const bool first = SERVE ? t == 0 : it.first != 0;
+  const bool store_last = SERVE ? (t + 1) % it.check == 0 : it.last != 0;
+  const bool store_prev = SERVE && (t + 2) % it.check == 0;
+  const bool skip_fwd = !SERVE && it.last;
   const float2 *Dk = it.Dh + (size_t)k * F;
   const float2 *rr = it.r + (size_t)slot * F;
   float2 *Wk = it.What + ((size_t)slot * K + k) * F;
   float2 *Zk = it.Zp + ((size_t)slot * K + k) * F;
+  float *Gk = it.Gam + ((size_t)slot * K + k) * P;
+  // Gamma is first needed after the inverse transforms: ask L2 for it now so
+  // that its DRAM reads overlap them (16 KB per request).
+  constexpr int kPre = 16384, NPRE = P * 4 / kPre;
+  if (!first && threadIdx.x < NPRE) prefetch_l2(reinterpret_cast<const char *>(Gk) + threadIdx.x * kPre, kPre);
+  load_twiddles<N, NT>(s_tw, tw);
 
   // 1. Z~-step z = w^ + conj(d) r_p over the half spectrum.  W^ of this
   //    filter comes into the tile (its global layout) by 16-byte asynchronous
   //    copies, all in flight at once; D~ and r are read two bins per 16-byte
-  //    load, four loads deep per thread.  Then columns 0 and N/2 are packed as
-  //    z0 + i zN/2 in column 0.
+  //    load, four loads deep per thread.
   constexpr int F2 = F / 2;  // bin pairs (F is even)
   if (!first) {
     const float4 *src = reinterpret_cast<const float4 *>(Wk);
     float4 *dst = reinterpret_cast<float4 *>(tile);
     for (int c = threadIdx.x; c < F2; c += NT) cp_async16(dst + c, src + c);
-    cp_async_wait_all();
+    cp_async_commit();
   }
-  __syncthreads();
   {
     const float4 *D4 = reinterpret_cast<const float4 *>(Dk);
     const float4 *R4 = reinterpret_cast<const float4 *>(rr);
@@ -133,6 +461,10 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
           dv[u] = D4[c];
           rv[u] = R4[c];
         }
+      }
+      if (c0 == (int)threadIdx.x) {  // the first loads are in flight with the copies of W^
+        cp_async_wait<0>();
+        __syncthreads();
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -152,16 +484,34 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
     }
   }
   __syncthreads();
-  for (int k1 = threadIdx.x; k1 < N; k1 += NT) {
-    const float2 z0 = tile[k1 * NH], zh = tile[k1 * NH + H];
-    tile[k1 * NH] = make_float2(z0.x - zh.y, z0.y + zh.x);  // z0 + i zN/2
+
+  // 2. Inverse transforms along k1 (length N) of the N/2 columns, columns 0
+  //    and N/2 packed into one by the first pass.
+  cols_inv_first_packed<N>(tile);
+  half_pass<N, N / 2, HalfPlan<N>::C1, HalfPlan<N>::C0, true, 1, NH, NT, 1>(tile, s_tw);
+
+  float *Uk = b.u[img] ? b.u[img] + (size_t)k * P : nullptr;
+  const bool resid = SERVE && store_last;
+  const bool wantu = (store_last || store_prev) && Uk;
+  float acc[kResidTerms] = {0.f, 0.f, 0.f, 0.f, 0.f};
+
+  if constexpr (N == 128) {
+    // 3-7. The c2r split with the first inverse row pass; the second inverse
+    //    row pass, the spatial step and the first forward row pass on
+    //    registers; the r2c split with the second forward row pass.
+    rows128_inv_first(tile, s_tw);
+    rows128_spatial(tile, s_tw, Gk, Uk, it.thr, first, resid, wantu, skip_fwd, acc);
+    if (resid) block_sum_terms(acc, it.resid + ((size_t)slot * K + k) * kResidTerms);
+    if (skip_fwd) return;
+    rows128_fwd_last(tile, s_tw);
+    // 8-9. Forward transforms along n1, the last pass storing W^.
+    half_pass<128, 64, 16, 1, false, 1, NH, NT, 1>(tile, s_tw);
+    cols128_fwd_last_store(tile, s_tw, Wk);
+    return;
   }
-  __syncthreads();
 
-  // 2. Inverse transforms along k1 (length N) of the N/2 columns.
-  half_cols<N, true>(tile, s_tw);
-
-  // 3. Per row, the half-length spectrum of the packed real row.
+  // 3-4. Per row, the half-length spectrum of the packed real row, then its
+  //    inverse transform (length N/2): P (z[2m] + i z[2m+1]).
   for (int q = threadIdx.x; q < N * Q; q += NT) {
     const int n1 = q / Q, kk = q - n1 * Q;
     float2 *row = tile + n1 * NH;
@@ -171,20 +521,11 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
     } else {
       const int kq = H - kk;
       const float2 a = row[kk], c = row[kq];
-      const float2 wa = make_float2(s_tw[kk].x, -s_tw[kk].y);  // W_N^-k
-      const float2 wc = make_float2(s_tw[kq].x, -s_tw[kq].y);
-      // H[k] = (a + conj c) + i W^-k (a - conj c)
-      const float2 da = cmul(wa, make_float2(a.x - c.x, a.y + c.y));
-      row[kk] = make_float2(a.x + c.x - da.y, a.y - c.y + da.x);
-      if (kq != kk) {
-        const float2 dc = cmul(wc, make_float2(c.x - a.x, c.y + a.y));
-        row[kq] = make_float2(c.x + a.x - dc.y, c.y - a.y + dc.x);
-      }
+      row[kk] = split_c2r(a, c, s_tw, kk);
+      if (kq != kk) row[kq] = split_c2r(c, a, s_tw, kq);
     }
   }
   __syncthreads();
-
-  // 4. Inverse transforms of the packed rows (length N/2): P (z[2m] + i z[2m+1]).
   half_rows<N, true>(tile, s_tw);
 
   // 5. Spatial step on groups of four pixels 4j .. 4j+3 of row n1 (tile
@@ -192,11 +533,6 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
   //    Gamma (and, for the serving residual, the previous U) are read four
   //    16-byte loads deep per thread before use.
   const float invP = 1.0f / (float)P;
-  float *Gk = it.Gam + ((size_t)slot * K + k) * P;
-  float *Uk = b.u[img] ? b.u[img] + (size_t)k * P : nullptr;
-  const bool resid = it.serve && store_last;
-  const bool wantu = (store_last || store_prev) && Uk;
-  float acc[kResidTerms] = {0.f, 0.f, 0.f, 0.f, 0.f};
   {
     constexpr int Q4 = N * N / 4, J = N / 4, U = 4;
     float4 *G4 = reinterpret_cast<float4 *>(Gk);
@@ -220,28 +556,16 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
         const int n1 = q / J, j = q - n1 * J;
         float2 *tp = tile + n1 * NH + 2 * j;
         const float2 c0 = tp[0], c1 = tp[1];
-        const float z[4] = {c0.x * invP, c0.y * invP, c1.x * invP, c1.y * invP};
-        const float g[4] = {gv[u].x, gv[u].y, gv[u].z, gv[u].w};
-        const float pu[4] = {pv[u].x, pv[u].y, pv[u].z, pv[u].w};
-        float un[4], gn[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float v = z[e] + g[e];
-          un[e] = soft_threshold(v, it.thr);
-          gn[e] = v - un[e];
-          if (resid) {
-            acc[0] += (z[e] - un[e]) * (z[e] - un[e]);
-            acc[1] += z[e] * z[e];
-            acc[2] += un[e] * un[e];
-            acc[3] += (un[e] - pu[e]) * (un[e] - pu[e]);
-            acc[4] += gn[e] * gn[e];
-          }
-        }
-        G4[q] = make_float4(gn[0], gn[1], gn[2], gn[3]);
-        if (wantu) U4[q] = make_float4(un[0], un[1], un[2], un[3]);
+        float4 g = gv[u], un;
+        const float2 w0 = make_float2(spatial_px(c0.x * invP, g.x, pv[u].x, it.thr, resid, acc, un.x),
+                                      spatial_px(c0.y * invP, g.y, pv[u].y, it.thr, resid, acc, un.y));
+        const float2 w1 = make_float2(spatial_px(c1.x * invP, g.z, pv[u].z, it.thr, resid, acc, un.z),
+                                      spatial_px(c1.y * invP, g.w, pv[u].w, it.thr, resid, acc, un.w));
+        G4[q] = g;
+        if (wantu) U4[q] = un;
         if (!skip_fwd) {
-          tp[0] = make_float2(un[0] - gn[0], un[1] - gn[1]);
-          tp[1] = make_float2(un[2] - gn[2], un[3] - gn[3]);
+          tp[0] = w0;
+          tp[1] = w1;
         }
       }
     }
@@ -250,11 +574,10 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
   if (skip_fwd) return;
   __syncthreads();
 
-  // 6. Forward transforms of the packed rows h[m] = w[2m] + i w[2m+1].
+  // 6-7. Forward transforms of the packed rows h[m] = w[2m] + i w[2m+1], then
+  //    the split of each row's H into the half spectrum X[0..N/2] of its real
+  //    row; X[0] and X[N/2] are real and stay packed in element 0.
   half_rows<N, false>(tile, s_tw);
-
-  // 7. Split each row's H into the half spectrum X[0..N/2] of its real row;
-  //    X[0] and X[N/2] are real and stay packed in element 0.
   for (int q = threadIdx.x; q < N * Q; q += NT) {
     const int n1 = q / Q, kk = q - n1 * Q;
     float2 *row = tile + n1 * NH;
@@ -264,22 +587,16 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
     } else {
       const int kq = H - kk;
       const float2 a = row[kk], c = row[kq];
-      // X[k] = (a + conj c) / 2 + W^k (a - conj c) / (2i)
-      const float2 ea = cmul(s_tw[kk], make_float2(a.y + c.y, c.x - a.x));  // W^k (a - conj c) / i
-      row[kk] = make_float2(0.5f * (a.x + c.x + ea.x), 0.5f * (a.y - c.y + ea.y));
-      if (kq != kk) {
-        const float2 ec = cmul(s_tw[kq], make_float2(c.y + a.y, a.x - c.x));
-        row[kq] = make_float2(0.5f * (c.x + a.x + ec.x), 0.5f * (c.y - a.y + ec.y));
-      }
+      row[kk] = split_r2c(a, c, s_tw, kk);
+      if (kq != kk) row[kq] = split_r2c(c, a, s_tw, kq);
     }
   }
   __syncthreads();
 
-  // 8. Forward transforms along n1 of the N/2 columns.
+  // 8-9. Forward transforms along n1 of the N/2 columns, and W^ to global
+  //    memory with columns 0 and N/2 unpacked from element 0 (C = X0^ + i XN/2^,
+  //    both columns Hermitian in k1).
   half_cols<N, false>(tile, s_tw);
-
-  // 9. W^ to global memory; columns 0 and N/2 unpacked from element 0:
-  //    C = X0^ + i XN/2^ with both columns Hermitian in k1.
   for (int p = threadIdx.x; p < F; p += NT) {
     const int k1 = p / NH, k2 = p - k1 * NH;
     float2 v;
