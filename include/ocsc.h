@@ -249,6 +249,8 @@ typedef struct {
   int gram_sc;      /* samples per chunk of the tensor-core contraction */
   int plane_ctas;   /* CTAs per SM the N <= 128 coding plane kernel's register
                        budget is sized for (2 or 3) */
+  int plane_ahead;  /* 1: each plane CTA asks L2 for the data of the CTA that
+                       runs one residency later (N <= 128); 0: it does not */
 } ocsc_tuning;
 ocsc_status ocsc_get_tuning(const ocsc_ctx *ctx, int N, ocsc_tuning *out);
 

@@ -45,7 +45,7 @@ class ocsc_opts(ctypes.Structure):
 
 class ocsc_tuning(ctypes.Structure):
     _fields_ = [("fold_threads", ctypes.c_int), ("spat_cb", ctypes.c_int), ("gram_sc", ctypes.c_int),
-                ("plane_ctas", ctypes.c_int)]
+                ("plane_ctas", ctypes.c_int), ("plane_ahead", ctypes.c_int)]
 
 
 class ocsc_counters(ctypes.Structure):
@@ -216,7 +216,7 @@ def ocsc_get_tuning(ctx, N: int) -> dict:
     t = ocsc_tuning()
     _check(ctx, lib().ocsc_get_tuning(ctx, N, ctypes.byref(t)))
     return {"fold_threads": t.fold_threads, "spat_cb": t.spat_cb, "gram_sc": t.gram_sc,
-            "plane_ctas": t.plane_ctas}
+            "plane_ctas": t.plane_ctas, "plane_ahead": t.plane_ahead}
 
 
 def ocsc_set_state(ctx, state: bytes) -> None:

@@ -75,7 +75,8 @@ template <int N, int MINB, bool SERVE>
 __global__ void __launch_bounds__(HalfPlan<N>::NT, MINB)
     code_plane_kernel(CodeIter it, ImgBatch b, const float2 *__restrict__ tw) {
   extern __shared__ __align__(16) float4 hsmem[];
-  code_plane_body<N, SERVE>(it, b, tw, blockIdx.x, blockIdx.y, hsmem);
+  const int pre = it.ahead > 0 ? (int)(blockIdx.y * gridDim.x + blockIdx.x) + it.ahead : -1;
+  code_plane_body<N, SERVE>(it, b, tw, blockIdx.x, blockIdx.y, hsmem, pre < (int)(gridDim.x * gridDim.y) ? pre : -1);
 }
 
 // Building block: batched real 2D FFT (pairs of planes share one complex FFT).
@@ -199,6 +200,15 @@ static cudaError_t code_plane_nms(const CodeIter &it, const ImgBatch &b, const f
   return cudaGetLastError();
 }
 
+// CTAs of the plane kernel resident at once with MINB per SM: the distance
+// of its L2 prefetch.
+static int plane_resident(int minb) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return sms * minb;
+}
+
 template <int N, int MINB>
 static cudaError_t code_plane_n(const CodeIter &it, const ImgBatch &b, const float2 *tw, cudaStream_t s) {
   return it.serve ? code_plane_nms<N, MINB, true>(it, b, tw, s) : code_plane_nms<N, MINB, false>(it, b, tw, s);
@@ -207,12 +217,14 @@ static cudaError_t code_plane_n(const CodeIter &it, const ImgBatch &b, const flo
 int plane_resid_groups(int K) { return K; }
 
 cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, const float2 *tw,
-                              cudaStream_t s, int ctas) {
+                              cudaStream_t s, int ctas, bool ahead) {
   if (b.n <= 0) return cudaSuccess;
   const bool three = ctas == 3;
+  CodeIter ia = it;
+  ia.ahead = ahead ? plane_resident(three ? 3 : 2) : 0;
   switch (N) {
-    case 64: return three ? code_plane_n<64, 3>(it, b, tw, s) : code_plane_n<64, 2>(it, b, tw, s);
-    case 128: return three ? code_plane_n<128, 3>(it, b, tw, s) : code_plane_n<128, 2>(it, b, tw, s);
+    case 64: return three ? code_plane_n<64, 3>(ia, b, tw, s) : code_plane_n<64, 2>(ia, b, tw, s);
+    case 128: return three ? code_plane_n<128, 3>(ia, b, tw, s) : code_plane_n<128, 2>(ia, b, tw, s);
     default: return cudaErrorInvalidValue;
   }
 }

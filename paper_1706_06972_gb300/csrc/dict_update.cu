@@ -348,6 +348,12 @@ __device__ __forceinline__ float2 df_blend(float oh, float ol, float S, float E,
   return two_sum(P1, E1);
 }
 
+// acc += conj(a) b by four FMAs (one rounding per FMA).
+__device__ __forceinline__ void fold_mac(float2 &acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
+  acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
+}
+
 // Barrier `id` (not 0, which __syncthreads uses) over the first `count`
 // threads of the block, a multiple of 32.
 __device__ __forceinline__ void named_barrier_sync(int id, int count) {
@@ -429,10 +435,10 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
         for (int s = 0; s < nb; ++s) {
           const float2 zi0 = zs[s * K + i0], zi1 = hi ? zs[s * K + i0 + 1] : zero;
           const float2 zj0 = zs[s * K + j0], zj1 = hj ? zs[s * K + j0 + 1] : zero;
-          a00 = cadd(a00, cconjmul(zi0, zj0));
-          a10 = cadd(a10, cconjmul(zi1, zj0));
-          a01 = cadd(a01, cconjmul(zi0, zj1));
-          a11 = cadd(a11, cconjmul(zi1, zj1));
+          fold_mac(a00, zi0, zj0);
+          fold_mac(a10, zi1, zj0);
+          fold_mac(a01, zi0, zj1);
+          fold_mac(a11, zi1, zj1);
         }
         S[2 * t00] = a00;
         if (hi) S[2 * (t00 + 1)] = a10;

@@ -44,6 +44,10 @@ struct CodeIter {
   const float2 *xh;    // [slots][F] sample spectra
   float2 *part;        // [slots][stages][F] partial sums of D^T w^
   int *cnt;            // [slots][N/2] arrival counters (zero between launches)
+  // N <= 128: the plane kernel's CTA i asks L2 for the W^ and Gamma of CTA
+  // i + ahead (about the CTAs resident at once, so the data arrives while
+  // this CTA computes); 0 turns it off.
+  int ahead;
 };
 constexpr int kResidTerms = 5;  // |Z-U|^2, |Z|^2, |U|^2, |U-U_prev|^2, |Gamma|^2
 
@@ -54,10 +58,11 @@ cudaError_t launch_code_resid(int N, const ImgBatch &b, const CodeIter &it, floa
 // Per-slot residual sums (double, fixed order) from `groups` partials per slot.
 cudaError_t launch_resid_reduce(const int *slots_dev, int n, int groups, const float *partials,
                                 double *out, cudaStream_t s);
-// ctas: CTAs per SM the kernel's register budget is sized for (2 or 3; the
-// results are the same).
+// ctas: CTAs per SM the kernel's register budget is sized for (2 or 3);
+// ahead: L2 prefetch of the data of the CTA one residency later (CodeIter::
+// ahead).  Neither changes the results.
 cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, const float2 *tw,
-                              cudaStream_t s, int ctas = 2);
+                              cudaStream_t s, int ctas = 2, bool ahead = true);
 // Residual partial sums per slot written by code_plane in serving mode (one per CTA).
 int plane_resid_groups(int K);
 cudaError_t launch_fft2(int N, int inverse, const float *in, float *out, int planes,

@@ -387,22 +387,28 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
     io.spat_cb = s.spat_cb;
   } else if (s.plane_ctas == 0) {
     s.plane_ctas = 2;
+    s.plane_ahead = 1;
     if (c->opts.autotune) {
-      // Time both register budgets of the plane kernel on this call's slots
-      // before the first iteration (which rewrites all of W^ and Gamma it
-      // touches; the timing runs read stale multipliers r, harmlessly).
+      // Time both register budgets of the plane kernel, with and without the
+      // L2 prefetch one residency ahead, as a middle iteration (W^ and Gamma
+      // read and written) on this call's slots before its first iteration,
+      // which rewrites all of W^ and Gamma it touches: the timing runs read
+      // stale state and multipliers, harmlessly.
       CodeIter tt = it;
-      tt.first = 1;
+      tt.first = 0;
       tt.last = 0;
       float best = -1.f;
-      for (int ctas : {2, 3}) {
-        const float ms = time_runs(c, 2, [&] { return launch_code_plane(s.N, tt, bt, s.tw, c->stream, ctas); });
-        if (ms < 0.f) return cuda_fail(c, cudaGetLastError(), "autotune coding plane");
-        if (best < 0.f || ms < best) {
-          best = ms;
-          s.plane_ctas = ctas;
+      for (int ctas : {2, 3})
+        for (int ahead : {0, 1}) {
+          const float ms =
+              time_runs(c, 2, [&] { return launch_code_plane(s.N, tt, bt, s.tw, c->stream, ctas, ahead != 0); });
+          if (ms < 0.f) return cuda_fail(c, cudaGetLastError(), "autotune coding plane");
+          if (best < 0.f || ms < best) {
+            best = ms;
+            s.plane_ctas = ctas;
+            s.plane_ahead = ahead;
+          }
         }
-      }
     }
   }
   for (int t = 0; t < c->opts.Jz; ++t) {
@@ -419,7 +425,8 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
     } else {
       e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(s.N, bt, it, (float)c->rho, s.dn, s.xhp, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(s.N, it, bt, s.tw, c->stream, s.plane_ctas); });
+        e = timed(c, OCSC_K_CODE_PLANE,
+                  [&] { return launch_code_plane(s.N, it, bt, s.tw, c->stream, s.plane_ctas, s.plane_ahead != 0); });
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "code iteration");
   }
@@ -1019,6 +1026,7 @@ ocsc_status ocsc_get_tuning(const ocsc_ctx *c, int N, ocsc_tuning *out) {
       out->fold_threads = s.fold_threads;
       out->spat_cb = s.spat_cb;
       out->plane_ctas = s.plane_ctas;
+      out->plane_ahead = s.plane_ahead;
       out->gram_sc = s.gram_sc;
       return OCSC_OK;
     }

@@ -311,6 +311,9 @@ __device__ __forceinline__ void rows128_spatial(float2 *tile, const float2 *s_tw
 #pragma unroll
   for (int pr = 0; pr < 2; ++pr) {
     const int ja = 4 * h + 2 * pr, jb = ja + 1;
+    float4 g[8];  // this pair's Gamma, in flight during the inverse pass
+#pragma unroll
+    for (int r = 0; r < 8; ++r) g[r] = first ? zero : G4[(2 * (2 * r + h) + pr) * 128 + row];
     float2 a[8], b[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -328,14 +331,13 @@ __device__ __forceinline__ void rows128_spatial(float2 *tile, const float2 *s_tw
     for (int r = 0; r < 8; ++r) {
       const int gi = (2 * (2 * r + h) + pr) * 128 + row;  // pixels 16r + 8h + 4pr .. + 3
       const int ui = row * 32 + 4 * r + 2 * h + pr;
-      float4 g = first ? zero : G4[gi];
       const float4 pu = resid && !first && Uk ? U4[ui] : zero;
       float4 u;
-      a[r] = make_float2(spatial_px(a[r].x * invP, g.x, pu.x, thr, resid, acc, u.x),
-                         spatial_px(a[r].y * invP, g.y, pu.y, thr, resid, acc, u.y));
-      b[r] = make_float2(spatial_px(b[r].x * invP, g.z, pu.z, thr, resid, acc, u.z),
-                         spatial_px(b[r].y * invP, g.w, pu.w, thr, resid, acc, u.w));
-      G4[gi] = g;
+      a[r] = make_float2(spatial_px(a[r].x * invP, g[r].x, pu.x, thr, resid, acc, u.x),
+                         spatial_px(a[r].y * invP, g[r].y, pu.y, thr, resid, acc, u.y));
+      b[r] = make_float2(spatial_px(b[r].x * invP, g[r].z, pu.z, thr, resid, acc, u.z),
+                         spatial_px(b[r].y * invP, g[r].w, pu.w, thr, resid, acc, u.w));
+      G4[gi] = g[r];
       if (wantu) U4[ui] = u;
     }
     if (skip_fwd) continue;
@@ -410,9 +412,29 @@ __device__ __forceinline__ void cols128_fwd_last_store(const float2 *tile, const
 
 // SERVE: the serving form (per-slot iteration counters, the stopping test's
 // residual terms every `check` iterations); the batch form has it.serve = 0.
+// L2 prefetch of the W^ and Gamma that the plane step of (filter k, image
+// img) will read; nothing on its first iteration (neither is read then).
+template <int N, bool SERVE>
+__device__ __forceinline__ void plane_prefetch(const CodeIter &it, const ImgBatch &b, int k, int img) {
+  constexpr int F = N * (N / 2 + 1), P = N * N, kPre = 16384;
+  constexpr int NW = (F * 8 + kPre - 1) / kPre, NG = P * 4 / kPre;
+  const int t = threadIdx.x;
+  if (t >= NW + NG) return;
+  const bool first = SERVE ? b.iter[img] == 0 : it.first != 0;
+  if (first) return;
+  const size_t unit = (size_t)b.slot[img] * it.K + k;
+  if (t < NW) {
+    const int bytes = min(kPre, F * 8 - t * kPre);
+    prefetch_l2(reinterpret_cast<const char *>(it.What + unit * F) + (size_t)t * kPre, (unsigned)bytes);
+  } else {
+    prefetch_l2(reinterpret_cast<const char *>(it.Gam + unit * P) + (size_t)(t - NW) * kPre, kPre);
+  }
+}
+
+// pre: the linear unit (img * K + k) whose data to prefetch, or -1.
 template <int N, bool SERVE>
 __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBatch &b, const float2 *__restrict__ tw,
-                                                int k, int img, float4 *hsmem) {
+                                                int k, int img, float4 *hsmem, int pre = -1) {
   constexpr int NT = HalfPlan<N>::NT, NH = N / 2 + 1, H = N / 2, Q = H / 2 + 1;
   constexpr int F = N * NH, P = N * N;
   float2 *tile = reinterpret_cast<float2 *>(hsmem);  // [N][NH]
@@ -430,9 +452,11 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
   float2 *Zk = it.Zp + ((size_t)slot * K + k) * F;
   float *Gk = it.Gam + ((size_t)slot * K + k) * P;
   // Gamma is first needed after the inverse transforms: ask L2 for it now so
-  // that its DRAM reads overlap them (16 KB per request).
+  // that its DRAM reads overlap them (16 KB per request); and for the W^ and
+  // Gamma of the unit `pre`, which runs about when this one ends.
   constexpr int kPre = 16384, NPRE = P * 4 / kPre;
   if (!first && threadIdx.x < NPRE) prefetch_l2(reinterpret_cast<const char *>(Gk) + threadIdx.x * kPre, kPre);
+  if (pre >= 0) plane_prefetch<N, SERVE>(it, b, pre % K, pre / K);
   load_twiddles<N, NT>(s_tw, tw);
 
   // 1. Z~-step z = w^ + conj(d) r_p over the half spectrum.  W^ of this

@@ -722,6 +722,7 @@ def test_autotuned_tiles_do_not_change_results(precision):
     assert t[64]["fold_threads"] in (256, 512) and t[256]["fold_threads"] in (256, 512)
     assert t[256]["spat_cb"] in (8, 16) and t[64]["spat_cb"] == 0
     assert t[64]["plane_ctas"] in (2, 3) and t[256]["plane_ctas"] == 0
+    assert t[64]["plane_ahead"] in (0, 1)
     if precision:
         assert t[64]["gram_sc"] in (32, 64, 128)
 
