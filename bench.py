@@ -60,9 +60,10 @@ def hbm_peak():
 
 # DRAM bytes from ncu captures (profiles/), per unit of work, valid only while
 # the kernel's source file is the one captured (sha1 of the file).
-#   code_plane: the code128 profile case (16 images of the headline workload
-#   per launch, a middle iteration) -> bytes per image; traffic grows in
-#   proportion to the images of a launch (one CTA per image and filter).
+#   code_plane: the code128 profile case (the headline launch: 64 images of
+#   the headline workload, a middle iteration) -> bytes per image; traffic
+#   grows in proportion to the images of a launch (one CTA per image and
+#   filter).
 #   fold_factor: the fold128 profile case (the headline workload's factor at
 #   mini-batch 1) -> bytes per launch at B = 1.
 TRAFFIC_CAPTURES = {
@@ -868,7 +869,7 @@ PROFILE_CASES = {
     # name: (K, M, FFT size, images, image side, Jz, history precision[, history variant[, update]])
     "large512": (32, 11, 512, 4, 400, 10, 0),
     "large256": (32, 11, 256, 8, 200, 10, 0),
-    "code128": (100, 11, 128, 16, 100, 10, 0),
+    "code128": (100, 11, 128, 64, 100, 10, 0),
     # K = 256 dictionary step (tensor-core fold, blocked FP64 factor, substitution
     # D-step) on the FFT 64 grid: 2112 frequencies, ~1.7 GB of history and factor.
     "bigk64": (256, 11, 64, 8, 53, 5, 1),
