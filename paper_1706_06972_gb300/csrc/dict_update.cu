@@ -584,9 +584,9 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
 // D-row step of eq. (sub_d_sol): d = (w A + rho I)^-1 (w b + rho (v^ - theta^))
 // = X^H (y + rho X r) with X = L^-1, y = L^-1 (w b) and r = v^ - theta^: two
 // triangular matrix-vector products per frequency, no sequential dependency.
-// One CTA per frequency: thread i forms t_i = y_i + rho sum_{j<=i} X_ij r_j
-// (i+1 terms, consecutive threads on consecutive entries of a column), then a
-// warp per column i forms d_i = sum_{k>=i} conj(X_ki) t_k.
+// One CTA per frequency, thread i owns row i: the first product
+// t_i = y_i + rho sum_{j<=i} X_ij r_j takes i+1 terms and the second
+// d_i = sum_{k>=i} conj(X_ki) t_k takes K-i, so every thread does K+1 terms.
 // X is staged in shared memory with 16-byte cp.async copies (the per-frequency
 // stride is even, so sources are 16-byte aligned).  Also writes E = d + theta^.
 __global__ void dstep_kernel(int K, int F, float rho_eff, const float2 *__restrict__ X,
@@ -598,7 +598,6 @@ __global__ void dstep_kernel(int K, int F, float rho_eff, const float2 *__restri
   float2 *sX = dsm;
   float2 *sr = sX + TS;
   float2 *st = sr + K;
-  float2 *sth = st + K;
   const int p = blockIdx.x + p0, i = threadIdx.x;  // X holds frequencies p0 .. only
   const float4 *g4 = reinterpret_cast<const float4 *>(X + (size_t)blockIdx.x * TS);
   float4 *s4 = reinterpret_cast<float4 *>(sX);
@@ -610,7 +609,6 @@ __global__ void dstep_kernel(int K, int F, float rho_eff, const float2 *__restri
     thi = th[o];
     yi = yb[o];
     sr[i] = make_float2(v.x - thi.x, v.y - thi.y);
-    sth[i] = thi;
   }
   cp_async_wait_all();
   __syncthreads();
@@ -624,28 +622,17 @@ __global__ void dstep_kernel(int K, int F, float rho_eff, const float2 *__restri
     st[i] = make_float2(yi.x + rho_eff * acc.x, yi.y + rho_eff * acc.y);
   }
   __syncthreads();
-  // Second product by columns: a warp per column c, its lanes over rows k
-  // (consecutive entries of the packed column: no bank conflicts), then a
-  // fixed-order butterfly sum over the lanes.
-  const int warp = i >> 5, lane = i & 31, nw = blockDim.x >> 5;
-  for (int c = warp; c < K; c += nw) {
-    const float2 *col = sX + tri_off(c, K) - c;
+  if (i < K) {
+    const float2 *col = sX + tri_off(i, K) - i;
     float2 acc = make_float2(0.f, 0.f);
-    for (int k = c + lane; k < K; k += 32) {
+    for (int k = i; k < K; ++k) {
       const float2 x = col[k], tk = st[k];
       acc.x += x.x * tk.x + x.y * tk.y;
       acc.y += x.x * tk.y - x.y * tk.x;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-    }
-    if (lane == 0) {
-      const size_t o = (size_t)c * F + p;
-      Dcur[o] = acc;
-      E[o] = cadd(acc, sth[c]);
-    }
+    const size_t o = (size_t)i * F + p;
+    Dcur[o] = acc;
+    E[o] = cadd(acc, thi);
   }
 }
 
@@ -856,7 +843,7 @@ cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const flo
                          const float2 *Vh, const float2 *th, float2 *Dcur, float2 *E,
                          cudaStream_t s, int p0, int nF) {
   if (K > 256) return cudaErrorInvalidValue;
-  const size_t sm = ((size_t)tri_stride(K) + 3 * (size_t)K) * sizeof(float2);
+  const size_t sm = ((size_t)tri_stride(K) + 2 * (size_t)K) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(dstep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int threads = (K + 31) / 32 * 32;
