@@ -67,8 +67,8 @@ def hbm_peak():
 #   fold_factor: the fold128 profile case (the headline workload's factor at
 #   mini-batch 1) -> bytes per launch at B = 1.
 TRAFFIC_CAPTURES = {
-    "code_plane": {"bytes": (230526208 + 174130432) / 16, "per": "image", "file": "plane_bodies.cuh",
-                   "source_sha1": "91d52c571e078fb1834344eddc8e7d35eb34140d"},
+    "code_plane": {"bytes": (892406272 + 787821568) / 64, "per": "image", "file": "plane_bodies.cuh",
+                   "source_sha1": "39850e57356ad6aad0bf05927b6aba5f38349556"},
     "fold_factor": {"bytes": 350429440 + 625175552, "per": "launch at mini-batch 1", "file": "dict_update.cu",
                     "source_sha1": "ea40f8f4e12ac24d0ea48bd233bddb9396a7d2aa"},
 }
