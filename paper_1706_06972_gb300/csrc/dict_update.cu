@@ -238,55 +238,91 @@ __device__ __forceinline__ void fold_trail_tiles(float4 *M, int K, int j0, int n
   }
 }
 
+// Barrier `id` (not 0, which __syncthreads uses) among `count` threads (a
+// multiple of 32: whole warps), all of which execute it.
+__device__ __forceinline__ void named_barrier_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
 // Forward substitution L X = I for the pivots of panel pb (FP32, L from the
-// panel's FP32 copy): for each column c <= j0 + nb - 1 taken by the calling
-// warp (c0, c0 + cs, ...), rows i >= j0 in registers (lane + 32 m): for every
-// pivot s of the panel, X_sc *= 1 / L_ss (X_ss = 1 / L_ss when c = s), then
-// X_ic -= L_is X_sc for i > s.
-__device__ __forceinline__ void fold_xpanel(float2 *XS, const float2 *Lb, const float2 *invf, int K, int pb,
-                                            int c0, int cs, int lane) {
-  const int j0 = pb * kPanel, nb = min(kPanel, K - j0), mrows = (K - j0 + 31) / 32;
+// panel's FP32 copy in Lb, 1 / L_ss from invf): for every column c <= j0 + nb
+// - 1 and every pivot s of the panel, X_sc *= 1 / L_ss (X_ss = 1 / L_ss when
+// c = s), then X_ic -= L_is X_sc for the rows i > s.  X_ic lives in the first
+// 8 bytes of slot (i, c) of the factor's storage (XS[2 slot]).  Two steps
+// over nt threads (t = 0 .. nt-1; nt a multiple of 32, all executing named
+// barrier `bar` between the steps):
+//   1. the panel's pivot rows s = j0 .. j0+nb-1 of every column c < j0 + nb,
+//      one thread per column, in registers (X_sc *= 1 / L_ss, X_s'c -= L_s's
+//      X_sc for the later pivots s' of the panel);
+//   2. the rows below the panel, X_ic -= sum_q L_{i,j0+q} X_{j0+q,c}, by 2 x 2
+//      tiles (row pair, column pair) of that rectangle: a tile loads the nb
+//      L values of its two rows and the nb X values of its two columns once.
+__device__ __forceinline__ void fold_xpanel_tiled(float2 *XS, const float2 *Lb, const float2 *invf, int K,
+                                                  int pb, int t, int nt, int bar) {
+  const int j0 = pb * kPanel, nb = min(kPanel, K - j0), nc = j0 + nb;
   const float2 *Lq = Lb + (pb % 3) * kPanel * K;
-  float2 lr[kPanel][4];
+  const float2 zero = make_float2(0.f, 0.f);
+  for (int c = t; c < nc; c += nt) {
+    const int base = tri_off(c, K) - c;  // XS[2 (base + i)]: slot (i, c)
+    float2 x[kPanel];
 #pragma unroll
-  for (int q = 0; q < kPanel; ++q)
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int i = j0 + lane + 32 * m;
-      lr[q][m] = (q < nb && i > j0 + q && i < K) ? Lq[q * K + i] : make_float2(0.f, 0.f);
-    }
-  for (int c = c0; c < j0 + nb; c += cs) {
-    const int base = tri_off(c, K) - c;
-    float2 x[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int i = j0 + lane + 32 * m;
-      x[m] = (c < j0 && i < K) ? XS[2 * (base + i)] : make_float2(0.f, 0.f);
-    }
+    for (int q = 0; q < kPanel; ++q) x[q] = (q < nb && c < j0) ? XS[2 * (base + j0 + q)] : zero;
 #pragma unroll
     for (int q = 0; q < kPanel; ++q) {
-      const int s = j0 + q;
-      if (q >= nb || c > s) continue;
-      const float is = invf[s].x;
-      const float2 own = (c == s) ? make_float2(is, 0.f) : make_float2(x[0].x * is, x[0].y * is);
-      const float2 xs = make_float2(__shfl_sync(0xffffffffu, own.x, q), __shfl_sync(0xffffffffu, own.y, q));
-      if (lane == q) x[0] = xs;
+      const int sq = j0 + q;
+      if (q >= nb || c > sq) continue;
+      const float is = invf[sq].x;
+      const float2 xs = (c == sq) ? make_float2(is, 0.f) : make_float2(x[q].x * is, x[q].y * is);
+      x[q] = xs;
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        if (m >= mrows) break;
-        const float2 l = lr[q][m];  // zero unless row j0 + lane + 32 m > s
-        x[m].x -= l.x * xs.x - l.y * xs.y;
-        x[m].y -= l.x * xs.y + l.y * xs.x;
+      for (int q2 = q + 1; q2 < kPanel; ++q2) {
+        if (q2 >= nb) break;
+        const float2 l = Lq[q * K + j0 + q2];
+        x[q2].x -= l.x * xs.x - l.y * xs.y;
+        x[q2].y -= l.x * xs.y + l.y * xs.x;
       }
     }
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int i = j0 + lane + 32 * m;
-      if (i < K && i >= c) XS[2 * (base + i)] = x[m];
+    for (int q = 0; q < kPanel; ++q)
+      if (q < nb && j0 + q >= c) XS[2 * (base + j0 + q)] = x[q];
+  }
+  named_barrier_sync(bar, nt);
+  const int r0 = j0 + nb, nr = (K - r0 + 1) / 2, ncp = (nc + 1) / 2;
+  for (int u = t; u < nr * ncp; u += nt) {
+    const int cp = u / nr, rp = u - cp * nr;
+    const int i0 = r0 + 2 * rp, c0 = 2 * cp;
+    const bool i1 = i0 + 1 < K, c1 = c0 + 1 < nc;
+    float2 li0[kPanel], li1[kPanel], xc0[kPanel], xc1[kPanel];
+#pragma unroll
+    for (int q = 0; q < kPanel; ++q) {
+      const bool ok = q < nb;
+      const int sq = j0 + q;
+      li0[q] = ok ? Lq[q * K + i0] : zero;
+      li1[q] = ok && i1 ? Lq[q * K + i0 + 1] : zero;
+      xc0[q] = ok && c0 <= sq ? XS[2 * (tri_off(c0, K) + sq - c0)] : zero;
+      xc1[q] = ok && c1 && c0 + 1 <= sq ? XS[2 * (tri_off(c0 + 1, K) + sq - c0 - 1)] : zero;
     }
+    const int s0 = tri_off(c0, K) + i0 - c0, s1 = c1 ? tri_off(c0 + 1, K) + i0 - c0 - 1 : 0;
+    float2 v00 = c0 < j0 ? XS[2 * s0] : zero, v10 = i1 && c0 < j0 ? XS[2 * (s0 + 1)] : zero;
+    float2 v01 = c1 && c0 + 1 < j0 ? XS[2 * s1] : zero, v11 = i1 && c1 && c0 + 1 < j0 ? XS[2 * (s1 + 1)] : zero;
+#pragma unroll
+    for (int q = 0; q < kPanel; ++q) {
+      if (q >= nb) break;
+      v00.x -= li0[q].x * xc0[q].x - li0[q].y * xc0[q].y;
+      v00.y -= li0[q].x * xc0[q].y + li0[q].y * xc0[q].x;
+      v10.x -= li1[q].x * xc0[q].x - li1[q].y * xc0[q].y;
+      v10.y -= li1[q].x * xc0[q].y + li1[q].y * xc0[q].x;
+      v01.x -= li0[q].x * xc1[q].x - li0[q].y * xc1[q].y;
+      v01.y -= li0[q].x * xc1[q].y + li0[q].y * xc1[q].x;
+      v11.x -= li1[q].x * xc1[q].x - li1[q].y * xc1[q].y;
+      v11.y -= li1[q].x * xc1[q].y + li1[q].y * xc1[q].x;
+    }
+    XS[2 * s0] = v00;
+    if (i1) XS[2 * (s0 + 1)] = v10;
+    if (c1) XS[2 * s1] = v01;
+    if (i1 && c1) XS[2 * (s1 + 1)] = v11;
   }
 }
-
 
 // One CTA per frequency p.
 //
@@ -305,9 +341,9 @@ __device__ __forceinline__ void fold_xpanel(float2 *XS, const float2 *Lb, const 
 //                  inside the panel, y);
 //        warps 1.. apply panel b's update to the rest of the trailing triangle
 //                  (fold_trail_tiles, 2 x 2 register tiles) and run the
-//                  forward substitution L X = I for
-//                  the pivots of panel b-1 (fold_xpanel), a warp per column of
-//                  X with its rows in registers.
+//                  forward substitution L X = I for the pivots of panel b-1
+//                  (fold_xpanel_tiled: the pivot rows a column per thread,
+//                  then the rows below by 2 x 2 register tiles).
 //      The trailing triangle is folded into a rectangle (row r: column r, then
 //      column n-1-r) whose rows go to warps and entries to lanes, so every
 //      packed offset is a per-row base plus the lane's index.  X_ic is written
@@ -352,12 +388,6 @@ __device__ __forceinline__ float2 df_blend(float oh, float ol, float S, float E,
 __device__ __forceinline__ void fold_mac(float2 &acc, float2 a, float2 b) {
   acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
   acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
-}
-
-// Barrier `id` (not 0, which __syncthreads uses) over the first `count`
-// threads of the block, a multiple of 32.
-__device__ __forceinline__ void named_barrier_sync(int id, int count) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 template <int kFoldThreads, bool DF>
@@ -552,7 +582,7 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
   __syncthreads();
 
   // 3. Blocked Cholesky (double-float), y alongside, X = L^-1 one panel behind.
-  const int warp = tid >> 5, lane = tid & 31, nwarps = kFoldThreads / 32;
+  const int warp = tid >> 5, lane = tid & 31;
   const float rho_fb = a.rho_eff > 0.0 ? (float)a.rho_eff : 1.f;
   const int nblk = (K + kPanel - 1) / kPanel;
   if (warp == 0) fold_panel(M, y, invf, Lb, K, 0, lane, a.err, rho_fb);
@@ -570,7 +600,7 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
         __syncwarp();
         if (nb2 > 0) fold_panel(M, y, invf, Lb, K, b + 1, lane, a.err, rho_fb);
       } else if (b >= 1) {
-        fold_xpanel(XS, Lb, invf, K, b - 1, warp - 1, nwarps - 1, lane);
+        fold_xpanel_tiled(XS, Lb, invf, K, b - 1, tid - 32, kFoldThreads - 32, 2);
       }
     } else {
       // Here nb2 = rw = kPanel: warps 0 .. kPanel-1 update one column of the
@@ -583,12 +613,12 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
         fold_panel(M, y, invf, Lb, K, b + 1, lane, a.err, rho_fb);
       } else {
         fold_trail_tiles(M, K, j0, nb, rw, tid - 32, kFoldThreads - 32);
-        if (b >= 1) fold_xpanel(XS, Lb, invf, K, b - 1, warp - 1, nwarps - 1, lane);
+        if (b >= 1) fold_xpanel_tiled(XS, Lb, invf, K, b - 1, tid - 32, kFoldThreads - 32, 2);
       }
     }
     __syncthreads();
   }
-  fold_xpanel(XS, Lb, invf, K, nblk - 1, warp, nwarps, lane);
+  fold_xpanel_tiled(XS, Lb, invf, K, nblk - 1, tid, kFoldThreads, 2);
   __syncthreads();
 
   // 4. Store X = L^-1 (FP32) and y = L^-1 (w b) (FP32).
