@@ -19,7 +19,7 @@
 
 namespace ocsc {
 
-constexpr int kFoldChunk = 8;   // samples per staged chunk (two chunk buffers)
+constexpr int kFoldChunk = 16;  // samples staged in shared memory at once
 constexpr int kPanel = 4;       // columns per Cholesky panel
 
 // 1 / sqrt(p) for p = ph + pl > 0 as a pair: the FP32 estimate r0 (a few
@@ -353,7 +353,7 @@ __device__ __forceinline__ void fold_xpanel_tiled(float2 *XS, const float2 *Lb, 
 // 4.   Store X (FP32, packed lower) and y (FP32).
 //
 // Shared memory: M [T] float4, y [K] float4 (double-float), invf [K] float2,
-// Lb [3][kPanel][K] float2, zs / xs (two chunks of pending codes).  During the
+// Lb [3][kPanel][K] float2, zs / xs (a chunk of pending codes).  During the
 // fold each M slot first holds the FP32 running sum of conj(z_i) z_j in its
 // first 8 bytes.
 // DF (history precision 3): the products conj(z_i) z_j and x~ conj(z_i) are
@@ -399,8 +399,8 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
   float4 *y = M + T;                                             // [K] double-float
   float2 *invf = reinterpret_cast<float2 *>(y + K);              // [K] 1 / L_jj, double-float
   float2 *Lb = invf + K;                                         // [3][kPanel][K]
-  float2 *zs0 = Lb + 3 * kPanel * K;                             // [2][kFoldChunk][K]
-  float2 *xs0 = zs0 + 2 * kFoldChunk * K;                        // [2][kFoldChunk]
+  float2 *zs = Lb + 3 * kPanel * K;                              // [kFoldChunk][K]
+  float2 *xs = zs + kFoldChunk * K;                              // [kFoldChunk]
   float2 *S = reinterpret_cast<float2 *>(M);                     // FP32 sums, stride 2
   float2 *XS = reinterpret_cast<float2 *>(M);                    // X_ic at slot t: XS[2 t]
   // Frequency p of the class's grid (a band context factors rows p0 .. of
@@ -423,31 +423,19 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
 
   // 1. FP32 sums over the pending samples of conj(z_i) z_j and x~ conj(z_i).
   //    The codes of frequency p (one 8-byte word per sample and filter, F
-  //    apart) come in chunks of kFoldChunk samples by asynchronous copies,
-  //    the next chunk in flight while the current one is summed.
+  //    apart) come in chunks of kFoldChunk samples, every copy of a chunk in
+  //    flight at once (asynchronous copies).
   const int mt = (K + 1) / 2, ntile = mt * (mt + 1) / 2;
-  const int nfold = a.prefolded ? 0 : B;
-  auto stage = [&](int c0, int buf) {
+  for (int c0 = 0; c0 < (a.prefolded ? 0 : B); c0 += kFoldChunk) {
     const int nb = min(kFoldChunk, B - c0);
-    float2 *zb = zs0 + buf * kFoldChunk * K, *xb = xs0 + buf * kFoldChunk;
+    __syncthreads();
     for (int e = tid; e < nb * K; e += kFoldThreads) {
       const int s = e / K, k = e - s * K;
-      cp_async8(zb + s * K + k, a.Zp + ((size_t)(c0 + s) * K + k) * zF + zp);
+      cp_async8(zs + s * K + k, a.Zp + ((size_t)(c0 + s) * K + k) * zF + zp);
     }
-    for (int s = tid; s < nb; s += kFoldThreads) cp_async8(xb + s, a.xh + (size_t)(c0 + s) * zF + zp);
-    cp_async_commit();
-  };
-  if (nfold > 0) stage(0, 0);
-  for (int c0 = 0, buf = 0; c0 < nfold; c0 += kFoldChunk, buf ^= 1) {
-    const int nb = min(kFoldChunk, B - c0);
-    if (c0 + kFoldChunk < nfold) {
-      stage(c0 + kFoldChunk, buf ^ 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
+    for (int s = tid; s < nb; s += kFoldThreads) cp_async8(xs + s, a.xh + (size_t)(c0 + s) * zF + zp);
+    cp_async_wait_all();
     __syncthreads();
-    const float2 *zs = zs0 + buf * kFoldChunk * K, *xs = xs0 + buf * kFoldChunk;
     // 2 x 2 tiles of the lower triangle (rows i0, i0 + 1, columns j0, j0 + 1):
     // the four codes of a sample are loaded once for the tile's four entries.
     // Entries outside the triangle (above the diagonal of a diagonal tile,
@@ -502,7 +490,6 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
           for (int s = 0; s < nb; ++s) sb[m] = cadd(sb[m], cmulc(xs[s], zs[s * K + i]));
       }
     }
-    __syncthreads();  // this buffer is staged again two chunks on
   }
   __syncthreads();
 
@@ -865,7 +852,7 @@ __global__ void dict_norms_kernel(int K, int F, const float2 *__restrict__ Dh, f
 
 size_t fold_smem_bytes(int K) {
   return (size_t)(tri_size(K) + K) * sizeof(float4) + (size_t)(1 + 3 * kPanel) * K * sizeof(float2) +
-         (size_t)2 * kFoldChunk * K * sizeof(float2) + 2 * kFoldChunk * sizeof(float2);
+         (size_t)kFoldChunk * K * sizeof(float2) + kFoldChunk * sizeof(float2);
 }
 
 // threads: 256 or 512 (CTA size of the per-frequency factorisation; every
