@@ -14,7 +14,7 @@
  *                       (sub_d_sol) with C^p = (A^p + rho I)^-1 = X^H X, X the
  *                       inverse of the Cholesky factor (computed in
  *                       double-float, FP32 hi + lo pairs, ~48 significant
- *                       bits; FP64 for K > 128), the support +
+ *                       bits; for K > 128 the factor L itself), the support +
  *                       unit-ball projection of Proposition 2 and the scaled
  *                       dual update.
  *   ocsc_get_dict    -- the filters D_t (Algorithm 3, last loop).
@@ -447,7 +447,7 @@ typedef enum {
                                 the spectral row kernels) */
   OCSC_K_CODE_PLANE = 2,     /* fused code-ADMM iteration per filter pair (N >= 256:
                                 the spatial column kernel) */
-  OCSC_K_FOLD_FACTOR = 3,    /* history fold + Cholesky (double-float; FP64 for K > 128)
+  OCSC_K_FOLD_FACTOR = 3,    /* history fold + Cholesky (double-float)
                                 + FP32 L^-1 per frequency; with history = 1 the
                                 Sherman-Morrison fold */
   OCSC_K_DSTEP = 4,          /* D-row solve of eq. (sub_d_sol) */

@@ -1,21 +1,23 @@
 // Dictionary step for K > 128 filters (up to 256), where one frequency's
-// packed K x K FP64 matrix (K(K+1)/2 x 16 bytes, 526 KB at K = 256) no longer
-// fits a CTA's shared memory.  Same mathematics as dict_update.cu (Sec. III-B
-// history fold, eq. (sub_d_sol) D-row solve with the FP64 Cholesky factor of
-// w A^p + rho I), different blocking:
+// packed K x K double-float matrix (K(K+1)/2 x 16 bytes, 526 KB at K = 256) no
+// longer fits a CTA's shared memory.  Same mathematics as dict_update.cu
+// (Sec. III-B history fold, eq. (sub_d_sol) D-row solve with the Cholesky
+// factor of w A^p + rho I), different blocking:
 //
 //   fold_big    FP32 fold A <- alpha A + beta sum_i conj(z_i) z_i^T and b on
 //               the CUDA cores (the all-FP32 path; the tensor-core fold of
 //               history_tc.cu is the other one);
-//   factor_big  blocked right-looking Cholesky in FP64: a persistent CTA keeps
-//               the packed matrix of the frequency it works on in a global
-//               FP64 workspace of its own (L2-resident), factors panels of 32
+//   factor_big  blocked right-looking Cholesky in double-float (FP32 pairs,
+//               ~48 bits, on the FP32 pipe): a persistent CTA keeps the packed
+//               matrix of the frequency it works on in a global workspace of
+//               its own (16 bytes per entry, L2-resident), factors panels of 32
 //               columns in shared memory and applies each panel to the
 //               trailing matrix with 2 x 2 register tiles; w b rides along as
 //               an extra column, giving y = L^-1 (w b).  Stores L in FP32;
 //   dstep_big   one warp per frequency: d = L^-H (y + rho L^-1 (v^ - theta^))
 //               by forward and back substitution with the FP32 factor.
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "launch.h"
 
 namespace ocsc {
@@ -25,14 +27,6 @@ namespace {
 constexpr int kBigThreads = 256;
 constexpr int kNB = 32;     // panel width of factor_big
 constexpr int kFoldS = 32;  // samples staged per chunk in fold_big
-
-// acc -= a * conj(b) (four FP64 FMAs).
-__device__ __forceinline__ void dfms_conj(double2 &acc, double2 a, double2 b) {
-  acc.x = fma(-a.x, b.x, acc.x);
-  acc.x = fma(-a.y, b.y, acc.x);
-  acc.y = fma(-a.y, b.x, acc.y);
-  acc.y = fma(a.x, b.y, acc.y);
-}
 
 // Micro-tile u of the lower triangle of an R x R matrix tiled by 2 x 2:
 // (mi, mk) with mk <= mi, enumerated row by row.
@@ -104,33 +98,51 @@ __global__ void __launch_bounds__(kBigThreads) fold_big_kernel(FoldArgs a) {
   }
 }
 
-// Persistent: CTA c factors frequencies c, c + gridDim.x, ...  Shared memory:
-// the panel Pn[K][kNB + 1] (rows J0.. of the current panel columns), y[K],
-// 1 / L_jj of the panel.
+// Persistent: CTA c factors frequencies c, c + gridDim.x, ...  All of the
+// factorisation is in double-float (dfloat.cuh: hi + lo FP32 pairs, complex
+// entries as float4 (re hi, im hi, re lo, im lo)), as in fold_factor; the
+// global workspace of a CTA holds its frequency's packed matrix in that form
+// (16 bytes per entry).  Shared memory: the panel Pn[K][kNB + 1] (rows J0..
+// of the current panel columns), y[K], 1 / L_jj of the panel.
 __global__ void __launch_bounds__(kBigThreads, 1) factor_big_kernel(FoldArgs a, double2 *work) {
   extern __shared__ __align__(16) unsigned char fks[];
   const int K = a.K, F = a.F, T = tri_size(K), TS = tri_stride(K);
   constexpr int PS = kNB + 1;
-  double2 *Pn = reinterpret_cast<double2 *>(fks);  // [K][PS]
-  double2 *yv = Pn + (size_t)K * PS;               // [K]
-  double *invd = reinterpret_cast<double *>(yv + K);  // [kNB]
-  double2 *W = work + (size_t)blockIdx.x * TS;
+  float4 *Pn = reinterpret_cast<float4 *>(fks);        // [K][PS]
+  float4 *yv = Pn + (size_t)K * PS;                    // [K]
+  float2 *invd = reinterpret_cast<float2 *>(yv + K);   // [kNB]
+  float4 *W = reinterpret_cast<float4 *>(work) + (size_t)blockIdx.x * TS;
+  const float2 wf = df_of(a.w), rf = df_of(a.rho_eff);
+  const float rho_fb = a.rho_eff > 0.0 ? (float)a.rho_eff : 1.f;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   const int tid = threadIdx.x;
   for (int p = blockIdx.x; p < F; p += gridDim.x) {
     const float2 *Ap = a.A + (size_t)p * TS;
     const float2 *Lo = a.Alo ? a.Alo + (size_t)p * TS : nullptr;
-    // 0. W = w A + rho I in FP64, y = w b.
+    // 0. W = w A + rho I, y = w b (A as its FP32 word plus compensation word).
     for (int t = tid; t < T; t += kBigThreads) {
       int i, j;
       tri_ij(t, K, i, j);
       const float2 v = Ap[t];
       const float2 l = Lo ? Lo[t] : make_float2(0.f, 0.f);
-      const double x = (double)v.x + (double)l.x, y = (double)v.y + (double)l.y;
-      W[t] = i == j ? make_double2(a.w * x + a.rho_eff, 0.0) : make_double2(a.w * x, a.w * y);
+      float Sr, Er, Si, Ei;
+      df_mul(v.x, l.x, wf.x, wf.y, Sr, Er);
+      df_mul(v.y, l.y, wf.x, wf.y, Si, Ei);
+      if (i == j) {
+        const float2 s2 = two_sum(Sr, rf.x);
+        Sr = s2.x;
+        Er += s2.y + rf.y;
+        Si = 0.f;
+        Ei = 0.f;
+      }
+      W[t] = make_float4(Sr, Si, Er, Ei);
     }
     for (int i = tid; i < K; i += kBigThreads) {
       const float2 bv = a.b[(size_t)i * F + p];
-      yv[i] = make_double2(a.w * (double)bv.x, a.w * (double)bv.y);
+      float Sr, Er, Si, Ei;
+      df_mul(bv.x, 0.f, wf.x, wf.y, Sr, Er);
+      df_mul(bv.y, 0.f, wf.x, wf.y, Si, Ei);
+      yv[i] = make_float4(Sr, Si, Er, Ei);
     }
     __syncthreads();
     float2 *Lp = a.L + (size_t)p * TS;
@@ -145,40 +157,36 @@ __global__ void __launch_bounds__(kBigThreads, 1) factor_big_kernel(FoldArgs a, 
       // b. unblocked right-looking factorisation of the panel; y carried.
       for (int c = 0; c < nbj; ++c) {
         if (tid == 0) {
-          double piv = Pn[c * PS + c].x;
-          if (!(piv > 0.0)) {
+          const float4 d = Pn[c * PS + c];
+          float2 pv = two_sum(d.x, d.z);
+          if (!(pv.x > 0.f)) {
             atomicOr(a.err, ERR_PIVOT);
-            piv = a.rho_eff > 0.0 ? a.rho_eff : 1.0;
+            pv = make_float2(rho_fb, 0.f);
           }
-          const double l = sqrt(piv);
-          Pn[c * PS + c] = make_double2(l, 0.0);
-          invd[c] = 1.0 / l;
-          yv[J0 + c].x /= l;
-          yv[J0 + c].y /= l;
+          const float2 r = df_rsqrt(pv.x, pv.y);
+          float S, E;
+          df_mul(pv.x, pv.y, r.x, r.y, S, E);
+          const float2 ljj = two_sum(S, E);  // L_jj = p / sqrt(p)
+          Pn[c * PS + c] = make_float4(ljj.x, 0.f, ljj.y, 0.f);
+          invd[c] = r;
+          yv[J0 + c] = df_scale(yv[J0 + c], r);
         }
         __syncthreads();
-        const double inv = invd[c];
-        for (int r = c + 1 + tid; r < R0; r += kBigThreads) {
-          double2 v = Pn[r * PS + c];
-          v.x *= inv;
-          v.y *= inv;
-          Pn[r * PS + c] = v;
-        }
+        const float2 inv = invd[c];
+        for (int r = c + 1 + tid; r < R0; r += kBigThreads) Pn[r * PS + c] = df_scale(Pn[r * PS + c], inv);
         __syncthreads();
         const int ncol = nbj - c - 1;
         for (int e = tid; e < ncol * R0; e += kBigThreads) {
           const int c2 = c + 1 + e / R0, r = e % R0;
           if (r < c2) continue;
-          double2 v = Pn[r * PS + c2];
-          dfms_conj(v, Pn[r * PS + c], Pn[c2 * PS + c]);
+          float4 v = Pn[r * PS + c2];
+          df_sub_lconjm(v, Pn[r * PS + c], Pn[c2 * PS + c]);
           Pn[r * PS + c2] = v;
         }
-        const double2 yc = yv[J0 + c];
+        const float4 yc = yv[J0 + c];
         for (int r = c + 1 + tid; r < R0; r += kBigThreads) {
-          const double2 l = Pn[r * PS + c];
-          double2 v = yv[J0 + r];
-          v.x -= l.x * yc.x - l.y * yc.y;
-          v.y -= l.x * yc.y + l.y * yc.x;
+          float4 v = yv[J0 + r];
+          df_sub_lm(v, Pn[r * PS + c], yc);
           yv[J0 + r] = v;
         }
         __syncthreads();
@@ -187,11 +195,13 @@ __global__ void __launch_bounds__(kBigThreads, 1) factor_big_kernel(FoldArgs a, 
       for (int c = 0; c < nbj; ++c) {
         const int off = tri_off(J0 + c, K);
         for (int r = c + tid; r < R0; r += kBigThreads) {
-          const double2 v = Pn[r * PS + c];
-          Lp[off + r - c] = make_float2((float)v.x, (float)v.y);
+          const float4 v = Pn[r * PS + c];
+          Lp[off + r - c] = make_float2(v.x + v.z, v.y + v.w);
         }
       }
-      // d. trailing update W[i][k] -= sum_c L[i][c] conj(L[k][c]), J1 <= k <= i.
+      // d. trailing update W[i][k] -= sum_c L[i][c] conj(L[k][c]), J1 <= k <= i:
+      //    each 2 x 2 tile sums its panel products in double-float registers,
+      //    then adds them to W.
       const int J1 = J0 + nbj, R = K - J1;
       if (R > 0) {
         const int hh = (R + 1) / 2, tiles = hh * (hh + 1) / 2;
@@ -200,15 +210,15 @@ __global__ void __launch_bounds__(kBigThreads, 1) factor_big_kernel(FoldArgs a, 
           micro_tile(u, mi, mk);
           const int i0 = nbj + 2 * mi, k0 = nbj + 2 * mk;  // panel rows (relative to J0)
           const bool i1 = i0 + 1 < R0, k1 = k0 + 1 < R0;
-          double2 acc[2][2] = {};
+          float4 acc[2][2] = {{zero4, zero4}, {zero4, zero4}};
           for (int c = 0; c < nbj; ++c) {
-            const double2 a0 = Pn[i0 * PS + c], b0 = Pn[k0 * PS + c];
-            const double2 a1 = i1 ? Pn[(i0 + 1) * PS + c] : make_double2(0.0, 0.0);
-            const double2 b1 = k1 ? Pn[(k0 + 1) * PS + c] : make_double2(0.0, 0.0);
-            dfms_conj(acc[0][0], a0, b0);
-            dfms_conj(acc[0][1], a0, b1);
-            dfms_conj(acc[1][0], a1, b0);
-            dfms_conj(acc[1][1], a1, b1);
+            const float4 a0 = Pn[i0 * PS + c], b0 = Pn[k0 * PS + c];
+            const float4 a1 = i1 ? Pn[(i0 + 1) * PS + c] : zero4;
+            const float4 b1 = k1 ? Pn[(k0 + 1) * PS + c] : zero4;
+            df_sub_lconjm(acc[0][0], a0, b0);
+            df_sub_lconjm(acc[0][1], a0, b1);
+            df_sub_lconjm(acc[1][0], a1, b0);
+            df_sub_lconjm(acc[1][1], a1, b1);
           }
 #pragma unroll
           for (int di = 0; di < 2; ++di)
@@ -216,10 +226,9 @@ __global__ void __launch_bounds__(kBigThreads, 1) factor_big_kernel(FoldArgs a, 
             for (int dk = 0; dk < 2; ++dk) {
               const int i = J0 + i0 + di, k = J0 + k0 + dk;
               if (i >= K || k > i) continue;
-              double2 *dst = W + tri_off(k, K) + i - k;
-              double2 v = *dst;
-              v.x += acc[di][dk].x;
-              v.y += acc[di][dk].y;
+              float4 *dst = W + tri_off(k, K) + i - k;
+              float4 v = *dst;
+              df_acc2(v, acc[di][dk]);
               *dst = v;
             }
         }
@@ -227,7 +236,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) factor_big_kernel(FoldArgs a, 
       __syncthreads();
     }
     for (int i = tid; i < K; i += kBigThreads)
-      a.g[(size_t)i * F + p] = make_float2((float)yv[i].x, (float)yv[i].y);
+      a.g[(size_t)i * F + p] = make_float2(yv[i].x + yv[i].z, yv[i].y + yv[i].w);
     __syncthreads();
   }
 }
@@ -320,7 +329,7 @@ cudaError_t launch_fold_big(const FoldArgs &a, cudaStream_t s) {
 size_t factor_big_workspace(int K, int ctas) { return (size_t)ctas * tri_stride(K); }
 
 cudaError_t launch_factor_big(const FoldArgs &a, double2 *work, int ctas, cudaStream_t s) {
-  const size_t sm = ((size_t)a.K * (kNB + 1) + a.K) * sizeof(double2) + kNB * sizeof(double);
+  const size_t sm = ((size_t)a.K * (kNB + 1) + a.K) * sizeof(float4) + kNB * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(factor_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   factor_big_kernel<<<ctas, kBigThreads, sm, s>>>(a, work);

@@ -22,57 +22,6 @@ namespace ocsc {
 constexpr int kFoldChunk = 16;  // samples staged in shared memory at once
 constexpr int kPanel = 4;       // columns per Cholesky panel
 
-// 1 / sqrt(p) for p = ph + pl > 0 as a pair: the FP32 estimate r0 (a few
-// ulp) refined by one Newton step r0 (1 + e / 2), e = 1 - p r0^2 formed in
-// double-float, which squares the relative error.
-__device__ __forceinline__ float2 df_rsqrt(float ph, float pl) {
-  const float r0 = rsqrtf(ph);
-  float S, E;
-  df_mul(r0, 0.f, r0, 0.f, S, E);
-  const float2 q = two_sum(S, E);
-  df_mul(ph, pl, q.x, q.y, S, E);
-  const float2 pr = two_sum(S, E);
-  const float2 e1 = two_sum(1.f, -pr.x);
-  const float e = e1.x + (e1.y - pr.y);
-  return two_sum(r0, 0.5f * r0 * e);
-}
-
-// Normalised pair product (v re, v im) x r for a complex pair v (possibly
-// unnormalised) and a real pair r.
-__device__ __forceinline__ float4 df_scale(float4 v, float2 r) {
-  const float2 vr = two_sum(v.x, v.z), vi = two_sum(v.y, v.w);
-  float Sr, Er, Si, Ei;
-  df_mul(vr.x, vr.y, r.x, r.y, Sr, Er);
-  df_mul(vi.x, vi.y, r.x, r.y, Si, Ei);
-  const float2 a = two_sum(Sr, Er), b = two_sum(Si, Ei);
-  return make_float4(a.x, b.x, a.y, b.y);
-}
-
-// v -= l conj(m) (complex pairs; v unnormalised).
-__device__ __forceinline__ void df_sub_lconjm(float4 &v, const float4 &l, const float4 &m) {
-  df_mac(-l.x, -l.z, m.x, m.z, v.x, v.z);  // Re: - Re l Re m - Im l Im m
-  df_mac(-l.y, -l.w, m.y, m.w, v.x, v.z);
-  df_mac(-l.y, -l.w, m.x, m.z, v.y, v.w);  // Im: - Im l Re m + Re l Im m
-  df_mac(l.x, l.z, m.y, m.w, v.y, v.w);
-}
-
-// w = -l conj(m) (complex pairs, unnormalised): the first product of each
-// part needs no TwoSum.
-__device__ __forceinline__ void df_neg_lconjm(float4 &w, const float4 &l, const float4 &m) {
-  df_mul(-l.x, -l.z, m.x, m.z, w.x, w.z);  // Re: - Re l Re m
-  df_mac(-l.y, -l.w, m.y, m.w, w.x, w.z);  //     - Im l Im m
-  df_mul(-l.y, -l.w, m.x, m.z, w.y, w.w);  // Im: - Im l Re m
-  df_mac(l.x, l.z, m.y, m.w, w.y, w.w);    //     + Re l Im m
-}
-
-// v -= l m (complex pairs; v unnormalised).
-__device__ __forceinline__ void df_sub_lm(float4 &v, const float4 &l, const float4 &m) {
-  df_mac(-l.x, -l.z, m.x, m.z, v.x, v.z);  // Re: - Re l Re m + Im l Im m
-  df_mac(l.y, l.w, m.y, m.w, v.x, v.z);
-  df_mac(-l.x, -l.z, m.y, m.w, v.y, v.w);  // Im: - Re l Im m - Im l Re m
-  df_mac(-l.y, -l.w, m.x, m.z, v.y, v.w);
-}
-
 // Factor panel pb (columns j0 .. j0+nb-1, all rows below) by one warp: pivot,
 // scaling of the column (kept in registers and as an FP32 copy in Lb), y, and
 // the update of the panel's later columns; lanes take rows j+1+lane+32m.

@@ -108,7 +108,7 @@ struct FoldArgs {
   float2 *b;            // [K][F]
   const float2 *Zp;     // [B][K][F]
   const float2 *xh;     // [B][F]
-  float2 *L;            // [F][stride] X = L^-1 of the FP64 Cholesky factor, FP32
+  float2 *L;            // [F][stride] X = L^-1 of the double-float Cholesky factor, FP32 (K > 128: L)
   float2 *g;            // [K][F]  y = L^-1 (w b)
   int *err;
   // prefolded = 1: A (+ Alo when not null) and b (+ blo when not null) already
@@ -160,7 +160,7 @@ cudaError_t launch_sm_fold(const SmArgs &a, cudaStream_t s);
 cudaError_t launch_dstep_sm(int K, int F, double r, double ths, const float4 *Cf, const float2 *b,
                             const float2 *Vh, float2 *th, float2 *Dcur, float2 *E, cudaStream_t s);
 
-// K > 128 (dict_big.cu): FP32 fold into A, b; blocked FP64 Cholesky of
+// K > 128 (dict_big.cu): FP32 fold into A, b; blocked double-float Cholesky of
 // w (A + Alo) + rho I storing L (FP32, in FoldArgs::L) and y = L^-1 (w b);
 // D-step by substitution with L.
 cudaError_t launch_fold_big(const FoldArgs &a, cudaStream_t s);

@@ -636,8 +636,8 @@ def test_history_fold_precision_matches_oracle(precision):
 
 @pytest.mark.parametrize("K,precision", [(136, 0), (136, 2), (256, 0), (256, 1), (256, 2)])
 def test_large_K_factor_matches_oracle(K, precision):
-    """K > 128: blocked FP64 Cholesky through the global workspace, D-step by
-    substitution, FP32 or tensor-core fold (two 128-row blocks); K = 256 is the
+    """K > 128: blocked double-float Cholesky through the global workspace,
+    D-step by substitution, FP32 or tensor-core fold (two 128-row blocks); K = 256 is the
     precision workload's filter count.  Relative objective, dictionary error
     and code error against the FP64 oracle per result."""
     _need_gpu()
