@@ -138,12 +138,16 @@ __device__ __forceinline__ void fold_trail(float4 *M, int K, int j0, int nb, int
 // o <= kk <= ii < n (local coordinates of the trailing triangle, whose first
 // row and column are j1 = j0 + nb), by 2 x 2 tiles of that sub-triangle:
 // tile (ti, tk), ti >= tk, holds rows o + 2 ti (+1) and columns o + 2 tk (+1),
-// and thread t of nt takes tiles t, t + nt, ... in packed lower-triangular
-// order (consecutive threads: consecutive row tiles of one column tile, whose
-// L values they share).  A tile loads the nb panel entries of its two rows
+// numbered in packed lower-triangular order (consecutive tiles: consecutive
+// row tiles of one column tile, whose L values they share).  A tile loads the
+// nb panel entries of its two rows
 // and two columns once for its (up to) four entries, and updates the four in
 // independent double-float chains.
-__device__ __forceinline__ void fold_trail_tiles(float4 *M, int K, int j0, int nb, int o, int t, int nt) {
+//
+// The calling warps take the tiles 32 at a time from the shared counter *ctr
+// (zero on entry; lane 0 claims, the warp's lanes take consecutive tiles), so
+// a warp that finishes its other work of the phase early takes more of them.
+__device__ __forceinline__ void fold_trail_tiles(float4 *M, int K, int j0, int nb, int o, int *ctr) {
   const int j1 = j0 + nb, n = K - j1, m = n - o;
   if (m <= 0) return;
   const int mt = (m + 1) / 2, ntiles = mt * (mt + 1) / 2;
@@ -151,7 +155,14 @@ __device__ __forceinline__ void fold_trail_tiles(float4 *M, int K, int j0, int n
 #pragma unroll
   for (int q = 0; q < kPanel; ++q) cq[q] = q < nb ? tri_off(j0 + q, K) - j0 - q + j1 : 0;
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  for (int u = t; u < ntiles; u += nt) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(ctr, 32);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= ntiles) break;
+    const int u = base + lane;
+    if (u >= ntiles) continue;
     int ti, tk;
     tri_ij(u, mt, ti, tk);
     const int r0 = o + 2 * ti, c0 = o + 2 * tk;
@@ -288,8 +299,9 @@ __device__ __forceinline__ void fold_xpanel_tiled(float2 *XS, const float2 *Lb, 
 //                  panel b+1 (fold_panel: pivots 1/sqrt by an FP32 estimate and
 //                  one double-float Newton step, column scaling, the update
 //                  inside the panel, y);
-//        warps 1.. apply panel b's update to the rest of the trailing triangle
-//                  (fold_trail_tiles, 2 x 2 register tiles) and run the
+//        all warps apply panel b's update to the rest of the trailing
+//                  triangle (fold_trail_tiles, 2 x 2 register tiles claimed
+//                  32 at a time: warp 0 joins after its panel), warps 1.. run the
 //                  forward substitution L X = I for the pivots of panel b-1
 //                  (fold_xpanel_tiled: the pivot rows a column per thread,
 //                  then the rows below by 2 x 2 register tiles).
@@ -521,6 +533,8 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
   const int warp = tid >> 5, lane = tid & 31;
   const float rho_fb = a.rho_eff > 0.0 ? (float)a.rho_eff : 1.f;
   const int nblk = (K + kPanel - 1) / kPanel;
+  __shared__ int s_ctr[2];  // tile counters of the trailing update, by phase parity
+  if (tid < 2) s_ctr[tid] = 0;
   if (warp == 0) fold_panel(M, y, invf, Lb, K, 0, lane, a.err, rho_fb);
   __syncthreads();
   for (int b = 0; b < nblk; ++b) {
@@ -547,10 +561,12 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
       }
       if (warp == 0) {
         fold_panel(M, y, invf, Lb, K, b + 1, lane, a.err, rho_fb);
+        fold_trail_tiles(M, K, j0, nb, rw, &s_ctr[b & 1]);
       } else {
-        fold_trail_tiles(M, K, j0, nb, rw, tid - 32, kFoldThreads - 32);
+        fold_trail_tiles(M, K, j0, nb, rw, &s_ctr[b & 1]);
         if (b >= 1) fold_xpanel_tiled(XS, Lb, invf, K, b - 1, tid - 32, kFoldThreads - 32, 2);
       }
+      if (tid == 0) s_ctr[(b + 1) & 1] = 0;  // the next phase's counter (unused in this one)
     }
     __syncthreads();
   }
