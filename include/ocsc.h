@@ -110,7 +110,9 @@ typedef struct {
                          fastest: threads per CTA of the factorisation
                          (256 or 512), columns per CTA of the N >= 256 spatial
                          FFT kernel in ocsc_code (8 or 16), CTAs per SM of the
-                         N <= 128 coding plane kernel (2 or 3), samples per
+                         N <= 128 coding plane kernel (256 threads at 2 or 3,
+                         512 threads at 2, each with and without the L2
+                         look-ahead), samples per
                          chunk of the tensor-core contraction (32, 64, 128).  Every
                          candidate performs the same operations in the same
                          order, so results do not depend on the choice.
@@ -251,8 +253,19 @@ typedef struct {
                        budget is sized for (2 or 3) */
   int plane_ahead;  /* 1: each plane CTA asks L2 for the data of the CTA that
                        runs one residency later (N <= 128); 0: it does not */
+  int plane_threads; /* CTA size of the N <= 128 coding plane kernel (256, or
+                        512 at N = 128 with 2 CTAs per SM) */
 } ocsc_tuning;
 ocsc_status ocsc_get_tuning(const ocsc_ctx *ctx, int N, ocsc_tuning *out);
+/* Pin tile shapes of FFT size N before (or instead of) the autotuner: every
+ * nonzero field is checked and kept, and the autotuner leaves a pinned knob
+ * alone.  plane_ctas != 0 sets the plane kernel's shape (plane_threads 256
+ * with plane_ctas 2 or 3, or 512 with 2 at N = 128; plane_ahead 0 or 1);
+ * fold_threads 256 or 512; spat_cb 8 or 16 for N >= 256 where supported;
+ * gram_sc must be 0.  No tile shape changes any result (each performs the
+ * same operations in the same order).  OCSC_EINVAL on a bad value (nothing
+ * is changed), OCSC_EUNSUPPORTED if the context has no class of side N. */
+ocsc_status ocsc_set_tuning(ocsc_ctx *ctx, int N, const ocsc_tuning *in);
 
 /* Block until all work queued on ctx's stream is done; reports device errors. */
 ocsc_status ocsc_sync(ocsc_ctx *ctx);

@@ -45,7 +45,7 @@ class ocsc_opts(ctypes.Structure):
 
 class ocsc_tuning(ctypes.Structure):
     _fields_ = [("fold_threads", ctypes.c_int), ("spat_cb", ctypes.c_int), ("gram_sc", ctypes.c_int),
-                ("plane_ctas", ctypes.c_int), ("plane_ahead", ctypes.c_int)]
+                ("plane_ctas", ctypes.c_int), ("plane_ahead", ctypes.c_int), ("plane_threads", ctypes.c_int)]
 
 
 class ocsc_counters(ctypes.Structure):
@@ -84,6 +84,7 @@ _PROTOS = {
     "ocsc_drop_pending": (_I, [_P]),
     "ocsc_get_state": (_I, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
     "ocsc_get_tuning": (_I, [_P, _I, _P]),
+    "ocsc_set_tuning": (_I, [_P, _I, _P]),
     "ocsc_set_state": (_I, [_P, _P, ctypes.c_size_t]),
     "ocsc_objective": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_I), ctypes.POINTER(_I),
                             ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_double)]),
@@ -216,7 +217,14 @@ def ocsc_get_tuning(ctx, N: int) -> dict:
     t = ocsc_tuning()
     _check(ctx, lib().ocsc_get_tuning(ctx, N, ctypes.byref(t)))
     return {"fold_threads": t.fold_threads, "spat_cb": t.spat_cb, "gram_sc": t.gram_sc,
-            "plane_ctas": t.plane_ctas, "plane_ahead": t.plane_ahead}
+            "plane_ctas": t.plane_ctas, "plane_ahead": t.plane_ahead, "plane_threads": t.plane_threads}
+
+
+def ocsc_set_tuning(ctx, N: int, **fields) -> None:
+    t = ocsc_tuning()
+    for k, v in fields.items():
+        setattr(t, k, int(v))
+    _check(ctx, lib().ocsc_set_tuning(ctx, N, ctypes.byref(t)))
 
 
 def ocsc_set_state(ctx, state: bytes) -> None:
@@ -400,6 +408,10 @@ class OCSC:
     def get_state(self) -> bytes:
         """Checkpoint of the learner (no samples may be pending)."""
         return ocsc_get_state(self.ctx)
+
+    def set_tuning(self, N: int, **fields) -> None:
+        """Pin tile shapes of FFT size N (ocsc_set_tuning); fields as tuning()."""
+        ocsc_set_tuning(self.ctx, N, **fields)
 
     def tuning(self, N: int) -> dict:
         """Tile shapes the autotuner picked for FFT size N."""

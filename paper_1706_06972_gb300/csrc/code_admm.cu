@@ -68,15 +68,18 @@ __global__ void code_resid_kernel(int K, int F, float rho, int first, int serve,
 }
 
 // One fused ADMM iteration for filter k of one sample (grid: K x images).
-// MINB is the number of CTAs per SM the register budget is sized for (2: no
-// spills; 3: a few spilled registers, more overlap); both perform the same
-// operations in the same order.  SERVE selects the serving form of the body.
-template <int N, int MINB, bool SERVE>
-__global__ void __launch_bounds__(HalfPlan<N>::NT, MINB)
+// NT threads per CTA (256; 512 for N = 128), MINB the number of CTAs per SM
+// the register budget is sized for (256 threads: 2, no spills, or 3, a few
+// spilled registers; 512 threads: 2, with half the values per thread); every
+// form performs the same operations in the same order.  SERVE selects the
+// serving form of the body.
+template <int N, int MINB, bool SERVE, int NT>
+__global__ void __launch_bounds__(NT, MINB)
     code_plane_kernel(CodeIter it, ImgBatch b, const float2 *__restrict__ tw) {
   extern __shared__ __align__(16) float4 hsmem[];
   const int pre = it.ahead > 0 ? (int)(blockIdx.y * gridDim.x + blockIdx.x) + it.ahead : -1;
-  code_plane_body<N, SERVE>(it, b, tw, blockIdx.x, blockIdx.y, hsmem, pre < (int)(gridDim.x * gridDim.y) ? pre : -1);
+  code_plane_body<N, SERVE, NT>(it, b, tw, blockIdx.x, blockIdx.y, hsmem,
+                                pre < (int)(gridDim.x * gridDim.y) ? pre : -1);
 }
 
 // Building block: batched real 2D FFT (pairs of planes share one complex FFT).
@@ -190,13 +193,13 @@ cudaError_t launch_code_resid(int N, const ImgBatch &b, const CodeIter &it, floa
   return cudaGetLastError();
 }
 
-template <int N, int MINB, bool SERVE>
+template <int N, int MINB, bool SERVE, int NT>
 static cudaError_t code_plane_nms(const CodeIter &it, const ImgBatch &b, const float2 *tw, cudaStream_t s) {
   const size_t sm = half_smem_bytes<N>();
-  cudaError_t e = set_smem(code_plane_kernel<N, MINB, SERVE>, sm);
+  cudaError_t e = set_smem(code_plane_kernel<N, MINB, SERVE, NT>, sm);
   if (e != cudaSuccess) return e;
   dim3 grid(it.K, b.n);
-  code_plane_kernel<N, MINB, SERVE><<<grid, HalfPlan<N>::NT, sm, s>>>(it, b, tw);
+  code_plane_kernel<N, MINB, SERVE, NT><<<grid, NT, sm, s>>>(it, b, tw);
   return cudaGetLastError();
 }
 
@@ -209,24 +212,29 @@ static int plane_resident(int minb) {
   return sms * minb;
 }
 
-template <int N, int MINB>
+template <int N, int MINB, int NT = 256>
 static cudaError_t code_plane_n(const CodeIter &it, const ImgBatch &b, const float2 *tw, cudaStream_t s) {
-  return it.serve ? code_plane_nms<N, MINB, true>(it, b, tw, s) : code_plane_nms<N, MINB, false>(it, b, tw, s);
+  return it.serve ? code_plane_nms<N, MINB, true, NT>(it, b, tw, s) : code_plane_nms<N, MINB, false, NT>(it, b, tw, s);
 }
 
 int plane_resid_groups(int K) { return K; }
 
+bool plane_shape_ok(int N, int threads, int ctas) {
+  if (N != 64 && N != 128) return false;
+  if (threads == 256) return ctas == 2 || ctas == 3;
+  return N == 128 && threads == 512 && ctas == 2;
+}
+
 cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, const float2 *tw,
-                              cudaStream_t s, int ctas, bool ahead) {
+                              cudaStream_t s, int ctas, bool ahead, int threads) {
   if (b.n <= 0) return cudaSuccess;
-  const bool three = ctas == 3;
+  if (!plane_shape_ok(N, threads, ctas)) return cudaErrorInvalidValue;
   CodeIter ia = it;
-  ia.ahead = ahead ? plane_resident(three ? 3 : 2) : 0;
-  switch (N) {
-    case 64: return three ? code_plane_n<64, 3>(ia, b, tw, s) : code_plane_n<64, 2>(ia, b, tw, s);
-    case 128: return three ? code_plane_n<128, 3>(ia, b, tw, s) : code_plane_n<128, 2>(ia, b, tw, s);
-    default: return cudaErrorInvalidValue;
-  }
+  ia.ahead = ahead ? plane_resident(ctas) : 0;
+  if (threads == 512) return code_plane_n<128, 2, 512>(ia, b, tw, s);
+  const bool three = ctas == 3;
+  if (N == 64) return three ? code_plane_n<64, 3>(ia, b, tw, s) : code_plane_n<64, 2>(ia, b, tw, s);
+  return three ? code_plane_n<128, 3>(ia, b, tw, s) : code_plane_n<128, 2>(ia, b, tw, s);
 }
 
 template <int N, bool INV>

@@ -48,7 +48,7 @@ struct SizeClass {
   long long n_seen = 0;
   int pending = 0;
   // tile shapes picked by the autotuner (0 = not tuned yet)
-  int fold_threads = 0, spat_cb = 0, gram_sc = 0, plane_ctas = 0, plane_ahead = 1;
+  int fold_threads = 0, spat_cb = 0, gram_sc = 0, plane_ctas = 0, plane_ahead = 1, plane_threads = 256;
   // graph path of ocsc_code: image and code staging per slot (lazily allocated)
   float *xstage = nullptr;  // [max_batch][N*N]
   float *ustage = nullptr;  // [max_batch][K][N*N]

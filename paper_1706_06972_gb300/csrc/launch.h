@@ -58,11 +58,14 @@ cudaError_t launch_code_resid(int N, const ImgBatch &b, const CodeIter &it, floa
 // Per-slot residual sums (double, fixed order) from `groups` partials per slot.
 cudaError_t launch_resid_reduce(const int *slots_dev, int n, int groups, const float *partials,
                                 double *out, cudaStream_t s);
-// ctas: CTAs per SM the kernel's register budget is sized for (2 or 3);
-// ahead: L2 prefetch of the data of the CTA one residency later (CodeIter::
-// ahead).  Neither changes the results.
+// threads: CTA size (256; 512 for N = 128); ctas: CTAs per SM the kernel's
+// register budget is sized for (2 or 3 with 256 threads, 2 with 512); ahead:
+// L2 prefetch of the data of the CTA one residency later (CodeIter::ahead).
+// None of them changes the results; an unsupported shape returns
+// cudaErrorInvalidValue.
 cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, const float2 *tw,
-                              cudaStream_t s, int ctas = 2, bool ahead = true);
+                              cudaStream_t s, int ctas = 2, bool ahead = true, int threads = 256);
+bool plane_shape_ok(int N, int threads, int ctas);
 // Residual partial sums per slot written by code_plane in serving mode (one per CTA).
 int plane_resid_groups(int K);
 cudaError_t launch_fft2(int N, int inverse, const float *in, float *out, int planes,

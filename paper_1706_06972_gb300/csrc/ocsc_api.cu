@@ -388,27 +388,33 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
   } else if (s.plane_ctas == 0) {
     s.plane_ctas = 2;
     s.plane_ahead = 1;
+    s.plane_threads = 256;
     if (c->opts.autotune) {
-      // Time both register budgets of the plane kernel, with and without the
-      // L2 prefetch one residency ahead, as a middle iteration (W^ and Gamma
-      // read and written) on this call's slots before its first iteration,
-      // which rewrites all of W^ and Gamma it touches: the timing runs read
-      // stale state and multipliers, harmlessly.
+      // Time the plane kernel's CTA shapes (256 threads at 2 or 3 CTAs per
+      // SM, 512 threads at 2), each with and without the L2 prefetch one
+      // residency ahead, as a middle iteration (W^ and Gamma read and
+      // written) on this call's slots before its first iteration, which
+      // rewrites all of W^ and Gamma it touches: the timing runs read stale
+      // state and multipliers, harmlessly.
       CodeIter tt = it;
       tt.first = 0;
       tt.last = 0;
       float best = -1.f;
-      for (int ctas : {2, 3})
+      const int shapes[3][2] = {{256, 2}, {256, 3}, {512, 2}};
+      for (const auto &sh : shapes) {
+        if (!plane_shape_ok(s.N, sh[0], sh[1])) continue;
         for (int ahead : {0, 1}) {
-          const float ms =
-              time_runs(c, 2, [&] { return launch_code_plane(s.N, tt, bt, s.tw, c->stream, ctas, ahead != 0); });
+          const float ms = time_runs(
+              c, 2, [&] { return launch_code_plane(s.N, tt, bt, s.tw, c->stream, sh[1], ahead != 0, sh[0]); });
           if (ms < 0.f) return cuda_fail(c, cudaGetLastError(), "autotune coding plane");
           if (best < 0.f || ms < best) {
             best = ms;
-            s.plane_ctas = ctas;
+            s.plane_threads = sh[0];
+            s.plane_ctas = sh[1];
             s.plane_ahead = ahead;
           }
         }
+      }
     }
   }
   for (int t = 0; t < c->opts.Jz; ++t) {
@@ -425,8 +431,9 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
     } else {
       e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(s.N, bt, it, (float)c->rho, s.dn, s.xhp, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_CODE_PLANE,
-                  [&] { return launch_code_plane(s.N, it, bt, s.tw, c->stream, s.plane_ctas, s.plane_ahead != 0); });
+        e = timed(c, OCSC_K_CODE_PLANE, [&] {
+          return launch_code_plane(s.N, it, bt, s.tw, c->stream, s.plane_ctas, s.plane_ahead != 0, s.plane_threads);
+        });
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "code iteration");
   }
@@ -1027,10 +1034,37 @@ ocsc_status ocsc_get_tuning(const ocsc_ctx *c, int N, ocsc_tuning *out) {
       out->spat_cb = s.spat_cb;
       out->plane_ctas = s.plane_ctas;
       out->plane_ahead = s.plane_ahead;
+      out->plane_threads = s.plane_threads;
       out->gram_sc = s.gram_sc;
       return OCSC_OK;
     }
   return OCSC_EUNSUPPORTED;
+}
+
+ocsc_status ocsc_set_tuning(ocsc_ctx *c, int N, const ocsc_tuning *in) {
+  if (!c || !in) return OCSC_EINVAL;
+  for (SizeClass &s : c->cls)
+    if (s.N == N) {
+      const bool plane = in->plane_ctas != 0;
+      if (plane && (large_fft(N) || !plane_shape_ok(N, in->plane_threads, in->plane_ctas) ||
+                    (in->plane_ahead != 0 && in->plane_ahead != 1)))
+        return fail(c, OCSC_EINVAL, "ocsc_set_tuning: unsupported plane kernel shape");
+      if (in->fold_threads != 0 && in->fold_threads != 256 && in->fold_threads != 512)
+        return fail(c, OCSC_EINVAL, "ocsc_set_tuning: fold_threads must be 256 or 512");
+      if (in->spat_cb != 0 && (!large_fft(N) || !large_cb_ok(N, in->spat_cb)))
+        return fail(c, OCSC_EINVAL, "ocsc_set_tuning: unsupported spat_cb");
+      if (in->gram_sc != 0)
+        return fail(c, OCSC_EINVAL, "ocsc_set_tuning: gram_sc is chosen by the library (pass 0)");
+      if (plane) {
+        s.plane_ctas = in->plane_ctas;
+        s.plane_threads = in->plane_threads;
+        s.plane_ahead = in->plane_ahead;
+      }
+      if (in->fold_threads) s.fold_threads = in->fold_threads;
+      if (in->spat_cb) s.spat_cb = in->spat_cb;
+      return OCSC_OK;
+    }
+  return fail(c, OCSC_EUNSUPPORTED, "ocsc_set_tuning: no size class of that FFT side");
 }
 
 ocsc_status ocsc_sync(ocsc_ctx *c) {

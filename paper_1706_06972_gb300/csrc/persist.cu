@@ -82,7 +82,7 @@ __device__ __noinline__ void small_unit(const PersistArgs &a, const PersistClass
     code_resid_body(it.K, F, it.rho, it.first, 0, a.b, it.Dh, it.dn, it.xh, it.What, it.r, v % NB, c.n0 + v / NB,
                     threadIdx.x & 31, threadIdx.x >> 5);
   } else {
-    code_plane_body<N, false>(it, a.b, c.tw, v % it.K, c.n0 + v / it.K, psm);
+    code_plane_body<N, false, 256>(it, a.b, c.tw, v % it.K, c.n0 + v / it.K, psm);
   }
 }
 

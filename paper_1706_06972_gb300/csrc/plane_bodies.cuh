@@ -128,10 +128,10 @@ __device__ __forceinline__ float2 split_r2c(float2 a, float2 c, const float2 *s_
 // First inverse column pass (radix C0, no twiddles) over the Z~ tile, with
 // columns 0 and N/2 packed as z0 + i zN/2 where the thread of column 0 loads
 // them.
-template <int N>
+template <int N, int NT>
 __device__ __forceinline__ void cols_inv_first_packed(float2 *tile) {
   using P = HalfPlan<N>;
-  constexpr int NT = P::NT, NH = N / 2 + 1, H = N / 2, R = P::C0, LINES = N / 2, STEP = N / R;
+  constexpr int NH = N / 2 + 1, H = N / 2, R = P::C0, LINES = N / 2, STEP = N / R;
   constexpr int G = LINES * STEP, PER = G / NT;
   static_assert(G % NT == 0, "threads must divide the butterfly groups");
   float2 v[PER][R];
@@ -161,12 +161,18 @@ __device__ __forceinline__ void cols_inv_first_packed(float2 *tile) {
 }
 
 // N = 128: rows of 64 points by two radix-8 passes.  A thread takes one row
-// and four of its eight butterfly groups (group j holds elements j + 8r):
-// threads 0..127 groups 0, 4, 1, 7 and threads 128..255 groups 2, 6, 3, 5, so
-// that every element's mirror 64 - k (group 8 - j, element 7 - r; group 0:
-// element 8 - r, element 0 the packed pair) is in the same thread.  The first
+// and whole mirror pairs of its eight butterfly groups (group j holds
+// elements j + 8r; element k's mirror 64 - k is group 8 - j, element 7 - r,
+// and for group 0 element 8 - r, element 0 the packed pair): pair P = 0 is
+// groups (0, 4), each its own mirror, and pairs 1, 2, 3 are (P, 8 - P).  With
+// NT threads a CTA has NT / 128 threads per row and each takes 512 / NT
+// pairs: threads 128 h .. 128 h + 127 pairs h (512 / NT) onwards.  The first
 // inverse pass then applies the c2r split where it loads, and the last
 // forward pass the r2c split where it stores.
+__device__ __forceinline__ void mirror_pair(int P, int &ga, int &gb) {
+  ga = P == 0 ? 0 : P;
+  gb = P == 0 ? 4 : 8 - P;
+}
 template <bool FWD>
 __device__ __forceinline__ float2 split_dir(float2 a, float2 c, const float2 *s_tw, int k) {
   return FWD ? split_r2c(a, c, s_tw, k) : split_c2r(a, c, s_tw, k);
@@ -200,32 +206,35 @@ __device__ __forceinline__ void rows128_split_pair(float2 (&a)[8], float2 (&b)[8
 }
 
 // First inverse row pass (radix 8, no twiddles) with the c2r split folded in.
+template <int NT>
 __device__ __forceinline__ void rows128_inv_first(float2 *tile, const float2 *s_tw) {
-  constexpr int NH = 65;
-  const int row = threadIdx.x & 127, half = threadIdx.x >> 7;
-  const int g0 = half ? 2 : 0, g1 = half ? 6 : 4, g2 = half ? 3 : 1, g3 = half ? 5 : 7;
+  constexpr int NH = 65, NPAIR = 512 / NT;
+  const int row = threadIdx.x & 127, P0 = (threadIdx.x >> 7) * NPAIR;
   float2 *rw = tile + row * NH;
-  float2 a[8], b[8], c[8], d[8];
+  float2 a[NPAIR][8], b[NPAIR][8];
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    a[r] = rw[g0 + 8 * r];
-    b[r] = rw[g1 + 8 * r];
-    c[r] = rw[g2 + 8 * r];
-    d[r] = rw[g3 + 8 * r];
+  for (int pp = 0; pp < NPAIR; ++pp) {
+    int ga, gb;
+    mirror_pair(P0 + pp, ga, gb);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      a[pp][r] = rw[ga + 8 * r];
+      b[pp][r] = rw[gb + 8 * r];
+    }
+    rows128_split_pair<false>(a[pp], b[pp], ga, gb, P0 + pp == 0, s_tw);
+    RegDFT<8, true>::run(a[pp]);
+    RegDFT<8, true>::run(b[pp]);
   }
-  rows128_split_pair<false>(a, b, g0, g1, half == 0, s_tw);
-  rows128_split_pair<false>(c, d, g2, g3, false, s_tw);
-  RegDFT<8, true>::run(a);
-  RegDFT<8, true>::run(b);
-  RegDFT<8, true>::run(c);
-  RegDFT<8, true>::run(d);
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < 8; ++r) {
-    rw[8 * g0 + r] = a[r];
-    rw[8 * g1 + r] = b[r];
-    rw[8 * g2 + r] = c[r];
-    rw[8 * g3 + r] = d[r];
+  for (int pp = 0; pp < NPAIR; ++pp) {
+    int ga, gb;
+    mirror_pair(P0 + pp, ga, gb);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      rw[8 * ga + r] = a[pp][r];
+      rw[8 * gb + r] = b[pp][r];
+    }
   }
   __syncthreads();
 }
@@ -237,14 +246,15 @@ __device__ __forceinline__ void rows128_inv_first(float2 *tile, const float2 *s_
 // holds (X[0], X[N/2])).  Each group's outputs land on its own inputs' places,
 // so no barrier separates the loads from the stores and each mirror pair is
 // finished before the next is loaded.
+template <int NT>
 __device__ __forceinline__ void rows128_fwd_last(float2 *tile, const float2 *s_tw) {
-  constexpr int NH = 65;
-  const int row = threadIdx.x & 127, half = threadIdx.x >> 7;
+  constexpr int NH = 65, NPAIR = 512 / NT;
+  const int row = threadIdx.x & 127, P0 = (threadIdx.x >> 7) * NPAIR;
   float2 *rw = tile + row * NH;
 #pragma unroll
-  for (int pr = 0; pr < 2; ++pr) {  // the mirror pairs (g0, g1) and (g2, g3), one at a time
-    const int ga = pr == 0 ? (half ? 2 : 0) : (half ? 3 : 1);
-    const int gb = pr == 0 ? (half ? 6 : 4) : (half ? 5 : 7);
+  for (int pp = 0; pp < NPAIR; ++pp) {
+    int ga, gb;
+    mirror_pair(P0 + pp, ga, gb);
     float2 a[8], b[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -258,7 +268,7 @@ __device__ __forceinline__ void rows128_fwd_last(float2 *tile, const float2 *s_t
     }
     RegDFT<8, false>::run(a);
     RegDFT<8, false>::run(b);
-    rows128_split_pair<true>(a, b, ga, gb, pr == 0 && half == 0, s_tw);
+    rows128_split_pair<true>(a, b, ga, gb, P0 + pp == 0, s_tw);
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
       rw[8 * ga + r] = a[r];
@@ -288,32 +298,38 @@ __device__ __forceinline__ float spatial_px(float z, float &g, float pu, float t
 
 // N = 128: the second inverse row pass (radix 8, twiddles W_64^-(r j)), the
 // spatial step and the first forward row pass (radix 8, no twiddles) on one
-// thread's registers, in place.  Thread t takes row t mod 128 and groups
-// j = 4h .. 4h + 3 (h = t / 128), two at a time; the inverse pass leaves
-// h[m] = (z[2m], z[2m+1]), m = j + 8r, in slot r of group j, so slot r of the
-// pair (j, j + 1) is pixels 16r + 2j .. 16r + 2j + 3 of the row.  The forward
-// pass transforms the same group (elements j + 8 n1, over n1) and writes its
-// outputs Y_j[k1] back to the places j + 8 k1 it read, leaving the
-// transposition of the 8 x 8 split to the next pass.  Gamma is kept in the
-// matching order, pixel 8c + e of row n1 at ((2c + e / 4) 128 + n1) 4 + e % 4,
-// so that a warp's 16-byte loads are 512 contiguous bytes; U keeps the image
-// layout.  Returns after the spatial step when skip_fwd is set.
+// thread's registers, in place.  Thread t takes row t mod 128 and the group
+// pairs (2P, 2P + 1), P = (t / 128) (512 / NT) .. (one or two pairs), one pair
+// at a time; the inverse pass leaves h[m] = (z[2m], z[2m+1]), m = j + 8r, in
+// slot r of group j, so slot r of the pair is pixels 16r + 4P .. 16r + 4P + 3
+// of the row.  The forward pass transforms the same group (elements j + 8 n1,
+// over n1) and writes its outputs Y_j[k1] back to the places j + 8 k1 it read,
+// leaving the transposition of the 8 x 8 split to the next pass.  Gamma is
+// kept in the matching order, pixels 16r + 4P .. + 3 of row n1 at float4
+// (4r + P) 128 + n1, so that a warp's 16-byte loads are 512 contiguous bytes
+// (pixel 8c + e of row n1 at ((2c + e / 4) 128 + n1) 4 + e % 4); U keeps the
+// image layout.  With 256 threads a pair's eight Gamma loads are issued before
+// its inverse pass.  Returns after the spatial step when skip_fwd is set.
+template <int NT>
 __device__ __forceinline__ void rows128_spatial(float2 *tile, const float2 *s_tw, float *__restrict__ Gk,
                                                 float *__restrict__ Uk, float thr, bool first, bool resid,
                                                 bool wantu, bool skip_fwd, float (&acc)[kResidTerms]) {
-  constexpr int NH = 65;
+  constexpr int NH = 65, NPAIR = 512 / NT;
+  constexpr bool HOIST = NT == 256;
   constexpr float invP = 1.0f / (128.0f * 128.0f);
-  const int row = threadIdx.x & 127, h = threadIdx.x >> 7;
+  const int row = threadIdx.x & 127, P0 = (threadIdx.x >> 7) * NPAIR;
   float2 *rw = tile + row * NH;
   float4 *G4 = reinterpret_cast<float4 *>(Gk);
   float4 *U4 = reinterpret_cast<float4 *>(Uk);
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-  for (int pr = 0; pr < 2; ++pr) {
-    const int ja = 4 * h + 2 * pr, jb = ja + 1;
-    float4 g[8];  // this pair's Gamma, in flight during the inverse pass
+  for (int pp = 0; pp < NPAIR; ++pp) {
+    const int P = P0 + pp, ja = 2 * P, jb = ja + 1;
+    float4 g[HOIST ? 8 : 1];
+    if constexpr (HOIST) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) g[r] = first ? zero : G4[(2 * (2 * r + h) + pr) * 128 + row];
+      for (int r = 0; r < 8; ++r) g[r] = first ? zero : G4[(4 * r + P) * 128 + row];
+    }
     float2 a[8], b[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -329,15 +345,18 @@ __device__ __forceinline__ void rows128_spatial(float2 *tile, const float2 *s_tw
     RegDFT<8, true>::run(b);
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      const int gi = (2 * (2 * r + h) + pr) * 128 + row;  // pixels 16r + 8h + 4pr .. + 3
-      const int ui = row * 32 + 4 * r + 2 * h + pr;
+      const int gi = (4 * r + P) * 128 + row;  // pixels 16r + 4P .. + 3
+      const int ui = row * 32 + 4 * r + P;
+      float4 gr;
+      if constexpr (HOIST) gr = g[r];
+      else gr = first ? zero : G4[gi];
       const float4 pu = resid && !first && Uk ? U4[ui] : zero;
       float4 u;
-      a[r] = make_float2(spatial_px(a[r].x * invP, g[r].x, pu.x, thr, resid, acc, u.x),
-                         spatial_px(a[r].y * invP, g[r].y, pu.y, thr, resid, acc, u.y));
-      b[r] = make_float2(spatial_px(b[r].x * invP, g[r].z, pu.z, thr, resid, acc, u.z),
-                         spatial_px(b[r].y * invP, g[r].w, pu.w, thr, resid, acc, u.w));
-      G4[gi] = g[r];
+      a[r] = make_float2(spatial_px(a[r].x * invP, gr.x, pu.x, thr, resid, acc, u.x),
+                         spatial_px(a[r].y * invP, gr.y, pu.y, thr, resid, acc, u.y));
+      b[r] = make_float2(spatial_px(b[r].x * invP, gr.z, pu.z, thr, resid, acc, u.z),
+                         spatial_px(b[r].y * invP, gr.w, pu.w, thr, resid, acc, u.w));
+      G4[gi] = gr;
       if (wantu) U4[ui] = u;
     }
     if (skip_fwd) continue;
@@ -355,23 +374,27 @@ __device__ __forceinline__ void rows128_spatial(float2 *tile, const float2 *s_tw
 // N = 128: the last forward column pass (radix 8 after radix 16, twiddles
 // W_128^(r j)) stores W^ straight from registers.  Group j of a column holds
 // rows j + 16r, in natural order, and its mirror rows 128 - k1 are group
-// 16 - j, element 7 - r (group 0: element 8 - r); threads 64q .. 64q + 63 take
-// the group pairs (0, 8), (4, 12) (q = 0) or (q, 16 - q), (8 - q, 8 + q), so
-// the thread of column 0, which unpacks X0^ and XN/2^ from the packed column,
-// holds every row's mirror.  The pass is in place and the last, so each pair
-// is transformed and stored before the next is loaded.
+// 16 - j, element 7 - r (group 0: element 8 - r).  The eight group pairs
+// are (0, 8), (4, 12) and, for q = 1 .. 3, (q, 16 - q), (8 - q, 8 + q): pair
+// index 2q + pr, and with NT threads threads 64i .. 64i + 63 take the 512 / NT
+// pairs from i (512 / NT) on, so the thread of column 0, which unpacks X0^ and
+// XN/2^ from the packed column, holds every row's mirror.  The pass is in
+// place and the last, so each pair is transformed and stored before the next
+// is loaded.
 __device__ __forceinline__ void unpack_cols0(float2 *__restrict__ Wk, float2 c, float2 cm, int k1) {
   constexpr int NH = 65, H = 64;
   Wk[k1 * NH] = make_float2(0.5f * (c.x + cm.x), 0.5f * (c.y - cm.y));
   Wk[k1 * NH + H] = make_float2(0.5f * (c.y + cm.y), -0.5f * (c.x - cm.x));
 }
 
+template <int NT>
 __device__ __forceinline__ void cols128_fwd_last_store(const float2 *tile, const float2 *s_tw,
                                                        float2 *__restrict__ Wk) {
-  constexpr int NH = 65, S = 16;
-  const int c = threadIdx.x & 63, q = threadIdx.x >> 6;
+  constexpr int NH = 65, S = 16, NPAIR = 512 / NT;
+  const int c = threadIdx.x & 63;
 #pragma unroll
-  for (int pr = 0; pr < 2; ++pr) {  // the mirror pairs, one at a time
+  for (int pp = 0; pp < NPAIR; ++pp) {  // the mirror pairs, one at a time
+    const int idx = (threadIdx.x >> 6) * NPAIR + pp, q = idx >> 1, pr = idx & 1;
     const int ja = pr == 0 ? q : (q == 0 ? 4 : 8 - q);
     const int jb = pr == 0 ? (q == 0 ? 8 : 16 - q) : (q == 0 ? 12 : 8 + q);
     float2 a[8], b[8];
@@ -410,8 +433,6 @@ __device__ __forceinline__ void cols128_fwd_last_store(const float2 *tile, const
   }
 }
 
-// SERVE: the serving form (per-slot iteration counters, the stopping test's
-// residual terms every `check` iterations); the batch form has it.serve = 0.
 // L2 prefetch of the W^ and Gamma that the plane step of (filter k, image
 // img) will read; nothing on its first iteration (neither is read then).
 template <int N, bool SERVE>
@@ -431,11 +452,15 @@ __device__ __forceinline__ void plane_prefetch(const CodeIter &it, const ImgBatc
   }
 }
 
-// pre: the linear unit (img * K + k) whose data to prefetch, or -1.
-template <int N, bool SERVE>
+// SERVE: the serving form (per-slot iteration counters, the stopping test's
+// residual terms every `check` iterations); the batch form has it.serve = 0.
+// NT: threads of the CTA (256; N = 128 also 512).  pre: the linear unit
+// (img * K + k) whose data to prefetch, or -1.
+template <int N, bool SERVE, int NT = HalfPlan<N>::NT>
 __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBatch &b, const float2 *__restrict__ tw,
                                                 int k, int img, float4 *hsmem, int pre = -1) {
-  constexpr int NT = HalfPlan<N>::NT, NH = N / 2 + 1, H = N / 2, Q = H / 2 + 1;
+  static_assert(NT == 256 || (N == 128 && NT == 512), "CTA size");
+  constexpr int NH = N / 2 + 1, H = N / 2, Q = H / 2 + 1;
   constexpr int F = N * NH, P = N * N;
   float2 *tile = reinterpret_cast<float2 *>(hsmem);  // [N][NH]
   float2 *s_tw = tile + F;                           // [N]
@@ -511,7 +536,7 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
 
   // 2. Inverse transforms along k1 (length N) of the N/2 columns, columns 0
   //    and N/2 packed into one by the first pass.
-  cols_inv_first_packed<N>(tile);
+  cols_inv_first_packed<N, NT>(tile);
   half_pass<N, N / 2, HalfPlan<N>::C1, HalfPlan<N>::C0, true, 1, NH, NT, 1>(tile, s_tw);
 
   float *Uk = b.u[img] ? b.u[img] + (size_t)k * P : nullptr;
@@ -523,14 +548,14 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
     // 3-7. The c2r split with the first inverse row pass; the second inverse
     //    row pass, the spatial step and the first forward row pass on
     //    registers; the r2c split with the second forward row pass.
-    rows128_inv_first(tile, s_tw);
-    rows128_spatial(tile, s_tw, Gk, Uk, it.thr, first, resid, wantu, skip_fwd, acc);
+    rows128_inv_first<NT>(tile, s_tw);
+    rows128_spatial<NT>(tile, s_tw, Gk, Uk, it.thr, first, resid, wantu, skip_fwd, acc);
     if (resid) block_sum_terms(acc, it.resid + ((size_t)slot * K + k) * kResidTerms);
     if (skip_fwd) return;
-    rows128_fwd_last(tile, s_tw);
+    rows128_fwd_last<NT>(tile, s_tw);
     // 8-9. Forward transforms along n1, the last pass storing W^.
     half_pass<128, 64, 16, 1, false, 1, NH, NT, 1>(tile, s_tw);
-    cols128_fwd_last_store(tile, s_tw, Wk);
+    cols128_fwd_last_store<NT>(tile, s_tw, Wk);
     return;
   }
 

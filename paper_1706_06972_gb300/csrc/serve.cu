@@ -202,7 +202,7 @@ cudaError_t launch_iteration(ocsc_server *s, int k, int v, const std::vector<int
     } else {
       e = timed(c, OCSC_K_CODE_RESID, [&] { return launch_code_resid(cl.N, b, it, (float)c->rho, q.dn[v], q.xh, c->stream); });
       if (e == cudaSuccess)
-        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(cl.N, it, b, cl.tw, c->stream, cl.plane_ctas ? cl.plane_ctas : 2); });
+        e = timed(c, OCSC_K_CODE_PLANE, [&] { return launch_code_plane(cl.N, it, b, cl.tw, c->stream, cl.plane_ctas ? cl.plane_ctas : 2, cl.plane_ahead != 0, cl.plane_threads); });
     }
     if (e != cudaSuccess) return e;
   }

@@ -722,7 +722,7 @@ def test_autotuned_tiles_do_not_change_results(precision):
     assert t[64]["fold_threads"] in (256, 512) and t[256]["fold_threads"] in (256, 512)
     assert t[256]["spat_cb"] in (8, 16) and t[64]["spat_cb"] == 0
     assert t[64]["plane_ctas"] in (2, 3) and t[256]["plane_ctas"] == 0
-    assert t[64]["plane_ahead"] in (0, 1)
+    assert t[64]["plane_ahead"] in (0, 1) and t[64]["plane_threads"] == 256
     if precision:
         assert t[64]["gram_sc"] in (32, 64, 128)
 
@@ -981,3 +981,37 @@ def test_band_context_rejects_the_whole_update_and_bad_bands():
         full.band_dict_step()
     assert e.value.status == 5
     full.close()
+
+
+def test_plane_kernel_shapes_give_identical_codes():
+    """Every shape of the N = 128 plane kernel (256 threads at 2 or 3 CTAs per
+    SM, 512 threads at 2; with and without the L2 look-ahead) runs the same
+    operations in the same order: pinned one at a time on fresh contexts, the
+    codes and the learned dictionary agree bit for bit.  A bad shape is
+    refused without changing the context."""
+    _need_gpu()
+    import paper_1706_06972_gb300 as pkg
+
+    K, M = 12, 5
+    raw = raw_filters(K, M, 171)
+    imgs = [make_image(100, 100, 1700 + i) for i in range(3)]
+    out = []
+    for threads, ctas in ((256, 2), (256, 3), (512, 2)):
+        for ahead in (0, 1):
+            lr = pkg.OCSC(K, M, 0.5, 1.0, fft_size=128, pad=10, Jz=7, Jd=3, max_batch=3, autotune=0)
+            lr.set_tuning(128, plane_threads=threads, plane_ctas=ctas, plane_ahead=ahead)
+            t = lr.tuning(128)
+            assert (t["plane_threads"], t["plane_ctas"], t["plane_ahead"]) == (threads, ctas, ahead)
+            lr.set_dict(raw, normalize=True)
+            us = lr.code([torch.from_numpy(x).cuda() for x in imgs])
+            lr.update_dict()
+            us2 = lr.code([torch.from_numpy(x).cuda() for x in imgs[:2]])
+            out.append(([u.cpu().numpy() for u in us + us2], lr.get_dict()))
+            with pytest.raises(pkg.OCSCError):
+                lr.set_tuning(128, plane_threads=512, plane_ctas=3)
+            assert lr.tuning(128)["plane_threads"] == threads
+            lr.close()
+    for codes, D in out[1:]:
+        for x, y in zip(out[0][0], codes):
+            assert np.array_equal(x, y)
+        assert np.array_equal(out[0][1], D)
