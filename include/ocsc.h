@@ -112,7 +112,8 @@ typedef struct {
                          FFT kernel in ocsc_code (8 or 16), CTAs per SM of the
                          N <= 128 coding plane kernel (256 threads at 2 or 3,
                          512 threads at 2, each with and without the L2
-                         look-ahead), samples per
+                         look-ahead, or 512-thread persistent CTAs with two
+                         tiles), samples per
                          chunk of the tensor-core contraction (32, 64, 128).  Every
                          candidate performs the same operations in the same
                          order, so results do not depend on the choice.
@@ -254,13 +255,15 @@ typedef struct {
   int plane_ahead;  /* 1: each plane CTA asks L2 for the data of the CTA that
                        runs one residency later (N <= 128); 0: it does not */
   int plane_threads; /* CTA size of the N <= 128 coding plane kernel (256, or
-                        512 at N = 128 with 2 CTAs per SM) */
+                        512 at N = 128: 2 CTAs per SM, or 1 persistent CTA
+                        per SM with two tiles) */
 } ocsc_tuning;
 ocsc_status ocsc_get_tuning(const ocsc_ctx *ctx, int N, ocsc_tuning *out);
 /* Pin tile shapes of FFT size N before (or instead of) the autotuner: every
  * nonzero field is checked and kept, and the autotuner leaves a pinned knob
  * alone.  plane_ctas != 0 sets the plane kernel's shape (plane_threads 256
- * with plane_ctas 2 or 3, or 512 with 2 at N = 128; plane_ahead 0 or 1);
+ * with plane_ctas 2 or 3, or at N = 128 512 with 2, or 512 with 1: persistent
+ * CTAs with two tiles, batch coding only; plane_ahead 0 or 1);
  * fold_threads 256 or 512; spat_cb 8 or 16 for N >= 256 where supported;
  * gram_sc must be 0.  No tile shape changes any result (each performs the
  * same operations in the same order).  OCSC_EINVAL on a bad value (nothing

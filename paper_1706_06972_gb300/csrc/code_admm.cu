@@ -82,6 +82,36 @@ __global__ void __launch_bounds__(NT, MINB)
                                 pre < (int)(gridDim.x * gridDim.y) ? pre : -1);
 }
 
+// N = 128, batch form: persistent CTAs of NT threads, one per SM, each with
+// two tiles.  CTA c takes the units (image, filter) c, c + gridDim.x, ...;
+// while it works on one unit the W^ copies of its next unit fill the other
+// tile (committed at the unit's start, waited for at the next one's).
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) code_plane_persist_kernel(CodeIter it, ImgBatch b, const float2 *__restrict__ tw) {
+  constexpr int N = 128, F = N * (N / 2 + 1), F2 = F / 2;
+  extern __shared__ __align__(16) float4 hsmem[];
+  float2 *s_tw = reinterpret_cast<float2 *>(hsmem);  // [N], then two [N][N/2+1] tiles
+  float2 *tiles[2] = {s_tw + N, s_tw + N + F};
+  load_twiddles<N, NT>(s_tw, tw);  // read after the first unit's first barrier
+  const int K = it.K, total = K * b.n, G = gridDim.x;
+  const bool read_w = it.first == 0;
+  auto w_of = [&](int u) { return it.What + ((size_t)b.slot[u / K] * K + u % K) * F; };
+  int u = blockIdx.x;
+  if (u < total && read_w) {
+    const float4 *src = reinterpret_cast<const float4 *>(w_of(u));
+    float4 *dst = reinterpret_cast<float4 *>(tiles[0]);
+    for (int c = threadIdx.x; c < F2; c += NT) cp_async16(dst + c, src + c);
+    cp_async_commit();
+  }
+  for (int buf = 0; u < total; u += G, buf ^= 1) {
+    const int nu = u + G;
+    const float2 *nw = read_w && nu < total ? w_of(nu) : nullptr;
+    code_plane_body<N, false, NT>(it, b, tw, u % K, u / K, hsmem, -1, tiles[buf], s_tw, read_w, nw,
+                                  tiles[buf ^ 1]);
+    __syncthreads();  // this tile is the copy target two units on
+  }
+}
+
 // Building block: batched real 2D FFT (pairs of planes share one complex FFT).
 template <int N, bool INV>
 __global__ void __launch_bounds__(TileThreads<N>::value)
@@ -222,7 +252,24 @@ int plane_resid_groups(int K) { return K; }
 bool plane_shape_ok(int N, int threads, int ctas) {
   if (N != 64 && N != 128) return false;
   if (threads == 256) return ctas == 2 || ctas == 3;
-  return N == 128 && threads == 512 && ctas == 2;
+  return N == 128 && threads == 512 && (ctas == 2 || ctas == 1);
+}
+
+// The persistent two-tile form (512 threads, one CTA per SM), batch form only.
+static cudaError_t code_plane_persist(const CodeIter &it, const ImgBatch &b, const float2 *tw, cudaStream_t s) {
+  constexpr int N = 128, F = N * (N / 2 + 1);
+  const size_t sm = (size_t)(N + 2 * F) * sizeof(float2);
+  cudaError_t e = set_smem(code_plane_persist_kernel<512>, sm);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, code_plane_persist_kernel<512>, 512, sm);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int total = it.K * b.n, grid = total < per_sm * sms ? total : per_sm * sms;
+  code_plane_persist_kernel<512><<<grid, 512, sm, s>>>(it, b, tw);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, const float2 *tw,
@@ -230,6 +277,11 @@ cudaError_t launch_code_plane(int N, const CodeIter &it, const ImgBatch &b, cons
   if (b.n <= 0) return cudaSuccess;
   if (!plane_shape_ok(N, threads, ctas)) return cudaErrorInvalidValue;
   CodeIter ia = it;
+  if (threads == 512 && ctas == 1) {
+    ia.ahead = 0;
+    if (!it.serve) return code_plane_persist(ia, b, tw, s);
+    ctas = 2;  // the serving form has no persistent variant
+  }
   ia.ahead = ahead ? plane_resident(ctas) : 0;
   if (threads == 512) return code_plane_n<128, 2, 512>(ia, b, tw, s);
   const bool three = ctas == 3;

@@ -391,7 +391,8 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
     s.plane_threads = 256;
     if (c->opts.autotune) {
       // Time the plane kernel's CTA shapes (256 threads at 2 or 3 CTAs per
-      // SM, 512 threads at 2), each with and without the L2 prefetch one
+      // SM, 512 threads at 2, and 512 threads at 1 as persistent CTAs with
+      // two tiles), each with and without the L2 prefetch one
       // residency ahead, as a middle iteration (W^ and Gamma read and
       // written) on this call's slots before its first iteration, which
       // rewrites all of W^ and Gamma it touches: the timing runs read stale
@@ -400,10 +401,11 @@ static ocsc_status enqueue_chunk(ocsc_ctx *c, SizeClass &s, const ImgBatch &bt) 
       tt.first = 0;
       tt.last = 0;
       float best = -1.f;
-      const int shapes[3][2] = {{256, 2}, {256, 3}, {512, 2}};
+      const int shapes[4][2] = {{256, 2}, {256, 3}, {512, 2}, {512, 1}};
       for (const auto &sh : shapes) {
         if (!plane_shape_ok(s.N, sh[0], sh[1])) continue;
         for (int ahead : {0, 1}) {
+          if (sh[1] == 1 && ahead) continue;  // the persistent form has no look-ahead
           const float ms = time_runs(
               c, 2, [&] { return launch_code_plane(s.N, tt, bt, s.tw, c->stream, sh[1], ahead != 0, sh[0]); });
           if (ms < 0.f) return cuda_fail(c, cudaGetLastError(), "autotune coding plane");

@@ -455,15 +455,22 @@ __device__ __forceinline__ void plane_prefetch(const CodeIter &it, const ImgBatc
 // SERVE: the serving form (per-slot iteration counters, the stopping test's
 // residual terms every `check` iterations); the batch form has it.serve = 0.
 // NT: threads of the CTA (256; N = 128 also 512).  pre: the linear unit
-// (img * K + k) whose data to prefetch, or -1.
+// (img * K + k) whose data to prefetch, or -1.  A persistent caller passes
+// its own tile and twiddles (tile_in, s_tw_in: the twiddles already loaded),
+// staged = true when this unit's W^ copies into tile_in were committed by the
+// previous unit, and next_W / next_tile to have this unit commit the next
+// unit's W^ copies (they stay in flight through this unit's work).
 template <int N, bool SERVE, int NT = HalfPlan<N>::NT>
 __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBatch &b, const float2 *__restrict__ tw,
-                                                int k, int img, float4 *hsmem, int pre = -1) {
+                                                int k, int img, float4 *hsmem, int pre = -1,
+                                                float2 *tile_in = nullptr, float2 *s_tw_in = nullptr,
+                                                bool staged = false, const float2 *next_W = nullptr,
+                                                float2 *next_tile = nullptr) {
   static_assert(NT == 256 || (N == 128 && NT == 512), "CTA size");
   constexpr int NH = N / 2 + 1, H = N / 2, Q = H / 2 + 1;
   constexpr int F = N * NH, P = N * N;
-  float2 *tile = reinterpret_cast<float2 *>(hsmem);  // [N][NH]
-  float2 *s_tw = tile + F;                           // [N]
+  float2 *tile = tile_in ? tile_in : reinterpret_cast<float2 *>(hsmem);  // [N][NH]
+  float2 *s_tw = s_tw_in ? s_tw_in : tile + F;                           // [N]
   const int K = it.K;
   const int slot = b.slot[img];
   const int t = b.iter[img];
@@ -482,16 +489,22 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
   constexpr int kPre = 16384, NPRE = P * 4 / kPre;
   if (!first && threadIdx.x < NPRE) prefetch_l2(reinterpret_cast<const char *>(Gk) + threadIdx.x * kPre, kPre);
   if (pre >= 0) plane_prefetch<N, SERVE>(it, b, pre % K, pre / K);
-  load_twiddles<N, NT>(s_tw, tw);
+  if (!s_tw_in) load_twiddles<N, NT>(s_tw, tw);
 
   // 1. Z~-step z = w^ + conj(d) r_p over the half spectrum.  W^ of this
   //    filter comes into the tile (its global layout) by 16-byte asynchronous
   //    copies, all in flight at once; D~ and r are read two bins per 16-byte
   //    load, four loads deep per thread.
   constexpr int F2 = F / 2;  // bin pairs (F is even)
-  if (!first) {
+  if (!first && !staged) {
     const float4 *src = reinterpret_cast<const float4 *>(Wk);
     float4 *dst = reinterpret_cast<float4 *>(tile);
+    for (int c = threadIdx.x; c < F2; c += NT) cp_async16(dst + c, src + c);
+    cp_async_commit();
+  }
+  if (next_W) {
+    const float4 *src = reinterpret_cast<const float4 *>(next_W);
+    float4 *dst = reinterpret_cast<float4 *>(next_tile);
     for (int c = threadIdx.x; c < F2; c += NT) cp_async16(dst + c, src + c);
     cp_async_commit();
   }
@@ -512,7 +525,8 @@ __device__ __forceinline__ void code_plane_body(const CodeIter &it, const ImgBat
         }
       }
       if (c0 == (int)threadIdx.x) {  // the first loads are in flight with the copies of W^
-        cp_async_wait<0>();
+        if (next_W) cp_async_wait<1>();  // the next unit's copies stay in flight
+        else cp_async_wait<0>();
         __syncthreads();
       }
 #pragma unroll

@@ -985,7 +985,8 @@ def test_band_context_rejects_the_whole_update_and_bad_bands():
 
 def test_plane_kernel_shapes_give_identical_codes():
     """Every shape of the N = 128 plane kernel (256 threads at 2 or 3 CTAs per
-    SM, 512 threads at 2; with and without the L2 look-ahead) runs the same
+    SM, 512 threads at 2, each with and without the L2 look-ahead; 512-thread
+    persistent CTAs with two tiles) runs the same
     operations in the same order: pinned one at a time on fresh contexts, the
     codes and the learned dictionary agree bit for bit.  A bad shape is
     refused without changing the context."""
@@ -996,8 +997,8 @@ def test_plane_kernel_shapes_give_identical_codes():
     raw = raw_filters(K, M, 171)
     imgs = [make_image(100, 100, 1700 + i) for i in range(3)]
     out = []
-    for threads, ctas in ((256, 2), (256, 3), (512, 2)):
-        for ahead in (0, 1):
+    for threads, ctas in ((256, 2), (256, 3), (512, 2), (512, 1)):
+        for ahead in ((0,) if ctas == 1 else (0, 1)):
             lr = pkg.OCSC(K, M, 0.5, 1.0, fft_size=128, pad=10, Jz=7, Jd=3, max_batch=3, autotune=0)
             lr.set_tuning(128, plane_threads=threads, plane_ctas=ctas, plane_ahead=ahead)
             t = lr.tuning(128)
