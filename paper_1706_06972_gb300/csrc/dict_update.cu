@@ -588,77 +588,50 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
 // d_i = sum_{k>=i} conj(X_ki) t_k takes K-i, so every thread does K+1 terms.
 // X is staged in shared memory with 16-byte cp.async copies (the per-frequency
 // stride is even, so sources are 16-byte aligned).  Also writes E = d + theta^.
-//
-// The CTAs are persistent: CTA c takes the frequencies c, c + gridDim.x, ...
-// of the launch (nq of them) with two X buffers, the next frequency's copies
-// (and its row vectors, in registers) in flight while the current one is
-// computed, so that the DRAM reads of X run continuously.
 __global__ void dstep_kernel(int K, int F, float rho_eff, const float2 *__restrict__ X,
                              const float2 *__restrict__ yb, const float2 *__restrict__ Vh,
                              const float2 *__restrict__ th, float2 *__restrict__ Dcur,
-                             float2 *__restrict__ E, int p0, int nq) {
+                             float2 *__restrict__ E, int p0) {
   extern __shared__ __align__(16) float2 dsm[];
   const int TS = tri_stride(K);
-  float2 *sr = dsm + 2 * TS;
+  float2 *sX = dsm;
+  float2 *sr = sX + TS;
   float2 *st = sr + K;
-  const int i = threadIdx.x, G = gridDim.x;
-  const float2 zero = make_float2(0.f, 0.f);
-  // Frequency q of the launch is p = p0 + q; X holds frequencies p0 .. only.
-  auto stage = [&](int q, int buf) {
-    const float4 *g4 = reinterpret_cast<const float4 *>(X + (size_t)q * TS);
-    float4 *s4 = reinterpret_cast<float4 *>(dsm + buf * TS);
-    for (int c = i; c < TS / 2; c += blockDim.x) cp_async16(s4 + c, g4 + c);
-    cp_async_commit();
-  };
-  auto rows = [&](int q, float2 &v, float2 &t, float2 &y) {
-    v = t = y = zero;
-    if (i < K) {
-      const size_t o = (size_t)i * F + p0 + q;
-      v = Vh[o];
-      t = th[o];
-      y = yb[o];
+  const int p = blockIdx.x + p0, i = threadIdx.x;  // X holds frequencies p0 .. only
+  const float4 *g4 = reinterpret_cast<const float4 *>(X + (size_t)blockIdx.x * TS);
+  float4 *s4 = reinterpret_cast<float4 *>(sX);
+  for (int c = i; c < TS / 2; c += blockDim.x) cp_async16(s4 + c, g4 + c);
+  float2 thi = make_float2(0.f, 0.f), yi = make_float2(0.f, 0.f);
+  if (i < K) {
+    const size_t o = (size_t)i * F + p;
+    const float2 v = Vh[o];
+    thi = th[o];
+    yi = yb[o];
+    sr[i] = make_float2(v.x - thi.x, v.y - thi.y);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (i < K) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int j = 0; j <= i; ++j) {
+      const float2 x = sX[tri_off(j, K) + i - j], rj = sr[j];
+      acc.x += x.x * rj.x - x.y * rj.y;
+      acc.y += x.x * rj.y + x.y * rj.x;
     }
-  };
-  int q = blockIdx.x;
-  if (q >= nq) return;
-  stage(q, 0);
-  float2 vn, tn, yn;
-  rows(q, vn, tn, yn);
-  for (int buf = 0; q < nq; q += G, buf ^= 1) {
-    const float2 vi = vn, thi = tn, yi = yn;
-    if (q + G < nq) {
-      stage(q + G, buf ^ 1);
-      rows(q + G, vn, tn, yn);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+    st[i] = make_float2(yi.x + rho_eff * acc.x, yi.y + rho_eff * acc.y);
+  }
+  __syncthreads();
+  if (i < K) {
+    const float2 *col = sX + tri_off(i, K) - i;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = i; k < K; ++k) {
+      const float2 x = col[k], tk = st[k];
+      acc.x += x.x * tk.x + x.y * tk.y;
+      acc.y += x.x * tk.y - x.y * tk.x;
     }
-    const float2 *sX = dsm + buf * TS;
-    if (i < K) sr[i] = make_float2(vi.x - thi.x, vi.y - thi.y);
-    __syncthreads();
-    if (i < K) {
-      float2 acc = make_float2(0.f, 0.f);
-      for (int j = 0; j <= i; ++j) {
-        const float2 x = sX[tri_off(j, K) + i - j], rj = sr[j];
-        acc.x += x.x * rj.x - x.y * rj.y;
-        acc.y += x.x * rj.y + x.y * rj.x;
-      }
-      st[i] = make_float2(yi.x + rho_eff * acc.x, yi.y + rho_eff * acc.y);
-    }
-    __syncthreads();
-    if (i < K) {
-      const float2 *col = sX + tri_off(i, K) - i;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int k = i; k < K; ++k) {
-        const float2 x = col[k], tk = st[k];
-        acc.x += x.x * tk.x + x.y * tk.y;
-        acc.y += x.x * tk.y - x.y * tk.x;
-      }
-      const size_t o = (size_t)i * F + p0 + q;
-      Dcur[o] = acc;
-      E[o] = cadd(acc, thi);
-    }
-    __syncthreads();  // this buffer, sr and st are written again two frequencies on
+    const size_t o = (size_t)i * F + p;
+    Dcur[o] = acc;
+    E[o] = cadd(acc, thi);
   }
 }
 
@@ -869,19 +842,11 @@ cudaError_t launch_dstep(int K, int F, float rho_eff, const float2 *X, const flo
                          const float2 *Vh, const float2 *th, float2 *Dcur, float2 *E,
                          cudaStream_t s, int p0, int nF) {
   if (K > 256) return cudaErrorInvalidValue;
-  const size_t sm = (2 * (size_t)tri_stride(K) + 2 * (size_t)K) * sizeof(float2);
+  const size_t sm = ((size_t)tri_stride(K) + 2 * (size_t)K) * sizeof(float2);
   cudaError_t e = cudaFuncSetAttribute(dstep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  const int threads = (K + 31) / 32 * 32, nq = nF ? nF : F;
-  int per_sm = 0, dev = 0, sms = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dstep_kernel, threads, sm);
-  if (e == cudaSuccess) e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  const int grid = nq < per_sm * sms ? nq : per_sm * sms;
-  if (grid <= 0) return cudaSuccess;
-  dstep_kernel<<<grid, threads, sm, s>>>(K, F, rho_eff, X, yb, Vh, th, Dcur, E, p0, nq);
+  const int threads = (K + 31) / 32 * 32;
+  dstep_kernel<<<nF ? nF : F, threads, sm, s>>>(K, F, rho_eff, X, yb, Vh, th, Dcur, E, p0);
   return cudaGetLastError();
 }
 
