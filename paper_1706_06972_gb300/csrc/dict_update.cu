@@ -360,8 +360,11 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
   float4 *y = M + T;                                             // [K] double-float
   float2 *invf = reinterpret_cast<float2 *>(y + K);              // [K] 1 / L_jj, double-float
   float2 *Lb = invf + K;                                         // [3][kPanel][K]
-  float2 *zs = Lb + 3 * kPanel * K;                              // [kFoldChunk][K]
-  float2 *xs = zs + kFoldChunk * K;                              // [kFoldChunk]
+  // Staged codes: rows of Kp = K rounded up to even, 16-byte aligned, so that
+  // a 2 x 2 fold tile reads each pair of codes with one 16-byte load.
+  const int Kp = K + (K & 1);
+  float2 *zs = Lb + 3 * kPanel * K + (K & 1);                    // [kFoldChunk][Kp]
+  float2 *xs = zs + kFoldChunk * Kp;                             // [kFoldChunk]
   float2 *S = reinterpret_cast<float2 *>(M);                     // FP32 sums, stride 2
   float2 *XS = reinterpret_cast<float2 *>(M);                    // X_ic at slot t: XS[2 t]
   // Frequency p of the class's grid (a band context factors rows p0 .. of
@@ -392,7 +395,7 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
     __syncthreads();
     for (int e = tid; e < nb * K; e += kFoldThreads) {
       const int s = e / K, k = e - s * K;
-      cp_async8(zs + s * K + k, a.Zp + ((size_t)(c0 + s) * K + k) * zF + zp);
+      cp_async8(zs + s * Kp + k, a.Zp + ((size_t)(c0 + s) * K + k) * zF + zp);
     }
     for (int s = tid; s < nb; s += kFoldThreads) cp_async8(xs + s, a.xh + (size_t)(c0 + s) * zF + zp);
     cp_async_wait_all();
@@ -413,8 +416,10 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
         const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
         float4 a00 = M[t00], a10 = hi ? M[t00 + 1] : z4, a01 = e01 ? M[t01] : z4, a11 = hi && hj ? M[t01 + 1] : z4;
         for (int s = 0; s < nb; ++s) {
-          const float2 zi0 = zs[s * K + i0], zi1 = hi ? zs[s * K + i0 + 1] : zero;
-          const float2 zj0 = zs[s * K + j0], zj1 = hj ? zs[s * K + j0 + 1] : zero;
+          const float4 zi = *reinterpret_cast<const float4 *>(zs + s * Kp + i0);
+          const float4 zj = *reinterpret_cast<const float4 *>(zs + s * Kp + j0);
+          const float2 zi0 = make_float2(zi.x, zi.y), zi1 = hi ? make_float2(zi.z, zi.w) : zero;
+          const float2 zj0 = make_float2(zj.x, zj.y), zj1 = hj ? make_float2(zj.z, zj.w) : zero;
           df_acc_cconjmul(a00, zi0, zj0);
           df_acc_cconjmul(a10, zi1, zj0);
           df_acc_cconjmul(a01, zi0, zj1);
@@ -428,8 +433,10 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
         float2 a00 = S[2 * t00], a10 = hi ? S[2 * (t00 + 1)] : zero, a01 = e01 ? S[2 * t01] : zero;
         float2 a11 = hi && hj ? S[2 * (t01 + 1)] : zero;
         for (int s = 0; s < nb; ++s) {
-          const float2 zi0 = zs[s * K + i0], zi1 = hi ? zs[s * K + i0 + 1] : zero;
-          const float2 zj0 = zs[s * K + j0], zj1 = hj ? zs[s * K + j0 + 1] : zero;
+          const float4 zi = *reinterpret_cast<const float4 *>(zs + s * Kp + i0);
+          const float4 zj = *reinterpret_cast<const float4 *>(zs + s * Kp + j0);
+          const float2 zi0 = make_float2(zi.x, zi.y), zi1 = hi ? make_float2(zi.z, zi.w) : zero;
+          const float2 zj0 = make_float2(zj.x, zj.y), zj1 = hj ? make_float2(zj.z, zj.w) : zero;
           fold_mac(a00, zi0, zj0);
           fold_mac(a10, zi1, zj0);
           fold_mac(a01, zi0, zj1);
@@ -446,9 +453,9 @@ __global__ void __launch_bounds__(kFoldThreads, 512 / kFoldThreads) fold_factor_
       const int i = tid + m * kFoldThreads;
       if (i < K) {
         if (DF)
-          for (int s = 0; s < nb; ++s) df_acc_cmulc(sbd[m], xs[s], zs[s * K + i]);
+          for (int s = 0; s < nb; ++s) df_acc_cmulc(sbd[m], xs[s], zs[s * Kp + i]);
         else
-          for (int s = 0; s < nb; ++s) sb[m] = cadd(sb[m], cmulc(xs[s], zs[s * K + i]));
+          for (int s = 0; s < nb; ++s) sb[m] = cadd(sb[m], cmulc(xs[s], zs[s * Kp + i]));
       }
     }
   }
@@ -817,7 +824,7 @@ __global__ void dict_norms_kernel(int K, int F, const float2 *__restrict__ Dh, f
 
 size_t fold_smem_bytes(int K) {
   return (size_t)(tri_size(K) + K) * sizeof(float4) + (size_t)(1 + 3 * kPanel) * K * sizeof(float2) +
-         (size_t)kFoldChunk * K * sizeof(float2) + kFoldChunk * sizeof(float2);
+         ((size_t)kFoldChunk * (K + (K & 1)) + (K & 1)) * sizeof(float2) + kFoldChunk * sizeof(float2);
 }
 
 // threads: 256 or 512 (CTA size of the per-frequency factorisation; every
