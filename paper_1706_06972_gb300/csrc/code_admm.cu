@@ -59,14 +59,12 @@ __global__ void __launch_bounds__(TileThreads<N>::value)
   }
 }
 
-// r_p = (x~(p) - sum_k D~_k(p) W^_k(p)) / (rho + |d_p|^2); block (32, 8), block row y
-// for the images 2y and 2y + 1.
-__global__ void __launch_bounds__(256, 3) code_resid_kernel(int K, int F, float rho, int first, int serve, ImgBatch b,
+// r_p = (x~(p) - sum_k D~_k(p) W^_k(p)) / (rho + |d_p|^2); block (32, 8).
+__global__ void code_resid_kernel(int K, int F, float rho, int first, int serve, ImgBatch b,
                                   const float2 *__restrict__ Dh, const float *__restrict__ dn,
                                   const float2 *__restrict__ xh, const float2 *__restrict__ What,
                                   float2 *__restrict__ r) {
-  const int img = 2 * blockIdx.y, img2 = img + 1 < b.n ? img + 1 : -1;  // a pair of images per block row
-  code_resid_body(K, F, rho, first, serve, b, Dh, dn, xh, What, r, blockIdx.x, img, img2, threadIdx.x, threadIdx.y);
+  code_resid_body(K, F, rho, first, serve, b, Dh, dn, xh, What, r, blockIdx.x, blockIdx.y, threadIdx.x, threadIdx.y);
 }
 
 // One fused ADMM iteration for filter k of one sample (grid: K x images).
@@ -220,7 +218,7 @@ cudaError_t launch_code_resid(int N, const ImgBatch &b, const CodeIter &it, floa
                               const float2 *xh, cudaStream_t s) {
   if (b.n <= 0) return cudaSuccess;
   const int F = N * (N / 2 + 1);
-  dim3 grid((F + kResidBins - 1) / kResidBins, (b.n + 1) / 2), block(32, 8);
+  dim3 grid((F + kResidBins - 1) / kResidBins, b.n), block(32, 8);
   code_resid_kernel<<<grid, block, 0, s>>>(it.K, F, rho, it.first, it.serve, b, it.Dh, dn, xh, it.What, it.r);
   return cudaGetLastError();
 }

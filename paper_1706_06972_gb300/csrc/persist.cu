@@ -63,7 +63,7 @@ __device__ __forceinline__ int units_of(const PersistClass &c, int phase, int t,
   const int npairs = (K + 1) / 2;
   if (c.N <= 128) {
     const int F = c.N * (c.N / 2 + 1);
-    if (phase == 0) return (c.n + 1) / 2 * ((F + kResidBins - 1) / kResidBins);
+    if (phase == 0) return c.n * ((F + kResidBins - 1) / kResidBins);
     if (phase == 1) return c.n * K;
     return 0;
   }
@@ -79,8 +79,7 @@ __device__ __noinline__ void small_unit(const PersistArgs &a, const PersistClass
                                            int phase, int v, float4 *psm) {
   constexpr int F = N * (N / 2 + 1), NB = (F + kResidBins - 1) / kResidBins;
   if (phase == 0) {
-    const int img = c.n0 + 2 * (v / NB), img2 = img + 1 < c.n0 + c.n ? img + 1 : -1;
-    code_resid_body(it.K, F, it.rho, it.first, 0, a.b, it.Dh, it.dn, it.xh, it.What, it.r, v % NB, img, img2,
+    code_resid_body(it.K, F, it.rho, it.first, 0, a.b, it.Dh, it.dn, it.xh, it.What, it.r, v % NB, c.n0 + v / NB,
                     threadIdx.x & 31, threadIdx.x >> 5);
   } else {
     code_plane_body<N, false, 256>(it, a.b, c.tw, v % it.K, c.n0 + v / it.K, psm);

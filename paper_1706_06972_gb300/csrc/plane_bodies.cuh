@@ -40,67 +40,55 @@ __device__ __forceinline__ void block_sum_terms(float (&v)[kResidTerms], float *
 }
 
 // r_p = (x~(p) - sum_k D~_k(p) W^_k(p)) / (rho + |d_p|^2) for the 64 bins
-// pb * 64 .. of image img and, when img2 >= 0, of image img2 too (F is
-// even); 256 threads as (32 bin pairs) x (8 filter lanes): lane ty sums the
-// filters k = ty, ty + 8, ... of two adjacent bins from 16-byte loads, each
-// D~ load serving both images, and the lanes' sums are added in order.
+// pb * 64 .. of image img (F is even); 256 threads as (32 bin pairs) x
+// (8 filter lanes): lane ty sums the filters k = ty, ty + 8, ... of two
+// adjacent bins from 16-byte loads, and the lanes' sums are added in order.
 constexpr int kResidBins = 64;
 
 __device__ __forceinline__ void code_resid_body(int K, int F, float rho, int first, int serve, const ImgBatch &b,
                                                 const float2 *__restrict__ Dh, const float *__restrict__ dn,
                                                 const float2 *__restrict__ xh, const float2 *__restrict__ What,
-                                                float2 *__restrict__ r, int pb, int img, int img2, int tx, int ty) {
-  __shared__ float4 part[2][8][33];
+                                                float2 *__restrict__ r, int pb, int img, int tx, int ty) {
+  __shared__ float4 part[8][33];
   const int F2 = F / 2, q = pb * 32 + tx;  // bins 2q, 2q + 1
-  const bool two = img2 >= 0;
-  const int slot = b.slot[img], slot2 = two ? b.slot[img2] : slot;
-  const bool use = !(serve ? b.iter[img] == 0 : first != 0);
-  const bool use2 = two && !(serve ? b.iter[img2] == 0 : first != 0);
-  float2 s0 = make_float2(0.f, 0.f), s1 = s0, t0 = s0, t1 = s0;
-  if ((use || use2) && q < F2) {
+  const int slot = b.slot[img];
+  const bool is_first = serve ? b.iter[img] == 0 : first != 0;
+  float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
+  if (!is_first && q < F2) {
     const float4 *w = reinterpret_cast<const float4 *>(What + (size_t)slot * K * F);
-    const float4 *w2 = reinterpret_cast<const float4 *>(What + (size_t)slot2 * K * F);
     const float4 *D = reinterpret_cast<const float4 *>(Dh);
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     constexpr int U = 4;  // loads in flight per operand
     for (int k0 = ty; k0 < K; k0 += 8 * U) {
-      float4 d[U], v[U], v2[U];
+      float4 d[U], v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int k = k0 + 8 * u;
         if (k < K) {
           d[u] = D[(size_t)k * F2 + q];
-          v[u] = use ? w[(size_t)k * F2 + q] : zero;
-          v2[u] = use2 ? w2[(size_t)k * F2 + q] : zero;
+          v[u] = w[(size_t)k * F2 + q];
         }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (k0 + 8 * u >= K) break;
-        const float2 da = make_float2(d[u].x, d[u].y), db = make_float2(d[u].z, d[u].w);
-        s0 = cadd(s0, cmul(da, make_float2(v[u].x, v[u].y)));
-        s1 = cadd(s1, cmul(db, make_float2(v[u].z, v[u].w)));
-        t0 = cadd(t0, cmul(da, make_float2(v2[u].x, v2[u].y)));
-        t1 = cadd(t1, cmul(db, make_float2(v2[u].z, v2[u].w)));
+        s0 = cadd(s0, cmul(make_float2(d[u].x, d[u].y), make_float2(v[u].x, v[u].y)));
+        s1 = cadd(s1, cmul(make_float2(d[u].z, d[u].w), make_float2(v[u].z, v[u].w)));
       }
     }
-    if (!use) s0 = s1 = make_float2(0.f, 0.f);
   }
-  part[0][ty][tx] = make_float4(s0.x, s0.y, s1.x, s1.y);
-  part[1][ty][tx] = make_float4(t0.x, t0.y, t1.x, t1.y);
+  part[ty][tx] = make_float4(s0.x, s0.y, s1.x, s1.y);
   __syncthreads();
-  if (ty < (two ? 2 : 1) && q < F2) {  // lane 0 finishes img, lane 1 img2
-    const int sl = ty == 0 ? slot : slot2;
-    float4 t = part[ty][0][tx];
+  if (ty == 0 && q < F2) {
+    float4 t = part[0][tx];
 #pragma unroll
     for (int y = 1; y < 8; ++y) {
-      const float4 u = part[ty][y][tx];
+      const float4 u = part[y][tx];
       t = make_float4(t.x + u.x, t.y + u.y, t.z + u.z, t.w + u.w);
     }
-    const float4 x = reinterpret_cast<const float4 *>(xh + (size_t)sl * F)[q];
+    const float4 x = reinterpret_cast<const float4 *>(xh + (size_t)slot * F)[q];
     const float2 dd = reinterpret_cast<const float2 *>(dn)[q];
     const float i0 = 1.0f / (rho + dd.x), i1 = 1.0f / (rho + dd.y);
-    reinterpret_cast<float4 *>(r + (size_t)sl * F)[q] =
+    reinterpret_cast<float4 *>(r + (size_t)slot * F)[q] =
         make_float4((x.x - t.x) * i0, (x.y - t.y) * i0, (x.z - t.z) * i1, (x.w - t.w) * i1);
   }
 }
